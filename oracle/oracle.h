@@ -1,0 +1,107 @@
+/*
+ * oracle.h -- plain, slow, FP64 CPU oracle for time-dependent multigroup
+ * fixed-source Monte Carlo neutron transport (track-length flux tally).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or execute this code: only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark use it.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * What it follows (the paper gives prose, two listings and no equations):
+ *  - "MC/DC on CPUs": a fixed-source run loops over particles and transports
+ *    each one until its history ends by a physical event (capture, time or
+ *    space boundary), a simulation event (time census) or a variance
+ *    reduction event.
+ *  - Figure "jitfunctions" (move_particle): the particle record holds
+ *    x, y, z, ux, uy, uz and speed v; a move of length d advances the
+ *    position by u*d and the time by d/v.
+ *  - Figure "forcpuvgpu": a tally bin index is found from the particle's
+ *    location (loc2index) and the score is added to that bin.
+ *  - "Monte Carlo Neutron Transport and MC/DC": hash-based random numbers
+ *    make a run replicable history by history.
+ * Everything else (sampling laws, the counter-based generator, event order,
+ * tie rules, normalisation, batch statistics, weight windows) is the
+ * textbook analog Monte Carlo loop (Lewis & Miller, cited in that section)
+ * in the readings listed at the top of each function.
+ */
+#ifndef MCDC_ORACLE_H
+#define MCDC_ORACLE_H
+#include <stdint.h>
+
+enum { ORC_BC_VACUUM = 0, ORC_BC_REFLECT = 1 };
+enum { ORC_SRC_ISOTROPIC = 0, ORC_SRC_BEAM = 1 };
+enum { ORC_EV_COLLISION = 0, ORC_EV_SURFACE = 1, ORC_EV_CENSUS = 2 };
+enum { ORC_END_ABSORBED = 1, ORC_END_LEAKED = 2, ORC_END_CENSUSED = 3,
+       ORC_END_ROULETTE = 4 };
+
+/* One problem: mesh, materials, source, time grid, optional weight windows. */
+typedef struct {
+    int32_t n[3];          /* cells along x, y, z                                */
+    double origin[3];      /* low corner                                         */
+    double width[3];       /* cell width; an axis with n==1 and width<=0 or inf
+                              is unbounded (no faces), e.g. y and z of a slab    */
+    const uint8_t *material;   /* [nz][ny][nx] material id                       */
+    int32_t bc[6];         /* -x,+x,-y,+y,-z,+z : ORC_BC_*                       */
+
+    int32_t n_mat, n_grp;
+    const double *sigma_t;     /* [M][G] total cross section (1/cm)              */
+    const double *sigma_s;     /* [M][G] total scattering cross section          */
+    const double *transfer;    /* [M][G][G] P(g -> g') given a scatter in g      */
+    const double *speed;       /* [G] particle speed                             */
+
+    double src_lo[3], src_hi[3];   /* uniform box                                */
+    int32_t src_kind;              /* ORC_SRC_*                                  */
+    double src_dir[3];             /* beam direction (unit)                      */
+    const double *src_pdf;         /* [G] source group probabilities             */
+    double src_t0, src_t1;         /* birth time uniform in [t0, t1]             */
+
+    int32_t n_tbin;            /* T; 0 = steady state                            */
+    const double *edges;       /* [T+1] time-bin edges (census times)            */
+
+    const double *ww_lower;    /* [cells][G][max(T,1)] or NULL (analog)          */
+    double ww_upper_ratio;     /* w_U = ratio * w_L                              */
+    double ww_survival_ratio;  /* w_S = ratio * w_L                              */
+    int32_t ww_nmax;           /* split cap                                      */
+
+    int32_t region_lo[3], region_hi[3];  /* cell box of the scalar tally [lo,hi) */
+} orc_problem;
+
+typedef struct {
+    uint64_t histories, segments, collisions, crossings, census;
+    uint64_t absorbed, leaked, censused, splits, children;
+    uint64_t roulette_killed, roulette_survived;
+    double w_source, w_absorbed, w_leaked, w_censused;
+} orc_counts;
+
+/* Summary of one primary particle (serial 0) of one history. */
+typedef struct {
+    uint64_t hid;
+    int32_t end;        /* ORC_END_* */
+    int32_t g;
+    uint32_t ctr;       /* counter value after the last draw */
+    uint32_t n_seg;
+    uint32_t n_col;
+    uint32_t n_cross;
+    double x, y, z, t, w;
+} orc_record;
+
+/* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Two 32-bit words -> double in (0, 1]. */
+double orc_uniform(uint32_t hi, uint32_t lo);
+/* (xi_mu, xi_phi) -> isotropic unit vector. */
+void orc_isotropic(double xi_mu, double xi_phi, double u[3]);
+
+/* Full run: histories [offset, offset+n) split into n_batches contiguous
+ * batches; mean/relerr are [cells][G][max(T,1)]; scalar = {mean, relerr} of
+ * the region sum.  Returns 0, or a negative value on invalid input. */
+int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
+            uint64_t offset, int32_t n_batches, int32_t n_threads,
+            double *mean, double *relerr, double *sum1, double *sum2,
+            double *scalar, orc_counts *counts);
+
+/* Replays the listed histories one by one and summarises each primary. */
+int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
+              int64_t n, orc_record *out);
+
+#endif

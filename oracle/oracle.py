@@ -1,0 +1,198 @@
+"""ctypes wrapper around the C oracle (``liborc.so``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+CPU-baseline leg of the benchmark, never by the product path.  It imports
+nothing from the CUDA package; problems are passed as any object carrying the
+attributes of a problem description (mesh, materials, source, time grid).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcProblem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32 * 3), ("origin", C.c_double * 3), ("width", C.c_double * 3),
+        ("material", C.c_void_p), ("bc", C.c_int32 * 6),
+        ("n_mat", C.c_int32), ("n_grp", C.c_int32),
+        ("sigma_t", C.c_void_p), ("sigma_s", C.c_void_p), ("transfer", C.c_void_p),
+        ("speed", C.c_void_p),
+        ("src_lo", C.c_double * 3), ("src_hi", C.c_double * 3), ("src_kind", C.c_int32),
+        ("src_dir", C.c_double * 3), ("src_pdf", C.c_void_p),
+        ("src_t0", C.c_double), ("src_t1", C.c_double),
+        ("n_tbin", C.c_int32), ("edges", C.c_void_p),
+        ("ww_lower", C.c_void_p), ("ww_upper_ratio", C.c_double),
+        ("ww_survival_ratio", C.c_double), ("ww_nmax", C.c_int32),
+        ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
+    ]
+
+
+class OrcCounts(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in (
+        "histories", "segments", "collisions", "crossings", "census", "absorbed", "leaked",
+        "censused", "splits", "children", "roulette_killed", "roulette_survived")] + [
+        (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused")]
+
+
+RECORD_DTYPE = np.dtype([
+    ("hid", np.uint64), ("end", np.int32), ("g", np.int32), ("ctr", np.uint32),
+    ("n_seg", np.uint32), ("n_col", np.uint32), ("n_cross", np.uint32),
+    ("x", np.float64), ("y", np.float64), ("z", np.float64), ("t", np.float64),
+    ("w", np.float64)], align=True)
+
+END_ABSORBED, END_LEAKED, END_CENSUSED, END_ROULETTE = 1, 2, 3, 4
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # an alternative build of the oracle (e.g. one with a planted mistake)
+        path = os.environ.get("MCDC_ORACLE_LIB") or _build.build()
+        L = C.CDLL(path)
+        L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_uniform.argtypes = [C.c_uint32, C.c_uint32]
+        L.orc_uniform.restype = C.c_double
+        L.orc_isotropic.argtypes = [C.c_double, C.c_double, C.c_void_p]
+        L.orc_run.argtypes = [C.POINTER(OrcProblem), C.c_uint64, C.c_uint64, C.c_uint64,
+                              C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.POINTER(OrcCounts)]
+        L.orc_run.restype = C.c_int
+        L.orc_trace.argtypes = [C.POINTER(OrcProblem), C.c_uint64, C.c_void_p, C.c_int64,
+                                C.c_void_p]
+        L.orc_trace.restype = C.c_int
+        if hasattr(L, "orc_mlp_forward"):
+            _bind_mlp(L)
+        _lib = L
+    return _lib
+
+
+def _bind_mlp(L):
+    L.orc_mlp_forward.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_void_p]
+    L.orc_mlp_loss_grad.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_adam_step.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64]
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Keep:
+    """Holds the arrays a C struct points into for the length of a call."""
+
+    def __init__(self):
+        self.arrays = []
+
+    def ptr(self, a):
+        self.arrays.append(a)
+        return a.ctypes.data
+
+
+def _struct(prob, ww=None, keep=None):
+    s = OrcProblem()
+    s.n[:] = list(prob.n)
+    s.origin[:] = [float(v) for v in prob.origin]
+    s.width[:] = [float(v) for v in prob.width]
+    mat = np.ascontiguousarray(prob.material, dtype=np.uint8)
+    s.material = keep.ptr(mat)
+    s.bc[:] = list(prob.bc)
+    st = _f64(prob.sigma_t)
+    s.n_mat, s.n_grp = st.shape
+    s.sigma_t = keep.ptr(st)
+    s.sigma_s = keep.ptr(_f64(prob.sigma_s))
+    s.transfer = keep.ptr(_f64(prob.transfer))
+    s.speed = keep.ptr(_f64(prob.speed))
+    s.src_lo[:] = [float(v) for v in prob.src_lo]
+    s.src_hi[:] = [float(v) for v in prob.src_hi]
+    s.src_kind = int(prob.src_kind)
+    s.src_dir[:] = [float(v) for v in prob.src_dir]
+    s.src_pdf = keep.ptr(_f64(prob.src_pdf))
+    s.src_t0, s.src_t1 = float(prob.src_t0), float(prob.src_t1)
+    if prob.edges is None:
+        s.n_tbin, s.edges = 0, None
+    else:
+        e = _f64(prob.edges)
+        s.n_tbin, s.edges = len(e) - 1, keep.ptr(e)
+    if ww is not None:
+        s.ww_lower = keep.ptr(_f64(ww["lower"]))
+        s.ww_upper_ratio = float(ww.get("upper_ratio", 5.0))
+        s.ww_survival_ratio = float(ww.get("survival_ratio", 2.5))
+        s.ww_nmax = int(ww.get("nmax", 16))
+    s.region_lo[:] = list(prob.region_lo)
+    s.region_hi[:] = list(prob.region_hi)
+    return s
+
+
+def n_bins(prob):
+    T = 1 if prob.edges is None else len(prob.edges) - 1
+    return int(np.prod(prob.n)) * int(np.asarray(prob.sigma_t).shape[1]) * T
+
+
+def tally_shape(prob):
+    nx, ny, nz = prob.n
+    T = 1 if prob.edges is None else len(prob.edges) - 1
+    return (nz, ny, nx, int(np.asarray(prob.sigma_t).shape[1]), T)
+
+
+def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None):
+    """Runs histories [offset, offset+n); returns mean/relerr/sums shaped
+    [nz, ny, nx, G, T], the region scalar and the event counts."""
+    L = lib()
+    keep = _Keep()
+    s = _struct(prob, ww, keep)
+    nb = n_bins(prob)
+    mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
+    scalar = np.zeros(2)
+    cnt = OrcCounts()
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = L.orc_run(C.byref(s), int(n), int(seed), int(offset), int(batches), int(threads),
+                   mean.ctypes.data, rel.ctypes.data, s1.ctypes.data, s2.ctypes.data,
+                   scalar.ctypes.data, C.byref(cnt))
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    shp = tally_shape(prob)
+    counts = {k: getattr(cnt, k) for k, _ in OrcCounts._fields_}
+    return {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "sum1": s1.reshape(shp),
+            "sum2": s2.reshape(shp), "scalar": (scalar[0], scalar[1]), "counts": counts,
+            "threads": int(threads)}
+
+
+def trace(prob, seed, hids, ww=None):
+    """Per-history summary of the primary particle of each listed history."""
+    L = lib()
+    keep = _Keep()
+    s = _struct(prob, ww, keep)
+    h = np.ascontiguousarray(hids, dtype=np.uint64)
+    out = np.zeros(len(h), dtype=RECORD_DTYPE)
+    rc = L.orc_trace(C.byref(s), int(seed), h.ctypes.data, len(h), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return out
+
+
+def philox(ctr, key):
+    L = lib()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    L.orc_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return o
+
+
+def uniform(hi, lo):
+    return lib().orc_uniform(int(hi), int(lo))
+
+
+def isotropic(xi_mu, xi_phi):
+    u = np.zeros(3)
+    lib().orc_isotropic(float(xi_mu), float(xi_phi), u.ctypes.data)
+    return u

@@ -1,0 +1,549 @@
+/*
+ * transport.c -- oracle particle tracker, FP64, one history at a time.
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Readings of the paper used here (it states the loop in prose only):
+ *  R1 random numbers: block = Philox4x32-10(key = seed, counter = (event
+ *     counter, particle serial, history id low, history id high)); one
+ *     double in (0,1] from words (0,1), a second from words (2,3).
+ *  R2 draws: source uses counters 0..3 (x,y | z,group | mu,phi | t); each
+ *     flight uses one block (distance to collision); a collision uses two
+ *     blocks (absorb-or-scatter, new group | mu, phi); a roulette one.
+ *  R3 the distance to collision is sampled afresh at every flight (the
+ *     exponential law is memoryless), so every flight is the same step.
+ *  R4 event = nearest of collision, mesh surface, time census; exact ties
+ *     go census first, then surface, then collision; among axes the lowest
+ *     index wins.
+ *  R5 a census at the last time edge ends the history ("censused"); the
+ *     time coordinate is set to the edge.
+ *  R6 a surface event snaps the crossed coordinate onto the face; leaving
+ *     the mesh through a vacuum face ends the history ("leaked"), through a
+ *     reflecting face flips that direction cosine.
+ *  R7 tally: track length w*d into bin (cell, group, time bin); the output
+ *     is the sum over histories divided by (N * cell volume).
+ *  R8 batches: histories split into B contiguous batches (the first N%B
+ *     batches one history longer); per-bin variance of the mean from the
+ *     spread of the batch means.
+ *  R9 weight windows at collisions and cell crossings: above w_U split into
+ *     n = min(ceil(w/w_U), nmax) equal copies, below w_L roulette with
+ *     survival probability w/w_S to weight w_S.  Children get a new serial
+ *     hashed from (serial, counter, child index) and restart their counter.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+/* ---- the particle record (Figure "jitfunctions" plus group, weight,
+ *      cell, time bin and random-number state) ------------------------ */
+typedef struct {
+    double x, y, z;        /* position                                     */
+    double ux, uy, uz;     /* direction cosines                            */
+    double v;              /* speed of the current group                   */
+    double t;              /* time                                         */
+    double w;              /* statistical weight                           */
+    int32_t g;             /* energy group                                 */
+    int32_t idx[3];        /* mesh cell (i, j, k)                          */
+    int32_t tbin;          /* current time bin                             */
+    uint32_t serial;       /* particle id inside the history (0 = primary) */
+    uint32_t ctr;          /* event counter of the random stream           */
+    uint32_t n_seg, n_col, n_cross;
+} part;
+
+typedef struct {
+    const orc_problem *p;
+    double *scat_ratio;    /* [M][G] sigma_s / sigma_t                      */
+    double *cdf;           /* [M][G][G] cumulative transfer probabilities   */
+    double *src_cdf;       /* [G]                                           */
+    int bounded[3];
+    int64_t n_cells;
+    int32_t T1;            /* time slots per (cell, group) = max(T, 1)       */
+    int64_t n_bins;
+    double volume;
+} tables;
+
+typedef struct {
+    part *items;
+    int64_t size, cap;
+} stack;
+
+static void push(stack *s, const part *P)
+{
+    if (s->size == s->cap) {
+        s->cap = s->cap ? 2 * s->cap : 64;
+        s->items = (part *)realloc(s->items, (size_t)s->cap * sizeof(part));
+    }
+    s->items[s->size++] = *P;
+}
+
+/* ---- random numbers (R1) ------------------------------------------- */
+typedef struct { double a, b; } pair;
+
+static pair draw(uint64_t seed, uint64_t hid, part *P)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { P->ctr, P->serial, (uint32_t)hid, (uint32_t)(hid >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    P->ctr += 1;
+    pair r = { orc_uniform(out[0], out[1]), orc_uniform(out[2], out[3]) };
+    return r;
+}
+
+/* ---- geometry ------------------------------------------------------- */
+static int axis_bounded(const orc_problem *p, int a)
+{
+    return !(p->n[a] == 1 && (!(p->width[a] > 0.0) || isinf(p->width[a])));
+}
+
+static double *pos(part *P, int a) { return a == 0 ? &P->x : (a == 1 ? &P->y : &P->z); }
+static double *dir(part *P, int a) { return a == 0 ? &P->ux : (a == 1 ? &P->uy : &P->uz); }
+
+/* loc2index (Figure "forcpuvgpu"): cell of a position; clamped so a point
+ * on the outer face belongs to the last cell. */
+static int32_t loc2index_axis(const orc_problem *p, const tables *tb, int a, double x)
+{
+    if (!tb->bounded[a]) return 0;
+    double f = floor((x - p->origin[a]) / p->width[a]);
+    int32_t i = (int32_t)f;
+    if (f < 0.0) i = 0;
+    if (f > (double)(p->n[a] - 1)) i = p->n[a] - 1;
+    return i;
+}
+
+static int64_t cell_of(const orc_problem *p, const part *P)
+{
+    return ((int64_t)P->idx[2] * p->n[1] + P->idx[1]) * p->n[0] + P->idx[0];
+}
+
+/* face coordinate of the cell side that a particle moving with sign s meets */
+static double face(const orc_problem *p, int a, int32_t i, double u)
+{
+    int32_t k = (u > 0.0) ? i + 1 : i;
+    return p->origin[a] + (double)k * p->width[a];
+}
+
+/* ---- move_particle (Figure "jitfunctions") --------------------------- */
+static void move_particle(part *P, double distance)
+{
+    P->x += P->ux * distance;
+    P->y += P->uy * distance;
+    P->z += P->uz * distance;
+    P->t += distance / P->v;
+}
+
+/* first k with xi <= cdf[k]; cdf is flat at 1.0 after its last rise */
+static int32_t sample_cdf(const double *cdf, int32_t n, double xi)
+{
+    for (int32_t k = 0; k < n; ++k)
+        if (xi <= cdf[k]) return k;
+    return n - 1;
+}
+
+static void build_cdf(const double *pdf, int32_t n, double *cdf)
+{
+    double acc = 0.0;
+    int32_t last = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        acc += pdf[k];
+        cdf[k] = acc;
+        if (pdf[k] > 0.0) last = k;
+    }
+    for (int32_t k = last; k < n; ++k) cdf[k] = 1.0;
+}
+
+/* ---- source (R2: counters 0..3) -------------------------------------- */
+static part source_particle(const orc_problem *p, const tables *tb,
+                            uint64_t seed, uint64_t hid)
+{
+    part P;
+    memset(&P, 0, sizeof P);
+    P.serial = 0;
+    P.ctr = 0;
+    pair r0 = draw(seed, hid, &P);   /* x, y        */
+    pair r1 = draw(seed, hid, &P);   /* z, group    */
+    pair r2 = draw(seed, hid, &P);   /* mu, phi     */
+    pair r3 = draw(seed, hid, &P);   /* t           */
+    P.x = p->src_lo[0] + r0.a * (p->src_hi[0] - p->src_lo[0]);
+    P.y = p->src_lo[1] + r0.b * (p->src_hi[1] - p->src_lo[1]);
+    P.z = p->src_lo[2] + r1.a * (p->src_hi[2] - p->src_lo[2]);
+    P.g = sample_cdf(tb->src_cdf, p->n_grp, r1.b);
+    if (p->src_kind == ORC_SRC_BEAM) {
+        P.ux = p->src_dir[0]; P.uy = p->src_dir[1]; P.uz = p->src_dir[2];
+    } else {
+        double u[3];
+        orc_isotropic(r2.a, r2.b, u);
+        P.ux = u[0]; P.uy = u[1]; P.uz = u[2];
+    }
+    P.t = p->src_t0 + r3.a * (p->src_t1 - p->src_t0);
+    P.v = p->speed[P.g];
+    P.w = 1.0;
+    P.idx[0] = loc2index_axis(p, tb, 0, P.x);
+    P.idx[1] = loc2index_axis(p, tb, 1, P.y);
+    P.idx[2] = loc2index_axis(p, tb, 2, P.z);
+    P.tbin = 0;
+    if (p->n_tbin > 0)
+        while (P.tbin < p->n_tbin && p->edges[P.tbin + 1] <= P.t) P.tbin += 1;
+    return P;
+}
+
+/* ---- weight windows (R9) ------------------------------------------- */
+/* Returns 1 if the particle survives.  Children go on the stack. */
+static int weight_window(const orc_problem *p, const tables *tb, uint64_t seed,
+                         uint64_t hid, part *P, stack *bank, orc_counts *c)
+{
+    if (p->ww_lower == NULL) return 1;
+    double wl = p->ww_lower[(cell_of(p, P) * p->n_grp + P->g) * tb->T1
+                            + (p->n_tbin > 0 ? P->tbin : 0)];
+    if (!(wl > 0.0)) return 1;
+    double wu = p->ww_upper_ratio * wl;
+    if (P->w > wu) {
+        double nd = ceil(P->w / wu);
+        int32_t n = nd > (double)p->ww_nmax ? p->ww_nmax : (int32_t)nd;
+        if (n > 1) {
+            double wc = P->w / (double)n;
+            uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+            for (int32_t k = 1; k < n; ++k) {
+                uint32_t ctr[4] = { 0xFFFFFFFFu, P->serial, P->ctr, (uint32_t)k };
+                uint32_t out[4];
+                orc_philox4x32_10(ctr, key, out);
+                part C = *P;
+                C.w = wc;
+                C.serial = out[0];
+                C.ctr = 0;
+                C.n_seg = C.n_col = C.n_cross = 0;
+                push(bank, &C);
+            }
+            P->w = wc;
+            c->splits += 1;
+            c->children += (uint64_t)(n - 1);
+        }
+        return 1;
+    }
+    if (P->w < wl) {
+        double ws = p->ww_survival_ratio * wl;
+        pair r = draw(seed, hid, P);
+        if (r.a < P->w / ws) {
+            P->w = ws;
+            c->roulette_survived += 1;
+            return 1;
+        }
+        c->roulette_killed += 1;
+        return 0;
+    }
+    return 1;
+}
+
+/* ---- one particle until its history branch ends -------------------- */
+static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
+                         uint64_t hid, part *P, double *tally, stack *bank,
+                         orc_counts *c)
+{
+    const int32_t G = p->n_grp;
+    for (;;) {
+        int64_t cell = cell_of(p, P);
+        int32_t m = p->material[cell];
+        double sig_t = p->sigma_t[m * G + P->g];
+
+        /* distance to collision */
+        pair r = draw(seed, hid, P);
+        double d_coll = sig_t > 0.0 ? -log(r.a) / sig_t : INFINITY;
+
+        /* distance to the mesh surface: nearest face over bounded axes */
+        double d_surf = INFINITY;
+        int ax = -1;
+        for (int a = 0; a < 3; ++a) {
+            double u = *dir(P, a);
+            if (!tb->bounded[a] || u == 0.0) continue;
+            double d = (face(p, a, P->idx[a], u) - *pos(P, a)) / u;
+            if (d < 0.0) d = 0.0;
+            if (d < d_surf) { d_surf = d; ax = a; }
+        }
+
+        /* distance to the time census */
+        double d_time = INFINITY;
+        if (p->n_tbin > 0) {
+            d_time = P->v * (p->edges[P->tbin + 1] - P->t);
+            if (d_time < 0.0) d_time = 0.0;   /* t may sit one ulp past the edge */
+        }
+
+        /* nearest event; ties: census, then surface, then collision */
+        int ev = ORC_EV_COLLISION;
+        double d = d_coll;
+        if (d_surf <= d) { d = d_surf; ev = ORC_EV_SURFACE; }
+        if (d_time <= d) { d = d_time; ev = ORC_EV_CENSUS; }
+
+        /* track-length tally into (cell, group, time bin) */
+        int64_t bin = (cell * G + P->g) * tb->T1 + (p->n_tbin > 0 ? P->tbin : 0);
+        tally[bin] += P->w * d;
+        P->n_seg += 1;
+        c->segments += 1;
+
+        move_particle(P, d);
+
+        if (ev == ORC_EV_CENSUS) {
+            c->census += 1;
+            P->t = p->edges[P->tbin + 1];
+            P->tbin += 1;
+            if (P->tbin == p->n_tbin) {
+                c->censused += 1;
+                c->w_censused += P->w;
+                return ORC_END_CENSUSED;
+            }
+        } else if (ev == ORC_EV_SURFACE) {
+            double u = *dir(P, ax);
+            *pos(P, ax) = face(p, ax, P->idx[ax], u);
+            int32_t step = u > 0.0 ? 1 : -1;
+            int32_t inext = P->idx[ax] + step;
+            if (inext < 0 || inext >= p->n[ax]) {
+                int side = 2 * ax + (step > 0 ? 1 : 0);
+                if (p->bc[side] == ORC_BC_REFLECT) {
+                    *dir(P, ax) = -u;
+                } else {
+                    c->leaked += 1;
+                    c->w_leaked += P->w;
+                    return ORC_END_LEAKED;
+                }
+            } else {
+                P->idx[ax] = inext;
+                P->n_cross += 1;
+                c->crossings += 1;
+                if (!weight_window(p, tb, seed, hid, P, bank, c)) return ORC_END_ROULETTE;
+            }
+        } else {
+            /* collision: absorb or scatter (analog), new group, new direction */
+            P->n_col += 1;
+            c->collisions += 1;
+            pair r1 = draw(seed, hid, P);
+            pair r2 = draw(seed, hid, P);
+            if (!(r1.a < tb->scat_ratio[m * G + P->g])) {
+                c->absorbed += 1;
+                c->w_absorbed += P->w;
+                return ORC_END_ABSORBED;
+            }
+            P->g = sample_cdf(tb->cdf + ((int64_t)m * G + P->g) * G, G, r1.b);
+            P->v = p->speed[P->g];
+            double u[3];
+            orc_isotropic(r2.a, r2.b, u);
+            P->ux = u[0]; P->uy = u[1]; P->uz = u[2];
+            if (!weight_window(p, tb, seed, hid, P, bank, c)) return ORC_END_ROULETTE;
+        }
+    }
+}
+
+/* One history: the primary and every child it splits into. */
+static void run_history(const orc_problem *p, const tables *tb, uint64_t seed,
+                        uint64_t hid, double *tally, orc_counts *c, orc_record *rec)
+{
+    stack bank = { NULL, 0, 0 };
+    part P = source_particle(p, tb, seed, hid);
+    c->histories += 1;
+    c->w_source += P.w;
+    if (p->n_tbin > 0 && P.tbin >= p->n_tbin) {
+        /* born after the last census time: censused at birth */
+        c->censused += 1;
+        c->w_censused += P.w;
+        if (rec) {
+            rec->hid = hid; rec->end = ORC_END_CENSUSED; rec->g = P.g; rec->ctr = P.ctr;
+            rec->n_seg = 0; rec->n_col = 0; rec->n_cross = 0;
+            rec->x = P.x; rec->y = P.y; rec->z = P.z; rec->t = P.t; rec->w = P.w;
+        }
+        return;
+    }
+    push(&bank, &P);
+    int first = 1;
+    while (bank.size > 0) {
+        part Q = bank.items[--bank.size];
+        int32_t end = transport(p, tb, seed, hid, &Q, tally, &bank, c);
+        if (first && rec) {
+            rec->hid = hid; rec->end = end; rec->g = Q.g; rec->ctr = Q.ctr;
+            rec->n_seg = Q.n_seg; rec->n_col = Q.n_col; rec->n_cross = Q.n_cross;
+            rec->x = Q.x; rec->y = Q.y; rec->z = Q.z; rec->t = Q.t; rec->w = Q.w;
+        }
+        first = 0;
+    }
+    free(bank.items);
+}
+
+/* ---- problem checks and derived tables -------------------------------- */
+static int make_tables(const orc_problem *p, tables *tb)
+{
+    memset(tb, 0, sizeof *tb);
+    tb->p = p;
+    if (p->n_mat < 1 || p->n_grp < 1 || p->n_tbin < 0) return -1;
+    for (int a = 0; a < 3; ++a) {
+        if (p->n[a] < 1) return -1;
+        tb->bounded[a] = axis_bounded(p, a);
+    }
+    tb->n_cells = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    tb->T1 = p->n_tbin > 0 ? p->n_tbin : 1;
+    tb->n_bins = tb->n_cells * p->n_grp * tb->T1;
+    tb->volume = 1.0;
+    for (int a = 0; a < 3; ++a)
+        if (tb->bounded[a]) tb->volume *= p->width[a];
+    const int32_t M = p->n_mat, G = p->n_grp;
+    tb->scat_ratio = (double *)calloc((size_t)M * G, sizeof(double));
+    tb->cdf = (double *)calloc((size_t)M * G * G, sizeof(double));
+    tb->src_cdf = (double *)calloc((size_t)G, sizeof(double));
+    for (int32_t m = 0; m < M; ++m)
+        for (int32_t g = 0; g < G; ++g) {
+            double st = p->sigma_t[m * G + g], ss = p->sigma_s[m * G + g];
+            if (!(st >= 0.0) || !(ss >= 0.0) || ss > st) return -1;
+            tb->scat_ratio[m * G + g] = st > 0.0 ? ss / st : 0.0;
+            build_cdf(p->transfer + ((int64_t)m * G + g) * G, G,
+                      tb->cdf + ((int64_t)m * G + g) * G);
+        }
+    build_cdf(p->src_pdf, G, tb->src_cdf);
+    if (p->n_tbin > 0 && p->src_t0 < p->edges[0]) return -1;
+    if (p->src_t1 < p->src_t0) return -1;
+    for (int64_t c = 0; c < tb->n_cells; ++c)
+        if (p->material[c] >= M) return -1;
+    return 0;
+}
+
+static void free_tables(tables *tb)
+{
+    free(tb->scat_ratio);
+    free(tb->cdf);
+    free(tb->src_cdf);
+}
+
+static int in_region(const orc_problem *p, int64_t cell)
+{
+    int64_t i = cell % p->n[0];
+    int64_t j = (cell / p->n[0]) % p->n[1];
+    int64_t k = cell / ((int64_t)p->n[0] * p->n[1]);
+    return i >= p->region_lo[0] && i < p->region_hi[0] &&
+           j >= p->region_lo[1] && j < p->region_hi[1] &&
+           k >= p->region_lo[2] && k < p->region_hi[2];
+}
+
+/* ---- batches over threads (R8) ---------------------------------------- */
+typedef struct {
+    const orc_problem *p;
+    const tables *tb;
+    uint64_t n, seed, offset;
+    int32_t B, nthreads, tid;
+    double *s1, *s2;          /* thread partial sums over its batches */
+    double r1, r2;            /* region scalar partials               */
+    orc_counts c;
+} worker;
+
+static uint64_t batch_start(uint64_t n, int32_t B, int32_t b)
+{
+    uint64_t q = n / (uint64_t)B, r = n % (uint64_t)B;
+    uint64_t bb = (uint64_t)b;
+    return bb * q + (bb < r ? bb : r);
+}
+
+static void *work(void *arg)
+{
+    worker *wk = (worker *)arg;
+    const tables *tb = wk->tb;
+    double *tally = (double *)malloc((size_t)tb->n_bins * sizeof(double));
+    for (int32_t b = wk->tid; b < wk->B; b += wk->nthreads) {
+        memset(tally, 0, (size_t)tb->n_bins * sizeof(double));
+        uint64_t h0 = batch_start(wk->n, wk->B, b), h1 = batch_start(wk->n, wk->B, b + 1);
+        for (uint64_t h = h0; h < h1; ++h)
+            run_history(wk->p, tb, wk->seed, wk->offset + h, tally, &wk->c, NULL);
+        double region = 0.0;
+        for (int64_t k = 0; k < tb->n_bins; ++k) {
+            wk->s1[k] += tally[k];
+            wk->s2[k] += tally[k] * tally[k];
+            if (in_region(wk->p, k / ((int64_t)wk->p->n_grp * tb->T1))) region += tally[k];
+        }
+        wk->r1 += region;
+        wk->r2 += region * region;
+    }
+    free(tally);
+    return NULL;
+}
+
+static void add_counts(orc_counts *a, const orc_counts *b)
+{
+    a->histories += b->histories; a->segments += b->segments;
+    a->collisions += b->collisions; a->crossings += b->crossings;
+    a->census += b->census; a->absorbed += b->absorbed; a->leaked += b->leaked;
+    a->censused += b->censused; a->splits += b->splits; a->children += b->children;
+    a->roulette_killed += b->roulette_killed;
+    a->roulette_survived += b->roulette_survived;
+    a->w_source += b->w_source; a->w_absorbed += b->w_absorbed;
+    a->w_leaked += b->w_leaked; a->w_censused += b->w_censused;
+}
+
+/* mean and relative error from batch sums: m_b = B s_b / (N V) */
+static void batch_moments(double s1, double s2, uint64_t n, int32_t B, double vol,
+                          double *mean, double *rel)
+{
+    double nv = (double)n * vol;
+    double m = s1 / nv;
+    double ss = s2 - s1 * s1 / (double)B;
+    if (ss < 0.0) ss = 0.0;
+    double var = ((double)B * (double)B / (nv * nv)) * ss / ((double)B * (double)(B - 1));
+    *mean = m;
+    *rel = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
+}
+
+int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
+            uint64_t offset, int32_t n_batches, int32_t n_threads,
+            double *mean, double *relerr, double *sum1, double *sum2,
+            double *scalar, orc_counts *counts)
+{
+    tables tb;
+    if (n_batches < 2 || n_hist < (uint64_t)n_batches) return -1;
+    if (make_tables(p, &tb) != 0) { free_tables(&tb); return -1; }
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_batches) n_threads = n_batches;
+
+    worker *wk = (worker *)calloc((size_t)n_threads, sizeof(worker));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int32_t t = 0; t < n_threads; ++t) {
+        wk[t].p = p; wk[t].tb = &tb; wk[t].n = n_hist; wk[t].seed = seed;
+        wk[t].offset = offset; wk[t].B = n_batches; wk[t].nthreads = n_threads;
+        wk[t].tid = t;
+        wk[t].s1 = (double *)calloc((size_t)tb.n_bins, sizeof(double));
+        wk[t].s2 = (double *)calloc((size_t)tb.n_bins, sizeof(double));
+        pthread_create(&th[t], NULL, work, &wk[t]);
+    }
+    for (int32_t t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+
+    orc_counts c;
+    memset(&c, 0, sizeof c);
+    double r1 = 0.0, r2 = 0.0;
+    for (int64_t k = 0; k < tb.n_bins; ++k) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int32_t t = 0; t < n_threads; ++t) { s1 += wk[t].s1[k]; s2 += wk[t].s2[k]; }
+        if (sum1) sum1[k] = s1;
+        if (sum2) sum2[k] = s2;
+        double m, rel;
+        batch_moments(s1, s2, n_hist, n_batches, tb.volume, &m, &rel);
+        if (mean) mean[k] = m;
+        if (relerr) relerr[k] = rel;
+    }
+    for (int32_t t = 0; t < n_threads; ++t) {
+        r1 += wk[t].r1; r2 += wk[t].r2;
+        add_counts(&c, &wk[t].c);
+        free(wk[t].s1); free(wk[t].s2);
+    }
+    if (scalar) batch_moments(r1, r2, n_hist, n_batches, tb.volume, &scalar[0], &scalar[1]);
+    if (counts) *counts = c;
+    free(wk); free(th);
+    free_tables(&tb);
+    return 0;
+}
+
+int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
+              int64_t n, orc_record *out)
+{
+    tables tb;
+    if (make_tables(p, &tb) != 0) { free_tables(&tb); return -1; }
+    double *tally = (double *)calloc((size_t)tb.n_bins, sizeof(double));
+    orc_counts c;
+    memset(&c, 0, sizeof c);
+    for (int64_t i = 0; i < n; ++i)
+        run_history(p, &tb, seed, hids[i], tally, &c, &out[i]);
+    free(tally);
+    free_tables(&tb);
+    return 0;
+}
