@@ -1,0 +1,302 @@
+"""Benchmark: histories/s of the transport hot path on one B300 (or N, weak
+scaling with disjoint history ranges per rank), printed as one JSON line.
+
+Default workload: the 20 cm two-region time-dependent slab (1e7 histories,
+50 time bins x 200 spatial bins, one group), FP32-split tracking with FP64
+position/time/tally reduction.  A step is one full run (every history of the
+workload through source, flights, tally, collisions and the batch
+statistics).  Inputs (problem tables) are resident in HBM before timing; the
+per-step L2 flush writes a 256 MiB buffer.
+
+``--impl reference`` times the CPU oracle (FP64, all host cores) on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_04668_b300 import workloads as W  # noqa: E402
+
+METRIC = "histories/sec and tally figure of merit (1/sigma^2 T), 1 B300"
+WORKLOADS = {
+    "c1": (W.c1_slab, 100_000),
+    "c2": (W.c2_two_region, 10_000_000),
+    "c3": (W.c3_channel, 100_000_000),
+    "c4": (W.c4_deep, 100_000_000),
+}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "fallback": True}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def oracle_sample(prob, seconds, threads, seed=1, offset=0):
+    """Runs the CPU oracle on growing history counts until `seconds` of wall
+    time have been spent; returns (histories, segments, wall_s)."""
+    from oracle import oracle as O
+    n, done, segs, t_all = 20_000, 0, 0, 0.0
+    while t_all < seconds:
+        t0 = time.perf_counter()
+        r = O.run(prob, n, seed=seed, offset=offset + done, batches=max(2, min(32, n // 1000)),
+                  threads=threads)
+        dt = time.perf_counter() - t0
+        done += n
+        segs += r["counts"]["segments"]
+        t_all += dt
+        n = int(min(max(n * 2, 20_000), max(20_000, n * (seconds - t_all) / max(dt, 1e-3))))
+        if seconds - t_all < 0.5:
+            break
+    return done, segs, t_all
+
+
+def run_reference(args, prob, n_hist):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals, segs_all, hist_all, t_all = [], 0, 0, 0.0
+    for s in range(args.warmup + args.steps):
+        h, sg, dt = oracle_sample(prob, per_step, threads, offset=s * 10_000_000)
+        if s >= args.warmup:
+            vals.append(h / dt)
+            hist_all += h
+            segs_all += sg
+            t_all += dt
+    value = hist_all / t_all
+    cpu = {"value": value, "unit": "histories/s", "cores": threads, "kind": "oracle",
+           "sample": f"{hist_all} histories of {prob.name} in {t_all:.1f} s on {threads} host threads "
+                     f"(FP64 oracle, {segs_all / t_all:.3g} segments/s)"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "histories_per_step": int(hist_all / args.steps),
+                       "l2": "n/a (host)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--histories", type=int, default=0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+
+    make, n_default = WORKLOADS[args.workload]
+    prob = make()
+    n_hist = args.histories or n_default
+    if args.impl == "reference":
+        run_reference(args, prob, n_hist)
+        return
+
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_04668_b300 import mcdc as M
+
+    prec = M.PREC_FP32 if args.precision == "fp32" else M.PREC_FP64
+    P = M.Problem(prob, precision=prec)
+    dev = torch.device("cuda", local)
+    mean = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
+    rel = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    offset0 = rank * n_hist * 1000
+
+    def step(s):
+        return P.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, mean=mean, relerr=rel,
+                        stream=stream.cuda_stream, want_scalar=True, want_stats=True)
+
+    for s in range(args.warmup):
+        step(s)
+        flush.fill_(float(s))
+    torch.cuda.synchronize()
+
+    kernel_ms, stats_all, scal_all = [], [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(args.steps):
+            st, sc = step(args.warmup + s)
+            kernel_ms.append(st["kernel_ms"])
+            stats_all.append(st)
+            scal_all.append(sc)
+            flush.fill_(float(s))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    region_ms = e0.elapsed_time(e1)
+    t = torch.tensor([region_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    region_ms = float(t.item())
+    hist_total = n_hist * args.steps * world
+    value = hist_total / (region_ms / 1e3)
+    segs = sum(s["segments"] for s in stats_all) / args.steps
+    ms_step = region_ms / args.steps
+    k_ms = float(np.mean(kernel_ms))
+
+    # ---- end to end through the public API with host buffers: create
+    # (uploads the tables), run with host outputs (D2H), destroy
+    nb = P.n_bins
+    h_mean = np.zeros(nb)
+    h_rel = np.zeros(nb)
+    h2d = int(prob.material.nbytes + 8 * (prob.sigma_t.size * 2 + prob.transfer.size +
+                                          prob.speed.size + prob.src_pdf.size +
+                                          (0 if prob.edges is None else prob.edges.size)))
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for s in range(e2e_steps):
+        with M.Problem(prob, precision=prec) as Q:
+            Q.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, mean=h_mean, relerr=h_rel,
+                     want_stats=False)
+    te = time.perf_counter() - te0
+    e2e_val = n_hist * e2e_steps * world / te
+
+    pk = peaks()
+    fom = None
+    if scal_all and scal_all[-1] and scal_all[-1][1] > 0:
+        fom = 1.0 / (scal_all[-1][1] ** 2 * (ms_step / 1e3))
+    line = {
+        "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == M.PREC_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "histories_per_step": n_hist, "precision": args.precision,
+                   "tally_mode": ["auto", "shared", "global"][stats_all[-1]["tally_mode"]],
+                   "n_batches": stats_all[-1]["n_batches"], "block": stats_all[-1]["block_size"],
+                   "bank_per_cta": stats_all[-1]["bank_per_cta"],
+                   "ctas_per_sm": stats_all[-1]["ctas_per_sm"],
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
+        "segments_per_sec": segs * args.steps * world / (region_ms / 1e3),
+        "segments_per_history": segs / n_hist,
+        "fom_region": fom,
+        "region_relerr": scal_all[-1][1] if scal_all[-1] else None,
+        "kernel_ms": k_ms,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": "histories/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 2 * 8 * nb},
+        "gpu_launches": None,
+        "roofline": None,
+    }
+    launches_per_step = 2 if stats_all[-1]["tally_mode"] == 1 else 3 * stats_all[-1]["n_batches"] + 1
+    line["gpu_launches"] = launches_per_step * args.steps
+    # roofline of the tracker: per-segment figures are stated in the design doc
+    seg_rate = segs / (k_ms / 1e3)
+    line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"])
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        h, sg, dt = oracle_sample(prob, args.cpu_seconds, os.cpu_count() or 1, offset=10**12)
+        line["cpu_baseline"] = {"value": h / dt, "unit": "histories/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"{h} histories of {prob.name} ({sg / dt:.3g} segments/s) "
+                                          f"in {dt:.1f} s, FP64 oracle on all host threads"}
+    if world > 1:
+        dist.destroy_process_group()
+    P.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def roofline(prob, seg_rate, pk, tally_mode):
+    """Shared-tally mode keeps the tally and bank on chip: the tracker is
+    bound by issue slots (ALU); the global-tally mode streams 16 B of tally
+    read-modify-write per segment to HBM/L2."""
+    if tally_mode == 2:
+        ach = seg_rate * 16 / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": "measured copy"}
+    # issue-slot roofline: lane-instructions per segment of the algorithm as
+    # written against 148 SMs x 128 lanes x max SM clock
+    ops_per_seg = 160.0
+    peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    ach = seg_rate * ops_per_seg / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
+            "traffic": None, "ops_per_segment": ops_per_seg,
+            "peak_kind": "148 SM x 128 lanes x max SM clock"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * mcdc.h -- C-ABI of the B300 (sm_103a) Monte Carlo neutron transport library.
+ *
+ * Scope: time-dependent, multigroup, fixed-source transport in
+ * non-multiplying media on a uniform Cartesian mesh with a track-length flux
+ * tally into (cell, group, time bin), analog or with weight windows.
+ *
+ * Paper passages the calls stand for (arXiv 2409.04668, "Performant and
+ * Portable Monte Carlo Neutron Transport via Numba"):
+ *  - "MC/DC on CPUs": the user describes physics, materials and parameters
+ *    through input functions; initialisation builds one typed global record
+ *    holding inputs, meshes, particle banks and tallies (-> the problem
+ *    handle); a fixed-source run transports every particle until capture,
+ *    a time or space boundary, a time census or a variance-reduction event
+ *    ends its history (-> mcdc_run); finalisation returns the tallies with
+ *    their statistical error (-> mean and relative error outputs).
+ *  - "MC/DC on GPUs": device memory is allocated and the global record is
+ *    copied to the GPU once at initialisation, transport kernels run until
+ *    the work is done, and the results are copied back once (-> create
+ *    uploads, run downloads); the profile in "Performance" shows why the
+ *    allocation must not be repeated per run.
+ *  - Figure "jitfunctions" (move_particle) and Figure "forcpuvgpu"
+ *    (loc2index + atomic add into a tally) define one flight's move and
+ *    tally scatter.
+ *
+ * Conventions
+ *  - Every call returns MCDC_OK (0) or a negative MCDC_ERR_* code;
+ *    mcdc_last_error() gives a message for the calling thread.
+ *  - Input arrays are read during the call and copied: the caller keeps
+ *    ownership and may free them afterwards.
+ *  - Output arrays are caller-owned and may be host or device pointers
+ *    (the library asks CUDA which); device outputs are written on the run's
+ *    stream, host outputs are complete when the call returns.
+ *  - Tally layout: [nz][ny][nx][G][T] (x fastest among cells), T = number
+ *    of time bins, or 1 in steady state.  Values are track length per
+ *    source particle per unit cell volume, integrated over the time bin.
+ *  - A problem handle is not thread-safe; runs are deterministic for a
+ *    given (seed, history offset, histories, batches) up to the order of
+ *    floating-point additions.
+ */
+#ifndef MCDC_B300_H
+#define MCDC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCDC_OK                  0
+#define MCDC_ERR_INVALID        -1   /* bad argument or problem data            */
+#define MCDC_ERR_OOM            -2   /* device allocation failed                */
+#define MCDC_ERR_CUDA           -3   /* a CUDA call failed                      */
+#define MCDC_ERR_BANK_OVERFLOW  -4   /* split children exceeded the bank        */
+#define MCDC_ERR_TIMEOUT        -5   /* a bounded device wait gave up           */
+#define MCDC_ERR_NO_DEVICE      -6   /* no usable sm_103 device                 */
+
+#define MCDC_BC_VACUUM   0
+#define MCDC_BC_REFLECT  1
+
+#define MCDC_SRC_ISOTROPIC 0
+#define MCDC_SRC_BEAM      1
+
+#define MCDC_PREC_FP64   0   /* every step in FP64: event-exact with the FP64 reference      */
+#define MCDC_PREC_FP32   1   /* FP32 direction/distance/xs, FP64 position, time and tallies  */
+
+#define MCDC_TALLY_AUTO    0
+#define MCDC_TALLY_SHARED  1  /* per-CTA privatised tally in shared memory, one batch per CTA */
+#define MCDC_TALLY_GLOBAL  2  /* device-wide tally, batches run one after another            */
+
+/* Uniform Cartesian mesh.  An axis with n == 1 and width <= 0 or infinite is
+ * unbounded (no faces): a 1-D slab is nx cells with ny = nz = 1 and
+ * dy = dz = INFINITY.  material[(k*ny + j)*nx + i] < n_materials. */
+typedef struct mcdc_mesh {
+    int32_t nx, ny, nz;
+    double x0, y0, z0;          /* low corner (cm) */
+    double dx, dy, dz;          /* cell widths (cm) */
+    const uint8_t *material;    /* [nz][ny][nx], host pointer */
+    int32_t bc[6];              /* -x,+x,-y,+y,-z,+z: MCDC_BC_* */
+} mcdc_mesh;
+
+/* Multigroup data.  sigma_s <= sigma_t; transfer rows are P(g -> g') given a
+ * scatter in g and must sum to 1 (checked to 1e-9). */
+typedef struct mcdc_materials {
+    int32_t n_materials, n_groups;   /* 1..255, 1..16 */
+    const double *sigma_t;           /* [M][G] 1/cm */
+    const double *sigma_s;           /* [M][G] 1/cm */
+    const double *transfer;          /* [M][G][G]   */
+    const double *speed;             /* [G] cm per time unit, > 0 */
+} mcdc_materials;
+
+/* Source: position uniform in the box [lo, hi] (lo == hi on an axis gives a
+ * plane or a point), isotropic or a beam along dir, group from group_pdf,
+ * birth time uniform in [t0, t1] (t0 == t1: a pulse). */
+typedef struct mcdc_source {
+    double lo[3], hi[3];
+    int32_t kind;                    /* MCDC_SRC_* */
+    double dir[3];                   /* unit vector, BEAM only */
+    const double *group_pdf;         /* [G], sums to 1 */
+    double t0, t1;
+} mcdc_source;
+
+/* Time census grid: n_bins > 0 edges[0] < ... < edges[n_bins] (the last edge
+ * ends the run: particles alive then are "censused"); n_bins == 0 is steady
+ * state (one tally time slot, no census). */
+typedef struct mcdc_time_grid {
+    int32_t n_bins;
+    const double *edges;             /* [n_bins + 1], may be NULL if n_bins == 0 */
+} mcdc_time_grid;
+
+/* Run-independent options fixed at create.  Zero means "choose for me". */
+typedef struct mcdc_options {
+    int32_t precision;          /* MCDC_PREC_*                                    */
+    int32_t tally_mode;         /* MCDC_TALLY_*                                   */
+    int32_t n_batches;          /* batches for the error estimate (>= 2); 0: auto */
+    int32_t block_size;         /* threads per CTA; 0: autotuned                  */
+    int32_t bank_per_cta;       /* particle slots per CTA; 0: autotuned           */
+    int32_t ctas_per_sm;        /* resident CTAs per SM; 0: autotuned             */
+    int32_t warp_aggregate;     /* -1 off, 1 on, 0 auto                           */
+    int32_t autotune;           /* 1: time candidate launch shapes at create      */
+    int32_t overflow_per_cta;   /* split-children overflow slots per CTA; 0: auto */
+    int32_t region_lo[3];       /* cell box [lo, hi) of the scalar tally used for */
+    int32_t region_hi[3];       /*   the figure of merit; hi == 0: whole mesh      */
+} mcdc_options;
+
+/* Event and weight counts of one run (summed over all particles). */
+typedef struct mcdc_stats {
+    uint64_t histories, segments, collisions, crossings, census;
+    uint64_t absorbed, leaked, censused, splits, children;
+    uint64_t roulette_killed, roulette_survived;
+    double w_source, w_absorbed, w_leaked, w_censused;
+    double kernel_ms;           /* device time of the transport kernels      */
+    double total_ms;            /* device time of the whole run              */
+    int32_t block_size, bank_per_cta, ctas_per_sm, tally_mode, n_batches, warp_aggregate;
+} mcdc_stats;
+
+/* Per-history summary of the primary particle (serial 0), for checking a run
+ * history by history against a reference tracker. */
+typedef struct mcdc_record {
+    uint64_t hid;
+    int32_t end;                /* 1 absorbed, 2 leaked, 3 censused, 4 rouletted */
+    int32_t g;
+    uint32_t ctr;               /* random-number counter after the last draw    */
+    uint32_t n_seg, n_col, n_cross;
+    double x, y, z, t, w;
+} mcdc_record;
+
+typedef struct mcdc_run_args {
+    uint64_t n_histories;       /* > 0                                            */
+    int32_t n_batches;          /* >= 2 and <= n_histories; 0: the create option, else auto */
+    uint64_t seed;              /* Philox key                                     */
+    uint64_t hist_offset;       /* histories [offset, offset + n) are run         */
+    double *mean_out;           /* [n_bins] or NULL; host or device               */
+    double *relerr_out;         /* [n_bins] or NULL; host or device               */
+    double *sum1_out;           /* [n_bins] sum over batches of batch sums, or NULL */
+    double *sum2_out;           /* [n_bins] sum of squared batch sums, or NULL    */
+    double *scalar_out;         /* [2] region scalar mean and relative error, or NULL (host) */
+    mcdc_record *records;       /* [n_records] for histories offset..offset+n_records-1, or NULL (host or device) */
+    uint64_t n_records;
+    void *stream;               /* cudaStream_t; NULL: the legacy default stream  */
+} mcdc_run_args;
+
+/* Fills *opt with defaults (FP32 split, automatic tally mode, autotuning on). */
+void mcdc_default_options(mcdc_options *opt);
+
+/* Validates the problem, builds its device tables (group-transfer CDFs,
+ * FP32 copies), uploads them once and picks launch shapes.  Errors:
+ * MCDC_ERR_INVALID (bad sizes, negative or NaN data, sigma_s > sigma_t,
+ * rows not summing to 1, source outside the mesh or before the first time
+ * edge), MCDC_ERR_NO_DEVICE, MCDC_ERR_OOM, MCDC_ERR_CUDA.  On error *out is
+ * NULL and nothing is leaked. */
+int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat,
+                        const mcdc_source *src, const mcdc_time_grid *time,
+                        const mcdc_options *opt, struct mcdc_problem **out);
+
+/* Runs histories [0, n_histories) with the given seed and writes the mean
+ * tally (layout above) to tally_out (host or device, may be NULL).  Blocks
+ * until the result is complete. */
+int mcdc_run(struct mcdc_problem *prob, uint64_t n_histories, uint64_t seed,
+             double *tally_out);
+
+/* Full form: history offset, error estimate, raw batch moments, region
+ * scalar, per-history records, event statistics and a caller stream.  With a
+ * non-NULL stream and only device outputs it returns once the work is queued
+ * (stats->kernel_ms and total_ms are then 0); otherwise it synchronises. */
+int mcdc_run_ex(struct mcdc_problem *prob, const mcdc_run_args *args, mcdc_stats *stats);
+
+/* Weight windows: w_lower[cell][G][T] (double, host or device; <= 0 turns the
+ * window off in that bin), w_U = upper_ratio*w_L, w_S = survival_ratio*w_L,
+ * at most nmax copies per split.  NULL w_lower switches back to analog.
+ * Errors: MCDC_ERR_INVALID for ratios that are not 1 < survival < upper or
+ * nmax < 2. */
+int mcdc_set_weight_windows(struct mcdc_problem *prob, const double *w_lower,
+                            double upper_ratio, double survival_ratio, int32_t nmax);
+
+/* Number of tally bins (cells * G * T). */
+int64_t mcdc_tally_size(const struct mcdc_problem *prob);
+
+void mcdc_problem_destroy(struct mcdc_problem *prob);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *mcdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -24,6 +24,7 @@
  *  R8 batches: histories split into B contiguous batches (the first N%B
  *     batches one history longer); per-bin variance of the mean from the
  *     spread of the batch means.
+ *  R10 a flight with nothing ahead (infinite distance) is a leak.
  *  R9 weight windows at collisions and cell crossings: above w_U split into
  *     n = min(ceil(w/w_U), nmax) equal copies, below w_L roulette with
  *     survival probability w/w_S to weight w_S.  Children get a new serial
@@ -274,11 +275,19 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
         if (d_surf <= d) { d = d_surf; ev = ORC_EV_SURFACE; }
         if (d_time <= d) { d = d_time; ev = ORC_EV_CENSUS; }
 
+        P->n_seg += 1;
+        c->segments += 1;
+        if (isinf(d)) {
+            /* nothing ahead (void, no face in the flight direction, steady
+             * state): the particle leaves to infinity */
+            c->leaked += 1;
+            c->w_leaked += P->w;
+            return ORC_END_LEAKED;
+        }
+
         /* track-length tally into (cell, group, time bin) */
         int64_t bin = (cell * G + P->g) * tb->T1 + (p->n_tbin > 0 ? P->tbin : 0);
         tally[bin] += P->w * d;
-        P->n_seg += 1;
-        c->segments += 1;
 
         move_particle(P, d);
 

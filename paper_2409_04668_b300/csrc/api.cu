@@ -1,0 +1,687 @@
+// api.cu -- the C-ABI (include/mcdc.h): problem validation, device tables,
+// launch-shape selection and the run sequence.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mcdc.h"
+#include "launch.h"
+#include "tracker.cuh"
+
+using namespace mcdc;
+
+static_assert(sizeof(mcdc_record) == sizeof(Record), "record layout");
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? MCDC_ERR_OOM : MCDC_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device buffers owned by a problem
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mcdc_problem {
+  int device = 0;
+  int sms = 0;
+  DevProblem P{};
+  mcdc_options opt{};
+  // host copies needed later
+  std::vector<double> edges;
+  int dim = 3;
+  TrackKey key{};
+  // launch shape
+  int block = 256, S = 512, ctas_per_sm = 1, grid = 0, smem = 0;
+  Layout L{};
+  int tally_mode = MCDC_TALLY_SHARED;
+  int warp_aggregate = 0;
+  int overflow_cap = 0;
+  // device memory
+  std::vector<void *> allocs;
+  double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
+         *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
+  Stats *stats = nullptr;
+  int32_t *error = nullptr;
+  unsigned long long *work = nullptr;   // [max batches] work counters
+  int work_slots = 0;
+  void *overflow = nullptr;
+  size_t overflow_bytes = 0;
+  Record *rec_tmp = nullptr;
+  uint64_t rec_cap = 0;
+  double *ww64 = nullptr;
+  float *ww32 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  // host staging
+  Stats *h_stats = nullptr;   // pinned
+  int32_t *h_error = nullptr; // pinned
+};
+
+namespace {
+
+template <class T>
+int dalloc(mcdc_problem *pr, T **out, size_t count) {
+  void *p = nullptr;
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCDC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  pr->allocs.push_back(p);
+  *out = (T *)p;
+  return MCDC_OK;
+}
+
+template <class T>
+int upload(mcdc_problem *pr, const T **dst, const std::vector<T> &src) {
+  T *d = nullptr;
+  int rc = dalloc(pr, &d, src.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(d, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = d;
+  return MCDC_OK;
+}
+
+void release(mcdc_problem *pr) {
+  if (!pr) return;
+  cudaSetDevice(pr->device);
+  for (void *p : pr->allocs) cudaFree(p);
+  pr->allocs.clear();
+  if (pr->ev0) cudaEventDestroy(pr->ev0);
+  if (pr->ev1) cudaEventDestroy(pr->ev1);
+  if (pr->ev2) cudaEventDestroy(pr->ev2);
+  if (pr->h_stats) cudaFreeHost(pr->h_stats);
+  if (pr->h_error) cudaFreeHost(pr->h_error);
+  delete pr;
+}
+
+void build_cdf(const double *pdf, int n, double *cdf) {
+  double acc = 0.0;
+  int last = 0;
+  for (int k = 0; k < n; ++k) {
+    acc += pdf[k];
+    cdf[k] = acc;
+    if (pdf[k] > 0.0) last = k;
+  }
+  for (int k = last; k < n; ++k) cdf[k] = 1.0;
+}
+
+// Shared memory one CTA needs for a given slot count.
+Layout make_layout(const mcdc_problem *pr, int S, int tally_mode) {
+  Layout L{};
+  L.S = S;
+  const bool f64 = pr->key.f64;
+  L.tables_bytes = tables_bytes_of(f64, pr->P.M, pr->P.G, pr->P.T);
+  L.tally_bytes = tally_mode == MCDC_TALLY_SHARED
+                      ? align16((long long)pr->P.n_bins * (f64 ? 8 : 4))
+                      : 0;
+  L.bank_bytes = S * slot_bytes(f64, pr->dim);
+  L.total = (int)(L.tables_bytes + L.tally_bytes + L.bank_bytes + 64);
+  return L;
+}
+
+struct DeviceLimits {
+  int sms, smem_sm, smem_block, max_threads_sm;
+};
+
+int device_limits(int dev, DeviceLimits *d) {
+  CK(cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&d->smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  CK(cudaDeviceGetAttribute(&d->smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CK(cudaDeviceGetAttribute(&d->max_threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+  return MCDC_OK;
+}
+
+// Picks block size, slots, CTAs per SM and the tally mode from the options
+// and the device limits.  Shared mode needs the whole tally plus the bank in
+// one CTA's shared memory.
+int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
+  const mcdc_options &o = pr->opt;
+  const bool f64 = pr->key.f64;
+  int block = o.block_size > 0 ? o.block_size : 256;
+  if (block % 32 != 0 || block > 512) return fail(MCDC_ERR_INVALID, "block_size must be a multiple of 32, <= 512");
+  int S = o.bank_per_cta > 0 ? o.bank_per_cta : 2 * block;
+  if (S < block || S > 8192 || S % 32 != 0)
+    return fail(MCDC_ERR_INVALID, "bank_per_cta must be a multiple of 32 in [block_size, 8192]");
+  int mode = o.tally_mode;
+  const long long tally_b = (long long)pr->P.n_bins * (f64 ? 8 : 4);
+  if (mode == MCDC_TALLY_AUTO) {
+    const Layout Ls = make_layout(pr, S, MCDC_TALLY_SHARED);
+    mode = (tally_b <= 96 * 1024 && Ls.total <= dl.smem_block - 1024) ? MCDC_TALLY_SHARED
+                                                                       : MCDC_TALLY_GLOBAL;
+  }
+  Layout L = make_layout(pr, S, mode);
+  const int dyn_max = dl.smem_block - 1024;   // room for the kernel's static shared memory
+  if (L.total > dyn_max) {
+    if (o.tally_mode == MCDC_TALLY_SHARED)
+      return fail(MCDC_ERR_INVALID, "shared tally + bank exceed shared memory; use the global tally");
+    return fail(MCDC_ERR_INVALID, "bank_per_cta too large for shared memory");
+  }
+  pr->key.shared = (mode == MCDC_TALLY_SHARED);
+  {
+    cudaError_t e = prepare_track(pr->key, dyn_max);
+    if (e != cudaSuccess) return fail(MCDC_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  int cps = track_occupancy(pr->key, block, L.total);
+  if (cps < 1) return fail(MCDC_ERR_INVALID, "launch shape does not fit on an SM (registers or shared memory)");
+  if (o.ctas_per_sm > 0) {
+    if (o.ctas_per_sm > cps) return fail(MCDC_ERR_INVALID, "ctas_per_sm exceeds what fits on an SM");
+    cps = o.ctas_per_sm;
+  }
+  pr->block = block;
+  pr->S = S;
+  pr->ctas_per_sm = cps;
+  pr->grid = dl.sms * cps;
+  pr->smem = L.total;
+  pr->L = L;
+  pr->tally_mode = mode;
+  if (o.warp_aggregate > 0) pr->warp_aggregate = 1;
+  else if (o.warp_aggregate < 0) pr->warp_aggregate = 0;
+  else pr->warp_aggregate = pr->P.n_bins <= 4096 ? 1 : 0;
+  pr->key.shared = (mode == MCDC_TALLY_SHARED);
+  return MCDC_OK;
+}
+
+int default_batches(const mcdc_problem *pr, uint64_t n) {
+  int B = pr->opt.n_batches;
+  if (B <= 0) {
+    if (pr->tally_mode == MCDC_TALLY_SHARED) {
+      // enough whole batches to keep every CTA busy, each a few thousand histories
+      const uint64_t by_size = n / 2048;
+      B = (int)std::min<uint64_t>(std::max<uint64_t>(by_size, 32), (uint64_t)pr->grid * 8);
+    } else {
+      B = 32;
+    }
+  }
+  if ((uint64_t)B > n) B = (int)n;
+  return B;
+}
+
+int ensure_work_slots(mcdc_problem *pr, int n) {
+  if (pr->work_slots >= n) return MCDC_OK;
+  unsigned long long *w = nullptr;
+  int rc = dalloc(pr, &w, (size_t)n);
+  if (rc) return rc;
+  pr->work = w;
+  pr->work_slots = n;
+  return MCDC_OK;
+}
+
+int ensure_overflow(mcdc_problem *pr) {
+  if (pr->P.ww_lower == nullptr) return MCDC_OK;
+  int cap = pr->opt.overflow_per_cta > 0 ? pr->opt.overflow_per_cta : 4096;
+  const size_t part_b = pr->key.f64 ? sizeof(Part<double>) : sizeof(Part<float>);
+  const size_t need = (size_t)pr->grid * cap * part_b;
+  if (pr->overflow_bytes >= need && pr->overflow_cap == cap) return MCDC_OK;
+  unsigned char *p = nullptr;
+  int rc = dalloc(pr, &p, need);
+  if (rc) return rc;
+  pr->overflow = p;
+  pr->overflow_bytes = need;
+  pr->overflow_cap = cap;
+  return MCDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mcdc_default_options(mcdc_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MCDC_PREC_FP32;
+  o->tally_mode = MCDC_TALLY_AUTO;
+  o->autotune = 0;
+}
+
+const char *mcdc_last_error(void) { return g_err.c_str(); }
+
+int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const mcdc_source *src,
+                        const mcdc_time_grid *time, const mcdc_options *opt,
+                        struct mcdc_problem **out) {
+  g_err.clear();
+  if (!out) return fail(MCDC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !mat || !src) return fail(MCDC_ERR_INVALID, "mesh, materials and source are required");
+  mcdc_options o;
+  if (opt) o = *opt; else mcdc_default_options(&o);
+  if (o.precision != MCDC_PREC_FP64 && o.precision != MCDC_PREC_FP32)
+    return fail(MCDC_ERR_INVALID, "unknown precision");
+
+  // ---- mesh
+  const int n[3] = {mesh->nx, mesh->ny, mesh->nz};
+  const double org[3] = {mesh->x0, mesh->y0, mesh->z0};
+  const double wid[3] = {mesh->dx, mesh->dy, mesh->dz};
+  int bounded[3];
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] < 1 || n[a] > 65535) return fail(MCDC_ERR_INVALID, "cells per axis must be in 1..65535");
+    bounded[a] = !(n[a] == 1 && (!(wid[a] > 0.0) || std::isinf(wid[a])));
+    if (bounded[a] && !(std::isfinite(wid[a]) && wid[a] > 0.0))
+      return fail(MCDC_ERR_INVALID, "cell widths must be finite and > 0");
+    if (!std::isfinite(org[a])) return fail(MCDC_ERR_INVALID, "mesh origin must be finite");
+  }
+  if (!mesh->material) return fail(MCDC_ERR_INVALID, "material map is NULL");
+  for (int s = 0; s < 6; ++s)
+    if (mesh->bc[s] != MCDC_BC_VACUUM && mesh->bc[s] != MCDC_BC_REFLECT)
+      return fail(MCDC_ERR_INVALID, "unknown boundary condition");
+  const int64_t n_cells = (int64_t)n[0] * n[1] * n[2];
+
+  // ---- materials
+  const int M = mat->n_materials, G = mat->n_groups;
+  if (M < 1 || M > 255) return fail(MCDC_ERR_INVALID, "n_materials must be in 1..255");
+  if (G < 1 || G > kMaxGroups) return fail(MCDC_ERR_INVALID, "n_groups must be in 1..16");
+  if (!mat->sigma_t || !mat->sigma_s || !mat->transfer || !mat->speed)
+    return fail(MCDC_ERR_INVALID, "material arrays must not be NULL");
+  for (int64_t c = 0; c < n_cells; ++c)
+    if (mesh->material[c] >= M) return fail(MCDC_ERR_INVALID, "material id out of range");
+  std::vector<double> st(M * G), scat(M * G), cdf((size_t)M * G * G);
+  for (int m = 0; m < M; ++m)
+    for (int g = 0; g < G; ++g) {
+      const double t = mat->sigma_t[m * G + g], s = mat->sigma_s[m * G + g];
+      if (!finite_nonneg(t) || !finite_nonneg(s) || s > t)
+        return fail(MCDC_ERR_INVALID, "need 0 <= sigma_s <= sigma_t, finite");
+      st[m * G + g] = t;
+      scat[m * G + g] = t > 0.0 ? s / t : 0.0;
+      const double *row = mat->transfer + ((size_t)m * G + g) * G;
+      double sum = 0.0;
+      for (int h = 0; h < G; ++h) {
+        if (!finite_nonneg(row[h])) return fail(MCDC_ERR_INVALID, "transfer entries must be >= 0");
+        sum += row[h];
+      }
+      if (s > 0.0 && std::fabs(sum - 1.0) > 1e-9)
+        return fail(MCDC_ERR_INVALID, "transfer rows must sum to 1");
+      build_cdf(row, G, cdf.data() + ((size_t)m * G + g) * G);
+    }
+  std::vector<double> speed(G);
+  for (int g = 0; g < G; ++g) {
+    if (!(std::isfinite(mat->speed[g]) && mat->speed[g] > 0.0))
+      return fail(MCDC_ERR_INVALID, "speeds must be finite and > 0");
+    speed[g] = mat->speed[g];
+  }
+
+  // ---- time grid
+  int T = 0;
+  std::vector<double> edges(1, 0.0);
+  if (time && time->n_bins > 0) {
+    T = time->n_bins;
+    if (T > 65534) return fail(MCDC_ERR_INVALID, "too many time bins");
+    if (!time->edges) return fail(MCDC_ERR_INVALID, "time edges are NULL");
+    edges.assign(time->edges, time->edges + T + 1);
+    for (int j = 0; j <= T; ++j)
+      if (!std::isfinite(edges[j]) || (j > 0 && !(edges[j] > edges[j - 1])))
+        return fail(MCDC_ERR_INVALID, "time edges must be finite and increasing");
+  } else if (time && time->n_bins < 0) {
+    return fail(MCDC_ERR_INVALID, "negative number of time bins");
+  }
+
+  // ---- source
+  if (!src->group_pdf) return fail(MCDC_ERR_INVALID, "source group pdf is NULL");
+  std::vector<double> scdf(G);
+  {
+    double sum = 0.0;
+    for (int g = 0; g < G; ++g) {
+      if (!finite_nonneg(src->group_pdf[g])) return fail(MCDC_ERR_INVALID, "source pdf must be >= 0");
+      sum += src->group_pdf[g];
+    }
+    if (std::fabs(sum - 1.0) > 1e-9) return fail(MCDC_ERR_INVALID, "source pdf must sum to 1");
+    build_cdf(src->group_pdf, G, scdf.data());
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (!std::isfinite(src->lo[a]) || !std::isfinite(src->hi[a]) || src->lo[a] > src->hi[a])
+      return fail(MCDC_ERR_INVALID, "source box must be finite with lo <= hi");
+    if (bounded[a] && (src->lo[a] < org[a] || src->hi[a] > org[a] + n[a] * wid[a]))
+      return fail(MCDC_ERR_INVALID, "source box must lie inside the mesh");
+  }
+  if (src->kind != MCDC_SRC_ISOTROPIC && src->kind != MCDC_SRC_BEAM)
+    return fail(MCDC_ERR_INVALID, "unknown source kind");
+  if (src->kind == MCDC_SRC_BEAM) {
+    const double nn = src->dir[0] * src->dir[0] + src->dir[1] * src->dir[1] + src->dir[2] * src->dir[2];
+    if (!(std::fabs(nn - 1.0) < 1e-9)) return fail(MCDC_ERR_INVALID, "beam direction must be a unit vector");
+  }
+  if (!std::isfinite(src->t0) || !std::isfinite(src->t1) || src->t1 < src->t0)
+    return fail(MCDC_ERR_INVALID, "need finite t0 <= t1");
+  if (T > 0 && src->t0 < edges[0]) return fail(MCDC_ERR_INVALID, "source starts before the first time edge");
+
+  // ---- device
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(MCDC_ERR_NO_DEVICE, "no CUDA device");
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(MCDC_ERR_NO_DEVICE, std::string("built for sm_103 (B300), found ") + prop.name);
+  DeviceLimits dl;
+  if (int rc = device_limits(dev, &dl)) return rc;
+
+  mcdc_problem *pr = new mcdc_problem();
+  pr->device = dev;
+  pr->sms = dl.sms;
+  pr->opt = o;
+  pr->edges = edges;
+  DevProblem &P = pr->P;
+  for (int a = 0; a < 3; ++a) {
+    P.n[a] = n[a];
+    P.bounded[a] = bounded[a];
+    P.origin[a] = org[a];
+    P.width[a] = bounded[a] ? wid[a] : 0.0;
+  }
+  for (int s = 0; s < 6; ++s) P.bc[s] = mesh->bc[s];
+  P.M = M; P.G = G; P.T = T; P.T1 = T > 0 ? T : 1;
+  P.n_cells = n_cells;
+  P.n_bins = n_cells * G * P.T1;
+  P.volume = 1.0;
+  for (int a = 0; a < 3; ++a)
+    if (bounded[a]) P.volume *= wid[a];
+  for (int a = 0; a < 3; ++a) {
+    P.src_lo[a] = src->lo[a];
+    P.src_hi[a] = src->hi[a];
+    P.src_dir[a] = src->dir[a];
+  }
+  P.src_kind = src->kind;
+  P.t0 = src->t0;
+  P.t1 = src->t1;
+  for (int a = 0; a < 3; ++a) {
+    int hi = o.region_hi[a] > 0 ? o.region_hi[a] : n[a];
+    int lo = std::max(0, o.region_lo[a]);
+    P.region_lo[a] = lo;
+    P.region_hi[a] = std::min(hi, n[a]);
+  }
+  pr->dim = (!bounded[1] && !bounded[2]) ? 1 : 3;
+  pr->key.f64 = (o.precision == MCDC_PREC_FP64);
+  pr->key.dim = pr->dim;
+
+  int rc = MCDC_OK;
+  auto bail = [&](int code) {
+    std::string keep = g_err;
+    release(pr);
+    g_err = keep;
+    return code;
+  };
+  {
+    std::vector<uint8_t> matv(mesh->material, mesh->material + n_cells);
+    if ((rc = upload(pr, &P.material, matv))) return bail(rc);
+    if ((rc = upload(pr, &P.sigma_t, st))) return bail(rc);
+    if ((rc = upload(pr, &P.scat, scat))) return bail(rc);
+    if ((rc = upload(pr, &P.cdf, cdf))) return bail(rc);
+    if ((rc = upload(pr, &P.speed, speed))) return bail(rc);
+    if ((rc = upload(pr, &P.edges, edges))) return bail(rc);
+    if ((rc = upload(pr, &P.src_cdf, scdf))) return bail(rc);
+    auto f32 = [](const std::vector<double> &v) {
+      std::vector<float> r(v.size());
+      for (size_t q = 0; q < v.size(); ++q) r[q] = (float)v[q];
+      return r;
+    };
+    std::vector<float> inv(G);
+    for (int g = 0; g < G; ++g) inv[g] = (float)(1.0 / speed[g]);
+    if ((rc = upload(pr, &P.sigma_t32, f32(st)))) return bail(rc);
+    if ((rc = upload(pr, &P.scat32, f32(scat)))) return bail(rc);
+    if ((rc = upload(pr, &P.cdf32, f32(cdf)))) return bail(rc);
+    if ((rc = upload(pr, &P.speed32, f32(speed)))) return bail(rc);
+    if ((rc = upload(pr, &P.inv_speed32, inv))) return bail(rc);
+    if ((rc = upload(pr, &P.src_cdf32, f32(scdf)))) return bail(rc);
+  }
+  if ((rc = choose_shape(pr, dl))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->sum1, (size_t)P.n_bins))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->sum2, (size_t)P.n_bins))) return bail(rc);
+  if (pr->tally_mode == MCDC_TALLY_GLOBAL)
+    if ((rc = dalloc(pr, &pr->tally, (size_t)P.n_bins))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->region, 4))) return bail(rc);
+  pr->region_batch = pr->region + 2;
+  if ((rc = dalloc(pr, &pr->stats, 1))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->error, 4))) return bail(rc);
+  if ((rc = ensure_work_slots(pr, 64))) return bail(rc);
+  if (cudaEventCreate(&pr->ev0) != cudaSuccess || cudaEventCreate(&pr->ev1) != cudaSuccess ||
+      cudaEventCreate(&pr->ev2) != cudaSuccess ||
+      cudaMallocHost(&pr->h_stats, sizeof(Stats)) != cudaSuccess ||
+      cudaMallocHost(&pr->h_error, sizeof(int32_t) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    fail(MCDC_ERR_CUDA, "event or pinned buffer creation failed");
+    return bail(MCDC_ERR_CUDA);
+  }
+  if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
+    cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_bins);
+    if (e != cudaSuccess) { fail(MCDC_ERR_CUDA, cudaGetErrorString(e)); return bail(MCDC_ERR_CUDA); }
+  }
+  *out = pr;
+  return MCDC_OK;
+}
+
+int64_t mcdc_tally_size(const struct mcdc_problem *pr) { return pr ? pr->P.n_bins : -1; }
+
+void mcdc_problem_destroy(struct mcdc_problem *pr) { release(pr); }
+
+int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, double upper_ratio,
+                            double survival_ratio, int32_t nmax) {
+  g_err.clear();
+  if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
+  if (w_lower == nullptr) {
+    pr->P.ww_lower = nullptr;
+    pr->P.ww_lower32 = nullptr;
+    return MCDC_OK;
+  }
+  if (!(upper_ratio > survival_ratio && survival_ratio > 1.0) || nmax < 2 || nmax > 1024)
+    return fail(MCDC_ERR_INVALID, "need 1 < survival_ratio < upper_ratio and 2 <= nmax <= 1024");
+  CK(cudaSetDevice(pr->device));
+  const size_t nb = (size_t)pr->P.n_bins;
+  std::vector<double> h(nb);
+  if (is_device_ptr(w_lower)) CK(cudaMemcpy(h.data(), w_lower, nb * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(h.data(), w_lower, nb * 8);
+  std::vector<float> h32(nb);
+  for (size_t q = 0; q < nb; ++q) {
+    if (std::isnan(h[q])) return fail(MCDC_ERR_INVALID, "weight-window bound is NaN");
+    h32[q] = (float)h[q];
+  }
+  if (!pr->ww64) {
+    int rc;
+    if ((rc = dalloc(pr, &pr->ww64, nb))) return rc;
+    if ((rc = dalloc(pr, &pr->ww32, nb))) return rc;
+  }
+  CK(cudaMemcpy(pr->ww64, h.data(), nb * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pr->ww32, h32.data(), nb * 4, cudaMemcpyHostToDevice));
+  pr->P.ww_lower = pr->ww64;
+  pr->P.ww_lower32 = pr->ww32;
+  pr->P.ww_upper = upper_ratio;
+  pr->P.ww_survival = survival_ratio;
+  pr->P.ww_nmax = nmax;
+  return ensure_overflow(pr);
+}
+
+int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *stats) {
+  g_err.clear();
+  if (!pr || !a) return fail(MCDC_ERR_INVALID, "problem and args are required");
+  if (a->n_histories == 0) return fail(MCDC_ERR_INVALID, "n_histories must be > 0");
+  CK(cudaSetDevice(pr->device));
+  cudaStream_t s = (cudaStream_t)a->stream;
+  const DevProblem &P = pr->P;
+  int B = a->n_batches > 0 ? a->n_batches : default_batches(pr, a->n_histories);
+  if (B < 2 || (uint64_t)B > a->n_histories)
+    return fail(MCDC_ERR_INVALID, "need 2 <= n_batches <= n_histories");
+  if (int rc = ensure_overflow(pr)) return rc;
+  if (int rc = ensure_work_slots(pr, pr->tally_mode == MCDC_TALLY_GLOBAL ? B : 1)) return rc;
+
+  const size_t nb = (size_t)P.n_bins;
+  const bool mean_dev = is_device_ptr(a->mean_out), rel_dev = is_device_ptr(a->relerr_out);
+  const bool s1_dev = is_device_ptr(a->sum1_out), s2_dev = is_device_ptr(a->sum2_out);
+  const bool rec_dev = is_device_ptr(a->records);
+  if (a->records && a->n_records == 0) return fail(MCDC_ERR_INVALID, "records given with n_records == 0");
+  if ((a->mean_out && !mean_dev) || (a->relerr_out && !rel_dev)) {
+    if (!pr->mean_tmp) {
+      int rc;
+      if ((rc = dalloc(pr, &pr->mean_tmp, nb))) return rc;
+      if ((rc = dalloc(pr, &pr->rel_tmp, nb))) return rc;
+    }
+  }
+  Record *rec_buf = nullptr;
+  uint64_t n_rec = a->records ? std::min<uint64_t>(a->n_records, a->n_histories) : 0;
+  if (a->records) {
+    if (rec_dev) {
+      rec_buf = (Record *)a->records;
+    } else {
+      if (pr->rec_cap < n_rec) {
+        int rc;
+        if ((rc = dalloc(pr, &pr->rec_tmp, (size_t)n_rec))) return rc;
+        pr->rec_cap = n_rec;
+      }
+      rec_buf = pr->rec_tmp;
+    }
+  }
+
+  CK(cudaEventRecord(pr->ev0, s));
+  CK(cudaMemsetAsync(pr->sum1, 0, nb * 8, s));
+  CK(cudaMemsetAsync(pr->sum2, 0, nb * 8, s));
+  CK(cudaMemsetAsync(pr->region, 0, 4 * sizeof(double), s));
+  CK(cudaMemsetAsync(pr->stats, 0, sizeof(Stats), s));
+  CK(cudaMemsetAsync(pr->error, 0, 4 * sizeof(int32_t), s));
+  CK(cudaMemsetAsync(pr->work, 0, sizeof(unsigned long long) * pr->work_slots, s));
+
+  RunArgs A{};
+  A.n_hist = a->n_histories;
+  A.offset = a->hist_offset;
+  A.seed = a->seed;
+  A.n_batches = B;
+  A.sum1 = pr->sum1;
+  A.sum2 = pr->sum2;
+  A.region = pr->region;
+  A.stats = pr->stats;
+  A.records = rec_buf;
+  A.n_records = n_rec;
+  A.error = pr->error;
+  A.overflow = pr->overflow;
+  A.overflow_cap = pr->overflow_cap;
+  A.warp_aggregate = pr->warp_aggregate;
+  A.tally = pr->tally;
+
+  CK(cudaEventRecord(pr->ev1, s));
+  if (pr->tally_mode == MCDC_TALLY_SHARED) {
+    A.work = pr->work;
+    A.batch = 0;
+    A.chunk = 0;
+    CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+  } else {
+    for (int b = 0; b < B; ++b) {
+      A.work = pr->work + b;
+      A.batch = b;
+      const uint64_t nb_hist = a->n_histories / B + 1;
+      A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));
+      CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+      CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+    }
+  }
+  CK(cudaEventRecord(pr->ev2, s));
+
+  // outputs
+  double *mean_d = a->mean_out ? (mean_dev ? a->mean_out : pr->mean_tmp) : nullptr;
+  double *rel_d = a->relerr_out ? (rel_dev ? a->relerr_out : pr->rel_tmp) : nullptr;
+  if (mean_d || rel_d)
+    CK(launch_finalize(s, (int64_t)nb, pr->sum1, pr->sum2, a->n_histories, B, P.volume, mean_d,
+                       rel_d, pr->sms));
+  if (a->mean_out && !mean_dev)
+    CK(cudaMemcpyAsync(a->mean_out, pr->mean_tmp, nb * 8, cudaMemcpyDeviceToHost, s));
+  if (a->relerr_out && !rel_dev)
+    CK(cudaMemcpyAsync(a->relerr_out, pr->rel_tmp, nb * 8, cudaMemcpyDeviceToHost, s));
+  if (a->sum1_out)
+    CK(cudaMemcpyAsync(a->sum1_out, pr->sum1, nb * 8, s1_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (a->sum2_out)
+    CK(cudaMemcpyAsync(a->sum2_out, pr->sum2, nb * 8, s2_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (a->records && !rec_dev)
+    CK(cudaMemcpyAsync(a->records, rec_buf, n_rec * sizeof(Record), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pr->h_stats, pr->stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pr->h_error, pr->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  double region_h[2] = {0, 0};
+  const bool need_sync = (s == nullptr) || stats || a->scalar_out || (a->mean_out && !mean_dev) ||
+                         (a->relerr_out && !rel_dev) || (a->sum1_out && !s1_dev) ||
+                         (a->sum2_out && !s2_dev) || (a->records && !rec_dev);
+  if (a->scalar_out) CK(cudaMemcpyAsync(region_h, pr->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!need_sync) return MCDC_OK;
+  CK(cudaStreamSynchronize(s));
+  if (a->scalar_out) {
+    const double nv = (double)a->n_histories * P.volume, Bd = (double)B;
+    const double m = region_h[0] / nv;
+    double ss = region_h[1] - region_h[0] * region_h[0] / Bd;
+    if (ss < 0.0) ss = 0.0;
+    const double var = (Bd * Bd / (nv * nv)) * ss / (Bd * (Bd - 1.0));
+    a->scalar_out[0] = m;
+    a->scalar_out[1] = m != 0.0 ? std::sqrt(var) / std::fabs(m) : 0.0;
+  }
+  if (stats) {
+    const Stats &h = *pr->h_stats;
+    stats->histories = h.histories; stats->segments = h.segments;
+    stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
+    stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
+    stats->splits = h.splits; stats->children = h.children;
+    stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
+    stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
+    stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
+    float k_ms = 0.f, t_ms = 0.f;
+    cudaEventElapsedTime(&k_ms, pr->ev1, pr->ev2);
+    cudaEventElapsedTime(&t_ms, pr->ev0, pr->ev2);
+    stats->kernel_ms = k_ms;
+    stats->total_ms = t_ms;
+    stats->block_size = pr->block;
+    stats->bank_per_cta = pr->S;
+    stats->ctas_per_sm = pr->ctas_per_sm;
+    stats->tally_mode = pr->tally_mode;
+    stats->n_batches = B;
+    stats->warp_aggregate = pr->warp_aggregate;
+  }
+  if (*pr->h_error & ERRBIT_OVERFLOW)
+    return fail(MCDC_ERR_BANK_OVERFLOW, "split children overflowed the per-CTA stack; raise overflow_per_cta");
+  if (*pr->h_error & ERRBIT_TIMEOUT) return fail(MCDC_ERR_TIMEOUT, "a bounded device wait gave up");
+  return MCDC_OK;
+}
+
+int mcdc_run(struct mcdc_problem *pr, uint64_t n_histories, uint64_t seed, double *tally_out) {
+  mcdc_run_args a;
+  std::memset(&a, 0, sizeof a);
+  a.n_histories = n_histories;
+  a.seed = seed;
+  a.mean_out = tally_out;
+  a.stream = nullptr;
+  int rc = mcdc_run_ex(pr, &a, nullptr);
+  if (rc == MCDC_OK) {
+    cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return fail(MCDC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// common.cuh -- device data layout shared by the tracker kernels and the host
+// side of the library: problem tables, run arguments, the counter-based
+// generator and the warp-aggregated queue append.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcdc {
+
+constexpr int kMaxGroups = 16;
+constexpr int kWarp = 32;
+
+enum End : int32_t { END_NONE = 0, END_ABSORBED = 1, END_LEAKED = 2, END_CENSUSED = 3,
+                     END_ROULETTE = 4 };
+
+enum ErrBits : int32_t { ERRBIT_OVERFLOW = 1, ERRBIT_TIMEOUT = 2 };
+
+// Problem tables in device memory (built once at create).
+struct DevProblem {
+  int32_t n[3];
+  int32_t bounded[3];
+  double origin[3];
+  double width[3];
+  int32_t bc[6];
+  int32_t M, G, T, T1;        // T time bins (0: steady), T1 = max(T, 1)
+  int64_t n_cells, n_bins;
+  double volume;
+  const uint8_t *material;    // [cells]
+  // FP64 tables
+  const double *sigma_t;      // [M*G]
+  const double *scat;         // [M*G]  sigma_s / sigma_t
+  const double *cdf;          // [M*G*G] cumulative transfer, flat 1.0 after the last rise
+  const double *speed;        // [G]
+  const double *edges;        // [T+1]
+  const double *src_cdf;      // [G]
+  // FP32 copies
+  const float *sigma_t32, *scat32, *cdf32, *speed32, *inv_speed32, *src_cdf32;
+  // source
+  double src_lo[3], src_hi[3];
+  int32_t src_kind;
+  double src_dir[3];
+  double t0, t1;
+  // weight windows (nullptr: analog)
+  const double *ww_lower;     // [n_bins]
+  const float *ww_lower32;
+  double ww_upper, ww_survival;
+  int32_t ww_nmax;
+  int32_t region_lo[3], region_hi[3];
+};
+
+// One particle as it moves between the tracker phases (kept in registers).
+template <class R>
+struct Part {
+  double x, y, z;     // position (FP64 in both precisions)
+  double t;           // time (FP64)
+  R ux, uy, uz;       // direction
+  R w;                // weight
+  int32_t g;
+  int32_t i, j, k;    // cell
+  int32_t tbin;
+  uint32_t ctr, serial;
+  uint64_t hid;
+  uint32_t nseg, ncol, ncross;
+};
+
+// Per-history record (mirrors mcdc_record).
+struct Record {
+  uint64_t hid;
+  int32_t end, g;
+  uint32_t ctr, n_seg, n_col, n_cross;
+  double x, y, z, t, w;
+};
+
+// Event counters; summed per warp, then one atomic per warp per field.
+struct Stats {
+  unsigned long long histories, segments, collisions, crossings, census;
+  unsigned long long absorbed, leaked, censused, splits, children;
+  unsigned long long roulette_killed, roulette_survived;
+  double w_source, w_absorbed, w_leaked, w_censused;
+};
+
+struct RunArgs {
+  uint64_t n_hist;            // histories in the whole run
+  uint64_t offset;            // first history id
+  uint64_t seed;
+  int32_t n_batches;
+  // shared-tally mode: CTAs claim whole batches through *work
+  // global-tally mode: this launch covers batch `batch`; CTAs claim chunks
+  unsigned long long *work;
+  int32_t batch;
+  int32_t chunk;
+  double *tally;              // global mode: batch tally [n_bins]
+  double *sum1, *sum2;        // shared mode: folded per batch
+  double *region;             // [2]: sum of region batch sums and of their squares
+  Stats *stats;
+  Record *records;            // or nullptr
+  uint64_t n_records;
+  int32_t *error;             // ERRBIT_* flags
+  // per-CTA overflow stacks for split children: [gridDim.x][overflow_cap]
+  void *overflow;
+  int32_t overflow_cap;
+  int32_t warp_aggregate;
+};
+
+// ---- counter-based generator: Philox4x32-10 (Salmon et al., SC'11) -------
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// draw one block for the particle and advance its counter
+template <class R>
+__device__ __forceinline__ U4 draw(const Part<R> &p, uint32_t &ctr, uint64_t seed) {
+  U4 r = philox4x32_10(ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32),
+                       (uint32_t)seed, (uint32_t)(seed >> 32));
+  ctr += 1;
+  return r;
+}
+
+// 53 bits -> (0, 1]
+__device__ __forceinline__ double u01_f64(uint32_t hi, uint32_t lo) {
+  const uint64_t bits = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return (double)((bits >> 11) + 1ull) * 0x1.0p-53;
+}
+
+// 24 bits -> (0, 1]: the top 24 bits of the same word pair, so an FP32 run
+// follows its FP64 twin until the first decision the rounding flips.
+__device__ __forceinline__ float u01_f32(uint32_t hi) {
+  return (float)((hi >> 8) + 1u) * 0x1.0p-24f;
+}
+
+// ---- warp-level queue append: ballot + popc prefix, one atomic per warp ---
+__device__ __forceinline__ int warp_append(bool pred, int *counter) {
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(counter, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ uint64_t batch_start(uint64_t n, int32_t B, int32_t b) {
+  const uint64_t q = n / (uint64_t)B, r = n % (uint64_t)B;
+  const uint64_t bb = (uint64_t)b;
+  return bb * q + (bb < r ? bb : r);
+}
+
+}  // namespace mcdc

@@ -1,0 +1,35 @@
+// launch.h -- host-side entry points into the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace mcdc {
+
+struct Layout;
+
+struct TrackKey {
+  bool f64;
+  bool shared;
+  int dim;   // 1 or 3
+};
+
+// Launches the persistent tracker for one configuration.
+cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem_bytes,
+                         cudaStream_t stream, const DevProblem &P, const RunArgs &A,
+                         const Layout &L);
+// Raises the dynamic shared-memory limit of that instantiation.
+cudaError_t prepare_track(const TrackKey &key, int smem_bytes);
+// Registers per thread of that instantiation (for occupancy decisions).
+int track_regs(const TrackKey &key);
+// Resident CTAs per SM for a block size and dynamic shared memory.
+int track_occupancy(const TrackKey &key, int block, int smem_bytes);
+
+// batch fold (global tally mode): sum1 += x, sum2 += x^2, region partial, x = 0
+cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
+                        double *sum2, double *region_batch, double *region, int sms);
+// mean and relative error from the batch sums (host-side formula mirrored)
+cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,
+                            const double *sum2, uint64_t n_hist, int n_batches, double volume,
+                            double *mean, double *relerr, int sms);
+
+}  // namespace mcdc

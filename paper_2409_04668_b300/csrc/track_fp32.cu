@@ -1,0 +1,52 @@
+// track_fp32.cu -- FP32-split instantiations of the tracker (FP32 direction,
+// distance and cross sections; FP64 position, time and tally reduction) and
+// the dispatch over both precisions.
+#include "launch.h"
+#include "tracker.cuh"
+
+namespace mcdc {
+
+cudaError_t launch_track_f64(const TrackKey &, int, int, int, cudaStream_t, const DevProblem &,
+                             const RunArgs &, const Layout &);
+cudaError_t prepare_track_f64(const TrackKey &, int);
+int track_regs_f64(const TrackKey &);
+int track_occupancy_f64(const TrackKey &, int, int);
+
+namespace {
+template <bool SH, int DIM>
+void *fp32_kernel() { return (void *)k_track<PrecF32, SH, DIM>; }
+
+void *pick(const TrackKey &k) {
+  if (k.shared) return k.dim == 1 ? fp32_kernel<true, 1>() : fp32_kernel<true, 3>();
+  return k.dim == 1 ? fp32_kernel<false, 1>() : fp32_kernel<false, 3>();
+}
+}  // namespace
+
+cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem, cudaStream_t stream,
+                         const DevProblem &P, const RunArgs &A, const Layout &L) {
+  if (key.f64) return launch_track_f64(key, grid, block, smem, stream, P, A, L);
+  void *args[] = {(void *)&P, (void *)&A, (void *)&L};
+  return cudaLaunchKernel(pick(key), dim3(grid), dim3(block), args, (size_t)smem, stream);
+}
+
+cudaError_t prepare_track(const TrackKey &key, int smem) {
+  if (key.f64) return prepare_track_f64(key, smem);
+  return cudaFuncSetAttribute(pick(key), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+int track_occupancy(const TrackKey &key, int block, int smem) {
+  if (key.f64) return track_occupancy_f64(key, block, smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(key), block, (size_t)smem) != cudaSuccess)
+    return -1;
+  return n;
+}
+
+int track_regs(const TrackKey &key) {
+  if (key.f64) return track_regs_f64(key);
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, pick(key)) != cudaSuccess) return -1;
+  return a.numRegs;
+}
+
+}  // namespace mcdc

@@ -1,0 +1,42 @@
+// track_fp64.cu -- FP64 instantiations of the tracker.  This translation unit
+// is compiled with -fmad=false so that every product and sum is rounded on
+// its own, in the order the source states them.
+#include "launch.h"
+#include "tracker.cuh"
+
+namespace mcdc {
+namespace {
+template <bool SH, int DIM>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM>; }
+
+void *pick(const TrackKey &k) {
+  if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1>() : fp64_kernel<true, 3>();
+  return k.dim == 1 ? fp64_kernel<false, 1>() : fp64_kernel<false, 3>();
+}
+}  // namespace
+
+cudaError_t launch_track_f64(const TrackKey &key, int grid, int block, int smem,
+                             cudaStream_t stream, const DevProblem &P, const RunArgs &A,
+                             const Layout &L) {
+  void *args[] = {(void *)&P, (void *)&A, (void *)&L};
+  return cudaLaunchKernel(pick(key), dim3(grid), dim3(block), args, (size_t)smem, stream);
+}
+
+cudaError_t prepare_track_f64(const TrackKey &key, int smem) {
+  return cudaFuncSetAttribute(pick(key), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+int track_occupancy_f64(const TrackKey &key, int block, int smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(key), block, (size_t)smem) != cudaSuccess)
+    return -1;
+  return n;
+}
+
+int track_regs_f64(const TrackKey &key) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, pick(key)) != cudaSuccess) return -1;
+  return a.numRegs;
+}
+
+}  // namespace mcdc

@@ -1,0 +1,279 @@
+"""Thin Python binding of the C-ABI in ``include/mcdc.h`` (argument marshalling
+only: every step of a run executes in the CUDA library).
+
+The low-level functions keep the C names (``mcdc_problem_create``,
+``mcdc_run``, ``mcdc_run_ex``, ``mcdc_set_weight_windows``,
+``mcdc_problem_destroy``, ...).  ``Problem`` wraps a handle built from a
+``workloads.Problem`` description.  Device outputs are torch tensors (their
+``data_ptr``); the run's stream is torch's current stream unless given.
+
+Importing this module loads ``libmcdc_b300.so`` and raises if it is missing:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmcdc_b300.so")
+
+MCDC_OK = 0
+MCDC_ERR_INVALID, MCDC_ERR_OOM, MCDC_ERR_CUDA = -1, -2, -3
+MCDC_ERR_BANK_OVERFLOW, MCDC_ERR_TIMEOUT, MCDC_ERR_NO_DEVICE = -4, -5, -6
+PREC_FP64, PREC_FP32 = 0, 1
+TALLY_AUTO, TALLY_SHARED, TALLY_GLOBAL = 0, 1, 2
+
+
+class mcdc_mesh(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("material", C.c_void_p), ("bc", C.c_int32 * 6)]
+
+
+class mcdc_materials(C.Structure):
+    _fields_ = [("n_materials", C.c_int32), ("n_groups", C.c_int32),
+                ("sigma_t", C.c_void_p), ("sigma_s", C.c_void_p), ("transfer", C.c_void_p),
+                ("speed", C.c_void_p)]
+
+
+class mcdc_source(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("kind", C.c_int32),
+                ("dir", C.c_double * 3), ("group_pdf", C.c_void_p),
+                ("t0", C.c_double), ("t1", C.c_double)]
+
+
+class mcdc_time_grid(C.Structure):
+    _fields_ = [("n_bins", C.c_int32), ("edges", C.c_void_p)]
+
+
+class mcdc_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tally_mode", C.c_int32), ("n_batches", C.c_int32),
+                ("block_size", C.c_int32), ("bank_per_cta", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("warp_aggregate", C.c_int32),
+                ("autotune", C.c_int32), ("overflow_per_cta", C.c_int32),
+                ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3)]
+
+
+class mcdc_stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in (
+        "histories", "segments", "collisions", "crossings", "census", "absorbed", "leaked",
+        "censused", "splits", "children", "roulette_killed", "roulette_survived")] + [
+        (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused",
+                                  "kernel_ms", "total_ms")] + [
+        (k, C.c_int32) for k in ("block_size", "bank_per_cta", "ctas_per_sm", "tally_mode",
+                                 "n_batches", "warp_aggregate")]
+
+
+class mcdc_record(C.Structure):
+    _fields_ = [("hid", C.c_uint64), ("end", C.c_int32), ("g", C.c_int32),
+                ("ctr", C.c_uint32), ("n_seg", C.c_uint32), ("n_col", C.c_uint32),
+                ("n_cross", C.c_uint32), ("x", C.c_double), ("y", C.c_double),
+                ("z", C.c_double), ("t", C.c_double), ("w", C.c_double)]
+
+
+RECORD_DTYPE = np.dtype([
+    ("hid", np.uint64), ("end", np.int32), ("g", np.int32), ("ctr", np.uint32),
+    ("n_seg", np.uint32), ("n_col", np.uint32), ("n_cross", np.uint32),
+    ("x", np.float64), ("y", np.float64), ("z", np.float64), ("t", np.float64),
+    ("w", np.float64)], align=True)
+assert RECORD_DTYPE.itemsize == C.sizeof(mcdc_record)
+
+
+class mcdc_run_args(C.Structure):
+    _fields_ = [("n_histories", C.c_uint64), ("n_batches", C.c_int32), ("seed", C.c_uint64),
+                ("hist_offset", C.c_uint64), ("mean_out", C.c_void_p),
+                ("relerr_out", C.c_void_p), ("sum1_out", C.c_void_p),
+                ("sum2_out", C.c_void_p), ("scalar_out", C.c_void_p),
+                ("records", C.c_void_p), ("n_records", C.c_uint64), ("stream", C.c_void_p)]
+
+
+# name -> (restype, argtypes); kept in the order of include/mcdc.h
+SIGNATURES = {
+    "mcdc_default_options": (None, [C.POINTER(mcdc_options)]),
+    "mcdc_problem_create": (C.c_int, [C.POINTER(mcdc_mesh), C.POINTER(mcdc_materials),
+                                      C.POINTER(mcdc_source), C.POINTER(mcdc_time_grid),
+                                      C.POINTER(mcdc_options), C.POINTER(C.c_void_p)]),
+    "mcdc_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "mcdc_run_ex": (C.c_int, [C.c_void_p, C.POINTER(mcdc_run_args), C.POINTER(mcdc_stats)]),
+    "mcdc_set_weight_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                          C.c_int32]),
+    "mcdc_tally_size": (C.c_int64, [C.c_void_p]),
+    "mcdc_problem_destroy": (None, [C.c_void_p]),
+    "mcdc_last_error": (C.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2409_04668_b300.build` (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+mcdc_default_options = _lib.mcdc_default_options
+mcdc_problem_create = _lib.mcdc_problem_create
+mcdc_run = _lib.mcdc_run
+mcdc_run_ex = _lib.mcdc_run_ex
+mcdc_set_weight_windows = _lib.mcdc_set_weight_windows
+mcdc_tally_size = _lib.mcdc_tally_size
+mcdc_problem_destroy = _lib.mcdc_problem_destroy
+mcdc_last_error = _lib.mcdc_last_error
+
+
+class MCDCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mcdc error {code}: {msg}")
+        self.code = code
+
+
+def check(rc):
+    if rc != MCDC_OK:
+        raise MCDCError(rc, mcdc_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Problem:
+    """A problem handle on the current CUDA device (see mcdc_problem_create)."""
+
+    def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
+                 block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
+                 overflow_per_cta=0, region=None):
+        self.desc = prob
+        keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        m = mcdc_mesh()
+        m.nx, m.ny, m.nz = (int(v) for v in prob.n)
+        m.x0, m.y0, m.z0 = (float(v) for v in prob.origin)
+        m.dx, m.dy, m.dz = (float(v) for v in prob.width)
+        m.material = arr(prob.material, np.uint8)
+        m.bc[:] = [int(v) for v in prob.bc]
+        mt = mcdc_materials()
+        st = np.asarray(prob.sigma_t, dtype=np.float64)
+        mt.n_materials, mt.n_groups = st.shape
+        mt.sigma_t = arr(st, np.float64)
+        mt.sigma_s = arr(prob.sigma_s, np.float64)
+        mt.transfer = arr(prob.transfer, np.float64)
+        mt.speed = arr(prob.speed, np.float64)
+        s = mcdc_source()
+        s.lo[:] = [float(v) for v in prob.src_lo]
+        s.hi[:] = [float(v) for v in prob.src_hi]
+        s.kind = int(prob.src_kind)
+        s.dir[:] = [float(v) for v in prob.src_dir]
+        s.group_pdf = arr(prob.src_pdf, np.float64)
+        s.t0, s.t1 = float(prob.src_t0), float(prob.src_t1)
+        tg = mcdc_time_grid()
+        if prob.edges is not None:
+            tg.n_bins = len(prob.edges) - 1
+            tg.edges = arr(prob.edges, np.float64)
+        o = mcdc_options()
+        mcdc_default_options(C.byref(o))
+        o.precision = precision
+        o.tally_mode = tally_mode
+        o.n_batches = n_batches
+        o.block_size = block_size
+        o.bank_per_cta = bank_per_cta
+        o.ctas_per_sm = ctas_per_sm
+        o.warp_aggregate = warp_aggregate
+        o.overflow_per_cta = overflow_per_cta
+        lo, hi = region if region is not None else (prob.region_lo, prob.region_hi)
+        o.region_lo[:] = [int(v) for v in lo]
+        o.region_hi[:] = [int(v) for v in hi]
+        h = C.c_void_p()
+        check(mcdc_problem_create(C.byref(m), C.byref(mt), C.byref(s), C.byref(tg), C.byref(o),
+                                  C.byref(h)))
+        self.handle = h
+        self.n_bins = int(mcdc_tally_size(h))
+        self.shape = tuple(prob.tally_shape)
+
+    def set_weight_windows(self, lower, upper_ratio=5.0, survival_ratio=2.5, nmax=16):
+        if lower is None:
+            check(mcdc_set_weight_windows(self.handle, None, 0.0, 0.0, 0))
+            return
+        if isinstance(lower, np.ndarray):
+            lower = np.ascontiguousarray(lower, dtype=np.float64)
+        check(mcdc_set_weight_windows(self.handle, _ptr(lower), float(upper_ratio),
+                                      float(survival_ratio), int(nmax)))
+
+    def run_ex(self, n, seed, offset=0, batches=0, mean=None, relerr=None, sum1=None, sum2=None,
+               records=None, n_records=None, stream=None, want_scalar=True, want_stats=True):
+        """One run; outputs are filled in place (numpy arrays or torch tensors).
+        Returns (stats dict or None, (scalar mean, scalar relerr) or None)."""
+        a = mcdc_run_args()
+        a.n_histories = int(n)
+        a.n_batches = int(batches)
+        a.seed = int(seed)
+        a.hist_offset = int(offset)
+        a.mean_out = _ptr(mean)
+        a.relerr_out = _ptr(relerr)
+        a.sum1_out = _ptr(sum1)
+        a.sum2_out = _ptr(sum2)
+        scal = np.zeros(2) if want_scalar else None
+        a.scalar_out = _ptr(scal)
+        a.records = _ptr(records)
+        a.n_records = int(n_records if n_records is not None else
+                          (len(records) if records is not None else 0))
+        a.stream = stream
+        st = mcdc_stats() if want_stats else None
+        check(mcdc_run_ex(self.handle, C.byref(a), C.byref(st) if st is not None else None))
+        stats = {k: getattr(st, k) for k, _ in mcdc_stats._fields_} if st is not None else None
+        return stats, (tuple(scal) if scal is not None else None)
+
+    def run(self, n, seed, tally_out=None):
+        check(mcdc_run(self.handle, int(n), int(seed), _ptr(tally_out)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mcdc_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def run_numpy(prob, n, seed, offset=0, batches=0, records=0, **opts):
+    """Convenience: one run with host outputs; returns a dict like the
+    oracle wrapper's (mean, relerr, sum1, sum2 shaped [nz,ny,nx,G,T],
+    scalar, counts, records)."""
+    with Problem(prob, **opts) as P:
+        nb = P.n_bins
+        mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
+        rec = np.zeros(records, dtype=RECORD_DTYPE) if records else None
+        stats, scal = P.run_ex(n, seed, offset=offset, batches=batches, mean=mean, relerr=rel,
+                               sum1=s1, sum2=s2, records=rec)
+        shp = P.shape
+    return {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "sum1": s1.reshape(shp),
+            "sum2": s2.reshape(shp), "scalar": scal, "counts": stats, "records": rec}

@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every function include/mcdc.h declares, and rejects invalid problems on the
+host with MCDC_ERR_INVALID before touching a device (or reports
+MCDC_ERR_NO_DEVICE when none is present)."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2409_04668_b300 import build as B
+from paper_2409_04668_b300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "mcdc.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(mcdc_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_2409_04668_b300 import mcdc
+    return mcdc
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mcdc_problem_create", "mcdc_run", "mcdc_problem_destroy", "mcdc_run_ex",
+                     "mcdc_set_weight_windows", "mcdc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = C.CDLL(lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+        assert name in lib.SIGNATURES, name
+
+
+def _create(lib, prob, **kw):
+    try:
+        P = lib.Problem(prob, **kw)
+    except lib.MCDCError as e:
+        return e.code, str(e)
+    P.close()
+    return 0, ""
+
+
+def _bad(prob, **changes):
+    import dataclasses
+    return dataclasses.replace(prob, **changes)
+
+
+@pytest.mark.parametrize("case", [
+    "sigma_s_gt_sigma_t", "negative_sigma", "nan_sigma", "bad_transfer_row", "bad_material_id",
+    "source_outside", "source_before_first_edge", "edges_not_increasing", "bad_speed",
+    "bad_pdf", "beam_not_unit", "bad_bc"])
+def test_invalid_problems_rejected_on_host(lib, case):
+    p = W.c2_two_region()
+    if case == "sigma_s_gt_sigma_t":
+        q = _bad(p, sigma_s=p.sigma_t * 1.5)
+    elif case == "negative_sigma":
+        q = _bad(p, sigma_t=-p.sigma_t)
+    elif case == "nan_sigma":
+        st = p.sigma_t.copy()
+        st[0, 0] = math.nan
+        q = _bad(p, sigma_t=st)
+    elif case == "bad_transfer_row":
+        q = _bad(p, transfer=p.transfer * 0.5)
+    elif case == "bad_material_id":
+        m = p.material.copy()
+        m[0, 0, 3] = 7
+        q = _bad(p, material=m)
+    elif case == "source_outside":
+        q = _bad(p, src_hi=(25.0, 0.0, 0.0))
+    elif case == "source_before_first_edge":
+        q = _bad(p, src_t0=-1.0, src_t1=-1.0)
+    elif case == "edges_not_increasing":
+        e = p.edges.copy()
+        e[5] = e[4]
+        q = _bad(p, edges=e)
+    elif case == "bad_speed":
+        q = _bad(p, speed=np.array([0.0]))
+    elif case == "bad_pdf":
+        q = _bad(p, src_pdf=np.array([0.5]))
+    elif case == "beam_not_unit":
+        q = _bad(p, src_kind=W.SRC_BEAM, src_dir=(1.0, 1.0, 0.0))
+    elif case == "bad_bc":
+        q = _bad(p, bc=(0, 0, 0, 0, 0, 9))
+    code, msg = _create(lib, q)
+    assert code == lib.MCDC_ERR_INVALID, (code, msg)
+
+
+def test_valid_problem_without_gpu_reports_no_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    code, msg = _create(lib, W.c1_slab())
+    assert code == lib.MCDC_ERR_NO_DEVICE, msg

@@ -1,0 +1,218 @@
+"""GPU parity against the FP64 CPU oracle, through the C-ABI.
+
+FP64 mode: every history's primary particle ends the same way, in the same
+group, after the same number of flights, collisions, crossings and random
+draws, at the same place and time (relative 1e-12); every tally bin's batch
+sums agree to relative 1e-9.  FP32-split mode: bins agree statistically with
+an independent oracle run (|z| < 4 on coarsened bins), the paired bias
+against the FP64 twin is bounded, and particle balance is exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2409_04668_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_TALLY = 1e-9
+
+
+@pytest.fixture(scope="module")
+def mcdc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2409_04668_b300 import build
+    build.build()
+    from paper_2409_04668_b300 import mcdc as M
+    return M
+
+
+def small_channel(n=12, G=7, T=8, seed=3):
+    """A scaled-down copy of the channel problem: same materials, groups,
+    speeds and time grid shape on an n^3 mesh."""
+    full = W.c3_channel(seed)
+    f = 60 // n
+    mat = full.material[::f, ::f, ::f].copy()
+    return W.box("channel_small", (n, n, n), (1.0 * f,) * 3, mat, full.sigma_t, full.sigma_s /
+                 full.sigma_t, full.transfer, full.speed, (0.0,) * 3, (10.0,) * 3,
+                 np.linspace(0.0, 1e-6, T + 1), (n // 2,) * 3, (n,) * 3)
+
+
+def compare_records(gpu, orc, dim):
+    assert np.array_equal(gpu["hid"], orc["hid"])
+    for f in ("end", "g", "ctr", "n_seg", "n_col", "n_cross"):
+        bad = np.nonzero(gpu[f] != orc[f])[0]
+        assert bad.size == 0, (f, bad[:10], gpu[f][bad[:5]], orc[f][bad[:5]])
+    axes = ("x", "t") if dim == 1 else ("x", "y", "z", "t")
+    for f in axes:
+        np.testing.assert_allclose(gpu[f], orc[f], rtol=1e-12, atol=1e-12 * (1 + np.abs(orc[f]).max()))
+    np.testing.assert_allclose(gpu["w"], orc["w"], rtol=1e-12)
+
+
+def compare_tallies(g, o):
+    for key in ("sum1", "sum2"):
+        a, b = g[key], o[key]
+        scale = np.maximum(np.abs(b), 1e-300)
+        rel = np.abs(a - b) / scale
+        assert np.all((rel <= REL_TALLY) | (np.abs(a - b) <= 1e-300)), (key, rel.max())
+    nz = o["mean"] != 0
+    np.testing.assert_allclose(g["mean"][nz], o["mean"][nz], rtol=REL_TALLY)
+    np.testing.assert_array_equal(g["mean"] == 0, o["mean"] == 0)
+    np.testing.assert_allclose(g["relerr"], o["relerr"], rtol=1e-6, atol=1e-12)
+
+
+COUNT_KEYS = ("histories", "segments", "collisions", "crossings", "census", "absorbed", "leaked",
+              "censused", "splits", "children", "roulette_killed", "roulette_survived")
+
+
+def compare_counts(g, o):
+    for k in COUNT_KEYS:
+        assert g[k] == o[k], (k, g[k], o[k])
+
+
+@pytest.mark.parametrize("mode", ["shared", "global"])
+def test_fp64_c1_slab_full_size(mcdc, mode):
+    prob = W.c1_slab()
+    N, B = 100_000, 32
+    tm = mcdc.TALLY_SHARED if mode == "shared" else mcdc.TALLY_GLOBAL
+    g = mcdc.run_numpy(prob, N, seed=1, batches=B, records=N, precision=mcdc.PREC_FP64,
+                       tally_mode=tm)
+    o = O.run(prob, N, seed=1, batches=B)
+    compare_tallies(g, o)
+    compare_counts(g["counts"], o["counts"])
+    compare_records(g["records"], O.trace(prob, 1, np.arange(N)), dim=1)
+
+
+@pytest.mark.parametrize("mode", ["shared", "global"])
+def test_fp64_c2_two_region_ragged(mcdc, mode):
+    prob = W.c2_two_region()
+    N, B = 100_003, 10
+    tm = mcdc.TALLY_SHARED if mode == "shared" else mcdc.TALLY_GLOBAL
+    g = mcdc.run_numpy(prob, N, seed=7, offset=12345, batches=B, records=N,
+                       precision=mcdc.PREC_FP64, tally_mode=tm, block_size=128,
+                       bank_per_cta=160)
+    o = O.run(prob, N, seed=7, offset=12345, batches=B)
+    compare_tallies(g, o)
+    compare_counts(g["counts"], o["counts"])
+    compare_records(g["records"], O.trace(prob, 7, 12345 + np.arange(N)), dim=1)
+
+
+@pytest.mark.parametrize("mode", ["shared", "global"])
+def test_fp64_3d_channel_small(mcdc, mode):
+    # the shared tally must fit one CTA's shared memory: 6^3 x 7 x 4 bins in FP64
+    prob = small_channel() if mode == "global" else small_channel(n=6, T=4)
+    N, B = 20_000, 8
+    tm = mcdc.TALLY_SHARED if mode == "shared" else mcdc.TALLY_GLOBAL
+    g = mcdc.run_numpy(prob, N, seed=3, batches=B, records=N, precision=mcdc.PREC_FP64,
+                       tally_mode=tm)
+    o = O.run(prob, N, seed=3, batches=B)
+    compare_tallies(g, o)
+    compare_counts(g["counts"], o["counts"])
+    compare_records(g["records"], O.trace(prob, 3, np.arange(N)), dim=3)
+    assert g["scalar"][0] == pytest.approx(o["scalar"][0], rel=REL_TALLY)
+
+
+def test_fp64_weight_windows_infinite_medium(mcdc):
+    mat = np.zeros((2, 2, 4), np.uint8)
+    prob = W.box("inf_ww", (4, 2, 2), (0.5, 1.0, 1.0), mat, [[1.0]], [[0.8]], np.ones((1, 1, 1)),
+                 [1.0], (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), None, (0, 0, 0), (4, 2, 2),
+                 bc=(W.BC_REFLECT,) * 6)
+    lower = np.random.default_rng(7).uniform(0.05, 0.6, size=prob.n_bins)
+    N, B = 20_000, 10
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP64, overflow_per_cta=8192) as P:
+        P.set_weight_windows(lower, 5.0, 2.5, 16)
+        s1, s2, mean, rel = (np.zeros(P.n_bins) for _ in range(4))
+        stats, scal = P.run_ex(N, 13, batches=B, sum1=s1, sum2=s2, mean=mean, relerr=rel)
+    o = O.run(prob, N, seed=13, batches=B,
+              ww={"lower": lower, "upper_ratio": 5.0, "survival_ratio": 2.5, "nmax": 16})
+    g = {"sum1": s1.reshape(prob.tally_shape), "sum2": s2.reshape(prob.tally_shape),
+         "mean": mean.reshape(prob.tally_shape), "relerr": rel.reshape(prob.tally_shape)}
+    compare_tallies(g, o)
+    compare_counts(stats, o["counts"])
+    assert stats["splits"] > 100 and stats["roulette_killed"] > 100
+
+
+def test_fp32_c2_statistical_and_paired_bias(mcdc):
+    prob = W.c2_two_region()
+    N = 1_000_000
+    g32 = mcdc.run_numpy(prob, N, seed=2, batches=40, precision=mcdc.PREC_FP32)
+    o = O.run(prob, N, seed=1, batches=40)
+    c = g32["counts"]
+    assert c["absorbed"] + c["leaked"] + c["censused"] == N
+    # coarsen to 20 x 10 blocks of (space, time): every block |z| < 4
+    def coarse(res):
+        s = res["mean"][0, 0, :, 0, :]
+        v = (res["mean"] * res["relerr"])[0, 0, :, 0, :] ** 2
+        return (s.reshape(20, 10, 10, 5).sum(axis=(1, 3)),
+                v.reshape(20, 10, 10, 5).sum(axis=(1, 3)))
+    gm, gv = coarse(g32)
+    om, ov = coarse(o)
+    ok = (gv + ov) > 0
+    z = (gm - om)[ok] / np.sqrt((gv + ov)[ok])
+    assert np.all(np.abs(z) < 4.0), np.abs(z).max()
+    # per bin: exceedances consistent with chance
+    s = np.sqrt((g32["mean"] * g32["relerr"]) ** 2 + (o["mean"] * o["relerr"]) ** 2)
+    nzb = s > 0
+    zb = (g32["mean"] - o["mean"])[nzb] / s[nzb]
+    assert (np.abs(zb) > 4).sum() <= 5
+    # paired with its FP64 twin (same seed, same random streams): the
+    # FP32-split bias of the region total stays far below the noise
+    g64 = mcdc.run_numpy(prob, N, seed=2, batches=40, precision=mcdc.PREC_FP64)
+    bias = g32["scalar"][0] / g64["scalar"][0] - 1.0
+    assert abs(bias) < 0.2 * g64["scalar"][1], (bias, g64["scalar"][1])
+
+
+def test_edge_cases(mcdc):
+    prob = W.c1_slab()
+    # the smallest run: two histories, two batches
+    g = mcdc.run_numpy(prob, 2, seed=5, batches=2, records=2, precision=mcdc.PREC_FP64)
+    o = O.run(prob, 2, seed=5, batches=2)
+    compare_tallies(g, o)
+    compare_records(g["records"], O.trace(prob, 5, np.arange(2)), dim=1)
+    # invalid run arguments are rejected
+    with mcdc.Problem(prob) as P:
+        with pytest.raises(mcdc.MCDCError):
+            P.run_ex(0, 1)
+        with pytest.raises(mcdc.MCDCError):
+            P.run_ex(10, 1, batches=11)
+        with pytest.raises(mcdc.MCDCError):
+            P.run_ex(10, 1, batches=1)
+
+
+def test_born_after_last_census(mcdc):
+    prob = W.c2_two_region()
+    import dataclasses
+    late = dataclasses.replace(prob, src_t0=0.0, src_t1=40.0)   # half are born after t = 20
+    N = 20_000
+    g = mcdc.run_numpy(late, N, seed=9, batches=4, records=N, precision=mcdc.PREC_FP64)
+    o = O.run(late, N, seed=9, batches=4)
+    compare_tallies(g, o)
+    compare_counts(g["counts"], o["counts"])
+    compare_records(g["records"], O.trace(late, 9, np.arange(N)), dim=1)
+
+
+def test_history_partition_invariance(mcdc):
+    prob = W.c2_two_region()
+    a = mcdc.run_numpy(prob, 40_000, seed=8, batches=4, precision=mcdc.PREC_FP64)
+    b1 = mcdc.run_numpy(prob, 20_000, seed=8, offset=0, batches=2, precision=mcdc.PREC_FP64)
+    b2 = mcdc.run_numpy(prob, 20_000, seed=8, offset=20_000, batches=2, precision=mcdc.PREC_FP64)
+    np.testing.assert_allclose(a["sum1"], b1["sum1"] + b2["sum1"], rtol=1e-11, atol=1e-300)
+
+
+def test_fp_full_size_c2_sampled_histories(mcdc):
+    """The full 1e7-history two-region workload: FP32-split balance is exact,
+    and in FP64 mode 2000 sampled histories match the oracle event for
+    event."""
+    prob = W.c2_two_region()
+    N = 10_000_000
+    g = mcdc.run_numpy(prob, N, seed=1, precision=mcdc.PREC_FP32)
+    c = g["counts"]
+    assert c["histories"] == N
+    assert c["absorbed"] + c["leaked"] + c["censused"] == N
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP64) as P:
+        rec = np.zeros(N, dtype=mcdc.RECORD_DTYPE)
+        stats, _ = P.run_ex(N, 1, records=rec)
+    pick = np.sort(np.random.default_rng(0).choice(N, 2000, replace=False))
+    compare_records(rec[pick], O.trace(prob, 1, pick), dim=1)
+    assert stats["absorbed"] + stats["leaked"] + stats["censused"] == N
