@@ -199,6 +199,27 @@ int64_t mcdc_tally_size(const struct mcdc_problem *prob);
 
 void mcdc_problem_destroy(struct mcdc_problem *prob);
 
+/* Allocation-free run (the paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc while transport runs, e.g. a code
+ * whose pool allocator owns all device memory, or a loop where an
+ * allocation would stall the device).  The problem must come from
+ * mcdc_problem_create, made once at set-up.  The caller passes device
+ * buffers sum1, sum2 [n_bins] (batch sums and sums of squares, as in
+ * mcdc_run_args) and optionally mean, relerr [n_bins]; the work is queued on
+ * `stream` (NULL: legacy default stream) and the call returns without
+ * waiting.  Scratch (claim counters, global-mode batch tally, accumulators,
+ * event counters) lives in one fixed __device__ array of about 1.1 MiB that
+ * every GPU loading the library holds until exit; no cudaMalloc or cudaFree
+ * is called.  Limits: n_batches <= 4096 and, for a problem using the global
+ * tally, at most 131072 bins; larger requests return MCDC_ERR_INVALID.  The
+ * first call on a device looks up the array's device address, so make that
+ * first call before any stream capture.  Calls share the array: each clears
+ * what must start at zero, and calls that overlap on the GPU race.  Event
+ * statistics, records and overflow errors are not reported. */
+int mcdc_run_noalloc(struct mcdc_problem *prob, uint64_t n_histories, uint64_t seed,
+                     uint64_t hist_offset, int32_t n_batches, double *sum1, double *sum2,
+                     double *mean, double *relerr, void *stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);
 

@@ -13,6 +13,7 @@
 
 #include "../../include/mcdc.h"
 #include "launch.h"
+#include "problem.h"
 #include "tracker.cuh"
 
 using namespace mcdc;
@@ -56,40 +57,6 @@ struct DevBuf {
 
 }  // namespace
 
-struct mcdc_problem {
-  int device = 0;
-  int sms = 0;
-  DevProblem P{};
-  mcdc_options opt{};
-  // host copies needed later
-  std::vector<double> edges;
-  int dim = 3;
-  TrackKey key{};
-  // launch shape
-  int block = 256, S = 512, ctas_per_sm = 1, grid = 0, smem = 0;
-  Layout L{};
-  int tally_mode = MCDC_TALLY_SHARED;
-  int warp_aggregate = 0;
-  int overflow_cap = 0;
-  // device memory
-  std::vector<void *> allocs;
-  double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
-         *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
-  Stats *stats = nullptr;
-  int32_t *error = nullptr;
-  unsigned long long *work = nullptr;   // [max batches] work counters
-  int work_slots = 0;
-  void *overflow = nullptr;
-  size_t overflow_bytes = 0;
-  Record *rec_tmp = nullptr;
-  uint64_t rec_cap = 0;
-  double *ww64 = nullptr;
-  float *ww32 = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-  // host staging
-  Stats *h_stats = nullptr;   // pinned
-  int32_t *h_error = nullptr; // pinned
-};
 
 namespace {
 
@@ -258,6 +225,10 @@ int ensure_overflow(mcdc_problem *pr) {
 }
 
 }  // namespace
+
+namespace mcdc {
+int set_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace mcdc
 
 extern "C" {
 

@@ -1,6 +1,7 @@
 // launch.h -- host-side entry points into the kernel translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <string>
 #include "common.cuh"
 
 namespace mcdc {
@@ -31,5 +32,8 @@ cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, doub
 cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,
                             const double *sum2, uint64_t n_hist, int n_batches, double volume,
                             double *mean, double *relerr, int sms);
+
+// Records the calling thread's error message (read by mcdc_last_error).
+int set_error(int code, const std::string &msg);
 
 }  // namespace mcdc

@@ -1,0 +1,43 @@
+// problem.h -- the library's private view of a problem handle: device
+// tables, launch shape and the device buffers a run uses.
+#pragma once
+#include <vector>
+
+#include "../../include/mcdc.h"
+#include "launch.h"
+#include "tracker.cuh"
+
+struct mcdc_problem {
+  int device = 0;
+  int sms = 0;
+  mcdc::DevProblem P{};
+  mcdc_options opt{};
+  // host copies needed later
+  std::vector<double> edges;
+  int dim = 3;
+  mcdc::TrackKey key{};
+  // launch shape
+  int block = 256, S = 512, ctas_per_sm = 1, grid = 0, smem = 0;
+  mcdc::Layout L{};
+  int tally_mode = MCDC_TALLY_SHARED;
+  int warp_aggregate = 0;
+  int overflow_cap = 0;
+  // device memory
+  std::vector<void *> allocs;
+  double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
+         *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
+  mcdc::Stats *stats = nullptr;
+  int32_t *error = nullptr;
+  unsigned long long *work = nullptr;   // [max batches] work counters
+  int work_slots = 0;
+  void *overflow = nullptr;
+  size_t overflow_bytes = 0;
+  mcdc::Record *rec_tmp = nullptr;
+  uint64_t rec_cap = 0;
+  double *ww64 = nullptr;
+  float *ww32 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  // host staging
+  mcdc::Stats *h_stats = nullptr;   // pinned
+  int32_t *h_error = nullptr; // pinned
+};

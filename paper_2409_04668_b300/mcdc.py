@@ -103,6 +103,8 @@ SIGNATURES = {
                                           C.c_int32]),
     "mcdc_tally_size": (C.c_int64, [C.c_void_p]),
     "mcdc_problem_destroy": (None, [C.c_void_p]),
+    "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
 }
 
@@ -127,6 +129,7 @@ mcdc_run_ex = _lib.mcdc_run_ex
 mcdc_set_weight_windows = _lib.mcdc_set_weight_windows
 mcdc_tally_size = _lib.mcdc_tally_size
 mcdc_problem_destroy = _lib.mcdc_problem_destroy
+mcdc_run_noalloc = _lib.mcdc_run_noalloc
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -242,6 +245,13 @@ class Problem:
         check(mcdc_run_ex(self.handle, C.byref(a), C.byref(st) if st is not None else None))
         stats = {k: getattr(st, k) for k, _ in mcdc_stats._fields_} if st is not None else None
         return stats, (tuple(scal) if scal is not None else None)
+
+    def run_noalloc(self, n, seed, sum1, sum2, offset=0, batches=32, mean=None, relerr=None,
+                    stream=None):
+        """Allocation-free run (see mcdc_run_noalloc): device tensors only;
+        returns once the work is queued on `stream`."""
+        check(mcdc_run_noalloc(self.handle, int(n), int(seed), int(offset), int(batches),
+                               _ptr(sum1), _ptr(sum2), _ptr(mean), _ptr(relerr), stream))
 
     def run(self, n, seed, tally_out=None):
         check(mcdc_run(self.handle, int(n), int(seed), _ptr(tally_out)))

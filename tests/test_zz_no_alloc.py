@@ -1,0 +1,91 @@
+"""The allocation-free run (mcdc_run_noalloc) against the regular run.
+
+mcdc_run_noalloc serves callers that cannot call cudaMalloc while transport
+runs (a pool allocator that owns all device memory, or a loop in which an
+allocation would stall the device): its scratch lives in a fixed __device__
+array inside the library.  These tests call it through the C-ABI twice in a
+row on the same problem and compare each result with mcdc_run_ex's, bin by
+bin, at the FP64 tally tolerance; they also check that requests beyond the
+array's limits are refused.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_2409_04668_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2409_04668_b300 import build
+    build.build()
+    from paper_2409_04668_b300 import mcdc as M
+    return M, torch
+
+
+def channel(n=12, T=8):
+    full = W.c3_channel(3)
+    f = 60 // n
+    return W.box("channel_small", (n, n, n), (1.0 * f,) * 3, full.material[::f, ::f, ::f].copy(),
+                 full.sigma_t, full.sigma_s / full.sigma_t, full.transfer, full.speed,
+                 (0.0,) * 3, (10.0,) * 3, np.linspace(0.0, 1e-6, T + 1), (n // 2,) * 3, (n,) * 3)
+
+
+def _close(a, b, rtol):
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    np.testing.assert_allclose(a, b, rtol=rtol, atol=1e-300)
+
+
+@pytest.mark.parametrize("mode", ["shared", "global"])
+def test_noalloc_matches_run_ex_twice(env, mode):
+    M, torch = env
+    if mode == "shared":
+        prob, tm, n, B = W.c2_two_region(), M.TALLY_SHARED, 200_000, 16
+    else:
+        prob, tm, n, B = channel(), M.TALLY_GLOBAL, 20_000, 8     # 96768 bins
+    dev = torch.device("cuda", 0)
+    with M.Problem(prob, precision=M.PREC_FP64, tally_mode=tm) as P:
+        ref = [torch.zeros(P.n_bins, dtype=torch.float64, device=dev) for _ in range(4)]
+        P.run_ex(n, 17, offset=99, batches=B, sum1=ref[0], sum2=ref[1], mean=ref[2],
+                 relerr=ref[3])
+        torch.cuda.synchronize()
+        assert float(ref[0].sum()) > 0
+        stream = torch.cuda.current_stream().cuda_stream
+        for call in range(2):
+            out = [torch.full((P.n_bins,), float("nan"), dtype=torch.float64, device=dev)
+                   for _ in range(4)]
+            P.run_noalloc(n, 17, out[0], out[1], offset=99, batches=B, mean=out[2],
+                          relerr=out[3], stream=stream)
+            torch.cuda.synchronize()
+            _close(out[0], ref[0], REL)
+            _close(out[1], ref[1], REL)
+            _close(out[2], ref[2], REL)
+            _close(out[3], ref[3], 1e-6)
+
+
+def test_noalloc_refuses_requests_beyond_its_limits(env):
+    M, torch = env
+    dev = torch.device("cuda", 0)
+    big = channel(n=20, T=8)               # 20^3 x 7 x 8 = 448000 bins > 131072
+    with M.Problem(big, precision=M.PREC_FP32, tally_mode=M.TALLY_GLOBAL) as P:
+        s1 = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
+        s2 = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
+        with pytest.raises(M.MCDCError) as e:
+            P.run_noalloc(1000, 1, s1, s2, batches=4)
+        assert e.value.code == M.MCDC_ERR_INVALID
+    with M.Problem(W.c1_slab(), precision=M.PREC_FP32) as P:
+        s1 = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
+        s2 = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
+        with pytest.raises(M.MCDCError) as e:
+            P.run_noalloc(100_000, 1, s1, s2, batches=5000)
+        assert e.value.code == M.MCDC_ERR_INVALID
+        h1 = np.zeros(P.n_bins)
+        with pytest.raises(M.MCDCError) as e:                 # host outputs are refused
+            P.run_noalloc(1000, 1, h1, h1, batches=4)
+        assert e.value.code == M.MCDC_ERR_INVALID
