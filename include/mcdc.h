@@ -115,11 +115,12 @@ typedef struct mcdc_options {
     int32_t tally_mode;         /* MCDC_TALLY_*                                   */
     int32_t n_batches;          /* batches for the error estimate (>= 2); 0: auto */
     int32_t block_size;         /* threads per CTA; 0: autotuned                  */
-    int32_t bank_per_cta;       /* particle slots per CTA; 0: autotuned           */
+    int32_t bank_per_cta;       /* ignored: each warp parks up to 96 particles    */
     int32_t ctas_per_sm;        /* resident CTAs per SM; 0: autotuned             */
     int32_t warp_aggregate;     /* -1 off, 1 on, 0 auto                           */
     int32_t autotune;           /* 1: time candidate launch shapes at create      */
-    int32_t overflow_per_cta;   /* split-children overflow slots per CTA; 0: auto */
+    int32_t overflow_per_cta;   /* split-children overflow slots per CTA (shared by
+                                   its warps, >= 64 each); 0: 1024 per warp      */
     int32_t region_lo[3];       /* cell box [lo, hi) of the scalar tally used for */
     int32_t region_hi[3];       /*   the figure of merit; hi == 0: whole mesh      */
 } mcdc_options;

@@ -142,9 +142,8 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   const bool f64 = pr->key.f64;
   int block = o.block_size > 0 ? o.block_size : 256;
   if (block % 32 != 0 || block > 512) return fail(MCDC_ERR_INVALID, "block_size must be a multiple of 32, <= 512");
-  int S = o.bank_per_cta > 0 ? o.bank_per_cta : 2 * block;
-  if (S < block || S > 8192 || S % 32 != 0)
-    return fail(MCDC_ERR_INVALID, "bank_per_cta must be a multiple of 32 in [block_size, 8192]");
+  // every warp parks up to kPool particles besides its 32 in flight
+  const int S = (block / 32) * kPool;
   int mode = o.tally_mode;
   const long long tally_b = (long long)pr->P.n_bins * (f64 ? 8 : 4);
   if (mode == MCDC_TALLY_AUTO) {
@@ -157,7 +156,7 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   if (L.total > dyn_max) {
     if (o.tally_mode == MCDC_TALLY_SHARED)
       return fail(MCDC_ERR_INVALID, "shared tally + bank exceed shared memory; use the global tally");
-    return fail(MCDC_ERR_INVALID, "bank_per_cta too large for shared memory");
+    return fail(MCDC_ERR_INVALID, "block_size too large for shared memory");
   }
   pr->key.shared = (mode == MCDC_TALLY_SHARED);
   {
@@ -188,9 +187,10 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
   int B = pr->opt.n_batches;
   if (B <= 0) {
     if (pr->tally_mode == MCDC_TALLY_SHARED) {
-      // enough whole batches to keep every CTA busy, each a few thousand histories
-      const uint64_t by_size = n / 2048;
-      B = (int)std::min<uint64_t>(std::max<uint64_t>(by_size, 32), (uint64_t)pr->grid * 8);
+      // every CTA gets about two whole batches (a CTA drains between its
+      // batches), each of at least a few thousand histories
+      const uint64_t by_size = n / 4096;
+      B = (int)std::min<uint64_t>(std::max<uint64_t>(by_size, 32), (uint64_t)pr->grid * 2);
     } else {
       B = 32;
     }
@@ -211,9 +211,10 @@ int ensure_work_slots(mcdc_problem *pr, int n) {
 
 int ensure_overflow(mcdc_problem *pr) {
   if (pr->P.ww_lower == nullptr) return MCDC_OK;
-  int cap = pr->opt.overflow_per_cta > 0 ? pr->opt.overflow_per_cta : 4096;
+  const int warps = pr->block / 32;
+  const int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
   const size_t part_b = pr->key.f64 ? sizeof(Part<double>) : sizeof(Part<float>);
-  const size_t need = (size_t)pr->grid * cap * part_b;
+  const size_t need = (size_t)pr->grid * warps * cap * part_b;
   if (pr->overflow_bytes >= need && pr->overflow_cap == cap) return MCDC_OK;
   unsigned char *p = nullptr;
   int rc = dalloc(pr, &p, need);
@@ -416,6 +417,16 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     if ((rc = upload(pr, &P.speed, speed))) return bail(rc);
     if ((rc = upload(pr, &P.edges, edges))) return bail(rc);
     if ((rc = upload(pr, &P.src_cdf, scdf))) return bail(rc);
+    for (int a = 0; a < 3; ++a) {
+      P.faces[a] = nullptr;
+      if (!bounded[a]) continue;
+      std::vector<double> fc(n[a] + 1);
+      for (int k = 0; k <= n[a]; ++k) {
+        const double step = (double)k * wid[a];   // two roundings, as on the device
+        fc[k] = org[a] + step;
+      }
+      if ((rc = upload(pr, &P.faces[a], fc))) return bail(rc);
+    }
     auto f32 = [](const std::vector<double> &v) {
       std::vector<float> r(v.size());
       for (size_t q = 0; q < v.size(); ++q) r[q] = (float)v[q];

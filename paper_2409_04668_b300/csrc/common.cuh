@@ -26,6 +26,7 @@ struct DevProblem {
   int64_t n_cells, n_bins;
   double volume;
   const uint8_t *material;    // [cells]
+  const double *faces[3];     // [n_a + 1] face coordinates origin + k * width (bounded axes)
   // FP64 tables
   const double *sigma_t;      // [M*G]
   const double *scat;         // [M*G]  sigma_s / sigma_t
@@ -96,9 +97,9 @@ struct RunArgs {
   Record *records;            // or nullptr
   uint64_t n_records;
   int32_t *error;             // ERRBIT_* flags
-  // per-CTA overflow stacks for split children: [gridDim.x][overflow_cap]
+  // per-warp overflow stacks for split children: [warps in grid][overflow_cap]
   void *overflow;
-  int32_t overflow_cap;
+  int32_t overflow_cap;       // per warp
   int32_t warp_aggregate;
 };
 

@@ -49,6 +49,7 @@ struct Tables {
   R *src_cdf;                // [G]
   double *speed;             // [G]
   R *inv_speed;              // [G] (FP32 path)
+  float *speed32;            // [G]
   double *edges;             // [T+1]
   const double *ww;          // global
   const float *ww32;
@@ -85,15 +86,18 @@ struct Bank {
   }
 };
 
-// bytes of one bank slot (kept in sync with Bank::carve)
+// bytes of one pool slot (kept in sync with the carve in k_track)
 __host__ __device__ inline int slot_bytes(bool f64, int dim) {
   const int r = f64 ? 8 : 4;
-  return 8 * 2 + (dim == 3 ? 16 : 0) + 8 + 4 * r + 4 * 5 + 2 * 4 + 1 + 2 * 4 /* lists */;
+  return 8 * 2 + (dim == 3 ? 16 : 0) + 8 + 4 * r + 4 * 5 + 2 * 4 + 1;
 }
+
+// particles a warp can park in shared memory besides the 32 in flight
+constexpr int kPool = 96;
 
 // shared-memory layout of one CTA
 struct Layout {
-  int S;                 // slots
+  int S;                 // pool slots of the whole CTA (warps x kPool)
   int tables_bytes;
   long long tally_bytes; // 0 in global mode
   int bank_bytes;
@@ -110,6 +114,7 @@ inline int tables_bytes_of(bool f64, int M, int G, int T) {
   b += align16((long long)r * G);                  // src cdf
   b += align16(8ll * G);                           // speed
   b += align16((long long)r * G);                  // inv speed
+  b += align16(4ll * G);                           // speed (FP32)
   b += align16(8ll * (T + 1));                     // edges
   return (int)b;
 }
@@ -121,9 +126,11 @@ struct LocalCount {
 
 // ---------------------------------------------------------------------------
 // geometry helpers (FP64 in both precisions)
+// face coordinate origin + k * width, read from a table built on the host
+// with the same two roundings
 __device__ __forceinline__ double face_of(const DevProblem &P, int a, int idx, bool up) {
   const int k = up ? idx + 1 : idx;
-  return P.origin[a] + (double)k * P.width[a];
+  return __ldg(P.faces[a] + k);
 }
 
 __device__ __forceinline__ int loc2index(const DevProblem &P, int a, double x) {
@@ -335,7 +342,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
   R d_time = rinf<R>();
   if (P.T > 0) {
     if constexpr (PR::kF64) d_time = tb.speed[p.g] * (tb.edges[p.tbin + 1] - p.t);
-    else d_time = (float)tb.speed[p.g] * (float)(tb.edges[p.tbin + 1] - p.t);
+    else d_time = tb.speed32[p.g] * (float)(tb.edges[p.tbin + 1] - p.t);
     if (d_time < (R)0) d_time = (R)0;
   }
 
@@ -468,13 +475,88 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
 }
 
 // ---------------------------------------------------------------------------
+// Warp-private pools.  A warp keeps up to kPool = 96 parked particles in
+// shared memory (SoA); slot states live in two 96-bit masks held in
+// registers (identical in every lane): `ready` (waiting for a lane to fly
+// it) and `coll` (waiting for its collision).
+struct Mask3 {
+  uint32_t w[3];
+};
+
+__device__ __forceinline__ int popc3(const Mask3 &m) {
+  return __popc(m.w[0]) + __popc(m.w[1]) + __popc(m.w[2]);
+}
+
+// index of the n-th (0-based) set bit of a 32-bit word (binary search on popc)
+__device__ __forceinline__ int nth32(uint32_t m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));
+    if (n >= c) { n -= c; m >>= s; pos += s; }
+  }
+  return pos;
+}
+
+__device__ __forceinline__ int nth3(const Mask3 &m, int n) {
+  const int c0 = __popc(m.w[0]);
+  if (n < c0) return nth32(m.w[0], n);
+  n -= c0;
+  const int c1 = __popc(m.w[1]);
+  if (n < c1) return 32 + nth32(m.w[1], n);
+  return 64 + nth32(m.w[2], n - c1);
+}
+
+// OR over the warp of the bit of slot s from every lane with pred set
+__device__ __forceinline__ Mask3 gather3(bool pred, int s) {
+  Mask3 r;
+  r.w[0] = __reduce_or_sync(0xffffffffu, (pred && s < 32) ? (1u << s) : 0u);
+  r.w[1] = __reduce_or_sync(0xffffffffu, (pred && s >= 32 && s < 64) ? (1u << (s - 32)) : 0u);
+  r.w[2] = __reduce_or_sync(0xffffffffu, (pred && s >= 64) ? (1u << (s - 64)) : 0u);
+  return r;
+}
+
+__device__ __forceinline__ void or3(Mask3 &a, const Mask3 &b) {
+  a.w[0] |= b.w[0]; a.w[1] |= b.w[1]; a.w[2] |= b.w[2];
+}
+__device__ __forceinline__ void andnot3(Mask3 &a, const Mask3 &b) {
+  a.w[0] &= ~b.w[0]; a.w[1] &= ~b.w[1]; a.w[2] &= ~b.w[2];
+}
+__device__ __forceinline__ Mask3 free3(const Mask3 &r, const Mask3 &c) {
+  Mask3 f;
+  f.w[0] = ~(r.w[0] | c.w[0]); f.w[1] = ~(r.w[1] | c.w[1]); f.w[2] = ~(r.w[2] | c.w[2]);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent tracker.  Each lane flies one particle held in registers; the
+// flights of a warp are one dense pass over its 32 lanes.  A flight that
+// ends in a collision parks its particle in the warp's pool; once 32 are
+// parked (or nothing else can progress) they are collided in one dense pass
+// and marked ready; empty lanes take ready particles; when none are left,
+// a dense pass of up to 32 births (split children first, then new source
+// histories) refills the pool.  Occupancy bound: births happen only when no
+// particle is ready and some lane is empty, so the warp never holds more
+// than 31 + 31 + 32 particles and at least 33 slots are free before every
+// flight pass -- room for every lane to park a collision.
+//
+// Shared mode: the CTA works on one batch at a time with its private
+// shared-memory tally; warps claim the batch's histories through a shared
+// cursor and meet at a CTA barrier only when the batch is drained, where the
+// private tally is folded into the batch sums.  Global mode: warps claim
+// histories of the launch's batch from a device-wide cursor and score into
+// the device-wide batch tally.
 template <class PR, bool SHARED, int DIM>
 __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs A, const Layout L) {
   using R = typename PR::R;
   using TT = typename PR::TT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
   const int S = L.S;
 
   // ---- carve shared memory
@@ -487,6 +569,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
   tb.src_cdf = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
   tb.speed = (double *)ptr; ptr += align16(8ll * G);
   tb.inv_speed = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
+  tb.speed32 = (float *)ptr; ptr += align16(4ll * G);
   tb.edges = (double *)ptr; ptr += align16(8ll * (P.T + 1));
   tb.ww = P.ww_lower;
   tb.ww32 = P.ww_lower32;
@@ -511,21 +594,16 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
   bk.j = (uint16_t *)ptr; ptr += 2 * S;
   bk.k = (uint16_t *)ptr; ptr += 2 * S;
   bk.tbin = (uint16_t *)ptr; ptr += 2 * S;
-  uint16_t *act = (uint16_t *)ptr; ptr += 2 * S;
-  uint16_t *nxt = (uint16_t *)ptr; ptr += 2 * S;
-  uint16_t *colq = (uint16_t *)ptr; ptr += 2 * S;
-  uint16_t *freel = (uint16_t *)ptr; ptr += 2 * S;
   bk.g = (uint8_t *)ptr; ptr += S;
 
-  __shared__ int s_nact, s_nnext, s_ncol, s_nfree, s_novf, s_take_ovf, s_take_src, s_done, s_nalloc,
-      s_exhausted;
   __shared__ unsigned long long s_h_next, s_h_end;
-  __shared__ int s_batch;
+  __shared__ int s_done, s_batch;
+  __shared__ int s_novf[16];
   __shared__ double s_w[4];
   __shared__ uint32_t s_n[8];
-  __shared__ double s_red[32];
+  __shared__ double s_red[16];
 
-  // ---- load tables
+  // ---- tables
   for (int q = tid; q < M * G; q += nth) {
     if constexpr (PR::kF64) { tb.sigma_t[q] = P.sigma_t[q]; tb.scat[q] = P.scat[q]; }
     else { tb.sigma_t[q] = P.sigma_t32[q]; tb.scat[q] = P.scat32[q]; }
@@ -537,203 +615,206 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
     if constexpr (PR::kF64) { tb.src_cdf[q] = P.src_cdf[q]; tb.inv_speed[q] = 1.0 / P.speed[q]; }
     else { tb.src_cdf[q] = P.src_cdf32[q]; tb.inv_speed[q] = P.inv_speed32[q]; }
     tb.speed[q] = P.speed[q];
+    tb.speed32[q] = P.speed32[q];
   }
-  for (int q = tid; q <= P.T; q += nth) tb.edges[q] = P.edges ? P.edges[q] : 0.0;
+  for (int q = tid; q <= P.T; q += nth) tb.edges[q] = P.edges[q];
   if (SHARED)
     for (long long q = tid; q < P.n_bins; q += nth) stally[q] = (TT)0;
-  for (int q = tid; q < S; q += nth) freel[q] = (uint16_t)(S - 1 - q);
-  if (tid == 0) {
-    s_nact = 0; s_nfree = S; s_novf = 0; s_done = 0; s_nalloc = 0; s_exhausted = 0;
-    s_h_next = s_h_end = 0; s_batch = -1;
-  }
+  if (tid < 16) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 8) s_n[tid] = 0u;
+  if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; }
   __syncthreads();
 
   EndSink es{s_w, s_n};
   LocalCount lc{0, 0, 0, 0};
-  Part<R> *ovf = reinterpret_cast<Part<R> *>(A.overflow) + (size_t)blockIdx.x * A.overflow_cap;
+  const int wid = blockIdx.x * nwarps + warp;                 // warp id in the grid
+  Part<R> *ovf = reinterpret_cast<Part<R> *>(A.overflow) + (size_t)wid * A.overflow_cap;
+  int *novf = &s_novf[warp];
+  const int pool0 = warp * kPool;                              // first slot of this warp
   const bool agg = A.warp_aggregate != 0;
+  uint64_t g_h0 = 0, g_h1 = 0;
+  if (!SHARED) {
+    g_h0 = batch_start(A.n_hist, A.n_batches, A.batch);
+    g_h1 = batch_start(A.n_hist, A.n_batches, A.batch + 1);
+  }
 
   for (;;) {
-    // ---- control: claim work.  Shared mode holds one batch in the private
-    // tally, so a new batch is claimed only once the bank has drained;
-    // global mode claims the next chunk as soon as the current one is used.
-    if (tid == 0) {
-      s_take_ovf = 0; s_take_src = 0;
-      if (s_h_next >= s_h_end && !s_exhausted) {
-        if (SHARED) {
-          if (s_nact == 0 && s_novf == 0) {
-            const unsigned long long b = atomicAdd(A.work, 1ull);
-            if ((long long)b < A.n_batches) {
-              s_batch = (int)b;
-              s_h_next = batch_start(A.n_hist, A.n_batches, (int)b);
-              s_h_end = batch_start(A.n_hist, A.n_batches, (int)b + 1);
+    if (SHARED) {
+      // ---- claim the next batch for the whole CTA
+      if (tid == 0) {
+        const unsigned long long b = atomicAdd(A.work, 1ull);
+        if ((long long)b < A.n_batches) {
+          s_batch = (int)b;
+          s_h_next = batch_start(A.n_hist, A.n_batches, (int)b);
+          s_h_end = batch_start(A.n_hist, A.n_batches, (int)b + 1);
+        } else {
+          s_done = 1;
+        }
+      }
+      __syncthreads();
+      if (s_done) break;
+    }
+
+    // ---- warp loop over this batch (shared) or the launch (global)
+    Part<R> p;
+    bool has = false;
+    Mask3 ready{{0u, 0u, 0u}}, coll{{0u, 0u, 0u}};
+    bool exhausted = false;
+    for (;;) {
+      __syncwarp();   // every lane sees the same overflow count below
+      // (1) collisions: a dense pass when 32 are parked, or whatever is
+      // parked once nothing is ready and no more births can come
+      {
+        const int nc = popc3(coll);
+        const bool drain = exhausted && (*novf == 0);
+        if (nc >= 32 || (nc > 0 && popc3(ready) == 0 && drain)) {
+          const bool mine = lane < nc;
+          const int s = mine ? nth3(coll, lane) : 0;
+          bool alive = false;
+          if (mine) {
+            Part<R> q;
+            bk.load(pool0 + s, q, DIM);
+            int end = END_NONE;
+            alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf);
+            if (alive) bk.store(pool0 + s, q, DIM);
+            else finish<R, DIM>(A, es, q, end);
+          }
+          andnot3(coll, gather3(mine, s));
+          or3(ready, gather3(mine && alive, s));
+          __syncwarp();
+        }
+      }
+      // (2) empty lanes take ready particles
+      {
+        const uint32_t empty = __ballot_sync(0xffffffffu, !has);
+        const int nr = popc3(ready);
+        if (empty && nr) {
+          const int r = __popc(empty & lanemask_lt());
+          const bool take = !has && r < nr;
+          const int s = take ? nth3(ready, r) : 0;
+          if (take) { bk.load(pool0 + s, p, DIM); has = true; }
+          andnot3(ready, gather3(take, s));
+          __syncwarp();
+        }
+      }
+      // (3) births when lanes are still empty and nothing is ready
+      if (__any_sync(0xffffffffu, !has) && popc3(ready) == 0 && !(exhausted && *novf == 0)) {
+        __syncwarp();
+        const int n_o = min(32, min(*novf, A.overflow_cap));
+        int n_s = 0;
+        unsigned long long h_first = 0;
+        if (n_o < 32 && !exhausted) {
+          const int want = 32 - n_o;
+          unsigned long long first = 0;
+          int got = 0;
+          if (lane == 0) {
+            if (SHARED) {
+              first = atomicAdd(&s_h_next, (unsigned long long)want);
+              got = first < s_h_end ? (int)min((unsigned long long)want, s_h_end - first) : 0;
             } else {
-              s_exhausted = 1;
+              const unsigned long long c = atomicAdd(A.work, (unsigned long long)want);
+              first = g_h0 + c;
+              got = first < g_h1 ? (int)min((unsigned long long)want, g_h1 - first) : 0;
             }
           }
-        } else {
-          const uint64_t h0 = batch_start(A.n_hist, A.n_batches, A.batch);
-          const uint64_t h1 = batch_start(A.n_hist, A.n_batches, A.batch + 1);
-          const unsigned long long c = atomicAdd(A.work, (unsigned long long)A.chunk);
-          if (h0 + c < h1) {
-            s_h_next = h0 + c;
-            s_h_end = min((unsigned long long)h1, (unsigned long long)(h0 + c + A.chunk));
-          } else {
-            s_exhausted = 1;
-          }
+          first = __shfl_sync(0xffffffffu, first, 0);
+          got = __shfl_sync(0xffffffffu, got, 0);
+          h_first = first;
+          n_s = got;
+          if (got < want) exhausted = true;
         }
-      }
-      if (s_exhausted && s_h_next >= s_h_end && s_nact == 0 && s_novf == 0) s_done = 1;
-      if (!s_done) {
-        int room = s_nfree;
-        const int from_ovf = min(room, min(s_novf, A.overflow_cap));
-        room -= from_ovf;
-        const unsigned long long left = s_h_end - s_h_next;
-        s_take_ovf = from_ovf;
-        s_take_src = (int)min((unsigned long long)room, left);
-      }
-    }
-    __syncthreads();
-    if (s_done) break;
-
-    // ---- refill: overflow children first, then new source particles.  Live
-    // births take the top entries of the free list in warp-append order;
-    // a birth after the last census edge is censused at once and takes none.
-    {
-      const int n_o = s_take_ovf, n_s = s_take_src, n_new = n_o + n_s;
-      const int top = s_nfree;
-      const int nact0 = s_nact;
-      const int base_ovf = min(s_novf, A.overflow_cap) - n_o;
-      for (int base = warp * 32; base < n_new; base += nth) {
-        const int q = base + lane;
-        const bool valid = q < n_new;
+        const int nb = n_o + n_s;
+        const int top = min(*novf, A.overflow_cap);
         bool alive = false;
-        Part<R> p;
-        if (valid) {
-          if (q < n_o) {
-            p = ovf[base_ovf + q];
+        Part<R> q;
+        if (lane < nb) {
+          if (lane < n_o) {
+            q = ovf[top - 1 - lane];
             alive = true;
           } else {
-            const uint64_t hid = A.offset + s_h_next + (uint64_t)(q - n_o);
-            source_particle<PR, DIM>(P, tb, A.seed, hid, p);
+            source_particle<PR, DIM>(P, tb, A.seed, A.offset + h_first + (lane - n_o), q);
             atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
-            alive = !(P.T > 0 && p.tbin >= P.T);
-            if (!alive) finish<R, DIM>(A, es, p, END_CENSUSED);
+            alive = !(P.T > 0 && q.tbin >= P.T);
+            if (!alive) finish<R, DIM>(A, es, q, END_CENSUSED);
           }
         }
-        const int k = warp_append(alive, &s_nalloc);
-        if (alive) {
-          const int slot = freel[top - 1 - k];
-          bk.store(slot, p, DIM);
-          act[nact0 + k] = (uint16_t)slot;
+        const uint32_t am = __ballot_sync(0xffffffffu, alive);
+        const Mask3 fr = free3(ready, coll);
+        const int s = alive ? nth3(fr, __popc(am & lanemask_lt())) : 0;
+        if (alive) bk.store(pool0 + s, q, DIM);
+        or3(ready, gather3(alive, s));
+        __syncwarp();
+        if (lane == 0) *novf = min(*novf, A.overflow_cap) - n_o;
+        __syncwarp();
+        // and hand them to the empty lanes
+        const uint32_t empty = __ballot_sync(0xffffffffu, !has);
+        const int nr = popc3(ready);
+        const int r = __popc(empty & lanemask_lt());
+        const bool take = !has && r < nr;
+        const int st = take ? nth3(ready, r) : 0;
+        if (take) { bk.load(pool0 + st, p, DIM); has = true; }
+        andnot3(ready, gather3(take, st));
+        __syncwarp();
+      }
+      // (4) nothing in flight: progress through collisions/births, or stop
+      if (!__any_sync(0xffffffffu, has)) {
+        if (popc3(coll) == 0 && popc3(ready) == 0 && exhausted && *novf == 0) break;
+        continue;
+      }
+      // (5) one flight for every lane that holds a particle
+      {
+        int outcome = OUT_CONT, end = END_NONE;
+        int64_t bin = -1;
+        R score = (R)0;
+        const bool flew = has;
+        if (has) {
+          outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
+          if (outcome == OUT_DEAD) { finish<R, DIM>(A, es, p, end); has = false; }
         }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        s_nfree = top - s_nalloc;
-        s_nact = nact0 + s_nalloc;
-        s_nalloc = 0;
-        s_novf = min(s_novf, A.overflow_cap) - n_o;
-        s_h_next += (unsigned long long)n_s;
-        s_nnext = 0;
-        s_ncol = 0;
-      }
-      __syncthreads();
-    }
-
-    // ---- flight phase over the live list
-    const int nact = s_nact;
-    for (int base = warp * 32; base < nact; base += nth) {
-      const int q = base + lane;
-      const bool valid = q < nact;
-      const int slot = valid ? act[q] : 0;
-      int outcome = OUT_CONT, end = END_NONE;
-      int64_t bin = -1;
-      R score = (R)0;
-      Part<R> p;
-      if (valid) {
-        bk.load(slot, p, DIM);
-        outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, &s_novf, ovf);
-        if (outcome == OUT_DEAD) finish<R, DIM>(A, es, p, end);
-        else bk.store(slot, p, DIM);
-      }
-      tally_scatter<TT, R>(stally, A.tally, SHARED, agg, valid, bin, score);
-      const bool to_next = valid && outcome == OUT_CONT;
-      const bool to_col = valid && outcome == OUT_COLL;
-      const bool to_free = valid && outcome == OUT_DEAD;
-      const int pn = warp_append(to_next, &s_nnext);
-      const int pc = warp_append(to_col, &s_ncol);
-      const int pf = warp_append(to_free, &s_nfree);
-      if (to_next) nxt[pn] = (uint16_t)slot;
-      if (to_col) colq[pc] = (uint16_t)slot;
-      if (to_free) freel[pf] = (uint16_t)slot;
-    }
-    __syncthreads();
-
-    // ---- collision phase over the compacted collision queue
-    const int ncol = s_ncol;
-    for (int base = warp * 32; base < ncol; base += nth) {
-      const int q = base + lane;
-      const bool valid = q < ncol;
-      const int slot = valid ? colq[q] : 0;
-      bool alive = false;
-      if (valid) {
-        Part<R> p;
-        bk.load(slot, p, DIM);
-        int end = END_NONE;
-        alive = collide<PR, DIM>(P, tb, A, es, p, end, lc, &s_novf, ovf);
-        if (alive) bk.store(slot, p, DIM);
-        else finish<R, DIM>(A, es, p, end);
-      }
-      const bool to_next = valid && alive;
-      const bool to_free = valid && !alive;
-      const int pn = warp_append(to_next, &s_nnext);
-      const int pf = warp_append(to_free, &s_nfree);
-      if (to_next) nxt[pn] = (uint16_t)slot;
-      if (to_free) freel[pf] = (uint16_t)slot;
-    }
-    __syncthreads();
-
-    // ---- swap lists; fold a finished batch out of the private tally
-    const int nn = s_nnext;
-    for (int q = tid; q < nn; q += nth) act[q] = nxt[q];
-    if (SHARED) {
-      const bool batch_done = (s_h_next >= s_h_end) && nn == 0 && s_novf == 0 && s_batch >= 0;
-      if (batch_done) {
-        double rsum = 0.0;
-        for (long long q = tid; q < P.n_bins; q += nth) {
-          const double v = (double)stally[q];
-          if (v != 0.0) {
-            atomicAdd(&A.sum1[q], v);
-            atomicAdd(&A.sum2[q], v * v);
-            const long long cell = q / ((long long)P.G * P.T1);
-            const int ci = (int)(cell % P.n[0]);
-            const int cj = (int)((cell / P.n[0]) % P.n[1]);
-            const int ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
-            if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-                cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
-              rsum += v;
-            stally[q] = (TT)0;
-          }
-        }
-        // block reduction of the region sum of this batch
-        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-        if (lane == 0) s_red[warp] = rsum;
-        __syncthreads();
-        if (tid == 0) {
-          double tot = 0.0;
-          for (int w = 0; w < nth / 32; ++w) tot += s_red[w];
-          atomicAdd(&A.region[0], tot);
-          atomicAdd(&A.region[1], tot * tot);
-          s_batch = -1;
+        tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score);
+        const bool park = has && outcome == OUT_COLL;
+        const uint32_t pm = __ballot_sync(0xffffffffu, park);
+        if (pm) {
+          const Mask3 fr = free3(ready, coll);
+          const int s = park ? nth3(fr, __popc(pm & lanemask_lt())) : 0;
+          if (park) { bk.store(pool0 + s, p, DIM); has = false; }
+          or3(coll, gather3(park, s));
+          __syncwarp();
         }
       }
     }
+
+    if (!SHARED) break;
+    // ---- the batch is drained in every warp: fold the private tally
     __syncthreads();
-    if (tid == 0) s_nact = nn;
+    double rsum = 0.0;
+    const long long per_cell = (long long)P.G * P.T1;
+    for (long long q = tid; q < P.n_bins; q += nth) {
+      const double v = (double)stally[q];
+      if (v != 0.0) {
+        atomicAdd(&A.sum1[q], v);
+        atomicAdd(&A.sum2[q], v * v);
+        const int cell = (int)(q / per_cell);
+        const int ci = cell % P.n[0];
+        const int cj = (cell / P.n[0]) % P.n[1];
+        const int ck = cell / (P.n[0] * P.n[1]);
+        if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
+            cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
+          rsum += v;
+        stally[q] = (TT)0;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+    if (lane == 0) s_red[warp] = rsum;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+      atomicAdd(&A.region[0], tot);
+      atomicAdd(&A.region[1], tot * tot);
+    }
     __syncthreads();
   }
 
@@ -747,7 +828,9 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
     atomicAdd(&A.stats->collisions, (unsigned long long)c4[1]);
     atomicAdd(&A.stats->crossings, (unsigned long long)c4[2]);
     atomicAdd(&A.stats->census, (unsigned long long)c4[3]);
+    if (*novf > A.overflow_cap) atomicOr(A.error, ERRBIT_OVERFLOW);
   }
+  __syncthreads();
   if (tid == 0) {
     atomicAdd(&A.stats->absorbed, (unsigned long long)s_n[0]);
     atomicAdd(&A.stats->leaked, (unsigned long long)s_n[1]);
@@ -761,7 +844,6 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
     atomicAdd(&A.stats->w_absorbed, s_w[1]);
     atomicAdd(&A.stats->w_leaked, s_w[2]);
     atomicAdd(&A.stats->w_censused, s_w[3]);
-    if (s_novf > A.overflow_cap) atomicOr(A.error, ERRBIT_OVERFLOW);
   }
 }
 
