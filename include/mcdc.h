@@ -64,6 +64,9 @@ extern "C" {
 
 #define MCDC_PREC_FP64   0   /* every step in FP64: event-exact with the FP64 reference      */
 #define MCDC_PREC_FP32   1   /* FP32 direction/distance/xs, FP64 position, time and tallies  */
+#define MCDC_PREC_FP32_LOCAL 2 /* FP32 flights: positions as FP32 offsets from exact FP64 cell
+                                  faces, time as FP32 time to the next exact FP64 census edge;
+                                  FP64 tally reduction                                         */
 
 #define MCDC_TALLY_AUTO    0
 #define MCDC_TALLY_SHARED  1  /* per-CTA privatised tally in shared memory, one batch per CTA */

@@ -117,7 +117,7 @@ Layout make_layout(const mcdc_problem *pr, int S, int tally_mode) {
   L.tally_bytes = tally_mode == MCDC_TALLY_SHARED
                       ? align16((long long)pr->P.n_bins * (f64 ? 8 : 4))
                       : 0;
-  L.bank_bytes = S * slot_bytes(f64, pr->dim);
+  L.bank_bytes = S * slot_bytes(f64, pr->dim, pr->key.local);
   L.total = (int)(L.tables_bytes + L.tally_bytes + L.bank_bytes + 64);
   return L;
 }
@@ -213,7 +213,8 @@ int ensure_overflow(mcdc_problem *pr) {
   if (pr->P.ww_lower == nullptr) return MCDC_OK;
   const int warps = pr->block / 32;
   const int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
-  const size_t part_b = pr->key.f64 ? sizeof(Part<double>) : sizeof(Part<float>);
+  const size_t part_b = pr->key.f64 ? sizeof(Part<double>)
+                       : (pr->key.local ? sizeof(Part<float, float>) : sizeof(Part<float>));
   const size_t need = (size_t)pr->grid * warps * cap * part_b;
   if (pr->overflow_bytes >= need && pr->overflow_cap == cap) return MCDC_OK;
   unsigned char *p = nullptr;
@@ -252,7 +253,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (!mesh || !mat || !src) return fail(MCDC_ERR_INVALID, "mesh, materials and source are required");
   mcdc_options o;
   if (opt) o = *opt; else mcdc_default_options(&o);
-  if (o.precision != MCDC_PREC_FP64 && o.precision != MCDC_PREC_FP32)
+  if (o.precision != MCDC_PREC_FP64 && o.precision != MCDC_PREC_FP32 &&
+      o.precision != MCDC_PREC_FP32_LOCAL)
     return fail(MCDC_ERR_INVALID, "unknown precision");
 
   // ---- mesh
@@ -399,6 +401,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   }
   pr->dim = (!bounded[1] && !bounded[2]) ? 1 : 3;
   pr->key.f64 = (o.precision == MCDC_PREC_FP64);
+  pr->key.local = (o.precision == MCDC_PREC_FP32_LOCAL);
   pr->key.dim = pr->dim;
 
   int rc = MCDC_OK;
@@ -427,6 +430,10 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
       }
       if ((rc = upload(pr, &P.faces[a], fc))) return bail(rc);
     }
+    for (int a = 0; a < 3; ++a) P.width32[a] = bounded[a] ? (float)wid[a] : 0.0f;
+    std::vector<float> bw(std::max(T, 1), 0.0f);
+    for (int j = 0; j < T; ++j) bw[j] = (float)(edges[j + 1] - edges[j]);
+    if ((rc = upload(pr, &P.binw32, bw))) return bail(rc);
     auto f32 = [](const std::vector<double> &v) {
       std::vector<float> r(v.size());
       for (size_t q = 0; q < v.size(); ++q) r[q] = (float)v[q];

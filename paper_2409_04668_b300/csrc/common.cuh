@@ -27,6 +27,8 @@ struct DevProblem {
   double volume;
   const uint8_t *material;    // [cells]
   const double *faces[3];     // [n_a + 1] face coordinates origin + k * width (bounded axes)
+  float width32[3];           // cell widths in FP32 (cell-local mode)
+  const float *binw32;        // [T] time-bin widths in FP32 (cell-local mode)
   // FP64 tables
   const double *sigma_t;      // [M*G]
   const double *scat;         // [M*G]  sigma_s / sigma_t
@@ -50,10 +52,13 @@ struct DevProblem {
 };
 
 // One particle as it moves between the tracker phases (kept in registers).
-template <class R>
+// Q = double: x, y, z are the position and t the time.  Q = float (the
+// cell-local FP32 mode): x, y, z are offsets from the low faces of the cell
+// and t is the time left to the next census edge.
+template <class R, class Q = double>
 struct Part {
-  double x, y, z;     // position (FP64 in both precisions)
-  double t;           // time (FP64)
+  Q x, y, z;          // position (or cell-local offsets)
+  Q t;                // time (or time to the next census edge)
   R ux, uy, uz;       // direction
   R w;                // weight
   int32_t g;
@@ -124,8 +129,8 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
 }
 
 // draw one block for the particle and advance its counter
-template <class R>
-__device__ __forceinline__ U4 draw(const Part<R> &p, uint32_t &ctr, uint64_t seed) {
+template <class PartT>
+__device__ __forceinline__ U4 draw(const PartT &p, uint32_t &ctr, uint64_t seed) {
   U4 r = philox4x32_10(ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32),
                        (uint32_t)seed, (uint32_t)(seed >> 32));
   ctr += 1;

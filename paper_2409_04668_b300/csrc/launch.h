@@ -9,7 +9,8 @@ namespace mcdc {
 struct Layout;
 
 struct TrackKey {
-  bool f64;
+  bool f64;     // FP64 everywhere
+  bool local;   // FP32 cell-local positions (when !f64)
   bool shared;
   int dim;   // 1 or 3
 };

@@ -1,6 +1,6 @@
 // track_fp32.cu -- FP32-split instantiations of the tracker (FP32 direction,
 // distance and cross sections; FP64 position, time and tally reduction) and
-// the dispatch over both precisions.
+// the FP32 cell-local instantiations, and the dispatch over all precisions.
 #include "launch.h"
 #include "tracker.cuh"
 
@@ -13,13 +13,16 @@ int track_regs_f64(const TrackKey &);
 int track_occupancy_f64(const TrackKey &, int, int);
 
 namespace {
-template <bool SH, int DIM>
-void *fp32_kernel() { return (void *)k_track<PrecF32, SH, DIM>; }
+template <class PR, bool SH, int DIM>
+void *fp32_kernel() { return (void *)k_track<PR, SH, DIM>; }
 
-void *pick(const TrackKey &k) {
-  if (k.shared) return k.dim == 1 ? fp32_kernel<true, 1>() : fp32_kernel<true, 3>();
-  return k.dim == 1 ? fp32_kernel<false, 1>() : fp32_kernel<false, 3>();
+template <class PR>
+void *pick_prec(const TrackKey &k) {
+  if (k.shared) return k.dim == 1 ? fp32_kernel<PR, true, 1>() : fp32_kernel<PR, true, 3>();
+  return k.dim == 1 ? fp32_kernel<PR, false, 1>() : fp32_kernel<PR, false, 3>();
 }
+
+void *pick(const TrackKey &k) { return k.local ? pick_prec<PrecF32L>(k) : pick_prec<PrecF32>(k); }
 }  // namespace
 
 cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem, cudaStream_t stream,

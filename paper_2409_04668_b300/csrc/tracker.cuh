@@ -27,16 +27,32 @@
 
 namespace mcdc {
 
-struct PrecF64 {
-  using R = double;    // direction, distance, cross sections
-  using TT = double;   // shared-memory tally
+// Precision modes.  R: direction, distance, cross sections; TT: shared
+// tally; Q: position and time.
+struct PrecF64 {        // everything in FP64 (event-exact with an FP64 tracker)
+  using R = double;
+  using TT = double;
+  using Q = double;
   static constexpr bool kF64 = true;
+  static constexpr bool kLocal = false;
 };
-struct PrecF32 {
+struct PrecF32 {        // FP32 split: FP64 position and time accumulated every flight
   using R = float;
   using TT = float;
+  using Q = double;
   static constexpr bool kF64 = false;
+  static constexpr bool kLocal = false;
 };
+struct PrecF32L {       // FP32 cell-local: offsets from exact FP64 faces and census edges
+  using R = float;
+  using TT = float;
+  using Q = float;
+  static constexpr bool kF64 = false;
+  static constexpr bool kLocal = true;
+};
+
+template <class PR>
+using PartOf = Part<typename PR::R, typename PR::Q>;
 
 template <class R> __device__ __forceinline__ R rinf();
 template <> __device__ __forceinline__ double rinf<double>() { return CUDART_INF; }
@@ -55,41 +71,69 @@ struct Tables {
   const float *ww32;
 };
 
-// SoA particle bank in shared memory
-template <class R>
+// Pool of parked particles in shared memory: one array per group of fields,
+// each element 8 or 16 bytes, so a particle moves in four to six vector
+// accesses.  Cell indices, time bin and group are packed into 32-bit words.
+template <class PR>
 struct Bank {
-  double *x, *y, *z, *t;
-  uint64_t *hid;
-  R *ux, *uy, *uz, *w;
-  uint32_t *ctr, *serial, *nseg, *ncol, *ncross;
-  uint16_t *i, *j, *k, *tbin;
-  uint8_t *g;
+  using R = typename PR::R;
+  void *xt;           // FP64 position: double2 {x, t}; cell-local: float4 {x, y, z, t}
+  double2 *yz;        // FP64 position, 3-D only: {y, z}
+  void *d0;           // FP32: float4 {ux, uy, uz, w}; FP64: double2 {ux, uy}
+  double2 *d1;        // FP64 only: {uz, w}
+  uint4 *ids;         // {ctr, serial, hid low, hid high}
+  uint4 *cell;        // {i | j << 16, k | tbin << 16, g, nseg}
+  uint2 *cnt;         // {ncol, ncross}
 
-  __device__ __forceinline__ void load(int s, Part<R> &p, int dim) const {
-    p.x = x[s]; p.t = t[s];
-    if (dim == 3) { p.y = y[s]; p.z = z[s]; } else { p.y = 0.0; p.z = 0.0; }
-    p.hid = hid[s];
-    p.ux = ux[s]; p.uy = uy[s]; p.uz = uz[s]; p.w = w[s];
-    p.ctr = ctr[s]; p.serial = serial[s];
-    p.nseg = nseg[s]; p.ncol = ncol[s]; p.ncross = ncross[s];
-    p.i = i[s]; p.j = j[s]; p.k = k[s]; p.tbin = tbin[s]; p.g = g[s];
+  __device__ __forceinline__ void load(int s, PartOf<PR> &p, int dim) const {
+    if constexpr (PR::kLocal) {
+      const float4 a = reinterpret_cast<const float4 *>(xt)[s];
+      p.x = a.x; p.y = a.y; p.z = a.z; p.t = a.w;
+    } else {
+      const double2 a = reinterpret_cast<const double2 *>(xt)[s];
+      p.x = a.x; p.t = a.y;
+      if (dim == 3) { const double2 b = yz[s]; p.y = b.x; p.z = b.y; } else { p.y = 0.0; p.z = 0.0; }
+    }
+    if constexpr (sizeof(R) == 4) {
+      const float4 c = reinterpret_cast<const float4 *>(d0)[s];
+      p.ux = c.x; p.uy = c.y; p.uz = c.z; p.w = c.w;
+    } else {
+      const double2 c0 = reinterpret_cast<const double2 *>(d0)[s];
+      const double2 c1 = d1[s];
+      p.ux = c0.x; p.uy = c0.y; p.uz = c1.x; p.w = c1.y;
+    }
+    const uint4 id = ids[s];
+    p.ctr = id.x; p.serial = id.y; p.hid = (uint64_t)id.z | ((uint64_t)id.w << 32);
+    const uint4 ce = cell[s];
+    p.i = (int)(ce.x & 0xffffu); p.j = (int)(ce.x >> 16);
+    p.k = (int)(ce.y & 0xffffu); p.tbin = (int)(ce.y >> 16);
+    p.g = (int)ce.z; p.nseg = ce.w;
+    const uint2 cn = cnt[s];
+    p.ncol = cn.x; p.ncross = cn.y;
   }
-  __device__ __forceinline__ void store(int s, const Part<R> &p, int dim) const {
-    x[s] = p.x; t[s] = p.t;
-    if (dim == 3) { y[s] = p.y; z[s] = p.z; }
-    hid[s] = p.hid;
-    ux[s] = p.ux; uy[s] = p.uy; uz[s] = p.uz; w[s] = p.w;
-    ctr[s] = p.ctr; serial[s] = p.serial;
-    nseg[s] = p.nseg; ncol[s] = p.ncol; ncross[s] = p.ncross;
-    i[s] = (uint16_t)p.i; j[s] = (uint16_t)p.j; k[s] = (uint16_t)p.k;
-    tbin[s] = (uint16_t)p.tbin; g[s] = (uint8_t)p.g;
+  __device__ __forceinline__ void store(int s, const PartOf<PR> &p, int dim) const {
+    if constexpr (PR::kLocal) {
+      reinterpret_cast<float4 *>(xt)[s] = make_float4(p.x, p.y, p.z, p.t);
+    } else {
+      reinterpret_cast<double2 *>(xt)[s] = make_double2(p.x, p.t);
+      if (dim == 3) yz[s] = make_double2(p.y, p.z);
+    }
+    if constexpr (sizeof(R) == 4) {
+      reinterpret_cast<float4 *>(d0)[s] = make_float4(p.ux, p.uy, p.uz, p.w);
+    } else {
+      reinterpret_cast<double2 *>(d0)[s] = make_double2(p.ux, p.uy);
+      d1[s] = make_double2(p.uz, p.w);
+    }
+    ids[s] = make_uint4(p.ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32));
+    cell[s] = make_uint4((uint32_t)p.i | ((uint32_t)p.j << 16), (uint32_t)p.k | ((uint32_t)p.tbin << 16),
+                         (uint32_t)p.g, p.nseg);
+    cnt[s] = make_uint2(p.ncol, p.ncross);
   }
 };
 
 // bytes of one pool slot (kept in sync with the carve in k_track)
-__host__ __device__ inline int slot_bytes(bool f64, int dim) {
-  const int r = f64 ? 8 : 4;
-  return 8 * 2 + (dim == 3 ? 16 : 0) + 8 + 4 * r + 4 * 5 + 2 * 4 + 1;
+__host__ __device__ inline int slot_bytes(bool f64, int dim, bool local) {
+  return 16 + ((dim == 3 && !local) ? 16 : 0) + (f64 ? 32 : 16) + 16 + 16 + 8;
 }
 
 // particles a warp can park in shared memory besides the 32 in flight
@@ -166,8 +210,9 @@ struct EndSink {
   uint32_t *n_end;      // shared [8]: absorbed, leaked, censused, roulette kill, survive, splits, children, histories
 };
 
-template <class R, int DIM>
-__device__ __forceinline__ void finish(const RunArgs &A, const EndSink &es, const Part<R> &p, int end) {
+template <class PR, int DIM>
+__device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, const EndSink &es,
+                                       const PartOf<PR> &p, int end) {
   if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); atomicAdd(&es.w_end[1], (double)p.w); }
   else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); atomicAdd(&es.w_end[2], (double)p.w); }
   else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); atomicAdd(&es.w_end[3], (double)p.w); }
@@ -178,7 +223,16 @@ __device__ __forceinline__ void finish(const RunArgs &A, const EndSink &es, cons
       Record rec;
       rec.hid = p.hid; rec.end = end; rec.g = p.g; rec.ctr = p.ctr;
       rec.n_seg = p.nseg; rec.n_col = p.ncol; rec.n_cross = p.ncross;
-      rec.x = p.x; rec.y = p.y; rec.z = p.z; rec.t = p.t; rec.w = (double)p.w;
+      if constexpr (PR::kLocal) {
+        // global coordinates from the exact anchors
+        rec.x = P.bounded[0] ? __ldg(P.faces[0] + p.i) + (double)p.x : 0.0;
+        rec.y = (DIM == 3 && P.bounded[1]) ? __ldg(P.faces[1] + p.j) + (double)p.y : 0.0;
+        rec.z = (DIM == 3 && P.bounded[2]) ? __ldg(P.faces[2] + p.k) + (double)p.z : 0.0;
+        rec.t = P.T > 0 ? (p.tbin < P.T ? P.edges[p.tbin + 1] - (double)p.t : P.edges[P.T]) : 0.0;
+      } else {
+        rec.x = p.x; rec.y = p.y; rec.z = p.z; rec.t = p.t;
+      }
+      rec.w = (double)p.w;
       A.records[r] = rec;
     }
   }
@@ -189,8 +243,8 @@ __device__ __forceinline__ void finish(const RunArgs &A, const EndSink &es, cons
 // particle is rouletted away.  Children go to the CTA's overflow stack.
 template <class PR, int DIM>
 __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> &tb,
-                              const RunArgs &A, const EndSink &es, Part<typename PR::R> &p,
-                              int *s_novf, Part<typename PR::R> *ovf) {
+                              const RunArgs &A, const EndSink &es, PartOf<PR> &p,
+                              int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   if (tb.ww == nullptr) return true;
   const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
@@ -207,7 +261,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
       for (int c = 1; c < n; ++c) {
         const U4 h = philox4x32_10(0xFFFFFFFFu, p.serial, p.ctr, (uint32_t)c,
                                    (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
-        Part<R> ch = p;
+        PartOf<PR> ch = p;
         ch.w = wc;
         ch.serial = h.a;
         ch.ctr = 0;
@@ -241,7 +295,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
 // source particle (counters 0..3: x,y | z,group | mu,phi | t)
 template <class PR, int DIM>
 __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R> &tb,
-                                uint64_t seed, uint64_t hid, Part<typename PR::R> &p) {
+                                uint64_t seed, uint64_t hid, PartOf<PR> &p) {
   using R = typename PR::R;
   p.serial = 0; p.ctr = 0; p.hid = hid;
   p.nseg = p.ncol = p.ncross = 0;
@@ -249,9 +303,6 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
   const U4 r1 = draw(p, p.ctr, seed);
   const U4 r2 = draw(p, p.ctr, seed);
   const U4 r3 = draw(p, p.ctr, seed);
-  p.x = P.src_lo[0] + u01_f64(r0.a, r0.b) * (P.src_hi[0] - P.src_lo[0]);
-  p.y = P.src_lo[1] + u01_f64(r0.c, r0.d) * (P.src_hi[1] - P.src_lo[1]);
-  p.z = P.src_lo[2] + u01_f64(r1.a, r1.b) * (P.src_hi[2] - P.src_lo[2]);
   if constexpr (PR::kF64) p.g = sample_cdf<double>(tb.src_cdf, P.G, u01_f64(r1.c, r1.d));
   else p.g = sample_cdf<float>(tb.src_cdf, P.G, u01_f32(r1.c));
   if (P.src_kind == 1) {
@@ -269,14 +320,26 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
     sincospif(2.0f * u01_f32(r2.c), &sn, &cs);
     p.ux = mu; p.uy = s * cs; p.uz = s * sn;
   }
-  p.t = P.t0 + u01_f64(r3.a, r3.b) * (P.t1 - P.t0);
   p.w = (R)1;
-  p.i = loc2index(P, 0, p.x);
-  p.j = (DIM == 3) ? loc2index(P, 1, p.y) : 0;
-  p.k = (DIM == 3) ? loc2index(P, 2, p.z) : 0;
+  const double x = P.src_lo[0] + u01_f64(r0.a, r0.b) * (P.src_hi[0] - P.src_lo[0]);
+  const double y = P.src_lo[1] + u01_f64(r0.c, r0.d) * (P.src_hi[1] - P.src_lo[1]);
+  const double z = P.src_lo[2] + u01_f64(r1.a, r1.b) * (P.src_hi[2] - P.src_lo[2]);
+  const double t = P.t0 + u01_f64(r3.a, r3.b) * (P.t1 - P.t0);
+  p.i = loc2index(P, 0, x);
+  p.j = (DIM == 3) ? loc2index(P, 1, y) : 0;
+  p.k = (DIM == 3) ? loc2index(P, 2, z) : 0;
   p.tbin = 0;
   if (P.T > 0)
-    while (p.tbin < P.T && tb.edges[p.tbin + 1] <= p.t) p.tbin += 1;
+    while (p.tbin < P.T && tb.edges[p.tbin + 1] <= t) p.tbin += 1;
+  if constexpr (PR::kLocal) {
+    // offsets from the cell's low faces; time left to the next census edge
+    p.x = P.bounded[0] ? (float)(x - __ldg(P.faces[0] + p.i)) : 0.0f;
+    p.y = (DIM == 3 && P.bounded[1]) ? (float)(y - __ldg(P.faces[1] + p.j)) : 0.0f;
+    p.z = (DIM == 3 && P.bounded[2]) ? (float)(z - __ldg(P.faces[2] + p.k)) : 0.0f;
+    p.t = (P.T > 0 && p.tbin < P.T) ? (float)(tb.edges[p.tbin + 1] - t) : 0.0f;
+  } else {
+    p.x = x; p.y = y; p.z = z; p.t = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -286,9 +349,9 @@ enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2 };
 template <class PR, int DIM>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
-                                      Part<typename PR::R> &p, int64_t &bin,
+                                      PartOf<PR> &p, int64_t &bin,
                                       typename PR::R &score, int &end, LocalCount &lc,
-                                      int *s_novf, Part<typename PR::R> *ovf) {
+                                      int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
@@ -306,44 +369,75 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     d_coll = sig_t > 0.0f ? -logf(xi) / sig_t : rinf<float>();
   }
 
-  // distance to the mesh surface
+  // distance to the mesh surface and to the time census
   R d_surf = rinf<R>();
   int ax = -1;
-  {
-    const R u = p.ux;
-    if (P.bounded[0] && u != (R)0) {
-      const double f = face_of(P, 0, p.i, u > (R)0);
-      R d;
-      if constexpr (PR::kF64) d = (f - p.x) / u; else d = (float)(f - p.x) / u;
-      if (d < (R)0) d = (R)0;
-      if (d < d_surf) { d_surf = d; ax = 0; }
-    }
-  }
-  if (DIM == 3) {
-    const R u = p.uy;
-    if (P.bounded[1] && u != (R)0) {
-      const double f = face_of(P, 1, p.j, u > (R)0);
-      R d;
-      if constexpr (PR::kF64) d = (f - p.y) / u; else d = (float)(f - p.y) / u;
-      if (d < (R)0) d = (R)0;
-      if (d < d_surf) { d_surf = d; ax = 1; }
-    }
-    const R v = p.uz;
-    if (P.bounded[2] && v != (R)0) {
-      const double f = face_of(P, 2, p.k, v > (R)0);
-      R d;
-      if constexpr (PR::kF64) d = (f - p.z) / v; else d = (float)(f - p.z) / v;
-      if (d < (R)0) d = (R)0;
-      if (d < d_surf) { d_surf = d; ax = 2; }
-    }
-  }
-
-  // distance to the time census
   R d_time = rinf<R>();
-  if (P.T > 0) {
-    if constexpr (PR::kF64) d_time = tb.speed[p.g] * (tb.edges[p.tbin + 1] - p.t);
-    else d_time = tb.speed32[p.g] * (float)(tb.edges[p.tbin + 1] - p.t);
-    if (d_time < (R)0) d_time = (R)0;
+  if constexpr (PR::kLocal) {
+    // cell-local offsets: the face ahead is at width (moving up) or 0
+    {
+      const float u = p.ux;
+      if (P.bounded[0] && u != 0.0f) {
+        float d = (u > 0.0f ? P.width32[0] - p.x : -p.x) / u;
+        if (d < 0.0f) d = 0.0f;
+        if (d < d_surf) { d_surf = d; ax = 0; }
+      }
+    }
+    if (DIM == 3) {
+      const float u = p.uy;
+      if (P.bounded[1] && u != 0.0f) {
+        float d = (u > 0.0f ? P.width32[1] - p.y : -p.y) / u;
+        if (d < 0.0f) d = 0.0f;
+        if (d < d_surf) { d_surf = d; ax = 1; }
+      }
+      const float v = p.uz;
+      if (P.bounded[2] && v != 0.0f) {
+        float d = (v > 0.0f ? P.width32[2] - p.z : -p.z) / v;
+        if (d < 0.0f) d = 0.0f;
+        if (d < d_surf) { d_surf = d; ax = 2; }
+      }
+    }
+    if (P.T > 0) {
+      d_time = tb.speed32[p.g] * p.t;
+      if (d_time < 0.0f) d_time = 0.0f;
+    }
+  } else {
+    {
+      const R u = p.ux;
+      if (P.bounded[0] && u != (R)0) {
+        const double f = face_of(P, 0, p.i, u > (R)0);
+        R d;
+        if constexpr (PR::kF64) d = (f - p.x) / u; else d = (float)(f - p.x) / u;
+        if (d < (R)0) d = (R)0;
+        if (d < d_surf) { d_surf = d; ax = 0; }
+      }
+    }
+    if (DIM == 3) {
+      const R u = p.uy;
+      if (P.bounded[1] && u != (R)0) {
+        const double f = face_of(P, 1, p.j, u > (R)0);
+        R d;
+        if constexpr (PR::kF64) d = (f - p.y) / u; else d = (float)(f - p.y) / u;
+        if (d < (R)0) d = (R)0;
+        if (d < d_surf) { d_surf = d; ax = 1; }
+      }
+      const R v = p.uz;
+      if (P.bounded[2] && v != (R)0) {
+        const double f = face_of(P, 2, p.k, v > (R)0);
+        R d;
+        if constexpr (PR::kF64) d = (f - p.z) / v; else d = (float)(f - p.z) / v;
+        if (d < (R)0) d = (R)0;
+        if (d < d_surf) { d_surf = d; ax = 2; }
+      }
+    }
+
+    // distance to the time census
+    if (P.T > 0) {
+      if constexpr (PR::kF64) d_time = tb.speed[p.g] * (tb.edges[p.tbin + 1] - p.t);
+      else d_time = tb.speed32[p.g] * (float)(tb.edges[p.tbin + 1] - p.t);
+      if (d_time < (R)0) d_time = (R)0;
+    }
+
   }
 
   int ev = 0;  // 0 collision, 1 surface, 2 census
@@ -362,7 +456,11 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
   score = p.w * d;
 
   // move_particle (Figure "jitfunctions"): x += u d, t += d / v
-  if constexpr (PR::kF64) {
+  if constexpr (PR::kLocal) {
+    p.x += p.ux * d;
+    if (DIM == 3) { p.y += p.uy * d; p.z += p.uz * d; }
+    if (P.T > 0) p.t -= d * tb.inv_speed[p.g];
+  } else if constexpr (PR::kF64) {
     p.x += p.ux * d;
     if (DIM == 3) { p.y += p.uy * d; p.z += p.uz * d; }
     p.t += d / tb.speed[p.g];
@@ -374,8 +472,9 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 
   if (ev == 2) {
     lc.census += 1;
-    p.t = tb.edges[p.tbin + 1];
     p.tbin += 1;
+    if constexpr (PR::kLocal) p.t = p.tbin < P.T ? __ldg(P.binw32 + p.tbin) : 0.0f;
+    else p.t = tb.edges[p.tbin];
     if (p.tbin == P.T) { end = END_CENSUSED; return OUT_DEAD; }
     return OUT_CONT;
   }
@@ -385,10 +484,18 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     else if (ax == 1) { u = p.uy; idx = p.j; }
     else { u = p.uz; idx = p.k; }
     const bool up = u > (R)0;
-    const double f = face_of(P, ax, idx, up);
-    if (ax == 0) p.x = f; else if (ax == 1) p.y = f; else p.z = f;
     const int nxt = idx + (up ? 1 : -1);
-    if (nxt < 0 || nxt >= P.n[ax]) {
+    const bool out = nxt < 0 || nxt >= P.n[ax];
+    if constexpr (PR::kLocal) {
+      // onto the face: the far side of the new cell, or the same face when
+      // a reflecting boundary keeps the particle in its cell
+      const float on = (up != out) ? 0.0f : P.width32[ax];
+      if (ax == 0) p.x = on; else if (ax == 1) p.y = on; else p.z = on;
+    } else {
+      const double f = face_of(P, ax, idx, up);
+      if (ax == 0) p.x = f; else if (ax == 1) p.y = f; else p.z = f;
+    }
+    if (out) {
       if (P.bc[2 * ax + (up ? 1 : 0)] == 1) {
         if (ax == 0) p.ux = -u; else if (ax == 1) p.uy = -u; else p.uz = -u;
         return OUT_CONT;
@@ -410,8 +517,8 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 template <class PR, int DIM>
 __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typename PR::R> &tb,
                                         const RunArgs &A, const EndSink &es,
-                                        Part<typename PR::R> &p, int &end, LocalCount &lc,
-                                        int *s_novf, Part<typename PR::R> *ovf) {
+                                        PartOf<PR> &p, int &end, LocalCount &lc,
+                                        int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
@@ -575,26 +682,14 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
   tb.ww32 = P.ww_lower32;
   TT *stally = nullptr;
   if (SHARED) { stally = (TT *)ptr; ptr += L.tally_bytes; }
-  Bank<R> bk;
-  bk.x = (double *)ptr; ptr += 8 * S;
-  bk.t = (double *)ptr; ptr += 8 * S;
-  if (DIM == 3) { bk.y = (double *)ptr; ptr += 8 * S; bk.z = (double *)ptr; ptr += 8 * S; }
-  else { bk.y = bk.z = nullptr; }
-  bk.hid = (uint64_t *)ptr; ptr += 8 * S;
-  bk.ux = (R *)ptr; ptr += sizeof(R) * S;
-  bk.uy = (R *)ptr; ptr += sizeof(R) * S;
-  bk.uz = (R *)ptr; ptr += sizeof(R) * S;
-  bk.w = (R *)ptr; ptr += sizeof(R) * S;
-  bk.ctr = (uint32_t *)ptr; ptr += 4 * S;
-  bk.serial = (uint32_t *)ptr; ptr += 4 * S;
-  bk.nseg = (uint32_t *)ptr; ptr += 4 * S;
-  bk.ncol = (uint32_t *)ptr; ptr += 4 * S;
-  bk.ncross = (uint32_t *)ptr; ptr += 4 * S;
-  bk.i = (uint16_t *)ptr; ptr += 2 * S;
-  bk.j = (uint16_t *)ptr; ptr += 2 * S;
-  bk.k = (uint16_t *)ptr; ptr += 2 * S;
-  bk.tbin = (uint16_t *)ptr; ptr += 2 * S;
-  bk.g = (uint8_t *)ptr; ptr += S;
+  Bank<PR> bk;
+  bk.xt = (void *)ptr; ptr += 16 * S;
+  if (DIM == 3 && !PR::kLocal) { bk.yz = (double2 *)ptr; ptr += 16 * S; } else { bk.yz = nullptr; }
+  bk.d0 = (void *)ptr; ptr += 16 * S;
+  if constexpr (PR::kF64) { bk.d1 = (double2 *)ptr; ptr += 16 * S; } else { bk.d1 = nullptr; }
+  bk.ids = (uint4 *)ptr; ptr += 16 * S;
+  bk.cell = (uint4 *)ptr; ptr += 16 * S;
+  bk.cnt = (uint2 *)ptr; ptr += 8 * S;
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -629,7 +724,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
   EndSink es{s_w, s_n};
   LocalCount lc{0, 0, 0, 0};
   const int wid = blockIdx.x * nwarps + warp;                 // warp id in the grid
-  Part<R> *ovf = reinterpret_cast<Part<R> *>(A.overflow) + (size_t)wid * A.overflow_cap;
+  PartOf<PR> *ovf = reinterpret_cast<PartOf<PR> *>(A.overflow) + (size_t)wid * A.overflow_cap;
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
   const bool agg = A.warp_aggregate != 0;
@@ -657,7 +752,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
     }
 
     // ---- warp loop over this batch (shared) or the launch (global)
-    Part<R> p;
+    PartOf<PR> p;
     bool has = false;
     Mask3 ready{{0u, 0u, 0u}}, coll{{0u, 0u, 0u}};
     bool exhausted = false;
@@ -673,12 +768,12 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
           const int s = mine ? nth3(coll, lane) : 0;
           bool alive = false;
           if (mine) {
-            Part<R> q;
+            PartOf<PR> q;
             bk.load(pool0 + s, q, DIM);
             int end = END_NONE;
             alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf);
             if (alive) bk.store(pool0 + s, q, DIM);
-            else finish<R, DIM>(A, es, q, end);
+            else finish<PR, DIM>(P, A, es, q, end);
           }
           andnot3(coll, gather3(mine, s));
           or3(ready, gather3(mine && alive, s));
@@ -727,7 +822,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
         const int nb = n_o + n_s;
         const int top = min(*novf, A.overflow_cap);
         bool alive = false;
-        Part<R> q;
+        PartOf<PR> q;
         if (lane < nb) {
           if (lane < n_o) {
             q = ovf[top - 1 - lane];
@@ -737,7 +832,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
             atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
-            if (!alive) finish<R, DIM>(A, es, q, END_CENSUSED);
+            if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
           }
         }
         const uint32_t am = __ballot_sync(0xffffffffu, alive);
@@ -771,7 +866,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
         const bool flew = has;
         if (has) {
           outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
-          if (outcome == OUT_DEAD) { finish<R, DIM>(A, es, p, end); has = false; }
+          if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score);
         const bool park = has && outcome == OUT_COLL;

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libmcdc_b300.so")
 MCDC_OK = 0
 MCDC_ERR_INVALID, MCDC_ERR_OOM, MCDC_ERR_CUDA = -1, -2, -3
 MCDC_ERR_BANK_OVERFLOW, MCDC_ERR_TIMEOUT, MCDC_ERR_NO_DEVICE = -4, -5, -6
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_LOCAL = 0, 1, 2
 TALLY_AUTO, TALLY_SHARED, TALLY_GLOBAL = 0, 1, 2
 
 

@@ -138,12 +138,14 @@ def _coarse(mean):
     return mean[0, 0, :, 0, :].reshape(20, 10, 10, 5).sum(axis=(1, 3))
 
 
-def test_fp32_c2_statistical_and_paired_bias(mcdc):
+@pytest.mark.parametrize("prec", ["fp32", "fp32_local"])
+def test_fp32_c2_statistical_and_paired_bias(mcdc, prec):
+    P32 = mcdc.PREC_FP32 if prec == "fp32" else mcdc.PREC_FP32_LOCAL
     prob = W.c2_two_region()
     # (1) every bin against an independent oracle run: per-bin batch errors
     # are valid, so |z| > 4 may only occur about as often as chance allows
     N = 2_000_000
-    g32 = mcdc.run_numpy(prob, N, seed=2, batches=40, precision=mcdc.PREC_FP32)
+    g32 = mcdc.run_numpy(prob, N, seed=2, batches=40, precision=P32)
     o = O.run(prob, 1_000_000, seed=1, batches=40)
     c = g32["counts"]
     assert c["absorbed"] + c["leaked"] + c["censused"] == N
@@ -158,16 +160,16 @@ def test_fp32_c2_statistical_and_paired_bias(mcdc):
     # path reproduces the oracle event for event, tested above)
     R, n = 32, 300_000
     reps = {}
-    for prec in (mcdc.PREC_FP32, mcdc.PREC_FP64):
-        with mcdc.Problem(prob, precision=prec) as P:
+    for pr in (P32, mcdc.PREC_FP64):
+        with mcdc.Problem(prob, precision=pr) as P:
             rows = []
             for r in range(R):
                 m = np.zeros(P.n_bins)
-                P.run_ex(n, 5, offset=(r + 1) * 10_000_000 + (prec * 1000_000_000), batches=8,
+                P.run_ex(n, 5, offset=(r + 1) * 10_000_000 + (pr * 1000_000_000), batches=8,
                          mean=m, want_stats=False)
                 rows.append(_coarse(m.reshape(prob.tally_shape)))
-        reps[prec] = np.array(rows)
-    a, b = reps[mcdc.PREC_FP32], reps[mcdc.PREC_FP64]
+        reps[pr] = np.array(rows)
+    a, b = reps[P32], reps[mcdc.PREC_FP64]
     se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
     ok = se > 0
     z = (a.mean(axis=0) - b.mean(axis=0))[ok] / se[ok]
@@ -181,6 +183,45 @@ def test_fp32_c2_statistical_and_paired_bias(mcdc):
     print("paired FP32-FP64 bias of the total", bias, "noise", g64["scalar"][1],
           "coarse max |bias|", float(np.abs(cb[_coarse(g64["mean"]) > 0]).max()))
     assert abs(bias) < 0.2 * g64["scalar"][1], (bias, g64["scalar"][1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_local"])
+def test_fp32_modes_3d_channel(mcdc, prec):
+    """3-D geometry of the FP32 modes: exact balance, and the region total
+    of a paired FP64 run (same random streams) within a small fraction of
+    the statistical error."""
+    P32 = mcdc.PREC_FP32 if prec == "fp32" else mcdc.PREC_FP32_LOCAL
+    prob = small_channel()
+    N = 400_000
+    whole = ((0, 0, 0), prob.n)
+    g = mcdc.run_numpy(prob, N, seed=4, batches=20, precision=P32, region=whole)
+    d = mcdc.run_numpy(prob, N, seed=4, batches=20, precision=mcdc.PREC_FP64, region=whole)
+    c = g["counts"]
+    assert c["absorbed"] + c["leaked"] + c["censused"] == N
+    tot32, tot64 = g["sum1"].sum(), d["sum1"].sum()
+    # total track length: relative error of the total is well below 1e-2 here
+    assert abs(tot32 / tot64 - 1.0) < 2e-3, (tot32, tot64)
+    bias = g["scalar"][0] / d["scalar"][0] - 1.0
+    assert abs(bias) < 0.3 * d["scalar"][1], (bias, d["scalar"][1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_local"])
+def test_fp32_modes_reflecting_infinite_medium(mcdc, prec):
+    """All faces reflecting, uniform source: every cell's flux is
+    1 / (Sigma_a V_box) (the closed form the oracle is pinned to)."""
+    P32 = mcdc.PREC_FP32 if prec == "fp32" else mcdc.PREC_FP32_LOCAL
+    mat = np.zeros((3, 2, 4), np.uint8)
+    n, w = (4, 2, 3), (0.5, 1.0, 0.7)
+    ext = tuple(k * d for k, d in zip(n, w))
+    prob = W.box("inf", n, w, mat, [[1.0]], [[0.8]], np.ones((1, 1, 1)),
+                 [1.0], (0.0, 0.0, 0.0), ext, None, (0, 0, 0), n, bc=(W.BC_REFLECT,) * 6)
+    N = 400_000
+    g = mcdc.run_numpy(prob, N, seed=6, batches=40, precision=P32)
+    ref = 1.0 / (0.2 * ext[0] * ext[1] * ext[2])
+    m = g["mean"].reshape(-1)
+    z = (m - ref) / (m * g["relerr"].reshape(-1))
+    assert np.all(np.abs(z) < 4.5), z
+    assert g["counts"]["absorbed"] == N
 
 
 def test_edge_cases(mcdc):
