@@ -149,7 +149,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--histories", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_local", "fp64"])
+    ap.add_argument("--batches", type=int, default=0, help="batches per run (0: library default)")
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -171,8 +173,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2409_04668_b300 import mcdc as M
 
-    prec = M.PREC_FP32 if args.precision == "fp32" else M.PREC_FP64
-    P = M.Problem(prob, precision=prec)
+    prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
+    P = M.Problem(prob, precision=prec, block_size=args.block)
     dev = torch.device("cuda", local)
     mean = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
     rel = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
@@ -181,7 +183,8 @@ def main():
     offset0 = rank * n_hist * 1000
 
     def step(s):
-        return P.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, mean=mean, relerr=rel,
+        return P.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, batches=args.batches,
+                        mean=mean, relerr=rel,
                         stream=stream.cuda_stream, want_scalar=True, want_stats=True)
 
     for s in range(args.warmup):
@@ -230,9 +233,9 @@ def main():
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     for s in range(e2e_steps):
-        with M.Problem(prob, precision=prec) as Q:
-            Q.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, mean=h_mean, relerr=h_rel,
-                     want_stats=False)
+        with M.Problem(prob, precision=prec, block_size=args.block) as Q:
+            Q.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, batches=args.batches,
+                     mean=h_mean, relerr=h_rel, want_stats=False)
     te = time.perf_counter() - te0
     e2e_val = n_hist * e2e_steps * world / te
 
@@ -244,7 +247,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if prec == M.PREC_FP32 else "f64", "data": "synthetic",
+        "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 anchors)",
+                  M.PREC_FP64: "f64"}[prec], "data": "synthetic",
         "config": {"workload": prob.name, "histories_per_step": n_hist, "precision": args.precision,
                    "tally_mode": ["auto", "shared", "global"][stats_all[-1]["tally_mode"]],
                    "n_batches": stats_all[-1]["n_batches"], "block": stats_all[-1]["block_size"],
