@@ -382,6 +382,10 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   P.M = M; P.G = G; P.T = T; P.T1 = T > 0 ? T : 1;
   P.n_cells = n_cells;
   P.n_bins = n_cells * G * P.T1;
+  if (P.n_bins >= (1ll << 31)) {
+    delete pr;
+    return fail(MCDC_ERR_INVALID, "the tally needs fewer than 2^31 bins (cells x groups x time bins)");
+  }
   P.volume = 1.0;
   for (int a = 0; a < 3; ++a)
     if (bounded[a]) P.volume *= wid[a];

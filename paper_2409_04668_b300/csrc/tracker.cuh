@@ -194,12 +194,12 @@ __device__ __forceinline__ int sample_cdf(const R *cdf, int n, R xi) {
 }
 
 template <int DIM>
-__device__ __forceinline__ int64_t cell_index(const DevProblem &P, int i, int j, int k) {
+__device__ __forceinline__ int cell_index(const DevProblem &P, int i, int j, int k) {
   if (DIM == 1) return i;
-  return ((int64_t)k * P.n[1] + j) * P.n[0] + i;
+  return (k * P.n[1] + j) * P.n[0] + i;
 }
 
-__device__ __forceinline__ int64_t bin_index(const DevProblem &P, int64_t cell, int g, int tbin) {
+__device__ __forceinline__ int bin_index(const DevProblem &P, int cell, int g, int tbin) {
   return (cell * P.G + g) * P.T1 + (P.T > 0 ? tbin : 0);
 }
 
@@ -247,8 +247,8 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
                               int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   if (tb.ww == nullptr) return true;
-  const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
-  const int64_t bin = bin_index(P, cell, p.g, p.tbin);
+  const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
+  const int bin = bin_index(P, cell, p.g, p.tbin);
   R wl;
   if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
   if (!(wl > (R)0)) return true;
@@ -349,11 +349,11 @@ enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2 };
 template <class PR, int DIM>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
-                                      PartOf<PR> &p, int64_t &bin,
+                                      PartOf<PR> &p, int &bin,
                                       typename PR::R &score, int &end, LocalCount &lc,
                                       int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
-  const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
+  const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
   const int mg = m * P.G + p.g;
   const R sig_t = tb.sigma_t[mg];
@@ -520,7 +520,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
                                         PartOf<PR> &p, int &end, LocalCount &lc,
                                         int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
-  const int64_t cell = cell_index<DIM>(P, p.i, p.j, p.k);
+  const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
   const int mg = m * P.G + p.g;
   p.ncol += 1;
@@ -554,13 +554,13 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
 // tally scatter of one warp: optional warp aggregation of equal bins
 template <class TT, class R>
 __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool shared_mode,
-                                              bool aggregate, bool valid, int64_t bin, R score) {
+                                              bool aggregate, bool valid, int bin, R score) {
   bool act = valid && bin >= 0;
   R v = score;
   if (aggregate) {
     // lanes scoring into the same bin add their scores first; the lowest
     // such lane issues the one atomic.  All 32 lanes run the same shuffles.
-    const long long key = act ? (long long)bin : -1ll;
+    const int key = act ? bin : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const bool dup = act && __popc(peers) > 1;
     if (__any_sync(0xffffffffu, dup)) {
@@ -582,18 +582,6 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
 }
 
 // ---------------------------------------------------------------------------
-// Warp-private pools.  A warp keeps up to kPool = 96 parked particles in
-// shared memory (SoA); slot states live in two 96-bit masks held in
-// registers (identical in every lane): `ready` (waiting for a lane to fly
-// it) and `coll` (waiting for its collision).
-struct Mask3 {
-  uint32_t w[3];
-};
-
-__device__ __forceinline__ int popc3(const Mask3 &m) {
-  return __popc(m.w[0]) + __popc(m.w[1]) + __popc(m.w[2]);
-}
-
 // index of the n-th (0-based) set bit of a 32-bit word (binary search on popc)
 __device__ __forceinline__ int nth32(uint32_t m, int n) {
   int pos = 0;
@@ -603,36 +591,6 @@ __device__ __forceinline__ int nth32(uint32_t m, int n) {
     if (n >= c) { n -= c; m >>= s; pos += s; }
   }
   return pos;
-}
-
-__device__ __forceinline__ int nth3(const Mask3 &m, int n) {
-  const int c0 = __popc(m.w[0]);
-  if (n < c0) return nth32(m.w[0], n);
-  n -= c0;
-  const int c1 = __popc(m.w[1]);
-  if (n < c1) return 32 + nth32(m.w[1], n);
-  return 64 + nth32(m.w[2], n - c1);
-}
-
-// OR over the warp of the bit of slot s from every lane with pred set
-__device__ __forceinline__ Mask3 gather3(bool pred, int s) {
-  Mask3 r;
-  r.w[0] = __reduce_or_sync(0xffffffffu, (pred && s < 32) ? (1u << s) : 0u);
-  r.w[1] = __reduce_or_sync(0xffffffffu, (pred && s >= 32 && s < 64) ? (1u << (s - 32)) : 0u);
-  r.w[2] = __reduce_or_sync(0xffffffffu, (pred && s >= 64) ? (1u << (s - 64)) : 0u);
-  return r;
-}
-
-__device__ __forceinline__ void or3(Mask3 &a, const Mask3 &b) {
-  a.w[0] |= b.w[0]; a.w[1] |= b.w[1]; a.w[2] |= b.w[2];
-}
-__device__ __forceinline__ void andnot3(Mask3 &a, const Mask3 &b) {
-  a.w[0] &= ~b.w[0]; a.w[1] &= ~b.w[1]; a.w[2] &= ~b.w[2];
-}
-__device__ __forceinline__ Mask3 free3(const Mask3 &r, const Mask3 &c) {
-  Mask3 f;
-  f.w[0] = ~(r.w[0] | c.w[0]); f.w[1] = ~(r.w[1] | c.w[1]); f.w[2] = ~(r.w[2] | c.w[2]);
-  return f;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -751,51 +709,55 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
       if (s_done) break;
     }
 
-    // ---- warp loop over this batch (shared) or the launch (global)
+    // ---- warp loop over this batch (shared) or the launch (global).  The
+    // warp's kPool slots hold two stacks: particles ready to fly grow up from
+    // slot 0 (rtop of them), particles waiting for their collision grow down
+    // from the last slot (ctop of them).  At most 94 particles are ever
+    // parked (see above), so the stacks never meet.
     PartOf<PR> p;
     bool has = false;
-    Mask3 ready{{0u, 0u, 0u}}, coll{{0u, 0u, 0u}};
+    int rtop = 0, ctop = 0;          // identical in every lane
     bool exhausted = false;
+    const uint32_t lt = lanemask_lt();
+    auto slot_of = [&](int s) { return pool0 + min(max(s, 0), kPool - 1); };
     for (;;) {
       __syncwarp();   // every lane sees the same overflow count below
       // (1) collisions: a dense pass when 32 are parked, or whatever is
       // parked once nothing is ready and no more births can come
       {
-        const int nc = popc3(coll);
         const bool drain = exhausted && (*novf == 0);
-        if (nc >= 32 || (nc > 0 && popc3(ready) == 0 && drain)) {
-          const bool mine = lane < nc;
-          const int s = mine ? nth3(coll, lane) : 0;
+        if (ctop >= 32 || (ctop > 0 && rtop == 0 && drain)) {
+          const int n = min(ctop, 32);
+          const bool mine = lane < n;
+          PartOf<PR> q;
+          if (mine) bk.load(slot_of(kPool - ctop + lane), q, DIM);
+          __syncwarp();   // every parked particle is read before survivors are written
+          ctop -= n;
           bool alive = false;
           if (mine) {
-            PartOf<PR> q;
-            bk.load(pool0 + s, q, DIM);
             int end = END_NONE;
             alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf);
-            if (alive) bk.store(pool0 + s, q, DIM);
-            else finish<PR, DIM>(P, A, es, q, end);
+            if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
-          andnot3(coll, gather3(mine, s));
-          or3(ready, gather3(mine && alive, s));
+          const uint32_t am = __ballot_sync(0xffffffffu, alive);
+          if (alive) bk.store(slot_of(rtop + __popc(am & lt)), q, DIM);
+          rtop += __popc(am);
           __syncwarp();
         }
       }
-      // (2) empty lanes take ready particles
+      // (2) empty lanes take ready particles from the top of the stack
       {
         const uint32_t empty = __ballot_sync(0xffffffffu, !has);
-        const int nr = popc3(ready);
-        if (empty && nr) {
-          const int r = __popc(empty & lanemask_lt());
-          const bool take = !has && r < nr;
-          const int s = take ? nth3(ready, r) : 0;
-          if (take) { bk.load(pool0 + s, p, DIM); has = true; }
-          andnot3(ready, gather3(take, s));
+        if (empty && rtop) {
+          const int r = __popc(empty & lt);
+          const bool take = !has && r < rtop;
+          if (take) { bk.load(slot_of(rtop - 1 - r), p, DIM); has = true; }
+          rtop -= min(rtop, __popc(empty));
           __syncwarp();
         }
       }
       // (3) births when lanes are still empty and nothing is ready
-      if (__any_sync(0xffffffffu, !has) && popc3(ready) == 0 && !(exhausted && *novf == 0)) {
-        __syncwarp();
+      if (__any_sync(0xffffffffu, !has) && rtop == 0 && !(exhausted && *novf == 0)) {
         const int n_o = min(32, min(*novf, A.overflow_cap));
         int n_s = 0;
         unsigned long long h_first = 0;
@@ -835,33 +797,50 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
           }
         }
+        // the newborns go straight to the empty lanes; any left over are parked
         const uint32_t am = __ballot_sync(0xffffffffu, alive);
-        const Mask3 fr = free3(ready, coll);
-        const int s = alive ? nth3(fr, __popc(am & lanemask_lt())) : 0;
-        if (alive) bk.store(pool0 + s, q, DIM);
-        or3(ready, gather3(alive, s));
+        const uint32_t empty = __ballot_sync(0xffffffffu, !has);
+        const int na = __popc(am), ne = __popc(empty);
+        const int k = __popc(am & lt);                 // rank of my newborn
+        const int r = __popc(empty & lt);              // rank of my empty lane
+        if (alive && k >= ne) bk.store(slot_of(k - ne), q, DIM);
         __syncwarp();
         if (lane == 0) *novf = min(*novf, A.overflow_cap) - n_o;
-        __syncwarp();
-        // and hand them to the empty lanes
-        const uint32_t empty = __ballot_sync(0xffffffffu, !has);
-        const int nr = popc3(ready);
-        const int r = __popc(empty & lanemask_lt());
-        const bool take = !has && r < nr;
-        const int st = take ? nth3(ready, r) : 0;
-        if (take) { bk.load(pool0 + st, p, DIM); has = true; }
-        andnot3(ready, gather3(take, st));
+        // lane with the r-th empty slot receives the r-th newborn (a shuffle per field)
+        const int src = (r < na) ? (int)nth32(am, r) : 0;
+        PartOf<PR> got;
+        got.x = __shfl_sync(0xffffffffu, q.x, src);
+        got.y = __shfl_sync(0xffffffffu, q.y, src);
+        got.z = __shfl_sync(0xffffffffu, q.z, src);
+        got.t = __shfl_sync(0xffffffffu, q.t, src);
+        got.ux = __shfl_sync(0xffffffffu, q.ux, src);
+        got.uy = __shfl_sync(0xffffffffu, q.uy, src);
+        got.uz = __shfl_sync(0xffffffffu, q.uz, src);
+        got.w = __shfl_sync(0xffffffffu, q.w, src);
+        got.g = __shfl_sync(0xffffffffu, q.g, src);
+        got.i = __shfl_sync(0xffffffffu, q.i, src);
+        got.j = __shfl_sync(0xffffffffu, q.j, src);
+        got.k = __shfl_sync(0xffffffffu, q.k, src);
+        got.tbin = __shfl_sync(0xffffffffu, q.tbin, src);
+        got.ctr = __shfl_sync(0xffffffffu, q.ctr, src);
+        got.serial = __shfl_sync(0xffffffffu, q.serial, src);
+        got.hid = __shfl_sync(0xffffffffu, q.hid, src);
+        got.nseg = __shfl_sync(0xffffffffu, q.nseg, src);
+        got.ncol = __shfl_sync(0xffffffffu, q.ncol, src);
+        got.ncross = __shfl_sync(0xffffffffu, q.ncross, src);
+        if (!has && r < na) { p = got; has = true; }
+        rtop = max(0, na - ne);
         __syncwarp();
       }
       // (4) nothing in flight: progress through collisions/births, or stop
       if (!__any_sync(0xffffffffu, has)) {
-        if (popc3(coll) == 0 && popc3(ready) == 0 && exhausted && *novf == 0) break;
+        if (ctop == 0 && rtop == 0 && exhausted && *novf == 0) break;
         continue;
       }
       // (5) one flight for every lane that holds a particle
       {
         int outcome = OUT_CONT, end = END_NONE;
-        int64_t bin = -1;
+        int bin = -1;
         R score = (R)0;
         const bool flew = has;
         if (has) {
@@ -872,10 +851,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
         const bool park = has && outcome == OUT_COLL;
         const uint32_t pm = __ballot_sync(0xffffffffu, park);
         if (pm) {
-          const Mask3 fr = free3(ready, coll);
-          const int s = park ? nth3(fr, __popc(pm & lanemask_lt())) : 0;
-          if (park) { bk.store(pool0 + s, p, DIM); has = false; }
-          or3(coll, gather3(park, s));
+          if (park) { bk.store(slot_of(kPool - ctop - 1 - __popc(pm & lt)), p, DIM); has = false; }
+          ctop += __popc(pm);
           __syncwarp();
         }
       }
