@@ -294,7 +294,7 @@ def roofline(prob, seg_rate, pk, tally_mode):
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": "measured copy"}
     # issue-slot roofline: lane-instructions per segment of the algorithm as
     # written against 148 SMs x 128 lanes x max SM clock
-    ops_per_seg = 160.0
+    ops_per_seg = 116.0   # algorithmic lane-ops per flight, counted in the design doc §6
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = seg_rate * ops_per_seg / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
