@@ -268,7 +268,7 @@ def main():
     }
     launches_per_step = 2 if stats_all[-1]["tally_mode"] == 1 else 3 * stats_all[-1]["n_batches"] + 1
     line["gpu_launches"] = launches_per_step * args.steps
-    # roofline of the tracker: per-segment figures are stated in the design doc
+    # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)
     line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"])
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -292,9 +292,11 @@ def roofline(prob, seg_rate, pk, tally_mode):
         ach = seg_rate * 16 / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": "measured copy"}
-    # issue-slot roofline: lane-instructions per segment of the algorithm as
-    # written against 148 SMs x 128 lanes x max SM clock
-    ops_per_seg = 116.0   # algorithmic lane-ops per flight, counted in the design doc §6
+    # issue-slot roofline: lane-operations per flight of the algorithm as
+    # written (Philox 60, uniform 4, log+divide 4, lookup 3, face 4, census 3,
+    # nearest event 4, tally 4, move 4, resolution 4, collisions 17 and births
+    # 5 amortised) against 148 SMs x 128 lanes x max SM clock
+    ops_per_seg = 116.0
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = seg_rate * ops_per_seg / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
