@@ -104,4 +104,13 @@ int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
 int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
               int64_t n, orc_record *out);
 
+/* Importance network (mlp.c): in -> H -> H -> 1, SiLU hidden layers. */
+int64_t orc_mlp_param_count(int32_t in, int32_t H);
+void orc_mlp_forward(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
+                     const double *X, double *out);
+double orc_mlp_loss_grad(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
+                         const double *X, const double *y, const double *w, double *grad);
+void orc_adam_step(int64_t np, double *p, double *m, double *v, const double *g, double lr,
+                   double b1, double b2, double eps, int64_t t);
+
 #endif

@@ -72,6 +72,8 @@ def lib():
 
 
 def _bind_mlp(L):
+    L.orc_mlp_param_count.argtypes = [C.c_int32, C.c_int32]
+    L.orc_mlp_param_count.restype = C.c_int64
     L.orc_mlp_forward.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                   C.c_void_p, C.c_void_p]
     L.orc_mlp_loss_grad.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
@@ -196,3 +198,39 @@ def isotropic(xi_mu, xi_phi):
     u = np.zeros(3)
     lib().orc_isotropic(float(xi_mu), float(xi_phi), u.ctypes.data)
     return u
+
+
+# ---- importance network (FP64) ------------------------------------------
+
+def mlp_param_count(n_in, hidden=64):
+    return int(lib().orc_mlp_param_count(int(n_in), int(hidden)))
+
+
+def mlp_forward(params, X, hidden=64):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    lib().orc_mlp_forward(X.shape[1], hidden, 0, p.ctypes.data, X.shape[0], X.ctypes.data,
+                          out.ctypes.data)
+    return out
+
+
+def mlp_loss_grad(params, X, y, w, hidden=64):
+    """Weighted mean-square loss and its gradient (backpropagation, FP64)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.zeros(p.size)
+    loss = lib().orc_mlp_loss_grad(X.shape[1], hidden, 0, p.ctypes.data, X.shape[0],
+                                   X.ctypes.data, y.ctypes.data, w.ctypes.data, g.ctypes.data)
+    return loss, g
+
+
+def adam_step(p, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().orc_adam_step(p.size, p.ctypes.data, m.ctypes.data, v.ctypes.data, g.ctypes.data,
+                        lr, b1, b2, eps, int(t))
