@@ -203,6 +203,63 @@ int64_t mcdc_tally_size(const struct mcdc_problem *prob);
 
 void mcdc_problem_destroy(struct mcdc_problem *prob);
 
+/* ---- learned importance proposal ----------------------------------------
+ * A 3-layer perceptron (4 + G) -> 64 -> 64 -> 1 with SiLU hidden layers maps
+ * a tally bin (cell centre and bin-centre time scaled to [-1, 1], group
+ * one-hot) to the log of its forward flux.  It is fit on the GPU (BF16
+ * tensor-core forward/backward, FP32 master weights, Adam) to the log mean of
+ * a pilot run, each bin weighted 1 / (1 + relerr^2), unscored bins left out;
+ * then every bin's weight-window lower bound is set to
+ * source_wl * phi_pred(bin) / max phi_pred (bounded below, see min_ratio), so
+ * particles split on their way
+ * into low-flux regions and are rouletted coming back.  The paper has no such
+ * network; the weight windows it drives are the variance-reduction events of
+ * "MC/DC on CPUs". */
+typedef struct mcdc_mlp_options {
+    int32_t epochs;             /* passes over the bins (default 40)             */
+    int32_t batch;              /* samples per Adam step (default 65536, >= 64)  */
+    double lr;                  /* Adam step size (default 2e-3)                 */
+    uint64_t seed;              /* weight initialisation                          */
+    double source_wl;           /* w_L of the highest-flux bin (default 0.5)     */
+    double upper_ratio;         /* w_U / w_L (default 5)                         */
+    double survival_ratio;      /* w_S / w_L (default 2.5)                       */
+    int32_t nmax;               /* split cap (default 16)                        */
+    double min_ratio;           /* floor of w_L / w_L(highest-flux bin) (default 1e-8);
+                                   w_L is also kept above a tenth of the least-scored
+                                   bin's value, so extrapolated windows cannot run away */
+} mcdc_mlp_options;
+
+typedef struct mcdc_mlp_report {
+    int64_t samples;            /* scored bins used for training                 */
+    double loss_first, loss_last;   /* mean minibatch loss, first and last epoch (normalised targets) */
+    double train_ms, bake_ms;   /* device time of training and of the bake       */
+    int32_t steps;              /* Adam steps                                    */
+    double target_mean;         /* weighted mean of the log-flux targets         */
+} mcdc_mlp_report;
+
+void mcdc_default_mlp_options(mcdc_mlp_options *opt);
+
+/* Trains the network on a pilot tally (pilot_mean required, pilot_relerr may
+ * be NULL; [n_bins] doubles, host or device) and switches the problem to the
+ * weight windows it predicts.  Errors: MCDC_ERR_INVALID (no scored bin, more
+ * than 12 groups, bad options), MCDC_ERR_OOM, MCDC_ERR_CUDA. */
+int mcdc_train_importance(struct mcdc_problem *prob, const double *pilot_mean,
+                          const double *pilot_relerr, const mcdc_mlp_options *opt,
+                          mcdc_mlp_report *report);
+
+/* Parameter count of the network for n_in inputs (1..16), -1 otherwise.
+ * Flat FP32 layout: W1[64][n_in], b1[64], W2[64][64], b2[64], W3[64], b3. */
+int64_t mcdc_mlp_param_count(int32_t n_in);
+
+/* Prediction f(X[i]) for n samples (FP32 inputs [n][n_in]; pointers host or
+ * device), on the tensor cores with BF16 weights and FP32 accumulation. */
+int mcdc_mlp_forward(const float *params, int32_t n_in, const float *X, int64_t n, float *out);
+
+/* Weighted least-squares loss sum_i w_i (f(X_i) - y_i)^2 / sum_i w_i and its
+ * gradient with respect to every parameter (same layout as params). */
+int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float *X, const float *y,
+                       const float *w, int64_t n, float *grad, double *loss);
+
 /* Allocation-free run (the paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc while transport runs, e.g. a code
  * whose pool allocator owns all device memory, or a loop where an

@@ -230,6 +230,7 @@ int ensure_overflow(mcdc_problem *pr) {
 
 namespace mcdc {
 int set_error(int code, const std::string &msg) { return fail(code, msg); }
+int ensure_overflow_for(mcdc_problem *pr) { return ensure_overflow(pr); }
 }  // namespace mcdc
 
 extern "C" {

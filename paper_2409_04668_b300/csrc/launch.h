@@ -36,5 +36,13 @@ cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,
 
 // Records the calling thread's error message (read by mcdc_last_error).
 int set_error(int code, const std::string &msg);
+}  // namespace mcdc
+struct mcdc_problem;
+namespace mcdc {
+// Allocates the per-warp overflow stacks once weight windows are on.
+int ensure_overflow_for(mcdc_problem *pr);
+// importance network (mlp.cu)
+cudaError_t mlp_prepare();
+int64_t mlp_param_count(int n_in);
 
 }  // namespace mcdc

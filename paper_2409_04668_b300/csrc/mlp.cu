@@ -1,0 +1,845 @@
+// mlp.cu -- the learned importance proposal: a 3-layer perceptron
+// in -> 64 -> 64 -> 1 (SiLU hidden layers) over (x, y, z, t, group one-hot)
+// that predicts the log of the forward flux of every tally bin.  Weight
+// windows follow the prediction (lower bound proportional to the predicted
+// flux, a forward-flux importance reading), so particles are split on their
+// way into regions the analog run hardly reaches and rouletted on their way
+// back.
+//
+// Training and inference run on the tensor cores: BF16 weights and
+// activations, FP32 accumulation (mma.sync m16n8k16), FP32 master weights
+// and Adam state.  A CTA handles tiles of 64 samples with 4 warps; every
+// operand of an MMA is read from shared memory with K contiguous, so each
+// fragment register is one aligned 32-bit load.
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcdc.h"
+#include "launch.h"
+#include "problem.h"
+
+namespace mcdc {
+namespace {
+
+constexpr int kH = 64;        // hidden width
+constexpr int kIn = 16;       // padded input width (n_in <= 16)
+constexpr int kS = 64;        // samples per CTA tile
+constexpr int kThreads = 128; // 4 warps, 16 samples each in the row-wise phases
+
+__host__ __device__ inline int64_t param_count(int n_in) {
+  return (int64_t)kH * n_in + kH + (int64_t)kH * kH + kH + kH + 1;
+}
+
+struct Params {              // offsets into the flat FP32 parameter vector
+  const float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+__device__ __forceinline__ Params split(const float *p, int n_in) {
+  Params q;
+  q.W1 = p; q.b1 = q.W1 + kH * n_in; q.W2 = q.b1 + kH; q.b2 = q.W2 + kH * kH;
+  q.W3 = q.b2 + kH; q.b3 = q.W3 + kH;
+  return q;
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {
+  return *reinterpret_cast<const uint32_t *>(p);
+}
+
+// C[16x8] += A[16x16] * B[16x8] on the tensor cores.  A(m, k) = A[m*lda + k],
+// B(k, n) = Bt[n*ldb + k]; lda, ldb even, rows 4-byte aligned.
+__device__ __forceinline__ void mma16816(float c[4], const __nv_bfloat16 *A, int lda,
+                                         const __nv_bfloat16 *Bt, int ldb) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t a0 = ld32(A + g * lda + 2 * t);
+  const uint32_t a1 = ld32(A + (g + 8) * lda + 2 * t);
+  const uint32_t a2 = ld32(A + g * lda + 2 * t + 8);
+  const uint32_t a3 = ld32(A + (g + 8) * lda + 2 * t + 8);
+  const uint32_t b0 = ld32(Bt + g * ldb + 2 * t);
+  const uint32_t b1 = ld32(Bt + g * ldb + 2 * t + 8);
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// shared memory of one CTA
+struct Smem {
+  __nv_bfloat16 W1[kH][kIn];      // layer-1 weights, [out][in]
+  __nv_bfloat16 W2[kH][kH];       // layer-2 weights, [out][in]
+  __nv_bfloat16 W2T[kH][kH];      // transposed, [in][out]
+  float b1[kH], b2[kH], W3[kH];
+  __nv_bfloat16 X[kS][kIn];       // tile inputs, [sample][feature]
+  __nv_bfloat16 XT[kIn][kS];      // [feature][sample]
+  float Z1[kS][kH];               // layer-1 pre-activations
+  __nv_bfloat16 H1[kS][kH];       // layer-1 outputs
+  __nv_bfloat16 H1T[kH][kS];
+  __nv_bfloat16 D2[kS][kH];       // dL/dz2
+  __nv_bfloat16 D2T[kH][kS];
+  __nv_bfloat16 D1T[kH][kS];      // dL/dz1, transposed
+  float y[kS], w[kS];             // targets and sample weights of the tile
+  float gW3[kH], gb2[kH], gb1[kH];
+  float gb3, loss;
+};
+
+__device__ void load_weights(Smem &s, const float *p, int n_in) {
+  const Params q = split(p, n_in);
+  for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
+    const int r = i / kIn, c = i % kIn;
+    s.W1[r][c] = __float2bfloat16(c < n_in ? q.W1[r * n_in + c] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const int r = i / kH, c = i % kH;
+    const __nv_bfloat16 v = __float2bfloat16(q.W2[i]);
+    s.W2[r][c] = v;
+    s.W2T[c][r] = v;
+  }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    s.b1[i] = q.b1[i]; s.b2[i] = q.b2[i]; s.W3[i] = q.W3[i];
+  }
+}
+
+// Load one tile of samples [base, base + kS) (rows past n get zero input and
+// zero weight, so they contribute nothing).
+__device__ void load_tile(Smem &s, const float *X, const float *Y, const float *Wt, int64_t n,
+                          int n_in, int64_t base) {
+  for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x) {
+    const int r = i / kIn, c = i % kIn;
+    const int64_t row = base + r;
+    const float v = (row < n && c < n_in) ? X[row * n_in + c] : 0.0f;
+    const __nv_bfloat16 b = __float2bfloat16(v);
+    s.X[r][c] = b;
+    s.XT[c][r] = b;
+  }
+  for (int r = threadIdx.x; r < kS; r += blockDim.x) {
+    const int64_t row = base + r;
+    s.y[r] = (row < n && Y) ? Y[row] : 0.0f;
+    s.w[r] = (row < n && Wt) ? Wt[row] : 0.0f;
+  }
+}
+
+// Forward pass of the warp's 16 rows: layer 1 into Z1/H1 (+H1T), layer 2 in
+// registers (z2[j][4] for the 8 column tiles), prediction per row.
+__device__ void forward_rows(Smem &s, int r0, float z2[8][4], float &y_lo, float &y_hi,
+                             float b3) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    mma16816(c, &s.X[r0][0], kIn, &s.W1[8 * j][0], kIn);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
+      const float z = c[e] + s.b1[col];
+      s.Z1[row][col] = z;
+      const __nv_bfloat16 h = __float2bfloat16(silu(z));
+      s.H1[row][col] = h;
+      s.H1T[col][row] = h;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) mma16816(c, &s.H1[r0][16 * kk], kH, &s.W2[8 * j][16 * kk], kH);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) z2[j][e] = c[e] + s.b2[8 * j + 2 * t + (e & 1)];
+  }
+  float lo = 0.f, hi = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float v = silu(z2[j][e]) * s.W3[8 * j + 2 * t + (e & 1)];
+      if (e < 2) lo += v; else hi += v;
+    }
+  lo += __shfl_xor_sync(0xffffffffu, lo, 1);
+  lo += __shfl_xor_sync(0xffffffffu, lo, 2);
+  hi += __shfl_xor_sync(0xffffffffu, hi, 1);
+  hi += __shfl_xor_sync(0xffffffffu, hi, 2);
+  y_lo = lo + b3;
+  y_hi = hi + b3;
+}
+
+// sum over the 8 row groups of a warp (lanes with equal t)
+__device__ __forceinline__ float sum_rows(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  return v;
+}
+
+}  // namespace
+
+// Loss and gradient of sum_i w_i (f(x_i) - y_i)^2 / wsum over samples
+// [0, n); gradients are added into grad (FP32, zeroed by the caller) and the
+// loss into *loss.
+__global__ void __launch_bounds__(kThreads) k_mlp_grad(const float *__restrict__ p, int n_in,
+                                                       const float *__restrict__ X,
+                                                       const float *__restrict__ Y,
+                                                       const float *__restrict__ Wt, int64_t n,
+                                                       int64_t first, float inv_wsum,
+                                                       float *__restrict__ grad,
+                                                       double *__restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  Smem &s = *reinterpret_cast<Smem *>(raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * warp;
+  load_weights(s, p, n_in);
+  const float b3 = p[param_count(n_in) - 1];
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) { s.gW3[i] = 0.f; s.gb2[i] = 0.f; s.gb1[i] = 0.f; }
+  if (threadIdx.x == 0) { s.gb3 = 0.f; s.loss = 0.f; }
+  float acc2[8][4], acc1[2][4];   // this warp's rows of dL/dW2 and dL/dW1
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+  acc1[0][0] = acc1[0][1] = acc1[0][2] = acc1[0][3] = 0.f;
+  acc1[1][0] = acc1[1][1] = acc1[1][2] = acc1[1][3] = 0.f;
+  __syncthreads();
+
+  const float *Xs = X + first * n_in;
+  const float *Ys = Y + first;
+  const float *Ws = Wt + first;
+  for (int64_t base = (int64_t)blockIdx.x * kS; base < n; base += (int64_t)gridDim.x * kS) {
+    load_tile(s, Xs, Ys, Ws, n, n_in, base);
+    __syncthreads();
+    float z2[8][4], y_lo, y_hi;
+    forward_rows(s, r0, z2, y_lo, y_hi, b3);
+    // dL/df per row, the loss, and dL/dz2
+    const int ra = r0 + g, rb = r0 + g + 8;
+    const float ea = y_lo - s.y[ra], eb = y_hi - s.y[rb];
+    const float da = 2.f * s.w[ra] * ea * inv_wsum, db = 2.f * s.w[rb] * eb * inv_wsum;
+    if (t == 0) atomicAdd(&s.loss, (s.w[ra] * ea * ea + s.w[rb] * eb * eb) * inv_wsum);
+    float gb3 = (t == 0) ? (da + db) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float gw3[2] = {0.f, 0.f}, gb2[2] = {0.f, 0.f};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = 8 * j + 2 * t + (e & 1);
+        const int row = (e < 2) ? ra : rb;
+        const float dy = (e < 2) ? da : db;
+        const float z = z2[j][e];
+        gw3[e & 1] += dy * silu(z);
+        const float d2 = dy * s.W3[col] * dsilu(z);
+        gb2[e & 1] += d2;
+        const __nv_bfloat16 b = __float2bfloat16(d2);
+        s.D2[row][col] = b;
+        s.D2T[col][row] = b;
+      }
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const float a = sum_rows(gw3[c2]), b = sum_rows(gb2[c2]);
+        if (g == 0) {
+          atomicAdd(&s.gW3[8 * j + 2 * t + c2], a);
+          atomicAdd(&s.gb2[8 * j + 2 * t + c2], b);
+        }
+      }
+    }
+    gb3 = sum_rows(gb3);
+    if (lane == 0) atomicAdd(&s.gb3, gb3);
+    __syncwarp();
+    // dL/dh1 = dL/dz2 * W2 (this warp's rows), then dL/dz1
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma16816(c, &s.D2[r0][16 * kk], kH, &s.W2T[8 * j][16 * kk], kH);
+      float gb1[2] = {0.f, 0.f};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = (e < 2) ? ra : rb, col = 8 * j + 2 * t + (e & 1);
+        const float d1 = c[e] * dsilu(s.Z1[row][col]);
+        gb1[e & 1] += d1;
+        s.D1T[col][row] = __float2bfloat16(d1);
+      }
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) {
+        const float a = sum_rows(gb1[c2]);
+        if (g == 0) atomicAdd(&s.gb1[8 * j + 2 * t + c2], a);
+      }
+    }
+    __syncthreads();
+    // weight gradients over the whole tile: this warp owns output rows
+    // [16 warp, 16 warp + 16) of dW2 = D2^T H1 and dW1 = D1^T X
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma16816(acc2[j], &s.D2T[r0][16 * kk], kS, &s.H1T[8 * j][16 * kk], kS);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma16816(acc1[j], &s.D1T[r0][16 * kk], kS, &s.XT[8 * j][16 * kk], kS);
+    __syncthreads();
+  }
+
+  // flush: this CTA's gradient into the global sum
+  float *gW1 = grad, *gb1 = gW1 + kH * n_in, *gW2 = gb1 + kH, *gb2 = gW2 + kH * kH;
+  float *gW3 = gb2 + kH, *gb3 = gW3 + kH;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
+      atomicAdd(&gW2[row * kH + col], acc2[j][e]);
+    }
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
+      if (col < n_in) atomicAdd(&gW1[row * n_in + col], acc1[j][e]);
+    }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    atomicAdd(&gW3[i], s.gW3[i]);
+    atomicAdd(&gb2[i], s.gb2[i]);
+    atomicAdd(&gb1[i], s.gb1[i]);
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(gb3, s.gb3);
+    atomicAdd(loss, (double)s.loss);
+  }
+}
+
+// Prediction for samples [0, n).
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(const float *__restrict__ p, int n_in,
+                                                          const float *__restrict__ X, int64_t n,
+                                                          float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  Smem &s = *reinterpret_cast<Smem *>(raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * warp;
+  load_weights(s, p, n_in);
+  const float b3 = p[param_count(n_in) - 1];
+  __syncthreads();
+  for (int64_t base = (int64_t)blockIdx.x * kS; base < n; base += (int64_t)gridDim.x * kS) {
+    load_tile(s, X, nullptr, nullptr, n, n_in, base);
+    __syncthreads();
+    float z2[8][4], y_lo, y_hi;
+    forward_rows(s, r0, z2, y_lo, y_hi, b3);
+    if (t == 0) {
+      const int64_t a = base + r0 + g, b = a + 8;
+      if (a < n) out[a] = y_lo;
+      if (b < n) out[b] = y_hi;
+    }
+    __syncthreads();
+  }
+}
+
+// Adam (Kingma & Ba): FP32 master weights and moments.
+__global__ void k_adam(int64_t np, float *__restrict__ p, float *__restrict__ m,
+                       float *__restrict__ v, const float *__restrict__ g, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// ---- host side -------------------------------------------------------------
+
+size_t mlp_smem_bytes() { return sizeof(Smem); }
+
+cudaError_t mlp_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(Smem));
+}
+
+cudaError_t launch_mlp_grad(cudaStream_t st, int sms, const float *p, int n_in, const float *X,
+                            const float *Y, const float *W, int64_t n, int64_t first,
+                            float inv_wsum, float *grad, double *loss) {
+  const int64_t tiles = (n + kS - 1) / kS;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 2));
+  k_mlp_grad<<<grid, kThreads, sizeof(Smem), st>>>(p, n_in, X, Y, W, n, first, inv_wsum, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(cudaStream_t st, int sms, const float *p, int n_in, const float *X,
+                               int64_t n, float *out) {
+  const int64_t tiles = (n + kS - 1) / kS;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 4));
+  k_mlp_forward<<<grid, kThreads, sizeof(Smem), st>>>(p, n_in, X, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(cudaStream_t st, int64_t np, float *p, float *m, float *v, const float *g,
+                        float lr, int64_t t) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  k_adam<<<(int)((np + 255) / 256), 256, 0, st>>>(np, p, m, v, g, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError();
+}
+
+int64_t mlp_param_count(int n_in) { return param_count(n_in); }
+
+// ---- training data from a pilot tally --------------------------------------
+
+// Sample s holds tally bin perm(s) = (s * stride) mod n_bins (stride coprime
+// with n_bins), so consecutive minibatches mix the whole mesh.  Features:
+// cell centre and bin-centre time scaled to [-1, 1], then the group one-hot.
+// Target: log of the pilot mean; weight 1 / (1 + relerr^2), 0 where the pilot
+// never scored.
+__global__ void k_make_samples(const DevProblem P, int n_in, uint64_t stride,
+                               const double *__restrict__ mean, const double *__restrict__ rel,
+                               float *__restrict__ X, float *__restrict__ Y,
+                               float *__restrict__ W, double *__restrict__ moments) {
+  double sw = 0.0, swt = 0.0, swt2 = 0.0;
+  const int64_t nb = P.n_bins;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nb;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = (int64_t)(((unsigned __int128)s * stride) % (unsigned __int128)nb);
+    const int tb = (int)(b % P.T1);
+    const int g = (int)((b / P.T1) % P.G);
+    const int64_t cell = b / ((int64_t)P.T1 * P.G);
+    const int ci = (int)(cell % P.n[0]);
+    const int cj = (int)((cell / P.n[0]) % P.n[1]);
+    const int ck = (int)(cell / ((int64_t)P.n[0] * P.n[1]));
+    float *x = X + s * n_in;
+    const int idx[3] = {ci, cj, ck};
+    for (int a = 0; a < 3; ++a)
+      x[a] = P.bounded[a] ? (float)(2.0 * (idx[a] + 0.5) / P.n[a] - 1.0) : 0.0f;
+    x[3] = P.T > 0 ? (float)(2.0 * (tb + 0.5) / P.T - 1.0) : 0.0f;
+    for (int k = 4; k < n_in; ++k) x[k] = (k - 4 == g) ? 1.0f : 0.0f;
+    const double m = mean ? mean[b] : 0.0;
+    if (m > 0.0) {
+      const double r = rel ? rel[b] : 0.0;
+      const double w = 1.0 / (1.0 + r * r);
+      const double t = log(m);
+      Y[s] = (float)t;
+      W[s] = (float)w;
+      sw += w; swt += w * t; swt2 += w * t * t;
+    } else {
+      Y[s] = 0.0f;
+      W[s] = 0.0f;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    swt += __shfl_xor_sync(0xffffffffu, swt, o);
+    swt2 += __shfl_xor_sync(0xffffffffu, swt2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&moments[0], sw);
+    atomicAdd(&moments[1], swt);
+    atomicAdd(&moments[2], swt2);
+  }
+}
+
+// targets to zero mean and unit variance (weighted); moments[3..4] keep the
+// shift and scale for the bake
+__global__ void k_normalize_targets(int64_t n, float *__restrict__ Y, const float *__restrict__ W,
+                                    double *__restrict__ moments) {
+  const double sw = moments[0] > 0.0 ? moments[0] : 1.0;
+  const double mu = moments[1] / sw;
+  const double var = moments[2] / sw - mu * mu;
+  const double sd = var > 1e-12 ? sqrt(var) : 1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) { moments[3] = mu; moments[4] = sd; }
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    if (W[s] > 0.0f) Y[s] = (float)((Y[s] - mu) / sd);
+}
+
+__global__ void k_step_counter(int64_t *t) { *t += 1; }
+
+// Adam whose step count lives on the device (so a captured epoch can be
+// replayed): c1 = 1 - b1^t, c2 = 1 - b2^t.
+__global__ void k_adam_dev(int64_t np, float *__restrict__ p, float *__restrict__ m,
+                           float *__restrict__ v, const float *__restrict__ g, float lr,
+                           const int64_t *__restrict__ t) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)*t), c2 = 1.f - powf(b2, (float)*t);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+  }
+}
+
+// largest prediction (denormalised log flux) over bins, as ordered bits of a
+// non-negative offset: predictions are shifted by +1e4 so they stay positive
+__global__ void k_pred_max(int64_t n, const float *__restrict__ pred,
+                           const double *__restrict__ moments, unsigned long long *__restrict__ mx) {
+  double best = -1e300;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    best = fmax(best, (double)pred[s] * moments[4] + moments[3]);
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best > -1e300) {
+    const double shifted = fmax(0.0, best + 1e4);
+    atomicMax(mx, (unsigned long long)__double_as_longlong(shifted));
+  }
+}
+
+// smallest prediction over the bins the pilot scored (same ordered-bits trick)
+__global__ void k_pred_min_scored(int64_t n, const float *__restrict__ pred,
+                                  const float *__restrict__ W, const double *__restrict__ moments,
+                                  unsigned long long *__restrict__ mn) {
+  double best = 1e300;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    if (W[s] > 0.0f) best = fmin(best, (double)pred[s] * moments[4] + moments[3]);
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best < 1e300) {
+    const double shifted = fmax(0.0, best + 1e4);
+    atomicMin(mn, (unsigned long long)__double_as_longlong(shifted));
+  }
+}
+
+// weight-window lower bounds: w_L = wl0 * exp(log phi - max log phi), but no
+// lower than a tenth of the least-scored bin's value and no lower than
+// min_ratio: where the pilot never scored, the network extrapolates, and a
+// window far below the true flux would split every arriving particle again
+// and again
+__global__ void k_ww_from_pred(const DevProblem P, uint64_t stride, const float *__restrict__ pred,
+                               const double *__restrict__ moments,
+                               const unsigned long long *__restrict__ mx,
+                               const unsigned long long *__restrict__ mn, double wl0,
+                               double min_ratio, double *__restrict__ ww64,
+                               float *__restrict__ ww32) {
+  const double top = __longlong_as_double((long long)*mx) - 1e4;
+  const double low = __longlong_as_double((long long)*mn) - 1e4;
+  const double floor_lp = fmax(low - 2.302585092994046, top + log(min_ratio));
+  const int64_t nb = P.n_bins;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nb;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = (int64_t)(((unsigned __int128)s * stride) % (unsigned __int128)nb);
+    const double lp = fmax((double)pred[s] * moments[4] + moments[3], floor_lp);
+    const double w = wl0 * exp(fmin(0.0, lp - top));
+    ww64[b] = w;
+    ww32[b] = (float)w;
+  }
+}
+
+namespace {
+uint64_t gcd64(uint64_t a, uint64_t b) {
+  while (b) { const uint64_t r = a % b; a = b; b = r; }
+  return a;
+}
+// a stride near n * 0.618 that is coprime with n
+uint64_t coprime_stride(uint64_t n) {
+  if (n <= 2) return 1;
+  uint64_t s = (uint64_t)((double)n * 0.6180339887498949) | 1ull;
+  while (gcd64(s, n) != 1) s += 2;
+  return s % n ? s % n : 1;
+}
+}  // namespace
+
+}  // namespace mcdc
+
+// ---- C-ABI -----------------------------------------------------------------
+using namespace mcdc;
+
+namespace {
+int fail(int code, const std::string &m) { return mcdc::set_error(code, m); }
+
+bool on_dev(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device copy of a host-or-device array (owned by the caller through *keep)
+template <class T>
+cudaError_t as_device(const T *p, size_t count, const T **out, void **keep) {
+  *keep = nullptr;
+  if (on_dev(p)) { *out = p; return cudaSuccess; }
+  void *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, std::max<size_t>(count * sizeof(T), 16));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(d, p, count * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(d); return e; }
+  *keep = d;
+  *out = (const T *)d;
+  return cudaSuccess;
+}
+
+struct Frees {
+  std::vector<void *> v;
+  ~Frees() { for (void *p : v) if (p) cudaFree(p); }
+  void *add(void *p) { v.push_back(p); return p; }
+};
+
+int device_sms() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+#define CKM(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? MCDC_ERR_OOM : MCDC_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+}  // namespace
+
+extern "C" int64_t mcdc_mlp_param_count(int32_t n_in) {
+  if (n_in < 1 || n_in > kIn) return -1;
+  return mlp_param_count(n_in);
+}
+
+extern "C" int mcdc_mlp_forward(const float *params, int32_t n_in, const float *X, int64_t n,
+                                float *out) {
+  if (n_in < 1 || n_in > kIn) return fail(MCDC_ERR_INVALID, "n_in must be in 1..16");
+  if (n < 0 || !params || !X || !out) return fail(MCDC_ERR_INVALID, "bad arguments");
+  if (n == 0) return MCDC_OK;
+  Frees fr;
+  const float *dp, *dx;
+  void *k1, *k2;
+  CKM(as_device(params, (size_t)mlp_param_count(n_in), &dp, &k1)); fr.add(k1);
+  CKM(as_device(X, (size_t)n * n_in, &dx, &k2)); fr.add(k2);
+  float *dout = out;
+  if (!on_dev(out)) { CKM(cudaMalloc(&dout, n * sizeof(float))); fr.add(dout); }
+  CKM(mlp_prepare());
+  CKM(launch_mlp_forward(nullptr, device_sms(), dp, n_in, dx, n, dout));
+  if (dout != out) CKM(cudaMemcpy(out, dout, n * sizeof(float), cudaMemcpyDeviceToHost));
+  CKM(cudaDeviceSynchronize());
+  return MCDC_OK;
+}
+
+extern "C" int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float *X,
+                                  const float *y, const float *w, int64_t n, float *grad,
+                                  double *loss) {
+  if (n_in < 1 || n_in > kIn) return fail(MCDC_ERR_INVALID, "n_in must be in 1..16");
+  if (n <= 0 || !params || !X || !y || !w || !grad) return fail(MCDC_ERR_INVALID, "bad arguments");
+  const int64_t np = mlp_param_count(n_in);
+  Frees fr;
+  const float *dp, *dx, *dy, *dw;
+  void *k;
+  CKM(as_device(params, (size_t)np, &dp, &k)); fr.add(k);
+  CKM(as_device(X, (size_t)n * n_in, &dx, &k)); fr.add(k);
+  CKM(as_device(y, (size_t)n, &dy, &k)); fr.add(k);
+  CKM(as_device(w, (size_t)n, &dw, &k)); fr.add(k);
+  std::vector<float> hw(n);
+  CKM(cudaMemcpy(hw.data(), dw, n * sizeof(float), on_dev(w) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  double wsum = 0.0;
+  for (float v : hw) wsum += v;
+  if (!(wsum > 0.0)) return fail(MCDC_ERR_INVALID, "sample weights sum to zero");
+  float *dg = nullptr;
+  double *dl = nullptr;
+  CKM(cudaMalloc(&dg, np * sizeof(float))); fr.add(dg);
+  CKM(cudaMalloc(&dl, sizeof(double))); fr.add(dl);
+  CKM(cudaMemset(dg, 0, np * sizeof(float)));
+  CKM(cudaMemset(dl, 0, sizeof(double)));
+  CKM(mlp_prepare());
+  CKM(launch_mlp_grad(nullptr, device_sms(), dp, n_in, dx, dy, dw, n, 0, (float)(1.0 / wsum), dg, dl));
+  CKM(cudaMemcpy(grad, dg, np * sizeof(float), on_dev(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  double lh = 0.0;
+  CKM(cudaMemcpy(&lh, dl, sizeof(double), cudaMemcpyDeviceToHost));
+  if (loss) *loss = lh;
+  return MCDC_OK;
+}
+
+extern "C" void mcdc_default_mlp_options(mcdc_mlp_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->epochs = 40;
+  o->batch = 65536;
+  o->lr = 2e-3;
+  o->seed = 1;
+  o->source_wl = 0.5;
+  o->upper_ratio = 5.0;
+  o->survival_ratio = 2.5;
+  o->nmax = 16;
+  o->min_ratio = 1e-8;
+}
+
+extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilot_mean,
+                                     const double *pilot_relerr, const mcdc_mlp_options *opt,
+                                     mcdc_mlp_report *rep) {
+  if (!pr || !pilot_mean) return fail(MCDC_ERR_INVALID, "problem and pilot tally are required");
+  mcdc_mlp_options o;
+  if (opt) o = *opt; else mcdc_default_mlp_options(&o);
+  if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0))
+    return fail(MCDC_ERR_INVALID, "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0");
+  const DevProblem &P = pr->P;
+  const int n_in = 4 + P.G;
+  if (n_in > kIn) return fail(MCDC_ERR_INVALID, "the importance network takes at most 12 groups");
+  CKM(cudaSetDevice(pr->device));
+  const int64_t nb = P.n_bins, np = mlp_param_count(n_in);
+  Frees fr;
+  const double *dmean, *drel = nullptr;
+  void *k;
+  CKM(as_device(pilot_mean, (size_t)nb, &dmean, &k)); fr.add(k);
+  if (pilot_relerr) { CKM(as_device(pilot_relerr, (size_t)nb, &drel, &k)); fr.add(k); }
+  float *X, *Y, *W, *pred, *prm, *m, *v, *g;
+  double *mom, *losses;
+  int64_t *tstep;
+  unsigned long long *mx;
+  CKM(cudaMalloc(&X, sizeof(float) * nb * n_in)); fr.add(X);
+  CKM(cudaMalloc(&Y, sizeof(float) * nb)); fr.add(Y);
+  CKM(cudaMalloc(&W, sizeof(float) * nb)); fr.add(W);
+  CKM(cudaMalloc(&pred, sizeof(float) * nb)); fr.add(pred);
+  CKM(cudaMalloc(&prm, sizeof(float) * np)); fr.add(prm);
+  CKM(cudaMalloc(&m, sizeof(float) * np)); fr.add(m);
+  CKM(cudaMalloc(&v, sizeof(float) * np)); fr.add(v);
+  CKM(cudaMalloc(&g, sizeof(float) * np)); fr.add(g);
+  CKM(cudaMalloc(&mom, sizeof(double) * 8)); fr.add(mom);
+  CKM(cudaMalloc(&tstep, sizeof(int64_t))); fr.add(tstep);
+  CKM(cudaMalloc(&mx, 2 * sizeof(unsigned long long))); fr.add(mx);
+  const int64_t steps_per_epoch = (nb + o.batch - 1) / o.batch;
+  CKM(cudaMalloc(&losses, sizeof(double) * steps_per_epoch * 2)); fr.add(losses);
+
+  // parameters: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
+  std::vector<float> h(np, 0.0f);
+  {
+    uint64_t st = o.seed * 0x9E3779B97F4A7C15ull + 12345;
+    auto unif = [&]() {   // splitmix64 -> (0, 1)
+      st += 0x9E3779B97F4A7C15ull;
+      uint64_t z = st;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return ((z >> 11) + 0.5) * 0x1.0p-53;
+    };
+    const float a1 = 1.0f / std::sqrt((float)n_in), a2 = 1.0f / std::sqrt((float)kH);
+    int64_t off = 0;
+    for (int64_t i = 0; i < (int64_t)kH * n_in; ++i) h[off + i] = (float)((2 * unif() - 1) * a1);
+    off += (int64_t)kH * n_in + kH;
+    for (int64_t i = 0; i < (int64_t)kH * kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
+    off += (int64_t)kH * kH + kH;
+    for (int64_t i = 0; i < kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
+  }
+  cudaEvent_t e0, e1, e2;
+  CKM(cudaEventCreate(&e0)); CKM(cudaEventCreate(&e1)); CKM(cudaEventCreate(&e2));
+  cudaStream_t st;
+  CKM(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  struct Cleanup {
+    cudaStream_t s; cudaEvent_t a, b, c; cudaGraph_t gr = nullptr; cudaGraphExec_t ex = nullptr;
+    ~Cleanup() {
+      if (ex) cudaGraphExecDestroy(ex);
+      if (gr) cudaGraphDestroy(gr);
+      cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c);
+      cudaStreamDestroy(s);
+    }
+  } cl{st, e0, e1, e2};
+  const int sms = pr->sms;
+  const uint64_t stride = coprime_stride((uint64_t)nb);
+  CKM(mlp_prepare());
+  CKM(cudaEventRecord(e0, st));
+  CKM(cudaMemcpyAsync(prm, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice, st));
+  CKM(cudaMemsetAsync(m, 0, sizeof(float) * np, st));
+  CKM(cudaMemsetAsync(v, 0, sizeof(float) * np, st));
+  CKM(cudaMemsetAsync(mom, 0, sizeof(double) * 8, st));
+  CKM(cudaMemsetAsync(tstep, 0, sizeof(int64_t), st));
+  CKM(cudaMemsetAsync(losses, 0, sizeof(double) * steps_per_epoch * 2, st));
+  const int blocks = sms * 8;
+  k_make_samples<<<blocks, 256, 0, st>>>(P, n_in, stride, dmean, drel, X, Y, W, mom);
+  CKM(cudaGetLastError());
+  k_normalize_targets<<<blocks, 256, 0, st>>>(nb, Y, W, mom);
+  CKM(cudaGetLastError());
+  double hmom[8];
+  CKM(cudaMemcpyAsync(hmom, mom, sizeof(hmom), cudaMemcpyDeviceToHost, st));
+  CKM(cudaStreamSynchronize(st));
+  if (!(hmom[0] > 0.0)) return fail(MCDC_ERR_INVALID, "the pilot tally scored no bin");
+  // per-minibatch weight sums (host side, from the device weights)
+  std::vector<float> hw(nb);
+  CKM(cudaMemcpy(hw.data(), W, sizeof(float) * nb, cudaMemcpyDeviceToHost));
+  std::vector<float> inv(steps_per_epoch, 0.0f);
+  int64_t n_samples = 0;
+  for (int64_t b = 0; b < steps_per_epoch; ++b) {
+    double ws = 0.0;
+    for (int64_t i = b * o.batch; i < std::min<int64_t>(nb, (b + 1) * o.batch); ++i) {
+      ws += hw[i];
+      n_samples += hw[i] > 0.0f;
+    }
+    inv[b] = ws > 0.0 ? (float)(1.0 / ws) : 0.0f;
+  }
+  // one epoch as a CUDA graph: per minibatch zero the gradient, forward and
+  // backward on the tensor cores, count the step, Adam
+  CKM(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  for (int64_t b = 0; b < steps_per_epoch; ++b) {
+    if (inv[b] == 0.0f) continue;
+    const int64_t first = b * o.batch, cnt = std::min<int64_t>(o.batch, nb - first);
+    cudaMemsetAsync(g, 0, sizeof(float) * np, st);
+    launch_mlp_grad(st, sms, prm, n_in, X, Y, W, cnt, first, inv[b], g, losses + b);
+    k_step_counter<<<1, 1, 0, st>>>(tstep);
+    k_adam_dev<<<(int)((np + 255) / 256), 256, 0, st>>>(np, prm, m, v, g, (float)o.lr, tstep);
+  }
+  CKM(cudaStreamEndCapture(st, &cl.gr));
+  CKM(cudaGraphInstantiate(&cl.ex, cl.gr, 0));
+  double loss_first = 0.0, loss_last = 0.0;
+  std::vector<double> hl(steps_per_epoch);
+  int32_t steps = 0;
+  for (int ep = 0; ep < o.epochs; ++ep) {
+    CKM(cudaMemsetAsync(losses, 0, sizeof(double) * steps_per_epoch, st));
+    CKM(cudaGraphLaunch(cl.ex, st));
+    if (ep == 0 || ep == o.epochs - 1) {
+      CKM(cudaMemcpyAsync(hl.data(), losses, sizeof(double) * steps_per_epoch, cudaMemcpyDeviceToHost, st));
+      CKM(cudaStreamSynchronize(st));
+      double s = 0.0, c = 0.0;
+      for (int64_t b = 0; b < steps_per_epoch; ++b)
+        if (inv[b] != 0.0f) { s += hl[b]; c += 1.0; }
+      (ep == 0 ? loss_first : loss_last) = c > 0 ? s / c : 0.0;
+    }
+    for (int64_t b = 0; b < steps_per_epoch; ++b) steps += inv[b] != 0.0f;
+  }
+  CKM(cudaEventRecord(e1, st));
+  // bake: predict every bin, weight windows proportional to the predicted flux
+  CKM(launch_mlp_forward(st, sms, prm, n_in, X, nb, pred));
+  CKM(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), st));
+  CKM(cudaMemsetAsync(mx + 1, 0xff, sizeof(unsigned long long), st));
+  k_pred_max<<<blocks, 256, 0, st>>>(nb, pred, mom, mx);
+  CKM(cudaGetLastError());
+  k_pred_min_scored<<<blocks, 256, 0, st>>>(nb, pred, W, mom, mx + 1);
+  CKM(cudaGetLastError());
+  if (!pr->ww64) {
+    void *a, *b;
+    CKM(cudaMalloc(&a, sizeof(double) * nb));
+    pr->allocs.push_back(a);
+    CKM(cudaMalloc(&b, sizeof(float) * nb));
+    pr->allocs.push_back(b);
+    pr->ww64 = (double *)a;
+    pr->ww32 = (float *)b;
+  }
+  k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
+                                         o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64, pr->ww32);
+  CKM(cudaGetLastError());
+  CKM(cudaEventRecord(e2, st));
+  CKM(cudaStreamSynchronize(st));
+  // switch the problem to weight windows (w_U, w_S ratios as given)
+  pr->P.ww_lower = pr->ww64;
+  pr->P.ww_lower32 = pr->ww32;
+  pr->P.ww_upper = o.upper_ratio;
+  pr->P.ww_survival = o.survival_ratio;
+  pr->P.ww_nmax = o.nmax;
+  if (int rc = mcdc::ensure_overflow_for(pr)) return rc;
+  if (rep) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    rep->samples = n_samples;
+    rep->loss_first = loss_first;
+    rep->loss_last = loss_last;
+    rep->train_ms = a;
+    rep->bake_ms = b;
+    rep->steps = steps;
+    rep->target_mean = hmom[1] / hmom[0];
+  }
+  return MCDC_OK;
+}

@@ -91,6 +91,18 @@ class mcdc_run_args(C.Structure):
                 ("records", C.c_void_p), ("n_records", C.c_uint64), ("stream", C.c_void_p)]
 
 
+class mcdc_mlp_options(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("seed", C.c_uint64), ("source_wl", C.c_double), ("upper_ratio", C.c_double),
+                ("survival_ratio", C.c_double), ("nmax", C.c_int32), ("min_ratio", C.c_double)]
+
+
+class mcdc_mlp_report(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("train_ms", C.c_double), ("bake_ms", C.c_double), ("steps", C.c_int32),
+                ("target_mean", C.c_double)]
+
+
 # name -> (restype, argtypes); kept in the order of include/mcdc.h
 SIGNATURES = {
     "mcdc_default_options": (None, [C.POINTER(mcdc_options)]),
@@ -103,6 +115,13 @@ SIGNATURES = {
                                           C.c_int32]),
     "mcdc_tally_size": (C.c_int64, [C.c_void_p]),
     "mcdc_problem_destroy": (None, [C.c_void_p]),
+    "mcdc_default_mlp_options": (None, [C.POINTER(mcdc_mlp_options)]),
+    "mcdc_train_importance": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.POINTER(mcdc_mlp_options), C.POINTER(mcdc_mlp_report)]),
+    "mcdc_mlp_param_count": (C.c_int64, [C.c_int32]),
+    "mcdc_mlp_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mcdc_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
@@ -130,6 +149,11 @@ mcdc_set_weight_windows = _lib.mcdc_set_weight_windows
 mcdc_tally_size = _lib.mcdc_tally_size
 mcdc_problem_destroy = _lib.mcdc_problem_destroy
 mcdc_run_noalloc = _lib.mcdc_run_noalloc
+mcdc_default_mlp_options = _lib.mcdc_default_mlp_options
+mcdc_train_importance = _lib.mcdc_train_importance
+mcdc_mlp_param_count = _lib.mcdc_mlp_param_count
+mcdc_mlp_forward = _lib.mcdc_mlp_forward
+mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -253,6 +277,21 @@ class Problem:
         check(mcdc_run_noalloc(self.handle, int(n), int(seed), int(offset), int(batches),
                                _ptr(sum1), _ptr(sum2), _ptr(mean), _ptr(relerr), stream))
 
+    def train_importance(self, pilot_mean, pilot_relerr=None, **opts):
+        """Fits the importance network to a pilot tally and switches this
+        problem to the weight windows it predicts; returns the report."""
+        o = mcdc_mlp_options()
+        mcdc_default_mlp_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        mean = np.ascontiguousarray(pilot_mean, dtype=np.float64) if isinstance(
+            pilot_mean, np.ndarray) else pilot_mean
+        rel = np.ascontiguousarray(pilot_relerr, dtype=np.float64) if isinstance(
+            pilot_relerr, np.ndarray) else pilot_relerr
+        r = mcdc_mlp_report()
+        check(mcdc_train_importance(self.handle, _ptr(mean), _ptr(rel), C.byref(o), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in mcdc_mlp_report._fields_}
+
     def run(self, n, seed, tally_out=None):
         check(mcdc_run(self.handle, int(n), int(seed), _ptr(tally_out)))
 
@@ -287,3 +326,25 @@ def run_numpy(prob, n, seed, offset=0, batches=0, records=0, **opts):
         shp = P.shape
     return {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "sum1": s1.reshape(shp),
             "sum2": s2.reshape(shp), "scalar": scal, "counts": stats, "records": rec}
+
+
+def mlp_forward(params, X):
+    """Network prediction on the GPU (FP32 host arrays in and out)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    out = np.zeros(X.shape[0], dtype=np.float32)
+    check(mcdc_mlp_forward(_ptr(p), X.shape[1], _ptr(X), X.shape[0], _ptr(out)))
+    return out
+
+
+def mlp_loss_grad(params, X, y, w):
+    """Weighted least-squares loss and gradient computed by the GPU kernels."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    g = np.zeros(p.size, dtype=np.float32)
+    loss = C.c_double()
+    check(mcdc_mlp_loss_grad(_ptr(p), X.shape[1], _ptr(X), _ptr(y), _ptr(w), X.shape[0], _ptr(g),
+                             C.byref(loss)))
+    return loss.value, g
