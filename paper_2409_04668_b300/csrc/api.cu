@@ -94,6 +94,7 @@ void release(mcdc_problem *pr) {
   if (pr->ev2) cudaEventDestroy(pr->ev2);
   if (pr->h_stats) cudaFreeHost(pr->h_stats);
   if (pr->h_error) cudaFreeHost(pr->h_error);
+  if (pr->h_spill) cudaFreeHost(pr->h_spill);
   delete pr;
 }
 
@@ -212,7 +213,31 @@ int ensure_work_slots(mcdc_problem *pr, int n) {
 int ensure_overflow(mcdc_problem *pr) {
   if (pr->P.ww_lower == nullptr) return MCDC_OK;
   const int warps = pr->block / 32;
-  const int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
+  int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
+  if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
+    // a small stack per warp; the rest spills to the device-wide banks so
+    // one large family of split children is shared by every warp
+    cap = std::min(cap, 256);
+    if (!pr->spill[0]) {
+      const unsigned long long scap = 1ull << 26;   // particles per bank (4.3 GB in FP32)
+      const size_t pb = pr->key.f64 ? sizeof(Part<double>)
+                        : (pr->key.local ? sizeof(Part<float, float>) : sizeof(Part<float>));
+      unsigned char *a = nullptr, *b = nullptr;
+      unsigned long long *c = nullptr;
+      int rc;
+      if ((rc = dalloc(pr, &a, scap * pb))) return rc;
+      if ((rc = dalloc(pr, &b, scap * pb))) return rc;
+      if ((rc = dalloc(pr, &c, 4))) return rc;
+      if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCDC_ERR_OOM, "pinned buffer");
+      }
+      pr->spill[0] = a;
+      pr->spill[1] = b;
+      pr->spill_cnt = c;
+      pr->spill_cap = scap;
+    }
+  }
   const size_t part_b = pr->key.f64 ? sizeof(Part<double>)
                        : (pr->key.local ? sizeof(Part<float, float>) : sizeof(Part<float>));
   const size_t need = (size_t)pr->grid * warps * cap * part_b;
@@ -591,12 +616,38 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     A.chunk = 0;
     CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
   } else {
+    const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
     for (int b = 0; b < B; ++b) {
       A.work = pr->work + b;
       A.batch = b;
       const uint64_t nb_hist = a->n_histories / B + 1;
       A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));
+      A.spill_in = nullptr;
+      A.spill_out = nullptr;
+      if (spill) {
+        CK(cudaMemsetAsync(pr->spill_cnt, 0, 4 * sizeof(unsigned long long), s));
+        A.spill_out = pr->spill[0];
+        A.spill_out_count = pr->spill_cnt + 0;
+        A.spill_cap = pr->spill_cap;
+      }
       CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+      // passes over the spilled children, ping-ponging between the banks,
+      // until a pass spills nothing
+      for (int pass = 1; spill && pass < 100000; ++pass) {
+        const int in = (pass - 1) & 1, out = pass & 1;
+        CK(cudaMemcpyAsync(pr->h_spill, pr->spill_cnt + in, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*pr->h_spill == 0) break;
+        CK(cudaMemsetAsync(pr->spill_cnt + out, 0, sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(pr->spill_cnt + 2, 0, sizeof(unsigned long long), s));
+        A.spill_in = pr->spill[in];
+        A.spill_in_count = pr->spill_cnt + in;
+        A.spill_in_cursor = pr->spill_cnt + 2;
+        A.spill_out = pr->spill[out];
+        A.spill_out_count = pr->spill_cnt + out;
+        CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+      }
       CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
     }
   }
@@ -658,7 +709,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->warp_aggregate = pr->warp_aggregate;
   }
   if (*pr->h_error & ERRBIT_OVERFLOW)
-    return fail(MCDC_ERR_BANK_OVERFLOW, "split children overflowed the per-CTA stack; raise overflow_per_cta");
+    return fail(MCDC_ERR_BANK_OVERFLOW, "split children overflowed the warp stacks or the device-wide spill bank");
   if (*pr->h_error & ERRBIT_TIMEOUT) return fail(MCDC_ERR_TIMEOUT, "a bounded device wait gave up");
   return MCDC_OK;
 }

@@ -106,6 +106,14 @@ struct RunArgs {
   void *overflow;
   int32_t overflow_cap;       // per warp
   int32_t warp_aggregate;
+  // global-tally mode with weight windows: children beyond the warp's stack
+  // spill to a device-wide bank, run in a later pass by every warp
+  void *spill_out;            // bank written by this pass (nullptr: no spill)
+  unsigned long long *spill_out_count;
+  unsigned long long spill_cap;
+  const void *spill_in;       // bank this pass runs instead of new histories
+  const unsigned long long *spill_in_count;
+  unsigned long long *spill_in_cursor;
 };
 
 // ---- counter-based generator: Philox4x32-10 (Salmon et al., SC'11) -------

@@ -31,6 +31,10 @@ struct mcdc_problem {
   unsigned long long *work = nullptr;   // [max batches] work counters
   int work_slots = 0;
   void *overflow = nullptr;
+  void *spill[2] = {nullptr, nullptr};   // device-wide banks of spilled children
+  unsigned long long *spill_cnt = nullptr; // [4]: counts of both banks, input cursor
+  unsigned long long spill_cap = 0;
+  unsigned long long *h_spill = nullptr;   // pinned copy of a count
   size_t overflow_bytes = 0;
   mcdc::Record *rec_tmp = nullptr;
   uint64_t rec_cap = 0;

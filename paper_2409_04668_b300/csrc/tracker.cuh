@@ -267,8 +267,16 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
         ch.ctr = 0;
         ch.nseg = ch.ncol = ch.ncross = 0;
         const int slot = atomicAdd(s_novf, 1);
-        if (slot < A.overflow_cap) ovf[slot] = ch;
-        else atomicOr(A.error, ERRBIT_OVERFLOW);
+        if (slot < A.overflow_cap) {
+          ovf[slot] = ch;
+        } else if (A.spill_out != nullptr) {
+          atomicSub(s_novf, 1);   // not kept here: to the device-wide bank
+          const unsigned long long gs = atomicAdd(A.spill_out_count, 1ull);
+          if (gs < A.spill_cap) reinterpret_cast<PartOf<PR> *>(A.spill_out)[gs] = ch;
+          else atomicOr(A.error, ERRBIT_OVERFLOW);
+        } else {
+          atomicOr(A.error, ERRBIT_OVERFLOW);
+        }
       }
       p.w = wc;
       atomicAdd(&es.n_end[5], 1u);
@@ -766,7 +774,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
           unsigned long long first = 0;
           int got = 0;
           if (lane == 0) {
-            if (SHARED) {
+            if (A.spill_in != nullptr) {
+              const unsigned long long total = min(*A.spill_in_count, A.spill_cap);
+              first = atomicAdd(A.spill_in_cursor, (unsigned long long)want);
+              got = first < total ? (int)min((unsigned long long)want, total - first) : 0;
+            } else if (SHARED) {
               first = atomicAdd(&s_h_next, (unsigned long long)want);
               got = first < s_h_end ? (int)min((unsigned long long)want, s_h_end - first) : 0;
             } else {
@@ -788,6 +800,9 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
         if (lane < nb) {
           if (lane < n_o) {
             q = ovf[top - 1 - lane];
+            alive = true;
+          } else if (A.spill_in != nullptr) {
+            q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[h_first + (lane - n_o)];
             alive = true;
           } else {
             source_particle<PR, DIM>(P, tb, A.seed, A.offset + h_first + (lane - n_o), q);

@@ -133,6 +133,30 @@ def test_fp64_weight_windows_infinite_medium(mcdc):
     assert stats["splits"] > 100 and stats["roulette_killed"] > 100
 
 
+def test_fp64_weight_windows_global_tally_with_spill(mcdc):
+    """Global tally, 64-slot warp stacks and strong splitting: children spill
+    to the device-wide banks and run in later passes on other warps; each
+    keeps its own random stream, so the tallies still match the oracle."""
+    mat = np.zeros((2, 2, 4), np.uint8)
+    prob = W.box("inf_ww", (4, 2, 2), (0.5, 1.0, 1.0), mat, [[1.0]], [[0.9]], np.ones((1, 1, 1)),
+                 [1.0], (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), None, (0, 0, 0), (4, 2, 2),
+                 bc=(W.BC_REFLECT,) * 6)
+    lower = np.random.default_rng(9).uniform(0.002, 0.05, size=prob.n_bins)
+    N, B = 4000, 4
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP64, tally_mode=mcdc.TALLY_GLOBAL,
+                      overflow_per_cta=512) as P:
+        P.set_weight_windows(lower, 5.0, 2.5, 16)
+        s1, s2, mean, rel = (np.zeros(P.n_bins) for _ in range(4))
+        stats, scal = P.run_ex(N, 21, batches=B, sum1=s1, sum2=s2, mean=mean, relerr=rel)
+    o = O.run(prob, N, seed=21, batches=B,
+              ww={"lower": lower, "upper_ratio": 5.0, "survival_ratio": 2.5, "nmax": 16})
+    g = {"sum1": s1.reshape(prob.tally_shape), "sum2": s2.reshape(prob.tally_shape),
+         "mean": mean.reshape(prob.tally_shape), "relerr": rel.reshape(prob.tally_shape)}
+    compare_tallies(g, o)
+    compare_counts(stats, o["counts"])
+    assert stats["children"] > 64 * 8 * 148 * 2, stats["children"]   # more than the warp stacks hold
+
+
 def _coarse(mean):
     """20 x 10 blocks of (space, time) bins of the two-region slab."""
     return mean[0, 0, :, 0, :].reshape(20, 10, 10, 5).sum(axis=(1, 3))
