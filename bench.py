@@ -154,6 +154,7 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
     args = ap.parse_args()
 
     make, n_default = WORKLOADS[args.workload]
@@ -271,6 +272,8 @@ def main():
     # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)
     line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"])
+    if rank == 0 and not args.no_fom and world == 1:
+        line["fom"] = fom_deep(M, prec)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         h, sg, dt = oracle_sample(prob, args.cpu_seconds, os.cpu_count() or 1, offset=10**12)
         line["cpu_baseline"] = {"value": h / dt, "unit": "histories/s", "cores": os.cpu_count(),
@@ -282,6 +285,55 @@ def main():
     P.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):
+    """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
+    deep-penetration box (30 mfp absorber between a corner source and the
+    region x in [90, 100]), analog against the learned weight windows.  The
+    analog run's tally is the pilot; the network is refit once on the tally of
+    a first weight-window run (each such tally is an unbiased flux estimate
+    that reaches deeper).  T is the device time of the measured run; the
+    training time is reported beside it."""
+    import torch
+    prob = W.c4_deep()
+    out = {"workload": prob.name, "region_cells": [list(prob.region_lo), list(prob.region_hi)]}
+    dev = torch.device("cuda")
+    with M.Problem(prob, precision=prec, overflow_per_cta=8192 * 4) as P:
+        mean = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
+        rel = torch.zeros_like(mean)
+        P.run_ex(1_000_000, 7, mean=mean, relerr=rel)            # warm-up
+        st, (m_a, r_a) = P.run_ex(n_analog, 7, mean=mean, relerr=rel)
+        t_a = st["kernel_ms"] / 1e3
+        out["analog"] = {"histories": n_analog, "mean": m_a, "relerr": r_a if m_a > 0 else None,
+                         "seconds": t_a, "histories_per_s": n_analog / t_a,
+                         "fom": (1.0 / (r_a ** 2 * t_a)) if m_a > 0 and r_a > 0 else None,
+                         "fom_upper_bound": None if m_a > 0 else 1.0 / t_a,
+                         "note": None if m_a > 0 else "no analog history scored in the region: "
+                                 "relerr >= 1, so FOM <= 1/T"}
+        train_ms, ww_ms = 0.0, 0.0
+        seed = 11
+        for it in range(refits + 1):
+            rep = P.train_importance(mean, rel, epochs=6, min_ratio=1e-20)
+            train_ms += rep["train_ms"] + rep["bake_ms"]
+            if it < refits:
+                st, _ = P.run_ex(n_ww, seed, batches=16, mean=mean, relerr=rel)
+                ww_ms += st["kernel_ms"]
+                seed += 1
+        st, (m_w, r_w) = P.run_ex(n_ww, seed, batches=16)
+        t_w = st["kernel_ms"] / 1e3
+        out["learned"] = {"histories": n_ww, "mean": m_w, "relerr": r_w, "seconds": t_w,
+                          "histories_per_s": n_ww / t_w,
+                          "fom": (1.0 / (r_w ** 2 * t_w)) if m_w > 0 and r_w > 0 else None,
+                          "splits": st["splits"], "segments_per_history": st["segments"] / n_ww,
+                          "training_seconds": train_ms / 1e3,
+                          "refit_runs_seconds": ww_ms / 1e3, "refits": refits}
+    a, l = out["analog"], out["learned"]
+    if l["fom"] and a["fom"]:
+        out["ratio"] = l["fom"] / a["fom"]
+    elif l["fom"] and a["fom_upper_bound"]:
+        out["ratio_lower_bound"] = l["fom"] / a["fom_upper_bound"]
+    return out
 
 
 def roofline(prob, seg_rate, pk, tally_mode):
