@@ -121,7 +121,10 @@ typedef struct mcdc_options {
     int32_t bank_per_cta;       /* ignored: each warp parks up to 96 particles    */
     int32_t ctas_per_sm;        /* resident CTAs per SM; 0: autotuned             */
     int32_t warp_aggregate;     /* -1 off, 1 on, 0 auto                           */
-    int32_t autotune;           /* 1: time candidate launch shapes at create      */
+    int32_t autotune;           /* 1 (default): when block_size is 0, time candidate
+                                   launch shapes (threads per CTA, whole batches per
+                                   CTA, warp aggregation) on this problem at create
+                                   and keep the fastest; cached per problem shape */
     int32_t overflow_per_cta;   /* split-children overflow slots per CTA (shared by
                                    its warps, >= 64 each); 0: 1024 per warp      */
     int32_t region_lo[3];       /* cell box [lo, hi) of the scalar tally used for */

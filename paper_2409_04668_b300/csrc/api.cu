@@ -191,7 +191,8 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
       // every CTA gets about two whole batches (a CTA drains between its
       // batches), each of at least a few thousand histories
       const uint64_t by_size = n / 4096;
-      B = (int)std::min<uint64_t>(std::max<uint64_t>(by_size, 32), (uint64_t)pr->grid * 2);
+      B = (int)std::min<uint64_t>(std::max<uint64_t>(by_size, 32),
+                                  (uint64_t)pr->grid * (uint64_t)pr->batch_per_cta);
     } else {
       B = 32;
     }
@@ -251,6 +252,81 @@ int ensure_overflow(mcdc_problem *pr) {
   return MCDC_OK;
 }
 
+// ---- autotuner ---------------------------------------------------------------
+// Times candidate launch shapes on the problem itself -- threads per CTA
+// (which sets the CTA's particle bank: warps x 96 parked slots plus one
+// flying particle per lane), whole batches per CTA in the shared-tally mode,
+// and warp aggregation of tally atomics -- and keeps the fastest.  Choices
+// are cached per problem shape for the life of the process.
+struct TuneChoice {
+  int block, batch_per_cta, aggregate;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+
+std::string tune_key(const mcdc_problem *pr) {
+  const DevProblem &P = pr->P;
+  char b[256];
+  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d", (int)pr->key.f64,
+           (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T, (long long)P.n_bins,
+           P.n[0], P.n[1], P.n[2], pr->sms);
+  return b;
+}
+
+int apply_choice(mcdc_problem *pr, const DeviceLimits &dl, const TuneChoice &c) {
+  pr->opt.block_size = c.block;
+  pr->opt.warp_aggregate = c.aggregate ? 1 : -1;
+  pr->opt.tally_mode = pr->tally_mode;
+  pr->batch_per_cta = c.batch_per_cta;
+  return choose_shape(pr, dl);
+}
+
+}  // namespace
+
+extern "C" int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *stats);
+
+namespace {
+int autotune(mcdc_problem *pr, const DeviceLimits &dl) {
+  const std::string key = tune_key(pr);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return apply_choice(pr, dl, it->second);
+  }
+  const bool shared = pr->tally_mode == MCDC_TALLY_SHARED;
+  std::vector<TuneChoice> cand;
+  for (int b : {128, 256, 512})
+    for (int bpc : shared ? std::vector<int>{1, 2, 4} : std::vector<int>{2})
+      for (int agg : pr->P.n_bins <= 65536 ? std::vector<int>{0, 1} : std::vector<int>{0})
+        cand.push_back({b, bpc, agg});
+  const TuneChoice keep{pr->block, pr->batch_per_cta, pr->warp_aggregate};
+  const uint64_t n_trial = 1ull << 20;
+  double best_t = 1e300;
+  TuneChoice best = keep;
+  for (const TuneChoice &c : cand) {
+    if (apply_choice(pr, dl, c) != MCDC_OK) { g_err.clear(); continue; }
+    mcdc_run_args a;
+    std::memset(&a, 0, sizeof a);
+    a.n_histories = n_trial;
+    a.seed = 0x5eed;
+    a.n_batches = shared ? 0 : 8;
+    mcdc_stats st;
+    double t = 0.0;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      a.hist_offset = (uint64_t)rep * n_trial;
+      ok = mcdc_run_ex(pr, &a, &st) == MCDC_OK;
+      t = st.kernel_ms;
+    }
+    if (ok && t < best_t) { best_t = t; best = c; }
+    g_err.clear();
+  }
+  if (int rc = apply_choice(pr, dl, best)) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return MCDC_OK;
+}
+
 }  // namespace
 
 namespace mcdc {
@@ -265,7 +341,7 @@ void mcdc_default_options(mcdc_options *o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = MCDC_PREC_FP32;
   o->tally_mode = MCDC_TALLY_AUTO;
-  o->autotune = 0;
+  o->autotune = 1;
 }
 
 const char *mcdc_last_error(void) { return g_err.c_str(); }
@@ -499,6 +575,9 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
     cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_bins);
     if (e != cudaSuccess) { fail(MCDC_ERR_CUDA, cudaGetErrorString(e)); return bail(MCDC_ERR_CUDA); }
+  }
+  if (o.autotune && o.block_size == 0) {
+    if ((rc = autotune(pr, dl))) return bail(rc);
   }
   *out = pr;
   return MCDC_OK;

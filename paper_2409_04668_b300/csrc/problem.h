@@ -21,6 +21,7 @@ struct mcdc_problem {
   mcdc::Layout L{};
   int tally_mode = MCDC_TALLY_SHARED;
   int warp_aggregate = 0;
+  int batch_per_cta = 2;      // shared tally: default batches = grid x this
   int overflow_cap = 0;
   // device memory
   std::vector<void *> allocs;
