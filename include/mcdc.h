@@ -206,6 +206,21 @@ int64_t mcdc_tally_size(const struct mcdc_problem *prob);
 
 void mcdc_problem_destroy(struct mcdc_problem *prob);
 
+/* Many independent problems in one run (analog): per batch, one persistent
+ * launch in which CTAs claim (problem, history range) work items, largest
+ * first, and load a problem's tables when they switch to it; then one fused
+ * fold of every problem's batch tally; the whole run is one CUDA graph.  All
+ * problems must share device, precision and dimension and have no weight
+ * windows.  Problem i uses seed + i * 0x9E3779B97F4A7C15 (mod 2^64) and
+ * histories [0, n_histories[i]) in n_batches batches (0: 16).
+ * mean_out[i] / relerr_out[i]: [n_bins of problem i], host or device, or
+ * NULL; scalar_out: [2n] region mean and relative error, or NULL.
+ * (The paper runs one problem per process; this batching has no paper
+ * counterpart beyond its fixed-source loop.) */
+int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_histories,
+                     uint64_t seed, int32_t n_batches, double *const *mean_out,
+                     double *const *relerr_out, double *scalar_out, mcdc_stats *stats);
+
 /* ---- learned importance proposal ----------------------------------------
  * A 3-layer perceptron (4 + G) -> 64 -> 64 -> 1 with SiLU hidden layers maps
  * a tally bin (cell centre and bin-centre time scaled to [-1, 1], group

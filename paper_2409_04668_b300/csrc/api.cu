@@ -112,6 +112,9 @@ void build_cdf(const double *pdf, int n, double *cdf) {
 // Shared memory one CTA needs for a given slot count.
 Layout make_layout(const mcdc_problem *pr, int S, int tally_mode) {
   Layout L{};
+  L.M = pr->P.M;
+  L.G = pr->P.G;
+  L.T = pr->P.T;
   L.S = S;
   const bool f64 = pr->key.f64;
   L.tables_bytes = tables_bytes_of(f64, pr->P.M, pr->P.G, pr->P.T);

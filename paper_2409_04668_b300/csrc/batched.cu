@@ -1,0 +1,320 @@
+// batched.cu -- many independent problems in one run: per batch, one
+// persistent launch in which CTAs claim (problem, history range) work items
+// (largest first), load the item's problem tables into shared memory when the
+// problem changes, and score into that problem's device tally; then one fused
+// fold of every problem's batch tally.  The whole sequence is captured as a
+// CUDA graph and launched once.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcdc.h"
+#include "launch.h"
+#include "problem.h"
+#include "tracker.cuh"
+
+namespace mcdc {
+
+// Fold of every problem's batch tally: sum1 += x, sum2 += x^2, x = 0, and the
+// batch's region sum per problem.  Bins of all problems are numbered one
+// after another; off[p] is the first bin of problem p.
+struct FoldItem {
+  double *tally, *sum1, *sum2, *region_batch;
+};
+
+__global__ void __launch_bounds__(512) k_fold_multi(const DevProblem *__restrict__ probs,
+                                                    const FoldItem *__restrict__ fi,
+                                                    const long long *__restrict__ off, int n,
+                                                    long long total) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;           // last problem whose first bin is <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const long long b = q - off[lo];
+    const FoldItem &f = fi[lo];
+    const double v = f.tally[b];
+    if (v != 0.0) {
+      f.sum1[b] += v;
+      f.sum2[b] += v * v;
+      f.tally[b] = 0.0;
+      const DevProblem &P = probs[lo];
+      const long long cell = b / ((long long)P.G * P.T1);
+      const int ci = (int)(cell % P.n[0]);
+      const int cj = (int)((cell / P.n[0]) % P.n[1]);
+      const int ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
+      if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
+          cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
+        atomicAdd(f.region_batch, v);
+    }
+  }
+}
+
+__global__ void k_region_fold_multi(const FoldItem *__restrict__ fi, double *const *regions, int n) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const double b = *fi[p].region_batch;
+    regions[p][0] += b;
+    regions[p][1] += b * b;
+    *fi[p].region_batch = 0.0;
+  }
+}
+
+}  // namespace mcdc
+
+using namespace mcdc;
+
+namespace {
+int fail(int code, const std::string &m) { return mcdc::set_error(code, m); }
+
+struct DevFree {
+  std::vector<void *> v;
+  ~DevFree() { for (void *p : v) cudaFree(p); }
+};
+
+#define CKB(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? MCDC_ERR_OOM : MCDC_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+template <class T>
+cudaError_t dnew(DevFree &f, T **p, size_t n) {
+  cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n * sizeof(T), 16));
+  if (e == cudaSuccess) f.v.push_back(*p);
+  return e;
+}
+
+bool dev_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
+                                const uint64_t *n_histories, uint64_t seed, int32_t n_batches,
+                                double *const *mean_out, double *const *relerr_out,
+                                double *scalar_out, mcdc_stats *stats) {
+  if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
+  const int B = n_batches > 0 ? n_batches : 16;
+  if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");
+  mcdc_problem *p0 = probs[0];
+  for (int i = 0; i < n; ++i) {
+    const mcdc_problem *p = probs[i];
+    if (!p) return fail(MCDC_ERR_INVALID, "problem is NULL");
+    if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
+        p->dim != p0->dim)
+      return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
+    if (p->P.ww_lower != nullptr) return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows)");
+    if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
+  }
+  CKB(cudaSetDevice(p0->device));
+  DevFree fr;
+  // every problem scores into a device tally of its own
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    if (!p->tally) {
+      double *t = nullptr;
+      CKB(cudaMalloc(&t, sizeof(double) * p->P.n_bins));
+      p->allocs.push_back(t);
+      p->tally = t;
+      CKB(cudaMemset(t, 0, sizeof(double) * p->P.n_bins));
+    }
+  }
+  // launch shape: the largest tables of the batch, no shared tally
+  TrackKey key = p0->key;
+  key.shared = false;
+  key.multi = true;
+  const int block = 256;
+  Layout L{};
+  for (int i = 0; i < n; ++i) {
+    L.M = std::max(L.M, probs[i]->P.M);
+    L.G = std::max(L.G, probs[i]->P.G);
+    L.T = std::max(L.T, probs[i]->P.T);
+  }
+  L.S = (block / 32) * kPool;
+  L.tables_bytes = tables_bytes_of(key.f64, L.M, L.G, L.T);
+  L.tally_bytes = 0;
+  L.bank_bytes = L.S * slot_bytes(key.f64, p0->dim, key.local);
+  L.total = (int)(L.tables_bytes + L.bank_bytes + 64);
+  int smem_max = 0;
+  CKB(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p0->device));
+  if (L.total > smem_max - 2048) return fail(MCDC_ERR_INVALID, "tables too large for shared memory");
+  CKB(prepare_track(key, smem_max - 2048));
+  const int cps = track_occupancy(key, block, L.total);
+  if (cps < 1) return fail(MCDC_ERR_INVALID, "launch shape does not fit");
+  const int grid = p0->sms * cps;
+
+  // per-problem device arguments, one stats block and error word for all
+  Stats *d_stats = nullptr;
+  int32_t *d_err = nullptr;
+  CKB(dnew(fr, &d_stats, 1));
+  CKB(dnew(fr, &d_err, 4));
+  std::vector<DevProblem> hp(n);
+  std::vector<RunArgs> ha(n);
+  std::vector<FoldItem> hf(n);
+  std::vector<double *> hreg(n);
+  std::vector<long long> hoff(n);
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    hp[i] = p->P;
+    RunArgs A{};
+    A.n_hist = n_histories[i];
+    A.offset = 0;
+    A.seed = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;   // independent streams per problem
+    A.n_batches = B;
+    A.tally = p->tally;
+    A.stats = d_stats;
+    A.error = d_err;
+    A.warp_aggregate = p->warp_aggregate;
+    ha[i] = A;
+    hf[i] = {p->tally, p->sum1, p->sum2, p->region_batch};
+    hreg[i] = p->region;
+    hoff[i] = total;
+    total += p->P.n_bins;
+  }
+  // work items, batch by batch, largest first within a batch
+  const unsigned long long chunk = 1ull << 16;
+  std::vector<WorkItem> items;
+  std::vector<int> item_off(B + 1, 0);
+  for (int b = 0; b < B; ++b) {
+    std::vector<WorkItem> bi;
+    for (int i = 0; i < n; ++i) {
+      const uint64_t h0 = batch_start(n_histories[i], B, b), h1 = batch_start(n_histories[i], B, b + 1);
+      for (uint64_t h = h0; h < h1; h += chunk) bi.push_back({i, 0, h, std::min<uint64_t>(h1, h + chunk)});
+    }
+    std::stable_sort(bi.begin(), bi.end(), [](const WorkItem &x, const WorkItem &y) {
+      return (x.h1 - x.h0) > (y.h1 - y.h0);
+    });
+    items.insert(items.end(), bi.begin(), bi.end());
+    item_off[b + 1] = (int)items.size();
+  }
+  DevProblem *d_probs;
+  RunArgs *d_args;
+  WorkItem *d_items;
+  FoldItem *d_fold;
+  double **d_reg;
+  long long *d_off;
+  unsigned long long *d_ctr;
+  CKB(dnew(fr, &d_probs, n));
+  CKB(dnew(fr, &d_args, n));
+  CKB(dnew(fr, &d_items, items.size()));
+  CKB(dnew(fr, &d_fold, n));
+  CKB(dnew(fr, &d_reg, n));
+  CKB(dnew(fr, &d_off, n));
+  CKB(dnew(fr, &d_ctr, B));
+  CKB(cudaMemcpy(d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(d_args, ha.data(), sizeof(RunArgs) * n, cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(d_fold, hf.data(), sizeof(FoldItem) * n, cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(d_reg, hreg.data(), sizeof(double *) * n, cudaMemcpyHostToDevice));
+  CKB(cudaMemcpy(d_off, hoff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+
+  cudaStream_t st;
+  CKB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  CKB(cudaEventCreate(&e0));
+  CKB(cudaEventCreate(&e1));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Release {
+    cudaStream_t s; cudaEvent_t a, b; cudaGraph_t *g; cudaGraphExec_t *x;
+    ~Release() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+      cudaEventDestroy(a); cudaEventDestroy(b); cudaStreamDestroy(s);
+    }
+  } rel{st, e0, e1, &graph, &exec};
+
+  // the run as one graph: zero the accumulators, then per batch one
+  // persistent launch over every problem and one fused fold
+  CKB(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(d_stats, 0, sizeof(Stats), st);
+  cudaMemsetAsync(d_err, 0, 4 * sizeof(int32_t), st);
+  cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * B, st);
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    cudaMemsetAsync(p->sum1, 0, sizeof(double) * p->P.n_bins, st);
+    cudaMemsetAsync(p->sum2, 0, sizeof(double) * p->P.n_bins, st);
+    cudaMemsetAsync(p->region, 0, 4 * sizeof(double), st);
+  }
+  const int fold_blocks = (int)std::max<long long>(1, std::min<long long>((total + 511) / 512, (long long)p0->sms * 8));
+  for (int b = 0; b < B; ++b) {
+    MultiArgs MA{d_probs, d_args, d_items + item_off[b], item_off[b + 1] - item_off[b], d_ctr + b};
+    launch_track(key, grid, block, L.total, st, hp[0], ha[0], L, &MA);
+    k_fold_multi<<<fold_blocks, 512, 0, st>>>(d_probs, d_fold, d_off, n, total);
+    k_region_fold_multi<<<(n + 255) / 256, 256, 0, st>>>(d_fold, d_reg, n);
+  }
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    double *m = mean_out && mean_out[i] && dev_ptr(mean_out[i]) ? mean_out[i] : nullptr;
+    double *r = relerr_out && relerr_out[i] && dev_ptr(relerr_out[i]) ? relerr_out[i] : nullptr;
+    if (m || r)
+      launch_finalize(st, p->P.n_bins, p->sum1, p->sum2, n_histories[i], B, p->P.volume, m, r, p->sms);
+  }
+  CKB(cudaStreamEndCapture(st, &graph));
+  CKB(cudaGraphInstantiate(&exec, graph, 0));
+  CKB(cudaEventRecord(e0, st));
+  CKB(cudaGraphLaunch(exec, st));
+  CKB(cudaEventRecord(e1, st));
+  CKB(cudaStreamSynchronize(st));
+
+  // host outputs: finalise on the device into scratch, then copy
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    const size_t nb = (size_t)p->P.n_bins;
+    const bool hm = mean_out && mean_out[i] && !dev_ptr(mean_out[i]);
+    const bool hr = relerr_out && relerr_out[i] && !dev_ptr(relerr_out[i]);
+    if (hm || hr) {
+      double *m = nullptr, *r = nullptr;
+      CKB(dnew(fr, &m, nb));
+      CKB(dnew(fr, &r, nb));
+      CKB(launch_finalize(st, nb, p->sum1, p->sum2, n_histories[i], B, p->P.volume, m, r, p->sms));
+      if (hm) CKB(cudaMemcpyAsync(mean_out[i], m, nb * 8, cudaMemcpyDeviceToHost, st));
+      if (hr) CKB(cudaMemcpyAsync(relerr_out[i], r, nb * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (scalar_out) {
+      double reg[2];
+      CKB(cudaMemcpyAsync(reg, p->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CKB(cudaStreamSynchronize(st));
+      const double nv = (double)n_histories[i] * p->P.volume, Bd = (double)B;
+      const double mm = reg[0] / nv;
+      double ss = reg[1] - reg[0] * reg[0] / Bd;
+      if (ss < 0.0) ss = 0.0;
+      const double var = (Bd * Bd / (nv * nv)) * ss / (Bd * (Bd - 1.0));
+      scalar_out[2 * i] = mm;
+      scalar_out[2 * i + 1] = mm != 0.0 ? std::sqrt(var) / std::fabs(mm) : 0.0;
+    }
+  }
+  CKB(cudaStreamSynchronize(st));
+  if (stats) {
+    Stats h;
+    CKB(cudaMemcpy(&h, d_stats, sizeof(Stats), cudaMemcpyDeviceToHost));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->histories = h.histories; stats->segments = h.segments;
+    stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
+    stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
+    stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
+    stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->kernel_ms = ms;
+    stats->total_ms = ms;
+    stats->block_size = block;
+    stats->ctas_per_sm = cps;
+    stats->tally_mode = MCDC_TALLY_GLOBAL;
+    stats->n_batches = B;
+  }
+  int32_t herr = 0;
+  CKB(cudaMemcpy(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (herr) return fail(MCDC_ERR_BANK_OVERFLOW, "device error flag set");
+  return MCDC_OK;
+}

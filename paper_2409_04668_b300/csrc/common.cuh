@@ -167,7 +167,7 @@ __device__ __forceinline__ int warp_append(bool pred, int *counter) {
   return base + __popc(mask & ((1u << lane) - 1u));
 }
 
-__device__ __forceinline__ uint64_t batch_start(uint64_t n, int32_t B, int32_t b) {
+__host__ __device__ __forceinline__ uint64_t batch_start(uint64_t n, int32_t B, int32_t b) {
   const uint64_t q = n / (uint64_t)B, r = n % (uint64_t)B;
   const uint64_t bb = (uint64_t)b;
   return bb * q + (bb < r ? bb : r);

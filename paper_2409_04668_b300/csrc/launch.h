@@ -8,17 +8,20 @@ namespace mcdc {
 
 struct Layout;
 
+struct MultiArgs;
+
 struct TrackKey {
   bool f64;     // FP64 everywhere
   bool local;   // FP32 cell-local positions (when !f64)
+  bool multi = false;   // batched problems (work items over several problems)
   bool shared;
   int dim;   // 1 or 3
 };
 
-// Launches the persistent tracker for one configuration.
+// Launches the persistent tracker for one configuration (MA: batched mode only).
 cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem_bytes,
                          cudaStream_t stream, const DevProblem &P, const RunArgs &A,
-                         const Layout &L);
+                         const Layout &L, const MultiArgs *MA = nullptr);
 // Raises the dynamic shared-memory limit of that instantiation.
 cudaError_t prepare_track(const TrackKey &key, int smem_bytes);
 // Registers per thread of that instantiation (for occupancy decisions).

@@ -7,28 +7,31 @@
 namespace mcdc {
 
 cudaError_t launch_track_f64(const TrackKey &, int, int, int, cudaStream_t, const DevProblem &,
-                             const RunArgs &, const Layout &);
+                             const RunArgs &, const Layout &, const MultiArgs *);
 cudaError_t prepare_track_f64(const TrackKey &, int);
 int track_regs_f64(const TrackKey &);
 int track_occupancy_f64(const TrackKey &, int, int);
 
 namespace {
-template <class PR, bool SH, int DIM>
-void *fp32_kernel() { return (void *)k_track<PR, SH, DIM>; }
+template <class PR, bool SH, int DIM, bool MU>
+void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU>; }
 
 template <class PR>
 void *pick_prec(const TrackKey &k) {
-  if (k.shared) return k.dim == 1 ? fp32_kernel<PR, true, 1>() : fp32_kernel<PR, true, 3>();
-  return k.dim == 1 ? fp32_kernel<PR, false, 1>() : fp32_kernel<PR, false, 3>();
+  if (k.multi) return k.dim == 1 ? fp32_kernel<PR, false, 1, true>() : fp32_kernel<PR, false, 3, true>();
+  if (k.shared) return k.dim == 1 ? fp32_kernel<PR, true, 1, false>() : fp32_kernel<PR, true, 3, false>();
+  return k.dim == 1 ? fp32_kernel<PR, false, 1, false>() : fp32_kernel<PR, false, 3, false>();
 }
 
 void *pick(const TrackKey &k) { return k.local ? pick_prec<PrecF32L>(k) : pick_prec<PrecF32>(k); }
 }  // namespace
 
 cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem, cudaStream_t stream,
-                         const DevProblem &P, const RunArgs &A, const Layout &L) {
-  if (key.f64) return launch_track_f64(key, grid, block, smem, stream, P, A, L);
-  void *args[] = {(void *)&P, (void *)&A, (void *)&L};
+                         const DevProblem &P, const RunArgs &A, const Layout &L,
+                         const MultiArgs *MA) {
+  if (key.f64) return launch_track_f64(key, grid, block, smem, stream, P, A, L, MA);
+  const MultiArgs none{};
+  void *args[] = {(void *)&P, (void *)&A, (void *)&L, (void *)(MA ? MA : &none)};
   return cudaLaunchKernel(pick(key), dim3(grid), dim3(block), args, (size_t)smem, stream);
 }
 

@@ -6,19 +6,21 @@
 
 namespace mcdc {
 namespace {
-template <bool SH, int DIM>
-void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM>; }
+template <bool SH, int DIM, bool MU>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU>; }
 
 void *pick(const TrackKey &k) {
-  if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1>() : fp64_kernel<true, 3>();
-  return k.dim == 1 ? fp64_kernel<false, 1>() : fp64_kernel<false, 3>();
+  if (k.multi) return k.dim == 1 ? fp64_kernel<false, 1, true>() : fp64_kernel<false, 3, true>();
+  if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1, false>() : fp64_kernel<true, 3, false>();
+  return k.dim == 1 ? fp64_kernel<false, 1, false>() : fp64_kernel<false, 3, false>();
 }
 }  // namespace
 
 cudaError_t launch_track_f64(const TrackKey &key, int grid, int block, int smem,
                              cudaStream_t stream, const DevProblem &P, const RunArgs &A,
-                             const Layout &L) {
-  void *args[] = {(void *)&P, (void *)&A, (void *)&L};
+                             const Layout &L, const MultiArgs *MA) {
+  const MultiArgs none{};
+  void *args[] = {(void *)&P, (void *)&A, (void *)&L, (void *)(MA ? MA : &none)};
   return cudaLaunchKernel(pick(key), dim3(grid), dim3(block), args, (size_t)smem, stream);
 }
 

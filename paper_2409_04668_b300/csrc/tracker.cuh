@@ -141,6 +141,7 @@ constexpr int kPool = 96;
 
 // shared-memory layout of one CTA
 struct Layout {
+  int M, G, T;           // table sizes the carve reserves (the largest problem of a batch)
   int S;                 // pool slots of the whole CTA (warps x kPool)
   int tables_bytes;
   long long tally_bytes; // 0 in global mode
@@ -623,29 +624,49 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // private tally is folded into the batch sums.  Global mode: warps claim
 // histories of the launch's batch from a device-wide cursor and score into
 // the device-wide batch tally.
-template <class PR, bool SHARED, int DIM>
-__global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs A, const Layout L) {
+// batched problems: CTAs claim (problem, history range) work items
+struct WorkItem {
+  int32_t p;
+  int32_t pad;
+  unsigned long long h0, h1;   // histories [h0, h1) of problem p
+};
+struct MultiArgs {
+  const DevProblem *probs;
+  const RunArgs *args;
+  const WorkItem *items;
+  int32_t n_items;
+  unsigned long long *counter;
+};
+
+template <class PR, bool SHARED, int DIM, bool MULTI>
+__global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
+                                               const MultiArgs MA) {
   using R = typename PR::R;
   using TT = typename PR::TT;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
   const int S = L.S;
+  __shared__ DevProblem sP;      // batched problems: the current problem
+  __shared__ RunArgs sA;
+  __shared__ int s_cur_p;
+  const DevProblem &P = MULTI ? sP : Pin;
+  const RunArgs &A = MULTI ? sA : Ain;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
   Tables<R> tb;
-  const int M = P.M, G = P.G;
-  tb.sigma_t = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G);
-  tb.scat = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G);
-  tb.cdf = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G * G);
-  tb.src_cdf = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
-  tb.speed = (double *)ptr; ptr += align16(8ll * G);
-  tb.inv_speed = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
-  tb.speed32 = (float *)ptr; ptr += align16(4ll * G);
-  tb.edges = (double *)ptr; ptr += align16(8ll * (P.T + 1));
-  tb.ww = P.ww_lower;
-  tb.ww32 = P.ww_lower32;
+  {
+    const int M = L.M, G = L.G;
+    tb.sigma_t = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G);
+    tb.scat = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G);
+    tb.cdf = (R *)ptr; ptr += align16((long long)sizeof(R) * M * G * G);
+    tb.src_cdf = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
+    tb.speed = (double *)ptr; ptr += align16(8ll * G);
+    tb.inv_speed = (R *)ptr; ptr += align16((long long)sizeof(R) * G);
+    tb.speed32 = (float *)ptr; ptr += align16(4ll * G);
+    tb.edges = (double *)ptr; ptr += align16(8ll * (L.T + 1));
+  }
   TT *stally = nullptr;
   if (SHARED) { stally = (TT *)ptr; ptr += L.tally_bytes; }
   Bank<PR> bk;
@@ -664,44 +685,73 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
   __shared__ uint32_t s_n[8];
   __shared__ double s_red[16];
 
-  // ---- tables
-  for (int q = tid; q < M * G; q += nth) {
-    if constexpr (PR::kF64) { tb.sigma_t[q] = P.sigma_t[q]; tb.scat[q] = P.scat[q]; }
-    else { tb.sigma_t[q] = P.sigma_t32[q]; tb.scat[q] = P.scat32[q]; }
-  }
-  for (int q = tid; q < M * G * G; q += nth) {
-    if constexpr (PR::kF64) tb.cdf[q] = P.cdf[q]; else tb.cdf[q] = P.cdf32[q];
-  }
-  for (int q = tid; q < G; q += nth) {
-    if constexpr (PR::kF64) { tb.src_cdf[q] = P.src_cdf[q]; tb.inv_speed[q] = 1.0 / P.speed[q]; }
-    else { tb.src_cdf[q] = P.src_cdf32[q]; tb.inv_speed[q] = P.inv_speed32[q]; }
-    tb.speed[q] = P.speed[q];
-    tb.speed32[q] = P.speed32[q];
-  }
-  for (int q = tid; q <= P.T; q += nth) tb.edges[q] = P.edges[q];
+  // ---- tables of the current problem into shared memory
+  auto load_tables = [&]() {
+    const int M = P.M, G = P.G;
+    tb.ww = P.ww_lower;
+    tb.ww32 = P.ww_lower32;
+    for (int q = tid; q < M * G; q += nth) {
+      if constexpr (PR::kF64) { tb.sigma_t[q] = P.sigma_t[q]; tb.scat[q] = P.scat[q]; }
+      else { tb.sigma_t[q] = P.sigma_t32[q]; tb.scat[q] = P.scat32[q]; }
+    }
+    for (int q = tid; q < M * G * G; q += nth) {
+      if constexpr (PR::kF64) tb.cdf[q] = P.cdf[q]; else tb.cdf[q] = P.cdf32[q];
+    }
+    for (int q = tid; q < G; q += nth) {
+      if constexpr (PR::kF64) { tb.src_cdf[q] = P.src_cdf[q]; tb.inv_speed[q] = 1.0 / P.speed[q]; }
+      else { tb.src_cdf[q] = P.src_cdf32[q]; tb.inv_speed[q] = P.inv_speed32[q]; }
+      tb.speed[q] = P.speed[q];
+      tb.speed32[q] = P.speed32[q];
+    }
+    for (int q = tid; q <= P.T; q += nth) tb.edges[q] = P.edges[q];
+  };
+  if (!MULTI) load_tables();
   if (SHARED)
     for (long long q = tid; q < P.n_bins; q += nth) stally[q] = (TT)0;
   if (tid < 16) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 8) s_n[tid] = 0u;
-  if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; }
+  if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }
   __syncthreads();
 
   EndSink es{s_w, s_n};
   LocalCount lc{0, 0, 0, 0};
   const int wid = blockIdx.x * nwarps + warp;                 // warp id in the grid
-  PartOf<PR> *ovf = reinterpret_cast<PartOf<PR> *>(A.overflow) + (size_t)wid * A.overflow_cap;
+  PartOf<PR> *ovf = MULTI ? nullptr
+                          : reinterpret_cast<PartOf<PR> *>(A.overflow) + (size_t)wid * A.overflow_cap;
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
-  const bool agg = A.warp_aggregate != 0;
+  bool agg = MULTI ? false : A.warp_aggregate != 0;
   uint64_t g_h0 = 0, g_h1 = 0;
-  if (!SHARED) {
+  if (!SHARED && !MULTI) {
     g_h0 = batch_start(A.n_hist, A.n_batches, A.batch);
     g_h1 = batch_start(A.n_hist, A.n_batches, A.batch + 1);
   }
 
   for (;;) {
-    if (SHARED) {
+    if (MULTI) {
+      // ---- claim the next work item; switch problem when it changes
+      if (tid == 0) {
+        const unsigned long long it = atomicAdd(MA.counter, 1ull);
+        if ((long long)it < MA.n_items) {
+          const WorkItem w = MA.items[it];
+          s_batch = w.p;
+          s_h_next = w.h0;
+          s_h_end = w.h1;
+        } else {
+          s_done = 1;
+        }
+      }
+      __syncthreads();
+      if (s_done) break;
+      if (s_batch != s_cur_p) {
+        if (tid == 0) { sP = MA.probs[s_batch]; sA = MA.args[s_batch]; s_cur_p = s_batch; }
+        __syncthreads();
+        load_tables();
+        agg = A.warp_aggregate != 0;
+        __syncthreads();
+      }
+    } else if (SHARED) {
       // ---- claim the next batch for the whole CTA
       if (tid == 0) {
         const unsigned long long b = atomicAdd(A.work, 1ull);
@@ -774,11 +824,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
           unsigned long long first = 0;
           int got = 0;
           if (lane == 0) {
-            if (A.spill_in != nullptr) {
+            if (A.spill_in != nullptr && !MULTI) {
               const unsigned long long total = min(*A.spill_in_count, A.spill_cap);
               first = atomicAdd(A.spill_in_cursor, (unsigned long long)want);
               got = first < total ? (int)min((unsigned long long)want, total - first) : 0;
-            } else if (SHARED) {
+            } else if (SHARED || MULTI) {
               first = atomicAdd(&s_h_next, (unsigned long long)want);
               got = first < s_h_end ? (int)min((unsigned long long)want, s_h_end - first) : 0;
             } else {
@@ -801,7 +851,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
           if (lane < n_o) {
             q = ovf[top - 1 - lane];
             alive = true;
-          } else if (A.spill_in != nullptr) {
+          } else if (A.spill_in != nullptr && !MULTI) {
             q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[h_first + (lane - n_o)];
             alive = true;
           } else {
@@ -873,6 +923,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
       }
     }
 
+    if (MULTI) { __syncthreads(); continue; }   // the item is drained in every warp
     if (!SHARED) break;
     // ---- the batch is drained in every warp: fold the private tally
     __syncthreads();
@@ -905,32 +956,37 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem P, const RunArgs
     __syncthreads();
   }
 
-  // ---- flush event counters: warp sums, one atomic per field per warp
+  // ---- flush event counters: warp sums, one atomic per field per warp.
+  // (Batched problems share one stats block and error word; a CTA that never
+  // claimed an item must not read its per-problem arguments.)
+  Stats *const stats = MULTI ? MA.args[0].stats : A.stats;
+  int32_t *const errw = MULTI ? MA.args[0].error : A.error;
+  const int ovf_cap = MULTI ? 0 : A.overflow_cap;
   uint32_t c4[4] = {lc.seg, lc.col, lc.cross, lc.census};
 #pragma unroll
   for (int f = 0; f < 4; ++f)
     for (int o = 16; o > 0; o >>= 1) c4[f] += __shfl_xor_sync(0xffffffffu, c4[f], o);
   if (lane == 0) {
-    atomicAdd(&A.stats->segments, (unsigned long long)c4[0]);
-    atomicAdd(&A.stats->collisions, (unsigned long long)c4[1]);
-    atomicAdd(&A.stats->crossings, (unsigned long long)c4[2]);
-    atomicAdd(&A.stats->census, (unsigned long long)c4[3]);
-    if (*novf > A.overflow_cap) atomicOr(A.error, ERRBIT_OVERFLOW);
+    atomicAdd(&stats->segments, (unsigned long long)c4[0]);
+    atomicAdd(&stats->collisions, (unsigned long long)c4[1]);
+    atomicAdd(&stats->crossings, (unsigned long long)c4[2]);
+    atomicAdd(&stats->census, (unsigned long long)c4[3]);
+    if (*novf > ovf_cap) atomicOr(errw, ERRBIT_OVERFLOW);
   }
   __syncthreads();
   if (tid == 0) {
-    atomicAdd(&A.stats->absorbed, (unsigned long long)s_n[0]);
-    atomicAdd(&A.stats->leaked, (unsigned long long)s_n[1]);
-    atomicAdd(&A.stats->censused, (unsigned long long)s_n[2]);
-    atomicAdd(&A.stats->roulette_killed, (unsigned long long)s_n[3]);
-    atomicAdd(&A.stats->roulette_survived, (unsigned long long)s_n[4]);
-    atomicAdd(&A.stats->splits, (unsigned long long)s_n[5]);
-    atomicAdd(&A.stats->children, (unsigned long long)s_n[6]);
-    atomicAdd(&A.stats->histories, (unsigned long long)s_n[7]);
-    atomicAdd(&A.stats->w_source, s_w[0]);
-    atomicAdd(&A.stats->w_absorbed, s_w[1]);
-    atomicAdd(&A.stats->w_leaked, s_w[2]);
-    atomicAdd(&A.stats->w_censused, s_w[3]);
+    atomicAdd(&stats->absorbed, (unsigned long long)s_n[0]);
+    atomicAdd(&stats->leaked, (unsigned long long)s_n[1]);
+    atomicAdd(&stats->censused, (unsigned long long)s_n[2]);
+    atomicAdd(&stats->roulette_killed, (unsigned long long)s_n[3]);
+    atomicAdd(&stats->roulette_survived, (unsigned long long)s_n[4]);
+    atomicAdd(&stats->splits, (unsigned long long)s_n[5]);
+    atomicAdd(&stats->children, (unsigned long long)s_n[6]);
+    atomicAdd(&stats->histories, (unsigned long long)s_n[7]);
+    atomicAdd(&stats->w_source, s_w[0]);
+    atomicAdd(&stats->w_absorbed, s_w[1]);
+    atomicAdd(&stats->w_leaked, s_w[2]);
+    atomicAdd(&stats->w_censused, s_w[3]);
   }
 }
 

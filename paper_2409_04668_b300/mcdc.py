@@ -115,6 +115,8 @@ SIGNATURES = {
                                           C.c_int32]),
     "mcdc_tally_size": (C.c_int64, [C.c_void_p]),
     "mcdc_problem_destroy": (None, [C.c_void_p]),
+    "mcdc_run_batched": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_uint64, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(mcdc_stats)]),
     "mcdc_default_mlp_options": (None, [C.POINTER(mcdc_mlp_options)]),
     "mcdc_train_importance": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.POINTER(mcdc_mlp_options), C.POINTER(mcdc_mlp_report)]),
@@ -150,6 +152,7 @@ mcdc_tally_size = _lib.mcdc_tally_size
 mcdc_problem_destroy = _lib.mcdc_problem_destroy
 mcdc_run_noalloc = _lib.mcdc_run_noalloc
 mcdc_default_mlp_options = _lib.mcdc_default_mlp_options
+mcdc_run_batched = _lib.mcdc_run_batched
 mcdc_train_importance = _lib.mcdc_train_importance
 mcdc_mlp_param_count = _lib.mcdc_mlp_param_count
 mcdc_mlp_forward = _lib.mcdc_mlp_forward
@@ -348,3 +351,20 @@ def mlp_loss_grad(params, X, y, w):
     check(mcdc_mlp_loss_grad(_ptr(p), X.shape[1], _ptr(X), _ptr(y), _ptr(w), X.shape[0], _ptr(g),
                              C.byref(loss)))
     return loss.value, g
+
+
+def run_batched(problems, n_histories, seed, batches=0, means=None, relerrs=None):
+    """One batched run over Problem handles (see mcdc_run_batched); means /
+    relerrs are lists of output arrays (numpy or torch) or None.  Returns
+    (stats dict, [(region mean, region relerr)] per problem)."""
+    n = len(problems)
+    handles = (C.c_void_p * n)(*[p.handle.value for p in problems])
+    hist = np.ascontiguousarray(n_histories, dtype=np.uint64)
+    mp = (C.c_void_p * n)(*[_ptr(x) for x in means]) if means is not None else None
+    rp = (C.c_void_p * n)(*[_ptr(x) for x in relerrs]) if relerrs is not None else None
+    scal = np.zeros(2 * n)
+    st = mcdc_stats()
+    check(mcdc_run_batched(handles, n, _ptr(hist), int(seed), int(batches), mp, rp, _ptr(scal),
+                           C.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in mcdc_stats._fields_}
+    return stats, [(scal[2 * i], scal[2 * i + 1]) for i in range(n)]

@@ -157,6 +157,37 @@ def test_fp64_weight_windows_global_tally_with_spill(mcdc):
     assert stats["children"] > 64 * 8 * 148 * 2, stats["children"]   # more than the warp stacks hold
 
 
+def test_fp64_batched_problems_match_independent_oracle_runs(mcdc):
+    """Five random 3-D problems of different size and group count in one
+    batched run: each problem's tally equals an oracle run of that problem
+    with its own seed, to 1e-9."""
+    probs, _ = W.c5_batch(n_problems=5, seed=17)
+    small = []
+    for p in probs:        # keep the oracle fast: at most 12^3 cells
+        k = min(p.n[0], 12)
+        small.append(W.box(p.name, (k, k, k), p.width, p.material[:k, :k, :k].copy(), p.sigma_t,
+                           p.sigma_s / p.sigma_t, p.transfer, p.speed, (0.0,) * 3, (float(k),) * 3,
+                           None, (0, 0, 0), (k, k, k)))
+    hist = [3000, 5000, 2048, 4001, 2500]
+    seed, B = 99, 4
+    handles = [mcdc.Problem(p, precision=mcdc.PREC_FP64) for p in small]
+    means = [np.zeros(h.n_bins) for h in handles]
+    rels = [np.zeros(h.n_bins) for h in handles]
+    stats, scal = mcdc.run_batched(handles, hist, seed, batches=B, means=means, relerrs=rels)
+    assert stats["histories"] == sum(hist)
+    for i, p in enumerate(small):
+        s = (seed + i * 0x9E3779B97F4A7C15) % (1 << 64)
+        o = O.run(p, hist[i], seed=s, batches=B)
+        nz = o["mean"] != 0
+        got = means[i].reshape(p.tally_shape)
+        np.testing.assert_allclose(got[nz], o["mean"][nz], rtol=REL_TALLY)
+        np.testing.assert_array_equal(got == 0, o["mean"] == 0)
+        np.testing.assert_allclose(rels[i].reshape(p.tally_shape), o["relerr"], rtol=1e-6, atol=1e-12)
+        assert scal[i][0] == pytest.approx(o["scalar"][0], rel=REL_TALLY)
+    for h in handles:
+        h.close()
+
+
 def _coarse(mean):
     """20 x 10 blocks of (space, time) bins of the two-region slab."""
     return mean[0, 0, :, 0, :].reshape(20, 10, 10, 5).sum(axis=(1, 3))
