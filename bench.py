@@ -32,6 +32,7 @@ WORKLOADS = {
     "c2": (W.c2_two_region, 10_000_000),
     "c3": (W.c3_channel, 100_000_000),
     "c4": (W.c4_deep, 100_000_000),
+    "c5": (None, 0),          # 256 independent problems in one batched run
 }
 
 
@@ -157,6 +158,9 @@ def main():
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
     args = ap.parse_args()
 
+    if args.workload == "c5":
+        run_batched_bench(args)
+        return
     make, n_default = WORKLOADS[args.workload]
     prob = make()
     n_hist = args.histories or n_default
@@ -285,6 +289,62 @@ def main():
     P.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_batched_bench(args):
+    """256 independent 3-D problems of uneven size (meshes 16^3..64^3, 1..7
+    groups, 1e4..1e7 histories) in one batched run per step."""
+    import torch
+    from paper_2409_04668_b300 import mcdc as M
+    probs, hist = W.c5_batch()
+    if args.impl == "reference":
+        # the oracle on a bounded sample: the 16 smallest problems
+        idx = np.argsort(hist)[:16]
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        done = 0
+        for i in idx:
+            n = int(min(hist[i], 20_000))
+            O.run(probs[i], n, seed=1, batches=4, threads=os.cpu_count() or 1)
+            done += n
+        dt = time.perf_counter() - t0
+        v = done / dt
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "histories/s",
+                          "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "c5_batched_256_problems"},
+                          "cpu_baseline": {"value": v, "unit": "histories/s", "kind": "oracle",
+                                           "cores": os.cpu_count(),
+                                           "sample": f"{done} histories of the 16 smallest problems"},
+                          "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    torch.cuda.set_device(0)
+    prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
+    handles = [M.Problem(p, precision=prec) for p in probs]
+    for s in range(args.warmup):
+        M.run_batched(handles, hist, 1 + s, batches=16)
+    ms, segs = [], 0
+    with Clocks(0) as clk:
+        for s in range(args.steps):
+            st, _ = M.run_batched(handles, hist, 100 + s, batches=16)
+            ms.append(st["kernel_ms"])
+            segs += st["segments"]
+    total = sum(hist) * args.steps
+    t = sum(ms) / 1e3
+    line = {"metric": METRIC, "value": total / t, "unit": "histories/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 anchors)",
+                      M.PREC_FP64: "f64"}[prec], "data": "synthetic",
+            "config": {"workload": "c5_batched_256_problems", "problems": len(probs),
+                       "histories_per_step": int(sum(hist)), "batches": 16,
+                       "l2": "inputs (tallies 2.2 GB) larger than L2"},
+            "segments_per_sec": segs / t, "clocks": clk.summary(), "gpu_launches": 16 * 3 + 1}
+    for h in handles:
+        h.close()
+    print(json.dumps(line), flush=True)
 
 
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):
