@@ -678,6 +678,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.n_hist = a->n_histories;
   A.offset = a->hist_offset;
   A.seed = a->seed;
+  A.rk = round_keys(a->seed);
   A.n_batches = B;
   A.sum1 = pr->sum1;
   A.sum2 = pr->sum2;
@@ -778,6 +779,12 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
     stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
+    if (P.ww_lower == nullptr) {        // analog: every weight is 1
+      stats->w_source = (double)h.histories;
+      stats->w_absorbed = (double)h.absorbed;
+      stats->w_leaked = (double)h.leaked;
+      stats->w_censused = (double)h.censused;
+    }
     float k_ms = 0.f, t_ms = 0.f;
     cudaEventElapsedTime(&k_ms, pr->ev1, pr->ev2);
     cudaEventElapsedTime(&t_ms, pr->ev0, pr->ev2);

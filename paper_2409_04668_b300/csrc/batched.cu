@@ -170,6 +170,7 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
     A.n_hist = n_histories[i];
     A.offset = 0;
     A.seed = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;   // independent streams per problem
+    A.rk = round_keys(A.seed);
     A.n_batches = B;
     A.tally = p->tally;
     A.stats = d_stats;
@@ -302,8 +303,8 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
     stats->histories = h.histories; stats->segments = h.segments;
     stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
     stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
-    stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
-    stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
+    stats->w_source = (double)h.histories; stats->w_absorbed = (double)h.absorbed;   // analog
+    stats->w_leaked = (double)h.leaked; stats->w_censused = (double)h.censused;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     stats->kernel_ms = ms;

@@ -85,7 +85,14 @@ struct Stats {
   double w_source, w_absorbed, w_leaked, w_censused;
 };
 
+// Philox round keys of one seed: (k0 + r W0, k1 + r W1) for rounds r = 0..9,
+// computed once per run so each round reads its key instead of adding it.
+struct RoundKeys {
+  uint32_t k[20];
+};
+
 struct RunArgs {
+  RoundKeys rk;               // round keys of `seed`
   uint64_t n_hist;            // histories in the whole run
   uint64_t offset;            // first history id
   uint64_t seed;
@@ -136,11 +143,38 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
   return U4{c0, c1, c2, c3};
 }
 
+// the same ten rounds with the round keys given
+__device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ rk.k[2 * r];
+    const uint32_t n2 = hi0 ^ c3 ^ rk.k[2 * r + 1];
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+__host__ __device__ inline RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+
 // draw one block for the particle and advance its counter
 template <class PartT>
-__device__ __forceinline__ U4 draw(const PartT &p, uint32_t &ctr, uint64_t seed) {
-  U4 r = philox4x32_10(ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32),
-                       (uint32_t)seed, (uint32_t)(seed >> 32));
+__device__ __forceinline__ U4 draw(const PartT &p, uint32_t &ctr, const RoundKeys &rk) {
+  U4 r = philox4x32_10_rk(ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32), rk);
   ctr += 1;
   return r;
 }

@@ -120,6 +120,7 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   A.n_hist = n_histories;
   A.offset = hist_offset;
   A.seed = seed;
+  A.rk = round_keys(seed);
   A.n_batches = n_batches;
   A.sum1 = sum1;
   A.sum2 = sum2;

@@ -214,9 +214,12 @@ struct EndSink {
 template <class PR, int DIM>
 __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, const EndSink &es,
                                        const PartOf<PR> &p, int end) {
-  if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); atomicAdd(&es.w_end[1], (double)p.w); }
-  else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); atomicAdd(&es.w_end[2], (double)p.w); }
-  else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); atomicAdd(&es.w_end[3], (double)p.w); }
+  // analog runs carry weight 1 throughout: their weight sums are the counts
+  // (filled in on the host), so only weighted runs add weights here
+  const bool weighted = P.ww_lower != nullptr;
+  if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); if (weighted) atomicAdd(&es.w_end[1], (double)p.w); }
+  else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); if (weighted) atomicAdd(&es.w_end[2], (double)p.w); }
+  else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); if (weighted) atomicAdd(&es.w_end[3], (double)p.w); }
   else if (end == END_ROULETTE) { atomicAdd(&es.n_end[3], 1u); }
   if (A.records != nullptr && p.serial == 0u) {
     const uint64_t r = p.hid - A.offset;
@@ -260,8 +263,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
     if (n > 1) {
       const R wc = p.w / (R)n;
       for (int c = 1; c < n; ++c) {
-        const U4 h = philox4x32_10(0xFFFFFFFFu, p.serial, p.ctr, (uint32_t)c,
-                                   (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+        const U4 h = philox4x32_10_rk(0xFFFFFFFFu, p.serial, p.ctr, (uint32_t)c, A.rk);
         PartOf<PR> ch = p;
         ch.w = wc;
         ch.serial = h.a;
@@ -287,7 +289,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
   }
   if (p.w < wl) {
     const R ws = (R)P.ww_survival * wl;
-    const U4 r = draw(p, p.ctr, A.seed);
+    const U4 r = draw(p, p.ctr, A.rk);
     R xi;
     if constexpr (PR::kF64) xi = u01_f64(r.a, r.b); else xi = u01_f32(r.a);
     if (xi < p.w / ws) {
@@ -304,14 +306,14 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
 // source particle (counters 0..3: x,y | z,group | mu,phi | t)
 template <class PR, int DIM>
 __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R> &tb,
-                                uint64_t seed, uint64_t hid, PartOf<PR> &p) {
+                                const RoundKeys &rk, uint64_t hid, PartOf<PR> &p) {
   using R = typename PR::R;
   p.serial = 0; p.ctr = 0; p.hid = hid;
   p.nseg = p.ncol = p.ncross = 0;
-  const U4 r0 = draw(p, p.ctr, seed);
-  const U4 r1 = draw(p, p.ctr, seed);
-  const U4 r2 = draw(p, p.ctr, seed);
-  const U4 r3 = draw(p, p.ctr, seed);
+  const U4 r0 = draw(p, p.ctr, rk);
+  const U4 r1 = draw(p, p.ctr, rk);
+  const U4 r2 = draw(p, p.ctr, rk);
+  const U4 r3 = draw(p, p.ctr, rk);
   if constexpr (PR::kF64) p.g = sample_cdf<double>(tb.src_cdf, P.G, u01_f64(r1.c, r1.d));
   else p.g = sample_cdf<float>(tb.src_cdf, P.G, u01_f32(r1.c));
   if (P.src_kind == 1) {
@@ -368,7 +370,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
   const R sig_t = tb.sigma_t[mg];
 
   // distance to collision
-  const U4 r = draw(p, p.ctr, A.seed);
+  const U4 r = draw(p, p.ctr, A.rk);
   R d_coll;
   if constexpr (PR::kF64) {
     const double xi = u01_f64(r.a, r.b);
@@ -534,8 +536,8 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   const int mg = m * P.G + p.g;
   p.ncol += 1;
   lc.col += 1;
-  const U4 r1 = draw(p, p.ctr, A.seed);
-  const U4 r2 = draw(p, p.ctr, A.seed);
+  const U4 r1 = draw(p, p.ctr, A.rk);
+  const U4 r2 = draw(p, p.ctr, A.rk);
   if constexpr (PR::kF64) {
     const double xi1 = u01_f64(r1.a, r1.b), xi2 = u01_f64(r1.c, r1.d);
     if (!(xi1 < tb.scat[mg])) { end = END_ABSORBED; return false; }
@@ -855,8 +857,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[h_first + (lane - n_o)];
             alive = true;
           } else {
-            source_particle<PR, DIM>(P, tb, A.seed, A.offset + h_first + (lane - n_o), q);
-            atomicAdd(&s_w[0], 1.0);
+            source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
+            if (P.ww_lower != nullptr) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
