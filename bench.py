@@ -36,6 +36,20 @@ WORKLOADS = {
 }
 
 
+def history_offset(rank, step, n_hist, max_steps=1000):
+    """First history id a rank runs at a step: every rank owns a disjoint
+    block of max_steps consecutive runs, so ranks never repeat a history and
+    the union over ranks is as many independent histories as one long run."""
+    return (rank * max_steps + step) * n_hist
+
+
+def job_value(local_ms, n_hist, steps, world, reduce_max=None):
+    """Whole-job histories/s: all ranks' histories over the slowest rank's
+    time (reduce_max(x) returns the maximum of x over ranks)."""
+    slowest = reduce_max(local_ms) if reduce_max else local_ms
+    return n_hist * steps * world / (slowest / 1e3), slowest
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -185,10 +199,9 @@ def main():
     rel = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    offset0 = rank * n_hist * 1000
 
     def step(s):
-        return P.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, batches=args.batches,
+        return P.run_ex(n_hist, seed=1, offset=history_offset(rank, s, n_hist), batches=args.batches,
                         mean=mean, relerr=rel,
                         stream=stream.cuda_stream, want_scalar=True, want_stats=True)
 
@@ -215,13 +228,13 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    region_ms = e0.elapsed_time(e1)
-    t = torch.tensor([region_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    region_ms = float(t.item())
-    hist_total = n_hist * args.steps * world
-    value = hist_total / (region_ms / 1e3)
+    def reduce_max(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    value, region_ms = job_value(e0.elapsed_time(e1), n_hist, args.steps, world, reduce_max)
     segs = sum(s["segments"] for s in stats_all) / args.steps
     ms_step = region_ms / args.steps
     k_ms = float(np.mean(kernel_ms))
@@ -239,7 +252,7 @@ def main():
     te0 = time.perf_counter()
     for s in range(e2e_steps):
         with M.Problem(prob, precision=prec, block_size=args.block) as Q:
-            Q.run_ex(n_hist, seed=1, offset=offset0 + s * n_hist, batches=args.batches,
+            Q.run_ex(n_hist, seed=1, offset=history_offset(rank, 500 + s, n_hist), batches=args.batches,
                      mean=h_mean, relerr=h_rel, want_stats=False)
     te = time.perf_counter() - te0
     e2e_val = n_hist * e2e_steps * world / te

@@ -1,0 +1,45 @@
+"""Failure paths on the GPU, without faulting it: a run whose split children
+overflow the warp stacks reports MCDC_ERR_BANK_OVERFLOW (the kernel raises a
+flag and drops the excess, it never traps), and the same context runs a
+correct problem right afterwards.  The kernels have no device-side waits, so
+there is no timeout path to exercise."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2409_04668_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcdc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2409_04668_b300 import build
+    build.build()
+    from paper_2409_04668_b300 import mcdc as M
+    return M
+
+
+def test_split_overflow_is_reported_and_the_context_survives(mcdc):
+    mat = np.zeros((2, 2, 2), np.uint8)
+    prob = W.box("box", (2, 2, 2), (1.0, 1.0, 1.0), mat, [[1.0]], [[0.95]], np.ones((1, 1, 1)),
+                 [1.0], (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), None, (0, 0, 0), (2, 2, 2),
+                 bc=(W.BC_REFLECT,) * 6)
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP32, tally_mode=mcdc.TALLY_SHARED,
+                      block_size=128, overflow_per_cta=256) as P:
+        # windows 1e6 times below the source weight: every event splits 16-fold
+        P.set_weight_windows(np.full(P.n_bins, 1e-6), 5.0, 2.5, 16)
+        with pytest.raises(mcdc.MCDCError) as e:
+            P.run_ex(2000, 3, batches=4)
+        assert e.value.code == mcdc.MCDC_ERR_BANK_OVERFLOW
+        P.set_weight_windows(None)                    # back to analog
+        stats, _ = P.run_ex(2000, 3, batches=4)
+        assert stats["absorbed"] == 2000
+    # and a fresh problem still matches the oracle exactly
+    p2 = W.c1_slab()
+    g = mcdc.run_numpy(p2, 5000, 2, batches=5, precision=mcdc.PREC_FP64)
+    o = O.run(p2, 5000, seed=2, batches=5)
+    nz = o["sum1"] != 0
+    np.testing.assert_allclose(g["sum1"][nz], o["sum1"][nz], rtol=1e-9)
