@@ -288,7 +288,17 @@ def main():
     line["gpu_launches"] = launches_per_step * args.steps
     # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)
-    line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"])
+    line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"], args.precision)
+    if args.precision == "fp32" and world == 1:
+        # the same workload in the cell-local mode (no FP64 in a flight)
+        with M.Problem(prob, precision=M.PREC_FP32_LOCAL) as Q:
+            for s in range(args.warmup):
+                Q.run_ex(n_hist, 1, offset=history_offset(rank, 700 + s, n_hist), mean=mean)
+            tl = []
+            for s in range(args.steps):
+                st, _ = Q.run_ex(n_hist, 1, offset=history_offset(rank, 720 + s, n_hist), mean=mean)
+                tl.append(st["kernel_ms"])
+        line["value_fp32_local"] = n_hist / (np.mean(tl) / 1e3)
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_deep(M, prec)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -409,24 +419,38 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):
     return out
 
 
-def roofline(prob, seg_rate, pk, tally_mode):
-    """Shared-tally mode keeps the tally and bank on chip: the tracker is
-    bound by issue slots (ALU); the global-tally mode streams 16 B of tally
-    read-modify-write per segment to HBM/L2."""
-    if tally_mode == 2:
+def roofline(prob, seg_rate, pk, tally_mode, prec_name):
+    """Roofline of the tracker for the binding unit of its precision mode.
+
+    FP32 split: every flight accumulates x (and y, z in 3-D) and t in FP64 and
+    takes the face and census distances from them -- 8 FP64-pipe operations
+    per 1-D flight, 16 per 3-D flight (conversions and adds) -- and the FP64
+    pipe binds; peak = the recipe's nominal B300 FP64 rate, 1.25 TFLOP/s = 0.625
+    T FP64-pipe operations/s.  Cell-local mode: no FP64 in a flight; bound by
+    issue slots, lane-operations per flight of the algorithm as written
+    (Philox 60, uniform 4, log+divide 4, lookup 3, face 4, census 3, nearest
+    event 4, tally 4, move 4, resolution 4, collisions 17 and births 5
+    amortised = 116) against 148 SMs x 128 lanes x max SM clock.  Global tally
+    (large meshes): 16 B of FP64 read-modify-write per flight against the
+    measured copy bandwidth."""
+    three_d = prob.n[1] > 1 or prob.n[2] > 1
+    if tally_mode == 2 and prec_name != "fp32":
         ach = seg_rate * 16 / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": "measured copy"}
-    # issue-slot roofline: lane-operations per flight of the algorithm as
-    # written (Philox 60, uniform 4, log+divide 4, lookup 3, face 4, census 3,
-    # nearest event 4, tally 4, move 4, resolution 4, collisions 17 and births
-    # 5 amortised) against 148 SMs x 128 lanes x max SM clock
+    if prec_name == "fp32":
+        ops = 16.0 if three_d else 8.0
+        peak = 0.625
+        ach = seg_rate * ops / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe ops/s",
+                "frac": ach / peak, "traffic": None, "ops_per_segment": ops,
+                "peak_kind": "nominal B300 FP64 1.25 TFLOP/s = 0.625 T pipe ops/s (recipe)"}
     ops_per_seg = 116.0
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = seg_rate * ops_per_seg / 1e12
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
-            "traffic": None, "ops_per_segment": ops_per_seg,
-            "peak_kind": "148 SM x 128 lanes x max SM clock"}
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T lane-ops/s",
+            "frac": ach / peak, "traffic": None, "ops_per_segment": ops_per_seg,
+            "peak_kind": "issue slots: 148 SM x 128 lanes x max SM clock"}
 
 
 if __name__ == "__main__":
