@@ -33,6 +33,7 @@ enum { ORC_SRC_ISOTROPIC = 0, ORC_SRC_BEAM = 1 };
 enum { ORC_EV_COLLISION = 0, ORC_EV_SURFACE = 1, ORC_EV_CENSUS = 2 };
 enum { ORC_END_ABSORBED = 1, ORC_END_LEAKED = 2, ORC_END_CENSUSED = 3,
        ORC_END_ROULETTE = 4 };
+enum { ORC_EST_TRACK = 0, ORC_EST_COLLISION = 1 };
 
 /* One problem: mesh, materials, source, time grid, optional weight windows. */
 typedef struct {
@@ -64,6 +65,11 @@ typedef struct {
     int32_t ww_nmax;           /* split cap                                      */
 
     int32_t region_lo[3], region_hi[3];  /* cell box of the scalar tally [lo,hi) */
+
+    int32_t estimator;         /* ORC_EST_TRACK or ORC_EST_COLLISION             */
+    int32_t implicit_capture;  /* 1: survival biasing at collisions              */
+    double weight_cutoff;      /* implicit capture: roulette below this weight   */
+    double cutoff_survival;    /*   ... surviving with this weight               */
 } orc_problem;
 
 typedef struct {

@@ -29,6 +29,8 @@ class OrcProblem(C.Structure):
         ("ww_lower", C.c_void_p), ("ww_upper_ratio", C.c_double),
         ("ww_survival_ratio", C.c_double), ("ww_nmax", C.c_int32),
         ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
+        ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
+        ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
     ]
 
 
@@ -46,6 +48,7 @@ RECORD_DTYPE = np.dtype([
     ("w", np.float64)], align=True)
 
 END_ABSORBED, END_LEAKED, END_CENSUSED, END_ROULETTE = 1, 2, 3, 4
+EST_TRACK, EST_COLLISION = 0, 1
 
 
 def lib():
@@ -98,7 +101,8 @@ class _Keep:
         return a.ctypes.data
 
 
-def _struct(prob, ww=None, keep=None):
+def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None):
+    """implicit: None (analog collisions) or (weight cutoff, survival weight)."""
     s = OrcProblem()
     s.n[:] = list(prob.n)
     s.origin[:] = [float(v) for v in prob.origin]
@@ -130,6 +134,10 @@ def _struct(prob, ww=None, keep=None):
         s.ww_nmax = int(ww.get("nmax", 16))
     s.region_lo[:] = list(prob.region_lo)
     s.region_hi[:] = list(prob.region_hi)
+    s.estimator = int(estimator)
+    if implicit is not None:
+        s.implicit_capture = 1
+        s.weight_cutoff, s.cutoff_survival = float(implicit[0]), float(implicit[1])
     return s
 
 
@@ -144,12 +152,15 @@ def tally_shape(prob):
     return (nz, ny, nx, int(np.asarray(prob.sigma_t).shape[1]), T)
 
 
-def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None):
+def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=EST_TRACK,
+        implicit=None):
     """Runs histories [offset, offset+n); returns mean/relerr/sums shaped
-    [nz, ny, nx, G, T], the region scalar and the event counts."""
+    [nz, ny, nx, G, T], the region scalar and the event counts.  estimator:
+    EST_TRACK (track length) or EST_COLLISION; implicit: None or (weight
+    cutoff, survival weight) for implicit capture."""
     L = lib()
     keep = _Keep()
-    s = _struct(prob, ww, keep)
+    s = _struct(prob, ww, keep, estimator, implicit)
     nb = n_bins(prob)
     mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
     scalar = np.zeros(2)
@@ -168,11 +179,11 @@ def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None):
             "threads": int(threads)}
 
 
-def trace(prob, seed, hids, ww=None):
+def trace(prob, seed, hids, ww=None, implicit=None):
     """Per-history summary of the primary particle of each listed history."""
     L = lib()
     keep = _Keep()
-    s = _struct(prob, ww, keep)
+    s = _struct(prob, ww, keep, EST_TRACK, implicit)
     h = np.ascontiguousarray(hids, dtype=np.uint64)
     out = np.zeros(len(h), dtype=RECORD_DTYPE)
     rc = L.orc_trace(C.byref(s), int(seed), h.ctypes.data, len(h), out.ctypes.data)

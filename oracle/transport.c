@@ -29,6 +29,18 @@
  *     n = min(ceil(w/w_U), nmax) equal copies, below w_L roulette with
  *     survival probability w/w_S to weight w_S.  Children get a new serial
  *     hashed from (serial, counter, child index) and restart their counter.
+ *  R11 collision estimator (optional, replaces R7's score): every collision
+ *     scores w / sigma_t into the bin (cell, group, time bin) of the particle
+ *     as it arrives, before the collision changes its group; same
+ *     normalisation as R7.  Its expectation is the same flux.
+ *  R12 implicit capture (optional): a collision never ends the history by
+ *     absorption; the weight is multiplied by sigma_s / sigma_t and the
+ *     removed part w (1 - sigma_s / sigma_t) is counted as absorbed weight (a
+ *     weight that becomes 0, sigma_s = 0, ends the history as absorbed).  The
+ *     collision draws the same two blocks as an analog one (the first number
+ *     then goes unused).  After the scatter a weight below the cutoff w_c is
+ *     rouletted: it survives with probability w / w_s at weight w_s (one more
+ *     block), else the history branch ends.  Weight windows, if any, follow.
  */
 #include <math.h>
 #include <pthread.h>
@@ -287,7 +299,7 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
 
         /* track-length tally into (cell, group, time bin) */
         int64_t bin = (cell * G + P->g) * tb->T1 + (p->n_tbin > 0 ? P->tbin : 0);
-        tally[bin] += P->w * d;
+        if (p->estimator == ORC_EST_TRACK) tally[bin] += P->w * d;
 
         move_particle(P, d);
 
@@ -321,12 +333,21 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
                 if (!weight_window(p, tb, seed, hid, P, bank, c)) return ORC_END_ROULETTE;
             }
         } else {
-            /* collision: absorb or scatter (analog), new group, new direction */
+            /* collision: absorb or scatter, new group, new direction */
             P->n_col += 1;
             c->collisions += 1;
+            if (p->estimator == ORC_EST_COLLISION) tally[bin] += P->w / sig_t;   /* R11 */
             pair r1 = draw(seed, hid, P);
             pair r2 = draw(seed, hid, P);
-            if (!(r1.a < tb->scat_ratio[m * G + P->g])) {
+            double ratio = tb->scat_ratio[m * G + P->g];
+            if (p->implicit_capture) {                                         /* R12 */
+                c->w_absorbed += P->w * (1.0 - ratio);
+                P->w *= ratio;
+                if (!(P->w > 0.0)) {
+                    c->absorbed += 1;
+                    return ORC_END_ABSORBED;
+                }
+            } else if (!(r1.a < ratio)) {
                 c->absorbed += 1;
                 c->w_absorbed += P->w;
                 return ORC_END_ABSORBED;
@@ -336,6 +357,16 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
             double u[3];
             orc_isotropic(r2.a, r2.b, u);
             P->ux = u[0]; P->uy = u[1]; P->uz = u[2];
+            if (p->implicit_capture && P->w < p->weight_cutoff) {
+                pair r = draw(seed, hid, P);
+                if (r.a < P->w / p->cutoff_survival) {
+                    P->w = p->cutoff_survival;
+                    c->roulette_survived += 1;
+                } else {
+                    c->roulette_killed += 1;
+                    return ORC_END_ROULETTE;
+                }
+            }
             if (!weight_window(p, tb, seed, hid, P, bank, c)) return ORC_END_ROULETTE;
         }
     }
@@ -406,6 +437,9 @@ static int make_tables(const orc_problem *p, tables *tb)
     build_cdf(p->src_pdf, G, tb->src_cdf);
     if (p->n_tbin > 0 && p->src_t0 < p->edges[0]) return -1;
     if (p->src_t1 < p->src_t0) return -1;
+    if (p->estimator != ORC_EST_TRACK && p->estimator != ORC_EST_COLLISION) return -1;
+    if (p->implicit_capture &&
+        !(p->weight_cutoff > 0.0 && p->cutoff_survival > p->weight_cutoff)) return -1;
     for (int64_t c = 0; c < tb->n_cells; ++c)
         if (p->material[c] >= M) return -1;
     return 0;
