@@ -170,6 +170,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the same workload in the other modes (cell-local FP32, "
+                         "collision estimator, implicit capture)")
     args = ap.parse_args()
 
     if args.workload == "c5":
@@ -289,16 +292,8 @@ def main():
     # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)
     line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"], args.precision)
-    if args.precision == "fp32" and world == 1:
-        # the same workload in the cell-local mode (no FP64 in a flight)
-        with M.Problem(prob, precision=M.PREC_FP32_LOCAL) as Q:
-            for s in range(args.warmup):
-                Q.run_ex(n_hist, 1, offset=history_offset(rank, 700 + s, n_hist), mean=mean)
-            tl = []
-            for s in range(args.steps):
-                st, _ = Q.run_ex(n_hist, 1, offset=history_offset(rank, 720 + s, n_hist), mean=mean)
-                tl.append(st["kernel_ms"])
-        line["value_fp32_local"] = n_hist / (np.mean(tl) / 1e3)
+    if world == 1 and not args.no_variants:
+        line["variants"] = variants(M, prob, n_hist, args, mean, rel, stream)
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_deep(M, prec)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -368,6 +363,40 @@ def run_batched_bench(args):
     for h in handles:
         h.close()
     print(json.dumps(line), flush=True)
+
+
+def variants(M, prob, n_hist, args, mean, rel, stream):
+    """The headline workload in the other modes of the tracker: device-timed
+    histories/s and the region scalar's figure of merit 1/(relerr^2 T) for
+    the cell-local FP32 mode and, in the headline precision, for the
+    collision estimator and for implicit capture (weight cutoff 0.25,
+    survival weight 0.5)."""
+    prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
+    modes = {"track_analog": {"precision": prec},
+             "fp32_local": {"precision": M.PREC_FP32_LOCAL},
+             "collision_estimator": {"precision": prec, "estimator": M.EST_COLLISION},
+             "implicit_capture": {"precision": prec, "implicit": (0.25, 0.5)}}
+    out = {}
+    for name, kw in modes.items():
+        with M.Problem(prob, block_size=args.block, **kw) as Q:
+            def one(s):
+                st, sc = Q.run_ex(n_hist, seed=1, offset=history_offset(0, s, n_hist),
+                                  batches=args.batches, mean=mean, relerr=rel,
+                                  stream=stream.cuda_stream, want_scalar=True, want_stats=True)
+                return st, sc
+            for s in range(args.warmup):
+                one(700 + s)
+            ms, rels = [], []
+            for s in range(args.steps):
+                st, sc = one(720 + s)
+                ms.append(st["kernel_ms"])
+                rels.append(sc[1])
+            t = float(np.mean(ms)) / 1e3
+            r = float(np.mean(rels))
+            out[name] = {"histories_per_s": n_hist / t, "region_relerr": r,
+                         "fom_region": 1.0 / (r * r * t) if r > 0 else None,
+                         "segments_per_history": st["segments"] / n_hist}
+    return out
 
 
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):

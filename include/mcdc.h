@@ -52,7 +52,8 @@ extern "C" {
 #define MCDC_ERR_INVALID        -1   /* bad argument or problem data            */
 #define MCDC_ERR_OOM            -2   /* device allocation failed                */
 #define MCDC_ERR_CUDA           -3   /* a CUDA call failed                      */
-#define MCDC_ERR_BANK_OVERFLOW  -4   /* split children exceeded the bank        */
+#define MCDC_ERR_BANK_OVERFLOW  -4   /* reserved: a split that finds no room is
+                                        skipped (mcdc_stats.splits_dropped)    */
 #define MCDC_ERR_TIMEOUT        -5   /* a bounded device wait gave up           */
 #define MCDC_ERR_NO_DEVICE      -6   /* no usable sm_103 device                 */
 
@@ -71,6 +72,12 @@ extern "C" {
 #define MCDC_TALLY_AUTO    0
 #define MCDC_TALLY_SHARED  1  /* per-CTA privatised tally in shared memory, one batch per CTA */
 #define MCDC_TALLY_GLOBAL  2  /* device-wide tally, batches run one after another            */
+
+/* Flux estimators (mcdc_options.estimator).  Both estimate the same flux per
+ * (cell, group, time bin), normalised by N x cell volume. */
+#define MCDC_EST_TRACK     0  /* track length: every flight scores w x d                     */
+#define MCDC_EST_COLLISION 1  /* collision: every collision scores w / sigma_t of the arriving
+                                 particle (its group, cell and time bin before the collision) */
 
 /* Uniform Cartesian mesh.  An axis with n == 1 and width <= 0 or infinite is
  * unbounded (no faces): a 1-D slab is nx cells with ny = nz = 1 and
@@ -129,6 +136,14 @@ typedef struct mcdc_options {
                                    its warps, >= 64 each); 0: 1024 per warp      */
     int32_t region_lo[3];       /* cell box [lo, hi) of the scalar tally used for */
     int32_t region_hi[3];       /*   the figure of merit; hi == 0: whole mesh      */
+    int32_t estimator;          /* MCDC_EST_* (default track length)              */
+    int32_t implicit_capture;   /* 1: survival biasing -- a collision never absorbs;
+                                   the weight is multiplied by sigma_s / sigma_t and
+                                   the removed part counts as absorbed weight     */
+    double weight_cutoff;       /* implicit capture: a weight below this after a
+                                   collision is rouletted (default 0.25) ...      */
+    double cutoff_survival;     /*   ... surviving with this weight (default 0.5);
+                                   need 0 < weight_cutoff < cutoff_survival       */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */
@@ -140,6 +155,10 @@ typedef struct mcdc_stats {
     double kernel_ms;           /* device time of the transport kernels      */
     double total_ms;            /* device time of the whole run              */
     int32_t block_size, bank_per_cta, ctas_per_sm, tally_mode, n_batches, warp_aggregate;
+    uint64_t splits_dropped;    /* weight-window children not made because the warp
+                                   stack and the spill bank were full: the parent
+                                   kept their weight (unbiased, less variance
+                                   reduction)                                   */
 } mcdc_stats;
 
 /* Per-history summary of the primary particle (serial 0), for checking a run
@@ -172,7 +191,9 @@ typedef struct mcdc_run_args {
 void mcdc_default_options(mcdc_options *opt);
 
 /* Validates the problem, builds its device tables (group-transfer CDFs,
- * FP32 copies), uploads them once and picks launch shapes.  Errors:
+ * FP32 copies), uploads them once and picks launch shapes.  A steady-state
+ * problem whose bounded faces all reflect must absorb in every material and
+ * group (0 <= sigma_s < sigma_t), else a history could run forever.  Errors:
  * MCDC_ERR_INVALID (bad sizes, negative or NaN data, sigma_s > sigma_t,
  * rows not summing to 1, source outside the mesh or before the first time
  * edge), MCDC_ERR_NO_DEVICE, MCDC_ERR_OOM, MCDC_ERR_CUDA.  On error *out is

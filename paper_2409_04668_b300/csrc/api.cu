@@ -270,9 +270,9 @@ std::map<std::string, TuneChoice> g_tune_cache;
 std::string tune_key(const mcdc_problem *pr) {
   const DevProblem &P = pr->P;
   char b[256];
-  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d", (int)pr->key.f64,
+  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
            (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T, (long long)P.n_bins,
-           P.n[0], P.n[1], P.n[2], pr->sms);
+           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit);
   return b;
 }
 
@@ -345,6 +345,9 @@ void mcdc_default_options(mcdc_options *o) {
   o->precision = MCDC_PREC_FP32;
   o->tally_mode = MCDC_TALLY_AUTO;
   o->autotune = 1;
+  o->estimator = MCDC_EST_TRACK;
+  o->weight_cutoff = 0.25;
+  o->cutoff_survival = 0.5;
 }
 
 const char *mcdc_last_error(void) { return g_err.c_str(); }
@@ -361,6 +364,13 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (o.precision != MCDC_PREC_FP64 && o.precision != MCDC_PREC_FP32 &&
       o.precision != MCDC_PREC_FP32_LOCAL)
     return fail(MCDC_ERR_INVALID, "unknown precision");
+  if (o.estimator != MCDC_EST_TRACK && o.estimator != MCDC_EST_COLLISION)
+    return fail(MCDC_ERR_INVALID, "unknown estimator");
+  if (o.implicit_capture != 0 && o.implicit_capture != 1)
+    return fail(MCDC_ERR_INVALID, "implicit_capture must be 0 or 1");
+  if (o.implicit_capture &&
+      !(std::isfinite(o.cutoff_survival) && o.weight_cutoff > 0.0 && o.cutoff_survival > o.weight_cutoff))
+    return fail(MCDC_ERR_INVALID, "implicit capture needs 0 < weight_cutoff < cutoff_survival");
 
   // ---- mesh
   const int n[3] = {mesh->nx, mesh->ny, mesh->nz};
@@ -455,6 +465,22 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (!std::isfinite(src->t0) || !std::isfinite(src->t1) || src->t1 < src->t0)
     return fail(MCDC_ERR_INVALID, "need finite t0 <= t1");
   if (T > 0 && src->t0 < edges[0]) return fail(MCDC_ERR_INVALID, "source starts before the first time edge");
+  if (T == 0) {
+    // steady state closed by reflecting faces: only absorption ends a history
+    bool open = false;
+    for (int a = 0; a < 3; ++a)
+      if (bounded[a] && (mesh->bc[2 * a] == MCDC_BC_VACUUM || mesh->bc[2 * a + 1] == MCDC_BC_VACUUM))
+        open = true;
+    if (!open) {
+      std::vector<char> used(M, 0);
+      for (int64_t c = 0; c < n_cells; ++c) used[mesh->material[c]] = 1;
+      for (int m = 0; m < M; ++m)
+        for (int g = 0; g < G && used[m]; ++g)
+          if (!(mat->sigma_s[m * G + g] < mat->sigma_t[m * G + g]))
+            return fail(MCDC_ERR_INVALID, "a steady-state problem closed by reflecting faces needs "
+                                          "sigma_s < sigma_t in every material and group");
+    }
+  }
 
   // ---- device
   int ndev = 0;
@@ -502,6 +528,12 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   P.src_kind = src->kind;
   P.t0 = src->t0;
   P.t1 = src->t1;
+  P.estimator = o.estimator;
+  P.implicit = o.implicit_capture;
+  P.wcut = o.weight_cutoff;
+  P.wsurv = o.cutoff_survival;
+  P.wcut32 = (float)o.weight_cutoff;
+  P.wsurv32 = (float)o.cutoff_survival;
   for (int a = 0; a < 3; ++a) {
     int hi = o.region_hi[a] > 0 ? o.region_hi[a] : n[a];
     int lo = std::max(0, o.region_lo[a]);
@@ -716,12 +748,14 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
       // passes over the spilled children, ping-ponging between the banks,
       // until a pass spills nothing
-      for (int pass = 1; spill && pass < 100000; ++pass) {
+      for (int pass = 1; spill; ++pass) {
         const int in = (pass - 1) & 1, out = pass & 1;
         CK(cudaMemcpyAsync(pr->h_spill, pr->spill_cnt + in, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*pr->h_spill == 0) break;
+        if (pass == 100000)
+          return fail(MCDC_ERR_BANK_OVERFLOW, "split children still pending after 100000 spill passes");
         CK(cudaMemsetAsync(pr->spill_cnt + out, 0, sizeof(unsigned long long), s));
         CK(cudaMemsetAsync(pr->spill_cnt + 2, 0, sizeof(unsigned long long), s));
         A.spill_in = pr->spill[in];
@@ -776,10 +810,11 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
     stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
     stats->splits = h.splits; stats->children = h.children;
+    stats->splits_dropped = h.splits_dropped;
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
     stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
-    if (P.ww_lower == nullptr) {        // analog: every weight is 1
+    if (P.ww_lower == nullptr && !P.implicit) {   // analog: every weight is 1
       stats->w_source = (double)h.histories;
       stats->w_absorbed = (double)h.absorbed;
       stats->w_leaked = (double)h.leaked;

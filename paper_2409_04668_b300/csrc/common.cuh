@@ -49,6 +49,11 @@ struct DevProblem {
   double ww_upper, ww_survival;
   int32_t ww_nmax;
   int32_t region_lo[3], region_hi[3];
+  // estimator and collision physics options
+  int32_t estimator;          // 0 track length, 1 collision
+  int32_t implicit;           // 1: implicit capture with weight-cutoff roulette
+  double wcut, wsurv;         // cutoff and survival weight (implicit capture)
+  float wcut32, wsurv32;
 };
 
 // One particle as it moves between the tracker phases (kept in registers).
@@ -83,6 +88,7 @@ struct Stats {
   unsigned long long absorbed, leaked, censused, splits, children;
   unsigned long long roulette_killed, roulette_survived;
   double w_source, w_absorbed, w_leaked, w_censused;
+  unsigned long long splits_dropped;
 };
 
 // Philox round keys of one seed: (k0 + r W0, k1 + r W1) for rounds r = 0..9,

@@ -208,7 +208,8 @@ __device__ __forceinline__ int bin_index(const DevProblem &P, int cell, int g, i
 // records and termination bookkeeping
 struct EndSink {
   double *w_end;        // shared [4]: source, absorbed, leaked, censused
-  uint32_t *n_end;      // shared [8]: absorbed, leaked, censused, roulette kill, survive, splits, children, histories
+  uint32_t *n_end;      // shared [9]: absorbed, leaked, censused, roulette kill, survive, splits,
+                        // children, histories, children not made (no room)
 };
 
 template <class PR, int DIM>
@@ -216,7 +217,7 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
                                        const PartOf<PR> &p, int end) {
   // analog runs carry weight 1 throughout: their weight sums are the counts
   // (filled in on the host), so only weighted runs add weights here
-  const bool weighted = P.ww_lower != nullptr;
+  const bool weighted = P.ww_lower != nullptr || P.implicit;
   if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); if (weighted) atomicAdd(&es.w_end[1], (double)p.w); }
   else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); if (weighted) atomicAdd(&es.w_end[2], (double)p.w); }
   else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); if (weighted) atomicAdd(&es.w_end[3], (double)p.w); }
@@ -261,7 +262,11 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
     const R nd = ceil(p.w / wu);
     const int n = nd > (R)P.ww_nmax ? P.ww_nmax : (int)nd;
     if (n > 1) {
+      // children go to the warp's stack, else to the device-wide spill bank;
+      // a child that finds no room is not made and the parent keeps its
+      // weight (splitting is optional, so the estimate stays unbiased)
       const R wc = p.w / (R)n;
+      int made = 0;
       for (int c = 1; c < n; ++c) {
         const U4 h = philox4x32_10_rk(0xFFFFFFFFu, p.serial, p.ctr, (uint32_t)c, A.rk);
         PartOf<PR> ch = p;
@@ -272,18 +277,22 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
         const int slot = atomicAdd(s_novf, 1);
         if (slot < A.overflow_cap) {
           ovf[slot] = ch;
-        } else if (A.spill_out != nullptr) {
-          atomicSub(s_novf, 1);   // not kept here: to the device-wide bank
-          const unsigned long long gs = atomicAdd(A.spill_out_count, 1ull);
-          if (gs < A.spill_cap) reinterpret_cast<PartOf<PR> *>(A.spill_out)[gs] = ch;
-          else atomicOr(A.error, ERRBIT_OVERFLOW);
+          made += 1;
         } else {
-          atomicOr(A.error, ERRBIT_OVERFLOW);
+          atomicSub(s_novf, 1);
+          if (A.spill_out != nullptr) {
+            const unsigned long long gs = atomicAdd(A.spill_out_count, 1ull);
+            if (gs < A.spill_cap) {
+              reinterpret_cast<PartOf<PR> *>(A.spill_out)[gs] = ch;
+              made += 1;
+            }
+          }
         }
       }
-      p.w = wc;
+      p.w = (made == n - 1) ? wc : p.w - (R)made * wc;
       atomicAdd(&es.n_end[5], 1u);
-      atomicAdd(&es.n_end[6], (uint32_t)(n - 1));
+      atomicAdd(&es.n_end[6], (uint32_t)made);
+      if (made < n - 1) atomicAdd(&es.n_end[8], (uint32_t)(n - 1 - made));
     }
     return true;
   }
@@ -463,8 +472,10 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     end = END_LEAKED;
     return OUT_DEAD;
   }
-  bin = bin_index(P, cell, p.g, p.tbin);
-  score = p.w * d;
+  if (P.estimator == 0) {         // track-length estimator
+    bin = bin_index(P, cell, p.g, p.tbin);
+    score = p.w * d;
+  }
 
   // move_particle (Figure "jitfunctions"): x += u d, t += d / v
   if constexpr (PR::kLocal) {
@@ -524,38 +535,68 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 }
 
 // collision: absorb or scatter, new group from the transfer CDF, isotropic
-// direction.  Returns true if the particle lives on.
+// direction.  Returns true if the particle lives on.  Collision estimator:
+// (cbin, cscore) is the arriving particle's score w / sigma_t.  Implicit
+// capture: the weight is multiplied by sigma_s / sigma_t (the removed part is
+// returned in wabs), a weight that reaches 0 ends as absorbed, and a weight
+// below the cutoff is rouletted after the scatter (one more block).
 template <class PR, int DIM>
 __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typename PR::R> &tb,
                                         const RunArgs &A, const EndSink &es,
                                         PartOf<PR> &p, int &end, LocalCount &lc,
-                                        int *s_novf, PartOf<PR> *ovf) {
+                                        int *s_novf, PartOf<PR> *ovf,
+                                        int &cbin, typename PR::R &cscore, double &wabs) {
   using R = typename PR::R;
   const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
   const int mg = m * P.G + p.g;
   p.ncol += 1;
   lc.col += 1;
+  if (P.estimator == 1) {
+    cbin = bin_index(P, cell, p.g, p.tbin);
+    cscore = p.w / tb.sigma_t[mg];
+  }
   const U4 r1 = draw(p, p.ctr, A.rk);
   const U4 r2 = draw(p, p.ctr, A.rk);
+  const R ratio = tb.scat[mg];
+  R xi1, xi2;
+  if constexpr (PR::kF64) { xi1 = u01_f64(r1.a, r1.b); xi2 = u01_f64(r1.c, r1.d); }
+  else { xi1 = u01_f32(r1.a); xi2 = u01_f32(r1.c); }
+  if (P.implicit) {
+    if constexpr (PR::kF64) wabs = p.w * (1.0 - ratio);
+    else wabs = (double)p.w * (1.0 - (double)ratio);
+    p.w *= ratio;
+    if (!(p.w > (R)0)) { end = END_ABSORBED; return false; }
+  } else if (!(xi1 < ratio)) {
+    end = END_ABSORBED;
+    return false;
+  }
+  p.g = sample_cdf<R>(tb.cdf + mg * P.G, P.G, xi2);
   if constexpr (PR::kF64) {
-    const double xi1 = u01_f64(r1.a, r1.b), xi2 = u01_f64(r1.c, r1.d);
-    if (!(xi1 < tb.scat[mg])) { end = END_ABSORBED; return false; }
-    p.g = sample_cdf<double>(tb.cdf + (int64_t)mg * P.G, P.G, xi2);
     const double two_pi = 6.283185307179586;
     const double mu = 2.0 * u01_f64(r2.a, r2.b) - 1.0;
     const double phi = two_pi * u01_f64(r2.c, r2.d);
     const double s = sqrt(1.0 - mu * mu);
     p.ux = mu; p.uy = s * cos(phi); p.uz = s * sin(phi);
   } else {
-    const float xi1 = u01_f32(r1.a), xi2 = u01_f32(r1.c);
-    if (!(xi1 < tb.scat[mg])) { end = END_ABSORBED; return false; }
-    p.g = sample_cdf<float>(tb.cdf + mg * P.G, P.G, xi2);
     const float mu = 2.0f * u01_f32(r2.a) - 1.0f;
     const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
     float sn, cs;
     sincospif(2.0f * u01_f32(r2.c), &sn, &cs);
     p.ux = mu; p.uy = s * cs; p.uz = s * sn;
+  }
+  if (P.implicit) {
+    R wcut, wsurv;
+    if constexpr (PR::kF64) { wcut = P.wcut; wsurv = P.wsurv; }
+    else { wcut = P.wcut32; wsurv = P.wsurv32; }
+    if (p.w < wcut) {
+      const U4 r = draw(p, p.ctr, A.rk);
+      R xi;
+      if constexpr (PR::kF64) xi = u01_f64(r.a, r.b); else xi = u01_f32(r.a);
+      if (!(xi < p.w / wsurv)) { end = END_ROULETTE; return false; }
+      p.w = wsurv;
+      atomicAdd(&es.n_end[4], 1u);
+    }
   }
   if (!weight_window<PR, DIM>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
   return true;
@@ -684,7 +725,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   __shared__ int s_done, s_batch;
   __shared__ int s_novf[16];
   __shared__ double s_w[4];
-  __shared__ uint32_t s_n[8];
+  __shared__ uint32_t s_n[9];
   __shared__ double s_red[16];
 
   // ---- tables of the current problem into shared memory
@@ -712,7 +753,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     for (long long q = tid; q < P.n_bins; q += nth) stally[q] = (TT)0;
   if (tid < 16) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
-  if (tid < 8) s_n[tid] = 0u;
+  if (tid < 9) s_n[tid] = 0u;
   if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }
   __syncthreads();
 
@@ -794,10 +835,19 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           __syncwarp();   // every parked particle is read before survivors are written
           ctop -= n;
           bool alive = false;
+          int cbin = -1;
+          R cscore = (R)0;
+          double wabs = 0.0;
           if (mine) {
             int end = END_NONE;
-            alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf);
+            alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
+          }
+          if (P.estimator == 1) tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine, cbin, cscore);
+          if (P.implicit) {
+            // weight removed by implicit capture: one shared add per warp
+            for (int o = 16; o > 0; o >>= 1) wabs += __shfl_xor_sync(0xffffffffu, wabs, o);
+            if (lane == 0) atomicAdd(&s_w[1], wabs);
           }
           const uint32_t am = __ballot_sync(0xffffffffu, alive);
           if (alive) bk.store(slot_of(rtop + __popc(am & lt)), q, DIM);
@@ -858,7 +908,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             alive = true;
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
-            if (P.ww_lower != nullptr) atomicAdd(&s_w[0], 1.0);
+            if (P.ww_lower != nullptr || P.implicit) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
@@ -985,6 +1035,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     atomicAdd(&stats->splits, (unsigned long long)s_n[5]);
     atomicAdd(&stats->children, (unsigned long long)s_n[6]);
     atomicAdd(&stats->histories, (unsigned long long)s_n[7]);
+    atomicAdd(&stats->splits_dropped, (unsigned long long)s_n[8]);
     atomicAdd(&stats->w_source, s_w[0]);
     atomicAdd(&stats->w_absorbed, s_w[1]);
     atomicAdd(&stats->w_leaked, s_w[2]);

@@ -25,6 +25,7 @@ MCDC_ERR_INVALID, MCDC_ERR_OOM, MCDC_ERR_CUDA = -1, -2, -3
 MCDC_ERR_BANK_OVERFLOW, MCDC_ERR_TIMEOUT, MCDC_ERR_NO_DEVICE = -4, -5, -6
 PREC_FP64, PREC_FP32, PREC_FP32_LOCAL = 0, 1, 2
 TALLY_AUTO, TALLY_SHARED, TALLY_GLOBAL = 0, 1, 2
+EST_TRACK, EST_COLLISION = 0, 1
 
 
 class mcdc_mesh(C.Structure):
@@ -55,7 +56,9 @@ class mcdc_options(C.Structure):
                 ("block_size", C.c_int32), ("bank_per_cta", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("warp_aggregate", C.c_int32),
                 ("autotune", C.c_int32), ("overflow_per_cta", C.c_int32),
-                ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3)]
+                ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
+                ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
+                ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double)]
 
 
 class mcdc_stats(C.Structure):
@@ -65,7 +68,7 @@ class mcdc_stats(C.Structure):
         (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused",
                                   "kernel_ms", "total_ms")] + [
         (k, C.c_int32) for k in ("block_size", "bank_per_cta", "ctas_per_sm", "tally_mode",
-                                 "n_batches", "warp_aggregate")]
+                                 "n_batches", "warp_aggregate")] + [("splits_dropped", C.c_uint64)]
 
 
 class mcdc_record(C.Structure):
@@ -187,7 +190,9 @@ class Problem:
 
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
-                 overflow_per_cta=0, region=None):
+                 overflow_per_cta=0, region=None, estimator=0, implicit=None):
+        """estimator: EST_TRACK or EST_COLLISION; implicit: None (analog
+        collisions) or (weight cutoff, survival weight) for implicit capture."""
         self.desc = prob
         keep = []
 
@@ -233,6 +238,10 @@ class Problem:
         lo, hi = region if region is not None else (prob.region_lo, prob.region_hi)
         o.region_lo[:] = [int(v) for v in lo]
         o.region_hi[:] = [int(v) for v in hi]
+        o.estimator = int(estimator)
+        if implicit is not None:
+            o.implicit_capture = 1
+            o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])
         h = C.c_void_p()
         check(mcdc_problem_create(C.byref(m), C.byref(mt), C.byref(s), C.byref(tg), C.byref(o),
                                   C.byref(h)))

@@ -99,6 +99,30 @@ def test_invalid_problems_rejected_on_host(lib, case):
     assert code == lib.MCDC_ERR_INVALID, (code, msg)
 
 
+@pytest.mark.parametrize("case", ["unknown_estimator", "cutoff_above_survival", "zero_cutoff",
+                                  "closed_steady_pure_scatterer", "closed_steady_void"])
+def test_invalid_options_rejected_on_host(lib, case):
+    p, kw = W.c2_two_region(), {}
+    if case == "unknown_estimator":
+        kw["estimator"] = 2
+    elif case == "cutoff_above_survival":
+        kw["implicit"] = (0.5, 0.25)
+    elif case == "zero_cutoff":
+        kw["implicit"] = (0.0, 0.5)
+    else:
+        # steady state, every face reflecting: only absorption can end a history
+        mat = np.zeros((2, 2, 2), np.uint8)
+        c = 1.0 if case == "closed_steady_pure_scatterer" else 0.0
+        st = 1.0 if case == "closed_steady_pure_scatterer" else 0.0
+        p = W.box("closed", (2, 2, 2), (1.0, 1.0, 1.0), mat, [[st]], [[c]], np.ones((1, 1, 1)),
+                  [1.0], (0.0,) * 3, (2.0,) * 3, None, (0, 0, 0), (2, 2, 2),
+                  bc=(W.BC_REFLECT,) * 6)
+    code, msg = _create(lib, p, **kw)
+    assert code == lib.MCDC_ERR_INVALID, (code, msg)
+    if case.startswith("closed"):
+        assert "reflecting" in msg, msg
+
+
 def test_valid_problem_without_gpu_reports_no_device(lib):
     import torch
     if torch.cuda.is_available():

@@ -12,10 +12,10 @@ import pytest
 
 from oracle import oracle as O
 from paper_2409_04668_b300 import workloads as W
+from parity_util import (REL_TALLY, compare_counts, compare_records, compare_tallies,
+                         small_channel)
 
 pytestmark = pytest.mark.gpu
-
-REL_TALLY = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -26,49 +26,6 @@ def mcdc():
     build.build()
     from paper_2409_04668_b300 import mcdc as M
     return M
-
-
-def small_channel(n=12, G=7, T=8, seed=3):
-    """A scaled-down copy of the channel problem: same materials, groups,
-    speeds and time grid shape on an n^3 mesh."""
-    full = W.c3_channel(seed)
-    f = 60 // n
-    mat = full.material[::f, ::f, ::f].copy()
-    return W.box("channel_small", (n, n, n), (1.0 * f,) * 3, mat, full.sigma_t, full.sigma_s /
-                 full.sigma_t, full.transfer, full.speed, (0.0,) * 3, (10.0,) * 3,
-                 np.linspace(0.0, 1e-6, T + 1), (n // 2,) * 3, (n,) * 3)
-
-
-def compare_records(gpu, orc, dim):
-    assert np.array_equal(gpu["hid"], orc["hid"])
-    for f in ("end", "g", "ctr", "n_seg", "n_col", "n_cross"):
-        bad = np.nonzero(gpu[f] != orc[f])[0]
-        assert bad.size == 0, (f, bad[:10], gpu[f][bad[:5]], orc[f][bad[:5]])
-    axes = ("x", "t") if dim == 1 else ("x", "y", "z", "t")
-    for f in axes:
-        np.testing.assert_allclose(gpu[f], orc[f], rtol=1e-12, atol=1e-12 * (1 + np.abs(orc[f]).max()))
-    np.testing.assert_allclose(gpu["w"], orc["w"], rtol=1e-12)
-
-
-def compare_tallies(g, o):
-    for key in ("sum1", "sum2"):
-        a, b = g[key], o[key]
-        scale = np.maximum(np.abs(b), 1e-300)
-        rel = np.abs(a - b) / scale
-        assert np.all((rel <= REL_TALLY) | (np.abs(a - b) <= 1e-300)), (key, rel.max())
-    nz = o["mean"] != 0
-    np.testing.assert_allclose(g["mean"][nz], o["mean"][nz], rtol=REL_TALLY)
-    np.testing.assert_array_equal(g["mean"] == 0, o["mean"] == 0)
-    np.testing.assert_allclose(g["relerr"], o["relerr"], rtol=1e-6, atol=1e-12)
-
-
-COUNT_KEYS = ("histories", "segments", "collisions", "crossings", "census", "absorbed", "leaked",
-              "censused", "splits", "children", "roulette_killed", "roulette_survived")
-
-
-def compare_counts(g, o):
-    for k in COUNT_KEYS:
-        assert g[k] == o[k], (k, g[k], o[k])
 
 
 @pytest.mark.parametrize("mode", ["shared", "global"])
