@@ -70,6 +70,9 @@ typedef struct {
     int32_t implicit_capture;  /* 1: survival biasing at collisions              */
     double weight_cutoff;      /* implicit capture: roulette below this weight   */
     double cutoff_survival;    /*   ... surviving with this weight               */
+
+    int32_t pc_target;         /* population control: particles per batch after
+                                  each comb at an interior census edge; 0 = off */
 } orc_problem;
 
 typedef struct {
@@ -77,6 +80,8 @@ typedef struct {
     uint64_t absorbed, leaked, censused, splits, children;
     uint64_t roulette_killed, roulette_survived;
     double w_source, w_absorbed, w_leaked, w_censused;
+    uint64_t pc_combs, pc_in, pc_out;      /* combs, particles in, particles out */
+    double w_pc_in, w_pc_out;              /* weight into and out of the combs   */
 } orc_counts;
 
 /* Summary of one primary particle (serial 0) of one history. */
@@ -90,6 +95,11 @@ typedef struct {
     uint32_t n_cross;
     double x, y, z, t, w;
 } orc_record;
+
+/* The comb of population control: n particles of weights w (in their bank
+ * order) -> M teeth at (k + xi) W / M, W = sum w; sel[k] = the particle whose
+ * cumulative-weight interval [S_i, S_i + w_i) holds tooth k. */
+void orc_comb(int64_t n, const double *w, int64_t M, double xi, int64_t *sel);
 
 /* Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

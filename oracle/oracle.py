@@ -31,6 +31,7 @@ class OrcProblem(C.Structure):
         ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
         ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
         ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
+        ("pc_target", C.c_int32),
     ]
 
 
@@ -38,7 +39,9 @@ class OrcCounts(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in (
         "histories", "segments", "collisions", "crossings", "census", "absorbed", "leaked",
         "censused", "splits", "children", "roulette_killed", "roulette_survived")] + [
-        (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused")]
+        (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused")] + [
+        (k, C.c_uint64) for k in ("pc_combs", "pc_in", "pc_out")] + [
+        (k, C.c_double) for k in ("w_pc_in", "w_pc_out")]
 
 
 RECORD_DTYPE = np.dtype([
@@ -68,6 +71,7 @@ def lib():
         L.orc_trace.argtypes = [C.POINTER(OrcProblem), C.c_uint64, C.c_void_p, C.c_int64,
                                 C.c_void_p]
         L.orc_trace.restype = C.c_int
+        L.orc_comb.argtypes = [C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]
         if hasattr(L, "orc_mlp_forward"):
             _bind_mlp(L)
         _lib = L
@@ -101,8 +105,9 @@ class _Keep:
         return a.ctypes.data
 
 
-def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None):
-    """implicit: None (analog collisions) or (weight cutoff, survival weight)."""
+def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None, pc_target=0):
+    """implicit: None (analog collisions) or (weight cutoff, survival weight);
+    pc_target: particles per batch after each census comb (0: no comb)."""
     s = OrcProblem()
     s.n[:] = list(prob.n)
     s.origin[:] = [float(v) for v in prob.origin]
@@ -135,6 +140,7 @@ def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None):
     s.region_lo[:] = list(prob.region_lo)
     s.region_hi[:] = list(prob.region_hi)
     s.estimator = int(estimator)
+    s.pc_target = int(pc_target)
     if implicit is not None:
         s.implicit_capture = 1
         s.weight_cutoff, s.cutoff_survival = float(implicit[0]), float(implicit[1])
@@ -153,14 +159,15 @@ def tally_shape(prob):
 
 
 def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=EST_TRACK,
-        implicit=None):
+        implicit=None, pc_target=0):
     """Runs histories [offset, offset+n); returns mean/relerr/sums shaped
     [nz, ny, nx, G, T], the region scalar and the event counts.  estimator:
     EST_TRACK (track length) or EST_COLLISION; implicit: None or (weight
-    cutoff, survival weight) for implicit capture."""
+    cutoff, survival weight) for implicit capture; pc_target: population
+    control, particles per batch after each comb at an interior census edge."""
     L = lib()
     keep = _Keep()
-    s = _struct(prob, ww, keep, estimator, implicit)
+    s = _struct(prob, ww, keep, estimator, implicit, pc_target)
     nb = n_bins(prob)
     mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
     scalar = np.zeros(2)
@@ -179,17 +186,26 @@ def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=ES
             "threads": int(threads)}
 
 
-def trace(prob, seed, hids, ww=None, implicit=None):
-    """Per-history summary of the primary particle of each listed history."""
+def trace(prob, seed, hids, ww=None, implicit=None, pc_target=0):
+    """Per-history summary of the primary particle of each listed history
+    (refused under population control, where histories mix)."""
     L = lib()
     keep = _Keep()
-    s = _struct(prob, ww, keep, EST_TRACK, implicit)
+    s = _struct(prob, ww, keep, EST_TRACK, implicit, pc_target)
     h = np.ascontiguousarray(hids, dtype=np.uint64)
     out = np.zeros(len(h), dtype=RECORD_DTYPE)
     rc = L.orc_trace(C.byref(s), int(seed), h.ctypes.data, len(h), out.ctypes.data)
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return out
+
+
+def comb(weights, M, xi):
+    """Indices of the particles the M teeth of a comb with offset xi pick."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    sel = np.zeros(int(M), dtype=np.int64)
+    lib().orc_comb(w.size, w.ctypes.data, int(M), float(xi), sel.ctypes.data)
+    return sel
 
 
 def philox(ctr, key):

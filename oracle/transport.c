@@ -41,6 +41,18 @@
  *     then goes unused).  After the scatter a weight below the cutoff w_c is
  *     rouletted: it survives with probability w / w_s at weight w_s (one more
  *     block), else the history branch ends.  Weight windows, if any, follow.
+ *  R13 population control (optional; needs every source particle born in the
+ *     first time bin and no weight windows): each batch is one time-stepped
+ *     simulation.  Step j transports the batch's bank until every particle
+ *     has ended or reached the census edge t_{j+1}; particles at an interior
+ *     edge are banked.  The bank, ordered by (history id, serial), is combed
+ *     to M particles of weight W/M (W = the bank's weight): tooth k at
+ *     (k + xi) W/M picks the particle whose cumulative-weight interval holds
+ *     it, xi = U from the block (key seed; counter 0xFFFFFFFC, j, first
+ *     history id of the batch lo, hi).  Tooth k's particle keeps the parent's
+ *     state and history id, takes serial = word 0 of the block (key seed;
+ *     counter 0xFFFFFFFD, parent serial, j, k) and restarts its counter.
+ *     The next step runs the combed bank.
  */
 #include <math.h>
 #include <pthread.h>
@@ -62,6 +74,7 @@ typedef struct {
     uint32_t serial;       /* particle id inside the history (0 = primary) */
     uint32_t ctr;          /* event counter of the random stream           */
     uint32_t n_seg, n_col, n_cross;
+    uint64_t hid;          /* history the particle belongs to (its stream)  */
 } part;
 
 typedef struct {
@@ -174,6 +187,7 @@ static part source_particle(const orc_problem *p, const tables *tb,
     memset(&P, 0, sizeof P);
     P.serial = 0;
     P.ctr = 0;
+    P.hid = hid;
     pair r0 = draw(seed, hid, &P);   /* x, y        */
     pair r1 = draw(seed, hid, &P);   /* z, group    */
     pair r2 = draw(seed, hid, &P);   /* mu, phi     */
@@ -248,6 +262,10 @@ static int weight_window(const orc_problem *p, const tables *tb, uint64_t seed,
     return 1;
 }
 
+/* internal return of transport(): reached an interior census edge with
+ * population control on (not an end of the history) */
+enum { BANKED = 100 };
+
 /* ---- one particle until its history branch ends -------------------- */
 static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
                          uint64_t hid, part *P, double *tally, stack *bank,
@@ -312,6 +330,7 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
                 c->w_censused += P->w;
                 return ORC_END_CENSUSED;
             }
+            if (p->pc_target > 0) return BANKED;     /* R13: wait for the comb */
         } else if (ev == ORC_EV_SURFACE) {
             double u = *dir(P, ax);
             *pos(P, ax) = face(p, ax, P->idx[ax], u);
@@ -406,6 +425,85 @@ static void run_history(const orc_problem *p, const tables *tb, uint64_t seed,
     free(bank.items);
 }
 
+/* ---- population control (R13) ---------------------------------------- */
+void orc_comb(int64_t n, const double *w, int64_t M, double xi, int64_t *sel)
+{
+    double W = 0.0;
+    for (int64_t i = 0; i < n; ++i) W += w[i];
+    double S = 0.0;          /* cumulative weight before particle i */
+    int64_t i = 0;
+    for (int64_t k = 0; k < M; ++k) {
+        double tooth = ((double)k + xi) * (W / (double)M);
+        while (i < n - 1 && S + w[i] <= tooth) { S += w[i]; ++i; }
+        sel[k] = i;
+    }
+}
+
+static int by_history_then_serial(const void *a, const void *b)
+{
+    const part *x = (const part *)a, *y = (const part *)b;
+    if (x->hid != y->hid) return x->hid < y->hid ? -1 : 1;
+    if (x->serial != y->serial) return x->serial < y->serial ? -1 : 1;
+    return 0;
+}
+
+/* One batch [h0, h1) as a time-stepped simulation with a comb at every
+ * interior census edge.  All source particles are born in the first bin. */
+static void run_batch_pc(const orc_problem *p, const tables *tb, uint64_t seed, uint64_t h0,
+                         uint64_t h1, double *tally, orc_counts *c)
+{
+    const int64_t M = p->pc_target;
+    int64_t cap = (int64_t)(h1 - h0) > M ? (int64_t)(h1 - h0) : M;
+    part *bank = (part *)malloc(sizeof(part) * (size_t)(cap > 0 ? cap : 1));
+    part *cen = (part *)malloc(sizeof(part) * (size_t)(cap > 0 ? cap : 1));
+    double *w = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    int64_t *sel = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1));
+    int64_t n = 0;
+    stack none = { NULL, 0, 0 };      /* weight windows are off: no children */
+    for (uint64_t h = h0; h < h1; ++h) {
+        part P = source_particle(p, tb, seed, h);
+        c->histories += 1;
+        c->w_source += P.w;
+        bank[n++] = P;
+    }
+    for (int32_t j = 0; j < p->n_tbin && n > 0; ++j) {
+        int64_t nc = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            part Q = bank[i];
+            int32_t end = transport(p, tb, seed, Q.hid, &Q, tally, &none, c);
+            if (end == BANKED) cen[nc++] = Q;
+        }
+        if (nc == 0) break;
+        /* the comb: bank order (history id, serial), M teeth, new streams */
+        qsort(cen, (size_t)nc, sizeof(part), by_history_then_serial);
+        uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+        uint32_t cx[4] = { 0xFFFFFFFCu, (uint32_t)j, (uint32_t)h0, (uint32_t)(h0 >> 32) };
+        uint32_t ox[4];
+        orc_philox4x32_10(cx, key, ox);
+        double xi = orc_uniform(ox[0], ox[1]);
+        double W = 0.0;
+        for (int64_t i = 0; i < nc; ++i) { w[i] = cen[i].w; W += cen[i].w; }
+        orc_comb(nc, w, M, xi, sel);
+        c->pc_combs += 1;
+        c->pc_in += (uint64_t)nc;
+        c->pc_out += (uint64_t)M;
+        c->w_pc_in += W;
+        for (int64_t k = 0; k < M; ++k) {
+            part Q = cen[sel[k]];
+            uint32_t cs[4] = { 0xFFFFFFFDu, Q.serial, (uint32_t)j, (uint32_t)k };
+            uint32_t os[4];
+            orc_philox4x32_10(cs, key, os);
+            Q.serial = os[0];
+            Q.ctr = 0;
+            Q.w = W / (double)M;
+            c->w_pc_out += Q.w;
+            bank[k] = Q;
+        }
+        n = M;
+    }
+    free(bank); free(cen); free(w); free(sel);
+}
+
 /* ---- problem checks and derived tables -------------------------------- */
 static int make_tables(const orc_problem *p, tables *tb)
 {
@@ -440,6 +538,9 @@ static int make_tables(const orc_problem *p, tables *tb)
     if (p->estimator != ORC_EST_TRACK && p->estimator != ORC_EST_COLLISION) return -1;
     if (p->implicit_capture &&
         !(p->weight_cutoff > 0.0 && p->cutoff_survival > p->weight_cutoff)) return -1;
+    if (p->pc_target < 0) return -1;
+    if (p->pc_target > 0 &&
+        (p->n_tbin < 2 || p->ww_lower != NULL || !(p->src_t1 < p->edges[1]))) return -1;
     for (int64_t c = 0; c < tb->n_cells; ++c)
         if (p->material[c] >= M) return -1;
     return 0;
@@ -488,8 +589,11 @@ static void *work(void *arg)
     for (int32_t b = wk->tid; b < wk->B; b += wk->nthreads) {
         memset(tally, 0, (size_t)tb->n_bins * sizeof(double));
         uint64_t h0 = batch_start(wk->n, wk->B, b), h1 = batch_start(wk->n, wk->B, b + 1);
-        for (uint64_t h = h0; h < h1; ++h)
-            run_history(wk->p, tb, wk->seed, wk->offset + h, tally, &wk->c, NULL);
+        if (wk->p->pc_target > 0)
+            run_batch_pc(wk->p, tb, wk->seed, wk->offset + h0, wk->offset + h1, tally, &wk->c);
+        else
+            for (uint64_t h = h0; h < h1; ++h)
+                run_history(wk->p, tb, wk->seed, wk->offset + h, tally, &wk->c, NULL);
         double region = 0.0;
         for (int64_t k = 0; k < tb->n_bins; ++k) {
             wk->s1[k] += tally[k];
@@ -513,6 +617,8 @@ static void add_counts(orc_counts *a, const orc_counts *b)
     a->roulette_survived += b->roulette_survived;
     a->w_source += b->w_source; a->w_absorbed += b->w_absorbed;
     a->w_leaked += b->w_leaked; a->w_censused += b->w_censused;
+    a->pc_combs += b->pc_combs; a->pc_in += b->pc_in; a->pc_out += b->pc_out;
+    a->w_pc_in += b->w_pc_in; a->w_pc_out += b->w_pc_out;
 }
 
 /* mean and relative error from batch sums: m_b = B s_b / (N V) */
@@ -580,6 +686,7 @@ int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
               int64_t n, orc_record *out)
 {
     tables tb;
+    if (p->pc_target > 0) return -1;     /* histories are not separate under a comb */
     if (make_tables(p, &tb) != 0) { free_tables(&tb); return -1; }
     double *tally = (double *)calloc((size_t)tb.n_bins, sizeof(double));
     orc_counts c;
