@@ -369,19 +369,22 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     """The headline workload in the other modes of the tracker: device-timed
     histories/s and the region scalar's figure of merit 1/(relerr^2 T) for
     the cell-local FP32 mode and, in the headline precision, for the
-    collision estimator and for implicit capture (weight cutoff 0.25,
-    survival weight 0.5)."""
+    collision estimator, for implicit capture (weight cutoff 0.25,
+    survival weight 0.5) and for population control (32 batches, each combed
+    back to its own size at every interior time edge)."""
     prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
     modes = {"track_analog": {"precision": prec},
              "fp32_local": {"precision": M.PREC_FP32_LOCAL},
              "collision_estimator": {"precision": prec, "estimator": M.EST_COLLISION},
-             "implicit_capture": {"precision": prec, "implicit": (0.25, 0.5)}}
+             "implicit_capture": {"precision": prec, "implicit": (0.25, 0.5)},
+             "population_control": {"precision": prec, "pc_target": n_hist // 32}}
     out = {}
     for name, kw in modes.items():
         with M.Problem(prob, block_size=args.block, **kw) as Q:
+            nb = 32 if "pc_target" in kw else args.batches
             def one(s):
                 st, sc = Q.run_ex(n_hist, seed=1, offset=history_offset(0, s, n_hist),
-                                  batches=args.batches, mean=mean, relerr=rel,
+                                  batches=nb, mean=mean, relerr=rel,
                                   stream=stream.cuda_stream, want_scalar=True, want_stats=True)
                 return st, sc
             for s in range(args.warmup):

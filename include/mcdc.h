@@ -144,6 +144,13 @@ typedef struct mcdc_options {
                                    collision is rouletted (default 0.25) ...      */
     double cutoff_survival;     /*   ... surviving with this weight (default 0.5);
                                    need 0 < weight_cutoff < cutoff_survival       */
+    int32_t pc_target;          /* population control: 0 off; else every batch runs
+                                   as a time-stepped simulation whose census bank
+                                   (particles reaching an interior time edge) is
+                                   combed to pc_target particles of equal weight.
+                                   Needs >= 2 time bins, every source particle
+                                   born in the first bin, the global tally, no
+                                   weight windows and no per-history records      */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */
@@ -159,6 +166,9 @@ typedef struct mcdc_stats {
                                    stack and the spill bank were full: the parent
                                    kept their weight (unbiased, less variance
                                    reduction)                                   */
+    uint64_t pc_combs, pc_in, pc_out;   /* population control: combs, particles
+                                           into and out of them             */
+    double w_pc_in, w_pc_out;           /* weight into and out of the combs */
 } mcdc_stats;
 
 /* Per-history summary of the primary particle (serial 0), for checking a run

@@ -20,7 +20,7 @@ NVCC = os.environ.get("NVCC", shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
-NO_FMA = {"track_fp64.cu", "misc.cu"}
+NO_FMA = {"track_fp64.cu", "misc.cu", "comb.cu"}
 
 
 def sources():

@@ -13,6 +13,7 @@
 
 #include "../../include/mcdc.h"
 #include "launch.h"
+#include "comb.h"
 #include "problem.h"
 #include "tracker.cuh"
 
@@ -204,6 +205,38 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
   return B;
 }
 
+// Population control buffers for a census bank of up to cap particles.
+int ensure_pc(mcdc_problem *pr, int cap) {
+  if (pr->pc_cap >= cap) return MCDC_OK;
+  const size_t pb = part_bytes(pr->key);
+  int rc;
+  unsigned char *bank = nullptr, *combed = nullptr;
+  if ((rc = dalloc(pr, &bank, pb * (size_t)cap))) return rc;
+  if (!pr->pc_combed) {
+    if ((rc = dalloc(pr, &combed, pb * (size_t)pr->P.pc_target))) return rc;
+    pr->pc_combed = combed;
+  }
+  if (!pr->pc_cnt && (rc = dalloc(pr, &pr->pc_cnt, 4))) return rc;
+  for (int q = 0; q < 2; ++q) {
+    if ((rc = dalloc(pr, &pr->pc_keys[q], (size_t)cap))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_idx[q], (size_t)cap))) return rc;
+  }
+  if ((rc = dalloc(pr, &pr->pc_w, (size_t)cap))) return rc;
+  if ((rc = dalloc(pr, &pr->pc_S, (size_t)cap))) return rc;
+  const size_t tb = comb_temp_bytes(cap);
+  unsigned char *temp = nullptr;
+  if ((rc = dalloc(pr, &temp, tb))) return rc;
+  if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCDC_ERR_OOM, "cudaMallocHost failed");
+  }
+  pr->pc_bank = bank;
+  pr->pc_temp = temp;
+  pr->pc_temp_bytes = tb;
+  pr->pc_cap = cap;
+  return MCDC_OK;
+}
+
 int ensure_work_slots(mcdc_problem *pr, int n) {
   if (pr->work_slots >= n) return MCDC_OK;
   unsigned long long *w = nullptr;
@@ -371,6 +404,9 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (o.implicit_capture &&
       !(std::isfinite(o.cutoff_survival) && o.weight_cutoff > 0.0 && o.cutoff_survival > o.weight_cutoff))
     return fail(MCDC_ERR_INVALID, "implicit capture needs 0 < weight_cutoff < cutoff_survival");
+  if (o.pc_target < 0) return fail(MCDC_ERR_INVALID, "pc_target must be >= 0");
+  if (o.pc_target > 0 && o.tally_mode == MCDC_TALLY_SHARED)
+    return fail(MCDC_ERR_INVALID, "population control runs on the global tally");
 
   // ---- mesh
   const int n[3] = {mesh->nx, mesh->ny, mesh->nz};
@@ -465,6 +501,9 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (!std::isfinite(src->t0) || !std::isfinite(src->t1) || src->t1 < src->t0)
     return fail(MCDC_ERR_INVALID, "need finite t0 <= t1");
   if (T > 0 && src->t0 < edges[0]) return fail(MCDC_ERR_INVALID, "source starts before the first time edge");
+  if (o.pc_target > 0 && (T < 2 || !(src->t1 < edges[1])))
+    return fail(MCDC_ERR_INVALID, "population control needs >= 2 time bins and every source "
+                                  "particle born in the first bin");
   if (T == 0) {
     // steady state closed by reflecting faces: only absorption ends a history
     bool open = false;
@@ -534,6 +573,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   P.wsurv = o.cutoff_survival;
   P.wcut32 = (float)o.weight_cutoff;
   P.wsurv32 = (float)o.cutoff_survival;
+  P.pc_target = o.pc_target;
+  if (o.pc_target > 0) pr->opt.tally_mode = MCDC_TALLY_GLOBAL;
   for (int a = 0; a < 3; ++a) {
     int hi = o.region_hi[a] > 0 ? o.region_hi[a] : n[a];
     int lo = std::max(0, o.region_lo[a]);
@@ -611,7 +652,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_bins);
     if (e != cudaSuccess) { fail(MCDC_ERR_CUDA, cudaGetErrorString(e)); return bail(MCDC_ERR_CUDA); }
   }
-  if (o.autotune && o.block_size == 0) {
+  if (o.autotune && o.block_size == 0 && o.pc_target == 0) {
     if ((rc = autotune(pr, dl))) return bail(rc);
   }
   *out = pr;
@@ -631,6 +672,8 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
     pr->P.ww_lower32 = nullptr;
     return MCDC_OK;
   }
+  if (pr->P.pc_target > 0)
+    return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
   if (!(upper_ratio > survival_ratio && survival_ratio > 1.0) || nmax < 2 || nmax > 1024)
     return fail(MCDC_ERR_INVALID, "need 1 < survival_ratio < upper_ratio and 2 <= nmax <= 1024");
   CK(cudaSetDevice(pr->device));
@@ -676,6 +719,8 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   const bool s1_dev = is_device_ptr(a->sum1_out), s2_dev = is_device_ptr(a->sum2_out);
   const bool rec_dev = is_device_ptr(a->records);
   if (a->records && a->n_records == 0) return fail(MCDC_ERR_INVALID, "records given with n_records == 0");
+  if (a->records && P.pc_target > 0)
+    return fail(MCDC_ERR_INVALID, "no per-history records under population control (histories mix)");
   if ((a->mean_out && !mean_dev) || (a->relerr_out && !rel_dev)) {
     if (!pr->mean_tmp) {
       int rc;
@@ -730,6 +775,63 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     A.batch = 0;
     A.chunk = 0;
     CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+  } else if (P.pc_target > 0) {
+    // population control: every batch is a time-stepped simulation; after
+    // each step the census bank is combed and the next step runs it
+    const int M = P.pc_target;
+    const uint64_t bmax = a->n_histories / (uint64_t)B + 1;
+    if (int rc = ensure_pc(pr, (int)std::max<uint64_t>(bmax, (uint64_t)M))) return rc;
+    for (int b = 0; b < B; ++b) {
+      A.work = pr->work + b;
+      A.batch = b;
+      const uint64_t nb_hist = a->n_histories / B + 1;
+      A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));
+      A.spill_in = nullptr;
+      A.spill_out = nullptr;
+      A.census_out = pr->pc_bank;
+      A.census_count = pr->pc_cnt;
+      A.census_cap = (unsigned long long)pr->pc_cap;
+      const uint64_t b0 = batch_start(a->n_histories, B, b);
+      const uint64_t nbh = batch_start(a->n_histories, B, b + 1) - b0;
+      int key_bits = 33;
+      while (key_bits < 64 && (1ull << (key_bits - 32)) < nbh) ++key_bits;
+      for (int step = 0;; ++step) {
+        CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
+        CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+        if (step >= P.T - 1) break;
+        CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const unsigned long long n = *pr->h_spill;
+        if (n == 0) break;
+        if (n > (unsigned long long)pr->pc_cap)
+          return fail(MCDC_ERR_BANK_OVERFLOW, "census bank overflow under population control");
+        CombArgs c{};
+        c.bank = pr->pc_bank;
+        c.n = (int)n;
+        c.out = pr->pc_combed;
+        c.M = M;
+        c.out_count = pr->pc_cnt + 1;
+        c.h0 = a->hist_offset + b0;
+        c.step = step;
+        c.rk = A.rk;
+        c.key_bits = key_bits;
+        c.keys[0] = pr->pc_keys[0]; c.keys[1] = pr->pc_keys[1];
+        c.idx[0] = pr->pc_idx[0]; c.idx[1] = pr->pc_idx[1];
+        c.w = pr->pc_w;
+        c.S = pr->pc_S;
+        c.temp = pr->pc_temp;
+        c.temp_bytes = pr->pc_temp_bytes;
+        c.stats = pr->stats;
+        CK(comb_bank(pr->key, s, c));
+        CK(cudaMemsetAsync(pr->pc_cnt + 2, 0, sizeof(unsigned long long), s));
+        A.spill_in = pr->pc_combed;
+        A.spill_in_count = pr->pc_cnt + 1;
+        A.spill_in_cursor = pr->pc_cnt + 2;
+        A.spill_cap = (unsigned long long)M;
+      }
+      CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+    }
   } else {
     const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
     for (int b = 0; b < B; ++b) {
@@ -811,10 +913,12 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
     stats->splits = h.splits; stats->children = h.children;
     stats->splits_dropped = h.splits_dropped;
+    stats->pc_combs = h.pc_combs; stats->pc_in = h.pc_in; stats->pc_out = h.pc_out;
+    stats->w_pc_in = h.w_pc_in; stats->w_pc_out = h.w_pc_out;
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
     stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
-    if (P.ww_lower == nullptr && !P.implicit) {   // analog: every weight is 1
+    if (P.ww_lower == nullptr && !P.implicit && P.pc_target == 0) {   // analog: every weight is 1
       stats->w_source = (double)h.histories;
       stats->w_absorbed = (double)h.absorbed;
       stats->w_leaked = (double)h.leaked;

@@ -112,8 +112,8 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
     if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
         p->dim != p0->dim)
       return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
-    if (p->P.ww_lower != nullptr || p->P.implicit)
-      return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, no implicit capture)");
+    if (p->P.ww_lower != nullptr || p->P.implicit || p->P.pc_target > 0)
+      return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
     if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
   }
   CKB(cudaSetDevice(p0->device));

@@ -54,6 +54,7 @@ struct DevProblem {
   int32_t implicit;           // 1: implicit capture with weight-cutoff roulette
   double wcut, wsurv;         // cutoff and survival weight (implicit capture)
   float wcut32, wsurv32;
+  int32_t pc_target;          // population control: particles per batch after a comb (0: off)
 };
 
 // One particle as it moves between the tracker phases (kept in registers).
@@ -89,6 +90,8 @@ struct Stats {
   unsigned long long roulette_killed, roulette_survived;
   double w_source, w_absorbed, w_leaked, w_censused;
   unsigned long long splits_dropped;
+  unsigned long long pc_combs, pc_in, pc_out;
+  double w_pc_in, w_pc_out;
 };
 
 // Philox round keys of one seed: (k0 + r W0, k1 + r W1) for rounds r = 0..9,
@@ -127,6 +130,11 @@ struct RunArgs {
   const void *spill_in;       // bank this pass runs instead of new histories
   const unsigned long long *spill_in_count;
   unsigned long long *spill_in_cursor;
+  // population control: particles reaching an interior census edge are
+  // appended here instead of flying on (nullptr: off)
+  void *census_out;
+  unsigned long long *census_count;
+  unsigned long long census_cap;
 };
 
 // ---- counter-based generator: Philox4x32-10 (Salmon et al., SC'11) -------

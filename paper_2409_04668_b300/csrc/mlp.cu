@@ -673,6 +673,8 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
                                      const double *pilot_relerr, const mcdc_mlp_options *opt,
                                      mcdc_mlp_report *rep) {
   if (!pr || !pilot_mean) return fail(MCDC_ERR_INVALID, "problem and pilot tally are required");
+  if (pr->P.pc_target > 0)
+    return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
   mcdc_mlp_options o;
   if (opt) o = *opt; else mcdc_default_mlp_options(&o);
   if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0))

@@ -81,6 +81,8 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
                                 uint64_t hist_offset, int32_t n_batches, double *sum1,
                                 double *sum2, double *mean, double *relerr, void *stream) {
   if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
+  if (pr->P.pc_target > 0)
+    return fail(MCDC_ERR_INVALID, "population control needs its bank buffers: use mcdc_run_ex");
   if (n_histories < 2) return fail(MCDC_ERR_INVALID, "n_histories must be >= 2");
   if (n_batches < 2 || (uint64_t)n_batches > n_histories)
     return fail(MCDC_ERR_INVALID, "need 2 <= n_batches <= n_histories");

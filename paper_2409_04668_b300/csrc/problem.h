@@ -41,6 +41,15 @@ struct mcdc_problem {
   uint64_t rec_cap = 0;
   double *ww64 = nullptr;
   float *ww32 = nullptr;
+  // population control: census bank, combed bank and the comb's scratch
+  int pc_cap = 0;                          // particles the census bank holds
+  void *pc_bank = nullptr, *pc_combed = nullptr;
+  unsigned long long *pc_cnt = nullptr;    // [4]: census count, combed count, cursor
+  unsigned long long *pc_keys[2] = {nullptr, nullptr};
+  uint32_t *pc_idx[2] = {nullptr, nullptr};
+  double *pc_w = nullptr, *pc_S = nullptr;
+  void *pc_temp = nullptr;
+  size_t pc_temp_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
   // host staging
   mcdc::Stats *h_stats = nullptr;   // pinned

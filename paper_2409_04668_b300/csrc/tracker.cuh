@@ -217,7 +217,7 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
                                        const PartOf<PR> &p, int end) {
   // analog runs carry weight 1 throughout: their weight sums are the counts
   // (filled in on the host), so only weighted runs add weights here
-  const bool weighted = P.ww_lower != nullptr || P.implicit;
+  const bool weighted = P.ww_lower != nullptr || P.implicit || P.pc_target > 0;
   if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); if (weighted) atomicAdd(&es.w_end[1], (double)p.w); }
   else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); if (weighted) atomicAdd(&es.w_end[2], (double)p.w); }
   else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); if (weighted) atomicAdd(&es.w_end[3], (double)p.w); }
@@ -363,8 +363,9 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 }
 
 // ---------------------------------------------------------------------------
-// one flight.  Returns 0 continue, 1 collision queued, 2 ended (end code in *end)
-enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2 };
+// one flight.  Returns 0 continue, 1 collision queued, 2 ended (end code in
+// *end), 3 reached an interior census edge under population control (banked)
+enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3 };
 
 template <class PR, int DIM>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
@@ -498,6 +499,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if constexpr (PR::kLocal) p.t = p.tbin < P.T ? __ldg(P.binw32 + p.tbin) : 0.0f;
     else p.t = tb.edges[p.tbin];
     if (p.tbin == P.T) { end = END_CENSUSED; return OUT_DEAD; }
+    if (A.census_out != nullptr) return OUT_BANKED;   // waits for the comb
     return OUT_CONT;
   }
   if (ev == 1) {
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             alive = true;
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
-            if (P.ww_lower != nullptr || P.implicit) atomicAdd(&s_w[0], 1.0);
+            if (P.ww_lower != nullptr || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
@@ -965,6 +967,22 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score);
+        if (A.census_out != nullptr) {
+          // population control: append the warp's banked particles
+          const bool bank = has && outcome == OUT_BANKED;
+          const uint32_t bm = __ballot_sync(0xffffffffu, bank);
+          if (bm) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(A.census_count, (unsigned long long)__popc(bm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (bank) {
+              const unsigned long long slot = base + __popc(bm & lt);
+              if (slot < A.census_cap) reinterpret_cast<PartOf<PR> *>(A.census_out)[slot] = p;
+              else atomicOr(A.error, ERRBIT_OVERFLOW);
+              has = false;
+            }
+          }
+        }
         const bool park = has && outcome == OUT_COLL;
         const uint32_t pm = __ballot_sync(0xffffffffu, park);
         if (pm) {

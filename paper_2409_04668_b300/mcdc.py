@@ -58,7 +58,8 @@ class mcdc_options(C.Structure):
                 ("autotune", C.c_int32), ("overflow_per_cta", C.c_int32),
                 ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
                 ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
-                ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double)]
+                ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
+                ("pc_target", C.c_int32)]
 
 
 class mcdc_stats(C.Structure):
@@ -68,7 +69,9 @@ class mcdc_stats(C.Structure):
         (k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_censused",
                                   "kernel_ms", "total_ms")] + [
         (k, C.c_int32) for k in ("block_size", "bank_per_cta", "ctas_per_sm", "tally_mode",
-                                 "n_batches", "warp_aggregate")] + [("splits_dropped", C.c_uint64)]
+                                 "n_batches", "warp_aggregate")] + [("splits_dropped", C.c_uint64)] + [
+        (k, C.c_uint64) for k in ("pc_combs", "pc_in", "pc_out")] + [
+        (k, C.c_double) for k in ("w_pc_in", "w_pc_out")]
 
 
 class mcdc_record(C.Structure):
@@ -190,9 +193,11 @@ class Problem:
 
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
-                 overflow_per_cta=0, region=None, estimator=0, implicit=None):
+                 overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0):
         """estimator: EST_TRACK or EST_COLLISION; implicit: None (analog
-        collisions) or (weight cutoff, survival weight) for implicit capture."""
+        collisions) or (weight cutoff, survival weight) for implicit capture;
+        pc_target: population control, particles per batch after each comb
+        at an interior census edge (0: off)."""
         self.desc = prob
         keep = []
 
@@ -239,6 +244,7 @@ class Problem:
         o.region_lo[:] = [int(v) for v in lo]
         o.region_hi[:] = [int(v) for v in hi]
         o.estimator = int(estimator)
+        o.pc_target = int(pc_target)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])
