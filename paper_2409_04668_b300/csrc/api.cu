@@ -205,35 +205,50 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
   return B;
 }
 
-// Population control buffers for a census bank of up to cap particles.
-int ensure_pc(mcdc_problem *pr, int cap) {
-  if (pr->pc_cap >= cap) return MCDC_OK;
+// Population control buffers: a census bank of cap particles, a combed
+// bank of combed particles, B tally slices and the comb's scratch.
+int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
   const size_t pb = part_bytes(pr->key);
   int rc;
-  unsigned char *bank = nullptr, *combed = nullptr;
-  if ((rc = dalloc(pr, &bank, pb * (size_t)cap))) return rc;
-  if (!pr->pc_combed) {
-    if ((rc = dalloc(pr, &combed, pb * (size_t)pr->P.pc_target))) return rc;
-    pr->pc_combed = combed;
+  if (pr->pc_cap < cap) {
+    unsigned char *bank = nullptr, *temp = nullptr;
+    if ((rc = dalloc(pr, &bank, pb * (size_t)cap))) return rc;
+    for (int q = 0; q < 2; ++q) {
+      if ((rc = dalloc(pr, &pr->pc_keys[q], (size_t)cap))) return rc;
+      if ((rc = dalloc(pr, &pr->pc_idx[q], (size_t)cap))) return rc;
+    }
+    if ((rc = dalloc(pr, &pr->pc_w, (size_t)cap))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_S, (size_t)cap))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_bid, (size_t)cap))) return rc;
+    const size_t tb = comb_temp_bytes(cap);
+    if ((rc = dalloc(pr, &temp, tb))) return rc;
+    pr->pc_bank = bank;
+    pr->pc_temp = temp;
+    pr->pc_temp_bytes = tb;
+    pr->pc_cap = cap;
+  }
+  if (pr->pc_combed_cap < combed) {
+    unsigned char *c = nullptr;
+    if ((rc = dalloc(pr, &c, pb * (size_t)combed))) return rc;
+    pr->pc_combed = c;
+    pr->pc_combed_cap = combed;
+  }
+  if (pr->pc_seg_cap < B) {
+    if ((rc = dalloc(pr, &pr->pc_seg, 3 * (size_t)B))) return rc;
+    pr->pc_seg_cap = B;
+  }
+  const long long bins = (long long)B * pr->P.n_bins;
+  if (pr->pc_tally_bins < bins) {
+    if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
+    if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess)
+      return fail(MCDC_ERR_CUDA, "cudaMemset of the tally slices failed");
+    pr->pc_tally_bins = bins;
   }
   if (!pr->pc_cnt && (rc = dalloc(pr, &pr->pc_cnt, 4))) return rc;
-  for (int q = 0; q < 2; ++q) {
-    if ((rc = dalloc(pr, &pr->pc_keys[q], (size_t)cap))) return rc;
-    if ((rc = dalloc(pr, &pr->pc_idx[q], (size_t)cap))) return rc;
-  }
-  if ((rc = dalloc(pr, &pr->pc_w, (size_t)cap))) return rc;
-  if ((rc = dalloc(pr, &pr->pc_S, (size_t)cap))) return rc;
-  const size_t tb = comb_temp_bytes(cap);
-  unsigned char *temp = nullptr;
-  if ((rc = dalloc(pr, &temp, tb))) return rc;
   if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return fail(MCDC_ERR_OOM, "cudaMallocHost failed");
   }
-  pr->pc_bank = bank;
-  pr->pc_temp = temp;
-  pr->pc_temp_bytes = tb;
-  pr->pc_cap = cap;
   return MCDC_OK;
 }
 
@@ -776,62 +791,69 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     A.chunk = 0;
     CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
   } else if (P.pc_target > 0) {
-    // population control: every batch is a time-stepped simulation; after
-    // each step the census bank is combed and the next step runs it
+    // population control: every batch is a time-stepped simulation with its
+    // own tally slice; one launch runs one step of all batches, then the
+    // census bank is combed batch by batch and the next step runs it
     const int M = P.pc_target;
-    const uint64_t bmax = a->n_histories / (uint64_t)B + 1;
-    if (int rc = ensure_pc(pr, (int)std::max<uint64_t>(bmax, (uint64_t)M))) return rc;
-    for (int b = 0; b < B; ++b) {
-      A.work = pr->work + b;
-      A.batch = b;
-      const uint64_t nb_hist = a->n_histories / B + 1;
-      A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));
-      A.spill_in = nullptr;
-      A.spill_out = nullptr;
-      A.census_out = pr->pc_bank;
-      A.census_count = pr->pc_cnt;
-      A.census_cap = (unsigned long long)pr->pc_cap;
-      const uint64_t b0 = batch_start(a->n_histories, B, b);
-      const uint64_t nbh = batch_start(a->n_histories, B, b + 1) - b0;
-      int key_bits = 33;
-      while (key_bits < 64 && (1ull << (key_bits - 32)) < nbh) ++key_bits;
-      for (int step = 0;; ++step) {
-        CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
-        CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
-        if (step >= P.T - 1) break;
-        CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const unsigned long long n = *pr->h_spill;
-        if (n == 0) break;
-        if (n > (unsigned long long)pr->pc_cap)
-          return fail(MCDC_ERR_BANK_OVERFLOW, "census bank overflow under population control");
-        CombArgs c{};
-        c.bank = pr->pc_bank;
-        c.n = (int)n;
-        c.out = pr->pc_combed;
-        c.M = M;
-        c.out_count = pr->pc_cnt + 1;
-        c.h0 = a->hist_offset + b0;
-        c.step = step;
-        c.rk = A.rk;
-        c.key_bits = key_bits;
-        c.keys[0] = pr->pc_keys[0]; c.keys[1] = pr->pc_keys[1];
-        c.idx[0] = pr->pc_idx[0]; c.idx[1] = pr->pc_idx[1];
-        c.w = pr->pc_w;
-        c.S = pr->pc_S;
-        c.temp = pr->pc_temp;
-        c.temp_bytes = pr->pc_temp_bytes;
-        c.stats = pr->stats;
-        CK(comb_bank(pr->key, s, c));
-        CK(cudaMemsetAsync(pr->pc_cnt + 2, 0, sizeof(unsigned long long), s));
-        A.spill_in = pr->pc_combed;
-        A.spill_in_count = pr->pc_cnt + 1;
-        A.spill_in_cursor = pr->pc_cnt + 2;
-        A.spill_cap = (unsigned long long)M;
-      }
-      CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+    const uint64_t N = a->n_histories;
+    if (N > 0x7fffffffull || (uint64_t)B * (uint64_t)M > 0x7fffffffull)
+      return fail(MCDC_ERR_INVALID, "population control needs n_histories and n_batches x pc_target < 2^31");
+    if (int rc = ensure_pc(pr, (int)std::max<uint64_t>(N, (uint64_t)B * M), (long long)B * M, B))
+      return rc;
+    A.work = pr->work;
+    A.batch = 0;
+    A.tally = pr->pc_tally;
+    A.tally_per_batch = 1;
+    A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, N / ((uint64_t)pr->grid * 4) + 1));
+    A.spill_in = nullptr;
+    A.spill_out = nullptr;
+    A.census_out = pr->pc_bank;
+    A.census_count = pr->pc_cnt;
+    A.census_cap = (unsigned long long)pr->pc_cap;
+    int key_bits = 33;
+    while (key_bits < 64 && (1ull << (key_bits - 32)) < N) ++key_bits;
+    for (int step = 0;; ++step) {
+      CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
+      CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+      if (step >= P.T - 1) break;
+      CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const unsigned long long n = *pr->h_spill;
+      if (n == 0) break;
+      if (n > (unsigned long long)pr->pc_cap)
+        return fail(MCDC_ERR_BANK_OVERFLOW, "census bank overflow under population control");
+      CombArgs c{};
+      c.bank = pr->pc_bank;
+      c.n = (int)n;
+      c.out = pr->pc_combed;
+      c.M = M;
+      c.out_count = pr->pc_cnt + 1;
+      c.offset = a->hist_offset;
+      c.n_hist = N;
+      c.B = B;
+      c.step = step;
+      c.rk = A.rk;
+      c.key_bits = key_bits;
+      c.keys[0] = pr->pc_keys[0]; c.keys[1] = pr->pc_keys[1];
+      c.idx[0] = pr->pc_idx[0]; c.idx[1] = pr->pc_idx[1];
+      c.w = pr->pc_w;
+      c.S = pr->pc_S;
+      c.bid = pr->pc_bid;
+      c.seg = pr->pc_seg;
+      c.temp = pr->pc_temp;
+      c.temp_bytes = pr->pc_temp_bytes;
+      c.stats = pr->stats;
+      CK(comb_bank(pr->key, s, c));
+      CK(cudaMemsetAsync(pr->pc_cnt + 2, 0, sizeof(unsigned long long), s));
+      A.spill_in = pr->pc_combed;
+      A.spill_in_count = pr->pc_cnt + 1;
+      A.spill_in_cursor = pr->pc_cnt + 2;
+      A.spill_cap = (unsigned long long)pr->pc_combed_cap;
     }
+    for (int b = 0; b < B; ++b)
+      CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nb, pr->sum1, pr->sum2, pr->region_batch,
+                     pr->region, pr->sms));
   } else {
     const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
     for (int b = 0; b < B; ++b) {

@@ -135,6 +135,9 @@ struct RunArgs {
   void *census_out;
   unsigned long long *census_count;
   unsigned long long census_cap;
+  // population control runs every batch in each launch: the global tally is
+  // one slice of n_bins per batch, picked from the particle's history id
+  int32_t tally_per_batch;
 };
 
 // ---- counter-based generator: Philox4x32-10 (Salmon et al., SC'11) -------
@@ -213,6 +216,14 @@ __device__ __forceinline__ int warp_append(bool pred, int *counter) {
   if (lane == 0 && mask) base = atomicAdd(counter, __popc(mask));
   base = __shfl_sync(0xffffffffu, base, 0);
   return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// batch of history h (0-based within the run): the first n % B batches hold
+// one history more than the others
+__host__ __device__ __forceinline__ int32_t batch_of(uint64_t n, int32_t B, uint64_t h) {
+  const uint64_t q = n / (uint64_t)B, r = n % (uint64_t)B;
+  const uint64_t big = r * (q + 1);
+  return (int32_t)(h < big ? h / (q + 1) : r + (h - big) / q);
 }
 
 __host__ __device__ __forceinline__ uint64_t batch_start(uint64_t n, int32_t B, int32_t b) {

@@ -43,6 +43,11 @@ struct mcdc_problem {
   float *ww32 = nullptr;
   // population control: census bank, combed bank and the comb's scratch
   int pc_cap = 0;                          // particles the census bank holds
+  long long pc_combed_cap = 0;             // particles the combed bank holds
+  long long pc_tally_bins = 0;             // bins of the per-batch tally slices
+  double *pc_tally = nullptr;              // [batches][n_bins]
+  int32_t *pc_bid = nullptr, *pc_seg = nullptr;
+  int pc_seg_cap = 0;
   void *pc_bank = nullptr, *pc_combed = nullptr;
   unsigned long long *pc_cnt = nullptr;    // [4]: census count, combed count, cursor
   unsigned long long *pc_keys[2] = {nullptr, nullptr};

@@ -608,13 +608,14 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
 // tally scatter of one warp: optional warp aggregation of equal bins
 template <class TT, class R>
 __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool shared_mode,
-                                              bool aggregate, bool valid, int bin, R score) {
+                                              bool aggregate, bool valid, int bin, R score,
+                                              long long goff = 0) {
   bool act = valid && bin >= 0;
   R v = score;
   if (aggregate) {
     // lanes scoring into the same bin add their scores first; the lowest
     // such lane issues the one atomic.  All 32 lanes run the same shuffles.
-    const int key = act ? bin : -1;
+    const long long key = act ? goff + bin : -1ll;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const bool dup = act && __popc(peers) > 1;
     if (__any_sync(0xffffffffu, dup)) {
@@ -631,8 +632,15 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
   }
   if (act) {
     if (shared_mode) atomicAdd(&stally[bin], (TT)v);
-    else atomicAdd(&gtally[bin], (double)v);
+    else atomicAdd(&gtally[goff + bin], (double)v);
   }
+}
+
+// offset of the particle's tally slice (population control: one per batch)
+__device__ __forceinline__ long long tally_offset(const DevProblem &P, const RunArgs &A,
+                                                  uint64_t hid) {
+  if (!A.tally_per_batch) return 0;
+  return (long long)batch_of(A.n_hist, A.n_batches, hid - A.offset) * P.n_bins;
 }
 
 // ---------------------------------------------------------------------------
@@ -769,8 +777,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   bool agg = MULTI ? false : A.warp_aggregate != 0;
   uint64_t g_h0 = 0, g_h1 = 0;
   if (!SHARED && !MULTI) {
-    g_h0 = batch_start(A.n_hist, A.n_batches, A.batch);
-    g_h1 = batch_start(A.n_hist, A.n_batches, A.batch + 1);
+    g_h0 = A.tally_per_batch ? 0 : batch_start(A.n_hist, A.n_batches, A.batch);
+    g_h1 = A.tally_per_batch ? A.n_hist : batch_start(A.n_hist, A.n_batches, A.batch + 1);
   }
 
   for (;;) {
@@ -845,7 +853,9 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
-          if (P.estimator == 1) tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine, cbin, cscore);
+          if (P.estimator == 1)
+            tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine, cbin, cscore,
+                                 mine ? tally_offset(P, A, q.hid) : 0);
           if (P.implicit) {
             // weight removed by implicit capture: one shared add per warp
             for (int o = 16; o > 0; o >>= 1) wabs += __shfl_xor_sync(0xffffffffu, wabs, o);
@@ -966,7 +976,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
-        tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score);
+        tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score,
+                             flew ? tally_offset(P, A, p.hid) : 0);
         if (A.census_out != nullptr) {
           // population control: append the warp's banked particles
           const bool bank = has && outcome == OUT_BANKED;
