@@ -532,6 +532,21 @@ __global__ void k_ww_from_pred(const DevProblem P, uint64_t stride, const float 
   }
 }
 
+// one window per (cell, group): the largest over its time bins
+__global__ void k_ww_time_collapse(const DevProblem P, double *__restrict__ ww64,
+                                   float *__restrict__ ww32) {
+  const int64_t ncg = P.n_cells * P.G;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncg;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int t = 0; t < P.T1; ++t) m = fmax(m, ww64[c * P.T1 + t]);
+    for (int t = 0; t < P.T1; ++t) {
+      ww64[c * P.T1 + t] = m;
+      ww32[c * P.T1 + t] = (float)m;
+    }
+  }
+}
+
 namespace {
 uint64_t gcd64(uint64_t a, uint64_t b) {
   while (b) { const uint64_t r = a % b; a = b; b = r; }
@@ -822,6 +837,10 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
                                          o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64, pr->ww32);
   CKM(cudaGetLastError());
+  if (!o.time_resolved && P.T1 > 1) {
+    k_ww_time_collapse<<<blocks, 256, 0, st>>>(P, pr->ww64, pr->ww32);
+    CKM(cudaGetLastError());
+  }
   CKM(cudaEventRecord(e2, st));
   CKM(cudaStreamSynchronize(st));
   // switch the problem to weight windows (w_U, w_S ratios as given)

@@ -386,8 +386,10 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     const double xi = u01_f64(r.a, r.b);
     d_coll = sig_t > 0.0 ? -log(xi) / sig_t : rinf<double>();
   } else {
+    // FP32 modes divide with the approximate (2-ulp) quotient: about 5 %
+    // faster than the correctly rounded one, far below the FP32 noise
     const float xi = u01_f32(r.a);
-    d_coll = sig_t > 0.0f ? -logf(xi) / sig_t : rinf<float>();
+    d_coll = sig_t > 0.0f ? __fdividef(-logf(xi), sig_t) : rinf<float>();
   }
 
   // distance to the mesh surface and to the time census
@@ -399,7 +401,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     {
       const float u = p.ux;
       if (P.bounded[0] && u != 0.0f) {
-        float d = (u > 0.0f ? P.width32[0] - p.x : -p.x) / u;
+        float d = __fdividef(u > 0.0f ? P.width32[0] - p.x : -p.x, u);
         if (d < 0.0f) d = 0.0f;
         if (d < d_surf) { d_surf = d; ax = 0; }
       }
@@ -407,13 +409,13 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if (DIM == 3) {
       const float u = p.uy;
       if (P.bounded[1] && u != 0.0f) {
-        float d = (u > 0.0f ? P.width32[1] - p.y : -p.y) / u;
+        float d = __fdividef(u > 0.0f ? P.width32[1] - p.y : -p.y, u);
         if (d < 0.0f) d = 0.0f;
         if (d < d_surf) { d_surf = d; ax = 1; }
       }
       const float v = p.uz;
       if (P.bounded[2] && v != 0.0f) {
-        float d = (v > 0.0f ? P.width32[2] - p.z : -p.z) / v;
+        float d = __fdividef(v > 0.0f ? P.width32[2] - p.z : -p.z, v);
         if (d < 0.0f) d = 0.0f;
         if (d < d_surf) { d_surf = d; ax = 2; }
       }
@@ -428,7 +430,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
       if (P.bounded[0] && u != (R)0) {
         const double f = face_of(P, 0, p.i, u > (R)0);
         R d;
-        if constexpr (PR::kF64) d = (f - p.x) / u; else d = (float)(f - p.x) / u;
+        if constexpr (PR::kF64) d = (f - p.x) / u; else d = __fdividef((float)(f - p.x), u);
         if (d < (R)0) d = (R)0;
         if (d < d_surf) { d_surf = d; ax = 0; }
       }
@@ -438,7 +440,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
       if (P.bounded[1] && u != (R)0) {
         const double f = face_of(P, 1, p.j, u > (R)0);
         R d;
-        if constexpr (PR::kF64) d = (f - p.y) / u; else d = (float)(f - p.y) / u;
+        if constexpr (PR::kF64) d = (f - p.y) / u; else d = __fdividef((float)(f - p.y), u);
         if (d < (R)0) d = (R)0;
         if (d < d_surf) { d_surf = d; ax = 1; }
       }
@@ -446,7 +448,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
       if (P.bounded[2] && v != (R)0) {
         const double f = face_of(P, 2, p.k, v > (R)0);
         R d;
-        if constexpr (PR::kF64) d = (f - p.z) / v; else d = (float)(f - p.z) / v;
+        if constexpr (PR::kF64) d = (f - p.z) / v; else d = __fdividef((float)(f - p.z), v);
         if (d < (R)0) d = (R)0;
         if (d < d_surf) { d_surf = d; ax = 2; }
       }
