@@ -276,11 +276,16 @@ typedef struct mcdc_mlp_options {
     double min_ratio;           /* floor of w_L / w_L(highest-flux bin) (default 1e-8);
                                    w_L is also kept above a tenth of the least-scored
                                    bin's value, so extrapolated windows cannot run away */
-    int32_t time_resolved;      /* 0 (default): one window per (cell, group), the
-                                   largest over the time bins; 1: one per time bin.
+    int32_t time_resolved;      /* 0 (default): windows do not depend on the time
+                                   bin (the largest over the bins); 1: one per bin.
                                    Per-time windows are tiny where few particles
                                    arrive early (deep cells, first time bins), and
                                    those few then split again and again          */
+    int32_t group_resolved;     /* 0 (default): windows do not depend on the group
+                                   (the largest over the groups); 1: one per group.
+                                   Flux = density x speed, so per-group windows are
+                                   low for slow groups, whose particles then split
+                                   heavily while hardly moving                   */
 } mcdc_mlp_options;
 
 typedef struct mcdc_mlp_report {

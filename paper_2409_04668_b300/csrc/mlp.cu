@@ -532,18 +532,27 @@ __global__ void k_ww_from_pred(const DevProblem P, uint64_t stride, const float 
   }
 }
 
-// one window per (cell, group): the largest over its time bins
-__global__ void k_ww_time_collapse(const DevProblem P, double *__restrict__ ww64,
-                                   float *__restrict__ ww32) {
-  const int64_t ncg = P.n_cells * P.G;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncg;
+// one window per (cell, group) -- the largest over its time bins -- or per
+// cell, the largest over its groups and time bins
+__global__ void k_ww_collapse(const DevProblem P, bool over_groups, bool over_time,
+                              double *__restrict__ ww64, float *__restrict__ ww32) {
+  const int G = over_groups ? P.G : 1;        // groups folded into one window
+  const int T = over_time ? P.T1 : 1;         // time bins folded into one window
+  const int64_t n = P.n_bins / ((int64_t)G * T);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
+    // c enumerates (cell, kept group, kept time bin); bin = (cell G + g) T1 + t
+    const int64_t cell = over_groups ? c / (over_time ? 1 : P.T1) : c / ((int64_t)P.G * (over_time ? 1 : P.T1));
+    const int g0 = over_groups ? 0 : (int)((c / (over_time ? 1 : P.T1)) % P.G);
+    const int t0 = over_time ? 0 : (int)(c % P.T1);
     double m = 0.0;
-    for (int t = 0; t < P.T1; ++t) m = fmax(m, ww64[c * P.T1 + t]);
-    for (int t = 0; t < P.T1; ++t) {
-      ww64[c * P.T1 + t] = m;
-      ww32[c * P.T1 + t] = (float)m;
-    }
+    for (int g = 0; g < G; ++g)
+      for (int t = 0; t < T; ++t) m = fmax(m, ww64[(cell * P.G + g0 + g) * P.T1 + t0 + t]);
+    for (int g = 0; g < G; ++g)
+      for (int t = 0; t < T; ++t) {
+        ww64[(cell * P.G + g0 + g) * P.T1 + t0 + t] = m;
+        ww32[(cell * P.G + g0 + g) * P.T1 + t0 + t] = (float)m;
+      }
   }
 }
 
@@ -837,8 +846,9 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
                                          o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64, pr->ww32);
   CKM(cudaGetLastError());
-  if (!o.time_resolved && P.T1 > 1) {
-    k_ww_time_collapse<<<blocks, 256, 0, st>>>(P, pr->ww64, pr->ww32);
+  const bool fold_g = !o.group_resolved && P.G > 1, fold_t = !o.time_resolved && P.T1 > 1;
+  if (fold_g || fold_t) {
+    k_ww_collapse<<<blocks, 256, 0, st>>>(P, fold_g, fold_t, pr->ww64, pr->ww32);
     CKM(cudaGetLastError());
   }
   CKM(cudaEventRecord(e2, st));
