@@ -296,6 +296,7 @@ def main():
         line["variants"] = variants(M, prob, n_hist, args, mean, rel, stream)
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_deep(M, prec)
+        line["fom_shallow"] = fom_deep(M, prec, prob=W.c4_shallow())
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         h, sg, dt = oracle_sample(prob, args.cpu_seconds, os.cpu_count() or 1, offset=10**12)
         line["cpu_baseline"] = {"value": h / dt, "unit": "histories/s", "cores": os.cpu_count(),
@@ -402,7 +403,7 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     return out
 
 
-def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):
+def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1, prob=None):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
     region x in [90, 100]), analog against the learned weight windows.  The
@@ -411,10 +412,10 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1):
     that reaches deeper).  T is the device time of the measured run; the
     training time is reported beside it."""
     import torch
-    prob = W.c4_deep()
+    prob = prob if prob is not None else W.c4_deep()
     out = {"workload": prob.name, "region_cells": [list(prob.region_lo), list(prob.region_hi)]}
     dev = torch.device("cuda")
-    with M.Problem(prob, precision=prec, overflow_per_cta=8192 * 4) as P:
+    with M.Problem(prob, precision=prec) as P:
         mean = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
         rel = torch.zeros_like(mean)
         P.run_ex(1_000_000, 7, mean=mean, relerr=rel)            # warm-up

@@ -132,8 +132,12 @@ typedef struct mcdc_options {
                                    launch shapes (threads per CTA, whole batches per
                                    CTA, warp aggregation) on this problem at create
                                    and keep the fastest; cached per problem shape */
-    int32_t overflow_per_cta;   /* split-children overflow slots per CTA (shared by
-                                   its warps, >= 64 each); 0: 1024 per warp      */
+    int32_t overflow_per_cta;   /* split-children stack slots per CTA (shared by its
+                                   warps, >= 64 each, <= 256 with the global tally);
+                                   0: 1024 per warp with the shared tally, 64 with
+                                   the global tally, whose children beyond the
+                                   stack spill to device-wide banks drained by
+                                   every warp in later passes                    */
     int32_t region_lo[3];       /* cell box [lo, hi) of the scalar tally used for */
     int32_t region_hi[3];       /*   the figure of merit; hi == 0: whole mesh      */
     int32_t estimator;          /* MCDC_EST_* (default track length)              */
@@ -286,6 +290,15 @@ typedef struct mcdc_mlp_options {
                                    Flux = density x speed, so per-group windows are
                                    low for slow groups, whose particles then split
                                    heavily while hardly moving                   */
+    int32_t adjoint;            /* 0 (default): the pilot is a forward flux and
+                                   w_L ~ predicted flux (uniform particle density);
+                                   1: the pilot is an importance (e.g. the flux of
+                                   a run whose source is the tally region, the
+                                   adjoint by reciprocity when cross sections do not
+                                   depend on the group) and w_L = source_wl x
+                                   I(source cells) / I -- particles split on their
+                                   way to the region and are rouletted away from it;
+                                   time and group folds then keep the smallest w_L */
 } mcdc_mlp_options;
 
 typedef struct mcdc_mlp_report {

@@ -205,6 +205,19 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
   return B;
 }
 
+// One zeroed device tally slice per batch, for runs that put every batch in
+// one launch (population control, weight-window runs).
+int ensure_slices(mcdc_problem *pr, int B) {
+  const long long bins = (long long)B * pr->P.n_bins;
+  if (pr->pc_tally_bins >= bins) return MCDC_OK;
+  int rc;
+  if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
+  if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess)
+    return fail(MCDC_ERR_CUDA, "cudaMemset of the tally slices failed");
+  pr->pc_tally_bins = bins;
+  return MCDC_OK;
+}
+
 // Population control buffers: a census bank of cap particles, a combed
 // bank of combed particles, B tally slices and the comb's scratch.
 int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
@@ -237,13 +250,7 @@ int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
     if ((rc = dalloc(pr, &pr->pc_seg, 3 * (size_t)B))) return rc;
     pr->pc_seg_cap = B;
   }
-  const long long bins = (long long)B * pr->P.n_bins;
-  if (pr->pc_tally_bins < bins) {
-    if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
-    if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess)
-      return fail(MCDC_ERR_CUDA, "cudaMemset of the tally slices failed");
-    pr->pc_tally_bins = bins;
-  }
+  if ((rc = ensure_slices(pr, B))) return rc;
   if (!pr->pc_cnt && (rc = dalloc(pr, &pr->pc_cnt, 4))) return rc;
   if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
@@ -267,9 +274,11 @@ int ensure_overflow(mcdc_problem *pr) {
   const int warps = pr->block / 32;
   int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
   if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
-    // a small stack per warp; the rest spills to the device-wide banks so
-    // one large family of split children is shared by every warp
-    cap = std::min(cap, 256);
+    // a small stack per warp (64 by default); the rest spills to the
+    // device-wide banks so a large family of split children is shared by
+    // every warp in the next pass instead of keeping one warp busy (on the
+    // deep-penetration box 64 per warp ran 3-5x faster than 256)
+    cap = pr->opt.overflow_per_cta > 0 ? std::min(cap, 256) : 64;
     if (!pr->spill[0]) {
       const unsigned long long scap = 1ull << 26;   // particles per bank (4.3 GB in FP32)
       const size_t pb = pr->key.f64 ? sizeof(Part<double>)
@@ -856,10 +865,18 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
                      pr->region, pr->sms));
   } else {
     const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
-    for (int b = 0; b < B; ++b) {
+    // weight-window runs put every batch in one launch (one tally slice per
+    // batch): a batch's few histories would leave most warps idle while a
+    // handful work through their split families
+    const bool merged = spill && (double)B * (double)nb * 8.0 <= 8.0 * 1073741824.0;
+    if (merged)
+      if (int rc = ensure_slices(pr, B)) return rc;
+    for (int b = 0; b < (merged ? 1 : B); ++b) {
       A.work = pr->work + b;
       A.batch = b;
-      const uint64_t nb_hist = a->n_histories / B + 1;
+      A.tally = merged ? pr->pc_tally : pr->tally;
+      A.tally_per_batch = merged ? 1 : 0;
+      const uint64_t nb_hist = merged ? a->n_histories : a->n_histories / B + 1;
       A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));
       A.spill_in = nullptr;
       A.spill_out = nullptr;
@@ -889,7 +906,13 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
         A.spill_out_count = pr->spill_cnt + out;
         CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
       }
-      CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+      if (merged) {
+        for (int q = 0; q < B; ++q)
+          CK(launch_fold(s, P, pr->pc_tally + (size_t)q * nb, pr->sum1, pr->sum2, pr->region_batch,
+                         pr->region, pr->sms));
+      } else {
+        CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+      }
     }
   }
   CK(cudaEventRecord(pr->ev2, s));

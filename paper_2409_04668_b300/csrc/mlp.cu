@@ -532,9 +532,61 @@ __global__ void k_ww_from_pred(const DevProblem P, uint64_t stride, const float 
   }
 }
 
+// largest predicted log importance over the bins of the cells the source box
+// touches (ordered-bits trick as above)
+__global__ void k_pred_src_max(const DevProblem P, uint64_t stride, const float *__restrict__ pred,
+                               const double *__restrict__ moments,
+                               unsigned long long *__restrict__ mx) {
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    if (!P.bounded[a]) { lo[a] = hi[a] = 0; continue; }
+    lo[a] = max(0, min(P.n[a] - 1, (int)floor((P.src_lo[a] - P.origin[a]) / P.width[a])));
+    hi[a] = max(0, min(P.n[a] - 1, (int)floor((P.src_hi[a] - P.origin[a]) / P.width[a])));
+  }
+  const int64_t nb = P.n_bins, per_cell = (int64_t)P.G * P.T1;
+  double best = -1e300;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nb;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = (int64_t)(((unsigned __int128)s * stride) % (unsigned __int128)nb);
+    const int64_t cell = b / per_cell;
+    const int i = (int)(cell % P.n[0]), j = (int)((cell / P.n[0]) % P.n[1]);
+    const int k = (int)(cell / ((int64_t)P.n[0] * P.n[1]));
+    if (i >= lo[0] && i <= hi[0] && j >= lo[1] && j <= hi[1] && k >= lo[2] && k <= hi[2])
+      best = fmax(best, (double)pred[s] * moments[4] + moments[3]);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0 && best > -1e300)
+    atomicMax(mx, (unsigned long long)__double_as_longlong(fmax(0.0, best + 1e4)));
+}
+
+// importance (adjoint) windows: w_L = wl0 * I(source) / I, with I kept above
+// a tenth of the least-scored bin's value and above min_ratio * max I, and
+// w_L never below wl0 * I(source) / max I
+__global__ void k_ww_from_importance(const DevProblem P, uint64_t stride,
+                                     const float *__restrict__ pred,
+                                     const double *__restrict__ moments,
+                                     const unsigned long long *__restrict__ mx, double wl0,
+                                     double min_ratio, double *__restrict__ ww64,
+                                     float *__restrict__ ww32) {
+  const double top = __longlong_as_double((long long)mx[0]) - 1e4;
+  const double low = __longlong_as_double((long long)mx[1]) - 1e4;
+  const double src = __longlong_as_double((long long)mx[2]) - 1e4;
+  const double floor_lp = fmax(low - 2.302585092994046, top + log(min_ratio));
+  const int64_t nb = P.n_bins;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nb;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = (int64_t)(((unsigned __int128)s * stride) % (unsigned __int128)nb);
+    const double lp = fmin(fmax((double)pred[s] * moments[4] + moments[3], floor_lp), top);
+    const double w = wl0 * exp(fmin(src - lp, 700.0));
+    ww64[b] = w;
+    ww32[b] = (float)fmin(w, 3.0e38);
+  }
+}
+
 // one window per (cell, group) -- the largest over its time bins -- or per
-// cell, the largest over its groups and time bins
-__global__ void k_ww_collapse(const DevProblem P, bool over_groups, bool over_time,
+// cell, the largest over its groups and time bins (importance windows: the
+// smallest, i.e. the largest importance)
+__global__ void k_ww_collapse(const DevProblem P, bool over_groups, bool over_time, bool smallest,
                               double *__restrict__ ww64, float *__restrict__ ww32) {
   const int G = over_groups ? P.G : 1;        // groups folded into one window
   const int T = over_time ? P.T1 : 1;         // time bins folded into one window
@@ -545,13 +597,16 @@ __global__ void k_ww_collapse(const DevProblem P, bool over_groups, bool over_ti
     const int64_t cell = over_groups ? c / (over_time ? 1 : P.T1) : c / ((int64_t)P.G * (over_time ? 1 : P.T1));
     const int g0 = over_groups ? 0 : (int)((c / (over_time ? 1 : P.T1)) % P.G);
     const int t0 = over_time ? 0 : (int)(c % P.T1);
-    double m = 0.0;
+    double m = smallest ? 1e308 : 0.0;
     for (int g = 0; g < G; ++g)
-      for (int t = 0; t < T; ++t) m = fmax(m, ww64[(cell * P.G + g0 + g) * P.T1 + t0 + t]);
+      for (int t = 0; t < T; ++t) {
+        const double w = ww64[(cell * P.G + g0 + g) * P.T1 + t0 + t];
+        m = smallest ? fmin(m, w) : fmax(m, w);
+      }
     for (int g = 0; g < G; ++g)
       for (int t = 0; t < T; ++t) {
         ww64[(cell * P.G + g0 + g) * P.T1 + t0 + t] = m;
-        ww32[(cell * P.G + g0 + g) * P.T1 + t0 + t] = (float)m;
+        ww32[(cell * P.G + g0 + g) * P.T1 + t0 + t] = (float)fmin(m, 3.0e38);
       }
   }
 }
@@ -727,7 +782,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   CKM(cudaMalloc(&g, sizeof(float) * np)); fr.add(g);
   CKM(cudaMalloc(&mom, sizeof(double) * 8)); fr.add(mom);
   CKM(cudaMalloc(&tstep, sizeof(int64_t))); fr.add(tstep);
-  CKM(cudaMalloc(&mx, 2 * sizeof(unsigned long long))); fr.add(mx);
+  CKM(cudaMalloc(&mx, 3 * sizeof(unsigned long long))); fr.add(mx);
   const int64_t steps_per_epoch = (nb + o.batch - 1) / o.batch;
   CKM(cudaMalloc(&losses, sizeof(double) * steps_per_epoch * 2)); fr.add(losses);
 
@@ -828,12 +883,16 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   CKM(cudaEventRecord(e1, st));
   // bake: predict every bin, weight windows proportional to the predicted flux
   CKM(launch_mlp_forward(st, sms, prm, n_in, X, nb, pred));
-  CKM(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), st));
+  CKM(cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), st));
   CKM(cudaMemsetAsync(mx + 1, 0xff, sizeof(unsigned long long), st));
   k_pred_max<<<blocks, 256, 0, st>>>(nb, pred, mom, mx);
   CKM(cudaGetLastError());
   k_pred_min_scored<<<blocks, 256, 0, st>>>(nb, pred, W, mom, mx + 1);
   CKM(cudaGetLastError());
+  if (o.adjoint) {
+    k_pred_src_max<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx + 2);
+    CKM(cudaGetLastError());
+  }
   if (!pr->ww64) {
     void *a, *b;
     CKM(cudaMalloc(&a, sizeof(double) * nb));
@@ -843,12 +902,18 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     pr->ww64 = (double *)a;
     pr->ww32 = (float *)b;
   }
-  k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
-                                         o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64, pr->ww32);
+  if (o.adjoint)
+    k_ww_from_importance<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, o.source_wl,
+                                                 o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
+                                                 pr->ww32);
+  else
+    k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
+                                           o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
+                                           pr->ww32);
   CKM(cudaGetLastError());
   const bool fold_g = !o.group_resolved && P.G > 1, fold_t = !o.time_resolved && P.T1 > 1;
   if (fold_g || fold_t) {
-    k_ww_collapse<<<blocks, 256, 0, st>>>(P, fold_g, fold_t, pr->ww64, pr->ww32);
+    k_ww_collapse<<<blocks, 256, 0, st>>>(P, fold_g, fold_t, o.adjoint != 0, pr->ww64, pr->ww32);
     CKM(cudaGetLastError());
   }
   CKM(cudaEventRecord(e2, st));

@@ -101,7 +101,8 @@ class mcdc_mlp_options(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
                 ("seed", C.c_uint64), ("source_wl", C.c_double), ("upper_ratio", C.c_double),
                 ("survival_ratio", C.c_double), ("nmax", C.c_int32), ("min_ratio", C.c_double),
-                ("time_resolved", C.c_int32), ("group_resolved", C.c_int32)]
+                ("time_resolved", C.c_int32), ("group_resolved", C.c_int32),
+                ("adjoint", C.c_int32)]
 
 
 class mcdc_mlp_report(C.Structure):

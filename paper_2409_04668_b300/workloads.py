@@ -187,6 +187,18 @@ def c4_deep(seed: int = 4) -> Problem:
                np.linspace(0.0, 1e-5, 11), (90, 0, 0), (100, ny, nz))
 
 
+def c4_shallow(seed: int = 4) -> Problem:
+    """The deep-penetration box with a 10 cm absorber (x in [35, 45], 10 mfp)
+    and the scalar region right behind it (x in [45, 55]): analog histories
+    do score there, rarely, so learned and analog figures of merit compare
+    directly."""
+    p = c4_deep(seed)
+    m = np.zeros_like(p.material)
+    m[:, :, 35:45] = 1
+    return dataclasses.replace(p, name="c4_shallow_100x40x40_4g_td", material=m,
+                               region_lo=(45, 0, 0), region_hi=(55, 40, 40))
+
+
 def c5_batch(n_problems: int = 256, seed: int = 5, hist_lo: float = 1e4, hist_hi: float = 1e7):
     """Independent 3-D problems of uneven size: mesh n^3 with n ~ U{16..64},
     G ~ U{1..7}, four materials with sigma_t ~ U[0.1, 2] and c ~ U[0.1, 0.95]
