@@ -118,3 +118,29 @@ def test_learned_weight_windows_reach_where_analog_does_not(mcdc):
     print("12 cm: analog", m_a, r_a, "learned", m_w, r_w, st["kernel_ms"])
     assert m_a == 0.0                      # no analog history gets through
     assert m_w > 0.0 and r_w < 0.05
+
+
+def test_importance_windows_from_a_region_source_pilot_are_unbiased(mcdc):
+    """Importance (adjoint) windows: the pilot is a run whose source is the
+    tally region (the adjoint by reciprocity here: cross sections do not
+    depend on the group); the windows fall towards the region and rise away
+    from it, and the region estimate agrees with analog."""
+    import dataclasses
+    prob = deep_slab(absorber=6)
+    lo = tuple(prob.origin[a] + prob.region_lo[a] * prob.width[a] for a in range(3))
+    hi = tuple(prob.origin[a] + prob.region_hi[a] * prob.width[a] for a in range(3))
+    adj = dataclasses.replace(prob, src_lo=lo, src_hi=hi, src_pdf=np.full(2, 0.5))
+    with mcdc.Problem(adj, precision=mcdc.PREC_FP32_LOCAL) as A:
+        am, ar = np.zeros(A.n_bins), np.zeros(A.n_bins)
+        A.run_ex(1_000_000, 3, mean=am, relerr=ar)
+    N = 2_000_000
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP32_LOCAL) as P:
+        _, (m_a, r_a) = P.run_ex(N, 2, batches=40)
+        P.train_importance(am, ar, epochs=60, batch=256, adjoint=1)
+        st, (m_w, r_w) = P.run_ex(N, 5, batches=40)
+    print("importance windows: analog", m_a, r_a, "learned", m_w, r_w, st["kernel_ms"],
+          "splits", st["splits"], "roulette", st["roulette_killed"])
+    assert st["splits"] > 0 and st["roulette_killed"] > 0
+    z = (m_w - m_a) / np.hypot(m_a * r_a, m_w * r_w)
+    assert abs(z) < 4.0, z
+    assert r_w < r_a
