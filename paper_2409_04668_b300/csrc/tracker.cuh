@@ -312,6 +312,37 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
 }
 
 // ---------------------------------------------------------------------------
+// isotropic direction from one block: mu = 2 xi - 1 is the x cosine, phi =
+// 2 pi xi' the azimuth.  A 1-D slab only ever uses the x cosine, so there
+// the azimuth is drawn (the block is the same) but not evaluated.
+template <class PR, int DIM>
+__device__ __forceinline__ void isotropic(const U4 &r2, PartOf<PR> &p) {
+  if constexpr (PR::kF64) {
+    const double mu = 2.0 * u01_f64(r2.a, r2.b) - 1.0;
+    p.ux = mu;
+    if (DIM == 3) {
+      const double two_pi = 6.283185307179586;
+      const double phi = two_pi * u01_f64(r2.c, r2.d);
+      const double s = sqrt(1.0 - mu * mu);
+      p.uy = s * cos(phi); p.uz = s * sin(phi);
+    } else {
+      p.uy = 0.0; p.uz = 0.0;
+    }
+  } else {
+    const float mu = 2.0f * u01_f32(r2.a) - 1.0f;
+    p.ux = mu;
+    if (DIM == 3) {
+      const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+      float sn, cs;
+      sincospif(2.0f * u01_f32(r2.c), &sn, &cs);
+      p.uy = s * cs; p.uz = s * sn;
+    } else {
+      p.uy = 0.0f; p.uz = 0.0f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // source particle (counters 0..3: x,y | z,group | mu,phi | t)
 template <class PR, int DIM>
 __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R> &tb,
@@ -327,18 +358,8 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
   else p.g = sample_cdf<float>(tb.src_cdf, P.G, u01_f32(r1.c));
   if (P.src_kind == 1) {
     p.ux = (R)P.src_dir[0]; p.uy = (R)P.src_dir[1]; p.uz = (R)P.src_dir[2];
-  } else if constexpr (PR::kF64) {
-    const double two_pi = 6.283185307179586;
-    const double mu = 2.0 * u01_f64(r2.a, r2.b) - 1.0;
-    const double phi = two_pi * u01_f64(r2.c, r2.d);
-    const double s = sqrt(1.0 - mu * mu);
-    p.ux = mu; p.uy = s * cos(phi); p.uz = s * sin(phi);
   } else {
-    const float mu = 2.0f * u01_f32(r2.a) - 1.0f;
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
-    float sn, cs;
-    sincospif(2.0f * u01_f32(r2.c), &sn, &cs);
-    p.ux = mu; p.uy = s * cs; p.uz = s * sn;
+    isotropic<PR, DIM>(r2, p);
   }
   p.w = (R)1;
   const double x = P.src_lo[0] + u01_f64(r0.a, r0.b) * (P.src_hi[0] - P.src_lo[0]);
@@ -576,19 +597,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
     return false;
   }
   p.g = sample_cdf<R>(tb.cdf + mg * P.G, P.G, xi2);
-  if constexpr (PR::kF64) {
-    const double two_pi = 6.283185307179586;
-    const double mu = 2.0 * u01_f64(r2.a, r2.b) - 1.0;
-    const double phi = two_pi * u01_f64(r2.c, r2.d);
-    const double s = sqrt(1.0 - mu * mu);
-    p.ux = mu; p.uy = s * cos(phi); p.uz = s * sin(phi);
-  } else {
-    const float mu = 2.0f * u01_f32(r2.a) - 1.0f;
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
-    float sn, cs;
-    sincospif(2.0f * u01_f32(r2.c), &sn, &cs);
-    p.ux = mu; p.uy = s * cs; p.uz = s * sn;
-  }
+  isotropic<PR, DIM>(r2, p);
   if (P.implicit) {
     R wcut, wsurv;
     if constexpr (PR::kF64) { wcut = P.wcut; wsurv = P.wsurv; }
