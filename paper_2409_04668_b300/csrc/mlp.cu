@@ -6,11 +6,11 @@
 // way into regions the analog run hardly reaches and rouletted on their way
 // back.
 //
-// Training and inference run on the tensor cores: BF16 weights and
-// activations, FP32 accumulation (mma.sync m16n8k16), FP32 master weights
-// and Adam state.  A CTA handles tiles of 64 samples with 4 warps; every
-// operand of an MMA is read from shared memory with K contiguous, so each
-// fragment register is one aligned 32-bit load.
+// Training and inference run on the fifth-generation tensor cores (tcgen05):
+// BF16 weights and activations in shared memory, FP32 accumulators in
+// tensor memory, FP32 master weights and Adam state.  Tiles of 128 samples:
+// thread r of a 128-thread group owns sample r (tensor-memory lane r), one
+// thread issues the MMAs, completion arrives on an mbarrier.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cmath>
@@ -22,14 +22,14 @@
 #include "../../include/mcdc.h"
 #include "launch.h"
 #include "problem.h"
+#include "tc.cuh"
 
 namespace mcdc {
 namespace {
 
 constexpr int kH = 64;        // hidden width
 constexpr int kIn = 16;       // padded input width (n_in <= 16)
-constexpr int kS = 64;        // samples per CTA tile
-constexpr int kThreads = 128; // 4 warps, 16 samples each in the row-wise phases
+constexpr int kS = 64;        // smallest minibatch
 
 __host__ __device__ inline int64_t param_count(int n_in) {
   return (int64_t)kH * n_in + kH + (int64_t)kH * kH + kH + kH + 1;
@@ -45,294 +45,387 @@ __device__ __forceinline__ Params split(const float *p, int n_in) {
   return q;
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU and its derivative with the fast exponential and divide: the network
+// runs in BF16, far coarser than their few-ulp error
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
+  const float s = __fdividef(1.0f, 1.0f + __expf(-z));
   return s * (1.0f + z * (1.0f - s));
-}
-
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) {
-  return *reinterpret_cast<const uint32_t *>(p);
-}
-
-// C[16x8] += A[16x16] * B[16x8] on the tensor cores.  A(m, k) = A[m*lda + k],
-// B(k, n) = Bt[n*ldb + k]; lda, ldb even, rows 4-byte aligned.
-__device__ __forceinline__ void mma16816(float c[4], const __nv_bfloat16 *A, int lda,
-                                         const __nv_bfloat16 *Bt, int ldb) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const uint32_t a0 = ld32(A + g * lda + 2 * t);
-  const uint32_t a1 = ld32(A + (g + 8) * lda + 2 * t);
-  const uint32_t a2 = ld32(A + g * lda + 2 * t + 8);
-  const uint32_t a3 = ld32(A + (g + 8) * lda + 2 * t + 8);
-  const uint32_t b0 = ld32(Bt + g * ldb + 2 * t);
-  const uint32_t b1 = ld32(Bt + g * ldb + 2 * t + 8);
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// shared memory of one CTA
-struct Smem {
-  __nv_bfloat16 W1[kH][kIn];      // layer-1 weights, [out][in]
-  __nv_bfloat16 W2[kH][kH];       // layer-2 weights, [out][in]
-  __nv_bfloat16 W2T[kH][kH];      // transposed, [in][out]
-  float b1[kH], b2[kH], W3[kH];
-  __nv_bfloat16 X[kS][kIn];       // tile inputs, [sample][feature]
-  __nv_bfloat16 XT[kIn][kS];      // [feature][sample]
-  float Z1[kS][kH];               // layer-1 pre-activations
-  __nv_bfloat16 H1[kS][kH];       // layer-1 outputs
-  __nv_bfloat16 H1T[kH][kS];
-  __nv_bfloat16 D2[kS][kH];       // dL/dz2
-  __nv_bfloat16 D2T[kH][kS];
-  __nv_bfloat16 D1T[kH][kS];      // dL/dz1, transposed
-  float y[kS], w[kS];             // targets and sample weights of the tile
-  float gW3[kH], gb2[kH], gb1[kH];
-  float gb3, loss;
-};
-
-__device__ void load_weights(Smem &s, const float *p, int n_in) {
-  const Params q = split(p, n_in);
-  for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
-    const int r = i / kIn, c = i % kIn;
-    s.W1[r][c] = __float2bfloat16(c < n_in ? q.W1[r * n_in + c] : 0.0f);
-  }
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    const int r = i / kH, c = i % kH;
-    const __nv_bfloat16 v = __float2bfloat16(q.W2[i]);
-    s.W2[r][c] = v;
-    s.W2T[c][r] = v;
-  }
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-    s.b1[i] = q.b1[i]; s.b2[i] = q.b2[i]; s.W3[i] = q.W3[i];
-  }
-}
-
-// Load one tile of samples [base, base + kS) (rows past n get zero input and
-// zero weight, so they contribute nothing).
-__device__ void load_tile(Smem &s, const float *X, const float *Y, const float *Wt, int64_t n,
-                          int n_in, int64_t base) {
-  for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x) {
-    const int r = i / kIn, c = i % kIn;
-    const int64_t row = base + r;
-    const float v = (row < n && c < n_in) ? X[row * n_in + c] : 0.0f;
-    const __nv_bfloat16 b = __float2bfloat16(v);
-    s.X[r][c] = b;
-    s.XT[c][r] = b;
-  }
-  for (int r = threadIdx.x; r < kS; r += blockDim.x) {
-    const int64_t row = base + r;
-    s.y[r] = (row < n && Y) ? Y[row] : 0.0f;
-    s.w[r] = (row < n && Wt) ? Wt[row] : 0.0f;
-  }
-}
-
-// Forward pass of the warp's 16 rows: layer 1 into Z1/H1 (+H1T), layer 2 in
-// registers (z2[j][4] for the 8 column tiles), prediction per row.
-__device__ void forward_rows(Smem &s, int r0, float z2[8][4], float &y_lo, float &y_hi,
-                             float b3) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma16816(c, &s.X[r0][0], kIn, &s.W1[8 * j][0], kIn);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
-      const float z = c[e] + s.b1[col];
-      s.Z1[row][col] = z;
-      const __nv_bfloat16 h = __float2bfloat16(silu(z));
-      s.H1[row][col] = h;
-      s.H1T[col][row] = h;
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) mma16816(c, &s.H1[r0][16 * kk], kH, &s.W2[8 * j][16 * kk], kH);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) z2[j][e] = c[e] + s.b2[8 * j + 2 * t + (e & 1)];
-  }
-  float lo = 0.f, hi = 0.f;
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float v = silu(z2[j][e]) * s.W3[8 * j + 2 * t + (e & 1)];
-      if (e < 2) lo += v; else hi += v;
-    }
-  lo += __shfl_xor_sync(0xffffffffu, lo, 1);
-  lo += __shfl_xor_sync(0xffffffffu, lo, 2);
-  hi += __shfl_xor_sync(0xffffffffu, hi, 1);
-  hi += __shfl_xor_sync(0xffffffffu, hi, 2);
-  y_lo = lo + b3;
-  y_hi = hi + b3;
-}
-
-// sum over the 8 row groups of a warp (lanes with equal t)
-__device__ __forceinline__ float sum_rows(float v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 16);
-  return v;
 }
 
 }  // namespace
 
-// Loss and gradient of sum_i w_i (f(x_i) - y_i)^2 / wsum over samples
-// [0, n); gradients are added into grad (FP32, zeroed by the caller) and the
-// loss into *loss.
-__global__ void __launch_bounds__(kThreads) k_mlp_grad(const float *__restrict__ p, int n_in,
-                                                       const float *__restrict__ X,
-                                                       const float *__restrict__ Y,
-                                                       const float *__restrict__ Wt, int64_t n,
-                                                       int64_t first, float inv_wsum,
-                                                       float *__restrict__ grad,
-                                                       double *__restrict__ loss) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  Smem &s = *reinterpret_cast<Smem *>(raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = 16 * warp;
-  load_weights(s, p, n_in);
+// ---- fifth-generation tensor cores (tcgen05): tiles of 128 samples -------
+constexpr int kTM = 128;                  // samples per tile = MMA M = TMEM lanes
+constexpr int kMbarTries = 1 << 22;       // bounded waits on MMA completion
+// set when a wait on the tensor cores ran out (read back by the host)
+__device__ int g_tc_timeout = 0;
+
+// shared memory of the tcgen05 forward pass (operands K-major, no swizzle)
+struct TcFwd {
+  __nv_bfloat16 W1[kH * kIn];             // B of layer 1: [out 64][in 16]
+  __nv_bfloat16 W2[kH * kH];              // B of layer 2: [out 64][in 64]
+  __nv_bfloat16 X[kTM * kIn];             // A of layer 1: [sample][in 16]
+  __nv_bfloat16 H1[kTM * kH];             // A of layer 2: [sample][hidden]
+  float b1[kH], b2[kH], W3[kH];
+  uint64_t mbar;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void st_bf16(void *tile, uint32_t off, float v) {
+  *reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(tile) + off) =
+      __float2bfloat16(v);
+}
+
+// Prediction for samples [0, n) with tcgen05: per tile, Z1 = X W1^T and
+// Z2 = H1 W2^T accumulate in tensor memory (columns [0, 64) and [64, 128));
+// thread r of the CTA owns sample row r (its tensor-memory lane).
+__global__ void __launch_bounds__(kTM) k_mlp_forward_tc(const float *__restrict__ p, int n_in,
+                                                         const float *__restrict__ X, int64_t n,
+                                                         float *__restrict__ out) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  TcFwd &s = *reinterpret_cast<TcFwd *>(raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const Params q = split(p, n_in);
+  for (int i = tid; i < kH * kIn; i += kTM) {
+    const int r = i / kIn, c = i % kIn;
+    st_bf16(s.W1, tc::kmaj(r, c, kIn), c < n_in ? q.W1[r * n_in + c] : 0.0f);
+  }
+  for (int i = tid; i < kH * kH; i += kTM) st_bf16(s.W2, tc::kmaj(i / kH, i % kH, kH), q.W2[i]);
+  for (int i = tid; i < kH; i += kTM) { s.b1[i] = q.b1[i]; s.b2[i] = q.b2[i]; s.W3[i] = q.W3[i]; }
   const float b3 = p[param_count(n_in) - 1];
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) { s.gW3[i] = 0.f; s.gb2[i] = 0.f; s.gb1[i] = 0.f; }
-  if (threadIdx.x == 0) { s.gb3 = 0.f; s.loss = 0.f; }
-  float acc2[8][4], acc1[2][4];   // this warp's rows of dL/dW2 and dL/dW1
-#pragma unroll
-  for (int j = 0; j < 8; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
-  acc1[0][0] = acc1[0][1] = acc1[0][2] = acc1[0][3] = 0.f;
-  acc1[1][0] = acc1[1][1] = acc1[1][2] = acc1[1][3] = 0.f;
+  if (warp == 0) tc::tmem_alloc(&s.tmem, 128);
+  if (tid == 0) { tc::mbar_init(&s.mbar, 1); s.abort = 0; }
+  tc::fence_before_sync();
   __syncthreads();
-
-  const float *Xs = X + first * n_in;
-  const float *Ys = Y + first;
-  const float *Ws = Wt + first;
-  for (int64_t base = (int64_t)blockIdx.x * kS; base < n; base += (int64_t)gridDim.x * kS) {
-    load_tile(s, Xs, Ys, Ws, n, n_in, base);
+  tc::fence_after_sync();
+  const uint32_t tm = s.tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t aX = tc::smem_u32(s.X), aW1 = tc::smem_u32(s.W1);
+  const uint32_t aH1 = tc::smem_u32(s.H1), aW2 = tc::smem_u32(s.W2);
+  uint32_t phase = 0;
+  bool pending = false;
+  for (int64_t base = (int64_t)blockIdx.x * kTM; base < n; base += (int64_t)gridDim.x * kTM) {
+    const int64_t row = base + tid;
+    for (int c = 0; c < kIn; ++c)
+      st_bf16(s.X, tc::kmaj(tid, c, kIn), (row < n && c < n_in) ? X[row * n_in + c] : 0.0f);
+    tc::fence_async_smem();
     __syncthreads();
-    float z2[8][4], y_lo, y_hi;
-    forward_rows(s, r0, z2, y_lo, y_hi, b3);
-    // dL/df per row, the loss, and dL/dz2
-    const int ra = r0 + g, rb = r0 + g + 8;
-    const float ea = y_lo - s.y[ra], eb = y_hi - s.y[rb];
-    const float da = 2.f * s.w[ra] * ea * inv_wsum, db = 2.f * s.w[rb] * eb * inv_wsum;
-    if (t == 0) atomicAdd(&s.loss, (s.w[ra] * ea * ea + s.w[rb] * eb * eb) * inv_wsum);
-    float gb3 = (t == 0) ? (da + db) : 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float gw3[2] = {0.f, 0.f}, gb2[2] = {0.f, 0.f};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int col = 8 * j + 2 * t + (e & 1);
-        const int row = (e < 2) ? ra : rb;
-        const float dy = (e < 2) ? da : db;
-        const float z = z2[j][e];
-        gw3[e & 1] += dy * silu(z);
-        const float d2 = dy * s.W3[col] * dsilu(z);
-        gb2[e & 1] += d2;
-        const __nv_bfloat16 b = __float2bfloat16(d2);
-        s.D2[row][col] = b;
-        s.D2T[col][row] = b;
-      }
-#pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
-        const float a = sum_rows(gw3[c2]), b = sum_rows(gb2[c2]);
-        if (g == 0) {
-          atomicAdd(&s.gW3[8 * j + 2 * t + c2], a);
-          atomicAdd(&s.gb2[8 * j + 2 * t + c2], b);
-        }
-      }
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::mma(tm, tc::desc(aX, 128, 256), tc::desc(aW1, 128, 256), tc::idesc_bf16(kTM, kH), 0);
+      tc::commit(&s.mbar);
     }
-    gb3 = sum_rows(gb3);
-    if (lane == 0) atomicAdd(&s.gb3, gb3);
-    __syncwarp();
-    // dL/dh1 = dL/dz2 * W2 (this warp's rows), then dL/dz1
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma16816(c, &s.D2[r0][16 * kk], kH, &s.W2T[8 * j][16 * kk], kH);
-      float gb1[2] = {0.f, 0.f};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int row = (e < 2) ? ra : rb, col = 8 * j + 2 * t + (e & 1);
-        const float d1 = c[e] * dsilu(s.Z1[row][col]);
-        gb1[e & 1] += d1;
-        s.D1T[col][row] = __float2bfloat16(d1);
-      }
-#pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2) {
-        const float a = sum_rows(gb1[c2]);
-        if (g == 0) atomicAdd(&s.gb1[8 * j + 2 * t + c2], a);
-      }
-    }
+    pending = true;
+    if (!tc::mbar_wait(&s.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
+    phase ^= 1u;
     __syncthreads();
-    // weight gradients over the whole tile: this warp owns output rows
-    // [16 warp, 16 warp + 16) of dW2 = D2^T H1 and dW1 = D1^T X
+    if (s.abort) break;
+    pending = false;
+    tc::fence_after_sync();
+    float z[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lane_base + 16 * q4, z);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma16816(acc2[j], &s.D2T[r0][16 * kk], kS, &s.H1T[8 * j][16 * kk], kS);
+      for (int c = 0; c < 16; ++c) st_bf16(s.H1, tc::kmaj(tid, 16 * q4 + c, kH), silu(z[c] + s.b1[16 * q4 + c]));
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+      for (int kk = 0; kk < kH / 16; ++kk)
+        tc::mma(tm + kH, tc::desc(aH1 + 256 * kk, 128, 1024), tc::desc(aW2 + 256 * kk, 128, 1024),
+                tc::idesc_bf16(kTM, kH), kk > 0);
+      tc::commit(&s.mbar);
+    }
+    pending = true;
+    if (!tc::mbar_wait(&s.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
+    phase ^= 1u;
+    __syncthreads();
+    if (s.abort) break;
+    pending = false;
+    tc::fence_after_sync();
+    float y = b3;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma16816(acc1[j], &s.D1T[r0][16 * kk], kS, &s.XT[8 * j][16 * kk], kS);
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lane_base + kH + 16 * q4, z);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) y += silu(z[c] + s.b2[16 * q4 + c]) * s.W3[16 * q4 + c];
+    }
+    if (row < n) out[row] = y;
+    tc::fence_before_sync();
     __syncthreads();
   }
-
-  // flush: this CTA's gradient into the global sum
-  float *gW1 = grad, *gb1 = gW1 + kH * n_in, *gW2 = gb1 + kH, *gb2 = gW2 + kH * kH;
-  float *gW3 = gb2 + kH, *gb3 = gW3 + kH;
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
-      atomicAdd(&gW2[row * kH + col], acc2[j][e]);
-    }
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = r0 + g + (e >> 1) * 8, col = 8 * j + 2 * t + (e & 1);
-      if (col < n_in) atomicAdd(&gW1[row * n_in + col], acc1[j][e]);
-    }
-  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-    atomicAdd(&gW3[i], s.gW3[i]);
-    atomicAdd(&gb2[i], s.gb2[i]);
-    atomicAdd(&gb1[i], s.gb1[i]);
-  }
-  if (threadIdx.x == 0) {
-    atomicAdd(gb3, s.gb3);
-    atomicAdd(loss, (double)s.loss);
+  // an MMA still in flight after a timed-out wait gets one more bounded wait
+  if (pending) tc::mbar_wait(&s.mbar, phase ^ 1u, kMbarTries);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tm, 128);
   }
 }
 
-// Prediction for samples [0, n).
-__global__ void __launch_bounds__(kThreads) k_mlp_forward(const float *__restrict__ p, int n_in,
-                                                          const float *__restrict__ X, int64_t n,
-                                                          float *__restrict__ out) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  Smem &s = *reinterpret_cast<Smem *>(raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = 16 * warp;
-  load_weights(s, p, n_in);
+// shared memory of the tcgen05 gradient kernel (operands K-major, no swizzle).
+// A CTA runs two independent tile pipelines (two groups of 4 warps); each
+// has its own operand tiles, tensor-memory columns, mbarrier and barrier.
+constexpr int kNB = 80;    // rows of BH: H1^T (64), ones (1), zero padding
+constexpr int kNX = 32;    // rows of XT: features (<= 16), ones (row 16), zero padding
+constexpr int kGroups = 2;
+struct TcTile {
+  __nv_bfloat16 X[kTM * kIn];             // A of Z1:  [sample][in]
+  __nv_bfloat16 XT[kNX * kTM];            // B of dW1: [feature | 1][sample]
+  __nv_bfloat16 H1[kTM * kH];             // A of Z2:  [sample][hidden]
+  __nv_bfloat16 BH[kNB * kTM];            // B of dW2: [H1^T | 1][sample]
+  __nv_bfloat16 D2[kTM * kH];             // A of dH1: [sample][out]
+  __nv_bfloat16 DT[kTM * kTM];            // A of dW2 / dW1: [D2^T | 0] then [D1^T | 0]
+  uint64_t mbar;
+  int abort;
+  int pad;
+};
+struct TcGrad {
+  __nv_bfloat16 W1[kH * kIn];             // B of Z1:  [out][in]
+  __nv_bfloat16 W2[kH * kH];              // B of Z2:  [out][in]
+  __nv_bfloat16 W2T[kH * kH];             // B of dH1: [in][out]
+  float b1[kH], b2[kH], W3[kH];
+  float red[kGroups * 4][kH + 2];         // per-warp sums of gW3, gb3, loss
+  uint32_t tmem;
+  int pad[3];
+  TcTile t[kGroups];
+};
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;\n" : : "r"(1 + g), "r"(kTM) : "memory");
+}
+
+// Loss sum_i w_i (f(x_i) - y_i)^2 / wsum over samples [0, n) and its gradient
+// (added into grad, zeroed by the caller) with tcgen05, 128 samples per tile and
+// two tiles in flight per CTA.  Tensor memory (512 columns), group g:
+// Z1 in [128 g, 128 g + 64), Z2 and later dH1 in [128 g + 64, 128 g + 128),
+// and its weight-gradient accumulators across tiles in [256 + 112 g,
+// 256 + 112 g + 80) (DT x BH: rows o < 64 hold dW2 (cols 0-63) and gb2
+// (col 64)) and [256 + 112 g + 80, 256 + 112 g + 112) (DT x XT: rows i < 64
+// hold dW1 (cols < n_in) and gb1 (col 16)).  Thread r of a group owns
+// sample row r of its tile (its tensor-memory lane); gW3 and gb3 build up in
+// registers and are reduced once at the end.
+__global__ void __launch_bounds__(kGroups * kTM) k_mlp_grad_tc(
+    const float *__restrict__ p, int n_in, const float *__restrict__ X,
+    const float *__restrict__ Y, const float *__restrict__ Wt, int64_t n, int64_t first,
+    float inv_wsum, float *__restrict__ grad, double *__restrict__ loss) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  TcGrad &s = *reinterpret_cast<TcGrad *>(raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = tid / kTM, r = tid % kTM;         // group and sample row
+  TcTile &t = s.t[g];
+  const Params q = split(p, n_in);
+  for (int i = tid; i < kH * kIn; i += kGroups * kTM) {
+    const int rr = i / kIn, c = i % kIn;
+    st_bf16(s.W1, tc::kmaj(rr, c, kIn), c < n_in ? q.W1[rr * n_in + c] : 0.0f);
+  }
+  for (int i = tid; i < kH * kH; i += kGroups * kTM) {
+    const int rr = i / kH, c = i % kH;
+    st_bf16(s.W2, tc::kmaj(rr, c, kH), q.W2[i]);
+    st_bf16(s.W2T, tc::kmaj(c, rr, kH), q.W2[i]);
+  }
+  for (int i = tid; i < kH; i += kGroups * kTM) { s.b1[i] = q.b1[i]; s.b2[i] = q.b2[i]; s.W3[i] = q.W3[i]; }
+  // constant rows of this group's tiles: ones of XT (16) and BH (64), zero padding
+  for (int rr = 0; rr < kNX; ++rr) st_bf16(t.XT, tc::kmaj(rr, r, kTM), rr == 16 ? 1.0f : 0.0f);
+  st_bf16(t.BH, tc::kmaj(kH, r, kTM), 1.0f);
+  for (int rr = kH + 1; rr < kNB; ++rr) st_bf16(t.BH, tc::kmaj(rr, r, kTM), 0.0f);
+  for (int rr = kH; rr < kTM; ++rr) st_bf16(t.DT, tc::kmaj(rr, r, kTM), 0.0f);
   const float b3 = p[param_count(n_in) - 1];
+  if (warp == 0) tc::tmem_alloc(&s.tmem, 512);
+  if (r == 0) { tc::mbar_init(&t.mbar, 1); t.abort = 0; }
+  tc::fence_before_sync();
   __syncthreads();
-  for (int64_t base = (int64_t)blockIdx.x * kS; base < n; base += (int64_t)gridDim.x * kS) {
-    load_tile(s, X, nullptr, nullptr, n, n_in, base);
-    __syncthreads();
-    float z2[8][4], y_lo, y_hi;
-    forward_rows(s, r0, z2, y_lo, y_hi, b3);
-    if (t == 0) {
-      const int64_t a = base + r0 + g, b = a + 8;
-      if (a < n) out[a] = y_lo;
-      if (b < n) out[b] = y_hi;
+  tc::fence_after_sync();
+  const uint32_t tm = s.tmem;
+  const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;   // this warp's lanes
+  const uint32_t cZ1 = 128u * g, cZ2 = cZ1 + 64, cW2 = 256u + 112u * g, cW1 = cW2 + 80;
+  const uint32_t aX = tc::smem_u32(t.X), aW1 = tc::smem_u32(s.W1), aH1 = tc::smem_u32(t.H1);
+  const uint32_t aW2 = tc::smem_u32(s.W2), aW2T = tc::smem_u32(s.W2T), aD2 = tc::smem_u32(t.D2);
+  const uint32_t aDT = tc::smem_u32(t.DT), aBH = tc::smem_u32(t.BH), aXT = tc::smem_u32(t.XT);
+  uint32_t phase = 0;
+  bool pending = false, started = false;
+  float my_loss = 0.0f, my_gb3 = 0.0f, gw3[kH];
+#pragma unroll
+  for (int o = 0; o < kH; ++o) gw3[o] = 0.0f;
+  const float *Xs = X + first * n_in;
+  const float *Ys = Y + first;
+  const float *Ws = Wt + first;
+  auto wait_mma = [&]() {
+    pending = true;
+    if (!tc::mbar_wait(&t.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); t.abort = 1; }
+    phase ^= 1u;
+    group_sync(g);
+    if (!t.abort) pending = false;
+    tc::fence_after_sync();
+    return !t.abort;
+  };
+  for (int64_t base = ((int64_t)blockIdx.x * kGroups + g) * kTM; base < n;
+       base += (int64_t)gridDim.x * kGroups * kTM) {
+    const int64_t row = base + r;
+    const bool valid = row < n;
+    const float yv = valid ? Ys[row] : 0.0f, wv = valid ? Ws[row] : 0.0f;
+    for (int c = 0; c < kIn; ++c) {
+      const float v = (valid && c < n_in) ? Xs[row * n_in + c] : 0.0f;
+      st_bf16(t.X, tc::kmaj(r, c, kIn), v);
+      if (c < n_in) st_bf16(t.XT, tc::kmaj(c, r, kTM), v);
     }
-    __syncthreads();
+    tc::fence_async_smem();
+    group_sync(g);
+    if (r == 0) {
+      tc::fence_after_sync();
+      tc::mma(tm + cZ1, tc::desc(aX, 128, 256), tc::desc(aW1, 128, 256), tc::idesc_bf16(kTM, kH), 0);
+      tc::commit(&t.mbar);
+    }
+    if (!wait_mma()) break;
+    // layer 1: H1 and H1^T
+    float v[16], u[16];
+#pragma unroll 1
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lb + cZ1 + 16 * q4, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int o = 16 * q4 + c;
+        const float h = silu(v[c] + s.b1[o]);
+        st_bf16(t.H1, tc::kmaj(r, o, kH), h);
+        st_bf16(t.BH, tc::kmaj(o, r, kTM), h);
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    group_sync(g);
+    if (r == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < kH / 16; ++kk)
+        tc::mma(tm + cZ2, tc::desc(aH1 + 256 * kk, 128, 1024), tc::desc(aW2 + 256 * kk, 128, 1024),
+                tc::idesc_bf16(kTM, kH), kk > 0);
+      tc::commit(&t.mbar);
+    }
+    if (!wait_mma()) break;
+    // layer 2 and the output: f, the loss, dL/df; then dL/dz2 and gW3
+    float f = b3;
+#pragma unroll 1
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) f += silu(v[c] + s.b2[16 * q4 + c]) * s.W3[16 * q4 + c];
+    }
+    const float e = f - yv;
+    const float dy = 2.0f * wv * e * inv_wsum;
+    my_loss += wv * e * e * inv_wsum;
+    my_gb3 += dy;
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int o = 16 * q4 + c;
+        const float z2 = v[c] + s.b2[o];
+        gw3[o] += dy * silu(z2);
+        const float d2 = dy * s.W3[o] * dsilu(z2);
+        st_bf16(t.D2, tc::kmaj(r, o, kH), d2);
+        st_bf16(t.DT, tc::kmaj(o, r, kTM), d2);
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    group_sync(g);
+    if (r == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < kH / 16; ++kk)           // dH1 = D2 W2 (over Z2's columns)
+        tc::mma(tm + cZ2, tc::desc(aD2 + 256 * kk, 128, 1024), tc::desc(aW2T + 256 * kk, 128, 1024),
+                tc::idesc_bf16(kTM, kH), kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < kTM / 16; ++kk)          // [dW2 | gb2] += DT BH
+        tc::mma(tm + cW2, tc::desc(aDT + 256 * kk, 128, 2048), tc::desc(aBH + 256 * kk, 128, 2048),
+                tc::idesc_bf16(kTM, kNB), (started || kk > 0) ? 1u : 0u);
+      tc::commit(&t.mbar);
+    }
+    if (!wait_mma()) break;
+    // dL/dz1 = dH1 * silu'(z1) -> DT rows [0, 64)
+#pragma unroll 1
+    for (int q4 = 0; q4 < 4; ++q4) {
+      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+      tc::ld16(tm + lb + cZ1 + 16 * q4, u);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int i = 16 * q4 + c;
+        st_bf16(t.DT, tc::kmaj(i, r, kTM), v[c] * dsilu(u[c] + s.b1[i]));
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    group_sync(g);
+    if (r == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < kTM / 16; ++kk)          // [dW1 | gb1] += DT XT
+        tc::mma(tm + cW1, tc::desc(aDT + 256 * kk, 128, 2048), tc::desc(aXT + 256 * kk, 128, 2048),
+                tc::idesc_bf16(kTM, kNX), (started || kk > 0) ? 1u : 0u);
+      tc::commit(&t.mbar);
+    }
+    started = true;
+    if (!wait_mma()) break;
+  }
+  if (pending) tc::mbar_wait(&t.mbar, phase ^ 1u, kMbarTries);
+  // gW3, gb3 and the loss: warp sums into shared memory, then one pass
+#pragma unroll
+  for (int o = 0; o < kH; ++o) {
+    float a = gw3[o];
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if (lane == 0) s.red[warp][o] = a;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    my_gb3 += __shfl_xor_sync(0xffffffffu, my_gb3, d);
+    my_loss += __shfl_xor_sync(0xffffffffu, my_loss, d);
+  }
+  if (lane == 0) { s.red[warp][kH] = my_gb3; s.red[warp][kH + 1] = my_loss; }
+  __syncthreads();
+  const bool ok = !s.t[0].abort && !s.t[1].abort;
+  float *gW1 = grad, *gb1 = gW1 + kH * n_in, *gW2 = gb1 + kH, *gb2 = gW2 + kH * kH;
+  float *gW3 = gb2 + kH, *gb3 = gW3 + kH;
+  if (ok && tid < kH + 2) {
+    float a = 0.0f;
+    for (int w = 0; w < kGroups * 4; ++w) a += s.red[w][tid];
+    if (tid < kH) atomicAdd(&gW3[tid], a);
+    else if (tid == kH) atomicAdd(gb3, a);
+    else atomicAdd(loss, (double)a);
+  }
+  if (ok && started && (warp & 3) < 2) {
+    // this group's accumulators: lanes 0-63 are warps 0, 1 of the group
+    tc::fence_after_sync();
+    const int o = r;                                  // 0..63
+    float v[16];
+#pragma unroll
+    for (int q4 = 0; q4 < 5; ++q4) {                  // columns 0-79 of DT BH
+      tc::ld16(tm + lb + cW2 + 16 * q4, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = 16 * q4 + c;
+        if (col < kH) atomicAdd(&gW2[o * kH + col], v[c]);
+        else if (col == kH) atomicAdd(&gb2[o], v[c]);
+      }
+    }
+    tc::ld16(tm + lb + cW1, v);
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < n_in) atomicAdd(&gW1[o * n_in + c], v[c]);
+    tc::ld16(tm + lb + cW1 + 16, v);
+    atomicAdd(&gb1[o], v[0]);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tm, 512);
   }
 }
 
@@ -353,30 +446,30 @@ __global__ void k_adam(int64_t np, float *__restrict__ p, float *__restrict__ m,
 
 // ---- host side -------------------------------------------------------------
 
-size_t mlp_smem_bytes() { return sizeof(Smem); }
+size_t mlp_smem_bytes() { return sizeof(TcGrad); }
 
 cudaError_t mlp_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem));
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(TcGrad));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(Smem));
+  return cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(TcFwd));
 }
 
 cudaError_t launch_mlp_grad(cudaStream_t st, int sms, const float *p, int n_in, const float *X,
                             const float *Y, const float *W, int64_t n, int64_t first,
                             float inv_wsum, float *grad, double *loss) {
-  const int64_t tiles = (n + kS - 1) / kS;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 2));
-  k_mlp_grad<<<grid, kThreads, sizeof(Smem), st>>>(p, n_in, X, Y, W, n, first, inv_wsum, grad, loss);
+  const int64_t tiles = (n + kTM - 1) / kTM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kGroups - 1) / kGroups, (int64_t)sms));
+  k_mlp_grad_tc<<<grid, kGroups * kTM, sizeof(TcGrad), st>>>(p, n_in, X, Y, W, n, first, inv_wsum, grad, loss);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_forward(cudaStream_t st, int sms, const float *p, int n_in, const float *X,
                                int64_t n, float *out) {
-  const int64_t tiles = (n + kS - 1) / kS;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 4));
-  k_mlp_forward<<<grid, kThreads, sizeof(Smem), st>>>(p, n_in, X, n, out);
+  const int64_t tiles = (n + kTM - 1) / kTM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 2));
+  k_mlp_forward_tc<<<grid, kTM, sizeof(TcFwd), st>>>(p, n_in, X, n, out);
   return cudaGetLastError();
 }
 
