@@ -430,7 +430,7 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1, prob=None):
         train_ms, ww_ms = 0.0, 0.0
         seed = 11
         for it in range(refits + 1):
-            rep = P.train_importance(mean, rel, epochs=6, min_ratio=1e-20)
+            rep = P.train_importance(mean, rel, epochs=6, batch=16384, min_ratio=1e-20)
             train_ms += rep["train_ms"] + rep["bake_ms"]
             if it < refits:
                 st, _ = P.run_ex(n_ww, seed, batches=16, mean=mean, relerr=rel)

@@ -23,6 +23,7 @@
 #include "launch.h"
 #include "problem.h"
 #include "tc.cuh"
+#include <cub/device/device_scan.cuh>
 
 namespace mcdc {
 namespace {
@@ -550,6 +551,28 @@ __global__ void k_normalize_targets(int64_t n, float *__restrict__ Y, const floa
     if (W[s] > 0.0f) Y[s] = (float)((Y[s] - mu) / sd);
 }
 
+// the scored samples only (weight > 0), in their order: flags, then a gather
+// at the exclusive prefix sum of the flags
+__global__ void k_sample_flags(int64_t n, const float *__restrict__ W, int32_t *__restrict__ flag) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    flag[s] = W[s] > 0.0f ? 1 : 0;
+}
+__global__ void k_sample_gather(int64_t n, int n_in, const float *__restrict__ X,
+                                const float *__restrict__ Y, const float *__restrict__ W,
+                                const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                                float *__restrict__ Xc, float *__restrict__ Yc,
+                                float *__restrict__ Wc) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    if (!flag[s]) continue;
+    const int64_t d = pos[s];
+    for (int k = 0; k < n_in; ++k) Xc[d * n_in + k] = X[s * n_in + k];
+    Yc[d] = Y[s];
+    Wc[d] = W[s];
+  }
+}
+
 __global__ void k_step_counter(int64_t *t) { *t += 1; }
 
 // Adam whose step count lives on the device (so a captured epoch can be
@@ -931,27 +954,49 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   CKM(cudaMemcpyAsync(hmom, mom, sizeof(hmom), cudaMemcpyDeviceToHost, st));
   CKM(cudaStreamSynchronize(st));
   if (!(hmom[0] > 0.0)) return fail(MCDC_ERR_INVALID, "the pilot tally scored no bin");
+  // training set: the scored bins only, compacted in sample order (the
+  // others carry zero weight and would only cost time)
+  int32_t *flag, *pos;
+  float *Xc, *Yc, *Wc;
+  void *scan_tmp = nullptr;
+  size_t scan_bytes = 0;
+  CKM(cudaMalloc(&flag, sizeof(int32_t) * nb)); fr.add(flag);
+  CKM(cudaMalloc(&pos, sizeof(int32_t) * nb)); fr.add(pos);
+  CKM(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, flag, pos, nb, st));
+  CKM(cudaMalloc(&scan_tmp, scan_bytes)); fr.add(scan_tmp);
+  k_sample_flags<<<blocks, 256, 0, st>>>(nb, W, flag);
+  CKM(cudaGetLastError());
+  CKM(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, flag, pos, nb, st));
+  int32_t last[2];
+  CKM(cudaMemcpyAsync(&last[0], pos + nb - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKM(cudaMemcpyAsync(&last[1], flag + nb - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKM(cudaStreamSynchronize(st));
+  const int64_t n_samples = (int64_t)last[0] + last[1];
+  CKM(cudaMalloc(&Xc, sizeof(float) * std::max<int64_t>(1, n_samples) * n_in)); fr.add(Xc);
+  CKM(cudaMalloc(&Yc, sizeof(float) * std::max<int64_t>(1, n_samples))); fr.add(Yc);
+  CKM(cudaMalloc(&Wc, sizeof(float) * std::max<int64_t>(1, n_samples))); fr.add(Wc);
+  k_sample_gather<<<blocks, 256, 0, st>>>(nb, n_in, X, Y, W, flag, pos, Xc, Yc, Wc);
+  CKM(cudaGetLastError());
   // per-minibatch weight sums (host side, from the device weights)
-  std::vector<float> hw(nb);
-  CKM(cudaMemcpy(hw.data(), W, sizeof(float) * nb, cudaMemcpyDeviceToHost));
+  const int64_t steps_used = (n_samples + o.batch - 1) / o.batch;
+  std::vector<float> hw(std::max<int64_t>(1, n_samples));
+  CKM(cudaMemcpyAsync(hw.data(), Wc, sizeof(float) * n_samples, cudaMemcpyDeviceToHost, st));
+  CKM(cudaStreamSynchronize(st));
   std::vector<float> inv(steps_per_epoch, 0.0f);
-  int64_t n_samples = 0;
-  for (int64_t b = 0; b < steps_per_epoch; ++b) {
+  for (int64_t b = 0; b < steps_used; ++b) {
     double ws = 0.0;
-    for (int64_t i = b * o.batch; i < std::min<int64_t>(nb, (b + 1) * o.batch); ++i) {
+    for (int64_t i = b * o.batch; i < std::min<int64_t>(n_samples, (b + 1) * o.batch); ++i)
       ws += hw[i];
-      n_samples += hw[i] > 0.0f;
-    }
     inv[b] = ws > 0.0 ? (float)(1.0 / ws) : 0.0f;
   }
   // one epoch as a CUDA graph: per minibatch zero the gradient, forward and
   // backward on the tensor cores, count the step, Adam
   CKM(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  for (int64_t b = 0; b < steps_per_epoch; ++b) {
+  for (int64_t b = 0; b < steps_used; ++b) {
     if (inv[b] == 0.0f) continue;
-    const int64_t first = b * o.batch, cnt = std::min<int64_t>(o.batch, nb - first);
+    const int64_t first = b * o.batch, cnt = std::min<int64_t>(o.batch, n_samples - first);
     cudaMemsetAsync(g, 0, sizeof(float) * np, st);
-    launch_mlp_grad(st, sms, prm, n_in, X, Y, W, cnt, first, inv[b], g, losses + b);
+    launch_mlp_grad(st, sms, prm, n_in, Xc, Yc, Wc, cnt, first, inv[b], g, losses + b);
     k_step_counter<<<1, 1, 0, st>>>(tstep);
     k_adam_dev<<<(int)((np + 255) / 256), 256, 0, st>>>(np, prm, m, v, g, (float)o.lr, tstep);
   }
