@@ -54,7 +54,8 @@ extern "C" {
 #define MCDC_ERR_CUDA           -3   /* a CUDA call failed                      */
 #define MCDC_ERR_BANK_OVERFLOW  -4   /* reserved: a split that finds no room is
                                         skipped (mcdc_stats.splits_dropped)    */
-#define MCDC_ERR_TIMEOUT        -5   /* a bounded device wait gave up           */
+#define MCDC_ERR_TIMEOUT        -5   /* a bounded device wait gave up (tensor-core
+                                        kernels of the importance network)     */
 #define MCDC_ERR_NO_DEVICE      -6   /* no usable sm_103 device                 */
 
 #define MCDC_BC_VACUUM   0
@@ -331,6 +332,15 @@ int mcdc_mlp_forward(const float *params, int32_t n_in, const float *X, int64_t 
  * gradient with respect to every parameter (same layout as params). */
 int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float *X, const float *y,
                        const float *w, int64_t n, float *grad, double *loss);
+
+/* Tries of the bounded waits on tensor-core completion inside the network's
+ * kernels (default 4194304; a negative value restores it).  A wait that runs
+ * out makes the kernel stop, await its work in flight, free its tensor
+ * memory and return; the call (mcdc_mlp_forward, mcdc_mlp_loss_grad,
+ * mcdc_train_importance) then fails with MCDC_ERR_TIMEOUT and the context
+ * stays usable.  With 0 every wait gives up at once: a way to exercise that
+ * failure path. */
+int mcdc_set_wait_limit(int32_t tries);
 
 /* Allocation-free run (the paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc while transport runs, e.g. a code

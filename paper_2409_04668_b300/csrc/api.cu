@@ -347,6 +347,7 @@ extern "C" int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc
 
 namespace {
 int autotune(mcdc_problem *pr, const DeviceLimits &dl) {
+  NvtxRange nvtx("autotune");
   const std::string key = tune_key(pr);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -412,6 +413,7 @@ const char *mcdc_last_error(void) { return g_err.c_str(); }
 int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const mcdc_source *src,
                         const mcdc_time_grid *time, const mcdc_options *opt,
                         struct mcdc_problem **out) {
+  NvtxRange nvtx("mcdc_problem_create");
   g_err.clear();
   if (!out) return fail(MCDC_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -726,6 +728,7 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
 }
 
 int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *stats) {
+  NvtxRange nvtx("mcdc_run_ex");
   g_err.clear();
   if (!pr || !a) return fail(MCDC_ERR_INVALID, "problem and args are required");
   if (a->n_histories == 0) return fail(MCDC_ERR_INVALID, "n_histories must be > 0");
@@ -832,6 +835,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       if (n == 0) break;
       if (n > (unsigned long long)pr->pc_cap)
         return fail(MCDC_ERR_BANK_OVERFLOW, "census bank overflow under population control");
+      NvtxRange nvtx_comb("comb");
       CombArgs c{};
       c.bank = pr->pc_bank;
       c.n = (int)n;

@@ -102,6 +102,7 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
                                 const uint64_t *n_histories, uint64_t seed, int32_t n_batches,
                                 double *const *mean_out, double *const *relerr_out,
                                 double *scalar_out, mcdc_stats *stats) {
+  NvtxRange nvtx("mcdc_run_batched");
   if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
   const int B = n_batches > 0 ? n_batches : 16;
   if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");

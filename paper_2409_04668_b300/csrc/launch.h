@@ -1,10 +1,19 @@
 // launch.h -- host-side entry points into the kernel translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include "common.cuh"
 
 namespace mcdc {
+
+// NVTX range for the scope (shows the library's phases in Nsight timelines)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Layout;
 

@@ -61,6 +61,10 @@ constexpr int kTM = 128;                  // samples per tile = MMA M = TMEM lan
 constexpr int kMbarTries = 1 << 22;       // bounded waits on MMA completion
 // set when a wait on the tensor cores ran out (read back by the host)
 __device__ int g_tc_timeout = 0;
+// tries of the waits on MMA completion (mcdc_set_wait_limit); a wait that
+// gives up leaves its MMA in flight, which the kernel still awaits (up to
+// kMbarTries) before freeing its tensor memory
+__device__ int g_tc_wait_limit = kMbarTries;
 
 // shared memory of the tcgen05 forward pass (operands K-major, no swizzle)
 struct TcFwd {
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(kTM) k_mlp_forward_tc(const float *__restrict_
       tc::commit(&s.mbar);
     }
     pending = true;
-    if (!tc::mbar_wait(&s.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
+    if (!tc::mbar_wait(&s.mbar, phase, g_tc_wait_limit)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
     phase ^= 1u;
     __syncthreads();
     if (s.abort) break;
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kTM) k_mlp_forward_tc(const float *__restrict_
       tc::commit(&s.mbar);
     }
     pending = true;
-    if (!tc::mbar_wait(&s.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
+    if (!tc::mbar_wait(&s.mbar, phase, g_tc_wait_limit)) { atomicOr(&g_tc_timeout, 1); s.abort = 1; }
     phase ^= 1u;
     __syncthreads();
     if (s.abort) break;
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(kGroups * kTM) k_mlp_grad_tc(
   const float *Ws = Wt + first;
   auto wait_mma = [&]() {
     pending = true;
-    if (!tc::mbar_wait(&t.mbar, phase, kMbarTries)) { atomicOr(&g_tc_timeout, 1); t.abort = 1; }
+    if (!tc::mbar_wait(&t.mbar, phase, g_tc_wait_limit)) { atomicOr(&g_tc_timeout, 1); t.abort = 1; }
     phase ^= 1u;
     group_sync(g);
     if (!t.abort) pending = false;
@@ -749,6 +753,21 @@ using namespace mcdc;
 namespace {
 int fail(int code, const std::string &m) { return mcdc::set_error(code, m); }
 
+// MCDC_ERR_TIMEOUT if a tensor-core wait gave up since the last check
+int tc_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCDC_ERR_CUDA, "reading the tensor-core status failed");
+  }
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int));
+    return fail(MCDC_ERR_TIMEOUT, "a wait on the tensor cores ran out (importance network)");
+  }
+  return MCDC_OK;
+}
+
 bool on_dev(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -814,7 +833,7 @@ extern "C" int mcdc_mlp_forward(const float *params, int32_t n_in, const float *
   CKM(launch_mlp_forward(nullptr, device_sms(), dp, n_in, dx, n, dout));
   if (dout != out) CKM(cudaMemcpy(out, dout, n * sizeof(float), cudaMemcpyDeviceToHost));
   CKM(cudaDeviceSynchronize());
-  return MCDC_OK;
+  return tc_status();
 }
 
 extern "C" int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float *X,
@@ -847,6 +866,15 @@ extern "C" int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float
   double lh = 0.0;
   CKM(cudaMemcpy(&lh, dl, sizeof(double), cudaMemcpyDeviceToHost));
   if (loss) *loss = lh;
+  return tc_status();
+}
+
+extern "C" int mcdc_set_wait_limit(int32_t tries) {
+  const int v = tries < 0 ? kMbarTries : tries;
+  if (cudaMemcpyToSymbol(g_tc_wait_limit, &v, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MCDC_ERR_CUDA, "setting the wait limit failed");
+  }
   return MCDC_OK;
 }
 
@@ -867,6 +895,7 @@ extern "C" void mcdc_default_mlp_options(mcdc_mlp_options *o) {
 extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilot_mean,
                                      const double *pilot_relerr, const mcdc_mlp_options *opt,
                                      mcdc_mlp_report *rep) {
+  NvtxRange nvtx("mcdc_train_importance");
   if (!pr || !pilot_mean) return fail(MCDC_ERR_INVALID, "problem and pilot tally are required");
   if (pr->P.pc_target > 0)
     return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
@@ -1056,6 +1085,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   }
   CKM(cudaEventRecord(e2, st));
   CKM(cudaStreamSynchronize(st));
+  if (int rc = tc_status()) return rc;      // the windows are not switched on
   // switch the problem to weight windows (w_U, w_S ratios as given)
   pr->P.ww_lower = pr->ww64;
   pr->P.ww_lower32 = pr->ww32;

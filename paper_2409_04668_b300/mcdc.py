@@ -130,6 +130,7 @@ SIGNATURES = {
                                         C.POINTER(mcdc_mlp_options), C.POINTER(mcdc_mlp_report)]),
     "mcdc_mlp_param_count": (C.c_int64, [C.c_int32]),
     "mcdc_mlp_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mcdc_set_wait_limit": (C.c_int, [C.c_int32]),
     "mcdc_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
@@ -165,6 +166,7 @@ mcdc_train_importance = _lib.mcdc_train_importance
 mcdc_mlp_param_count = _lib.mcdc_mlp_param_count
 mcdc_mlp_forward = _lib.mcdc_mlp_forward
 mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
+mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -355,6 +357,11 @@ def mlp_forward(params, X):
     out = np.zeros(X.shape[0], dtype=np.float32)
     check(mcdc_mlp_forward(_ptr(p), X.shape[1], _ptr(X), X.shape[0], _ptr(out)))
     return out
+
+
+def set_wait_limit(tries):
+    """Tries of the tensor-core kernels' bounded waits (negative: default)."""
+    check(mcdc_set_wait_limit(int(tries)))
 
 
 def mlp_loss_grad(params, X, y, w):

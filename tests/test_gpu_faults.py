@@ -3,7 +3,10 @@ find the warp stacks full does not fail or trap -- the children that find no
 room are not made, their parent keeps their weight, the count is reported,
 and the flux stays unbiased -- and the same context runs a correct problem
 right afterwards.  The kernels have no device-side waits, so there is no
-timeout path to exercise."""
+timeout path to exercise in the tracker.  The tensor-core kernels of the
+importance network do wait (on MMA completion, bounded): with the wait limit
+at zero every wait gives up, the call reports MCDC_ERR_TIMEOUT, and the same
+context computes correct results once the limit is restored."""
 import numpy as np
 import pytest
 
@@ -48,3 +51,24 @@ def test_split_overflow_drops_children_unbiased_and_the_context_survives(mcdc):
     o = O.run(p2, 5000, seed=2, batches=5)
     nz = o["sum1"] != 0
     np.testing.assert_allclose(g["sum1"][nz], o["sum1"][nz], rtol=1e-9)
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(mcdc):
+    rng = np.random.default_rng(5)
+    n_in = 8
+    p = rng.normal(0, 0.3, O.mlp_param_count(n_in))
+    X = rng.uniform(-1, 1, (3000, n_in))
+    y, w = rng.normal(size=3000), rng.uniform(0.5, 1.0, 3000)
+    try:
+        mcdc.set_wait_limit(0)
+        with pytest.raises(mcdc.MCDCError) as e:
+            mcdc.mlp_forward(p.astype(np.float32), X.astype(np.float32))
+        assert e.value.code == mcdc.MCDC_ERR_TIMEOUT
+        with pytest.raises(mcdc.MCDCError) as e:
+            mcdc.mlp_loss_grad(p, X, y, w)
+        assert e.value.code == mcdc.MCDC_ERR_TIMEOUT
+    finally:
+        mcdc.set_wait_limit(-1)
+    got = mcdc.mlp_forward(p.astype(np.float32), X.astype(np.float32))
+    ref = O.mlp_forward(p, X)
+    assert np.abs(got - ref).max() < 2e-2 * np.abs(ref).max()
