@@ -359,6 +359,7 @@ def run_batched_bench(args):
                       M.PREC_FP64: "f64"}[prec], "data": "synthetic",
             "config": {"workload": "c5_batched_256_problems", "problems": len(probs),
                        "histories_per_step": int(sum(hist)), "batches": 16,
+                       "block": st["block_size"], "ctas_per_sm": st["ctas_per_sm"],
                        "l2": "inputs (tallies 2.2 GB) larger than L2"},
             "segments_per_sec": segs / t, "clocks": clk.summary(), "gpu_launches": 16 * 3 + 1}
     for h in handles:

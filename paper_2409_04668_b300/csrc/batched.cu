@@ -6,7 +6,10 @@
 // CUDA graph and launched once.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -98,11 +101,13 @@ bool dev_ptr(const void *p) {
 }
 }  // namespace
 
-extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
-                                const uint64_t *n_histories, uint64_t seed, int32_t n_batches,
-                                double *const *mean_out, double *const *relerr_out,
-                                double *scalar_out, mcdc_stats *stats) {
-  NvtxRange nvtx("mcdc_run_batched");
+namespace {
+// One batched run with a given launch shape: threads per CTA and histories
+// per work item.
+int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_histories,
+                uint64_t seed, int32_t n_batches, double *const *mean_out,
+                double *const *relerr_out, double *scalar_out, mcdc_stats *stats, int block,
+                unsigned long long chunk) {
   if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
   const int B = n_batches > 0 ? n_batches : 16;
   if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");
@@ -134,7 +139,6 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
   TrackKey key = p0->key;
   key.shared = false;
   key.multi = true;
-  const int block = 256;
   Layout L{};
   for (int i = 0; i < n; ++i) {
     L.M = std::max(L.M, probs[i]->P.M);
@@ -185,7 +189,6 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
     total += p->P.n_bins;
   }
   // work items, batch by batch, largest first within a batch
-  const unsigned long long chunk = 1ull << 16;
   std::vector<WorkItem> items;
   std::vector<int> item_off(B + 1, 0);
   for (int b = 0; b < B; ++b) {
@@ -320,4 +323,65 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
   CKB(cudaMemcpy(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (herr) return fail(MCDC_ERR_BANK_OVERFLOW, "device error flag set");
   return MCDC_OK;
+}
+
+// launch shapes tried by the autotuner, and its choices per batch shape
+struct BatchedShape { int block; unsigned long long chunk; };
+std::mutex g_batched_mu;
+std::map<std::string, BatchedShape> g_batched_cache;
+}  // namespace
+
+extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
+                                const uint64_t *n_histories, uint64_t seed, int32_t n_batches,
+                                double *const *mean_out, double *const *relerr_out,
+                                double *scalar_out, mcdc_stats *stats) {
+  NvtxRange nvtx("mcdc_run_batched");
+  if (!probs || n < 1 || !n_histories || !probs[0]) return fail(MCDC_ERR_INVALID, "need problems and history counts");
+  // autotuner: the first time a batch shape is seen (problem count, total
+  // histories to a power of two, precision, dimension, largest tables),
+  // time each candidate launch shape on the same problems with an eighth of
+  // the histories and keep the fastest
+  uint64_t total = 0;
+  int maxM = 0, maxG = 0, maxT = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!probs[i]) return fail(MCDC_ERR_INVALID, "problem is NULL");
+    total += n_histories[i];
+    maxM = std::max(maxM, probs[i]->P.M);
+    maxG = std::max(maxG, probs[i]->P.G);
+    maxT = std::max(maxT, probs[i]->P.T);
+  }
+  int lg = 0;
+  while ((1ull << lg) < total && lg < 63) ++lg;
+  char kb[160];
+  snprintf(kb, sizeof kb, "%d|%d|%d|%d|%d|%d|%d|%d|%d", n, lg, (int)probs[0]->key.f64,
+           (int)probs[0]->key.local, probs[0]->dim, maxM, maxG, maxT, n_batches);
+  BatchedShape best{256, 1ull << 16};
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lk(g_batched_mu);
+    auto it = g_batched_cache.find(kb);
+    if (it != g_batched_cache.end()) { best = it->second; have = true; }
+  }
+  if (!have) {
+    const int B = n_batches > 0 ? n_batches : 16;
+    std::vector<uint64_t> trial(n);
+    for (int i = 0; i < n; ++i) trial[i] = std::max<uint64_t>((uint64_t)B, n_histories[i] / 8);
+    double best_ms = 1e300;
+    bool any = false;
+    for (int block : {128, 256, 512})
+      for (unsigned long long chunk : {1ull << 14, 1ull << 16}) {
+        mcdc_stats st{};
+        const int rc = run_batched(probs, n, trial.data(), seed ^ 0x5bd1e995ull, n_batches, nullptr,
+                                   nullptr, nullptr, &st, block, chunk);
+        if (rc == MCDC_ERR_INVALID) continue;        // this shape does not fit
+        if (rc != MCDC_OK) return rc;
+        any = true;
+        if (st.kernel_ms < best_ms) { best_ms = st.kernel_ms; best = {block, chunk}; }
+      }
+    if (!any) best = {256, 1ull << 16};
+    std::lock_guard<std::mutex> lk(g_batched_mu);
+    g_batched_cache[kb] = best;
+  }
+  return run_batched(probs, n, n_histories, seed, n_batches, mean_out, relerr_out, scalar_out, stats,
+                     best.block, best.chunk);
 }
