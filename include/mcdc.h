@@ -167,6 +167,9 @@ typedef struct mcdc_stats {
     double kernel_ms;           /* device time of the transport kernels      */
     double total_ms;            /* device time of the whole run              */
     int32_t block_size, bank_per_cta, ctas_per_sm, tally_mode, n_batches, warp_aggregate;
+                                /* launch shape used: threads per CTA, parked-
+                                   particle slots per CTA (warps x 96), CTAs per
+                                   SM, MCDC_TALLY_*, batches, warp aggregation  */
     uint64_t splits_dropped;    /* weight-window children not made because the warp
                                    stack and the spill bank were full: the parent
                                    kept their weight (unbiased, less variance

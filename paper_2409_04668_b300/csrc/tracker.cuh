@@ -1,19 +1,18 @@
 // tracker.cuh -- persistent, event-based particle tracker.
 //
-// Each CTA owns a bank of S particle slots (SoA, shared memory) and loops:
-//   refill   free slots <- split children (CTA-private overflow stack), then
-//            new source particles of its current work item;
-//   flight   every live particle takes one flight: distance to collision,
-//            mesh surface and time census, move, track-length tally; surface
-//            and census events are resolved in place; particles that reach a
-//            collision are queued;
-//   collide  the queued particles (now a dense list) absorb or scatter.
-// Queues are built with a warp ballot + popc prefix and one shared atomic
-// per warp, so every phase runs over a compacted list ("sort by event").
-// Cross-section tables sit in shared memory.  The tally is either a
-// CTA-private copy in shared memory holding one batch at a time (shared
-// mode) or a device-wide batch tally (global mode), both fed through
-// warp-aggregated atomics.
+// Every lane of a warp flies one particle held in registers; the warp's
+// flights are one dense pass.  A flight ends at a collision, a mesh surface,
+// a time census or the end of the history: surface and census events are
+// resolved in place, collisions park the particle in the warp's pool in
+// shared memory (a stack growing down), and once 32 are parked one dense
+// collision pass absorbs or scatters them and pushes the survivors on the
+// ready stack (growing up).  Empty lanes pop ready particles; when none are
+// ready, one dense pass of up to 32 births (split children first, then new
+// source histories) hands newborns to empty lanes by warp shuffle.  All
+// queues are built with warp ballots and popc prefixes.  Cross-section
+// tables sit in shared memory.  The tally is a CTA-private copy in shared
+// memory holding one batch at a time (shared mode) or a device-wide batch
+// tally, optionally one slice per batch (global mode).
 //
 // Per particle, the sequence of draws, distances and events is the same as
 // in the one-history-at-a-time loop of the paper's "MC/DC on CPUs" section,
