@@ -100,7 +100,9 @@ def test_invalid_problems_rejected_on_host(lib, case):
 
 
 @pytest.mark.parametrize("case", ["unknown_estimator", "cutoff_above_survival", "zero_cutoff",
-                                  "closed_steady_pure_scatterer", "closed_steady_void"])
+                                  "closed_steady_pure_scatterer", "closed_steady_void",
+                                  "comb_negative_target", "comb_with_shared_tally",
+                                  "comb_in_steady_state", "comb_source_after_first_bin"])
 def test_invalid_options_rejected_on_host(lib, case):
     p, kw = W.c2_two_region(), {}
     if case == "unknown_estimator":
@@ -109,6 +111,14 @@ def test_invalid_options_rejected_on_host(lib, case):
         kw["implicit"] = (0.5, 0.25)
     elif case == "zero_cutoff":
         kw["implicit"] = (0.0, 0.5)
+    elif case == "comb_negative_target":
+        kw["pc_target"] = -5
+    elif case == "comb_with_shared_tally":
+        kw.update(pc_target=100, tally_mode=lib.TALLY_SHARED)
+    elif case == "comb_in_steady_state":
+        p, kw["pc_target"] = W.c1_slab(), 100
+    elif case == "comb_source_after_first_bin":
+        p, kw["pc_target"] = _bad(p, src_t1=1.0), 100
     else:
         # steady state, every face reflecting: only absorption can end a history
         mat = np.zeros((2, 2, 2), np.uint8)
