@@ -404,13 +404,13 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     return out
 
 
-def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=1, prob=None):
+def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
     region x in [90, 100]), analog against the learned weight windows.  The
-    analog run's tally is the pilot; the network is refit once on the tally of
-    a first weight-window run (each such tally is an unbiased flux estimate
-    that reaches deeper).  T is the device time of the measured run; the
+    analog run's tally is the pilot; the network is refit twice, each time on
+    the tally of a weight-window run with the previous windows (each such
+    tally is an unbiased flux estimate that reaches deeper).  T is the device time of the measured run; the
     training time is reported beside it."""
     import torch
     prob = prob if prob is not None else W.c4_deep()
