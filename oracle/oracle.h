@@ -33,7 +33,7 @@ enum { ORC_SRC_ISOTROPIC = 0, ORC_SRC_BEAM = 1 };
 enum { ORC_EV_COLLISION = 0, ORC_EV_SURFACE = 1, ORC_EV_CENSUS = 2 };
 enum { ORC_END_ABSORBED = 1, ORC_END_LEAKED = 2, ORC_END_CENSUSED = 3,
        ORC_END_ROULETTE = 4 };
-enum { ORC_EST_TRACK = 0, ORC_EST_COLLISION = 1 };
+enum { ORC_EST_TRACK = 0, ORC_EST_COLLISION = 1, ORC_EST_COMBINED = 2 };
 
 /* One problem: mesh, materials, source, time grid, optional weight windows. */
 typedef struct {
@@ -66,7 +66,7 @@ typedef struct {
 
     int32_t region_lo[3], region_hi[3];  /* cell box of the scalar tally [lo,hi) */
 
-    int32_t estimator;         /* ORC_EST_TRACK or ORC_EST_COLLISION             */
+    int32_t estimator;         /* ORC_EST_TRACK, ORC_EST_COLLISION or ORC_EST_COMBINED */
     int32_t implicit_capture;  /* 1: survival biasing at collisions              */
     double weight_cutoff;      /* implicit capture: roulette below this weight   */
     double cutoff_survival;    /*   ... surviving with this weight               */
@@ -110,11 +110,24 @@ void orc_isotropic(double xi_mu, double xi_phi, double u[3]);
 
 /* Full run: histories [offset, offset+n) split into n_batches contiguous
  * batches; mean/relerr are [cells][G][max(T,1)]; scalar = {mean, relerr} of
- * the region sum.  Returns 0, or a negative value on invalid input. */
+ * the region sum.  With ORC_EST_COMBINED, sum1/sum2 hold [2][bins] (track
+ * length, then collision), sum12 [bins] the sums over batches of the product
+ * of the two batch sums, mean/relerr/scalar the combined estimate (R14) and
+ * scalar[2] the region's coefficient a; otherwise sum12 and scalar[2] are not
+ * written.  Returns 0, or a negative value on invalid
+ * input. */
 int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
             uint64_t offset, int32_t n_batches, int32_t n_threads,
-            double *mean, double *relerr, double *sum1, double *sum2,
+            double *mean, double *relerr, double *sum1, double *sum2, double *sum12,
             double *scalar, orc_counts *counts);
+
+/* R14: minimum-variance combination of two correlated batch series for n
+ * bins, from their batch sums s1, squared batch sums s2 and summed products
+ * s12 over B batches of n_hist histories, normalised by volume; any of mean,
+ * rel, alpha may be NULL. */
+void orc_combine(int64_t n, const double *s1x, const double *s2x, const double *s1y,
+                 const double *s2y, const double *s12, uint64_t n_hist, int32_t B,
+                 double vol, double *mean, double *rel, double *alpha);
 
 /* Replays the listed histories one by one and summarises each primary. */
 int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,

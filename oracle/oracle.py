@@ -51,7 +51,7 @@ RECORD_DTYPE = np.dtype([
     ("w", np.float64)], align=True)
 
 END_ABSORBED, END_LEAKED, END_CENSUSED, END_ROULETTE = 1, 2, 3, 4
-EST_TRACK, EST_COLLISION = 0, 1
+EST_TRACK, EST_COLLISION, EST_COMBINED = 0, 1, 2
 
 
 def lib():
@@ -66,12 +66,14 @@ def lib():
         L.orc_isotropic.argtypes = [C.c_double, C.c_double, C.c_void_p]
         L.orc_run.argtypes = [C.POINTER(OrcProblem), C.c_uint64, C.c_uint64, C.c_uint64,
                               C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
-                              C.c_void_p, C.c_void_p, C.POINTER(OrcCounts)]
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(OrcCounts)]
         L.orc_run.restype = C.c_int
         L.orc_trace.argtypes = [C.POINTER(OrcProblem), C.c_uint64, C.c_void_p, C.c_int64,
                                 C.c_void_p]
         L.orc_trace.restype = C.c_int
         L.orc_comb.argtypes = [C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]
+        L.orc_combine.argtypes = [C.c_int64] + [C.c_void_p] * 5 + [C.c_uint64, C.c_int32,
+                                                                    C.c_double] + [C.c_void_p] * 3
         if hasattr(L, "orc_mlp_forward"):
             _bind_mlp(L)
         _lib = L
@@ -162,28 +164,61 @@ def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=ES
         implicit=None, pc_target=0):
     """Runs histories [offset, offset+n); returns mean/relerr/sums shaped
     [nz, ny, nx, G, T], the region scalar and the event counts.  estimator:
-    EST_TRACK (track length) or EST_COLLISION; implicit: None or (weight
-    cutoff, survival weight) for implicit capture; pc_target: population
-    control, particles per batch after each comb at an interior census edge."""
+    EST_TRACK (track length), EST_COLLISION, or EST_COMBINED (both from the
+    same histories; mean/relerr/scalar are their minimum-variance combination,
+    sum1/sum2 gain a leading axis [track, collision], sum12 holds the summed
+    products of the two batch sums, alpha the track-length coefficient per bin
+    and scalar_alpha the region scalar's);
+    implicit: None or (weight cutoff, survival weight) for implicit capture;
+    pc_target: population control, particles per batch after each comb at an
+    interior census edge."""
     L = lib()
     keep = _Keep()
     s = _struct(prob, ww, keep, estimator, implicit, pc_target)
     nb = n_bins(prob)
-    mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
-    scalar = np.zeros(2)
+    ne = 2 if estimator == EST_COMBINED else 1
+    mean, rel, s12 = np.zeros(nb), np.zeros(nb), np.zeros(nb)
+    s1, s2 = np.zeros(ne * nb), np.zeros(ne * nb)
+    scalar = np.zeros(3)
     cnt = OrcCounts()
     if threads is None:
         threads = os.cpu_count() or 1
     rc = L.orc_run(C.byref(s), int(n), int(seed), int(offset), int(batches), int(threads),
                    mean.ctypes.data, rel.ctypes.data, s1.ctypes.data, s2.ctypes.data,
-                   scalar.ctypes.data, C.byref(cnt))
+                   s12.ctypes.data, scalar.ctypes.data, C.byref(cnt))
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     shp = tally_shape(prob)
     counts = {k: getattr(cnt, k) for k, _ in OrcCounts._fields_}
-    return {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "sum1": s1.reshape(shp),
-            "sum2": s2.reshape(shp), "scalar": (scalar[0], scalar[1]), "counts": counts,
-            "threads": int(threads)}
+    out = {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "scalar": (scalar[0], scalar[1]),
+           "counts": counts, "threads": int(threads)}
+    if ne == 2:
+        out["sum1"] = s1.reshape((2,) + shp)
+        out["sum2"] = s2.reshape((2,) + shp)
+        out["sum12"] = s12.reshape(shp)
+        alpha = np.zeros(nb)
+        vol = float(np.prod([w if np.isfinite(w) and w > 0 else 1.0 for w in prob.width]))
+        combine(s1[:nb], s2[:nb], s1[nb:], s2[nb:], s12, n, batches, vol, alpha=alpha)
+        out["alpha"] = alpha.reshape(shp)
+        out["scalar_alpha"] = scalar[2]
+    else:
+        out["sum1"] = s1.reshape(shp)
+        out["sum2"] = s2.reshape(shp)
+    return out
+
+
+def combine(s1x, s2x, s1y, s2y, s12, n_hist, batches, volume, alpha=None):
+    """Minimum-variance combination of two correlated batch series (the
+    oracle's R14) from their batch sums: returns (mean, relerr), and fills
+    alpha (the coefficient of the first series) if given."""
+    L = lib()
+    a = [np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (s1x, s2x, s1y, s2y, s12)]
+    k = len(a[0])
+    mean, rel = np.zeros(k), np.zeros(k)
+    ap = alpha.ctypes.data if alpha is not None else None
+    L.orc_combine(k, *[v.ctypes.data for v in a], int(n_hist), int(batches), float(volume),
+                  mean.ctypes.data, rel.ctypes.data, ap)
+    return mean, rel
 
 
 def trace(prob, seed, hids, ww=None, implicit=None, pc_target=0):

@@ -53,6 +53,17 @@
  *     state and history id, takes serial = word 0 of the block (key seed;
  *     counter 0xFFFFFFFD, parent serial, j, k) and restarts its counter.
  *     The next step runs the combed bank.
+ *  R14 combined estimator (optional): one run scores both R7 and R11 from
+ *     the same histories, into two tallies.  Per bin, with batch values x_b
+ *     (track length) and y_b (collision), the output is the minimum-variance
+ *     linear combination a x + (1 - a) y of the two batch means (the
+ *     combination of correlated estimators in Lux & Koblinger, "Monte Carlo
+ *     Particle Transport Methods", 1991): a = (s_yy - s_xy) / (s_xx + s_yy -
+ *     2 s_xy) from the sample (co)variances of the batch values, a = 1/2 when
+ *     that denominator is not positive (the two differ by a constant), and
+ *     the variance of the mean is that of the combination at this a divided
+ *     by B.  a is not clipped to [0, 1].  The region scalar is combined the
+ *     same way from its two batch series.
  */
 #include <math.h>
 #include <pthread.h>
@@ -317,7 +328,7 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
 
         /* track-length tally into (cell, group, time bin) */
         int64_t bin = (cell * G + P->g) * tb->T1 + (p->n_tbin > 0 ? P->tbin : 0);
-        if (p->estimator == ORC_EST_TRACK) tally[bin] += P->w * d;
+        if (p->estimator != ORC_EST_COLLISION) tally[bin] += P->w * d;
 
         move_particle(P, d);
 
@@ -355,7 +366,8 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
             /* collision: absorb or scatter, new group, new direction */
             P->n_col += 1;
             c->collisions += 1;
-            if (p->estimator == ORC_EST_COLLISION) tally[bin] += P->w / sig_t;   /* R11 */
+            if (p->estimator != ORC_EST_TRACK)                                 /* R11, R14 */
+                tally[(p->estimator == ORC_EST_COMBINED ? tb->n_bins : 0) + bin] += P->w / sig_t;
             pair r1 = draw(seed, hid, P);
             pair r2 = draw(seed, hid, P);
             double ratio = tb->scat_ratio[m * G + P->g];
@@ -535,7 +547,8 @@ static int make_tables(const orc_problem *p, tables *tb)
     build_cdf(p->src_pdf, G, tb->src_cdf);
     if (p->n_tbin > 0 && p->src_t0 < p->edges[0]) return -1;
     if (p->src_t1 < p->src_t0) return -1;
-    if (p->estimator != ORC_EST_TRACK && p->estimator != ORC_EST_COLLISION) return -1;
+    if (p->estimator != ORC_EST_TRACK && p->estimator != ORC_EST_COLLISION &&
+        p->estimator != ORC_EST_COMBINED) return -1;
     if (p->implicit_capture &&
         !(p->weight_cutoff > 0.0 && p->cutoff_survival > p->weight_cutoff)) return -1;
     if (p->pc_target < 0) return -1;
@@ -569,8 +582,10 @@ typedef struct {
     const tables *tb;
     uint64_t n, seed, offset;
     int32_t B, nthreads, tid;
-    double *s1, *s2;          /* thread partial sums over its batches */
-    double r1, r2;            /* region scalar partials               */
+    double *s1, *s2;          /* thread partial sums over its batches ([ne n_bins]) */
+    double *s12;              /* R14: sums of products track x collision, or NULL */
+    double r[5];              /* region scalar partials: s1, s2 (track or the one
+                                 estimator), s1, s2 (collision), s12 (R14)      */
     orc_counts c;
 } worker;
 
@@ -585,23 +600,32 @@ static void *work(void *arg)
 {
     worker *wk = (worker *)arg;
     const tables *tb = wk->tb;
-    double *tally = (double *)malloc((size_t)tb->n_bins * sizeof(double));
+    const int64_t nb = tb->n_bins;
+    const int ne = wk->p->estimator == ORC_EST_COMBINED ? 2 : 1;
+    double *tally = (double *)malloc((size_t)(ne * nb) * sizeof(double));
     for (int32_t b = wk->tid; b < wk->B; b += wk->nthreads) {
-        memset(tally, 0, (size_t)tb->n_bins * sizeof(double));
+        memset(tally, 0, (size_t)(ne * nb) * sizeof(double));
         uint64_t h0 = batch_start(wk->n, wk->B, b), h1 = batch_start(wk->n, wk->B, b + 1);
         if (wk->p->pc_target > 0)
             run_batch_pc(wk->p, tb, wk->seed, wk->offset + h0, wk->offset + h1, tally, &wk->c);
         else
             for (uint64_t h = h0; h < h1; ++h)
                 run_history(wk->p, tb, wk->seed, wk->offset + h, tally, &wk->c, NULL);
-        double region = 0.0;
-        for (int64_t k = 0; k < tb->n_bins; ++k) {
-            wk->s1[k] += tally[k];
-            wk->s2[k] += tally[k] * tally[k];
-            if (in_region(wk->p, k / ((int64_t)wk->p->n_grp * tb->T1))) region += tally[k];
-        }
-        wk->r1 += region;
-        wk->r2 += region * region;
+        double region[2] = {0.0, 0.0};
+        for (int e = 0; e < ne; ++e)
+            for (int64_t k = 0; k < nb; ++k) {
+                double v = tally[e * nb + k];
+                wk->s1[e * nb + k] += v;
+                wk->s2[e * nb + k] += v * v;
+                if (in_region(wk->p, k / ((int64_t)wk->p->n_grp * tb->T1))) region[e] += v;
+            }
+        if (ne == 2)
+            for (int64_t k = 0; k < nb; ++k) wk->s12[k] += tally[k] * tally[nb + k];
+        wk->r[0] += region[0];
+        wk->r[1] += region[0] * region[0];
+        wk->r[2] += region[1];
+        wk->r[3] += region[1] * region[1];
+        wk->r[4] += region[0] * region[1];
     }
     free(tally);
     return NULL;
@@ -634,9 +658,34 @@ static void batch_moments(double s1, double s2, uint64_t n, int32_t B, double vo
     *rel = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
 }
 
+/* R14: minimum-variance combination of two correlated batch series, bin by
+ * bin.  Batch values are x_b = B s_b / (N V); from the batch sums the sample
+ * moments are mean = sum / B and (co)variance = (sum of products - B mean
+ * mean') / (B - 1). */
+void orc_combine(int64_t n, const double *s1x, const double *s2x, const double *s1y,
+                 const double *s2y, const double *s12, uint64_t n_hist, int32_t B,
+                 double vol, double *mean, double *rel, double *alpha)
+{
+    const double Bd = (double)B, c = Bd / ((double)n_hist * vol);
+    for (int64_t k = 0; k < n; ++k) {
+        double mx = c * s1x[k] / Bd, my = c * s1y[k] / Bd;
+        double sxx = (c * c * s2x[k] - Bd * mx * mx) / (Bd - 1.0);
+        double syy = (c * c * s2y[k] - Bd * my * my) / (Bd - 1.0);
+        double sxy = (c * c * s12[k] - Bd * mx * my) / (Bd - 1.0);
+        double den = sxx + syy - 2.0 * sxy;
+        double a = den > 0.0 ? (syy - sxy) / den : 0.5;
+        double m = a * mx + (1.0 - a) * my;
+        double var = (a * a * sxx + (1.0 - a) * (1.0 - a) * syy + 2.0 * a * (1.0 - a) * sxy) / Bd;
+        if (var < 0.0) var = 0.0;
+        if (mean) mean[k] = m;
+        if (rel) rel[k] = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
+        if (alpha) alpha[k] = a;
+    }
+}
+
 int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
             uint64_t offset, int32_t n_batches, int32_t n_threads,
-            double *mean, double *relerr, double *sum1, double *sum2,
+            double *mean, double *relerr, double *sum1, double *sum2, double *sum12,
             double *scalar, orc_counts *counts)
 {
     tables tb;
@@ -644,6 +693,8 @@ int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
     if (make_tables(p, &tb) != 0) { free_tables(&tb); return -1; }
     if (n_threads < 1) n_threads = 1;
     if (n_threads > n_batches) n_threads = n_batches;
+    const int64_t nb = tb.n_bins;
+    const int ne = p->estimator == ORC_EST_COMBINED ? 2 : 1;
 
     worker *wk = (worker *)calloc((size_t)n_threads, sizeof(worker));
     pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
@@ -651,32 +702,47 @@ int orc_run(const orc_problem *p, uint64_t n_hist, uint64_t seed,
         wk[t].p = p; wk[t].tb = &tb; wk[t].n = n_hist; wk[t].seed = seed;
         wk[t].offset = offset; wk[t].B = n_batches; wk[t].nthreads = n_threads;
         wk[t].tid = t;
-        wk[t].s1 = (double *)calloc((size_t)tb.n_bins, sizeof(double));
-        wk[t].s2 = (double *)calloc((size_t)tb.n_bins, sizeof(double));
+        wk[t].s1 = (double *)calloc((size_t)(ne * nb), sizeof(double));
+        wk[t].s2 = (double *)calloc((size_t)(ne * nb), sizeof(double));
+        wk[t].s12 = ne == 2 ? (double *)calloc((size_t)nb, sizeof(double)) : NULL;
         pthread_create(&th[t], NULL, work, &wk[t]);
     }
     for (int32_t t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
 
     orc_counts c;
     memset(&c, 0, sizeof c);
-    double r1 = 0.0, r2 = 0.0;
-    for (int64_t k = 0; k < tb.n_bins; ++k) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int32_t t = 0; t < n_threads; ++t) { s1 += wk[t].s1[k]; s2 += wk[t].s2[k]; }
-        if (sum1) sum1[k] = s1;
-        if (sum2) sum2[k] = s2;
-        double m, rel;
-        batch_moments(s1, s2, n_hist, n_batches, tb.volume, &m, &rel);
-        if (mean) mean[k] = m;
-        if (relerr) relerr[k] = rel;
-    }
+    double *S1 = (double *)calloc((size_t)(ne * nb), sizeof(double));
+    double *S2 = (double *)calloc((size_t)(ne * nb), sizeof(double));
+    double *S12 = (double *)calloc((size_t)nb, sizeof(double));
+    double R[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int32_t t = 0; t < n_threads; ++t) {
-        r1 += wk[t].r1; r2 += wk[t].r2;
+        for (int64_t k = 0; k < ne * nb; ++k) { S1[k] += wk[t].s1[k]; S2[k] += wk[t].s2[k]; }
+        if (ne == 2)
+            for (int64_t k = 0; k < nb; ++k) S12[k] += wk[t].s12[k];
+        for (int q = 0; q < 5; ++q) R[q] += wk[t].r[q];
         add_counts(&c, &wk[t].c);
-        free(wk[t].s1); free(wk[t].s2);
+        free(wk[t].s1); free(wk[t].s2); free(wk[t].s12);
     }
-    if (scalar) batch_moments(r1, r2, n_hist, n_batches, tb.volume, &scalar[0], &scalar[1]);
+    if (sum1) memcpy(sum1, S1, (size_t)(ne * nb) * sizeof(double));
+    if (sum2) memcpy(sum2, S2, (size_t)(ne * nb) * sizeof(double));
+    if (sum12 && ne == 2) memcpy(sum12, S12, (size_t)nb * sizeof(double));
+    if (ne == 2) {
+        orc_combine(nb, S1, S2, S1 + nb, S2 + nb, S12, n_hist, n_batches, tb.volume,
+                    mean, relerr, NULL);
+        if (scalar)
+            orc_combine(1, &R[0], &R[1], &R[2], &R[3], &R[4], n_hist, n_batches, tb.volume,
+                        &scalar[0], &scalar[1], &scalar[2]);
+    } else {
+        for (int64_t k = 0; k < nb; ++k) {
+            double m, rel;
+            batch_moments(S1[k], S2[k], n_hist, n_batches, tb.volume, &m, &rel);
+            if (mean) mean[k] = m;
+            if (relerr) relerr[k] = rel;
+        }
+        if (scalar) batch_moments(R[0], R[1], n_hist, n_batches, tb.volume, &scalar[0], &scalar[1]);
+    }
     if (counts) *counts = c;
+    free(S1); free(S2); free(S12);
     free(wk); free(th);
     free_tables(&tb);
     return 0;

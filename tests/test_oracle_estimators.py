@@ -188,4 +188,4 @@ def test_estimator_options_validated():
     with pytest.raises(ValueError):
         O.run(prob, 100, seed=1, batches=4, implicit=(0.0, 0.5))
     with pytest.raises(ValueError):
-        O.run(prob, 100, seed=1, batches=4, estimator=2)
+        O.run(prob, 100, seed=1, batches=4, estimator=3)
