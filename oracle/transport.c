@@ -60,10 +60,13 @@
  *     combination of correlated estimators in Lux & Koblinger, "Monte Carlo
  *     Particle Transport Methods", 1991): a = (s_yy - s_xy) / (s_xx + s_yy -
  *     2 s_xy) from the sample (co)variances of the batch values, a = 1/2 when
- *     that denominator is not positive (the two differ by a constant), and
- *     the variance of the mean is that of the combination at this a divided
- *     by B.  a is not clipped to [0, 1].  The region scalar is combined the
- *     same way from its two batch series.
+ *     that denominator is not positive (the two differ by a constant), then
+ *     clipped to [0, 1], and the variance of the mean is that of the
+ *     combination at this a divided by B.  (Unclipped, a bin that only one
+ *     batch scores has perfectly correlated estimators, and their minimum-
+ *     variance combination extrapolates to an estimate of zero with zero
+ *     variance; clipped, the estimate stays between the two.)  The region
+ *     scalar is combined the same way from its two batch series.
  */
 #include <math.h>
 #include <pthread.h>
@@ -674,6 +677,8 @@ void orc_combine(int64_t n, const double *s1x, const double *s2x, const double *
         double sxy = (c * c * s12[k] - Bd * mx * my) / (Bd - 1.0);
         double den = sxx + syy - 2.0 * sxy;
         double a = den > 0.0 ? (syy - sxy) / den : 0.5;
+        if (a < 0.0) a = 0.0;
+        if (a > 1.0) a = 1.0;
         double m = a * mx + (1.0 - a) * my;
         double var = (a * a * sxx + (1.0 - a) * (1.0 - a) * syy + 2.0 * a * (1.0 - a) * sxy) / Bd;
         if (var < 0.0) var = 0.0;

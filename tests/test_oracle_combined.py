@@ -2,11 +2,13 @@
 here comes from the CUDA path).
 
 * the combination itself, on synthetic batch series: the coefficient and the
-  variance are the minimum over a fine grid of the sample variance of
-  a x + (1 - a) y (brute force, no formula retyped), also when the optimum
-  lies outside [0, 1] and for anticorrelated series; special cases: identical
-  series (a = 1/2, the single-series error), a constant second series (a = 0,
-  zero error);
+  variance are the minimum over a fine grid on [0, 1] of the sample variance
+  of a x + (1 - a) y (brute force, no formula retyped), for correlated,
+  anticorrelated and independent series and where the unconstrained optimum
+  lies outside [0, 1] (clipped: the end of the interval); special cases:
+  identical series (a = 1/2, the single-series error), a constant second
+  series (a = 0, zero error), a bin scored by one batch only (perfectly
+  correlated estimators: a clipped end, not an estimate of zero);
 * one run scoring both: its two halves equal, bit for bit, the sums of the
   track-length-only and collision-only runs with the same seed (the same
   histories), and the summed products equal those rebuilt from separate runs
@@ -34,7 +36,7 @@ def _sums(x, y, nv):
                                     (sx * sy).sum())]
 
 
-def _brute(x, y, lo=-4.0, hi=5.0, n=90_001):
+def _brute(x, y, lo=0.0, hi=1.0, n=100_001):
     """Grid minimum over a of the sample variance of the mean of a x + (1-a) y."""
     a = np.linspace(lo, hi, n)
     z = a[:, None] * x[None, :] + (1.0 - a[:, None]) * y[None, :]
@@ -51,7 +53,7 @@ def test_combination_is_the_grid_minimum(case):
     x = 10.0 + u
     y = {"positive": 10.0 + 0.6 * u + 0.5 * e,
          "negative": 10.0 - 0.7 * u + 0.4 * e,
-         "outside": 10.0 + 2.0 * u + 0.05 * e,      # optimum a near 2: no clipping
+         "outside": 10.0 + 2.0 * u + 0.05 * e,      # unconstrained optimum near 2
          "independent": 10.0 + 1.3 * e}[case]
     N, vol = 4000, 2.5
     alpha = np.zeros(1)
@@ -63,7 +65,7 @@ def test_combination_is_the_grid_minimum(case):
     # never worse than either estimator alone
     assert (m[0] * r[0]) ** 2 <= min(x.var(ddof=1), y.var(ddof=1)) / B * (1 + 1e-12)
     if case == "outside":
-        assert alpha[0] > 1.5
+        assert alpha[0] == 1.0
 
 
 def test_combination_special_cases():
@@ -82,6 +84,15 @@ def test_combination_special_cases():
     assert abs(alpha[0]) < 1e-12
     assert m[0] == pytest.approx(1.0, rel=1e-12)
     assert r[0] < 1e-6
+    # one scoring batch: y = (Y / X) x exactly; the unclipped optimum would be
+    # a = Y / (Y - X) and the estimate zero
+    X, Y = 6.0, 4.0
+    x1, y1 = np.zeros(B), np.zeros(B)
+    x1[3], y1[3] = X, Y
+    m, r = O.combine(*_sums(x1, y1, B), B, B, 1.0, alpha=alpha)
+    assert alpha[0] == 0.0                       # Y / (Y - X) = -2, clipped
+    assert m[0] == pytest.approx(Y / B, rel=1e-12)
+    assert r[0] == pytest.approx(y1.std(ddof=1) / math.sqrt(B) / y1.mean(), rel=1e-9)
 
 
 def _td_box():
