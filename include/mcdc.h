@@ -79,6 +79,13 @@ extern "C" {
 #define MCDC_EST_TRACK     0  /* track length: every flight scores w x d                     */
 #define MCDC_EST_COLLISION 1  /* collision: every collision scores w / sigma_t of the arriving
                                  particle (its group, cell and time bin before the collision) */
+#define MCDC_EST_COMBINED  2  /* both, from the same histories, into two tallies; the output
+                                 per bin (and for the region scalar) is their minimum-variance
+                                 combination a x + (1 - a) y of the track-length (x) and
+                                 collision (y) batch means, a = (s_yy - s_xy) / (s_xx + s_yy -
+                                 2 s_xy) from the sample (co)variances of the batch values
+                                 (a = 1/2 when that denominator is not positive), clipped to
+                                 [0, 1]; error from the variance of the combination at a  */
 
 /* Uniform Cartesian mesh.  An axis with n == 1 and width <= 0 or infinite is
  * unbounded (no faces): a 1-D slab is nx cells with ny = nz = 1 and
@@ -197,12 +204,21 @@ typedef struct mcdc_run_args {
     uint64_t hist_offset;       /* histories [offset, offset + n) are run         */
     double *mean_out;           /* [n_bins] or NULL; host or device               */
     double *relerr_out;         /* [n_bins] or NULL; host or device               */
-    double *sum1_out;           /* [n_bins] sum over batches of batch sums, or NULL */
-    double *sum2_out;           /* [n_bins] sum of squared batch sums, or NULL    */
+    double *sum1_out;           /* [n_bins] sum over batches of batch sums, or NULL;
+                                   combined estimator: [2][n_bins], track length then
+                                   collision                                      */
+    double *sum2_out;           /* [n_bins] sum of squared batch sums, or NULL (combined:
+                                   [2][n_bins])                                   */
     double *scalar_out;         /* [2] region scalar mean and relative error, or NULL (host) */
     mcdc_record *records;       /* [n_records] for histories offset..offset+n_records-1, or NULL (host or device) */
     uint64_t n_records;
     void *stream;               /* cudaStream_t; NULL: the legacy default stream  */
+    /* combined estimator only (ignored otherwise); host or device, or NULL: */
+    double *sum12_out;          /* [n_bins] sum over batches of (track-length batch sum x
+                                   collision batch sum)                           */
+    double *parts_out;          /* [5][n_bins] track-length mean, its relative error,
+                                   collision mean, its relative error, coefficient a */
+    double *scalar_parts_out;   /* [5] the same five for the region scalar (host)  */
 } mcdc_run_args;
 
 /* Fills *opt with defaults (FP32 split, automatic tally mode, autotuning on). */
@@ -250,7 +266,8 @@ void mcdc_problem_destroy(struct mcdc_problem *prob);
  * first, and load a problem's tables when they switch to it; then one fused
  * fold of every problem's batch tally; the whole run is one CUDA graph.  All
  * problems must share device, precision and dimension and have no weight
- * windows.  Problem i uses seed + i * 0x9E3779B97F4A7C15 (mod 2^64) and
+ * windows, implicit capture, population control or combined estimator.
+ * Problem i uses seed + i * 0x9E3779B97F4A7C15 (mod 2^64) and
  * histories [0, n_histories[i]) in n_batches batches (0: 16).
  * mean_out[i] / relerr_out[i]: [n_bins of problem i], host or device, or
  * NULL; scalar_out: [2n] region mean and relative error, or NULL.
@@ -357,7 +374,8 @@ int mcdc_set_wait_limit(int32_t tries);
  * event counters) lives in one fixed __device__ array of about 1.1 MiB that
  * every GPU loading the library holds until exit; no cudaMalloc or cudaFree
  * is called.  Limits: n_batches <= 4096 and, for a problem using the global
- * tally, at most 131072 bins; larger requests return MCDC_ERR_INVALID.  The
+ * tally, at most 131072 bins; larger requests, and problems with the combined
+ * estimator, return MCDC_ERR_INVALID.  The
  * first call on a device looks up the array's device address, so make that
  * first call before any stream capture.  Calls share the array: each clears
  * what must start at zero, and calls that overlap on the GPU race.  Event

@@ -120,7 +120,7 @@ Layout make_layout(const mcdc_problem *pr, int S, int tally_mode) {
   const bool f64 = pr->key.f64;
   L.tables_bytes = tables_bytes_of(f64, pr->P.M, pr->P.G, pr->P.T);
   L.tally_bytes = tally_mode == MCDC_TALLY_SHARED
-                      ? align16((long long)pr->P.n_bins * (f64 ? 8 : 4))
+                      ? align16((long long)pr->P.n_tally * (f64 ? 8 : 4))
                       : 0;
   L.bank_bytes = S * slot_bytes(f64, pr->dim, pr->key.local);
   L.total = (int)(L.tables_bytes + L.tally_bytes + L.bank_bytes + 64);
@@ -150,7 +150,7 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   // every warp parks up to kPool particles besides its 32 in flight
   const int S = (block / 32) * kPool;
   int mode = o.tally_mode;
-  const long long tally_b = (long long)pr->P.n_bins * (f64 ? 8 : 4);
+  const long long tally_b = (long long)pr->P.n_tally * (f64 ? 8 : 4);
   if (mode == MCDC_TALLY_AUTO) {
     const Layout Ls = make_layout(pr, S, MCDC_TALLY_SHARED);
     mode = (tally_b <= 96 * 1024 && Ls.total <= dl.smem_block - 1024) ? MCDC_TALLY_SHARED
@@ -208,7 +208,7 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
 // One zeroed device tally slice per batch, for runs that put every batch in
 // one launch (population control, weight-window runs).
 int ensure_slices(mcdc_problem *pr, int B) {
-  const long long bins = (long long)B * pr->P.n_bins;
+  const long long bins = (long long)B * pr->P.n_tally;
   if (pr->pc_tally_bins >= bins) return MCDC_OK;
   int rc;
   if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
@@ -423,7 +423,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (o.precision != MCDC_PREC_FP64 && o.precision != MCDC_PREC_FP32 &&
       o.precision != MCDC_PREC_FP32_LOCAL)
     return fail(MCDC_ERR_INVALID, "unknown precision");
-  if (o.estimator != MCDC_EST_TRACK && o.estimator != MCDC_EST_COLLISION)
+  if (o.estimator != MCDC_EST_TRACK && o.estimator != MCDC_EST_COLLISION &&
+      o.estimator != MCDC_EST_COMBINED)
     return fail(MCDC_ERR_INVALID, "unknown estimator");
   if (o.implicit_capture != 0 && o.implicit_capture != 1)
     return fail(MCDC_ERR_INVALID, "implicit_capture must be 0 or 1");
@@ -594,6 +595,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   P.t0 = src->t0;
   P.t1 = src->t1;
   P.estimator = o.estimator;
+  P.n_tally = P.n_bins * (o.estimator == MCDC_EST_COMBINED ? 2 : 1);
   P.implicit = o.implicit_capture;
   P.wcut = o.weight_cutoff;
   P.wsurv = o.cutoff_survival;
@@ -657,12 +659,16 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     if ((rc = upload(pr, &P.src_cdf32, f32(scdf)))) return bail(rc);
   }
   if ((rc = choose_shape(pr, dl))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->sum1, (size_t)P.n_bins))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->sum2, (size_t)P.n_bins))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->sum1, (size_t)P.n_tally))) return bail(rc);
+  if ((rc = dalloc(pr, &pr->sum2, (size_t)P.n_tally))) return bail(rc);
+  if (P.estimator == MCDC_EST_COMBINED)
+    if ((rc = dalloc(pr, &pr->sum12, (size_t)P.n_bins))) return bail(rc);
   if (pr->tally_mode == MCDC_TALLY_GLOBAL)
-    if ((rc = dalloc(pr, &pr->tally, (size_t)P.n_bins))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->region, 4))) return bail(rc);
-  pr->region_batch = pr->region + 2;
+    if ((rc = dalloc(pr, &pr->tally, (size_t)P.n_tally))) return bail(rc);
+  // region[0..4]: sums (track or the one estimator), squares, collision sums,
+  // squares, products; region_batch = region + 5: the batch's two region sums
+  if ((rc = dalloc(pr, &pr->region, 8))) return bail(rc);
+  pr->region_batch = pr->region + 5;
   if ((rc = dalloc(pr, &pr->stats, 1))) return bail(rc);
   if ((rc = dalloc(pr, &pr->error, 4))) return bail(rc);
   if ((rc = ensure_work_slots(pr, 64))) return bail(rc);
@@ -675,7 +681,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     return bail(MCDC_ERR_CUDA);
   }
   if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
-    cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_bins);
+    cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_tally);
     if (e != cudaSuccess) { fail(MCDC_ERR_CUDA, cudaGetErrorString(e)); return bail(MCDC_ERR_CUDA); }
   }
   if (o.autotune && o.block_size == 0 && o.pc_target == 0) {
@@ -741,9 +747,17 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   if (int rc = ensure_overflow(pr)) return rc;
   if (int rc = ensure_work_slots(pr, pr->tally_mode == MCDC_TALLY_GLOBAL ? B : 1)) return rc;
 
-  const size_t nb = (size_t)P.n_bins;
+  const size_t nb = (size_t)P.n_bins, nt = (size_t)P.n_tally;
+  const bool comb = P.estimator == MCDC_EST_COMBINED;
   const bool mean_dev = is_device_ptr(a->mean_out), rel_dev = is_device_ptr(a->relerr_out);
   const bool s1_dev = is_device_ptr(a->sum1_out), s2_dev = is_device_ptr(a->sum2_out);
+  double *const sum12_out = comb ? a->sum12_out : nullptr;
+  double *const parts_out = comb ? a->parts_out : nullptr;
+  const bool s12_dev = is_device_ptr(sum12_out), parts_dev = is_device_ptr(parts_out);
+  if (parts_out && !parts_dev && !pr->parts_tmp) {
+    int rc;
+    if ((rc = dalloc(pr, &pr->parts_tmp, 5 * nb))) return rc;
+  }
   const bool rec_dev = is_device_ptr(a->records);
   if (a->records && a->n_records == 0) return fail(MCDC_ERR_INVALID, "records given with n_records == 0");
   if (a->records && P.pc_target > 0)
@@ -771,9 +785,10 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   }
 
   CK(cudaEventRecord(pr->ev0, s));
-  CK(cudaMemsetAsync(pr->sum1, 0, nb * 8, s));
-  CK(cudaMemsetAsync(pr->sum2, 0, nb * 8, s));
-  CK(cudaMemsetAsync(pr->region, 0, 4 * sizeof(double), s));
+  CK(cudaMemsetAsync(pr->sum1, 0, nt * 8, s));
+  CK(cudaMemsetAsync(pr->sum2, 0, nt * 8, s));
+  if (comb) CK(cudaMemsetAsync(pr->sum12, 0, nb * 8, s));
+  CK(cudaMemsetAsync(pr->region, 0, 8 * sizeof(double), s));
   CK(cudaMemsetAsync(pr->stats, 0, sizeof(Stats), s));
   CK(cudaMemsetAsync(pr->error, 0, 4 * sizeof(int32_t), s));
   CK(cudaMemsetAsync(pr->work, 0, sizeof(unsigned long long) * pr->work_slots, s));
@@ -786,6 +801,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.n_batches = B;
   A.sum1 = pr->sum1;
   A.sum2 = pr->sum2;
+  A.sum12 = pr->sum12;
   A.region = pr->region;
   A.stats = pr->stats;
   A.records = rec_buf;
@@ -865,14 +881,14 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       A.spill_cap = (unsigned long long)pr->pc_combed_cap;
     }
     for (int b = 0; b < B; ++b)
-      CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nb, pr->sum1, pr->sum2, pr->region_batch,
-                     pr->region, pr->sms));
+      CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2, pr->sum12,
+                     pr->region_batch, pr->region, pr->sms));
   } else {
     const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
     // weight-window runs put every batch in one launch (one tally slice per
     // batch): a batch's few histories would leave most warps idle while a
     // handful work through their split families
-    const bool merged = spill && (double)B * (double)nb * 8.0 <= 8.0 * 1073741824.0;
+    const bool merged = spill && (double)B * (double)nt * 8.0 <= 8.0 * 1073741824.0;
     if (merged)
       if (int rc = ensure_slices(pr, B)) return rc;
     for (int b = 0; b < (merged ? 1 : B); ++b) {
@@ -912,10 +928,11 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       }
       if (merged) {
         for (int q = 0; q < B; ++q)
-          CK(launch_fold(s, P, pr->pc_tally + (size_t)q * nb, pr->sum1, pr->sum2, pr->region_batch,
-                         pr->region, pr->sms));
+          CK(launch_fold(s, P, pr->pc_tally + (size_t)q * nt, pr->sum1, pr->sum2, pr->sum12,
+                         pr->region_batch, pr->region, pr->sms));
       } else {
-        CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->region_batch, pr->region, pr->sms));
+        CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->sum12, pr->region_batch,
+                       pr->region, pr->sms));
       }
     }
   }
@@ -924,36 +941,50 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   // outputs
   double *mean_d = a->mean_out ? (mean_dev ? a->mean_out : pr->mean_tmp) : nullptr;
   double *rel_d = a->relerr_out ? (rel_dev ? a->relerr_out : pr->rel_tmp) : nullptr;
-  if (mean_d || rel_d)
+  double *parts_d = parts_out ? (parts_dev ? parts_out : pr->parts_tmp) : nullptr;
+  if (comb) {
+    if (mean_d || rel_d || parts_d)
+      CK(launch_finalize_combined(s, (int64_t)nb, pr->sum1, pr->sum2, pr->sum12, a->n_histories,
+                                  B, P.volume, mean_d, rel_d, parts_d, pr->sms));
+  } else if (mean_d || rel_d) {
     CK(launch_finalize(s, (int64_t)nb, pr->sum1, pr->sum2, a->n_histories, B, P.volume, mean_d,
                        rel_d, pr->sms));
+  }
+  const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost, d2d = cudaMemcpyDeviceToDevice;
   if (a->mean_out && !mean_dev)
-    CK(cudaMemcpyAsync(a->mean_out, pr->mean_tmp, nb * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(a->mean_out, pr->mean_tmp, nb * 8, d2h, s));
   if (a->relerr_out && !rel_dev)
-    CK(cudaMemcpyAsync(a->relerr_out, pr->rel_tmp, nb * 8, cudaMemcpyDeviceToHost, s));
-  if (a->sum1_out)
-    CK(cudaMemcpyAsync(a->sum1_out, pr->sum1, nb * 8, s1_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  if (a->sum2_out)
-    CK(cudaMemcpyAsync(a->sum2_out, pr->sum2, nb * 8, s2_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(a->relerr_out, pr->rel_tmp, nb * 8, d2h, s));
+  if (parts_out && !parts_dev)
+    CK(cudaMemcpyAsync(parts_out, pr->parts_tmp, 5 * nb * 8, d2h, s));
+  if (a->sum1_out) CK(cudaMemcpyAsync(a->sum1_out, pr->sum1, nt * 8, s1_dev ? d2d : d2h, s));
+  if (a->sum2_out) CK(cudaMemcpyAsync(a->sum2_out, pr->sum2, nt * 8, s2_dev ? d2d : d2h, s));
+  if (sum12_out) CK(cudaMemcpyAsync(sum12_out, pr->sum12, nb * 8, s12_dev ? d2d : d2h, s));
   if (a->records && !rec_dev)
-    CK(cudaMemcpyAsync(a->records, rec_buf, n_rec * sizeof(Record), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(pr->h_stats, pr->stats, sizeof(Stats), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(pr->h_error, pr->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  double region_h[2] = {0, 0};
-  const bool need_sync = (s == nullptr) || stats || a->scalar_out || (a->mean_out && !mean_dev) ||
+    CK(cudaMemcpyAsync(a->records, rec_buf, n_rec * sizeof(Record), d2h, s));
+  CK(cudaMemcpyAsync(pr->h_stats, pr->stats, sizeof(Stats), d2h, s));
+  CK(cudaMemcpyAsync(pr->h_error, pr->error, sizeof(int32_t), d2h, s));
+  double region_h[5] = {0, 0, 0, 0, 0};
+  const bool want_region = a->scalar_out || (comb && a->scalar_parts_out);
+  const bool need_sync = (s == nullptr) || stats || want_region || (a->mean_out && !mean_dev) ||
                          (a->relerr_out && !rel_dev) || (a->sum1_out && !s1_dev) ||
-                         (a->sum2_out && !s2_dev) || (a->records && !rec_dev);
-  if (a->scalar_out) CK(cudaMemcpyAsync(region_h, pr->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+                         (a->sum2_out && !s2_dev) || (a->records && !rec_dev) ||
+                         (sum12_out && !s12_dev) || (parts_out && !parts_dev);
+  if (want_region) CK(cudaMemcpyAsync(region_h, pr->region, 5 * sizeof(double), d2h, s));
   if (!need_sync) return MCDC_OK;
   CK(cudaStreamSynchronize(s));
-  if (a->scalar_out) {
-    const double nv = (double)a->n_histories * P.volume, Bd = (double)B;
-    const double m = region_h[0] / nv;
-    double ss = region_h[1] - region_h[0] * region_h[0] / Bd;
-    if (ss < 0.0) ss = 0.0;
-    const double var = (Bd * Bd / (nv * nv)) * ss / (Bd * (Bd - 1.0));
-    a->scalar_out[0] = m;
-    a->scalar_out[1] = m != 0.0 ? std::sqrt(var) / std::fabs(m) : 0.0;
+  if (comb && want_region) {
+    double m, rel, al;
+    combine_scalar(region_h, a->n_histories, B, P.volume, &m, &rel, &al);
+    if (a->scalar_out) { a->scalar_out[0] = m; a->scalar_out[1] = rel; }
+    if (double *sp = a->scalar_parts_out) {
+      scalar_moments(region_h[0], region_h[1], a->n_histories, B, P.volume, &sp[0], &sp[1]);
+      scalar_moments(region_h[2], region_h[3], a->n_histories, B, P.volume, &sp[2], &sp[3]);
+      sp[4] = al;
+    }
+  } else if (a->scalar_out) {
+    scalar_moments(region_h[0], region_h[1], a->n_histories, B, P.volume, &a->scalar_out[0],
+                   &a->scalar_out[1]);
   }
   if (stats) {
     const Stats &h = *pr->h_stats;

@@ -120,6 +120,8 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
       return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
     if (p->P.ww_lower != nullptr || p->P.implicit || p->P.pc_target > 0)
       return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
+    if (p->P.estimator == MCDC_EST_COMBINED)
+      return fail(MCDC_ERR_INVALID, "batched runs score one estimator (no combined estimator)");
     if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
   }
   CKB(cudaSetDevice(p0->device));

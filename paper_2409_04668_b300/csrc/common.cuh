@@ -24,6 +24,7 @@ struct DevProblem {
   int32_t bc[6];
   int32_t M, G, T, T1;        // T time bins (0: steady), T1 = max(T, 1)
   int64_t n_cells, n_bins;
+  int64_t n_tally;            // n_est x n_bins: one tally per estimator scored (2 when combined)
   double volume;
   const uint8_t *material;    // [cells]
   const double *faces[3];     // [n_a + 1] face coordinates origin + k * width (bounded axes)
@@ -50,7 +51,7 @@ struct DevProblem {
   int32_t ww_nmax;
   int32_t region_lo[3], region_hi[3];
   // estimator and collision physics options
-  int32_t estimator;          // 0 track length, 1 collision
+  int32_t estimator;          // 0 track length, 1 collision, 2 both (combined estimate)
   int32_t implicit;           // 1: implicit capture with weight-cutoff roulette
   double wcut, wsurv;         // cutoff and survival weight (implicit capture)
   float wcut32, wsurv32;
@@ -111,9 +112,11 @@ struct RunArgs {
   unsigned long long *work;
   int32_t batch;
   int32_t chunk;
-  double *tally;              // global mode: batch tally [n_bins]
-  double *sum1, *sum2;        // shared mode: folded per batch
-  double *region;             // [2]: sum of region batch sums and of their squares
+  double *tally;              // global mode: batch tally [n_est x n_bins]
+  double *sum1, *sum2;        // shared mode: folded per batch ([n_est x n_bins])
+  double *sum12;              // combined estimator: sums of track x collision batch products
+  double *region;             // [5]: region batch sums and squares (track or the one
+                              // estimator; collision), sum of their products
   Stats *stats;
   Record *records;            // or nullptr
   uint64_t n_records;
@@ -136,7 +139,7 @@ struct RunArgs {
   unsigned long long *census_count;
   unsigned long long census_cap;
   // population control runs every batch in each launch: the global tally is
-  // one slice of n_bins per batch, picked from the particle's history id
+  // one slice of n_est x n_bins per batch, picked from the particle's history id
   int32_t tally_per_batch;
 };
 

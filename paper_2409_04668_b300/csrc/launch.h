@@ -38,13 +38,28 @@ int track_regs(const TrackKey &key);
 // Resident CTAs per SM for a block size and dynamic shared memory.
 int track_occupancy(const TrackKey &key, int block, int smem_bytes);
 
-// batch fold (global tally mode): sum1 += x, sum2 += x^2, region partial, x = 0
+// batch fold (global tally mode): sum1 += x, sum2 += x^2, region partial, x = 0;
+// combined estimator: both halves of the tally and sum12 += x_track x_collision
+// (sum12 unused otherwise); region_batch [2], region [5]
 cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
-                        double *sum2, double *region_batch, double *region, int sms);
+                        double *sum2, double *sum12, double *region_batch, double *region,
+                        int sms);
 // mean and relative error from the batch sums (host-side formula mirrored)
 cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,
                             const double *sum2, uint64_t n_hist, int n_batches, double volume,
                             double *mean, double *relerr, int sms);
+// combined estimator: minimum-variance combination of the two halves per bin;
+// parts (or nullptr): [5][n_bins] track mean, relerr, collision mean, relerr, a
+cudaError_t launch_finalize_combined(cudaStream_t s, int64_t n_bins, const double *sum1,
+                                     const double *sum2, const double *sum12, uint64_t n_hist,
+                                     int n_batches, double volume, double *mean, double *relerr,
+                                     double *parts, int sms);
+// mean and relative error of one scalar from its batch sums, on the host
+void scalar_moments(double s1, double s2, uint64_t n_hist, int n_batches, double volume,
+                    double *mean, double *relerr);
+// the combination for one scalar (region[0..4] as in launch_fold), on the host
+void combine_scalar(const double r[5], uint64_t n_hist, int n_batches, double volume,
+                    double *mean, double *relerr, double *alpha);
 
 // Records the calling thread's error message (read by mcdc_last_error).
 int set_error(int code, const std::string &msg);

@@ -6,71 +6,152 @@ namespace mcdc {
 
 // Global-tally mode, after each batch: sum1 += x, sum2 += x*x, x = 0 for
 // every bin, plus the batch's region sum.  Reads 8 B per bin and
-// read-modify-writes 32 B per bin that scored.
+// read-modify-writes 32 B per bin that scored.  Combined estimator: the
+// collision tally (second half) likewise, plus sum12 += x_track x_collision
+// and the collision region sum.
 __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__restrict__ tally,
                                               double *__restrict__ sum1,
                                               double *__restrict__ sum2,
+                                              double *__restrict__ sum12,
                                               double *__restrict__ region_batch) {
-  __shared__ double red[16];
-  double rs = 0.0;
+  __shared__ double red[32];
+  double rs = 0.0, rc = 0.0;
   const long long per_cell = (long long)P.G * P.T1;
   const long long n = P.n_bins;
+  const bool comb = P.estimator == 2;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const double v = tally[q];
-    if (v != 0.0) {
+    const double vc = comb ? tally[n + q] : 0.0;
+    if (v != 0.0 || vc != 0.0) {
       sum1[q] += v;
       sum2[q] += v * v;
       tally[q] = 0.0;
+      if (comb) {
+        sum1[n + q] += vc;
+        sum2[n + q] += vc * vc;
+        sum12[q] += v * vc;
+        tally[n + q] = 0.0;
+      }
       const long long cell = q / per_cell;
       const int ci = (int)(cell % P.n[0]);
       const int cj = (int)((cell / P.n[0]) % P.n[1]);
       const int ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
       if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-          cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
+          cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2]) {
         rs += v;
+        rc += vc;
+      }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rs;
+  for (int o = 16; o > 0; o >>= 1) {
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    rc += __shfl_xor_sync(0xffffffffu, rc, o);
+  }
+  const int nw = (int)(blockDim.x >> 5);
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = rs; red[nw + (threadIdx.x >> 5)] = rc; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    if (t != 0.0) atomicAdd(region_batch, t);
+    double t = 0.0, tc = 0.0;
+    for (int w = 0; w < nw; ++w) { t += red[w]; tc += red[nw + w]; }
+    if (t != 0.0) atomicAdd(&region_batch[0], t);
+    if (tc != 0.0) atomicAdd(&region_batch[1], tc);
   }
 }
 
-__global__ void k_region_fold(double *region_batch, double *region) {
-  const double b = *region_batch;
+// region[0..1] += (b, b^2) of the track-length (or only) region batch sum b;
+// combined: region[2..3] for the collision sum c and region[4] += b c
+__global__ void k_region_fold(double *region_batch, double *region, bool comb) {
+  const double b = region_batch[0];
   region[0] += b;
   region[1] += b * b;
-  *region_batch = 0.0;
+  region_batch[0] = 0.0;
+  if (comb) {
+    const double c = region_batch[1];
+    region[2] += c;
+    region[3] += c * c;
+    region[4] += b * c;
+    region_batch[1] = 0.0;
+  }
 }
 
 // m_b = B s_b / (N V); mean = S1 / (N V); var of the mean from the spread of
 // the batch means: (B^2 / (N V)^2) (S2 - S1^2 / B) / (B (B - 1)).
+__host__ __device__ __forceinline__ void batch_moments(double s1, double s2, double nv, double B,
+                                                       double &m, double &rel) {
+  m = s1 / nv;
+  double ss = s2 - s1 * s1 / B;
+  if (ss < 0.0) ss = 0.0;
+  const double var = (B * B / (nv * nv)) * ss / (B * (B - 1.0));
+  rel = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
+}
+
 __global__ void __launch_bounds__(512) k_finalize(long long n, const double *__restrict__ sum1,
                                                   const double *__restrict__ sum2, double nv,
                                                   double B, double *__restrict__ mean,
                                                   double *__restrict__ relerr) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    const double s1 = sum1[q], s2 = sum2[q];
-    const double m = s1 / nv;
-    double ss = s2 - s1 * s1 / B;
-    if (ss < 0.0) ss = 0.0;
-    const double var = (B * B / (nv * nv)) * ss / (B * (B - 1.0));
+    double m, rel;
+    batch_moments(sum1[q], sum2[q], nv, B, m, rel);
     if (mean) mean[q] = m;
-    if (relerr) relerr[q] = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
+    if (relerr) relerr[q] = rel;
+  }
+}
+
+// Combined estimator, per bin: batch values x_b (track length) and y_b
+// (collision), each B s_b / (N V).  With the sample variances s_xx, s_yy and
+// covariance s_xy of the batch values, the minimum-variance combination
+// a x + (1 - a) y takes a = (s_yy - s_xy) / (s_xx + s_yy - 2 s_xy) (a = 1/2
+// if that denominator is not positive: the two differ by a constant), clipped
+// to [0, 1] (in a bin that one batch alone scores the two are perfectly
+// correlated and the unclipped optimum is an estimate of zero); the variance
+// of its mean is (a^2 s_xx + (1-a)^2 s_yy + 2 a (1-a) s_xy) / B.
+// parts (optional): [5][n] track mean, track relerr, collision mean,
+// collision relerr, a.
+__host__ __device__ __forceinline__ void combine_moments(double s1x, double s2x, double s1y, double s2y,
+                                                double s12, double nv, double B, double &m,
+                                                double &rel, double &a) {
+  const double c = B / nv;
+  const double mx = c * s1x / B, my = c * s1y / B;
+  const double sxx = (c * c * s2x - B * mx * mx) / (B - 1.0);
+  const double syy = (c * c * s2y - B * my * my) / (B - 1.0);
+  const double sxy = (c * c * s12 - B * mx * my) / (B - 1.0);
+  const double den = sxx + syy - 2.0 * sxy;
+  a = den > 0.0 ? (syy - sxy) / den : 0.5;
+  a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+  m = a * mx + (1.0 - a) * my;
+  double var = (a * a * sxx + (1.0 - a) * (1.0 - a) * syy + 2.0 * a * (1.0 - a) * sxy) / B;
+  if (var < 0.0) var = 0.0;
+  rel = m != 0.0 ? sqrt(var) / fabs(m) : 0.0;
+}
+
+__global__ void __launch_bounds__(512) k_finalize_combined(
+    long long n, const double *__restrict__ sum1, const double *__restrict__ sum2,
+    const double *__restrict__ sum12, double nv, double B, double *__restrict__ mean,
+    double *__restrict__ relerr, double *__restrict__ parts) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double s1x = sum1[q], s2x = sum2[q], s1y = sum1[n + q], s2y = sum2[n + q];
+    double m, rel, a;
+    combine_moments(s1x, s2x, s1y, s2y, sum12[q], nv, B, m, rel, a);
+    if (mean) mean[q] = m;
+    if (relerr) relerr[q] = rel;
+    if (parts) {
+      batch_moments(s1x, s2x, nv, B, parts[q], parts[n + q]);
+      batch_moments(s1y, s2y, nv, B, parts[2 * n + q], parts[3 * n + q]);
+      parts[4 * n + q] = a;
+    }
   }
 }
 
 cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
-                        double *sum2, double *region_batch, double *region, int sms) {
+                        double *sum2, double *sum12, double *region_batch, double *region,
+                        int sms) {
   const long long blocks = std::min<long long>((P.n_bins + 511) / 512, (long long)sms * 8);
-  k_fold<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(P, tally, sum1, sum2, region_batch);
-  k_region_fold<<<1, 1, 0, s>>>(region_batch, region);
+  k_fold<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(P, tally, sum1, sum2, sum12,
+                                                             region_batch);
+  k_region_fold<<<1, 1, 0, s>>>(region_batch, region, P.estimator == 2);
   return cudaGetLastError();
 }
 
@@ -81,6 +162,34 @@ cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,
   k_finalize<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(
       n_bins, sum1, sum2, (double)n_hist * volume, (double)n_batches, mean, relerr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_combined(cudaStream_t s, int64_t n_bins, const double *sum1,
+                                     const double *sum2, const double *sum12, uint64_t n_hist,
+                                     int n_batches, double volume, double *mean, double *relerr,
+                                     double *parts, int sms) {
+  const long long blocks = std::min<long long>((n_bins + 511) / 512, (long long)sms * 8);
+  k_finalize_combined<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(
+      n_bins, sum1, sum2, sum12, (double)n_hist * volume, (double)n_batches, mean, relerr, parts);
+  return cudaGetLastError();
+}
+
+void scalar_moments(double s1, double s2, uint64_t n_hist, int n_batches, double volume,
+                    double *mean, double *relerr) {
+  double m, rel;
+  batch_moments(s1, s2, (double)n_hist * volume, (double)n_batches, m, rel);
+  *mean = m;
+  *relerr = rel;
+}
+
+void combine_scalar(const double r[5], uint64_t n_hist, int n_batches, double volume,
+                    double *mean, double *relerr, double *alpha) {
+  double m, rel, a;
+  combine_moments(r[0], r[1], r[2], r[3], r[4], (double)n_hist * volume, (double)n_batches, m,
+                  rel, a);
+  if (mean) *mean = m;
+  if (relerr) *relerr = rel;
+  if (alpha) *alpha = a;
 }
 
 }  // namespace mcdc

@@ -36,7 +36,7 @@ constexpr int kMaxDevices = 64;
 struct Scratch {
   double tally[kMaxBins];
   unsigned long long work[kMaxBatches];
-  double region[4];     // region sum, sum of squares, batch partial, unused
+  double region[8];     // region sums and squares [0..4], batch partials [5..6]
   Stats stats;
   int32_t error[4];
 };
@@ -83,6 +83,8 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
   if (pr->P.pc_target > 0)
     return fail(MCDC_ERR_INVALID, "population control needs its bank buffers: use mcdc_run_ex");
+  if (pr->P.estimator == MCDC_EST_COMBINED)
+    return fail(MCDC_ERR_INVALID, "the combined estimator needs its second tally: use mcdc_run_ex");
   if (n_histories < 2) return fail(MCDC_ERR_INVALID, "n_histories must be >= 2");
   if (n_batches < 2 || (uint64_t)n_batches > n_histories)
     return fail(MCDC_ERR_INVALID, "need 2 <= n_batches <= n_histories");
@@ -146,7 +148,8 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
       A.chunk = (int)std::max<uint64_t>(
           32, std::min<uint64_t>(pr->S, per / ((uint64_t)pr->grid * 4) + 1));
       CKN(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, pr->P, A, pr->L));
-      CKN(launch_fold(s, pr->P, sc->tally, sum1, sum2, sc->region + 2, sc->region, pr->sms));
+      CKN(launch_fold(s, pr->P, sc->tally, sum1, sum2, nullptr, sc->region + 5, sc->region,
+                      pr->sms));
     }
   }
   if (mean || relerr)

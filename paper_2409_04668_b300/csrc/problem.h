@@ -27,6 +27,8 @@ struct mcdc_problem {
   std::vector<void *> allocs;
   double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
          *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
+  double *sum12 = nullptr;      // combined estimator: [n_bins]
+  double *parts_tmp = nullptr;  // combined estimator: [5][n_bins] staging of host parts_out
   mcdc::Stats *stats = nullptr;
   int32_t *error = nullptr;
   unsigned long long *work = nullptr;   // [max batches] work counters
@@ -44,8 +46,8 @@ struct mcdc_problem {
   // population control: census bank, combed bank and the comb's scratch
   int pc_cap = 0;                          // particles the census bank holds
   long long pc_combed_cap = 0;             // particles the combed bank holds
-  long long pc_tally_bins = 0;             // bins of the per-batch tally slices
-  double *pc_tally = nullptr;              // [batches][n_bins]
+  long long pc_tally_bins = 0;             // entries of the per-batch tally slices
+  double *pc_tally = nullptr;              // [batches][n_tally]
   int32_t *pc_bid = nullptr, *pc_seg = nullptr;
   int pc_seg_cap = 0;
   void *pc_bank = nullptr, *pc_combed = nullptr;

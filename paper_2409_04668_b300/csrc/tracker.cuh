@@ -495,7 +495,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     end = END_LEAKED;
     return OUT_DEAD;
   }
-  if (P.estimator == 0) {         // track-length estimator
+  if (P.estimator != 1) {         // track-length estimator (alone or combined)
     bin = bin_index(P, cell, p.g, p.tbin);
     score = p.w * d;
   }
@@ -576,7 +576,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   const int mg = m * P.G + p.g;
   p.ncol += 1;
   lc.col += 1;
-  if (P.estimator == 1) {
+  if (P.estimator != 0) {         // collision estimator (alone or combined)
     cbin = bin_index(P, cell, p.g, p.tbin);
     cscore = p.w / tb.sigma_t[mg];
   }
@@ -650,7 +650,7 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
 __device__ __forceinline__ long long tally_offset(const DevProblem &P, const RunArgs &A,
                                                   uint64_t hid) {
   if (!A.tally_per_batch) return 0;
-  return (long long)batch_of(A.n_hist, A.n_batches, hid - A.offset) * P.n_bins;
+  return (long long)batch_of(A.n_hist, A.n_batches, hid - A.offset) * P.n_tally;
 }
 
 // ---------------------------------------------------------------------------
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   __shared__ int s_novf[16];
   __shared__ double s_w[4];
   __shared__ uint32_t s_n[9];
-  __shared__ double s_red[16];
+  __shared__ double s_red[32];   // per-warp region sums (two estimators)
 
   // ---- tables of the current problem into shared memory
   auto load_tables = [&]() {
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   };
   if (!MULTI) load_tables();
   if (SHARED)
-    for (long long q = tid; q < P.n_bins; q += nth) stally[q] = (TT)0;
+    for (long long q = tid; q < P.n_tally; q += nth) stally[q] = (TT)0;
   if (tid < 16) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
@@ -863,9 +863,13 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
-          if (P.estimator == 1)
-            tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine, cbin, cscore,
-                                 mine ? tally_offset(P, A, q.hid) : 0);
+          if (P.estimator != 0) {
+            // combined estimator: the collision tally follows the track-length one
+            const long long coff = P.estimator == 2 ? P.n_bins : 0;
+            tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine,
+                                 (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
+                                 mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
+          }
           if (P.implicit) {
             // weight removed by implicit capture: one shared add per warp
             for (int o = 16; o > 0; o >>= 1) wabs += __shfl_xor_sync(0xffffffffu, wabs, o);
@@ -1017,32 +1021,51 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     if (MULTI) { __syncthreads(); continue; }   // the item is drained in every warp
     if (!SHARED) break;
     // ---- the batch is drained in every warp: fold the private tally
+    // (combined estimator: both halves, their product and both region sums)
     __syncthreads();
-    double rsum = 0.0;
+    double rsum = 0.0, rsum_c = 0.0;
     const long long per_cell = (long long)P.G * P.T1;
+    const bool comb = P.estimator == 2;
     for (long long q = tid; q < P.n_bins; q += nth) {
       const double v = (double)stally[q];
-      if (v != 0.0) {
+      const double vc = comb ? (double)stally[P.n_bins + q] : 0.0;
+      if (v != 0.0 || vc != 0.0) {
         atomicAdd(&A.sum1[q], v);
         atomicAdd(&A.sum2[q], v * v);
+        if (comb) {
+          atomicAdd(&A.sum1[P.n_bins + q], vc);
+          atomicAdd(&A.sum2[P.n_bins + q], vc * vc);
+          atomicAdd(&A.sum12[q], v * vc);
+          stally[P.n_bins + q] = (TT)0;
+        }
         const int cell = (int)(q / per_cell);
         const int ci = cell % P.n[0];
         const int cj = (cell / P.n[0]) % P.n[1];
         const int ck = cell / (P.n[0] * P.n[1]);
         if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-            cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
+            cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2]) {
           rsum += v;
+          rsum_c += vc;
+        }
         stally[q] = (TT)0;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-    if (lane == 0) s_red[warp] = rsum;
+    for (int o = 16; o > 0; o >>= 1) {
+      rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+      rsum_c += __shfl_xor_sync(0xffffffffu, rsum_c, o);
+    }
+    if (lane == 0) { s_red[warp] = rsum; s_red[nwarps + warp] = rsum_c; }
     __syncthreads();
     if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+      double tot = 0.0, tot_c = 0.0;
+      for (int w = 0; w < nwarps; ++w) { tot += s_red[w]; tot_c += s_red[nwarps + w]; }
       atomicAdd(&A.region[0], tot);
       atomicAdd(&A.region[1], tot * tot);
+      if (comb) {
+        atomicAdd(&A.region[2], tot_c);
+        atomicAdd(&A.region[3], tot_c * tot_c);
+        atomicAdd(&A.region[4], tot * tot_c);
+      }
     }
     __syncthreads();
   }

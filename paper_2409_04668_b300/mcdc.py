@@ -25,7 +25,7 @@ MCDC_ERR_INVALID, MCDC_ERR_OOM, MCDC_ERR_CUDA = -1, -2, -3
 MCDC_ERR_BANK_OVERFLOW, MCDC_ERR_TIMEOUT, MCDC_ERR_NO_DEVICE = -4, -5, -6
 PREC_FP64, PREC_FP32, PREC_FP32_LOCAL = 0, 1, 2
 TALLY_AUTO, TALLY_SHARED, TALLY_GLOBAL = 0, 1, 2
-EST_TRACK, EST_COLLISION = 0, 1
+EST_TRACK, EST_COLLISION, EST_COMBINED = 0, 1, 2
 
 
 class mcdc_mesh(C.Structure):
@@ -94,7 +94,9 @@ class mcdc_run_args(C.Structure):
                 ("hist_offset", C.c_uint64), ("mean_out", C.c_void_p),
                 ("relerr_out", C.c_void_p), ("sum1_out", C.c_void_p),
                 ("sum2_out", C.c_void_p), ("scalar_out", C.c_void_p),
-                ("records", C.c_void_p), ("n_records", C.c_uint64), ("stream", C.c_void_p)]
+                ("records", C.c_void_p), ("n_records", C.c_uint64), ("stream", C.c_void_p),
+                ("sum12_out", C.c_void_p), ("parts_out", C.c_void_p),
+                ("scalar_parts_out", C.c_void_p)]
 
 
 class mcdc_mlp_options(C.Structure):
@@ -198,7 +200,7 @@ class Problem:
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
                  overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0):
-        """estimator: EST_TRACK or EST_COLLISION; implicit: None (analog
+        """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
         at an interior census edge (0: off)."""
@@ -269,9 +271,13 @@ class Problem:
                                       float(survival_ratio), int(nmax)))
 
     def run_ex(self, n, seed, offset=0, batches=0, mean=None, relerr=None, sum1=None, sum2=None,
-               records=None, n_records=None, stream=None, want_scalar=True, want_stats=True):
+               records=None, n_records=None, stream=None, want_scalar=True, want_stats=True,
+               sum12=None, parts=None, scalar_parts=None):
         """One run; outputs are filled in place (numpy arrays or torch tensors).
-        Returns (stats dict or None, (scalar mean, scalar relerr) or None)."""
+        Combined estimator: sum1/sum2 hold [2, n_bins], sum12 [n_bins], parts
+        [5, n_bins] and scalar_parts [5] (numpy; track mean, relerr, collision
+        mean, relerr, coefficient).  Returns (stats dict or None, (scalar mean,
+        scalar relerr) or None)."""
         a = mcdc_run_args()
         a.n_histories = int(n)
         a.n_batches = int(batches)
@@ -287,6 +293,9 @@ class Problem:
         a.n_records = int(n_records if n_records is not None else
                           (len(records) if records is not None else 0))
         a.stream = stream
+        a.sum12_out = _ptr(sum12)
+        a.parts_out = _ptr(parts)
+        a.scalar_parts_out = _ptr(scalar_parts)
         st = mcdc_stats() if want_stats else None
         check(mcdc_run_ex(self.handle, C.byref(a), C.byref(st) if st is not None else None))
         stats = {k: getattr(st, k) for k, _ in mcdc_stats._fields_} if st is not None else None
@@ -338,16 +347,30 @@ class Problem:
 def run_numpy(prob, n, seed, offset=0, batches=0, records=0, **opts):
     """Convenience: one run with host outputs; returns a dict like the
     oracle wrapper's (mean, relerr, sum1, sum2 shaped [nz,ny,nx,G,T],
-    scalar, counts, records)."""
+    scalar, counts, records; with the combined estimator sum1/sum2 gain a
+    leading [track, collision] axis and sum12, parts, scalar_parts appear)."""
+    comb = opts.get("estimator", EST_TRACK) == EST_COMBINED
+    ne = 2 if comb else 1
     with Problem(prob, **opts) as P:
         nb = P.n_bins
-        mean, rel, s1, s2 = (np.zeros(nb) for _ in range(4))
+        mean, rel = np.zeros(nb), np.zeros(nb)
+        s1, s2 = np.zeros(ne * nb), np.zeros(ne * nb)
+        s12 = np.zeros(nb) if comb else None
+        parts = np.zeros(5 * nb) if comb else None
+        sparts = np.zeros(5) if comb else None
         rec = np.zeros(records, dtype=RECORD_DTYPE) if records else None
         stats, scal = P.run_ex(n, seed, offset=offset, batches=batches, mean=mean, relerr=rel,
-                               sum1=s1, sum2=s2, records=rec)
+                               sum1=s1, sum2=s2, records=rec, sum12=s12, parts=parts,
+                               scalar_parts=sparts)
         shp = P.shape
-    return {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "sum1": s1.reshape(shp),
-            "sum2": s2.reshape(shp), "scalar": scal, "counts": stats, "records": rec}
+    out = {"mean": mean.reshape(shp), "relerr": rel.reshape(shp), "scalar": scal,
+           "counts": stats, "records": rec}
+    if comb:
+        out.update(sum1=s1.reshape((2,) + shp), sum2=s2.reshape((2,) + shp),
+                   sum12=s12.reshape(shp), parts=parts.reshape((5,) + shp), scalar_parts=sparts)
+    else:
+        out.update(sum1=s1.reshape(shp), sum2=s2.reshape(shp))
+    return out
 
 
 def mlp_forward(params, X):

@@ -106,7 +106,7 @@ def test_invalid_problems_rejected_on_host(lib, case):
 def test_invalid_options_rejected_on_host(lib, case):
     p, kw = W.c2_two_region(), {}
     if case == "unknown_estimator":
-        kw["estimator"] = 2
+        kw["estimator"] = 3
     elif case == "cutoff_above_survival":
         kw["implicit"] = (0.5, 0.25)
     elif case == "zero_cutoff":
