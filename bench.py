@@ -371,13 +371,16 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     """The headline workload in the other modes of the tracker: device-timed
     histories/s and the region scalar's figure of merit 1/(relerr^2 T) for
     the cell-local FP32 mode and, in the headline precision, for the
-    collision estimator, for implicit capture (weight cutoff 0.25,
-    survival weight 0.5) and for population control (32 batches, each combed
-    back to its own size at every interior time edge)."""
+    collision estimator, for the combined track-length/collision estimator
+    (both tallies, their minimum-variance combination), for implicit capture
+    (weight cutoff 0.25, survival weight 0.5) and for population control (32
+    batches, each combed back to its own size at every interior time
+    edge)."""
     prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
     modes = {"track_analog": {"precision": prec},
              "fp32_local": {"precision": M.PREC_FP32_LOCAL},
              "collision_estimator": {"precision": prec, "estimator": M.EST_COLLISION},
+             "combined_estimator": {"precision": prec, "estimator": M.EST_COMBINED},
              "implicit_capture": {"precision": prec, "implicit": (0.25, 0.5)},
              "population_control": {"precision": prec, "pc_target": n_hist // 32}}
     out = {}
