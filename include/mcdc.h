@@ -65,7 +65,8 @@ extern "C" {
 #define MCDC_SRC_BEAM      1
 
 #define MCDC_PREC_FP64   0   /* every step in FP64: event-exact with the FP64 reference      */
-#define MCDC_PREC_FP32   1   /* FP32 direction/distance/xs, FP64 position, time and tallies  */
+#define MCDC_PREC_FP32   1   /* FP32 direction/distance/xs, FP64 position, time and tallies
+                                (see mcdc_options.flight_sampling)                          */
 #define MCDC_PREC_FP32_LOCAL 2 /* FP32 flights: positions as FP32 offsets from exact FP64 cell
                                   faces, time as FP32 time to the next exact FP64 census edge;
                                   FP64 tally reduction                                         */
@@ -163,6 +164,16 @@ typedef struct mcdc_options {
                                    Needs >= 2 time bins, every source particle
                                    born in the first bin, the global tally, no
                                    weight windows and no per-history records      */
+    int32_t flight_sampling;    /* FP32 modes, distance to collision: 0 (default)
+                                   carries the optical depth (mean free paths) to
+                                   the next collision across surface and census
+                                   events and draws it only at births, collisions
+                                   and for new split children -- the same
+                                   distribution, no random number per flight; 1
+                                   samples it afresh every flight as FP64 mode
+                                   does, so an FP32 run draws the same random
+                                   numbers as its FP64 twin (paired precision
+                                   studies).  FP64 mode always samples afresh.   */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */

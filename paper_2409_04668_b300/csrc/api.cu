@@ -327,9 +327,9 @@ std::map<std::string, TuneChoice> g_tune_cache;
 std::string tune_key(const mcdc_problem *pr) {
   const DevProblem &P = pr->P;
   char b[256];
-  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
+  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
            (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T, (long long)P.n_bins,
-           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit);
+           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit, P.fresh_tau);
   return b;
 }
 
@@ -432,6 +432,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
       !(std::isfinite(o.cutoff_survival) && o.weight_cutoff > 0.0 && o.cutoff_survival > o.weight_cutoff))
     return fail(MCDC_ERR_INVALID, "implicit capture needs 0 < weight_cutoff < cutoff_survival");
   if (o.pc_target < 0) return fail(MCDC_ERR_INVALID, "pc_target must be >= 0");
+  if (o.flight_sampling != 0 && o.flight_sampling != 1)
+    return fail(MCDC_ERR_INVALID, "flight_sampling must be 0 or 1");
   if (o.pc_target > 0 && o.tally_mode == MCDC_TALLY_SHARED)
     return fail(MCDC_ERR_INVALID, "population control runs on the global tally");
 
@@ -602,6 +604,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   P.wcut32 = (float)o.weight_cutoff;
   P.wsurv32 = (float)o.cutoff_survival;
   P.pc_target = o.pc_target;
+  P.fresh_tau = o.flight_sampling;
   if (o.pc_target > 0) pr->opt.tally_mode = MCDC_TALLY_GLOBAL;
   for (int a = 0; a < 3; ++a) {
     int hi = o.region_hi[a] > 0 ? o.region_hi[a] : n[a];

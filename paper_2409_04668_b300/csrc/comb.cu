@@ -106,6 +106,7 @@ __global__ void k_comb_teeth(const PT *__restrict__ bank, const uint32_t *__rest
     const U4 h = philox4x32_10_rk(0xFFFFFFFDu, q.serial, step, (uint32_t)k, rk);
     q.serial = h.a;
     q.ctr = 0;
+    q.tau = -1.0f;            // FP32 modes: every copy draws its own optical depth
     q.w = (R)wn;
     out[base + k] = q;
   }

@@ -56,6 +56,7 @@ struct DevProblem {
   double wcut, wsurv;         // cutoff and survival weight (implicit capture)
   float wcut32, wsurv32;
   int32_t pc_target;          // population control: particles per batch after a comb (0: off)
+  int32_t fresh_tau;          // FP32 modes: 1 = sample the distance to collision every flight
 };
 
 // One particle as it moves between the tracker phases (kept in registers).
@@ -74,6 +75,7 @@ struct Part {
   uint32_t ctr, serial;
   uint64_t hid;
   uint32_t nseg, ncol, ncross;
+  float tau;          // FP32 modes: mean free paths left to the next collision (< 0: draw afresh)
 };
 
 // Per-history record (mirrors mcdc_record).

@@ -83,6 +83,7 @@ struct Bank {
   uint4 *ids;         // {ctr, serial, hid low, hid high}
   uint4 *cell;        // {i | j << 16, k | tbin << 16, g, nseg}
   uint2 *cnt;         // {ncol, ncross}
+  float *tau;         // FP32 modes: optical depth to the next collision
 
   __device__ __forceinline__ void load(int s, PartOf<PR> &p, int dim) const {
     if constexpr (PR::kLocal) {
@@ -109,6 +110,7 @@ struct Bank {
     p.g = (int)ce.z; p.nseg = ce.w;
     const uint2 cn = cnt[s];
     p.ncol = cn.x; p.ncross = cn.y;
+    if constexpr (!PR::kF64) p.tau = tau[s];
   }
   __device__ __forceinline__ void store(int s, const PartOf<PR> &p, int dim) const {
     if constexpr (PR::kLocal) {
@@ -127,12 +129,13 @@ struct Bank {
     cell[s] = make_uint4((uint32_t)p.i | ((uint32_t)p.j << 16), (uint32_t)p.k | ((uint32_t)p.tbin << 16),
                          (uint32_t)p.g, p.nseg);
     cnt[s] = make_uint2(p.ncol, p.ncross);
+    if constexpr (!PR::kF64) tau[s] = p.tau;
   }
 };
 
 // bytes of one pool slot (kept in sync with the carve in k_track)
 __host__ __device__ inline int slot_bytes(bool f64, int dim, bool local) {
-  return 16 + ((dim == 3 && !local) ? 16 : 0) + (f64 ? 32 : 16) + 16 + 16 + 8;
+  return 16 + ((dim == 3 && !local) ? 16 : 0) + (f64 ? 32 : 16) + 16 + 16 + 8 + (f64 ? 0 : 4);
 }
 
 // particles a warp can park in shared memory besides the 32 in flight
@@ -273,6 +276,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
         ch.serial = h.a;
         ch.ctr = 0;
         ch.nseg = ch.ncol = ch.ncross = 0;
+        ch.tau = -1.0f;                 // FP32 modes: drawn from the child's own stream
         const int slot = atomicAdd(s_novf, 1);
         if (slot < A.overflow_cap) {
           ovf[slot] = ch;
@@ -289,6 +293,12 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
         }
       }
       p.w = (made == n - 1) ? wc : p.w - (R)made * wc;
+      // children's serials hash the parent's (serial, counter): when flights
+      // draw nothing (optical depth carried) a split consumes one counter
+      // value, so two splits of a particle never hand out the same streams
+      if constexpr (!PR::kF64) {
+        if (!P.fresh_tau) p.ctr += 1;
+      }
       atomicAdd(&es.n_end[5], 1u);
       atomicAdd(&es.n_end[6], (uint32_t)made);
       if (made < n - 1) atomicAdd(&es.n_end[8], (uint32_t)(n - 1 - made));
@@ -365,6 +375,9 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
   const double y = P.src_lo[1] + u01_f64(r0.c, r0.d) * (P.src_hi[1] - P.src_lo[1]);
   const double z = P.src_lo[2] + u01_f64(r1.a, r1.b) * (P.src_hi[2] - P.src_lo[2]);
   const double t = P.t0 + u01_f64(r3.a, r3.b) * (P.t1 - P.t0);
+  // FP32 modes carry the optical depth to the first collision from here; it
+  // comes from the time block's third word (unused by the FP32 draws)
+  if constexpr (PR::kF64) p.tau = -1.0f; else p.tau = -logf(u01_f32(r3.c));
   p.i = loc2index(P, 0, x);
   p.j = (DIM == 3) ? loc2index(P, 1, y) : 0;
   p.k = (DIM == 3) ? loc2index(P, 2, z) : 0;
@@ -399,17 +412,25 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
   const int mg = m * P.G + p.g;
   const R sig_t = tb.sigma_t[mg];
 
-  // distance to collision
-  const U4 r = draw(p, p.ctr, A.rk);
+  // distance to collision.  FP64: sampled afresh every flight (the oracle's
+  // reading, for event-exact parity).  FP32 modes: by default the optical
+  // depth tau to the next collision is carried across surface and census
+  // events (the exponential law is memoryless, so the collision sites have
+  // the same distribution) and redrawn only at collisions, births and for new
+  // split children -- a flight needs no random number; with fresh_tau every
+  // flight draws it as FP64 does (the same random numbers as an FP64 run).
+  // Division: the approximate (2-ulp) quotient, far below the FP32 noise.
   R d_coll;
   if constexpr (PR::kF64) {
+    const U4 r = draw(p, p.ctr, A.rk);
     const double xi = u01_f64(r.a, r.b);
     d_coll = sig_t > 0.0 ? -log(xi) / sig_t : rinf<double>();
   } else {
-    // FP32 modes divide with the approximate (2-ulp) quotient: about 5 %
-    // faster than the correctly rounded one, far below the FP32 noise
-    const float xi = u01_f32(r.a);
-    d_coll = sig_t > 0.0f ? __fdividef(-logf(xi), sig_t) : rinf<float>();
+    if (P.fresh_tau || !(p.tau >= 0.0f)) {
+      const U4 r = draw(p, p.ctr, A.rk);
+      p.tau = -logf(u01_f32(r.a));
+    }
+    d_coll = sig_t > 0.0f ? __fdividef(p.tau, sig_t) : rinf<float>();
   }
 
   // distance to the mesh surface and to the time census
@@ -494,6 +515,9 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     bin = -1; score = (R)0;
     end = END_LEAKED;
     return OUT_DEAD;
+  }
+  if constexpr (!PR::kF64) {      // optical depth used up by a flight that did not collide
+    if (ev != 0) p.tau = fmaxf(p.tau - sig_t * d, 0.0f);
   }
   if (P.estimator != 1) {         // track-length estimator (alone or combined)
     bin = bin_index(P, cell, p.g, p.tbin);
@@ -597,6 +621,9 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   }
   p.g = sample_cdf<R>(tb.cdf + mg * P.G, P.G, xi2);
   isotropic<PR, DIM>(r2, p);
+  // FP32 modes: optical depth to the next collision from the direction
+  // block's second word (unused by the FP32 draws)
+  if constexpr (!PR::kF64) p.tau = -logf(u01_f32(r2.b));
   if (P.implicit) {
     R wcut, wsurv;
     if constexpr (PR::kF64) { wcut = P.wcut; wsurv = P.wsurv; }
@@ -740,6 +767,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   bk.ids = (uint4 *)ptr; ptr += 16 * S;
   bk.cell = (uint4 *)ptr; ptr += 16 * S;
   bk.cnt = (uint2 *)ptr; ptr += 8 * S;
+  if constexpr (!PR::kF64) { bk.tau = (float *)ptr; ptr += 4 * S; } else { bk.tau = nullptr; }
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -971,6 +999,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         got.nseg = __shfl_sync(0xffffffffu, q.nseg, src);
         got.ncol = __shfl_sync(0xffffffffu, q.ncol, src);
         got.ncross = __shfl_sync(0xffffffffu, q.ncross, src);
+        if constexpr (!PR::kF64) got.tau = __shfl_sync(0xffffffffu, q.tau, src);
+        else got.tau = -1.0f;
         if (!has && r < na) { p = got; has = true; }
         rtop = max(0, na - ne);
         __syncwarp();

@@ -59,7 +59,7 @@ class mcdc_options(C.Structure):
                 ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
                 ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
                 ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
-                ("pc_target", C.c_int32)]
+                ("pc_target", C.c_int32), ("flight_sampling", C.c_int32)]
 
 
 class mcdc_stats(C.Structure):
@@ -199,11 +199,15 @@ class Problem:
 
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
-                 overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0):
+                 overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0,
+                 flight_sampling=0):
         """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
-        at an interior census edge (0: off)."""
+        at an interior census edge (0: off); flight_sampling: FP32 modes, 0
+        carries the optical depth across surface and census events, 1 samples
+        the distance to collision every flight (the FP64 twin's random
+        numbers)."""
         self.desc = prob
         keep = []
 
@@ -251,6 +255,7 @@ class Problem:
         o.region_hi[:] = [int(v) for v in hi]
         o.estimator = int(estimator)
         o.pc_target = int(pc_target)
+        o.flight_sampling = int(flight_sampling)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])

@@ -46,6 +46,23 @@ COUNT_KEYS = ("histories", "segments", "collisions", "crossings", "census", "abs
               "censused", "splits", "children", "roulette_killed", "roulette_survived")
 
 
+def fp32_bins_agree(g, o, max_exceed=5, rel_max=0.25):
+    """Per-bin statistical agreement of an FP32 run with an independent
+    oracle run: over the bins both estimate well (relative error <= rel_max,
+    about 16 or more scoring batches, where the batch-variance estimate is
+    close to normal) |z| > 4 at most max_exceed times; every bin the oracle
+    estimates well is scored by the GPU.  Returns (exceedances, bins)."""
+    gm, gr, om, orr = g["mean"], g["relerr"], o["mean"], o["relerr"]
+    well_o = (om != 0) & (orr <= rel_max)
+    assert np.all(gm[well_o] != 0), int((gm[well_o] == 0).sum())
+    both = well_o & (gm != 0) & (gr <= rel_max)
+    s = np.sqrt((gm * gr) ** 2 + (om * orr) ** 2)[both]
+    z = (gm - om)[both] / s
+    n = int((np.abs(z) > 4).sum())
+    assert n <= max_exceed, (n, int(both.sum()))
+    return n, int(both.sum())
+
+
 def compare_counts(g, o):
     for k in COUNT_KEYS:
         assert g[k] == o[k], (k, g[k], o[k])

@@ -102,7 +102,8 @@ def test_invalid_problems_rejected_on_host(lib, case):
 @pytest.mark.parametrize("case", ["unknown_estimator", "cutoff_above_survival", "zero_cutoff",
                                   "closed_steady_pure_scatterer", "closed_steady_void",
                                   "comb_negative_target", "comb_with_shared_tally",
-                                  "comb_in_steady_state", "comb_source_after_first_bin"])
+                                  "comb_in_steady_state", "comb_source_after_first_bin",
+                                  "bad_flight_sampling"])
 def test_invalid_options_rejected_on_host(lib, case):
     p, kw = W.c2_two_region(), {}
     if case == "unknown_estimator":
@@ -119,6 +120,8 @@ def test_invalid_options_rejected_on_host(lib, case):
         p, kw["pc_target"] = W.c1_slab(), 100
     elif case == "comb_source_after_first_bin":
         p, kw["pc_target"] = _bad(p, src_t1=1.0), 100
+    elif case == "bad_flight_sampling":
+        kw["flight_sampling"] = 2
     else:
         # steady state, every face reflecting: only absorption can end a history
         mat = np.zeros((2, 2, 2), np.uint8)
