@@ -261,6 +261,7 @@ def main():
     e2e_val = n_hist * e2e_steps * world / te
 
     pk = peaks()
+    measured_fp64 = M.measure_fp64_pipe() if args.precision == "fp32" else None
     fom = None
     if scal_all and scal_all[-1] and scal_all[-1][1] > 0:
         fom = 1.0 / (scal_all[-1][1] ** 2 * (ms_step / 1e3))
@@ -291,7 +292,8 @@ def main():
     line["gpu_launches"] = launches_per_step * args.steps
     # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)
-    line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"], args.precision)
+    line["roofline"] = roofline(prob, seg_rate, pk, stats_all[-1]["tally_mode"], args.precision,
+                                measured_fp64)
     if world == 1 and not args.no_variants:
         line["variants"] = variants(M, prob, n_hist, args, mean, rel, stream)
     if rank == 0 and not args.no_fom and world == 1:
@@ -475,7 +477,7 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207)):
     return out
 
 
-def roofline(prob, seg_rate, pk, tally_mode, prec_name):
+def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     """Roofline of the tracker for the binding unit of its precision mode.
 
     FP32 split: every flight accumulates x (and y, z in 3-D) and t in FP64 and
@@ -499,9 +501,18 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name):
         ops = 16.0 if three_d else 8.0
         peak = 0.625
         ach = seg_rate * ops / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe ops/s",
-                "frac": ach / peak, "traffic": None, "ops_per_segment": ops,
-                "peak_kind": "nominal B300 FP64 1.25 TFLOP/s = 0.625 T pipe ops/s (recipe)"}
+        out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe ops/s",
+               "frac": ach / peak, "traffic": None, "ops_per_segment": ops,
+               "peak_kind": "nominal B300 FP64 1.25 TFLOP/s = 0.625 T pipe ops/s (recipe)"}
+        if measured_fp64 is not None:
+            # half of a flight's FP64-pipe operations are conversions, half adds
+            add, cvt = measured_fp64
+            mix = 2.0 / (1.0 / add + 1.0 / cvt) / 1e12 if add > 0 and cvt > 0 else None
+            out["measured_pipe"] = {"add_T_per_s": add / 1e12, "cvt_T_per_s": cvt / 1e12,
+                                    "flight_mix_T_per_s": mix,
+                                    "frac_of_measured": ach / mix if mix else None,
+                                    "how": "mcdc_measure_fp64_pipe on this GPU before the run"}
+        return out
     ops_per_seg = 52.0
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = seg_rate * ops_per_seg / 1e12

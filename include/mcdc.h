@@ -395,6 +395,16 @@ int mcdc_run_noalloc(struct mcdc_problem *prob, uint64_t n_histories, uint64_t s
                      uint64_t hist_offset, int32_t n_batches, double *sum1, double *sum2,
                      double *mean, double *relerr, void *stream);
 
+/* Measures the FP64 pipe of the current device (no problem needed): the
+ * rate of FP64 adds (fused multiply-adds) and of FP32<->FP64 conversions, in
+ * lane-operations per second, from two short kernels (8 independent chains
+ * per thread, one 512-thread CTA per SM, best of three timed launches; about
+ * 10 ms in all).  These are the operations an FP32-split flight spends on its
+ * FP64 position and time, so the rates are the measured ceiling of that
+ * mode's roofline.  Allocates and frees a small device buffer.  Errors:
+ * MCDC_ERR_NO_DEVICE, MCDC_ERR_CUDA, MCDC_ERR_INVALID (NULL output). */
+int mcdc_measure_fp64_pipe(double *add_per_s, double *cvt_per_s);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);
 

@@ -137,6 +137,7 @@ SIGNATURES = {
                                      C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcdc_measure_fp64_pipe": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mcdc_last_error": (C.c_char_p, []),
 }
 
@@ -169,6 +170,7 @@ mcdc_mlp_param_count = _lib.mcdc_mlp_param_count
 mcdc_mlp_forward = _lib.mcdc_mlp_forward
 mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
 mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
+mcdc_measure_fp64_pipe = _lib.mcdc_measure_fp64_pipe
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -385,6 +387,14 @@ def mlp_forward(params, X):
     out = np.zeros(X.shape[0], dtype=np.float32)
     check(mcdc_mlp_forward(_ptr(p), X.shape[1], _ptr(X), X.shape[0], _ptr(out)))
     return out
+
+
+def measure_fp64_pipe():
+    """Measured FP64 add and FP32<->FP64 conversion rates of the current GPU
+    (lane-operations per second), see mcdc_measure_fp64_pipe."""
+    a, c = C.c_double(), C.c_double()
+    check(mcdc_measure_fp64_pipe(C.byref(a), C.byref(c)))
+    return a.value, c.value
 
 
 def set_wait_limit(tries):
