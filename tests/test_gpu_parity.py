@@ -292,3 +292,44 @@ def test_fp_full_size_c2_sampled_histories(mcdc):
     pick = np.sort(np.random.default_rng(0).choice(N, 2000, replace=False))
     compare_records(rec[pick], O.trace(prob, 1, pick), dim=1)
     assert stats["absorbed"] + stats["leaked"] + stats["censused"] == N
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_local", "fp64"])
+@pytest.mark.parametrize("sampling", [0, 1])
+def test_uncollided_beam_through_void_gap_and_census(mcdc, prec, sampling):
+    """Pure absorbers (sigma_t 0.8, then void, then 0.4) under a normal beam
+    with census edges every 0.5 time units (speed 1): the track-length flux
+    of every cell, summed over time bins, is the uncollided closed form
+    int exp(-tau(x)) dx / width.  Pins the optical depth the FP32 modes carry
+    across surfaces (including a change of sigma_t and a void, where it must
+    not change) and census events."""
+    P = {"fp32": mcdc.PREC_FP32, "fp32_local": mcdc.PREC_FP32_LOCAL,
+         "fp64": mcdc.PREC_FP64}[prec]
+    nc, L = 60, 12.0
+    w = L / nc
+    mats = np.array([0] * 15 + [1] * 15 + [2] * 30)
+    prob = W.slab("void_gap_beam", L, nc, mats, [[0.8], [0.0], [0.4]], [[0.0], [0.0], [0.0]],
+                  src=(0.0, 0.0), kind=W.SRC_BEAM, direction=(1.0, 0.0, 0.0),
+                  edges=np.linspace(0.0, 13.0, 27))
+    N = 2_000_000
+    g = mcdc.run_numpy(prob, N, seed=3, batches=40, precision=P, flight_sampling=sampling)
+    c = g["counts"]
+    assert c["absorbed"] + c["leaked"] == N and c["census"] > 2 * N
+    a = np.arange(nc) * w
+    b = a + w
+    ref = np.empty(nc)
+    r1 = b <= 3.0 + 1e-12
+    ref[r1] = (np.exp(-0.8 * a[r1]) - np.exp(-0.8 * b[r1])) / 0.8
+    rv = (a >= 3.0 - 1e-12) & (b <= 6.0 + 1e-12)
+    ref[rv] = np.exp(-2.4) * w
+    r3 = a >= 6.0 - 1e-12
+    ref[r3] = np.exp(-2.4) * (np.exp(-0.4 * (a[r3] - 6.0)) - np.exp(-0.4 * (b[r3] - 6.0))) / 0.4
+    ref /= w
+    s1 = g["sum1"].reshape(nc, -1).sum(axis=1) / (N * w)
+    # error of the time-summed cell flux from the batch sums of its bins is
+    # not available; bound it by the sum of the per-bin standard errors
+    se = np.sqrt(((g["mean"] * g["relerr"]).reshape(nc, -1) ** 2).sum(axis=1)) * np.sqrt(2.0)
+    z = (s1 - ref) / np.maximum(se, 1e-30)
+    assert np.all(np.abs(z) < 4.5), (np.abs(z).max(), int(np.abs(z).argmax()))
+    # the void cells: every history that reaches the gap crosses it whole
+    np.testing.assert_allclose(s1[rv], np.exp(-2.4), rtol=6 * np.sqrt((1 - np.exp(-2.4)) / (np.exp(-2.4) * N)))
