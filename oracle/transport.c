@@ -45,8 +45,9 @@
  *     first time bin and no weight windows): each batch is one time-stepped
  *     simulation.  Step j transports the batch's bank until every particle
  *     has ended or reached the census edge t_{j+1}; particles at an interior
- *     edge are banked.  The bank, ordered by (history id, serial), is combed
- *     to M particles of weight W/M (W = the bank's weight): tooth k at
+ *     edge are banked, in the order the step ran them (source order --
+ *     history id -- in the first step, tooth order after a comb).  The bank
+ *     is combed to M particles of weight W/M (W = the bank's weight): tooth k at
  *     (k + xi) W/M picks the particle whose cumulative-weight interval holds
  *     it, xi = U from the block (key seed; counter 0xFFFFFFFC, j, first
  *     history id of the batch lo, hi).  Tooth k's particle keeps the parent's
@@ -454,14 +455,6 @@ void orc_comb(int64_t n, const double *w, int64_t M, double xi, int64_t *sel)
     }
 }
 
-static int by_history_then_serial(const void *a, const void *b)
-{
-    const part *x = (const part *)a, *y = (const part *)b;
-    if (x->hid != y->hid) return x->hid < y->hid ? -1 : 1;
-    if (x->serial != y->serial) return x->serial < y->serial ? -1 : 1;
-    return 0;
-}
-
 /* One batch [h0, h1) as a time-stepped simulation with a comb at every
  * interior census edge.  All source particles are born in the first bin. */
 static void run_batch_pc(const orc_problem *p, const tables *tb, uint64_t seed, uint64_t h0,
@@ -489,8 +482,8 @@ static void run_batch_pc(const orc_problem *p, const tables *tb, uint64_t seed, 
             if (end == BANKED) cen[nc++] = Q;
         }
         if (nc == 0) break;
-        /* the comb: bank order (history id, serial), M teeth, new streams */
-        qsort(cen, (size_t)nc, sizeof(part), by_history_then_serial);
+        /* the comb, in bank order (the order the step ran its particles),
+         * M teeth, new streams */
         uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
         uint32_t cx[4] = { 0xFFFFFFFCu, (uint32_t)j, (uint32_t)h0, (uint32_t)(h0 >> 32) };
         uint32_t ox[4];
