@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_local", "fp64"])
     ap.add_argument("--batches", type=int, default=0, help="batches per run (0: library default)")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0: library default)")
+    ap.add_argument("--pc-target", type=int, default=0,
+                    help="population control in the timed run: particles per batch after "
+                         "each comb (0: off; the run then uses the global tally)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
@@ -196,7 +199,7 @@ def main():
     from paper_2409_04668_b300 import mcdc as M
 
     prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
-    P = M.Problem(prob, precision=prec, block_size=args.block)
+    P = M.Problem(prob, precision=prec, block_size=args.block, pc_target=args.pc_target)
     dev = torch.device("cuda", local)
     mean = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
     rel = torch.empty(P.n_bins, dtype=torch.float64, device=dev)
@@ -254,7 +257,7 @@ def main():
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     for s in range(e2e_steps):
-        with M.Problem(prob, precision=prec, block_size=args.block) as Q:
+        with M.Problem(prob, precision=prec, block_size=args.block, pc_target=args.pc_target) as Q:
             Q.run_ex(n_hist, seed=1, offset=history_offset(rank, 500 + s, n_hist), batches=args.batches,
                      mean=h_mean, relerr=h_rel, want_stats=False)
     te = time.perf_counter() - te0
@@ -289,6 +292,11 @@ def main():
         "roofline": None,
     }
     launches_per_step = 2 if stats_all[-1]["tally_mode"] == 1 else 3 * stats_all[-1]["n_batches"] + 1
+    if args.pc_target > 0:
+        # per time step one tracker launch and four comb kernels (none after
+        # the last), a fold pair per batch slice, one finalize
+        T = len(prob.edges) - 1
+        launches_per_step = T + 4 * (T - 1) + 2 * stats_all[-1]["n_batches"] + 1
     line["gpu_launches"] = launches_per_step * args.steps
     # roofline of the tracker from its per-flight algorithmic figures
     seg_rate = segs / (k_ms / 1e3)

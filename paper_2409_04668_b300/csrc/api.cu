@@ -221,18 +221,14 @@ int ensure_slices(mcdc_problem *pr, int B) {
 // Population control buffers: a census bank of cap particles, a combed
 // bank of combed particles, B tally slices and the comb's scratch.
 int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
-  const size_t pb = part_bytes(pr->key);
+  const size_t pb = bank_slot_bytes(pr->key);
   int rc;
   if (pr->pc_cap < cap) {
     unsigned char *bank = nullptr, *temp = nullptr;
     if ((rc = dalloc(pr, &bank, pb * (size_t)cap))) return rc;
-    for (int q = 0; q < 2; ++q) {
-      if ((rc = dalloc(pr, &pr->pc_keys[q], (size_t)cap))) return rc;
-      if ((rc = dalloc(pr, &pr->pc_idx[q], (size_t)cap))) return rc;
-    }
     if ((rc = dalloc(pr, &pr->pc_w, (size_t)cap))) return rc;
     if ((rc = dalloc(pr, &pr->pc_S, (size_t)cap))) return rc;
-    if ((rc = dalloc(pr, &pr->pc_bid, (size_t)cap))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_key, (size_t)cap))) return rc;
     const size_t tb = comb_temp_bytes(cap);
     if ((rc = dalloc(pr, &temp, tb))) return rc;
     pr->pc_bank = bank;
@@ -248,6 +244,8 @@ int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
   }
   if (pr->pc_seg_cap < B) {
     if ((rc = dalloc(pr, &pr->pc_seg, 3 * (size_t)B))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_segd, 4 * (size_t)B))) return rc;
+    if ((rc = dalloc(pr, &pr->pc_live, 2 * (size_t)B + 2))) return rc;
     pr->pc_seg_cap = B;
   }
   if ((rc = ensure_slices(pr, B))) return rc;
@@ -841,38 +839,47 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     A.census_out = pr->pc_bank;
     A.census_count = pr->pc_cnt;
     A.census_cap = (unsigned long long)pr->pc_cap;
-    int key_bits = 33;
-    while (key_bits < 64 && (1ull << (key_bits - 32)) < N) ++key_bits;
+    // every banked particle lands at its position in the step's input (the
+    // histories, then the combed bank): its census weight marks it
+    A.census_w = pr->pc_w;
+    int32_t *live[2] = {pr->pc_live, pr->pc_live + B};
+    int32_t *n_live[2] = {pr->pc_live + 2 * B, pr->pc_live + 2 * B + 1};
+    long long n_in = (long long)N;
     for (int step = 0;; ++step) {
       CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(pr->pc_w, 0, sizeof(double) * (size_t)n_in, s));
       CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
       if (step >= P.T - 1) break;
       CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
                          cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      const unsigned long long n = *pr->h_spill;
-      if (n == 0) break;
-      if (n > (unsigned long long)pr->pc_cap)
-        return fail(MCDC_ERR_BANK_OVERFLOW, "census bank overflow under population control");
+      if (*pr->h_spill == 0) break;
       NvtxRange nvtx_comb("comb");
       CombArgs c{};
       c.bank = pr->pc_bank;
-      c.n = (int)n;
+      c.bank_cap = pr->pc_cap;
+      c.out_cap = pr->pc_combed_cap;
+      c.dim = pr->dim;
+      c.w = pr->pc_w;
+      c.n_in = (int)n_in;
+      c.first_step = step == 0;
+      c.live_in = live[(step + 1) & 1];
+      c.n_live_in = n_live[(step + 1) & 1];
+      c.live_out = live[step & 1];
+      c.n_live_out = n_live[step & 1];
       c.out = pr->pc_combed;
-      c.M = M;
       c.out_count = pr->pc_cnt + 1;
+      c.banked = pr->pc_cnt;
+      c.M = M;
       c.offset = a->hist_offset;
       c.n_hist = N;
       c.B = B;
       c.step = step;
       c.rk = A.rk;
-      c.key_bits = key_bits;
-      c.keys[0] = pr->pc_keys[0]; c.keys[1] = pr->pc_keys[1];
-      c.idx[0] = pr->pc_idx[0]; c.idx[1] = pr->pc_idx[1];
-      c.w = pr->pc_w;
+      c.key = pr->pc_key;
       c.S = pr->pc_S;
-      c.bid = pr->pc_bid;
       c.seg = pr->pc_seg;
+      c.segd = pr->pc_segd;
       c.temp = pr->pc_temp;
       c.temp_bytes = pr->pc_temp_bytes;
       c.stats = pr->stats;
@@ -882,6 +889,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       A.spill_in_count = pr->pc_cnt + 1;
       A.spill_in_cursor = pr->pc_cnt + 2;
       A.spill_cap = (unsigned long long)pr->pc_combed_cap;
+      n_in = (long long)B * M;        // the next input: one chunk of M per combed batch
     }
     for (int b = 0; b < B; ++b)
       CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2, pr->sum12,

@@ -1,18 +1,20 @@
 // comb.cu -- population control: the comb of the census bank.
 //
 // Every batch is an independent time-stepped simulation, and one launch runs
-// the current step of all of them.  Particles that reached an interior
-// census edge sit in one bank in the order the warps appended them.  The comb
-// orders them by (history id, serial) -- one radix sort of the 64-bit key
-// (hid - offset) << 32 | serial; batches are contiguous history ranges, so
-// this also groups them by batch -- and does not depend on scheduling.  Per
-// batch it takes the exclusive prefix sum S of the weights in that order
-// (W_b = S[end-1] + w[end-1]) and emits M particles: tooth k at
-// (k + xi_b) W_b / M copies the particle whose interval [S_i, S_i + w_i)
-// holds it, with weight W_b / M, a serial hashed from (parent serial, step,
-// k) and a fresh counter.  xi_b comes from the block (key seed; counter
-// 0xFFFFFFFC, step, first history id of the batch).
-#include <cub/device/device_radix_sort.cuh>
+// the current step of all of them.  A particle that reaches an interior
+// census edge is written at its position in the step's input (nothing splits
+// under population control, so every input yields at most one), which keeps
+// the bank in the order the step ran its particles -- history order in the
+// first step, tooth order after a comb -- without a sort and independently of
+// scheduling.  Positions whose particle ended hold weight 0.  The input is
+// laid out batch by batch, so a segmented exclusive scan gives every batch's
+// cumulative weights S (W_b = S[end-1] + w[end-1]); the comb then emits M
+// particles per batch: tooth k at T_k = (k + xi_b) W_b / M copies the last
+// particle i with S_i <= T_k, with weight W_b / M, a serial hashed from
+// (parent serial, step, k) and a fresh counter.  xi_b comes from the block
+// (key seed; counter 0xFFFFFFFC, step, first history id of the batch).  One
+// thread per banked particle finds its teeth, a contiguous range because T_k
+// does not decrease with k, and writes them.
 #include <cub/device/device_scan.cuh>
 
 #include "comb.h"
@@ -20,145 +22,159 @@
 
 namespace mcdc {
 
-template <class PT>
-__global__ void k_comb_keys(const PT *__restrict__ bank, int n, uint64_t offset,
-                            unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const PT &q = bank[i];
-    keys[i] = ((unsigned long long)(q.hid - offset) << 32) | (unsigned long long)q.serial;
-    idx[i] = (uint32_t)i;
-  }
+// segment (batch in the first step, chunk of M afterwards) of every input position
+__global__ void k_comb_keys(int n, bool first_step, uint64_t n_hist, int B, int M,
+                            int32_t *__restrict__ key) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    key[i] = first_step ? batch_of(n_hist, B, (uint64_t)i) : i / M;
 }
 
-// weights and batch ids in key order; first and end of every batch's run
-template <class PT>
-__global__ void k_comb_gather(const PT *__restrict__ bank, const uint32_t *__restrict__ order,
-                              int n, uint64_t offset, uint64_t n_hist, int B,
-                              double *__restrict__ w, int32_t *__restrict__ bid,
-                              int32_t *__restrict__ seg) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const PT &q = bank[order[i]];
-    w[i] = (double)q.w;
-    const int b = batch_of(n_hist, B, q.hid - offset);
-    bid[i] = b;
-    const int bp = i > 0 ? batch_of(n_hist, B, bank[order[i - 1]].hid - offset) : -1;
-    const int bn = i < n - 1 ? batch_of(n_hist, B, bank[order[i + 1]].hid - offset) : -1;
-    if (bp != b) seg[b] = i;               // first of batch b
-    if (bn != b) seg[B + b] = i + 1;       // end of batch b
-  }
-}
-
-// output base of every batch that has particles; comb statistics
-template <class PT>
-__global__ void k_comb_bases(const double *__restrict__ S, const double *__restrict__ w, int n,
-                             int M, int B, int32_t *__restrict__ seg,
-                             unsigned long long *out_count, Stats *stats) {
-  using R = decltype(PT::w);
-  int base = 0, combs = 0;
+// Per segment: its range, total weight, xi and tooth spacing; the output
+// chunk of every segment that has weight; comb statistics.
+template <class PR>
+__global__ void k_comb_bases(CombArgs c) {
+  using R = typename PR::R;
+  const int nseg = c.first_step ? c.B : *c.n_live_in;
+  int chunks = 0;
   double win = 0.0, wout = 0.0;
-  for (int b = 0; b < B; ++b) {
-    const int s0 = seg[b], s1 = seg[B + b];
-    if (s1 > s0) {
-      seg[2 * B + b] = base;
-      base += M;
-      combs += 1;
-      const double W = S[s1 - 1] + w[s1 - 1];
-      win += W;
-      wout += (double)M * (double)(R)(W / (double)M);
-    } else {
-      seg[2 * B + b] = -1;
-    }
+  for (int q = 0; q < c.B; ++q) {
+    c.seg[2 * c.B + q] = -1;
+    if (q >= nseg) continue;
+    const int b = c.first_step ? q : c.live_in[q];
+    const int s0 = c.first_step ? (int)batch_start(c.n_hist, c.B, b) : q * c.M;
+    const int s1 = c.first_step ? (int)batch_start(c.n_hist, c.B, b + 1) : (q + 1) * c.M;
+    const double W = s1 > s0 ? c.S[s1 - 1] + c.w[s1 - 1] : 0.0;
+    if (!(W > 0.0)) continue;
+    const uint64_t h0 = c.offset + batch_start(c.n_hist, c.B, b);
+    const U4 r = philox4x32_10_rk(0xFFFFFFFCu, (uint32_t)c.step, (uint32_t)h0,
+                                  (uint32_t)(h0 >> 32), c.rk);
+    c.seg[q] = s0;
+    c.seg[c.B + q] = s1;
+    c.seg[2 * c.B + q] = chunks;
+    c.segd[q] = W;
+    c.segd[c.B + q] = u01_f64(r.a, r.b);
+    c.segd[2 * c.B + q] = W / (double)c.M;
+    c.segd[3 * c.B + q] = (double)c.M / W;
+    c.live_out[chunks] = b;
+    chunks += 1;
+    win += W;
+    wout += (double)c.M * (double)(R)(W / (double)c.M);
   }
-  *out_count = (unsigned long long)base;
-  stats->pc_combs += (unsigned long long)combs;
-  stats->pc_in += (unsigned long long)n;
-  stats->pc_out += (unsigned long long)base;
-  stats->w_pc_in += win;
-  stats->w_pc_out += wout;
+  *c.n_live_out = chunks;
+  *c.out_count = (unsigned long long)chunks * (unsigned long long)c.M;
+  c.stats->pc_combs += (unsigned long long)chunks;
+  c.stats->pc_in += *c.banked;
+  c.stats->pc_out += (unsigned long long)chunks * (unsigned long long)c.M;
+  c.stats->w_pc_in += win;
+  c.stats->w_pc_out += wout;
 }
 
-template <class PT>
-__global__ void k_comb_teeth(const PT *__restrict__ bank, const uint32_t *__restrict__ order,
-                             const double *__restrict__ S, const double *__restrict__ w,
-                             const int32_t *__restrict__ seg, int M, int B, RoundKeys rk,
-                             uint32_t step, uint64_t offset, uint64_t n_hist,
-                             PT *__restrict__ out) {
-  using R = decltype(PT::w);
-  const long long total = (long long)B * M;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / M), k = (int)(t % M);
-    const int base = seg[2 * B + b];
-    if (base < 0) continue;                       // the batch has no particle left
-    const int s0 = seg[b], s1 = seg[B + b];
-    const double W = S[s1 - 1] + w[s1 - 1];
-    const uint64_t h0 = offset + batch_start(n_hist, B, b);
-    const U4 r = philox4x32_10_rk(0xFFFFFFFCu, step, (uint32_t)h0, (uint32_t)(h0 >> 32), rk);
-    const double xi = u01_f64(r.a, r.b);
-    const double wn = W / (double)M;
-    const double tooth = ((double)k + xi) * wn;
-    int lo = s0, hi = s1 - 1;                     // the last i with S[i] <= tooth
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (S[mid] <= tooth) lo = mid; else hi = mid - 1;
+__device__ __forceinline__ double comb_tooth(int k, double xi, double wn) {
+  return ((double)k + xi) * wn;
+}
+
+// First k in [0, M] with T_k >= s (M if none).  The estimate e = s M / W - xi
+// is within ~8 u max(M, 1) of the exact boundary in units of teeth (u = 2^-53:
+// the rounding of e, of M / W and of T_k itself), at most 2e-6 for M < 2^31,
+// so a ceiling whose distance from e exceeds 1e-5 is the answer; closer cases
+// are settled by evaluating T_k as defined.  (FP64 arithmetic is scarce on
+// this GPU: the fast path costs a handful of FP64 operations, a division
+// several times that.)
+__device__ __forceinline__ int first_tooth_at_or_after(double s, double xi, double wn,
+                                                      double inv, int M) {
+  const double e = fma(s, inv, -xi);
+  const double ce = ceil(e);
+  if (ce <= 0.0) {
+    if (e < -1e-5) return 0;
+  } else if (ce >= (double)M) {
+    if (e > (double)M - 1.0 + 1e-5) return M;
+  } else if (ce - e > 1e-5 && ce - e < 1.0 - 1e-5) {
+    return (int)ce;
+  }
+  int k = ce < 0.0 ? 0 : (ce > (double)M ? M : (int)ce);
+  while (k > 0 && comb_tooth(k - 1, xi, wn) >= s) --k;
+  while (k < M && comb_tooth(k, xi, wn) < s) ++k;
+  return k;
+}
+
+// first tooth of every banked particle (into key[], which the scan no longer needs)
+__global__ void k_comb_first(CombArgs c) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_in; i += gridDim.x * blockDim.x) {
+    if (!(c.w[i] > 0.0)) continue;
+    const int q = c.first_step ? batch_of(c.n_hist, c.B, (uint64_t)i) : i / c.M;
+    if (c.seg[2 * c.B + q] < 0) continue;
+    c.key[i] = first_tooth_at_or_after(c.S[i], c.segd[c.B + q], c.segd[2 * c.B + q],
+                                       c.segd[3 * c.B + q], c.M);
+  }
+}
+
+// Banked particle i owns the teeth with S_i <= T_k < S_j, j the next banked
+// particle of its segment (all teeth from S_i on if there is none): the
+// assignment "last particle with S <= T_k" made per tooth.  Both banks have
+// the pool's structure-of-arrays layout.
+template <class PR, int DIM>
+__global__ void k_comb_teeth(CombArgs c) {
+  using R = typename PR::R;
+  const Bank<PR> in = bank_view<PR>(const_cast<void *>(c.bank), c.bank_cap, DIM);
+  const Bank<PR> out = bank_view<PR>(c.out, c.out_cap, DIM);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_in; i += gridDim.x * blockDim.x) {
+    if (!(c.w[i] > 0.0)) continue;
+    const int q = c.first_step ? batch_of(c.n_hist, c.B, (uint64_t)i) : i / c.M;
+    const int chunk = c.seg[2 * c.B + q];
+    if (chunk < 0) continue;
+    const int s1 = c.seg[c.B + q];
+    const double wn = c.segd[2 * c.B + q];
+    const int k0 = c.key[i];
+    int j = i + 1;
+    while (j < s1 && !(c.w[j] > 0.0)) ++j;
+    const int k1 = j < s1 ? c.key[j] : c.M;
+    if (k1 <= k0) continue;
+    PartOf<PR> parent;
+    in.load(i, parent, DIM);
+    const R wc = (R)wn;
+    for (int k = k0; k < k1; ++k) {
+      PartOf<PR> p = parent;
+      const U4 h = philox4x32_10_rk(0xFFFFFFFDu, p.serial, (uint32_t)c.step, (uint32_t)k, c.rk);
+      p.serial = h.a;
+      p.ctr = 0;
+      p.tau = -1.0f;            // FP32 modes: every copy draws its own optical depth
+      p.w = wc;
+      out.store(chunk * c.M + k, p, DIM);
     }
-    PT q = bank[order[lo]];
-    const U4 h = philox4x32_10_rk(0xFFFFFFFDu, q.serial, step, (uint32_t)k, rk);
-    q.serial = h.a;
-    q.ctr = 0;
-    q.tau = -1.0f;            // FP32 modes: every copy draws its own optical depth
-    q.w = (R)wn;
-    out[base + k] = q;
   }
 }
 
 size_t comb_temp_bytes(int cap) {
-  size_t a = 0, b = 0;
-  cub::DeviceRadixSort::SortPairs(nullptr, a, (const unsigned long long *)nullptr,
-                                  (unsigned long long *)nullptr, (const uint32_t *)nullptr,
-                                  (uint32_t *)nullptr, cap, 0, 64);
+  size_t b = 0;
   cub::DeviceScan::ExclusiveSumByKey(nullptr, b, (const int32_t *)nullptr,
                                      (const double *)nullptr, (double *)nullptr, cap);
-  return a > b ? a : b;
+  return b;
 }
 
-template <class PT>
+template <class PR>
 static cudaError_t comb_impl(cudaStream_t s, const CombArgs &c) {
-  const PT *bank = reinterpret_cast<const PT *>(c.bank);
   const int threads = 256;
-  const int blocks_n = (int)std::min<long long>((c.n + threads - 1) / threads, 4096);
-  k_comb_keys<PT><<<blocks_n, threads, 0, s>>>(bank, c.n, c.offset, c.keys[0], c.idx[0]);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((c.n_in + threads - 1) / threads, 8192));
+  k_comb_keys<<<blocks, threads, 0, s>>>(c.n_in, c.first_step, c.n_hist, c.B, c.M, c.key);
   size_t tb = c.temp_bytes;
-  cudaError_t e = cub::DeviceRadixSort::SortPairs(c.temp, tb, c.keys[0], c.keys[1], c.idx[0],
-                                                  c.idx[1], c.n, 0, c.key_bits, s);
+  cudaError_t e = cub::DeviceScan::ExclusiveSumByKey(c.temp, tb, c.key, c.w, c.S, c.n_in,
+                                                     ::cuda::std::equal_to<>(), s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(c.seg, 0, sizeof(int32_t) * 3 * (size_t)c.B, s);
-  if (e != cudaSuccess) return e;
-  k_comb_gather<PT><<<blocks_n, threads, 0, s>>>(bank, c.idx[1], c.n, c.offset, c.n_hist, c.B,
-                                                 c.w, c.bid, c.seg);
-  tb = c.temp_bytes;
-  e = cub::DeviceScan::ExclusiveSumByKey(c.temp, tb, c.bid, c.w, c.S, c.n,
-                                         ::cuda::std::equal_to<>(), s);
-  if (e != cudaSuccess) return e;
-  k_comb_bases<PT><<<1, 1, 0, s>>>(c.S, c.w, c.n, c.M, c.B, c.seg, c.out_count, c.stats);
-  const long long teeth = (long long)c.B * c.M;
-  const int blocks_t = (int)std::min<long long>((teeth + threads - 1) / threads, 8192);
-  k_comb_teeth<PT><<<blocks_t, threads, 0, s>>>(bank, c.idx[1], c.S, c.w, c.seg, c.M, c.B, c.rk,
-                                                (uint32_t)c.step, c.offset, c.n_hist,
-                                                reinterpret_cast<PT *>(c.out));
+  k_comb_bases<PR><<<1, 1, 0, s>>>(c);
+  k_comb_first<<<blocks, threads, 0, s>>>(c);
+  if (c.dim == 3) k_comb_teeth<PR, 3><<<blocks, threads, 0, s>>>(c);
+  else k_comb_teeth<PR, 1><<<blocks, threads, 0, s>>>(c);
   return cudaGetLastError();
 }
 
 cudaError_t comb_bank(const TrackKey &key, cudaStream_t s, const CombArgs &c) {
-  if (key.f64) return comb_impl<PartOf<PrecF64>>(s, c);
-  if (key.local) return comb_impl<PartOf<PrecF32L>>(s, c);
-  return comb_impl<PartOf<PrecF32>>(s, c);
+  if (key.f64) return comb_impl<PrecF64>(s, c);
+  if (key.local) return comb_impl<PrecF32L>(s, c);
+  return comb_impl<PrecF32>(s, c);
 }
 
-size_t part_bytes(const TrackKey &key) {
-  if (key.f64) return sizeof(PartOf<PrecF64>);
-  if (key.local) return sizeof(PartOf<PrecF32L>);
-  return sizeof(PartOf<PrecF32>);
+size_t bank_slot_bytes(const TrackKey &key) {
+  return (size_t)slot_bytes(key.f64, key.dim, key.local);
 }
 
 }  // namespace mcdc

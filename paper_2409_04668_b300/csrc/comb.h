@@ -7,33 +7,47 @@
 
 namespace mcdc {
 
+// One step's comb over all batches.  The step's input is laid out batch by
+// batch: in the first step the histories (batch b at [batch_start(N, B, b),
+// batch_start(N, B, b + 1))), after a comb one chunk of M particles per batch
+// that still had particles, in batch order.  The tracker wrote every banked
+// particle at its input position (bank, w); other positions hold weight 0.
 struct CombArgs {
-  const void *bank;             // census bank: n particles of the run's precision, all batches
-  int n;                        // particles in the bank (>= 1)
-  void *out;                    // combed bank: M per batch that had particles, batch by batch
+  const void *bank;             // banked particles by input position (pool layout, bank_cap slots)
+  long long bank_cap;
+  const double *w;              // [n_in] their weights, 0 where nothing was banked
+  int n_in;                     // input positions of the step (N, or B x M after a comb)
+  bool first_step;              // the input is the histories themselves
+  const int32_t *live_in;       // [B] after a comb: batch of chunk c; [0] <- chunk count
+  const int32_t *n_live_in;     //   (device; unused in the first step)
+  int32_t *live_out;            // [B] batches combed by this step, in order
+  int32_t *n_live_out;          // their count (device)
+  void *out;                    // combed bank: chunk c (batch live_out[c]) at [c M, (c + 1) M)
+  long long out_cap;            //   (pool layout, out_cap slots)
+  int dim;                      // 1 or 3
+  unsigned long long *out_count;   // set to M x n_live_out
+  const unsigned long long *banked;  // particles the tracker banked this step (device)
   int M;                        // particles per batch after the comb
-  unsigned long long *out_count;   // set to M x (batches that had particles)
   uint64_t offset;              // first history id of the run
   uint64_t n_hist;              // histories in the run
   int B;                        // batches
   int step;                     // index of the time bin that just ended
   RoundKeys rk;
-  int key_bits;                 // 32 + bits of the run's history count
-  unsigned long long *keys[2];  // [cap] sort keys in / out
-  uint32_t *idx[2];             // [cap] bank positions in / out
-  double *w, *S;                // [cap] weights in key order and their per-batch exclusive sums
-  int32_t *bid;                 // [cap] batch of each particle in key order
-  int32_t *seg;                 // [3 B]: first, end and output base of each batch's run
+  int32_t *key;                 // [n_in] scratch: segment of each input position, then the
+                                //   first tooth of each banked particle
+  double *S;                    // [n_in] scratch: per-segment exclusive sums of w
+  int32_t *seg;                 // [3 B] scratch: per segment first, end, output chunk (-1: none)
+  double *segd;                 // [4 B] scratch: per segment W, xi, W / M, M / W
   void *temp;                   // CUB scratch
   size_t temp_bytes;
   Stats *stats;
 };
 
-// CUB scratch bytes for a bank of up to cap particles.
+// CUB scratch bytes for up to cap input positions.
 size_t comb_temp_bytes(int cap);
-// Sorts, scans and combs one bank (all on stream s).
+// Scans and combs one step's bank (all on stream s).
 cudaError_t comb_bank(const TrackKey &key, cudaStream_t s, const CombArgs &c);
-// Bytes of one particle record of the run's precision.
-size_t part_bytes(const TrackKey &key);
+// Bytes per slot of a particle bank in the pool layout of the run's precision.
+size_t bank_slot_bytes(const TrackKey &key);
 
 }  // namespace mcdc

@@ -64,7 +64,7 @@ struct DevProblem {
 // cell-local FP32 mode): x, y, z are offsets from the low faces of the cell
 // and t is the time left to the next census edge.
 template <class R, class Q = double>
-struct Part {
+struct alignas(32) Part {   // whole 32-byte sectors: banks written at scattered positions
   Q x, y, z;          // position (or cell-local offsets)
   Q t;                // time (or time to the next census edge)
   R ux, uy, uz;       // direction
@@ -76,6 +76,7 @@ struct Part {
   uint64_t hid;
   uint32_t nseg, ncol, ncross;
   float tau;          // FP32 modes: mean free paths left to the next collision (< 0: draw afresh)
+  uint32_t slot;      // population control: the particle's position in this step's input
 };
 
 // Per-history record (mirrors mcdc_record).
@@ -135,9 +136,11 @@ struct RunArgs {
   const void *spill_in;       // bank this pass runs instead of new histories
   const unsigned long long *spill_in_count;
   unsigned long long *spill_in_cursor;
-  // population control: particles reaching an interior census edge are
-  // appended here instead of flying on (nullptr: off)
+  // population control: a particle reaching an interior census edge is
+  // written to census_out[slot] (its position in the step's input) with its
+  // weight in census_w[slot], instead of flying on (nullptr: off)
   void *census_out;
+  double *census_w;
   unsigned long long *census_count;
   unsigned long long census_cap;
   // population control runs every batch in each launch: the global tally is

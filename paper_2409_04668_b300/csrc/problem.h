@@ -43,18 +43,18 @@ struct mcdc_problem {
   uint64_t rec_cap = 0;
   double *ww64 = nullptr;
   float *ww32 = nullptr;
-  // population control: census bank, combed bank and the comb's scratch
-  int pc_cap = 0;                          // particles the census bank holds
+  // population control: census bank (by input position), combed bank and
+  // the comb's scratch
+  int pc_cap = 0;                          // input positions the census bank holds
   long long pc_combed_cap = 0;             // particles the combed bank holds
   long long pc_tally_bins = 0;             // entries of the per-batch tally slices
   double *pc_tally = nullptr;              // [batches][n_tally]
-  int32_t *pc_bid = nullptr, *pc_seg = nullptr;
+  int32_t *pc_key = nullptr, *pc_seg = nullptr, *pc_live = nullptr;
+  double *pc_segd = nullptr;
   int pc_seg_cap = 0;
   void *pc_bank = nullptr, *pc_combed = nullptr;
-  unsigned long long *pc_cnt = nullptr;    // [4]: census count, combed count, cursor
-  unsigned long long *pc_keys[2] = {nullptr, nullptr};
-  uint32_t *pc_idx[2] = {nullptr, nullptr};
-  double *pc_w = nullptr, *pc_S = nullptr;
+  unsigned long long *pc_cnt = nullptr;    // [4]: banked count, combed count, cursor
+  double *pc_w = nullptr, *pc_S = nullptr; // [cap] census weights, per-batch exclusive sums
   void *pc_temp = nullptr;
   size_t pc_temp_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;

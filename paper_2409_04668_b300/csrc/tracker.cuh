@@ -82,8 +82,7 @@ struct Bank {
   double2 *d1;        // FP64 only: {uz, w}
   uint4 *ids;         // {ctr, serial, hid low, hid high}
   uint4 *cell;        // {i | j << 16, k | tbin << 16, g, nseg}
-  uint2 *cnt;         // {ncol, ncross}
-  float *tau;         // FP32 modes: optical depth to the next collision
+  uint4 *cnt;         // {ncol, ncross, slot, optical depth (FP32 modes)}
 
   __device__ __forceinline__ void load(int s, PartOf<PR> &p, int dim) const {
     if constexpr (PR::kLocal) {
@@ -108,9 +107,8 @@ struct Bank {
     p.i = (int)(ce.x & 0xffffu); p.j = (int)(ce.x >> 16);
     p.k = (int)(ce.y & 0xffffu); p.tbin = (int)(ce.y >> 16);
     p.g = (int)ce.z; p.nseg = ce.w;
-    const uint2 cn = cnt[s];
-    p.ncol = cn.x; p.ncross = cn.y;
-    if constexpr (!PR::kF64) p.tau = tau[s];
+    const uint4 cn = cnt[s];
+    p.ncol = cn.x; p.ncross = cn.y; p.slot = cn.z; p.tau = __uint_as_float(cn.w);
   }
   __device__ __forceinline__ void store(int s, const PartOf<PR> &p, int dim) const {
     if constexpr (PR::kLocal) {
@@ -128,14 +126,33 @@ struct Bank {
     ids[s] = make_uint4(p.ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32));
     cell[s] = make_uint4((uint32_t)p.i | ((uint32_t)p.j << 16), (uint32_t)p.k | ((uint32_t)p.tbin << 16),
                          (uint32_t)p.g, p.nseg);
-    cnt[s] = make_uint2(p.ncol, p.ncross);
-    if constexpr (!PR::kF64) tau[s] = p.tau;
+    cnt[s] = make_uint4(p.ncol, p.ncross, p.slot, __float_as_uint(p.tau));
   }
 };
 
 // bytes of one pool slot (kept in sync with the carve in k_track)
 __host__ __device__ inline int slot_bytes(bool f64, int dim, bool local) {
-  return 16 + ((dim == 3 && !local) ? 16 : 0) + (f64 ? 32 : 16) + 16 + 16 + 8 + (f64 ? 0 : 4);
+  return 16 + ((dim == 3 && !local) ? 16 : 0) + (f64 ? 32 : 16) + 16 + 16 + 16;
+}
+
+// The pool's structure-of-arrays layout over any memory: cap slots carved
+// from base as xt, yz (3-D, not cell-local), d0, d1 (FP64), ids, cell, cnt,
+// 16 bytes per slot each -- slot_bytes(...) x cap bytes in all.  Shared
+// memory holds the warps' pools this way; device memory holds the banks that
+// population control writes at scattered positions and copies in bulk (one
+// 16-byte access per field group and slot, coalesced over consecutive slots).
+template <class PR>
+__device__ __forceinline__ Bank<PR> bank_view(void *base, long long cap, int dim) {
+  Bank<PR> b;
+  unsigned char *ptr = static_cast<unsigned char *>(base);
+  b.xt = ptr; ptr += 16 * cap;
+  if (dim == 3 && !PR::kLocal) { b.yz = (double2 *)ptr; ptr += 16 * cap; } else { b.yz = nullptr; }
+  b.d0 = ptr; ptr += 16 * cap;
+  if constexpr (PR::kF64) { b.d1 = (double2 *)ptr; ptr += 16 * cap; } else { b.d1 = nullptr; }
+  b.ids = (uint4 *)ptr; ptr += 16 * cap;
+  b.cell = (uint4 *)ptr; ptr += 16 * cap;
+  b.cnt = (uint4 *)ptr;
+  return b;
 }
 
 // particles a warp can park in shared memory besides the 32 in flight
@@ -359,6 +376,7 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
   using R = typename PR::R;
   p.serial = 0; p.ctr = 0; p.hid = hid;
   p.nseg = p.ncol = p.ncross = 0;
+  p.slot = 0;
   const U4 r0 = draw(p, p.ctr, rk);
   const U4 r1 = draw(p, p.ctr, rk);
   const U4 r2 = draw(p, p.ctr, rk);
@@ -759,15 +777,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   }
   TT *stally = nullptr;
   if (SHARED) { stally = (TT *)ptr; ptr += L.tally_bytes; }
-  Bank<PR> bk;
-  bk.xt = (void *)ptr; ptr += 16 * S;
-  if (DIM == 3 && !PR::kLocal) { bk.yz = (double2 *)ptr; ptr += 16 * S; } else { bk.yz = nullptr; }
-  bk.d0 = (void *)ptr; ptr += 16 * S;
-  if constexpr (PR::kF64) { bk.d1 = (double2 *)ptr; ptr += 16 * S; } else { bk.d1 = nullptr; }
-  bk.ids = (uint4 *)ptr; ptr += 16 * S;
-  bk.cell = (uint4 *)ptr; ptr += 16 * S;
-  bk.cnt = (uint2 *)ptr; ptr += 8 * S;
-  if constexpr (!PR::kF64) { bk.tau = (float *)ptr; ptr += 4 * S; } else { bk.tau = nullptr; }
+  const Bank<PR> bk = bank_view<PR>(ptr, S, DIM);
+  ptr += (long long)S * slot_bytes(PR::kF64, DIM, PR::kLocal);
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -958,10 +969,17 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             q = ovf[top - 1 - lane];
             alive = true;
           } else if (A.spill_in != nullptr && !MULTI) {
-            q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[h_first + (lane - n_o)];
+            const long long at = (long long)h_first + (lane - n_o);
+            if (A.census_out != nullptr)     // population control: the combed bank (pool layout)
+              bank_view<PR>(const_cast<void *>(A.spill_in), (long long)A.spill_cap, DIM)
+                  .load((int)at, q, DIM);
+            else
+              q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[at];
+            q.slot = (uint32_t)at;                           // position in the step's input
             alive = true;
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
+            q.slot = (uint32_t)(h_first + (lane - n_o));     // history's position in the run
             if (P.ww_lower != nullptr || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
@@ -999,6 +1017,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         got.nseg = __shfl_sync(0xffffffffu, q.nseg, src);
         got.ncol = __shfl_sync(0xffffffffu, q.ncol, src);
         got.ncross = __shfl_sync(0xffffffffu, q.ncross, src);
+        got.slot = __shfl_sync(0xffffffffu, q.slot, src);
         if constexpr (!PR::kF64) got.tau = __shfl_sync(0xffffffffu, q.tau, src);
         else got.tau = -1.0f;
         if (!has && r < na) { p = got; has = true; }
@@ -1023,17 +1042,20 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score,
                              flew ? tally_offset(P, A, p.hid) : 0);
         if (A.census_out != nullptr) {
-          // population control: append the warp's banked particles
+          // population control: a banked particle goes to its input position
+          // (no splitting here, so every input yields at most one), which
+          // keeps the bank in the order the step ran its particles
           const bool bank = has && outcome == OUT_BANKED;
           const uint32_t bm = __ballot_sync(0xffffffffu, bank);
           if (bm) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(A.census_count, (unsigned long long)__popc(bm));
-            base = __shfl_sync(0xffffffffu, base, 0);
+            if (lane == 0) atomicAdd(A.census_count, (unsigned long long)__popc(bm));
             if (bank) {
-              const unsigned long long slot = base + __popc(bm & lt);
-              if (slot < A.census_cap) reinterpret_cast<PartOf<PR> *>(A.census_out)[slot] = p;
-              else atomicOr(A.error, ERRBIT_OVERFLOW);
+              if (p.slot < A.census_cap) {
+                bank_view<PR>(A.census_out, (long long)A.census_cap, DIM).store((int)p.slot, p, DIM);
+                A.census_w[p.slot] = (double)p.w;
+              } else {
+                atomicOr(A.error, ERRBIT_OVERFLOW);
+              }
               has = false;
             }
           }
