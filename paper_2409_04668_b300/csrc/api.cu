@@ -158,6 +158,7 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   }
   Layout L = make_layout(pr, S, mode);
   const int dyn_max = dl.smem_block - 1024;   // room for the kernel's static shared memory
+  pr->dyn_max = dyn_max;
   if (L.total > dyn_max) {
     if (o.tally_mode == MCDC_TALLY_SHARED)
       return fail(MCDC_ERR_INVALID, "shared tally + bank exceed shared memory; use the global tally");
@@ -812,6 +813,8 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.overflow_cap = pr->overflow_cap;
   A.warp_aggregate = pr->warp_aggregate;
   A.tally = pr->tally;
+  A.batch_q = a->n_histories / (uint64_t)B;
+  A.batch_r = a->n_histories % (uint64_t)B;
 
   CK(cudaEventRecord(pr->ev1, s));
   if (pr->tally_mode == MCDC_TALLY_SHARED) {
@@ -839,6 +842,24 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     A.census_out = pr->pc_bank;
     A.census_count = pr->pc_cnt;
     A.census_cap = (unsigned long long)pr->pc_cap;
+    // every particle of a step is in that step's time bin: score it into a
+    // CTA-private shared tally over (estimator, batch, cell, group) when that
+    // fits beside the pool, else straight into the slices
+    Layout Ls = pr->L;
+    int smem_pc = pr->smem;
+    {
+      const long long bins = (long long)(P.estimator == MCDC_EST_COMBINED ? 2 : 1) * B *
+                             P.n_cells * P.G;
+      const long long bytes = (bins * (pr->key.f64 ? 8 : 4) + 15) & ~15ll;
+      const long long total = (long long)Ls.tables_bytes + bytes + Ls.bank_bytes + 64;
+      if (total <= pr->dyn_max && track_occupancy(pr->key, pr->block, (int)total) >= 1) {
+        Ls.tally_bytes = bytes;
+        Ls.total = (int)total;
+        smem_pc = (int)total;
+        A.step_tally = 1;
+        A.step_bins = (int)bins;
+      }
+    }
     // every banked particle lands at its position in the step's input (the
     // histories, then the combed bank): its census weight marks it
     A.census_w = pr->pc_w;
@@ -848,7 +869,8 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     for (int step = 0;; ++step) {
       CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(pr->pc_w, 0, sizeof(double) * (size_t)n_in, s));
-      CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
+      A.step_tbin = step;
+      CK(launch_track(pr->key, pr->grid, pr->block, smem_pc, s, P, A, Ls));
       if (step >= P.T - 1) break;
       CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
                          cudaMemcpyDeviceToHost, s));

@@ -146,7 +146,27 @@ struct RunArgs {
   // population control runs every batch in each launch: the global tally is
   // one slice of n_est x n_bins per batch, picked from the particle's history id
   int32_t tally_per_batch;
+  uint64_t batch_q, batch_r;  // n_hist / n_batches and n_hist % n_batches
+  // population control, one time step: every particle of the launch is in
+  // time bin step_tbin, so it scores into a CTA-private shared tally of
+  // step_bins = n_est x n_batches x cells x groups entries, added into the
+  // per-batch slices at the end of the launch (0: score the slices directly)
+  int32_t step_tally;
+  int32_t step_tbin;
+  int32_t step_bins;
 };
+
+// batch of history h (0-based within the run) from the run's precomputed
+// quotient and remainder; 32-bit division when the run allows it
+__device__ __forceinline__ int32_t batch_of_run(const RunArgs &A, uint64_t h) {
+  const uint64_t big = A.batch_r * (A.batch_q + 1);
+  if (A.n_hist <= 0xFFFFFFFFull) {
+    const uint32_t h32 = (uint32_t)h;
+    return (int32_t)(h < big ? h32 / (uint32_t)(A.batch_q + 1)
+                             : (uint32_t)A.batch_r + (h32 - (uint32_t)big) / (uint32_t)A.batch_q);
+  }
+  return (int32_t)(h < big ? h / (A.batch_q + 1) : A.batch_r + (h - big) / A.batch_q);
+}
 
 // ---- counter-based generator: Philox4x32-10 (Salmon et al., SC'11) -------
 struct U4 { uint32_t a, b, c, d; };

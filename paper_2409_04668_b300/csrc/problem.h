@@ -18,6 +18,7 @@ struct mcdc_problem {
   mcdc::TrackKey key{};
   // launch shape
   int block = 256, S = 512, ctas_per_sm = 1, grid = 0, smem = 0;
+  int dyn_max = 0;            // dynamic shared memory the tracker may use per CTA
   mcdc::Layout L{};
   int tally_mode = MCDC_TALLY_SHARED;
   int warp_aggregate = 0;

@@ -538,7 +538,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if (ev != 0) p.tau = fmaxf(p.tau - sig_t * d, 0.0f);
   }
   if (P.estimator != 1) {         // track-length estimator (alone or combined)
-    bin = bin_index(P, cell, p.g, p.tbin);
+    bin = A.step_tally ? cell * P.G + p.g : bin_index(P, cell, p.g, p.tbin);
     score = p.w * d;
   }
 
@@ -619,7 +619,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   p.ncol += 1;
   lc.col += 1;
   if (P.estimator != 0) {         // collision estimator (alone or combined)
-    cbin = bin_index(P, cell, p.g, p.tbin);
+    cbin = A.step_tally ? cell * P.G + p.g : bin_index(P, cell, p.g, p.tbin);
     cscore = p.w / tb.sigma_t[mg];
   }
   const U4 r1 = draw(p, p.ctr, A.rk);
@@ -695,7 +695,15 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
 __device__ __forceinline__ long long tally_offset(const DevProblem &P, const RunArgs &A,
                                                   uint64_t hid) {
   if (!A.tally_per_batch) return 0;
-  return (long long)batch_of(A.n_hist, A.n_batches, hid - A.offset) * P.n_tally;
+  return (long long)batch_of_run(A, hid - A.offset) * P.n_tally;
+}
+
+// population-control step tally: entry of (estimator half e, batch, cell x
+// group bin cg) -- the particle's time bin is the launch's
+__device__ __forceinline__ int step_bin(const DevProblem &P, const RunArgs &A, uint64_t hid,
+                                        int cg, int e) {
+  const int per = (int)(P.n_cells * P.G);
+  return (e * A.n_batches + batch_of_run(A, hid - A.offset)) * per + cg;
 }
 
 // ---------------------------------------------------------------------------
@@ -760,6 +768,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   __shared__ int s_cur_p;
   const DevProblem &P = MULTI ? sP : Pin;
   const RunArgs &A = MULTI ? sA : Ain;
+  // population-control step tally: from the launch's own arguments (batched
+  // launches fill sA only when a CTA claims an item, and never use it)
+  const bool step_tally = !SHARED && !MULTI && Ain.step_tally != 0;
+  const int step_bins = step_tally ? Ain.step_bins : 0;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
@@ -776,7 +788,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     tb.edges = (double *)ptr; ptr += align16(8ll * (L.T + 1));
   }
   TT *stally = nullptr;
-  if (SHARED) { stally = (TT *)ptr; ptr += L.tally_bytes; }
+  if (SHARED || step_tally) { stally = (TT *)ptr; ptr += L.tally_bytes; }
   const Bank<PR> bk = bank_view<PR>(ptr, S, DIM);
   ptr += (long long)S * slot_bytes(PR::kF64, DIM, PR::kLocal);
 
@@ -810,6 +822,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (!MULTI) load_tables();
   if (SHARED)
     for (long long q = tid; q < P.n_tally; q += nth) stally[q] = (TT)0;
+  for (int q = tid; q < step_bins; q += nth) stally[q] = (TT)0;
   if (tid < 16) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
@@ -905,9 +918,14 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           if (P.estimator != 0) {
             // combined estimator: the collision tally follows the track-length one
             const long long coff = P.estimator == 2 ? P.n_bins : 0;
-            tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine,
-                                 (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
-                                 mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
+            if (step_tally)
+              tally_scatter<TT, R>(stally, A.tally, true, agg, mine,
+                                   (mine && cbin >= 0) ? step_bin(P, A, q.hid, cbin, P.estimator == 2)
+                                                       : -1, cscore);
+            else
+              tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine,
+                                   (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
+                                   mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
           }
           if (P.implicit) {
             // weight removed by implicit capture: one shared add per warp
@@ -1039,8 +1057,12 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
-        tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score,
-                             flew ? tally_offset(P, A, p.hid) : 0);
+        if (step_tally)
+          tally_scatter<TT, R>(stally, A.tally, true, agg, flew,
+                               (flew && bin >= 0) ? step_bin(P, A, p.hid, bin, 0) : -1, score);
+        else
+          tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score,
+                               flew ? tally_offset(P, A, p.hid) : 0);
         if (A.census_out != nullptr) {
           // population control: a banked particle goes to its input position
           // (no splitting here, so every input yields at most one), which
@@ -1120,6 +1142,21 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
       }
     }
     __syncthreads();
+  }
+
+  // ---- population-control step tally: add the CTA's entries into the
+  // per-batch slices of the global tally (time bin step_tbin)
+  if (step_tally) {
+    __syncthreads();
+    const int per = (int)(P.n_cells * P.G);
+    for (int q = tid; q < step_bins; q += nth) {
+      const double v = (double)stally[q];
+      if (v == 0.0) continue;
+      const int cg = q % per, eb = q / per;
+      const int b = eb % A.n_batches, e = eb / A.n_batches;
+      atomicAdd(&A.tally[(long long)b * P.n_tally + e * P.n_bins + (long long)cg * P.T1 +
+                         A.step_tbin], v);
+    }
   }
 
   // ---- flush event counters: warp sums, one atomic per field per warp.
