@@ -845,20 +845,32 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     // every particle of a step is in that step's time bin: score it into a
     // CTA-private shared tally over (estimator, batch, cell, group) when that
     // fits beside the pool, else straight into the slices
+    // After a comb, each warp also stages its next 32 births from the combed
+    // bank in shared memory (bulk async copies overlapping the flights).
+    // Both are used only where they keep the CTAs per SM.
     Layout Ls = pr->L;
     int smem_pc = pr->smem;
     {
       const long long bins = (long long)(P.estimator == MCDC_EST_COMBINED ? 2 : 1) * B *
                              P.n_cells * P.G;
       const long long bytes = (bins * (pr->key.f64 ? 8 : 4) + 15) & ~15ll;
-      const long long total = (long long)Ls.tables_bytes + bytes + Ls.bank_bytes + 64;
-      if (total <= pr->dyn_max && track_occupancy(pr->key, pr->block, (int)total) >= 1) {
-        Ls.tally_bytes = bytes;
-        Ls.total = (int)total;
-        smem_pc = (int)total;
+      const long long stage = (long long)pr->block * slot_bytes(pr->key.f64, pr->dim, pr->key.local);
+      const long long base = (long long)Ls.tables_bytes + Ls.bank_bytes + 64;
+      auto fits = [&](long long total) {
+        return total <= pr->dyn_max &&
+               track_occupancy(pr->key, pr->block, (int)total) >= pr->ctas_per_sm;
+      };
+      if (fits(base + bytes + stage)) {
         A.step_tally = 1;
-        A.step_bins = (int)bins;
+        A.prefetch = 1;
+      } else if (fits(base + bytes)) {
+        A.step_tally = 1;
+      } else if (fits(base + stage)) {
+        A.prefetch = 1;
       }
+      if (A.step_tally) { Ls.tally_bytes = bytes; A.step_bins = (int)bins; }
+      Ls.total = (int)(base + (A.step_tally ? bytes : 0) + (A.prefetch ? stage : 0));
+      smem_pc = Ls.total;
     }
     // every banked particle lands at its position in the step's input (the
     // histories, then the combed bank): its census weight marks it

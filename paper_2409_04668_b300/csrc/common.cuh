@@ -154,6 +154,10 @@ struct RunArgs {
   int32_t step_tally;
   int32_t step_tbin;
   int32_t step_bins;
+  // population control after a comb: every warp stages its next 32 births
+  // from the combed bank (pool layout) in shared memory with bulk async
+  // copies while its particles fly (the launch's shared memory has room)
+  int32_t prefetch;
 };
 
 // batch of history h (0-based within the run) from the run's precomputed

@@ -77,6 +77,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int l
   return false;
 }
 
+// the calling thread arrives on the mbarrier and adds `bytes` of expected
+// asynchronous transfer to the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+               :
+               : "r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// bulk asynchronous copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_global, uint32_t bytes,
+                                         uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+      :
+      : "r"(smem_u32(dst_smem)), "l"(src_global), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // one warp allocates / frees `ncols` tensor-memory columns (a power of two >= 32)
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <math_constants.h>
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace mcdc {
 
@@ -772,6 +773,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   // launches fill sA only when a CTA claims an item, and never use it)
   const bool step_tally = !SHARED && !MULTI && Ain.step_tally != 0;
   const int step_bins = step_tally ? Ain.step_bins : 0;
+  const bool prefetch = !SHARED && !MULTI && Ain.prefetch != 0 && Ain.spill_in != nullptr;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
@@ -791,6 +793,13 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (SHARED || step_tally) { stally = (TT *)ptr; ptr += L.tally_bytes; }
   const Bank<PR> bk = bank_view<PR>(ptr, S, DIM);
   ptr += (long long)S * slot_bytes(PR::kF64, DIM, PR::kLocal);
+  // staged births (prefetch): 32 slots per warp in the pool layout
+  const Bank<PR> stage =
+      bank_view<PR>(ptr + (prefetch ? (long long)(tid >> 5) * 32 * slot_bytes(PR::kF64, DIM, PR::kLocal) : 0),
+                    32, DIM);
+  __shared__ uint64_t s_pf_bar[16];            // one mbarrier per warp
+  __shared__ unsigned long long s_pf_first[16];
+  __shared__ int s_pf_got[16], s_pf_phase[16], s_pf_lost[16];
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -827,6 +836,13 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
   if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }
+  if (prefetch && (tid & 31) == 0) {
+    tc::mbar_init(&s_pf_bar[tid >> 5], 1);
+    s_pf_got[tid >> 5] = 0;
+    s_pf_phase[tid >> 5] = 0;
+    s_pf_lost[tid >> 5] = -1;
+  }
+  if (prefetch) tc::fence_async_smem();
   __syncthreads();
 
   EndSink es{s_w, s_n};
@@ -898,7 +914,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
       // (1) collisions: a dense pass when 32 are parked, or whatever is
       // parked once nothing is ready and no more births can come
       {
-        const bool drain = exhausted && (*novf == 0);
+        const bool drain = exhausted && (*novf == 0) && !(prefetch && s_pf_got[warp] > 0);
         if (ctop >= 32 || (ctop > 0 && rtop == 0 && drain)) {
           const int n = min(ctop, 32);
           const bool mine = lane < n;
@@ -950,11 +966,32 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         }
       }
       // (3) births when lanes are still empty and nothing is ready
-      if (__any_sync(0xffffffffu, !has) && rtop == 0 && !(exhausted && *novf == 0)) {
+      const bool staged_ready = prefetch && s_pf_got[warp] > 0;
+      if (__any_sync(0xffffffffu, !has) && rtop == 0 &&
+          !(exhausted && *novf == 0 && !staged_ready)) {
         const int n_o = min(32, min(*novf, A.overflow_cap));
         int n_s = 0;
         unsigned long long h_first = 0;
-        if (n_o < 32 && !exhausted) {
+        bool staged = false;
+        if (n_o == 0 && staged_ready) {
+          // the chunk staged during the last round: wait for its copies
+          const bool done =
+              __all_sync(0xffffffffu, tc::mbar_wait(&s_pf_bar[warp], (uint32_t)s_pf_phase[warp], 1 << 26));
+          if (!done) {
+            if (lane == 0) {
+              atomicOr(A.error, ERRBIT_TIMEOUT);
+              s_pf_lost[warp] = s_pf_phase[warp];   // waited for once more before exit
+            }
+            exhausted = true;                   // its particles are lost: the run reports it
+          } else {
+            staged = true;
+            h_first = s_pf_first[warp];
+            n_s = s_pf_got[warp];
+          }
+          __syncwarp();
+          if (lane == 0) { s_pf_phase[warp] ^= 1; s_pf_got[warp] = 0; }
+          __syncwarp();
+        } else if (n_o < 32 && !exhausted) {
           const int want = 32 - n_o;
           unsigned long long first = 0;
           int got = 0;
@@ -988,7 +1025,9 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             alive = true;
           } else if (A.spill_in != nullptr && !MULTI) {
             const long long at = (long long)h_first + (lane - n_o);
-            if (A.census_out != nullptr)     // population control: the combed bank (pool layout)
+            if (staged)                      // staged by the bulk copies
+              stage.load(lane, q, DIM);
+            else if (A.census_out != nullptr)     // population control: the combed bank (pool layout)
               bank_view<PR>(const_cast<void *>(A.spill_in), (long long)A.spill_cap, DIM)
                   .load((int)at, q, DIM);
             else
@@ -1041,10 +1080,45 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         if (!has && r < na) { p = got; has = true; }
         rtop = max(0, na - ne);
         __syncwarp();
+        // prefetch: claim the next 32 input positions and stage them with one
+        // bulk copy per field array while the newborns fly (every lane has
+        // read its staged slot by now; the fence orders those reads before
+        // the copies' writes)
+        if (prefetch && !exhausted && s_pf_got[warp] == 0) {
+          int ng = 0;
+          if (lane == 0) {
+            const unsigned long long total = min(*A.spill_in_count, A.spill_cap);
+            const unsigned long long nf = atomicAdd(A.spill_in_cursor, 32ull);
+            ng = nf < total ? (int)min(32ull, total - nf) : 0;
+            if (ng > 0) {
+              const Bank<PR> src =
+                  bank_view<PR>(const_cast<void *>(A.spill_in), (long long)A.spill_cap, DIM);
+              const uint32_t bytes = (uint32_t)ng * 16u;
+              constexpr int arrays = 5 + ((DIM == 3 && !PR::kLocal) ? 1 : 0) + (PR::kF64 ? 1 : 0);
+              uint64_t *bar = &s_pf_bar[warp];
+              tc::fence_async_smem();
+              tc::mbar_expect_tx(bar, bytes * arrays);
+              tc::bulk_g2s(stage.xt, static_cast<const uint4 *>(src.xt) + nf, bytes, bar);
+              if (DIM == 3 && !PR::kLocal) tc::bulk_g2s(stage.yz, src.yz + nf, bytes, bar);
+              tc::bulk_g2s(stage.d0, static_cast<const uint4 *>(src.d0) + nf, bytes, bar);
+              if constexpr (PR::kF64) tc::bulk_g2s(stage.d1, src.d1 + nf, bytes, bar);
+              tc::bulk_g2s(stage.ids, src.ids + nf, bytes, bar);
+              tc::bulk_g2s(stage.cell, src.cell + nf, bytes, bar);
+              tc::bulk_g2s(stage.cnt, src.cnt + nf, bytes, bar);
+              s_pf_first[warp] = nf;
+              s_pf_got[warp] = ng;
+            }
+          }
+          ng = __shfl_sync(0xffffffffu, ng, 0);
+          if (ng < 32) exhausted = true;
+          __syncwarp();
+        }
       }
       // (4) nothing in flight: progress through collisions/births, or stop
       if (!__any_sync(0xffffffffu, has)) {
-        if (ctop == 0 && rtop == 0 && exhausted && *novf == 0) break;
+        if (ctop == 0 && rtop == 0 && exhausted && *novf == 0 &&
+            !(prefetch && s_pf_got[warp] > 0))
+          break;
         continue;
       }
       // (5) one flight for every lane that holds a particle
@@ -1143,6 +1217,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     }
     __syncthreads();
   }
+
+  // a staged chunk whose wait ran out: give its copies one more bounded wait
+  // so none is in flight when the CTA exits
+  if (prefetch && lane == 0 && s_pf_lost[warp] >= 0)
+    tc::mbar_wait(&s_pf_bar[warp], (uint32_t)s_pf_lost[warp], 1 << 26);
 
   // ---- population-control step tally: add the CTA's entries into the
   // per-batch slices of the global tally (time bin step_tbin)
