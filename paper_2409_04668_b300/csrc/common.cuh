@@ -64,7 +64,7 @@ struct DevProblem {
 // cell-local FP32 mode): x, y, z are offsets from the low faces of the cell
 // and t is the time left to the next census edge.
 template <class R, class Q = double>
-struct alignas(32) Part {   // whole 32-byte sectors: banks written at scattered positions
+struct Part {
   Q x, y, z;          // position (or cell-local offsets)
   Q t;                // time (or time to the next census edge)
   R ux, uy, uz;       // direction

@@ -85,7 +85,9 @@ struct Bank {
   uint4 *cell;        // {i | j << 16, k | tbin << 16, g, nseg}
   uint4 *cnt;         // {ncol, ncross, slot, optical depth (FP32 modes)}
 
-  __device__ __forceinline__ void load(int s, PartOf<PR> &p, int dim) const {
+  // with_slot: also the particle's input position (population control only;
+  // other launches leave it out of their registers)
+  __device__ __forceinline__ void load(int s, PartOf<PR> &p, int dim, bool with_slot = true) const {
     if constexpr (PR::kLocal) {
       const float4 a = reinterpret_cast<const float4 *>(xt)[s];
       p.x = a.x; p.y = a.y; p.z = a.z; p.t = a.w;
@@ -109,9 +111,9 @@ struct Bank {
     p.k = (int)(ce.y & 0xffffu); p.tbin = (int)(ce.y >> 16);
     p.g = (int)ce.z; p.nseg = ce.w;
     const uint4 cn = cnt[s];
-    p.ncol = cn.x; p.ncross = cn.y; p.slot = cn.z; p.tau = __uint_as_float(cn.w);
+    p.ncol = cn.x; p.ncross = cn.y; p.slot = with_slot ? cn.z : 0u; p.tau = __uint_as_float(cn.w);
   }
-  __device__ __forceinline__ void store(int s, const PartOf<PR> &p, int dim) const {
+  __device__ __forceinline__ void store(int s, const PartOf<PR> &p, int dim, bool with_slot = true) const {
     if constexpr (PR::kLocal) {
       reinterpret_cast<float4 *>(xt)[s] = make_float4(p.x, p.y, p.z, p.t);
     } else {
@@ -127,7 +129,7 @@ struct Bank {
     ids[s] = make_uint4(p.ctr, p.serial, (uint32_t)p.hid, (uint32_t)(p.hid >> 32));
     cell[s] = make_uint4((uint32_t)p.i | ((uint32_t)p.j << 16), (uint32_t)p.k | ((uint32_t)p.tbin << 16),
                          (uint32_t)p.g, p.nseg);
-    cnt[s] = make_uint4(p.ncol, p.ncross, p.slot, __float_as_uint(p.tau));
+    cnt[s] = make_uint4(p.ncol, p.ncross, with_slot ? p.slot : 0u, __float_as_uint(p.tau));
   }
 };
 
@@ -539,7 +541,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if (ev != 0) p.tau = fmaxf(p.tau - sig_t * d, 0.0f);
   }
   if (P.estimator != 1) {         // track-length estimator (alone or combined)
-    bin = A.step_tally ? cell * P.G + p.g : bin_index(P, cell, p.g, p.tbin);
+    bin = bin_index(P, cell, p.g, p.tbin);
     score = p.w * d;
   }
 
@@ -620,7 +622,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   p.ncol += 1;
   lc.col += 1;
   if (P.estimator != 0) {         // collision estimator (alone or combined)
-    cbin = A.step_tally ? cell * P.G + p.g : bin_index(P, cell, p.g, p.tbin);
+    cbin = bin_index(P, cell, p.g, p.tbin);
     cscore = p.w / tb.sigma_t[mg];
   }
   const U4 r1 = draw(p, p.ctr, A.rk);
@@ -700,11 +702,11 @@ __device__ __forceinline__ long long tally_offset(const DevProblem &P, const Run
 }
 
 // population-control step tally: entry of (estimator half e, batch, cell x
-// group bin cg) -- the particle's time bin is the launch's
+// group) for a tally bin of the launch's time bin
 __device__ __forceinline__ int step_bin(const DevProblem &P, const RunArgs &A, uint64_t hid,
-                                        int cg, int e) {
+                                        int bin, int e) {
   const int per = (int)(P.n_cells * P.G);
-  return (e * A.n_batches + batch_of_run(A, hid - A.offset)) * per + cg;
+  return (e * A.n_batches + batch_of_run(A, hid - A.offset)) * per + bin / P.T1;
 }
 
 // ---------------------------------------------------------------------------
@@ -774,6 +776,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   const bool step_tally = !SHARED && !MULTI && Ain.step_tally != 0;
   const int step_bins = step_tally ? Ain.step_bins : 0;
   const bool prefetch = !SHARED && !MULTI && Ain.prefetch != 0 && Ain.spill_in != nullptr;
+  // input positions matter to population control alone (global tally, single problem)
+  const bool use_slot = !SHARED && !MULTI && Ain.census_out != nullptr;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
@@ -919,7 +923,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           const int n = min(ctop, 32);
           const bool mine = lane < n;
           PartOf<PR> q;
-          if (mine) bk.load(slot_of(kPool - ctop + lane), q, DIM);
+          if (mine) bk.load(slot_of(kPool - ctop + lane), q, DIM, use_slot);
           __syncwarp();   // every parked particle is read before survivors are written
           ctop -= n;
           bool alive = false;
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             if (lane == 0) atomicAdd(&s_w[1], wabs);
           }
           const uint32_t am = __ballot_sync(0xffffffffu, alive);
-          if (alive) bk.store(slot_of(rtop + __popc(am & lt)), q, DIM);
+          if (alive) bk.store(slot_of(rtop + __popc(am & lt)), q, DIM, use_slot);
           rtop += __popc(am);
           __syncwarp();
         }
@@ -960,7 +964,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         if (empty && rtop) {
           const int r = __popc(empty & lt);
           const bool take = !has && r < rtop;
-          if (take) { bk.load(slot_of(rtop - 1 - r), p, DIM); has = true; }
+          if (take) { bk.load(slot_of(rtop - 1 - r), p, DIM, use_slot); has = true; }
           rtop -= min(rtop, __popc(empty));
           __syncwarp();
         }
@@ -1032,11 +1036,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
                   .load((int)at, q, DIM);
             else
               q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[at];
-            q.slot = (uint32_t)at;                           // position in the step's input
+            if (use_slot) q.slot = (uint32_t)at;             // position in the step's input
             alive = true;
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
-            q.slot = (uint32_t)(h_first + (lane - n_o));     // history's position in the run
+            if (use_slot) q.slot = (uint32_t)(h_first + (lane - n_o));   // history's position in the run
             if (P.ww_lower != nullptr || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
@@ -1049,7 +1053,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         const int na = __popc(am), ne = __popc(empty);
         const int k = __popc(am & lt);                 // rank of my newborn
         const int r = __popc(empty & lt);              // rank of my empty lane
-        if (alive && k >= ne) bk.store(slot_of(k - ne), q, DIM);
+        if (alive && k >= ne) bk.store(slot_of(k - ne), q, DIM, use_slot);
         __syncwarp();
         if (lane == 0) *novf = min(*novf, A.overflow_cap) - n_o;
         // lane with the r-th empty slot receives the r-th newborn (a shuffle per field)
@@ -1074,7 +1078,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         got.nseg = __shfl_sync(0xffffffffu, q.nseg, src);
         got.ncol = __shfl_sync(0xffffffffu, q.ncol, src);
         got.ncross = __shfl_sync(0xffffffffu, q.ncross, src);
-        got.slot = __shfl_sync(0xffffffffu, q.slot, src);
+        got.slot = use_slot ? __shfl_sync(0xffffffffu, q.slot, src) : 0u;
         if constexpr (!PR::kF64) got.tau = __shfl_sync(0xffffffffu, q.tau, src);
         else got.tau = -1.0f;
         if (!has && r < na) { p = got; has = true; }
@@ -1159,7 +1163,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         const bool park = has && outcome == OUT_COLL;
         const uint32_t pm = __ballot_sync(0xffffffffu, park);
         if (pm) {
-          if (park) { bk.store(slot_of(kPool - ctop - 1 - __popc(pm & lt)), p, DIM); has = false; }
+          if (park) { bk.store(slot_of(kPool - ctop - 1 - __popc(pm & lt)), p, DIM, use_slot); has = false; }
           ctop += __popc(pm);
           __syncwarp();
         }
