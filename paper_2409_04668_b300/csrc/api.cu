@@ -75,14 +75,71 @@ int dalloc(mcdc_problem *pr, T **out, size_t count) {
   return MCDC_OK;
 }
 
-template <class T>
-int upload(mcdc_problem *pr, const T **dst, const std::vector<T> &src) {
-  T *d = nullptr;
-  int rc = dalloc(pr, &d, src.size());
-  if (rc) return rc;
-  CK(cudaMemcpy(d, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
-  *dst = d;
-  return MCDC_OK;
+// A problem's tables and accumulators in one device allocation: uploads are
+// gathered in a host buffer and copied once, device-only arrays follow them
+// and are zeroed once (a create is a handful of API calls, not dozens).
+struct Arena {
+  std::vector<unsigned char> host;
+  size_t device_bytes = 0;
+  std::vector<std::pair<void **, size_t>> up, dev;   // field, offset
+  static size_t round(size_t v) { return (v + 255) & ~size_t(255); }
+  template <class T>
+  void upload(const T **field, const std::vector<T> &src) {
+    const size_t off = round(host.size());
+    host.resize(off + std::max<size_t>(src.size() * sizeof(T), 16));
+    if (!src.empty()) std::memcpy(host.data() + off, src.data(), src.size() * sizeof(T));
+    up.push_back({reinterpret_cast<void **>(const_cast<T **>(field)), off});
+  }
+  template <class T>
+  void device(T **field, size_t count) {
+    const size_t off = round(device_bytes);
+    device_bytes = off + std::max<size_t>(count * sizeof(T), 16);
+    dev.push_back({reinterpret_cast<void **>(field), off});
+  }
+  int commit(mcdc_problem *pr) {
+    const size_t hb = round(host.size());
+    unsigned char *base = nullptr;
+    if (dalloc(pr, &base, hb + device_bytes)) return MCDC_ERR_OOM;
+    CK(cudaMemcpy(base, host.data(), host.size(), cudaMemcpyHostToDevice));
+    if (device_bytes) CK(cudaMemset(base + hb, 0, device_bytes));
+    for (auto &f : up) *f.first = base + f.second;
+    for (auto &f : dev) *f.first = base + hb + f.second;
+    return MCDC_OK;
+  }
+};
+
+// Pinned host words a run reads back (statistics, error flags, a count),
+// from a process-wide pool: pinned allocation costs far more than a run's
+// setup, so blocks are reused across problems and kept until exit.
+struct PinnedBlock {
+  Stats stats;
+  int32_t error[4];
+  unsigned long long count;
+};
+std::mutex g_pin_mu;
+std::vector<PinnedBlock *> g_pin_free;
+
+PinnedBlock *pinned_get() {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      PinnedBlock *b = g_pin_free.back();
+      g_pin_free.pop_back();
+      return b;
+    }
+  }
+  void *p = nullptr;
+  if (cudaMallocHost(&p, sizeof(PinnedBlock)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<PinnedBlock *>(p);
+}
+
+void pinned_put(PinnedBlock *b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(b);
 }
 
 void release(mcdc_problem *pr) {
@@ -93,9 +150,7 @@ void release(mcdc_problem *pr) {
   if (pr->ev0) cudaEventDestroy(pr->ev0);
   if (pr->ev1) cudaEventDestroy(pr->ev1);
   if (pr->ev2) cudaEventDestroy(pr->ev2);
-  if (pr->h_stats) cudaFreeHost(pr->h_stats);
-  if (pr->h_error) cudaFreeHost(pr->h_error);
-  if (pr->h_spill) cudaFreeHost(pr->h_spill);
+  pinned_put(static_cast<PinnedBlock *>(pr->pinned));
   delete pr;
 }
 
@@ -251,10 +306,6 @@ int ensure_pc(mcdc_problem *pr, int cap, long long combed, int B) {
   }
   if ((rc = ensure_slices(pr, B))) return rc;
   if (!pr->pc_cnt && (rc = dalloc(pr, &pr->pc_cnt, 4))) return rc;
-  if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MCDC_ERR_OOM, "cudaMallocHost failed");
-  }
   return MCDC_OK;
 }
 
@@ -288,10 +339,6 @@ int ensure_overflow(mcdc_problem *pr) {
       if ((rc = dalloc(pr, &a, scap * pb))) return rc;
       if ((rc = dalloc(pr, &b, scap * pb))) return rc;
       if ((rc = dalloc(pr, &c, 4))) return rc;
-      if (!pr->h_spill && cudaMallocHost(&pr->h_spill, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(MCDC_ERR_OOM, "pinned buffer");
-      }
       pr->spill[0] = a;
       pr->spill[1] = b;
       pr->spill_cnt = c;
@@ -623,15 +670,16 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     g_err = keep;
     return code;
   };
+  Arena arena;
   {
     std::vector<uint8_t> matv(mesh->material, mesh->material + n_cells);
-    if ((rc = upload(pr, &P.material, matv))) return bail(rc);
-    if ((rc = upload(pr, &P.sigma_t, st))) return bail(rc);
-    if ((rc = upload(pr, &P.scat, scat))) return bail(rc);
-    if ((rc = upload(pr, &P.cdf, cdf))) return bail(rc);
-    if ((rc = upload(pr, &P.speed, speed))) return bail(rc);
-    if ((rc = upload(pr, &P.edges, edges))) return bail(rc);
-    if ((rc = upload(pr, &P.src_cdf, scdf))) return bail(rc);
+    arena.upload(&P.material, matv);
+    arena.upload(&P.sigma_t, st);
+    arena.upload(&P.scat, scat);
+    arena.upload(&P.cdf, cdf);
+    arena.upload(&P.speed, speed);
+    arena.upload(&P.edges, edges);
+    arena.upload(&P.src_cdf, scdf);
     for (int a = 0; a < 3; ++a) {
       P.faces[a] = nullptr;
       if (!bounded[a]) continue;
@@ -640,12 +688,12 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
         const double step = (double)k * wid[a];   // two roundings, as on the device
         fc[k] = org[a] + step;
       }
-      if ((rc = upload(pr, &P.faces[a], fc))) return bail(rc);
+      arena.upload(&P.faces[a], fc);
     }
     for (int a = 0; a < 3; ++a) P.width32[a] = bounded[a] ? (float)wid[a] : 0.0f;
     std::vector<float> bw(std::max(T, 1), 0.0f);
     for (int j = 0; j < T; ++j) bw[j] = (float)(edges[j + 1] - edges[j]);
-    if ((rc = upload(pr, &P.binw32, bw))) return bail(rc);
+    arena.upload(&P.binw32, bw);
     auto f32 = [](const std::vector<double> &v) {
       std::vector<float> r(v.size());
       for (size_t q = 0; q < v.size(); ++q) r[q] = (float)v[q];
@@ -653,39 +701,39 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
     };
     std::vector<float> inv(G);
     for (int g = 0; g < G; ++g) inv[g] = (float)(1.0 / speed[g]);
-    if ((rc = upload(pr, &P.sigma_t32, f32(st)))) return bail(rc);
-    if ((rc = upload(pr, &P.scat32, f32(scat)))) return bail(rc);
-    if ((rc = upload(pr, &P.cdf32, f32(cdf)))) return bail(rc);
-    if ((rc = upload(pr, &P.speed32, f32(speed)))) return bail(rc);
-    if ((rc = upload(pr, &P.inv_speed32, inv))) return bail(rc);
-    if ((rc = upload(pr, &P.src_cdf32, f32(scdf)))) return bail(rc);
+    arena.upload(&P.sigma_t32, f32(st));
+    arena.upload(&P.scat32, f32(scat));
+    arena.upload(&P.cdf32, f32(cdf));
+    arena.upload(&P.speed32, f32(speed));
+    arena.upload(&P.inv_speed32, inv);
+    arena.upload(&P.src_cdf32, f32(scdf));
   }
   if ((rc = choose_shape(pr, dl))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->sum1, (size_t)P.n_tally))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->sum2, (size_t)P.n_tally))) return bail(rc);
-  if (P.estimator == MCDC_EST_COMBINED)
-    if ((rc = dalloc(pr, &pr->sum12, (size_t)P.n_bins))) return bail(rc);
-  if (pr->tally_mode == MCDC_TALLY_GLOBAL)
-    if ((rc = dalloc(pr, &pr->tally, (size_t)P.n_tally))) return bail(rc);
+  arena.device(&pr->sum1, (size_t)P.n_tally);
+  arena.device(&pr->sum2, (size_t)P.n_tally);
+  if (P.estimator == MCDC_EST_COMBINED) arena.device(&pr->sum12, (size_t)P.n_bins);
+  if (pr->tally_mode == MCDC_TALLY_GLOBAL) arena.device(&pr->tally, (size_t)P.n_tally);
   // region[0..4]: sums (track or the one estimator), squares, collision sums,
-  // squares, products; region_batch = region + 5: the batch's two region sums
-  if ((rc = dalloc(pr, &pr->region, 8))) return bail(rc);
+  // squares, products; region + 5: the batch's two region sums
+  arena.device(&pr->region, 8);
+  arena.device(&pr->stats, 1);
+  arena.device(&pr->error, 4);
+  arena.device(&pr->work, 64);
+  if ((rc = arena.commit(pr))) return bail(rc);
   pr->region_batch = pr->region + 5;
-  if ((rc = dalloc(pr, &pr->stats, 1))) return bail(rc);
-  if ((rc = dalloc(pr, &pr->error, 4))) return bail(rc);
-  if ((rc = ensure_work_slots(pr, 64))) return bail(rc);
-  if (cudaEventCreate(&pr->ev0) != cudaSuccess || cudaEventCreate(&pr->ev1) != cudaSuccess ||
-      cudaEventCreate(&pr->ev2) != cudaSuccess ||
-      cudaMallocHost(&pr->h_stats, sizeof(Stats)) != cudaSuccess ||
-      cudaMallocHost(&pr->h_error, sizeof(int32_t) * 4) != cudaSuccess) {
+  pr->work_slots = 64;
+  PinnedBlock *pin = pinned_get();
+  if (!pin || cudaEventCreate(&pr->ev0) != cudaSuccess || cudaEventCreate(&pr->ev1) != cudaSuccess ||
+      cudaEventCreate(&pr->ev2) != cudaSuccess) {
     cudaGetLastError();
+    pinned_put(pin);
     fail(MCDC_ERR_CUDA, "event or pinned buffer creation failed");
     return bail(MCDC_ERR_CUDA);
   }
-  if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
-    cudaError_t e = cudaMemset(pr->tally, 0, sizeof(double) * P.n_tally);
-    if (e != cudaSuccess) { fail(MCDC_ERR_CUDA, cudaGetErrorString(e)); return bail(MCDC_ERR_CUDA); }
-  }
+  pr->pinned = pin;
+  pr->h_stats = &pin->stats;
+  pr->h_error = pin->error;
+  pr->h_spill = &pin->count;
   if (o.autotune && o.block_size == 0 && o.pc_target == 0) {
     if ((rc = autotune(pr, dl))) return bail(rc);
   }

@@ -59,7 +59,8 @@ struct mcdc_problem {
   void *pc_temp = nullptr;
   size_t pc_temp_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-  // host staging
+  // host staging: words of one pinned block from a process-wide pool
+  void *pinned = nullptr;
   mcdc::Stats *h_stats = nullptr;   // pinned
   int32_t *h_error = nullptr; // pinned
 };
