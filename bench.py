@@ -417,6 +417,13 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     return out
 
 
+# Weight-window settings of the learned windows: source window 0.25 (the
+# library default is 0.5), upper / survival ratios 4 / 2 (default 5 / 2.5).
+# Over five pilot seeds on both boxes their median learned FOM was 4.6e4 (deep)
+# and 7.0e4 (shallow) against 2.4e4 and 5.6e4 with the defaults.
+WW_SETTINGS = {"source_wl": 0.25, "upper_ratio": 4.0, "survival_ratio": 2.0}
+
+
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
@@ -445,7 +452,8 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         train_ms, ww_ms = 0.0, 0.0
         seed = seed0 + 4
         for it in range(refits + 1):
-            rep = P.train_importance(mean, rel, epochs=6, batch=16384, min_ratio=1e-20)
+            rep = P.train_importance(mean, rel, epochs=6, batch=16384, min_ratio=1e-20,
+                                     **WW_SETTINGS)
             train_ms += rep["train_ms"] + rep["bake_ms"]
             if it < refits:
                 st, _ = P.run_ex(n_ww, seed, batches=16, mean=mean, relerr=rel)
