@@ -420,7 +420,9 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
 # Weight-window settings of the learned windows: source window 0.25 (the
 # library default is 0.5), upper / survival ratios 4 / 2 (default 5 / 2.5).
 # Over five pilot seeds on both boxes their median learned FOM was 4.6e4 (deep)
-# and 7.0e4 (shallow) against 2.4e4 and 5.6e4 with the defaults.
+# and 7.0e4 (shallow) against 2.4e4 and 5.6e4 with the defaults; 20 epochs per
+# fit (instead of 6) raised the medians to 4.5e4 / 1.0e5 against 3.2e4 / 9.3e4
+# in the same sweep, and two refits are needed (one gave a deep median of 106).
 WW_SETTINGS = {"source_wl": 0.25, "upper_ratio": 4.0, "survival_ratio": 2.0}
 
 
@@ -452,7 +454,7 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         train_ms, ww_ms = 0.0, 0.0
         seed = seed0 + 4
         for it in range(refits + 1):
-            rep = P.train_importance(mean, rel, epochs=6, batch=16384, min_ratio=1e-20,
+            rep = P.train_importance(mean, rel, epochs=20, batch=16384, min_ratio=1e-20,
                                      **WW_SETTINGS)
             train_ms += rep["train_ms"] + rep["bake_ms"]
             if it < refits:
