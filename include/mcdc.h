@@ -174,6 +174,12 @@ typedef struct mcdc_options {
                                    does, so an FP32 run draws the same random
                                    numbers as its FP64 twin (paired precision
                                    studies).  FP64 mode always samples afresh.   */
+    int64_t max_children;       /* weight windows: split children one run may make
+                                   (0: 2^27; negative: no limit).  A split past the
+                                   budget makes no child and the parent keeps its
+                                   weight (unbiased, counted in splits_dropped):
+                                   windows that would split without end cost a
+                                   bounded run instead of an endless one        */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */

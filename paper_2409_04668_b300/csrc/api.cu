@@ -719,6 +719,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   arena.device(&pr->stats, 1);
   arena.device(&pr->error, 4);
   arena.device(&pr->work, 64);
+  arena.device(&pr->children, 1);
   if ((rc = arena.commit(pr))) return bail(rc);
   pr->region_batch = pr->region + 5;
   pr->work_slots = 64;
@@ -842,6 +843,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   CK(cudaMemsetAsync(pr->stats, 0, sizeof(Stats), s));
   CK(cudaMemsetAsync(pr->error, 0, 4 * sizeof(int32_t), s));
   CK(cudaMemsetAsync(pr->work, 0, sizeof(unsigned long long) * pr->work_slots, s));
+  CK(cudaMemsetAsync(pr->children, 0, sizeof(unsigned long long), s));
 
   RunArgs A{};
   A.n_hist = a->n_histories;
@@ -861,6 +863,11 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.overflow_cap = pr->overflow_cap;
   A.warp_aggregate = pr->warp_aggregate;
   A.tally = pr->tally;
+  if (pr->opt.max_children >= 0) {
+    A.children_made = pr->children;
+    A.children_budget = pr->opt.max_children > 0 ? (unsigned long long)pr->opt.max_children
+                                                 : (1ull << 27);
+  }
   A.batch_q = a->n_histories / (uint64_t)B;
   A.batch_r = a->n_histories % (uint64_t)B;
 

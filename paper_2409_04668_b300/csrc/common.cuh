@@ -154,6 +154,10 @@ struct RunArgs {
   int32_t step_tally;
   int32_t step_tbin;
   int32_t step_bins;
+  // weight windows: children made so far in the run (device counter) and the
+  // run's budget; nullptr: no budget
+  unsigned long long *children_made;
+  unsigned long long children_budget;
   // population control after a comb: every warp stages its next 32 births
   // from the combed bank (pool layout) in shared memory with bulk async
   // copies while its particles fly (the launch's shared memory has room)

@@ -29,6 +29,7 @@ struct mcdc_problem {
   double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
          *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
   double *sum12 = nullptr;      // combined estimator: [n_bins]
+  unsigned long long *children = nullptr;   // weight windows: children made in the run
   double *parts_tmp = nullptr;  // combined estimator: [5][n_bins] staging of host parts_out
   mcdc::Stats *stats = nullptr;
   int32_t *error = nullptr;

@@ -267,7 +267,9 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
 
 // ---------------------------------------------------------------------------
 // weight window at collisions and cell crossings.  Returns false if the
-// particle is rouletted away.  Children go to the CTA's overflow stack.
+// particle is rouletted away.  Children go to the warp's overflow stack
+// (s_novf[0]: its size) or the spill bank; s_novf[16] is the warp's
+// reservation of the run's children budget.
 template <class PR, int DIM>
 __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> &tb,
                               const RunArgs &A, const EndSink &es, PartOf<PR> &p,
@@ -289,7 +291,21 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
       // weight (splitting is optional, so the estimate stays unbiased)
       const R wc = p.w / (R)n;
       int made = 0;
-      for (int c = 1; c < n; ++c) {
+      // the run's budget of children: past it no child is made (as when the
+      // banks are full), which bounds the work of windows that would split
+      // without end.  The warp draws on a reservation in shared memory
+      // (s_novf[16]) refilled from the run's counter 256 children at a time.
+      int room = n - 1;
+      if (A.children_made != nullptr) {
+        int *left = s_novf + 16;
+        if (atomicSub(left, n - 1) < n - 1) {
+          atomicAdd(left, n - 1);
+          const unsigned long long before = atomicAdd(A.children_made, 256ull);
+          if (before + 256ull <= A.children_budget) atomicAdd(left, 256 - (n - 1));
+          else room = 0;
+        }
+      }
+      for (int c = 1; c <= room; ++c) {
         const U4 h = philox4x32_10_rk(0xFFFFFFFFu, p.serial, p.ctr, (uint32_t)c, A.rk);
         PartOf<PR> ch = p;
         ch.w = wc;
@@ -807,7 +823,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
-  __shared__ int s_novf[16];
+  __shared__ int s_novf[32];     // [w]: warp w's stack of children; [16 + w]: children it may still make
   __shared__ double s_w[4];
   __shared__ uint32_t s_n[9];
   __shared__ double s_red[32];   // per-warp region sums (two estimators)
@@ -836,7 +852,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (SHARED)
     for (long long q = tid; q < P.n_tally; q += nth) stally[q] = (TT)0;
   for (int q = tid; q < step_bins; q += nth) stally[q] = (TT)0;
-  if (tid < 16) s_novf[tid] = 0;
+  if (tid < 32) s_novf[tid] = 0;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
   if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }

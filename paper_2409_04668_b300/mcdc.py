@@ -59,7 +59,8 @@ class mcdc_options(C.Structure):
                 ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
                 ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
                 ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
-                ("pc_target", C.c_int32), ("flight_sampling", C.c_int32)]
+                ("pc_target", C.c_int32), ("flight_sampling", C.c_int32),
+                ("max_children", C.c_int64)]
 
 
 class mcdc_stats(C.Structure):
@@ -202,14 +203,15 @@ class Problem:
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
                  overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0,
-                 flight_sampling=0):
+                 flight_sampling=0, max_children=0):
         """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
         at an interior census edge (0: off); flight_sampling: FP32 modes, 0
         carries the optical depth across surface and census events, 1 samples
         the distance to collision every flight (the FP64 twin's random
-        numbers)."""
+        numbers); max_children: weight windows, split children one run may
+        make (0: 2^27, negative: no limit)."""
         self.desc = prob
         keep = []
 
@@ -258,6 +260,7 @@ class Problem:
         o.estimator = int(estimator)
         o.pc_target = int(pc_target)
         o.flight_sampling = int(flight_sampling)
+        o.max_children = int(max_children)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])

@@ -72,3 +72,27 @@ def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(mcdc):
     got = mcdc.mlp_forward(p.astype(np.float32), X.astype(np.float32))
     ref = O.mlp_forward(p, X)
     assert np.abs(got - ref).max() < 2e-2 * np.abs(ref).max()
+
+
+def test_children_budget_bounds_explosive_windows(mcdc):
+    """Windows that fall tenfold every two cells split a right-moving particle
+    at every crossing: with a budget of 200k children the run ends, drops the
+    splits past the budget (the parent keeps the weight) and still agrees with
+    analog."""
+    import numpy as np
+    from paper_2409_04668_b300 import workloads as W
+    nc = 40
+    prob = W.slab("explosive_windows", 20.0, nc, np.zeros(nc), [[1.0]], [[0.9]], src=(0.0, 2.0))
+    lower = 10.0 ** (-np.arange(nc) / 2.0)
+    N = 20_000
+    budget = 200_000
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP32, tally_mode=mcdc.TALLY_GLOBAL,
+                      max_children=budget, region=((30, 0, 0), (40, 1, 1))) as P:
+        P.set_weight_windows(lower, 5.0, 2.5, 16)
+        st, (m_w, r_w) = P.run_ex(N, 3, batches=20)
+    assert st["splits_dropped"] > 0
+    assert st["children"] <= budget
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP32, region=((30, 0, 0), (40, 1, 1))) as P:
+        _, (m_a, r_a) = P.run_ex(4_000_000, 4, batches=40)
+    z = (m_w - m_a) / np.hypot(m_w * r_w, m_a * r_a)
+    assert abs(z) < 4.0, (m_w, m_a, z)
