@@ -64,6 +64,13 @@ typedef struct {
     double ww_survival_ratio;  /* w_S = ratio * w_L                              */
     int32_t ww_nmax;           /* split cap                                      */
 
+    /* R15: per-event windows from the importance network instead of a table */
+    const double *ww_net;      /* network parameters (mlp.c layout), or NULL      */
+    int32_t ww_net_in, ww_net_h;   /* inputs (4 + G) and hidden width            */
+    double ww_net_shift, ww_net_scale; /* log importance = output * scale + shift */
+    double ww_net_top, ww_net_floor, ww_net_wl0;  /* w_L = wl0 exp(min(0,
+                                  max(log importance, floor) - top))            */
+
     int32_t region_lo[3], region_hi[3];  /* cell box of the scalar tally [lo,hi) */
 
     int32_t estimator;         /* ORC_EST_TRACK, ORC_EST_COLLISION or ORC_EST_COMBINED */
@@ -137,6 +144,10 @@ int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
 int64_t orc_mlp_param_count(int32_t in, int32_t H);
 void orc_mlp_forward(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
                      const double *X, double *out);
+/* R15: the network's inputs for a particle at (x, y, z, t) in time bin tbin
+ * and group g (see transport.c). */
+void orc_net_features(const orc_problem *p, double x, double y, double z, double t,
+                      int32_t tbin, int32_t g, double *f);
 double orc_mlp_loss_grad(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
                          const double *X, const double *y, const double *w, double *grad);
 void orc_adam_step(int64_t np, double *p, double *m, double *v, const double *g, double lr,

@@ -28,6 +28,9 @@ class OrcProblem(C.Structure):
         ("n_tbin", C.c_int32), ("edges", C.c_void_p),
         ("ww_lower", C.c_void_p), ("ww_upper_ratio", C.c_double),
         ("ww_survival_ratio", C.c_double), ("ww_nmax", C.c_int32),
+        ("ww_net", C.c_void_p), ("ww_net_in", C.c_int32), ("ww_net_h", C.c_int32),
+        ("ww_net_shift", C.c_double), ("ww_net_scale", C.c_double),
+        ("ww_net_top", C.c_double), ("ww_net_floor", C.c_double), ("ww_net_wl0", C.c_double),
         ("region_lo", C.c_int32 * 3), ("region_hi", C.c_int32 * 3),
         ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
         ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
@@ -72,6 +75,8 @@ def lib():
                                 C.c_void_p]
         L.orc_trace.restype = C.c_int
         L.orc_comb.argtypes = [C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]
+        L.orc_net_features.argtypes = [C.POINTER(OrcProblem), C.c_double, C.c_double, C.c_double,
+                                       C.c_double, C.c_int32, C.c_int32, C.c_void_p]
         L.orc_combine.argtypes = [C.c_int64] + [C.c_void_p] * 5 + [C.c_uint64, C.c_int32,
                                                                     C.c_double] + [C.c_void_p] * 3
         if hasattr(L, "orc_mlp_forward"):
@@ -135,7 +140,18 @@ def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None, pc_tar
         e = _f64(prob.edges)
         s.n_tbin, s.edges = len(e) - 1, keep.ptr(e)
     if ww is not None:
-        s.ww_lower = keep.ptr(_f64(ww["lower"]))
+        # a table of lower bounds ("lower"), or per-event windows from the
+        # network ("net": parameters, "hidden", "shift", "scale", "top",
+        # "floor", "wl0"; R15)
+        if "net" in ww:
+            s.ww_net = keep.ptr(_f64(ww["net"]))
+            s.ww_net_in = 4 + int(np.asarray(prob.sigma_t).shape[1])
+            s.ww_net_h = int(ww.get("hidden", 64))
+            s.ww_net_shift, s.ww_net_scale = float(ww["shift"]), float(ww["scale"])
+            s.ww_net_top, s.ww_net_floor = float(ww["top"]), float(ww["floor"])
+            s.ww_net_wl0 = float(ww["wl0"])
+        else:
+            s.ww_lower = keep.ptr(_f64(ww["lower"]))
         s.ww_upper_ratio = float(ww.get("upper_ratio", 5.0))
         s.ww_survival_ratio = float(ww.get("survival_ratio", 2.5))
         s.ww_nmax = int(ww.get("nmax", 16))
@@ -205,6 +221,18 @@ def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=ES
         out["sum1"] = s1.reshape(shp)
         out["sum2"] = s2.reshape(shp)
     return out
+
+
+def net_features(prob, x, y, z, t, tbin, g):
+    """The network's inputs for a particle (R15)."""
+    L = lib()
+    keep = _Keep()
+    s = _struct(prob, {"net": np.zeros(1), "shift": 0.0, "scale": 1.0, "top": 0.0,
+                       "floor": 0.0, "wl0": 1.0}, keep)
+    f = np.zeros(4 + int(np.asarray(prob.sigma_t).shape[1]))
+    L.orc_net_features(C.byref(s), float(x), float(y), float(z), float(t), int(tbin), int(g),
+                       f.ctypes.data)
+    return f
 
 
 def combine(s1x, s2x, s1y, s2y, s12, n_hist, batches, volume, alpha=None):

@@ -68,6 +68,15 @@
  *     variance combination extrapolates to an estimate of zero with zero
  *     variance; clipped, the estimate stays between the two.)  The region
  *     scalar is combined the same way from its two batch series.
+ *  R15 per-event windows (optional, instead of the table of R9): at every
+ *     window check the lower bound comes from the importance network
+ *     evaluated at the particle itself.  Inputs: position scaled to [-1, 1]
+ *     over each bounded axis of the mesh (0 on an unbounded axis), time as
+ *     2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time bin j (0 in steady
+ *     state), then the group one-hot -- the continuous versions of the cell
+ *     centre and bin centre the network is trained on.  With the output y,
+ *     lp = y scale + shift and w_L = wl0 exp(min(0, max(lp, floor) - top));
+ *     upper and survival bounds and the split cap as in R9.
  */
 #include <math.h>
 #include <pthread.h>
@@ -232,12 +241,44 @@ static part source_particle(const orc_problem *p, const tables *tb,
 
 /* ---- weight windows (R9) ------------------------------------------- */
 /* Returns 1 if the particle survives.  Children go on the stack. */
+void orc_net_features(const orc_problem *p, double x, double y, double z, double t,
+                      int32_t tbin, int32_t g, double *f)
+{
+    const double pos[3] = { x, y, z };
+    for (int a = 0; a < 3; ++a)
+        f[a] = axis_bounded(p, a)
+                   ? 2.0 * (pos[a] - p->origin[a]) / ((double)p->n[a] * p->width[a]) - 1.0
+                   : 0.0;
+    if (p->n_tbin > 0) {
+        int32_t j = tbin < p->n_tbin ? tbin : p->n_tbin - 1;
+        double u = (t - p->edges[j]) / (p->edges[j + 1] - p->edges[j]);
+        f[3] = 2.0 * ((double)j + u) / (double)p->n_tbin - 1.0;
+    } else {
+        f[3] = 0.0;
+    }
+    for (int32_t k = 4; k < p->ww_net_in; ++k) f[k] = (k - 4 == g) ? 1.0 : 0.0;
+}
+
+/* R15: the window's lower bound from the network at the particle */
+static double net_window(const orc_problem *p, const part *P)
+{
+    double f[64], out;
+    orc_net_features(p, P->x, P->y, P->z, P->t, P->tbin, P->g, f);
+    orc_mlp_forward(p->ww_net_in, p->ww_net_h, 0, p->ww_net, 1, f, &out);
+    double lp = out * p->ww_net_scale + p->ww_net_shift;
+    if (lp < p->ww_net_floor) lp = p->ww_net_floor;
+    double e = lp - p->ww_net_top;
+    return p->ww_net_wl0 * exp(e < 0.0 ? e : 0.0);
+}
+
 static int weight_window(const orc_problem *p, const tables *tb, uint64_t seed,
                          uint64_t hid, part *P, stack *bank, orc_counts *c)
 {
-    if (p->ww_lower == NULL) return 1;
-    double wl = p->ww_lower[(cell_of(p, P) * p->n_grp + P->g) * tb->T1
-                            + (p->n_tbin > 0 ? P->tbin : 0)];
+    if (p->ww_lower == NULL && p->ww_net == NULL) return 1;
+    double wl = p->ww_net != NULL
+                    ? net_window(p, P)
+                    : p->ww_lower[(cell_of(p, P) * p->n_grp + P->g) * tb->T1
+                                  + (p->n_tbin > 0 ? P->tbin : 0)];
     if (!(wl > 0.0)) return 1;
     double wu = p->ww_upper_ratio * wl;
     if (P->w > wu) {
@@ -549,7 +590,10 @@ static int make_tables(const orc_problem *p, tables *tb)
         !(p->weight_cutoff > 0.0 && p->cutoff_survival > p->weight_cutoff)) return -1;
     if (p->pc_target < 0) return -1;
     if (p->pc_target > 0 &&
-        (p->n_tbin < 2 || p->ww_lower != NULL || !(p->src_t1 < p->edges[1]))) return -1;
+        (p->n_tbin < 2 || p->ww_lower != NULL || p->ww_net != NULL ||
+         !(p->src_t1 < p->edges[1]))) return -1;
+    if (p->ww_net != NULL && (p->ww_net_in != 4 + p->n_grp || p->ww_net_in > 64 ||
+                              p->ww_net_h < 1)) return -1;
     for (int64_t c = 0; c < tb->n_cells; ++c)
         if (p->material[c] >= M) return -1;
     return 0;
