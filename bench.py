@@ -173,6 +173,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
+    ap.add_argument("--fom-per-event", action="store_true",
+                    help="also measure the deep box with the network evaluated per event")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the same workload in the other modes (cell-local FP32, "
                          "collision estimator, implicit capture)")
@@ -307,6 +309,8 @@ def main():
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_over_pilots(M, prec, None)
         line["fom_shallow"] = fom_over_pilots(M, prec, W.c4_shallow())
+        if args.fom_per_event:
+            line["fom_per_event"] = fom_over_pilots(M, prec, None, per_event=True)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         h, sg, dt = oracle_sample(prob, args.cpu_seconds, os.cpu_count() or 1, offset=10**12)
         line["cpu_baseline"] = {"value": h / dt, "unit": "histories/s", "cores": os.cpu_count(),
@@ -426,7 +430,8 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
 WW_SETTINGS = {"source_wl": 0.25, "upper_ratio": 4.0, "survival_ratio": 2.0}
 
 
-def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7):
+def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7,
+             per_event=False):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
     region x in [90, 100]), analog against the learned weight windows.  The
@@ -434,12 +439,15 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
     the tally of a weight-window run with the previous windows (each such
     tally is an unbiased flux estimate that reaches deeper).  T is the device time of the measured run; the
     training time is reported beside it.  seed0 seeds the pilot; the
-    weight-window runs use seed0 + 4, + 5, ...."""
+    weight-window runs use seed0 + 4, + 5, ....  per_event: the last fit's
+    network sets every window at the event instead of a baked table (the
+    refits still bake)."""
     import torch
     prob = prob if prob is not None else W.c4_deep()
     out = {"workload": prob.name, "region_cells": [list(prob.region_lo), list(prob.region_hi)]}
     dev = torch.device("cuda")
-    with M.Problem(prob, precision=prec) as P:
+    tm = M.TALLY_GLOBAL if per_event else M.TALLY_AUTO
+    with M.Problem(prob, precision=prec, tally_mode=tm) as P:
         mean = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
         rel = torch.zeros_like(mean)
         P.run_ex(1_000_000, seed0, mean=mean, relerr=rel)        # warm-up
@@ -455,7 +463,7 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         seed = seed0 + 4
         for it in range(refits + 1):
             rep = P.train_importance(mean, rel, epochs=20, batch=16384, min_ratio=1e-20,
-                                     **WW_SETTINGS)
+                                     per_event=int(per_event and it == refits), **WW_SETTINGS)
             train_ms += rep["train_ms"] + rep["bake_ms"]
             if it < refits:
                 st, _ = P.run_ex(n_ww, seed, batches=16, mean=mean, relerr=rel)
@@ -477,12 +485,12 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
     return out
 
 
-def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207)):
+def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False):
     """fom_deep for the first pilot seed in full, plus the learned FOM (and the
     ratio to analog, or its lower bound) for every seed and their medians: the
     windows depend on the pilot sample, so one seed is one draw of the whole
     pipeline."""
-    runs = [fom_deep(M, prec, prob=prob, seed0=s) for s in seeds]
+    runs = [fom_deep(M, prec, prob=prob, seed0=s, per_event=per_event) for s in seeds]
     out = runs[0]
     foms = [r["learned"]["fom"] or 0.0 for r in runs]
     key = "ratio" if "ratio" in out else "ratio_lower_bound"

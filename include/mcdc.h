@@ -337,6 +337,13 @@ typedef struct mcdc_mlp_options {
                                    I(source cells) / I -- particles split on their
                                    way to the region and are rouletted away from it;
                                    time and group folds then keep the smallest w_L */
+    int32_t per_event;          /* 0 (default): bake a table of windows; 1: no table --
+                                   every window check evaluates the trained network
+                                   at the particle (mcdc_set_network_windows with the
+                                   bake's constants), so windows vary continuously in
+                                   position and time and are resolved in time and
+                                   group (the folds above do not apply).  Needs a
+                                   forward pilot (adjoint 0) and the global tally   */
 } mcdc_mlp_options;
 
 typedef struct mcdc_mlp_report {
@@ -351,8 +358,10 @@ void mcdc_default_mlp_options(mcdc_mlp_options *opt);
 
 /* Trains the network on a pilot tally (pilot_mean required, pilot_relerr may
  * be NULL; [n_bins] doubles, host or device) and switches the problem to the
- * weight windows it predicts.  Errors: MCDC_ERR_INVALID (no scored bin, more
- * than 12 groups, bad options), MCDC_ERR_OOM, MCDC_ERR_CUDA. */
+ * weight windows it predicts (a baked table, or the network per event).
+ * Errors: MCDC_ERR_INVALID (no scored bin, more than 12 groups, bad options,
+ * per_event with an adjoint pilot or a shared tally), MCDC_ERR_OOM,
+ * MCDC_ERR_CUDA. */
 int mcdc_train_importance(struct mcdc_problem *prob, const double *pilot_mean,
                           const double *pilot_relerr, const mcdc_mlp_options *opt,
                           mcdc_mlp_report *report);
@@ -410,6 +419,25 @@ int mcdc_run_noalloc(struct mcdc_problem *prob, uint64_t n_histories, uint64_t s
  * mode's roofline.  Allocates and frees a small device buffer.  Errors:
  * MCDC_ERR_NO_DEVICE, MCDC_ERR_CUDA, MCDC_ERR_INVALID (NULL output). */
 int mcdc_measure_fp64_pipe(double *add_per_s, double *cvt_per_s);
+
+/* Per-event weight windows: instead of a table, every window check evaluates
+ * the importance network (the layout of mcdc_mlp_forward with `hidden` units
+ * per layer, 1..64; inputs 4 + G) at the particle itself.  Inputs: position
+ * scaled to [-1, 1] over each bounded mesh axis (0 on an unbounded one), time
+ * as 2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time bin j (0 in steady
+ * state), then the group one-hot -- the continuous versions of the cell and
+ * bin centres the network is trained on.  With its output y the lower bound
+ * is w_L = source_wl exp(min(0, max(y scale + shift, floor_lp) - top)); upper
+ * and survival bounds and the split cap as in mcdc_set_weight_windows.
+ * params: FP32, host or device, copied (FP64 mode evaluates in FP64 from the
+ * same values); NULL turns windows off.  Replaces any table.  Needs the
+ * global tally mode (the other kernels are built without the evaluation).
+ * Errors: MCDC_ERR_INVALID (sizes, ratios, non-finite values, population
+ * control, a shared-tally problem). */
+int mcdc_set_network_windows(struct mcdc_problem *prob, const float *params, int32_t hidden,
+                             double shift, double scale, double top, double floor_lp,
+                             double source_wl, double upper_ratio, double survival_ratio,
+                             int32_t nmax);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);

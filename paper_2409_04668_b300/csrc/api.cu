@@ -320,7 +320,7 @@ int ensure_work_slots(mcdc_problem *pr, int n) {
 }
 
 int ensure_overflow(mcdc_problem *pr) {
-  if (pr->P.ww_lower == nullptr) return MCDC_OK;
+  if (!ww_on(pr->P)) return MCDC_OK;
   const int warps = pr->block / 32;
   int cap = pr->opt.overflow_per_cta > 0 ? std::max(64, pr->opt.overflow_per_cta / warps) : 1024;
   if (pr->tally_mode == MCDC_TALLY_GLOBAL) {
@@ -373,9 +373,10 @@ std::map<std::string, TuneChoice> g_tune_cache;
 std::string tune_key(const mcdc_problem *pr) {
   const DevProblem &P = pr->P;
   char b[256];
-  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
+  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
            (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T, (long long)P.n_bins,
-           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit, P.fresh_tau);
+           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit, P.fresh_tau,
+           (int)pr->key.net);
   return b;
 }
 
@@ -434,6 +435,20 @@ int autotune(mcdc_problem *pr, const DeviceLimits &dl) {
   return MCDC_OK;
 }
 
+}  // namespace
+
+namespace {
+// Switches the problem between the tracker built with and without the
+// per-event network evaluation and redoes the launch shape for it (registers
+// and so CTAs per SM may differ).
+int set_net_kernel(mcdc_problem *pr, bool net) {
+  if (pr->key.net == net) return MCDC_OK;
+  pr->key.net = net;
+  DeviceLimits dl;
+  if (int rc = device_limits(pr->device, &dl)) return rc;
+  pr->opt.tally_mode = pr->tally_mode;
+  return choose_shape(pr, dl);
+}
 }  // namespace
 
 namespace mcdc {
@@ -753,7 +768,9 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
   if (w_lower == nullptr) {
     pr->P.ww_lower = nullptr;
     pr->P.ww_lower32 = nullptr;
-    return MCDC_OK;
+    pr->P.ww_net64 = nullptr;
+    pr->P.ww_net32 = nullptr;
+    return set_net_kernel(pr, false);
   }
   if (pr->P.pc_target > 0)
     return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
@@ -778,9 +795,69 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
   CK(cudaMemcpy(pr->ww32, h32.data(), nb * 4, cudaMemcpyHostToDevice));
   pr->P.ww_lower = pr->ww64;
   pr->P.ww_lower32 = pr->ww32;
+  pr->P.ww_net64 = nullptr;
+  pr->P.ww_net32 = nullptr;
   pr->P.ww_upper = upper_ratio;
   pr->P.ww_survival = survival_ratio;
   pr->P.ww_nmax = nmax;
+  if (int rc = set_net_kernel(pr, false)) return rc;
+  return ensure_overflow(pr);
+}
+
+int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32_t hidden,
+                              double shift, double scale, double top, double floor_lp,
+                              double source_wl, double upper_ratio, double survival_ratio,
+                              int32_t nmax) {
+  g_err.clear();
+  if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
+  if (params == nullptr) return mcdc_set_weight_windows(pr, nullptr, 0.0, 0.0, 0);
+  if (pr->P.pc_target > 0)
+    return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
+  if (hidden < 1 || hidden > 64) return fail(MCDC_ERR_INVALID, "hidden width must be 1..64");
+  if (pr->tally_mode != MCDC_TALLY_GLOBAL)
+    return fail(MCDC_ERR_INVALID, "per-event windows need the global tally (tally_mode)");
+  if (pr->P.G > 16) return fail(MCDC_ERR_INVALID, "per-event windows take at most 16 groups");  // inputs 4 + G fit the kernel's 20
+  if (!(upper_ratio > survival_ratio && survival_ratio > 1.0) || nmax < 2 || nmax > 1024)
+    return fail(MCDC_ERR_INVALID, "need 1 < survival_ratio < upper_ratio and 2 <= nmax <= 1024");
+  if (!(source_wl > 0.0) || !std::isfinite(shift) || !std::isfinite(scale) ||
+      !std::isfinite(top) || !std::isfinite(floor_lp))
+    return fail(MCDC_ERR_INVALID, "window constants must be finite (source_wl > 0)");
+  CK(cudaSetDevice(pr->device));
+  const int in = 4 + pr->P.G;
+  // W1[hidden][in], b1[hidden], W2[hidden][hidden], b2[hidden], W3[hidden], b3
+  const size_t n = (size_t)hidden * in + hidden + (size_t)hidden * hidden + 2 * (size_t)hidden + 1;
+  std::vector<float> h32(n);
+  if (is_device_ptr(params)) CK(cudaMemcpy(h32.data(), params, n * 4, cudaMemcpyDeviceToHost));
+  else std::memcpy(h32.data(), params, n * 4);
+  std::vector<double> h64(n);
+  for (size_t q = 0; q < n; ++q) {
+    if (!std::isfinite(h32[q])) return fail(MCDC_ERR_INVALID, "network parameter is not finite");
+    h64[q] = (double)h32[q];
+  }
+  if (pr->net_cap < n) {
+    int rc;
+    if ((rc = dalloc(pr, &pr->net64, n))) return rc;
+    if ((rc = dalloc(pr, &pr->net32, n))) return rc;
+    pr->net_cap = n;
+  }
+  CK(cudaMemcpy(pr->net64, h64.data(), n * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pr->net32, h32.data(), n * 4, cudaMemcpyHostToDevice));
+  DevProblem &P = pr->P;
+  P.ww_lower = nullptr;
+  P.ww_lower32 = nullptr;
+  P.ww_net64 = pr->net64;
+  P.ww_net32 = pr->net32;
+  P.ww_net_in = in;
+  P.ww_net_h = hidden;
+  P.ww_net_shift = shift;
+  P.ww_net_scale = scale;
+  P.ww_net_top = top;
+  P.ww_net_floor = floor_lp;
+  P.ww_net_wl0 = source_wl;
+  P.ww_upper = upper_ratio;
+  P.ww_survival = survival_ratio;
+  P.ww_nmax = nmax;
+  if (int rc = set_net_kernel(pr, true)) return rc;
   return ensure_overflow(pr);
 }
 
@@ -984,7 +1061,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2, pr->sum12,
                      pr->region_batch, pr->region, pr->sms));
   } else {
-    const bool spill = P.ww_lower != nullptr && pr->spill[0] != nullptr;
+    const bool spill = ww_on(P) && pr->spill[0] != nullptr;
     // weight-window runs put every batch in one launch (one tally slice per
     // batch): a batch's few histories would leave most warps idle while a
     // handful work through their split families
@@ -1098,7 +1175,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
     stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
-    if (P.ww_lower == nullptr && !P.implicit && P.pc_target == 0) {   // analog: every weight is 1
+    if (!ww_on(P) && !P.implicit && P.pc_target == 0) {   // analog: every weight is 1
       stats->w_source = (double)h.histories;
       stats->w_absorbed = (double)h.absorbed;
       stats->w_leaked = (double)h.leaked;

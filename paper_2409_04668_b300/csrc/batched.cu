@@ -118,7 +118,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
         p->dim != p0->dim)
       return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
-    if (p->P.ww_lower != nullptr || p->P.implicit || p->P.pc_target > 0)
+    if (ww_on(p->P) || p->P.implicit || p->P.pc_target > 0)
       return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
     if (p->P.estimator == MCDC_EST_COMBINED)
       return fail(MCDC_ERR_INVALID, "batched runs score one estimator (no combined estimator)");
@@ -141,6 +141,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   TrackKey key = p0->key;
   key.shared = false;
   key.multi = true;
+  key.net = false;
   Layout L{};
   for (int i = 0; i < n; ++i) {
     L.M = std::max(L.M, probs[i]->P.M);

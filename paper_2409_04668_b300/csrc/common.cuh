@@ -47,6 +47,13 @@ struct DevProblem {
   // weight windows (nullptr: analog)
   const double *ww_lower;     // [n_bins]
   const float *ww_lower32;
+  // per-event windows from the importance network instead of the table
+  // (nullptr: off): parameters, inputs (4 + G) and hidden width, and the
+  // map of its output y to w_L = wl0 exp(min(0, max(y scale + shift, floor) - top))
+  const double *ww_net64;
+  const float *ww_net32;
+  int32_t ww_net_in, ww_net_h;
+  double ww_net_shift, ww_net_scale, ww_net_top, ww_net_floor, ww_net_wl0;
   double ww_upper, ww_survival;
   int32_t ww_nmax;
   int32_t region_lo[3], region_hi[3];
@@ -58,6 +65,11 @@ struct DevProblem {
   int32_t pc_target;          // population control: particles per batch after a comb (0: off)
   int32_t fresh_tau;          // FP32 modes: 1 = sample the distance to collision every flight
 };
+
+// weight windows are on: a table or the network
+__host__ __device__ inline bool ww_on(const DevProblem &P) {
+  return P.ww_lower != nullptr || P.ww_net64 != nullptr;
+}
 
 // One particle as it moves between the tracker phases (kept in registers).
 // Q = double: x, y, z are the position and t the time.  Q = float (the

@@ -25,6 +25,7 @@ struct TrackKey {
   bool multi = false;   // batched problems (work items over several problems)
   bool shared;
   int dim;   // 1 or 3
+  bool net = false;     // per-event network windows (global tally, single problem)
 };
 
 // Launches the persistent tracker for one configuration (MA: batched mode only).

@@ -903,6 +903,8 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   if (opt) o = *opt; else mcdc_default_mlp_options(&o);
   if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0))
     return fail(MCDC_ERR_INVALID, "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0");
+  if (o.per_event && (o.adjoint || pr->tally_mode != MCDC_TALLY_GLOBAL))
+    return fail(MCDC_ERR_INVALID, "per-event windows need a forward pilot and the global tally");
   const DevProblem &P = pr->P;
   const int n_in = 4 + P.G;
   if (n_in > kIn) return fail(MCDC_ERR_INVALID, "the importance network takes at most 12 groups");
@@ -1060,6 +1062,25 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     k_pred_src_max<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx + 2);
     CKM(cudaGetLastError());
   }
+  if (o.per_event) {
+    // the network itself sets every window: the constants of the bake below
+    // (top, floor) with the trained parameters, evaluated at each event
+    unsigned long long hmx[2];
+    CKM(cudaMemcpyAsync(hmx, mx, sizeof hmx, cudaMemcpyDeviceToHost, st));
+    CKM(cudaEventRecord(e2, st));
+    CKM(cudaStreamSynchronize(st));
+    if (int rc = tc_status()) return rc;
+    double top, low;
+    std::memcpy(&top, &hmx[0], 8);
+    std::memcpy(&low, &hmx[1], 8);
+    top -= 1e4;
+    low -= 1e4;
+    const double floor_lp = std::fmax(low - 2.302585092994046,
+                                      top + std::log(o.min_ratio > 0.0 ? o.min_ratio : 1e-8));
+    if (int rc = mcdc_set_network_windows(pr, prm, kH, hmom[3], hmom[4], top, floor_lp,
+                                          o.source_wl, o.upper_ratio, o.survival_ratio, o.nmax))
+      return rc;
+  } else {
   if (!pr->ww64) {
     void *a, *b;
     CKM(cudaMalloc(&a, sizeof(double) * nb));
@@ -1093,6 +1114,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   pr->P.ww_survival = o.survival_ratio;
   pr->P.ww_nmax = o.nmax;
   if (int rc = mcdc::ensure_overflow_for(pr)) return rc;
+  }
   if (rep) {
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, e0, e1);

@@ -94,7 +94,7 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   if (global && pr->P.n_bins > kMaxBins)
     return fail(MCDC_ERR_INVALID, "tally exceeds the allocation-free limit of 131072 bins "
                                   "(global tally mode)");
-  if (pr->P.ww_lower != nullptr && pr->overflow == nullptr)
+  if (ww_on(pr->P) && pr->overflow == nullptr)
     return fail(MCDC_ERR_INVALID, "weight windows set without an overflow stack");
   cudaError_t e = cudaSetDevice(pr->device);
   if (e != cudaSuccess) return fail(MCDC_ERR_CUDA, cudaGetErrorString(e));

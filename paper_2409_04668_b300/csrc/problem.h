@@ -45,6 +45,9 @@ struct mcdc_problem {
   uint64_t rec_cap = 0;
   double *ww64 = nullptr;
   float *ww32 = nullptr;
+  double *net64 = nullptr;      // per-event windows: network parameters
+  float *net32 = nullptr;
+  size_t net_cap = 0;
   // population control: census bank (by input position), combed bank and
   // the comb's scratch
   int pc_cap = 0;                          // input positions the census bank holds

@@ -13,11 +13,13 @@ int track_regs_f64(const TrackKey &);
 int track_occupancy_f64(const TrackKey &, int, int);
 
 namespace {
-template <class PR, bool SH, int DIM, bool MU>
-void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU>; }
+template <class PR, bool SH, int DIM, bool MU, bool NET = false>
+void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU, NET>; }
 
 template <class PR>
 void *pick_prec(const TrackKey &k) {
+  if (k.net) return k.dim == 1 ? fp32_kernel<PR, false, 1, false, true>()
+                               : fp32_kernel<PR, false, 3, false, true>();
   if (k.multi) return k.dim == 1 ? fp32_kernel<PR, false, 1, true>() : fp32_kernel<PR, false, 3, true>();
   if (k.shared) return k.dim == 1 ? fp32_kernel<PR, true, 1, false>() : fp32_kernel<PR, true, 3, false>();
   return k.dim == 1 ? fp32_kernel<PR, false, 1, false>() : fp32_kernel<PR, false, 3, false>();

@@ -6,10 +6,11 @@
 
 namespace mcdc {
 namespace {
-template <bool SH, int DIM, bool MU>
-void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU>; }
+template <bool SH, int DIM, bool MU, bool NET = false>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET>; }
 
 void *pick(const TrackKey &k) {
+  if (k.net) return k.dim == 1 ? fp64_kernel<false, 1, false, true>() : fp64_kernel<false, 3, false, true>();
   if (k.multi) return k.dim == 1 ? fp64_kernel<false, 1, true>() : fp64_kernel<false, 3, true>();
   if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1, false>() : fp64_kernel<true, 3, false>();
   return k.dim == 1 ? fp64_kernel<false, 1, false>() : fp64_kernel<false, 3, false>();

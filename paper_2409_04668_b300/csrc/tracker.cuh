@@ -239,7 +239,7 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
                                        const PartOf<PR> &p, int end) {
   // analog runs carry weight 1 throughout: their weight sums are the counts
   // (filled in on the host), so only weighted runs add weights here
-  const bool weighted = P.ww_lower != nullptr || P.implicit || P.pc_target > 0;
+  const bool weighted = ww_on(P) || P.implicit || P.pc_target > 0;
   if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); if (weighted) atomicAdd(&es.w_end[1], (double)p.w); }
   else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); if (weighted) atomicAdd(&es.w_end[2], (double)p.w); }
   else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); if (weighted) atomicAdd(&es.w_end[3], (double)p.w); }
@@ -266,20 +266,82 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
 }
 
 // ---------------------------------------------------------------------------
+// Per-event windows: the importance network evaluated at the particle.
+// Inputs: position scaled to [-1, 1] over each bounded axis of the mesh,
+// time as 2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time bin j (0 in steady
+// state), the group one-hot -- the continuous versions of the cell and bin
+// centres the network is trained on.  FP64 mode evaluates in FP64 in the
+// order of the oracle's loops; the FP32 modes in FP32.  Not inlined: the
+// hidden layer lives in this call's own frame, off the tracker's registers.
+template <class PR, int DIM>
+__device__ __noinline__ typename PR::R net_window(const DevProblem &P, const PartOf<PR> &p) {
+  using R = typename PR::R;
+  double pos[3], t;
+  if constexpr (PR::kLocal) {
+    pos[0] = P.bounded[0] ? __ldg(P.faces[0] + p.i) + (double)p.x : 0.0;
+    pos[1] = (DIM == 3 && P.bounded[1]) ? __ldg(P.faces[1] + p.j) + (double)p.y : 0.0;
+    pos[2] = (DIM == 3 && P.bounded[2]) ? __ldg(P.faces[2] + p.k) + (double)p.z : 0.0;
+    t = P.T > 0 ? P.edges[p.tbin + 1] - (double)p.t : 0.0;
+  } else {
+    pos[0] = p.x; pos[1] = p.y; pos[2] = p.z; t = p.t;
+  }
+  R f[4 + 16];
+  for (int a = 0; a < 3; ++a)
+    f[a] = P.bounded[a] ? (R)(2.0 * (pos[a] - P.origin[a]) / ((double)P.n[a] * P.width[a]) - 1.0)
+                        : (R)0;
+  if (P.T > 0) {
+    const int j = p.tbin < P.T ? p.tbin : P.T - 1;
+    const double u = (t - P.edges[j]) / (P.edges[j + 1] - P.edges[j]);
+    f[3] = (R)(2.0 * ((double)j + u) / (double)P.T - 1.0);
+  } else {
+    f[3] = (R)0;
+  }
+  const int in = P.ww_net_in, H = P.ww_net_h;
+  for (int k = 4; k < in; ++k) f[k] = (k - 4 == p.g) ? (R)1 : (R)0;
+  const R *W1;
+  if constexpr (PR::kF64) W1 = P.ww_net64; else W1 = P.ww_net32;
+  const R *b1 = W1 + H * in, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H, *b3 = W3 + H;
+  R h1[64];
+  for (int j = 0; j < H; ++j) {
+    R a = b1[j];
+    for (int k = 0; k < in; ++k) a += W1[j * in + k] * f[k];
+    if constexpr (PR::kF64) h1[j] = a / (1.0 + exp(-a)); else h1[j] = __fdividef(a, 1.0f + __expf(-a));
+  }
+  R y = b3[0];
+  for (int j = 0; j < H; ++j) {
+    R a = b2[j];
+    for (int k = 0; k < H; ++k) a += W2[j * H + k] * h1[k];
+    R h2;
+    if constexpr (PR::kF64) h2 = a / (1.0 + exp(-a)); else h2 = __fdividef(a, 1.0f + __expf(-a));
+    y += W3[j] * h2;
+  }
+  double lp = (double)y * P.ww_net_scale + P.ww_net_shift;
+  if (lp < P.ww_net_floor) lp = P.ww_net_floor;
+  const double e = lp - P.ww_net_top;
+  return (R)(P.ww_net_wl0 * exp(e < 0.0 ? e : 0.0));
+}
+
+// ---------------------------------------------------------------------------
 // weight window at collisions and cell crossings.  Returns false if the
 // particle is rouletted away.  Children go to the warp's overflow stack
 // (s_novf[0]: its size) or the spill bank; s_novf[16] is the warp's
-// reservation of the run's children budget.
-template <class PR, int DIM>
+// reservation of the run's children budget.  NET: the lower bound comes from
+// the network when one is set (separate instantiations, so that the others
+// carry no call).
+template <class PR, int DIM, bool NET>
 __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> &tb,
                               const RunArgs &A, const EndSink &es, PartOf<PR> &p,
                               int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
-  if (tb.ww == nullptr) return true;
-  const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
-  const int bin = bin_index(P, cell, p.g, p.tbin);
+  if (tb.ww == nullptr && !(NET && P.ww_net64 != nullptr)) return true;
   R wl;
-  if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
+  if (NET && P.ww_net64 != nullptr) {
+    if constexpr (NET) wl = net_window<PR, DIM>(P, p);
+  } else {
+    const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
+    const int bin = bin_index(P, cell, p.g, p.tbin);
+    if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
+  }
   if (!(wl > (R)0)) return true;
   const R wu = (R)P.ww_upper * wl;
   if (p.w > wu) {
@@ -437,7 +499,7 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 // *end), 3 reached an interior census edge under population control (banked)
 enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3 };
 
-template <class PR, int DIM>
+template <class PR, int DIM, bool NET>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
                                       PartOf<PR> &p, int &bin,
@@ -613,7 +675,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if (ax == 0) p.i = nxt; else if (ax == 1) p.j = nxt; else p.k = nxt;
     p.ncross += 1;
     lc.cross += 1;
-    if (!weight_window<PR, DIM>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
+    if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
     return OUT_CONT;
   }
   return OUT_COLL;
@@ -625,7 +687,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 // capture: the weight is multiplied by sigma_s / sigma_t (the removed part is
 // returned in wabs), a weight that reaches 0 ends as absorbed, and a weight
 // below the cutoff is rouletted after the scatter (one more block).
-template <class PR, int DIM>
+template <class PR, int DIM, bool NET>
 __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typename PR::R> &tb,
                                         const RunArgs &A, const EndSink &es,
                                         PartOf<PR> &p, int &end, LocalCount &lc,
@@ -674,7 +736,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
       atomicAdd(&es.n_end[4], 1u);
     }
   }
-  if (!weight_window<PR, DIM>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
+  if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
   return true;
 }
 
@@ -773,7 +835,7 @@ struct MultiArgs {
   unsigned long long *counter;
 };
 
-template <class PR, bool SHARED, int DIM, bool MULTI>
+template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false>
 __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
                                                const MultiArgs MA) {
   using R = typename PR::R;
@@ -948,7 +1010,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           double wabs = 0.0;
           if (mine) {
             int end = END_NONE;
-            alive = collide<PR, DIM>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
+            alive = collide<PR, DIM, NET>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
           if (P.estimator != 0) {
@@ -1057,7 +1119,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
             if (use_slot) q.slot = (uint32_t)(h_first + (lane - n_o));   // history's position in the run
-            if (P.ww_lower != nullptr || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
+            if (ww_on(P) || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
@@ -1148,7 +1210,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         R score = (R)0;
         const bool flew = has;
         if (has) {
-          outcome = flight<PR, DIM>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
+          outcome = flight<PR, DIM, NET>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         if (step_tally)

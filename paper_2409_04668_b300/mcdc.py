@@ -105,7 +105,7 @@ class mcdc_mlp_options(C.Structure):
                 ("seed", C.c_uint64), ("source_wl", C.c_double), ("upper_ratio", C.c_double),
                 ("survival_ratio", C.c_double), ("nmax", C.c_int32), ("min_ratio", C.c_double),
                 ("time_resolved", C.c_int32), ("group_resolved", C.c_int32),
-                ("adjoint", C.c_int32)]
+                ("adjoint", C.c_int32), ("per_event", C.c_int32)]
 
 
 class mcdc_mlp_report(C.Structure):
@@ -139,6 +139,9 @@ SIGNATURES = {
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcdc_measure_fp64_pipe": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mcdc_set_network_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                           C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, C.c_int32]),
     "mcdc_last_error": (C.c_char_p, []),
 }
 
@@ -172,6 +175,7 @@ mcdc_mlp_forward = _lib.mcdc_mlp_forward
 mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
 mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
 mcdc_measure_fp64_pipe = _lib.mcdc_measure_fp64_pipe
+mcdc_set_network_windows = _lib.mcdc_set_network_windows
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -317,6 +321,15 @@ class Problem:
         returns once the work is queued on `stream`."""
         check(mcdc_run_noalloc(self.handle, int(n), int(seed), int(offset), int(batches),
                                _ptr(sum1), _ptr(sum2), _ptr(mean), _ptr(relerr), stream))
+
+    def set_network_windows(self, params, hidden, shift, scale, top, floor, wl0,
+                            upper_ratio=5.0, survival_ratio=2.5, nmax=16):
+        """Per-event windows from the network (see mcdc_set_network_windows);
+        params None turns windows off."""
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        check(mcdc_set_network_windows(self.handle, _ptr(p), int(hidden), float(shift),
+                                       float(scale), float(top), float(floor), float(wl0),
+                                       float(upper_ratio), float(survival_ratio), int(nmax)))
 
     def train_importance(self, pilot_mean, pilot_relerr=None, **opts):
         """Fits the importance network to a pilot tally and switches this
