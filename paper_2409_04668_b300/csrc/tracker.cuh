@@ -704,7 +704,15 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
     cscore = p.w / tb.sigma_t[mg];
   }
   const U4 r1 = draw(p, p.ctr, A.rk);
-  const U4 r2 = draw(p, p.ctr, A.rk);
+  // FP32 modes with the optical depth carried use one 24-bit number per
+  // choice: absorption r1.a, group r1.c, cosine and optical depth from the
+  // direction block's a and b, azimuth from its c.  When the direction needs
+  // no azimuth (1-D) or the group needs no number (one group), the first
+  // block's b and d serve as the cosine and the optical depth (and its c as
+  // the azimuth), and the collision draws one block instead of two.
+  bool one_block = false;
+  if constexpr (!PR::kF64) one_block = !P.fresh_tau && (DIM == 1 || P.G == 1);
+  const U4 r2 = one_block ? U4{r1.b, r1.d, r1.c, r1.d} : draw(p, p.ctr, A.rk);
   const R ratio = tb.scat[mg];
   R xi1, xi2;
   if constexpr (PR::kF64) { xi1 = u01_f64(r1.a, r1.b); xi2 = u01_f64(r1.c, r1.d); }
