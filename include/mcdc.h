@@ -420,6 +420,16 @@ int mcdc_run_noalloc(struct mcdc_problem *prob, uint64_t n_histories, uint64_t s
  * MCDC_ERR_NO_DEVICE, MCDC_ERR_CUDA, MCDC_ERR_INVALID (NULL output). */
 int mcdc_measure_fp64_pipe(double *add_per_s, double *cvt_per_s);
 
+/* The generator of every random number of a run: out[4 i .. 4 i + 3] =
+ * Philox4x32-10 (Salmon et al., SC'11; 10 rounds, the published multipliers
+ * and Weyl constants) of the counter ctr[4 i .. 4 i + 3] under the key (seed
+ * low 32 bits, seed high 32 bits), computed on the current device by the
+ * tracker's own routine.  A transport draw uses the counter (event counter,
+ * particle serial, history id low, history id high).  ctr and out: n x 4
+ * words, host or device, caller-owned.  Errors: MCDC_ERR_INVALID (n < 0 or
+ * NULL buffers), MCDC_ERR_NO_DEVICE, MCDC_ERR_OOM, MCDC_ERR_CUDA. */
+int mcdc_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
+
 /* Per-event weight windows: instead of a table, every window check evaluates
  * the importance network (the layout of mcdc_mlp_forward with `hidden` units
  * per layer, 1..64; inputs 4 + G) at the particle itself.  Inputs: position

@@ -142,6 +142,7 @@ SIGNATURES = {
     "mcdc_set_network_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
                                            C.c_double, C.c_double, C.c_double, C.c_double,
                                            C.c_double, C.c_double, C.c_int32]),
+    "mcdc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
 }
 
@@ -176,6 +177,7 @@ mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
 mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
 mcdc_measure_fp64_pipe = _lib.mcdc_measure_fp64_pipe
 mcdc_set_network_windows = _lib.mcdc_set_network_windows
+mcdc_philox = _lib.mcdc_philox
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -402,6 +404,15 @@ def mlp_forward(params, X):
     X = np.ascontiguousarray(X, dtype=np.float32)
     out = np.zeros(X.shape[0], dtype=np.float32)
     check(mcdc_mlp_forward(_ptr(p), X.shape[1], _ptr(X), X.shape[0], _ptr(out)))
+    return out
+
+
+def philox(seed, ctr):
+    """Philox4x32-10 blocks of the counters ctr ([n, 4] uint32) under seed, on
+    the GPU with the tracker's routine; returns [n, 4] uint32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    check(mcdc_philox(int(seed), _ptr(c), c.shape[0], _ptr(out)))
     return out
 
 

@@ -142,3 +142,14 @@ def test_valid_problem_without_gpu_reports_no_device(lib):
         pytest.skip("a GPU is present")
     code, msg = _create(lib, W.c1_slab())
     assert code == lib.MCDC_ERR_NO_DEVICE, msg
+
+
+def test_philox_arguments_checked_on_host(lib):
+    assert lib.mcdc_philox(1, None, -1, None) == lib.MCDC_ERR_INVALID
+    assert lib.mcdc_philox(1, None, 4, None) == lib.MCDC_ERR_INVALID
+    assert lib.mcdc_philox(1, None, 0, None) == lib.MCDC_OK
+    import torch
+    if not torch.cuda.is_available():
+        c = np.zeros((2, 4), np.uint32)
+        o = np.zeros_like(c)
+        assert lib.mcdc_philox(1, c.ctypes.data, 2, o.ctypes.data) == lib.MCDC_ERR_NO_DEVICE
