@@ -503,6 +503,14 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False):
     return out
 
 
+# DRAM bytes (read + write) per tracker launch from one ncu capture of the
+# bench's own command (profiles/k_track_two_region_slab.md, "DRAM traffic"),
+# keyed by (workload, precision, tally mode); re-measure when the kernel
+# changes.  The shared tally keeps the traffic to the tables and the fold's
+# atomics, which stay in L2.
+MEASURED_TRAFFIC = {("c2_slab_20cm_2region_td", "fp32", 1): 259840}
+
+
 def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     """Roofline of the tracker for the binding unit of its precision mode.
 
@@ -528,7 +536,9 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
         peak = 0.625
         ach = seg_rate * ops / 1e12
         out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe ops/s",
-               "frac": ach / peak, "traffic": None, "ops_per_segment": ops,
+               "frac": ach / peak,
+               "traffic": MEASURED_TRAFFIC.get((prob.name, prec_name, tally_mode)),
+               "traffic_unit": "DRAM bytes per launch (ncu)", "ops_per_segment": ops,
                "peak_kind": "nominal B300 FP64 1.25 TFLOP/s = 0.625 T pipe ops/s (recipe)"}
         if measured_fp64 is not None:
             # half of a flight's FP64-pipe operations are conversions, half adds
