@@ -384,7 +384,8 @@ def run_batched_bench(args):
 def variants(M, prob, n_hist, args, mean, rel, stream):
     """The headline workload in the other modes of the tracker: device-timed
     histories/s and the region scalar's figure of merit 1/(relerr^2 T) for
-    the cell-local FP32 mode and, in the headline precision, for the
+    the cell-local FP32 mode, the FP64 mode (the oracle's arithmetic, event
+    for event) and, in the headline precision, for the
     collision estimator, for the combined track-length/collision estimator
     (both tallies, their minimum-variance combination), for implicit capture
     (weight cutoff 0.25, survival weight 0.5) and for population control (32
@@ -393,6 +394,7 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
     modes = {"track_analog": {"precision": prec},
              "fp32_local": {"precision": M.PREC_FP32_LOCAL},
+             "fp64": {"precision": M.PREC_FP64},
              "collision_estimator": {"precision": prec, "estimator": M.EST_COLLISION},
              "combined_estimator": {"precision": prec, "estimator": M.EST_COMBINED},
              "implicit_capture": {"precision": prec, "implicit": (0.25, 0.5)},
