@@ -842,6 +842,12 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   }
   CK(cudaMemcpy(pr->net64, h64.data(), n * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pr->net32, h32.data(), n * 4, cudaMemcpyHostToDevice));
+  // the network kernel first: if its launch shape fails, nothing changes
+  if (int rc = set_net_kernel(pr, true)) {
+    const std::string msg = g_err;
+    set_net_kernel(pr, false);
+    return fail(rc, msg);
+  }
   DevProblem &P = pr->P;
   P.ww_lower = nullptr;
   P.ww_lower32 = nullptr;
@@ -857,7 +863,6 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   P.ww_upper = upper_ratio;
   P.ww_survival = survival_ratio;
   P.ww_nmax = nmax;
-  if (int rc = set_net_kernel(pr, true)) return rc;
   return ensure_overflow(pr);
 }
 
