@@ -95,3 +95,31 @@ def test_device_buffers_and_refusals(mcdc):
     with pytest.raises(mcdc.MCDCError):
         mcdc.check(mcdc.mcdc_philox(5, None, 4, None))
     assert mcdc.mcdc_philox(5, None, 0, None) == mcdc.MCDC_OK
+
+
+def test_uniformity_of_1e8_draws(mcdc):
+    """Chi-square of 1.3e8 words (2^25 blocks with the transport's counter
+    layout: event counter 0..7, serial 0, history ids 0..2^22 - 1) over 1024
+    equal cells of the top 10 bits, and of consecutive word pairs over 32 x 32
+    cells: both must look uniform (p > 1e-4 against the chi-square law)."""
+    from scipy import stats
+    seed = 20240904
+    n_hist = 1 << 22
+    cells = np.zeros(1024, np.int64)
+    pairs = np.zeros(1024, np.int64)
+    words = 0
+    for c in range(8):
+        ctr = np.zeros((n_hist, 4), np.uint32)
+        ctr[:, 0] = c
+        ctr[:, 2] = np.arange(n_hist, dtype=np.uint32)
+        out = mcdc.philox(seed, ctr)
+        w = out.reshape(-1)
+        cells += np.bincount(w >> 22, minlength=1024)
+        pairs += np.bincount(((w[0::2] >> 27) << 5) | (w[1::2] >> 27), minlength=1024)
+        words += w.size
+    for name, h in (("cells", cells), ("pairs", pairs)):
+        e = h.sum() / h.size
+        chi2 = float(((h - e) ** 2 / e).sum())
+        p = float(stats.chi2.sf(chi2, h.size - 1))
+        print(name, words, "chi2", chi2, "p", p)
+        assert 1e-4 < p, (name, chi2, p)
