@@ -236,6 +236,26 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        # ---- end to end through the public API with host buffers: create
+        # (uploads the tables), run with host outputs (D2H), destroy.  Inside
+        # the sampled region: stopping nvidia-smi leaves the driver slow for a
+        # while (creates 0.05 -> 0.3 ms, runs +0.25 ms measured), which is not
+        # the library's cost
+        nb = P.n_bins
+        h_mean = np.zeros(nb)
+        h_rel = np.zeros(nb)
+        h2d = int(prob.material.nbytes + 8 * (prob.sigma_t.size * 2 + prob.transfer.size +
+                                              prob.speed.size + prob.src_pdf.size +
+                                              (0 if prob.edges is None else prob.edges.size)))
+        e2e_steps = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for s in range(e2e_steps):
+            with M.Problem(prob, precision=prec, block_size=args.block,
+                           pc_target=args.pc_target) as Q:
+                Q.run_ex(n_hist, seed=1, offset=history_offset(rank, 500 + s, n_hist),
+                         batches=args.batches, mean=h_mean, relerr=h_rel, want_stats=False)
+        te = time.perf_counter() - te0
     def reduce_max(x):
         t = torch.tensor([x], dtype=torch.float64, device=dev)
         if world > 1:
@@ -247,22 +267,6 @@ def main():
     ms_step = region_ms / args.steps
     k_ms = float(np.mean(kernel_ms))
 
-    # ---- end to end through the public API with host buffers: create
-    # (uploads the tables), run with host outputs (D2H), destroy
-    nb = P.n_bins
-    h_mean = np.zeros(nb)
-    h_rel = np.zeros(nb)
-    h2d = int(prob.material.nbytes + 8 * (prob.sigma_t.size * 2 + prob.transfer.size +
-                                          prob.speed.size + prob.src_pdf.size +
-                                          (0 if prob.edges is None else prob.edges.size)))
-    e2e_steps = max(1, min(3, args.steps))
-    torch.cuda.synchronize()
-    te0 = time.perf_counter()
-    for s in range(e2e_steps):
-        with M.Problem(prob, precision=prec, block_size=args.block, pc_target=args.pc_target) as Q:
-            Q.run_ex(n_hist, seed=1, offset=history_offset(rank, 500 + s, n_hist), batches=args.batches,
-                     mean=h_mean, relerr=h_rel, want_stats=False)
-    te = time.perf_counter() - te0
     e2e_val = n_hist * e2e_steps * world / te
 
     pk = peaks()

@@ -61,16 +61,67 @@ struct DevBuf {
 
 namespace {
 
+// Problems take their device memory from one stream-ordered pool per device
+// that keeps up to 1 GiB of freed memory mapped, so a loop that creates,
+// runs and destroys problems (a serving loop) reuses it instead of paying
+// the driver's allocation and page mapping on every create and first run.
+// The pool's own non-blocking stream orders allocations and frees; each
+// allocation is complete (synchronised) before its pointer is handed out,
+// and a problem's memory is returned only after the device is idle.  Where
+// pools are unavailable, plain cudaMalloc is used.
+struct DevPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  bool ok = false;
+};
+std::mutex g_pool_mu;
+std::map<int, DevPool> g_pools;
+
+DevPool device_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  DevPool d;
+  int supported = 0;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess &&
+      supported && cudaMemPoolCreate(&d.pool, &props) == cudaSuccess) {
+    uint64_t keep = 1ull << 30;
+    if (cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&d.stream, cudaStreamNonBlocking) == cudaSuccess) {
+      d.ok = true;
+    } else {
+      cudaMemPoolDestroy(d.pool);
+      d.pool = nullptr;
+    }
+  }
+  cudaGetLastError();
+  g_pools[dev] = d;
+  return d;
+}
+
 template <class T>
 int dalloc(mcdc_problem *pr, T **out, size_t count) {
   void *p = nullptr;
   const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-  cudaError_t e = cudaMalloc(&p, bytes);
+  const DevPool d = device_pool(pr->device);
+  cudaError_t e;
+  if (d.ok) {
+    e = cudaMallocFromPoolAsync(&p, bytes, d.pool, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+  } else {
+    e = cudaMalloc(&p, bytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(MCDC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return fail(MCDC_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   }
-  pr->allocs.push_back(p);
+  (d.ok ? pr->pool_allocs : pr->allocs).push_back(p);
   *out = (T *)p;
   return MCDC_OK;
 }
@@ -110,7 +161,8 @@ struct Arena {
 
 // Pinned host words a run reads back (statistics, error flags, a count),
 // from a process-wide pool: pinned allocation costs far more than a run's
-// setup, so blocks are reused across problems and kept until exit.
+// setup, so blocks are allocated 16 at a time, reused across problems and
+// kept until exit.
 struct PinnedBlock {
   Stats stats;
   int32_t error[4];
@@ -128,12 +180,16 @@ PinnedBlock *pinned_get() {
       return b;
     }
   }
+  constexpr int kSlab = 16;
   void *p = nullptr;
-  if (cudaMallocHost(&p, sizeof(PinnedBlock)) != cudaSuccess) {
+  if (cudaMallocHost(&p, kSlab * sizeof(PinnedBlock)) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return static_cast<PinnedBlock *>(p);
+  PinnedBlock *slab = static_cast<PinnedBlock *>(p);
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  for (int q = kSlab - 1; q >= 1; --q) g_pin_free.push_back(slab + q);
+  return slab;
 }
 
 void pinned_put(PinnedBlock *b) {
@@ -147,6 +203,15 @@ void release(mcdc_problem *pr) {
   cudaSetDevice(pr->device);
   for (void *p : pr->allocs) cudaFree(p);
   pr->allocs.clear();
+  if (!pr->pool_allocs.empty()) {
+    // no kernel of this problem may still use the memory (cudaFree above
+    // waits for the device the same way)
+    cudaDeviceSynchronize();
+    const DevPool d = device_pool(pr->device);
+    for (void *p : pr->pool_allocs) cudaFreeAsync(p, d.stream);
+    pr->pool_allocs.clear();
+  }
+  cudaGetLastError();
   if (pr->ev0) cudaEventDestroy(pr->ev0);
   if (pr->ev1) cudaEventDestroy(pr->ev1);
   if (pr->ev2) cudaEventDestroy(pr->ev2);

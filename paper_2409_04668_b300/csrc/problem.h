@@ -25,7 +25,8 @@ struct mcdc_problem {
   int batch_per_cta = 2;      // shared tally: default batches = grid x this
   int overflow_cap = 0;
   // device memory
-  std::vector<void *> allocs;
+  std::vector<void *> allocs;        // cudaMalloc'ed, freed with cudaFree
+  std::vector<void *> pool_allocs;   // from the device's memory pool (dalloc)
   double *sum1 = nullptr, *sum2 = nullptr, *tally = nullptr, *region = nullptr,
          *region_batch = nullptr, *mean_tmp = nullptr, *rel_tmp = nullptr;
   double *sum12 = nullptr;      // combined estimator: [n_bins]
