@@ -175,7 +175,8 @@ typedef struct mcdc_options {
                                    numbers as its FP64 twin (paired precision
                                    studies).  FP64 mode always samples afresh.   */
     int64_t max_children;       /* weight windows: split children one run may make
-                                   (0: 2^27; negative: no limit).  A split past the
+                                   (0: 4096 per history, at least 2^27; negative:
+                                   no limit).  A split past the
                                    budget makes no child and the parent keeps its
                                    weight (unbiased, counted in splits_dropped):
                                    windows that would split without end cost a

@@ -1012,8 +1012,12 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.tally = pr->tally;
   if (pr->opt.max_children >= 0) {
     A.children_made = pr->children;
-    A.children_budget = pr->opt.max_children > 0 ? (unsigned long long)pr->opt.max_children
-                                                 : (1ull << 27);
+    // default: 4096 children per history, at least 2^27 -- 8x what learned
+    // windows on a 30-mean-free-path absorber make, so only a runaway map
+    // reaches it, and the bound grows with the run
+    A.children_budget = pr->opt.max_children > 0
+                            ? (unsigned long long)pr->opt.max_children
+                            : std::max<unsigned long long>(1ull << 27, 4096ull * a->n_histories);
   }
   A.batch_q = a->n_histories / (uint64_t)B;
   A.batch_r = a->n_histories % (uint64_t)B;

@@ -217,7 +217,7 @@ class Problem:
         carries the optical depth across surface and census events, 1 samples
         the distance to collision every flight (the FP64 twin's random
         numbers); max_children: weight windows, split children one run may
-        make (0: 2^27, negative: no limit)."""
+        make (0: 4096 per history, at least 2^27; negative: no limit)."""
         self.desc = prob
         keep = []
 
