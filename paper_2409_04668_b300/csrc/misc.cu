@@ -19,10 +19,15 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
   const long long per_cell = (long long)P.G * P.T1;
   const long long n = P.n_bins;
   const bool comb = P.estimator == 2;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const double v = tally[q];
-    const double vc = comb ? tally[n + q] : 0.0;
+  // the region test needs the bin's cell: no division when the region is the
+  // whole mesh, 32-bit divisions when the bins fit (64-bit integer division
+  // is a long software sequence and made the fold ALU-bound)
+  const bool whole = P.region_lo[0] == 0 && P.region_lo[1] == 0 && P.region_lo[2] == 0 &&
+                     P.region_hi[0] >= P.n[0] && P.region_hi[1] >= P.n[1] &&
+                     P.region_hi[2] >= P.n[2];
+  const bool narrow = n < (1ll << 31);
+  // one bin: fold its batch value (and the collision half's) if it scored
+  auto fold_one = [&](long long q, double v, double vc) {
     if (v != 0.0 || vc != 0.0) {
       sum1[q] += v;
       sum2[q] += v * v;
@@ -33,17 +38,33 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
         sum12[q] += v * vc;
         tally[n + q] = 0.0;
       }
-      const long long cell = q / per_cell;
-      const int ci = (int)(cell % P.n[0]);
-      const int cj = (int)((cell / P.n[0]) % P.n[1]);
-      const int ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
-      if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-          cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2]) {
+      bool in = whole;
+      if (!in) {
+        int ci, cj, ck;
+        if (narrow) {
+          const uint32_t cell = (uint32_t)q / (uint32_t)per_cell;
+          const uint32_t row = cell / (uint32_t)P.n[0];
+          ci = (int)(cell - row * (uint32_t)P.n[0]);
+          ck = (int)(row / (uint32_t)P.n[1]);
+          cj = (int)(row - (uint32_t)ck * (uint32_t)P.n[1]);
+        } else {
+          const long long cell = q / per_cell;
+          ci = (int)(cell % P.n[0]);
+          cj = (int)((cell / P.n[0]) % P.n[1]);
+          ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
+        }
+        in = ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
+             cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2];
+      }
+      if (in) {
         rs += v;
         rc += vc;
       }
     }
-  }
+  };
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    fold_one(q, tally[q], comb ? tally[n + q] : 0.0);
   for (int o = 16; o > 0; o >>= 1) {
     rs += __shfl_xor_sync(0xffffffffu, rs, o);
     rc += __shfl_xor_sync(0xffffffffu, rc, o);
