@@ -242,8 +242,11 @@ def main():
         # while (creates 0.05 -> 0.3 ms, runs +0.25 ms measured), which is not
         # the library's cost
         nb = P.n_bins
-        h_mean = np.zeros(nb)
-        h_rel = np.zeros(nb)
+        # pinned host buffers for the read-back (the channel's 3e7-bin mean
+        # and error are 484 MB: an end-to-end step took 175 ms into pageable
+        # buffers and 96 ms into pinned ones, against 79 ms on the device)
+        h_mean = torch.zeros(nb, dtype=torch.float64).pin_memory()
+        h_rel = torch.zeros(nb, dtype=torch.float64).pin_memory()
         h2d = int(prob.material.nbytes + 8 * (prob.sigma_t.size * 2 + prob.transfer.size +
                                               prob.speed.size + prob.src_pdf.size +
                                               (0 if prob.edges is None else prob.edges.size)))

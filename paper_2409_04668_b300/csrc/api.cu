@@ -62,7 +62,8 @@ struct DevBuf {
 namespace {
 
 // Problems take their device memory from one stream-ordered pool per device
-// that keeps up to 1 GiB of freed memory mapped, so a loop that creates,
+// that keeps up to 16 GiB of freed memory mapped (a global-tally problem's
+// batch slices alone can take 8 GiB), so a loop that creates,
 // runs and destroys problems (a serving loop) reuses it instead of paying
 // the driver's allocation and page mapping on every create and first run.
 // The pool's own non-blocking stream orders allocations and frees; each
@@ -91,7 +92,7 @@ DevPool device_pool(int dev) {
   props.location.id = dev;
   if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess &&
       supported && cudaMemPoolCreate(&d.pool, &props) == cudaSuccess) {
-    uint64_t keep = 1ull << 30;
+    uint64_t keep = 16ull << 30;
     if (cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess &&
         cudaStreamCreateWithFlags(&d.stream, cudaStreamNonBlocking) == cudaSuccess) {
       d.ok = true;
@@ -1136,10 +1137,12 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
                      pr->region_batch, pr->region, pr->sms));
   } else {
     const bool spill = ww_on(P) && pr->spill[0] != nullptr;
-    // weight-window runs put every batch in one launch (one tally slice per
-    // batch): a batch's few histories would leave most warps idle while a
-    // handful work through their split families
-    const bool merged = spill && (double)B * (double)nt * 8.0 <= 8.0 * 1073741824.0;
+    // every batch in one launch, one tally slice per batch, when the slices
+    // fit in 8 GiB: weight-window runs would otherwise leave most warps idle
+    // while a handful work through a batch's split families, and analog runs
+    // pay a launch tail per batch (one launch: +5 % on the 60^3 channel,
+    // +9 % on the deep box); otherwise one launch and one fold per batch
+    const bool merged = (double)B * (double)nt * 8.0 <= 8.0 * 1073741824.0;
     if (merged)
       if (int rc = ensure_slices(pr, B)) return rc;
     for (int b = 0; b < (merged ? 1 : B); ++b) {
