@@ -334,10 +334,27 @@ int ensure_slices(mcdc_problem *pr, int B) {
   if (pr->pc_tally_bins >= bins) return MCDC_OK;
   int rc;
   if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
-  if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess)
+  if ((rc = dalloc(pr, &pr->slice_rb, (size_t)(2 * B)))) return rc;
+  if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess ||
+      cudaMemset(pr->slice_rb, 0, sizeof(double) * (size_t)(2 * B)) != cudaSuccess)
     return fail(MCDC_ERR_CUDA, "cudaMemset of the tally slices failed");
   pr->pc_tally_bins = bins;
   return MCDC_OK;
+}
+
+// Folds the B tally slices of a one-launch run: one pass over the bins when
+// the per-batch region partials fit a block's shared memory, else slice by
+// slice.
+cudaError_t fold_slices(mcdc_problem *pr, cudaStream_t s, const DevProblem &P, size_t nt, int B) {
+  if (B <= 2048)
+    return launch_fold_slices(s, P, pr->pc_tally, (long long)nt, B, pr->sum1, pr->sum2, pr->sum12,
+                              pr->slice_rb, pr->region, pr->sms);
+  for (int b = 0; b < B; ++b) {
+    cudaError_t e = launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2,
+                                pr->sum12, pr->region_batch, pr->region, pr->sms);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Population control buffers: a census bank of cap particles, a combed
@@ -1132,9 +1149,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       A.spill_cap = (unsigned long long)pr->pc_combed_cap;
       n_in = (long long)B * M;        // the next input: one chunk of M per combed batch
     }
-    for (int b = 0; b < B; ++b)
-      CK(launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2, pr->sum12,
-                     pr->region_batch, pr->region, pr->sms));
+    CK(fold_slices(pr, s, P, nt, B));
   } else {
     const bool spill = ww_on(P) && pr->spill[0] != nullptr;
     // every batch in one launch, one tally slice per batch, when the slices
@@ -1181,9 +1196,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
         CK(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, P, A, pr->L));
       }
       if (merged) {
-        for (int q = 0; q < B; ++q)
-          CK(launch_fold(s, P, pr->pc_tally + (size_t)q * nt, pr->sum1, pr->sum2, pr->sum12,
-                         pr->region_batch, pr->region, pr->sms));
+        CK(fold_slices(pr, s, P, nt, B));
       } else {
         CK(launch_fold(s, P, pr->tally, pr->sum1, pr->sum2, pr->sum12, pr->region_batch,
                        pr->region, pr->sms));

@@ -4,6 +4,36 @@
 
 namespace mcdc {
 
+// The cell box of the scalar region, tested per bin without 64-bit division.
+struct RegionTest {
+  bool whole, narrow;
+  long long per_cell;
+  __device__ explicit RegionTest(const DevProblem &P) {
+    whole = P.region_lo[0] == 0 && P.region_lo[1] == 0 && P.region_lo[2] == 0 &&
+            P.region_hi[0] >= P.n[0] && P.region_hi[1] >= P.n[1] && P.region_hi[2] >= P.n[2];
+    narrow = P.n_bins < (1ll << 31);
+    per_cell = (long long)P.G * P.T1;
+  }
+  __device__ bool operator()(const DevProblem &P, long long q) const {
+    if (whole) return true;
+    int ci, cj, ck;
+    if (narrow) {
+      const uint32_t cell = (uint32_t)q / (uint32_t)per_cell;
+      const uint32_t row = cell / (uint32_t)P.n[0];
+      ci = (int)(cell - row * (uint32_t)P.n[0]);
+      ck = (int)(row / (uint32_t)P.n[1]);
+      cj = (int)(row - (uint32_t)ck * (uint32_t)P.n[1]);
+    } else {
+      const long long cell = q / per_cell;
+      ci = (int)(cell % P.n[0]);
+      cj = (int)((cell / P.n[0]) % P.n[1]);
+      ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
+    }
+    return ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
+           cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2];
+  }
+};
+
 // Global-tally mode, after each batch: sum1 += x, sum2 += x*x, x = 0 for
 // every bin, plus the batch's region sum.  Reads 8 B per bin and
 // read-modify-writes 32 B per bin that scored.  Combined estimator: the
@@ -16,18 +46,13 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
                                               double *__restrict__ region_batch) {
   __shared__ double red[32];
   double rs = 0.0, rc = 0.0;
-  const long long per_cell = (long long)P.G * P.T1;
   const long long n = P.n_bins;
   const bool comb = P.estimator == 2;
-  // the region test needs the bin's cell: no division when the region is the
-  // whole mesh, 32-bit divisions when the bins fit (64-bit integer division
-  // is a long software sequence and made the fold ALU-bound)
-  const bool whole = P.region_lo[0] == 0 && P.region_lo[1] == 0 && P.region_lo[2] == 0 &&
-                     P.region_hi[0] >= P.n[0] && P.region_hi[1] >= P.n[1] &&
-                     P.region_hi[2] >= P.n[2];
-  const bool narrow = n < (1ll << 31);
-  // one bin: fold its batch value (and the collision half's) if it scored
-  auto fold_one = [&](long long q, double v, double vc) {
+  const RegionTest region(P);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double v = tally[q];
+    const double vc = comb ? tally[n + q] : 0.0;
     if (v != 0.0 || vc != 0.0) {
       sum1[q] += v;
       sum2[q] += v * v;
@@ -38,33 +63,12 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
         sum12[q] += v * vc;
         tally[n + q] = 0.0;
       }
-      bool in = whole;
-      if (!in) {
-        int ci, cj, ck;
-        if (narrow) {
-          const uint32_t cell = (uint32_t)q / (uint32_t)per_cell;
-          const uint32_t row = cell / (uint32_t)P.n[0];
-          ci = (int)(cell - row * (uint32_t)P.n[0]);
-          ck = (int)(row / (uint32_t)P.n[1]);
-          cj = (int)(row - (uint32_t)ck * (uint32_t)P.n[1]);
-        } else {
-          const long long cell = q / per_cell;
-          ci = (int)(cell % P.n[0]);
-          cj = (int)((cell / P.n[0]) % P.n[1]);
-          ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
-        }
-        in = ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-             cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2];
-      }
-      if (in) {
+      if (region(P, q)) {
         rs += v;
         rc += vc;
       }
     }
-  };
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x)
-    fold_one(q, tally[q], comb ? tally[n + q] : 0.0);
+  }
   for (int o = 16; o > 0; o >>= 1) {
     rs += __shfl_xor_sync(0xffffffffu, rs, o);
     rc += __shfl_xor_sync(0xffffffffu, rc, o);
@@ -77,6 +81,81 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
     for (int w = 0; w < nw; ++w) { t += red[w]; tc += red[nw + w]; }
     if (t != 0.0) atomicAdd(&region_batch[0], t);
     if (tc != 0.0) atomicAdd(&region_batch[1], tc);
+  }
+}
+
+// One-launch runs: every slice folded in one pass over the bins.  Reads each
+// slice once and writes zeros back, and read-modify-writes sum1 and sum2 once
+// per bin instead of once per batch.
+__global__ void __launch_bounds__(256) k_fold_slices(const DevProblem P, double *__restrict__ tally,
+                                                     long long nt, int B,
+                                                     double *__restrict__ sum1,
+                                                     double *__restrict__ sum2,
+                                                     double *__restrict__ sum12,
+                                                     double *__restrict__ rb) {
+  extern __shared__ double srb[];          // [2 B] this block's region partials
+  for (int i = threadIdx.x; i < 2 * B; i += blockDim.x) srb[i] = 0.0;
+  __syncthreads();
+  const long long n = P.n_bins;
+  const bool comb = P.estimator == 2;
+  const RegionTest region(P);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    double s1 = 0.0, s2 = 0.0, c1 = 0.0, c2 = 0.0, x12 = 0.0;
+    bool any = false;
+    int in = -1;                           // region test, taken at the first score
+    for (int b = 0; b < B; ++b) {
+      double *slice = tally + (long long)b * nt;
+      const double v = slice[q];
+      const double vc = comb ? slice[n + q] : 0.0;
+      if (v != 0.0 || vc != 0.0) {
+        s1 += v;
+        s2 += v * v;
+        slice[q] = 0.0;
+        if (comb) {
+          c1 += vc;
+          c2 += vc * vc;
+          x12 += v * vc;
+          slice[n + q] = 0.0;
+        }
+        any = true;
+        if (in < 0) in = region(P, q) ? 1 : 0;
+        if (in) {
+          atomicAdd(&srb[b], v);
+          if (comb) atomicAdd(&srb[B + b], vc);
+        }
+      }
+    }
+    if (any) {
+      sum1[q] += s1;
+      sum2[q] += s2;
+      if (comb) {
+        sum1[n + q] += c1;
+        sum2[n + q] += c2;
+        sum12[q] += x12;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * B; i += blockDim.x)
+    if (srb[i] != 0.0) atomicAdd(&rb[i], srb[i]);
+}
+
+// region[0..4] from the B per-batch region sums, batch by batch (the order of
+// B k_region_fold calls); rb is zeroed for the next run
+__global__ void k_region_slices(double *rb, int B, double *region, bool comb) {
+  for (int b = 0; b < B; ++b) {
+    const double x = rb[b];
+    region[0] += x;
+    region[1] += x * x;
+    rb[b] = 0.0;
+    if (comb) {
+      const double c = rb[B + b];
+      region[2] += c;
+      region[3] += c * c;
+      region[4] += x * c;
+      rb[B + b] = 0.0;
+    }
   }
 }
 
@@ -173,6 +252,16 @@ cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, doub
   k_fold<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(P, tally, sum1, sum2, sum12,
                                                              region_batch);
   k_region_fold<<<1, 1, 0, s>>>(region_batch, region, P.estimator == 2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, double *tally, long long nt,
+                               int B, double *sum1, double *sum2, double *sum12, double *rb,
+                               double *region, int sms) {
+  const long long blocks = std::min<long long>((P.n_bins + 255) / 256, (long long)sms * 16);
+  k_fold_slices<<<(int)std::max<long long>(blocks, 1), 256, 2 * B * sizeof(double), s>>>(
+      P, tally, nt, B, sum1, sum2, sum12, rb);
+  k_region_slices<<<1, 1, 0, s>>>(rb, B, region, P.estimator == 2);
   return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ struct mcdc_problem {
   long long pc_combed_cap = 0;             // particles the combed bank holds
   long long pc_tally_bins = 0;             // entries of the per-batch tally slices
   double *pc_tally = nullptr;              // [batches][n_tally]
+  double *slice_rb = nullptr;              // [2 batches] per-batch region sums of the slices
   int32_t *pc_key = nullptr, *pc_seg = nullptr, *pc_live = nullptr;
   double *pc_segd = nullptr;
   int pc_seg_cap = 0;
