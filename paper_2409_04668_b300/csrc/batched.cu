@@ -21,39 +21,39 @@
 namespace mcdc {
 
 // Fold of every problem's batch tally: sum1 += x, sum2 += x^2, x = 0, and the
-// batch's region sum per problem.  Bins of all problems are numbered one
-// after another; off[p] is the first bin of problem p.
+// batch's region sum per problem (one row of blocks per problem).
 struct FoldItem {
   double *tally, *sum1, *sum2, *region_batch;
 };
 
 __global__ void __launch_bounds__(512) k_fold_multi(const DevProblem *__restrict__ probs,
-                                                    const FoldItem *__restrict__ fi,
-                                                    const long long *__restrict__ off, int n,
-                                                    long long total) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = n - 1;           // last problem whose first bin is <= q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (off[mid] <= q) lo = mid; else hi = mid - 1;
-    }
-    const long long b = q - off[lo];
-    const FoldItem &f = fi[lo];
+                                                    const FoldItem *__restrict__ fi) {
+  // blockIdx.y: the problem; its bins in a grid-stride loop over blockIdx.x
+  __shared__ double red[16];
+  const DevProblem &P = probs[blockIdx.y];
+  const FoldItem f = fi[blockIdx.y];
+  const RegionTest region(P);
+  const long long nb = P.n_bins;
+  double rs = 0.0;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
     const double v = f.tally[b];
     if (v != 0.0) {
       f.sum1[b] += v;
       f.sum2[b] += v * v;
       f.tally[b] = 0.0;
-      const DevProblem &P = probs[lo];
-      const long long cell = b / ((long long)P.G * P.T1);
-      const int ci = (int)(cell % P.n[0]);
-      const int cj = (int)((cell / P.n[0]) % P.n[1]);
-      const int ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
-      if (ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
-          cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2])
-        atomicAdd(f.region_batch, v);
+      if (region(P, b)) rs += v;
     }
+  }
+  // the block's region sum: one atomic per block instead of one per bin
+  for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+  const int nw = (int)(blockDim.x >> 5);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    if (t != 0.0) atomicAdd(f.region_batch, t);
   }
 }
 
@@ -109,6 +109,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
                 double *const *relerr_out, double *scalar_out, mcdc_stats *stats, int block,
                 unsigned long long chunk) {
   if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
+  if (n > 65535) return fail(MCDC_ERR_INVALID, "at most 65535 problems per batched run");
   const int B = n_batches > 0 ? n_batches : 16;
   if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");
   mcdc_problem *p0 = probs[0];
@@ -170,8 +171,6 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   std::vector<RunArgs> ha(n);
   std::vector<FoldItem> hf(n);
   std::vector<double *> hreg(n);
-  std::vector<long long> hoff(n);
-  long long total = 0;
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
     hp[i] = p->P;
@@ -188,8 +187,6 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     ha[i] = A;
     hf[i] = {p->tally, p->sum1, p->sum2, p->region_batch};
     hreg[i] = p->region;
-    hoff[i] = total;
-    total += p->P.n_bins;
   }
   // work items, batch by batch, largest first within a batch
   std::vector<WorkItem> items;
@@ -211,21 +208,18 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   WorkItem *d_items;
   FoldItem *d_fold;
   double **d_reg;
-  long long *d_off;
   unsigned long long *d_ctr;
   CKB(dnew(fr, &d_probs, n));
   CKB(dnew(fr, &d_args, n));
   CKB(dnew(fr, &d_items, items.size()));
   CKB(dnew(fr, &d_fold, n));
   CKB(dnew(fr, &d_reg, n));
-  CKB(dnew(fr, &d_off, n));
   CKB(dnew(fr, &d_ctr, B));
   CKB(cudaMemcpy(d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_args, ha.data(), sizeof(RunArgs) * n, cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_fold, hf.data(), sizeof(FoldItem) * n, cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_reg, hreg.data(), sizeof(double *) * n, cudaMemcpyHostToDevice));
-  CKB(cudaMemcpy(d_off, hoff.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
 
   cudaStream_t st;
   CKB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -255,11 +249,15 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     cudaMemsetAsync(p->sum2, 0, sizeof(double) * p->P.n_bins, st);
     cudaMemsetAsync(p->region, 0, 4 * sizeof(double), st);
   }
-  const int fold_blocks = (int)std::max<long long>(1, std::min<long long>((total + 511) / 512, (long long)p0->sms * 8));
+  // fold grid: x blocks per problem (enough for the largest), one row per problem
+  long long max_bins = 1;
+  for (int i = 0; i < n; ++i) max_bins = std::max<long long>(max_bins, probs[i]->P.n_bins);
+  const dim3 fold_grid((unsigned)std::max<long long>(1, std::min<long long>((max_bins + 511) / 512, 64)),
+                       (unsigned)n);
   for (int b = 0; b < B; ++b) {
     MultiArgs MA{d_probs, d_args, d_items + item_off[b], item_off[b + 1] - item_off[b], d_ctr + b};
     launch_track(key, grid, block, L.total, st, hp[0], ha[0], L, &MA);
-    k_fold_multi<<<fold_blocks, 512, 0, st>>>(d_probs, d_fold, d_off, n, total);
+    k_fold_multi<<<fold_grid, 512, 0, st>>>(d_probs, d_fold);
     k_region_fold_multi<<<(n + 255) / 256, 256, 0, st>>>(d_fold, d_reg, n);
   }
   for (int i = 0; i < n; ++i) {

@@ -15,6 +15,36 @@ struct NvtxRange {
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// The cell box of the scalar region, tested per bin without 64-bit division.
+struct RegionTest {
+  bool whole, narrow;
+  long long per_cell;
+  __device__ explicit RegionTest(const DevProblem &P) {
+    whole = P.region_lo[0] == 0 && P.region_lo[1] == 0 && P.region_lo[2] == 0 &&
+            P.region_hi[0] >= P.n[0] && P.region_hi[1] >= P.n[1] && P.region_hi[2] >= P.n[2];
+    narrow = P.n_bins < (1ll << 31);
+    per_cell = (long long)P.G * P.T1;
+  }
+  __device__ bool operator()(const DevProblem &P, long long q) const {
+    if (whole) return true;
+    int ci, cj, ck;
+    if (narrow) {
+      const uint32_t cell = (uint32_t)q / (uint32_t)per_cell;
+      const uint32_t row = cell / (uint32_t)P.n[0];
+      ci = (int)(cell - row * (uint32_t)P.n[0]);
+      ck = (int)(row / (uint32_t)P.n[1]);
+      cj = (int)(row - (uint32_t)ck * (uint32_t)P.n[1]);
+    } else {
+      const long long cell = q / per_cell;
+      ci = (int)(cell % P.n[0]);
+      cj = (int)((cell / P.n[0]) % P.n[1]);
+      ck = (int)(cell / ((long long)P.n[0] * P.n[1]));
+    }
+    return ci >= P.region_lo[0] && ci < P.region_hi[0] && cj >= P.region_lo[1] &&
+           cj < P.region_hi[1] && ck >= P.region_lo[2] && ck < P.region_hi[2];
+  }
+};
+
 struct Layout;
 
 struct MultiArgs;
