@@ -181,6 +181,14 @@ typedef struct mcdc_options {
                                    weight (unbiased, counted in splits_dropped):
                                    windows that would split without end cost a
                                    bounded run instead of an endless one        */
+    int64_t slice_bytes_max;    /* global tally: a run puts every batch in one
+                                   launch, each scoring its own tally slice, when
+                                   the slices (batches x bins x 8 bytes) fit in
+                                   this many bytes (0: 8 GiB; negative: never --
+                                   one launch and one fold per batch).  If the
+                                   slices cannot be allocated the run falls back
+                                   to one launch per batch.  Population control
+                                   always uses slices.                          */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */
@@ -406,7 +414,15 @@ int mcdc_set_wait_limit(int32_t tries);
  * first call on a device looks up the array's device address, so make that
  * first call before any stream capture.  Calls share the array: each clears
  * what must start at zero, and calls that overlap on the GPU race.  Event
- * statistics, records and overflow errors are not reported. */
+ * statistics, records and overflow errors are not reported.  Weight windows:
+ * split children come from the same per-run budget as in mcdc_run_ex
+ * (options.max_children), so a window map that would split without end
+ * still ends; a child that finds its warp's stack full is not made (its
+ * parent keeps the weight, which keeps the estimate unbiased).  mcdc_run_ex
+ * spills such children to device-wide banks it allocates, so in the global
+ * tally mode (64 stack slots per warp) a run that fills a stack differs from
+ * mcdc_run_ex's; in the shared mode (1024 slots) they agree unless a stack
+ * fills there too. */
 int mcdc_run_noalloc(struct mcdc_problem *prob, uint64_t n_histories, uint64_t seed,
                      uint64_t hist_offset, int32_t n_batches, double *sum1, double *sum2,
                      double *mean, double *relerr, void *stream);

@@ -127,6 +127,31 @@ int dalloc(mcdc_problem *pr, T **out, size_t count) {
   return MCDC_OK;
 }
 
+// Returns a buffer from dalloc to the device's pool (or frees it) once the
+// device has finished with it.
+void dfree(mcdc_problem *pr, void *p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  auto &pa = pr->pool_allocs;
+  for (size_t i = 0; i < pa.size(); ++i) {
+    if (pa[i] == p) {
+      cudaFreeAsync(p, device_pool(pr->device).stream);
+      pa.erase(pa.begin() + (long)i);
+      cudaGetLastError();
+      return;
+    }
+  }
+  auto &al = pr->allocs;
+  for (size_t i = 0; i < al.size(); ++i) {
+    if (al[i] == p) {
+      cudaFree(p);
+      al.erase(al.begin() + (long)i);
+      break;
+    }
+  }
+  cudaGetLastError();
+}
+
 // A problem's tables and accumulators in one device allocation: uploads are
 // gathered in a host buffer and copied once, device-only arrays follow them
 // and are zeroed once (a create is a handful of API calls, not dozens).
@@ -329,9 +354,17 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
 
 // One zeroed device tally slice per batch, for runs that put every batch in
 // one launch (population control, weight-window runs).
+// Growing them returns the smaller buffers first, so a problem never holds
+// two generations of slices.
 int ensure_slices(mcdc_problem *pr, int B) {
   const long long bins = (long long)B * pr->P.n_tally;
   if (pr->pc_tally_bins >= bins) return MCDC_OK;
+  dfree(pr, pr->pc_tally);
+  dfree(pr, pr->slice_rb);
+  pr->pc_tally = nullptr;
+  pr->slice_rb = nullptr;
+  pr->pc_tally_bins = 0;
+  pr->slices_dirty = false;
   int rc;
   if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
   if ((rc = dalloc(pr, &pr->slice_rb, (size_t)(2 * B)))) return rc;
@@ -1041,6 +1074,18 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.batch_r = a->n_histories % (uint64_t)B;
 
   CK(cudaEventRecord(pr->ev1, s));
+  // a run that returned early (a failed launch, the spill-pass limit) left
+  // scores in the batch tally or the slices, which a fold would otherwise
+  // zero: clear them before this run scores
+  if (pr->tally_dirty) {
+    CK(cudaMemsetAsync(pr->tally, 0, nt * 8, s));
+    pr->tally_dirty = false;
+  }
+  if (pr->slices_dirty && pr->pc_tally) {
+    CK(cudaMemsetAsync(pr->pc_tally, 0, sizeof(double) * (size_t)pr->pc_tally_bins, s));
+    CK(cudaMemsetAsync(pr->slice_rb, 0, sizeof(double) * 2 * (size_t)(pr->pc_tally_bins / std::max<long long>(1, P.n_tally)), s));
+    pr->slices_dirty = false;
+  }
   if (pr->tally_mode == MCDC_TALLY_SHARED) {
     A.work = pr->work;
     A.batch = 0;
@@ -1102,6 +1147,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     int32_t *live[2] = {pr->pc_live, pr->pc_live + B};
     int32_t *n_live[2] = {pr->pc_live + 2 * B, pr->pc_live + 2 * B + 1};
     long long n_in = (long long)N;
+    pr->slices_dirty = true;
     for (int step = 0;; ++step) {
       CK(cudaMemsetAsync(pr->pc_cnt, 0, sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(pr->pc_w, 0, sizeof(double) * (size_t)n_in, s));
@@ -1150,6 +1196,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       n_in = (long long)B * M;        // the next input: one chunk of M per combed batch
     }
     CK(fold_slices(pr, s, P, nt, B));
+    pr->slices_dirty = false;
   } else {
     const bool spill = ww_on(P) && pr->spill[0] != nullptr;
     // every batch in one launch, one tally slice per batch, when the slices
@@ -1157,9 +1204,22 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     // while a handful work through a batch's split families, and analog runs
     // pay a launch tail per batch (one launch: +5 % on the 60^3 channel,
     // +9 % on the deep box); otherwise one launch and one fold per batch
-    const bool merged = (double)B * (double)nt * 8.0 <= 8.0 * 1073741824.0;
-    if (merged)
-      if (int rc = ensure_slices(pr, B)) return rc;
+    // (options.slice_bytes_max moves the 8 GiB cap; negative: never).  When
+    // the slices cannot be allocated the run falls back to the per-batch
+    // launches, which need only the one batch tally.
+    const double cap = pr->opt.slice_bytes_max > 0 ? (double)pr->opt.slice_bytes_max
+                                                   : 8.0 * 1073741824.0;
+    bool merged = pr->opt.slice_bytes_max >= 0 && (double)B * (double)nt * 8.0 <= cap;
+    if (merged) {
+      if (int rc = ensure_slices(pr, B)) {
+        if (rc != MCDC_ERR_OOM) return rc;
+        cudaGetLastError();
+        g_err.clear();
+        merged = false;
+      }
+    }
+    if (merged) pr->slices_dirty = true;
+    else pr->tally_dirty = true;
     for (int b = 0; b < (merged ? 1 : B); ++b) {
       A.work = pr->work + b;
       A.batch = b;
@@ -1202,6 +1262,8 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
                        pr->region, pr->sms));
       }
     }
+    pr->slices_dirty = false;
+    pr->tally_dirty = false;
   }
   CK(cudaEventRecord(pr->ev2, s));
 

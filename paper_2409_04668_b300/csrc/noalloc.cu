@@ -11,7 +11,15 @@
 // the caller passes the output buffers.
 //
 // Limits: at most kMaxBins tally bins when the problem uses the global
-// tally, at most kMaxBatches batches; larger requests are rejected.  Every
+// tally, at most kMaxBatches batches; larger requests are rejected.
+// Weight windows: the run draws split children from the same per-run budget
+// as mcdc_run_ex (the problem's max_children option, by default 4096 per
+// history and at least 2^27), counted in the fixed array, so windows that
+// would split without end still end.  There is no device-wide spill bank
+// here: a child that finds its warp's stack full is not made and its parent
+// keeps the weight (unbiased, but in the global tally mode, whose warp
+// stacks hold 64 children, such a run then differs from mcdc_run_ex, which
+// spills those children to banks it allocates).  Every
 // GPU that loads the library holds the array (about 1.1 MiB) until exit.
 // All calls share it and it keeps the previous call's contents: each call
 // clears what must start at zero, and calls that overlap on the GPU (on
@@ -37,6 +45,7 @@ struct Scratch {
   double tally[kMaxBins];
   unsigned long long work[kMaxBatches];
   double region[8];     // region sums and squares [0..4], batch partials [5..6]
+  unsigned long long children;   // split children made so far (weight windows)
   Stats stats;
   int32_t error[4];
 };
@@ -116,6 +125,7 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   CKN(cudaMemsetAsync(sc->region, 0, sizeof(sc->region), s));
   CKN(cudaMemsetAsync(&sc->stats, 0, sizeof(Stats), s));
   CKN(cudaMemsetAsync(sc->error, 0, sizeof(sc->error), s));
+  CKN(cudaMemsetAsync(&sc->children, 0, sizeof(sc->children), s));
   CKN(cudaMemsetAsync(sum1, 0, nb * 8, s));
   CKN(cudaMemsetAsync(sum2, 0, nb * 8, s));
   if (global) CKN(cudaMemsetAsync(sc->tally, 0, nb * 8, s));
@@ -137,6 +147,14 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   A.overflow_cap = pr->overflow_cap;
   A.warp_aggregate = pr->warp_aggregate;
   A.tally = global ? sc->tally : nullptr;
+  if (pr->opt.max_children >= 0) {
+    // the budget of mcdc_run_ex: the option, else 4096 children per history
+    // and at least 2^27
+    A.children_made = &sc->children;
+    A.children_budget = pr->opt.max_children > 0
+                            ? (unsigned long long)pr->opt.max_children
+                            : std::max<unsigned long long>(1ull << 27, 4096ull * n_histories);
+  }
   if (!global) {
     A.work = sc->work;
     CKN(launch_track(pr->key, pr->grid, pr->block, pr->smem, s, pr->P, A, pr->L));

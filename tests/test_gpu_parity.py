@@ -70,6 +70,30 @@ def test_fp64_3d_channel_small(mcdc, mode):
     assert g["scalar"][0] == pytest.approx(o["scalar"][0], rel=REL_TALLY)
 
 
+@pytest.mark.parametrize("cap", [-1, 4096])
+def test_fp64_global_tally_one_launch_per_batch(mcdc, cap):
+    """The global tally's per-batch path (a launch and a fold per batch),
+    taken when the per-batch slices exceed their memory cap or cannot be
+    allocated: forced here by a cap of 'never' and one of 4 KiB, it matches
+    the oracle to 1e-9 (region scalar over the partial box of the far
+    octant included), and a second run on the same problem gives the same
+    sums."""
+    prob = small_channel(n=10, T=6)
+    N, B = 12_000, 6
+    o = O.run(prob, N, seed=5, batches=B)
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP64, tally_mode=mcdc.TALLY_GLOBAL,
+                      slice_bytes_max=cap) as P:
+        for _ in range(2):
+            s1, s2, mean, rel = (np.zeros(P.n_bins) for _ in range(4))
+            stats, scal = P.run_ex(N, 5, batches=B, sum1=s1, sum2=s2, mean=mean, relerr=rel)
+            g = {"sum1": s1.reshape(prob.tally_shape), "sum2": s2.reshape(prob.tally_shape),
+                 "mean": mean.reshape(prob.tally_shape), "relerr": rel.reshape(prob.tally_shape)}
+            compare_tallies(g, o)
+            compare_counts(stats, o["counts"])
+            assert scal[0] == pytest.approx(o["scalar"][0], rel=REL_TALLY)
+            assert scal[1] == pytest.approx(o["scalar"][1], rel=1e-6)
+
+
 def test_fp64_weight_windows_infinite_medium(mcdc):
     mat = np.zeros((2, 2, 4), np.uint8)
     prob = W.box("inf_ww", (4, 2, 2), (0.5, 1.0, 1.0), mat, [[1.0]], [[0.8]], np.ones((1, 1, 1)),
@@ -120,11 +144,15 @@ def test_fp64_batched_problems_match_independent_oracle_runs(mcdc):
     with its own seed, to 1e-9."""
     probs, _ = W.c5_batch(n_problems=5, seed=17)
     small = []
-    for p in probs:        # keep the oracle fast: at most 12^3 cells
+    for i, p in enumerate(probs):        # keep the oracle fast: at most 12^3 cells
         k = min(p.n[0], 12)
+        # two problems score a partial region box (the fold's cell test),
+        # the others the whole mesh
+        lo = {1: (k // 2, 0, 0), 3: (1, k // 3, k // 2)}.get(i, (0, 0, 0))
+        hi = {3: (k - 1, k, k - 2)}.get(i, (k, k, k))
         small.append(W.box(p.name, (k, k, k), p.width, p.material[:k, :k, :k].copy(), p.sigma_t,
                            p.sigma_s / p.sigma_t, p.transfer, p.speed, (0.0,) * 3, (float(k),) * 3,
-                           None, (0, 0, 0), (k, k, k)))
+                           None, lo, hi))
     hist = [3000, 5000, 2048, 4001, 2500]
     seed, B = 99, 4
     handles = [mcdc.Problem(p, precision=mcdc.PREC_FP64) for p in small]

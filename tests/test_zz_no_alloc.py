@@ -69,6 +69,80 @@ def test_noalloc_matches_run_ex_twice(env, mode):
             _close(out[3], ref[3], 1e-6)
 
 
+def _inf_medium_ww():
+    mat = np.zeros((2, 2, 4), np.uint8)
+    return W.box("inf_ww", (4, 2, 2), (0.5, 1.0, 1.0), mat, [[1.0]], [[0.8]], np.ones((1, 1, 1)),
+                 [1.0], (0.0, 0.0, 0.0), (2.0, 2.0, 2.0), None, (0, 0, 0), (4, 2, 2),
+                 bc=(W.BC_REFLECT,) * 6)
+
+
+def test_noalloc_weight_windows_match_run_ex_twice(env):
+    """Weight windows on the shared tally, whose warp stacks hold every child
+    here: the allocation-free run splits and roulettes exactly as
+    mcdc_run_ex does, with the same per-run children budget."""
+    M, torch = env
+    prob = _inf_medium_ww()
+    lower = np.random.default_rng(7).uniform(0.05, 0.6, size=prob.n_bins)
+    n, B = 20_000, 10
+    dev = torch.device("cuda", 0)
+    with M.Problem(prob, precision=M.PREC_FP64, tally_mode=M.TALLY_SHARED,
+                   overflow_per_cta=8192) as P:
+        P.set_weight_windows(lower, 5.0, 2.5, 16)
+        ref = [torch.zeros(P.n_bins, dtype=torch.float64, device=dev) for _ in range(4)]
+        st, _ = P.run_ex(n, 13, batches=B, sum1=ref[0], sum2=ref[1], mean=ref[2], relerr=ref[3])
+        torch.cuda.synchronize()
+        assert st["splits"] > 100 and st["roulette_killed"] > 100 and st["splits_dropped"] == 0
+        stream = torch.cuda.current_stream().cuda_stream
+        for call in range(2):
+            out = [torch.full((P.n_bins,), float("nan"), dtype=torch.float64, device=dev)
+                   for _ in range(4)]
+            P.run_noalloc(n, 13, out[0], out[1], batches=B, mean=out[2], relerr=out[3],
+                          stream=stream)
+            torch.cuda.synchronize()
+            _close(out[0], ref[0], REL)
+            _close(out[1], ref[1], REL)
+            _close(out[2], ref[2], REL)
+            _close(out[3], ref[3], 1e-6)
+
+
+def _explosive():
+    nc = 40
+    prob = W.slab("explosive_windows", 20.0, nc, np.zeros(nc), [[1.0]], [[0.9]], src=(0.0, 2.0))
+    return prob, 10.0 ** (-np.arange(nc) / 2.0)
+
+
+def test_noalloc_children_budget_bounds_explosive_windows(env):
+    """Windows that fall tenfold every two cells ask for a split at every
+    crossing of a right-moving particle, without end.  The allocation-free
+    run draws its children from the problem's budget as mcdc_run_ex does;
+    with a budget of 1 (a warp reserves 256 children at a time, so no
+    reservation ever succeeds) no child is made, every weight stays 1 and
+    no roulette fires, so the run ends and is the analog run event for
+    event: FP64 sums to the tally tolerance, twice.  (Which particles get
+    children under a budget that runs out partway depends on scheduling,
+    so such runs are not compared bin by bin.)"""
+    M, torch = env
+    prob, lower = _explosive()
+    n, B = 20_000, 20
+    dev = torch.device("cuda", 0)
+    kw = dict(precision=M.PREC_FP64, tally_mode=M.TALLY_GLOBAL)
+    with M.Problem(prob, **kw) as P:
+        ref = [torch.zeros(P.n_bins, dtype=torch.float64, device=dev) for _ in range(2)]
+        P.run_ex(n, 4, batches=B, sum1=ref[0], sum2=ref[1])
+    torch.cuda.synchronize()
+    assert float(ref[0].sum()) > 0
+    with M.Problem(prob, max_children=1, **kw) as P:
+        P.set_weight_windows(lower, 5.0, 2.5, 16)
+        for call in range(2):
+            out = [torch.full((P.n_bins,), float("nan"), dtype=torch.float64, device=dev)
+                   for _ in range(2)]
+            P.run_noalloc(n, 4, out[0], out[1], batches=B,
+                          stream=torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            _close(out[0], ref[0], REL)
+            _close(out[1], ref[1], REL)
+
+
 def test_noalloc_refuses_requests_beyond_its_limits(env):
     M, torch = env
     dev = torch.device("cuda", 0)
