@@ -12,7 +12,9 @@ per-step L2 flush writes a 256 MiB buffer.
 sample of the same workload and prints the same line with "impl": "reference".
 """
 import argparse
+import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -175,6 +177,8 @@ def main():
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
     ap.add_argument("--fom-per-event", action="store_true",
                     help="also measure the deep box with the network evaluated per event")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the 60^3 channel (HBM roofline) and the 256 batched problems")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the same workload in the other modes (cell-local FP32, "
                          "collision estimator, implicit capture)")
@@ -313,9 +317,12 @@ def main():
                                 measured_fp64)
     if world == 1 and not args.no_variants:
         line["variants"] = variants(M, prob, n_hist, args, mean, rel, stream)
+    if rank == 0 and world == 1 and not args.no_extra_workloads and args.workload == "c2":
+        line["c3"] = channel_block(M, prec, args, pk, measured_fp64)
+        line["c5"] = batched_block(M, prec, args)
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_over_pilots(M, prec, None)
-        line["fom_shallow"] = fom_over_pilots(M, prec, W.c4_shallow())
+        line["fom_shallow"] = fom_over_pilots(M, prec, W.c4_shallow(), match_relerr=0.04)
         if args.fom_per_event:
             line["fom_per_event"] = fom_over_pilots(M, prec, None, per_event=True)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -329,6 +336,81 @@ def main():
     P.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def channel_block(M, prec, args, pk, measured_fp64, n_hist=100_000_000):
+    """The 60^3 channel (7 groups, 20 time bins, 3.02e7 tally bins, 242 MB of
+    FP64 tally, larger than L2) at its full 1e8 histories: device-timed
+    histories/s and segments/s, and the HBM roofline of the tracker at 16
+    algorithmic bytes per segment (an FP64 read-modify-write of a tally bin)
+    against the measured copy bandwidth.  The time is that of the run's
+    launches (tracker and the slice fold), so the achieved figure is a
+    slight underestimate of the tracker's own."""
+    import torch
+    prob = W.c3_channel()
+    stream = torch.cuda.current_stream()
+    with M.Problem(prob, precision=prec) as P:
+        for s in range(args.warmup):
+            P.run_ex(n_hist, seed=1, offset=history_offset(0, 800 + s, n_hist),
+                     stream=stream.cuda_stream)
+        ms, segs, st = [], 0, None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(args.steps):
+            st, sc = P.run_ex(n_hist, seed=1, offset=history_offset(0, 820 + s, n_hist),
+                              stream=stream.cuda_stream)
+            ms.append(st["kernel_ms"])
+            segs += st["segments"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        region_ms = e0.elapsed_time(e1)
+    k_s = float(np.sum(ms)) / 1e3
+    seg_rate = segs / k_s
+    out = {"workload": prob.name, "histories_per_step": n_hist, "steps": args.steps,
+           "histories_per_s": n_hist * args.steps / (region_ms / 1e3),
+           "histories_per_s_kernels": n_hist * args.steps / k_s,
+           "segments_per_s": seg_rate, "segments_per_history": segs / (n_hist * args.steps),
+           "ms_per_step": region_ms / args.steps, "kernel_ms": k_s * 1e3 / args.steps,
+           "tally_mode": ["auto", "shared", "global"][st["tally_mode"]],
+           "n_batches": st["n_batches"], "region_relerr": sc[1],
+           "l2": "tally (242 MB) larger than L2",
+           "roofline": roofline(prob, seg_rate, pk, st["tally_mode"], args.precision)}
+    if args.precision == "fp32" and measured_fp64 is not None:
+        # the same flights seen from the FP64 pipe: 16 operations per 3-D flight
+        add, cvt = measured_fp64
+        mix = 2.0 / (1.0 / add + 1.0 / cvt) / 1e12
+        out["fp64_pipe"] = {"achieved_T_ops_per_s": seg_rate * 16 / 1e12,
+                            "frac_of_measured_pipe": seg_rate * 16 / 1e12 / mix}
+    return out
+
+
+def batched_block(M, prec, args):
+    """The 256 independent problems (meshes 16^3..64^3, 1..7 groups, 1e4..1e7
+    histories, 3.3e8 in all) in one batched run per step: histories/s and
+    segments/s over the run's device time."""
+    probs, hist = W.c5_batch()
+    handles = [M.Problem(p, precision=prec) for p in probs]
+    try:
+        for s in range(max(1, args.warmup)):
+            M.run_batched(handles, hist, 1 + s, batches=16)
+        ms, segs, tot = [], 0, []
+        for s in range(args.steps):
+            (st, _), wall = _timed(lambda: M.run_batched(handles, hist, 100 + s, batches=16))
+            ms.append(st["kernel_ms"])
+            tot.append(wall)
+            segs += st["segments"]
+    finally:
+        for h in handles:
+            h.close()
+    t = float(np.sum(ms)) / 1e3
+    return {"workload": "c5_batched_256_problems", "problems": len(probs),
+            "histories_per_step": int(sum(hist)), "steps": args.steps,
+            "histories_per_s": sum(hist) * args.steps / t, "segments_per_s": segs / t,
+            "ms_per_step": 1e3 * t / args.steps,
+            "wall_ms_per_step": 1e3 * float(np.mean(tot)),
+            "block": st["block_size"], "ctas_per_sm": st["ctas_per_sm"]}
 
 
 def run_batched_bench(args):
@@ -439,18 +521,44 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
 WW_SETTINGS = {"source_wl": 0.25, "upper_ratio": 4.0, "survival_ratio": 2.0}
 
 
+def fom_rel_uncertainty(n_batches):
+    """Relative standard uncertainty of a figure of merit 1/(relerr^2 T) whose
+    relerr comes from n batch means: the sample standard deviation of n
+    normal values has relative error about 1/sqrt(2 (n - 1)), and the FOM
+    goes as its inverse square."""
+    return math.sqrt(2.0 / max(1, n_batches - 1))
+
+
+def _timed(fn):
+    """(result, wall seconds) of fn() between two device synchronisations."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7,
-             per_event=False):
+             per_event=False, match_relerr=None, ww_batches=16):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
     region x in [90, 100]), analog against the learned weight windows.  The
     analog run's tally is the pilot; the network is refit twice, each time on
     the tally of a weight-window run with the previous windows (each such
-    tally is an unbiased flux estimate that reaches deeper).  T is the device time of the measured run; the
-    training time is reported beside it.  seed0 seeds the pilot; the
-    weight-window runs use seed0 + 4, + 5, ....  per_event: the last fit's
-    network sets every window at the event instead of a baked table (the
-    refits still bake)."""
+    tally is an unbiased flux estimate that reaches deeper).
+
+    T of the learned arm is reported three ways: the final weight-window
+    run alone (device time, fom_transport_only), with the three fits and the
+    two refit runs (wall time, fom_incl_fit), and with the analog pilot too
+    (fom_incl_pilot).  The analog arm's T is its run's device time.
+    match_relerr: also run the analog arm to about that relative error
+    (chunks of 1e9 histories) and the learned arm's final run at the
+    history count that reaches the same error, and compare the two at equal
+    variance with every cost of the learned pipeline in T.  seed0 seeds the
+    pilot; the weight-window runs use seed0 + 4, + 5, ....  per_event: the
+    last fit's network sets every window at the event instead of a baked
+    table (the refits still bake)."""
     import torch
     prob = prob if prob is not None else W.c4_deep()
     out = {"workload": prob.name, "region_cells": [list(prob.region_lo), list(prob.region_hi)]}
@@ -460,64 +568,150 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         mean = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
         rel = torch.zeros_like(mean)
         P.run_ex(1_000_000, seed0, mean=mean, relerr=rel)        # warm-up
-        st, (m_a, r_a) = P.run_ex(n_analog, seed0, mean=mean, relerr=rel)
+        (st, (m_a, r_a)), wall_a = _timed(lambda: P.run_ex(n_analog, seed0, mean=mean, relerr=rel))
         t_a = st["kernel_ms"] / 1e3
+        nb_a = st["n_batches"]
         out["analog"] = {"histories": n_analog, "mean": m_a, "relerr": r_a if m_a > 0 else None,
-                         "seconds": t_a, "histories_per_s": n_analog / t_a,
+                         "seconds": t_a, "histories_per_s": n_analog / t_a, "batches": nb_a,
                          "fom": (1.0 / (r_a ** 2 * t_a)) if m_a > 0 and r_a > 0 else None,
+                         "fom_rel_uncertainty": fom_rel_uncertainty(nb_a) if m_a > 0 else None,
                          "fom_upper_bound": None if m_a > 0 else 1.0 / t_a,
                          "note": None if m_a > 0 else "no analog history scored in the region: "
                                  "relerr >= 1, so FOM <= 1/T"}
-        train_ms, ww_ms = 0.0, 0.0
+        fit_wall, fit_dev, ww_wall = 0.0, 0.0, 0.0
         seed = seed0 + 4
         for it in range(refits + 1):
-            rep = P.train_importance(mean, rel, epochs=20, batch=16384, min_ratio=1e-20,
-                                     per_event=int(per_event and it == refits), **WW_SETTINGS)
-            train_ms += rep["train_ms"] + rep["bake_ms"]
+            rep, w = _timed(lambda: P.train_importance(
+                mean, rel, epochs=20, batch=16384, min_ratio=1e-20,
+                per_event=int(per_event and it == refits), **WW_SETTINGS))
+            fit_wall += w
+            fit_dev += (rep["train_ms"] + rep["bake_ms"]) / 1e3
             if it < refits:
-                st, _ = P.run_ex(n_ww, seed, batches=16, mean=mean, relerr=rel)
-                ww_ms += st["kernel_ms"]
+                _, w = _timed(lambda: P.run_ex(n_ww, seed, batches=ww_batches, mean=mean,
+                                               relerr=rel))
+                ww_wall += w
                 seed += 1
-        st, (m_w, r_w) = P.run_ex(n_ww, seed, batches=16)
+        st, (m_w, r_w) = P.run_ex(n_ww, seed, batches=ww_batches)
         t_w = st["kernel_ms"] / 1e3
+        t_incl_fit = fit_wall + ww_wall + t_w
+        t_incl_pilot = t_incl_fit + wall_a
+        fom_w = (1.0 / (r_w ** 2 * t_w)) if m_w > 0 and r_w > 0 else None
         out["learned"] = {"histories": n_ww, "mean": m_w, "relerr": r_w, "seconds": t_w,
-                          "histories_per_s": n_ww / t_w,
-                          "fom": (1.0 / (r_w ** 2 * t_w)) if m_w > 0 and r_w > 0 else None,
+                          "batches": ww_batches, "histories_per_s": n_ww / t_w,
+                          "fom_transport_only": fom_w,
+                          "fom": fom_w,
+                          "fom_incl_fit": (1.0 / (r_w ** 2 * t_incl_fit)) if fom_w else None,
+                          "fom_incl_pilot": (1.0 / (r_w ** 2 * t_incl_pilot)) if fom_w else None,
+                          "fom_rel_uncertainty": fom_rel_uncertainty(ww_batches),
+                          "seconds_incl_fit": t_incl_fit, "seconds_incl_pilot": t_incl_pilot,
                           "splits": st["splits"], "segments_per_history": st["segments"] / n_ww,
-                          "training_seconds": train_ms / 1e3,
-                          "refit_runs_seconds": ww_ms / 1e3, "refits": refits}
+                          "fit_seconds_wall": fit_wall, "fit_seconds_device": fit_dev,
+                          "refit_runs_seconds_wall": ww_wall, "pilot_seconds_wall": wall_a,
+                          "fits": refits + 1, "refits": refits}
+        if match_relerr and m_a > 0 and fom_w:
+            out["equal_variance"] = equal_variance(M, P, prob, prec, seed0, match_relerr, r_w, n_ww,
+                                                   seed + 1, ww_batches,
+                                                   fit_wall + ww_wall + wall_a)
     a, l = out["analog"], out["learned"]
     if l["fom"] and a["fom"]:
         out["ratio"] = l["fom"] / a["fom"]
+        out["ratio_incl_fit"] = l["fom_incl_fit"] / a["fom"]
+        out["ratio_incl_pilot"] = l["fom_incl_pilot"] / a["fom"]
+        out["ratio_rel_uncertainty"] = math.hypot(a["fom_rel_uncertainty"], l["fom_rel_uncertainty"])
     elif l["fom"] and a["fom_upper_bound"]:
         out["ratio_lower_bound"] = l["fom"] / a["fom_upper_bound"]
+        out["ratio_incl_fit_lower_bound"] = l["fom_incl_fit"] / a["fom_upper_bound"]
+        out["ratio_incl_pilot_lower_bound"] = l["fom_incl_pilot"] / a["fom_upper_bound"]
     return out
 
 
-def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False):
+def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batches, overhead_s,
+                   chunk=1_000_000_000, max_seconds=12.0):
+    """Analog and learned runs of the far-region flux taken to the same
+    relative error.  Analog: chunks of `chunk` histories (independent seeds)
+    until the combined relative error reaches `target` or max_seconds of
+    device time are spent; the learned arm's final run is then repeated with
+    the history count that reaches the analog's error (from its first run's
+    error, relerr ~ 1/sqrt(N)), and its T includes every cost of the
+    pipeline (pilot, fits, refit runs: overhead_s)."""
+    import torch
+    means, vars_, secs, nb = [], [], 0.0, 0
+    with M.Problem(prob, precision=prec) as A:
+        k = 0
+        while True:
+            st, (m, r) = A.run_ex(chunk, seed0 + 1000 + k, batches=32)
+            k += 1
+            means.append(m)
+            vars_.append((m * r) ** 2)
+            secs += st["kernel_ms"] / 1e3
+            nb += st["n_batches"]
+            mc = float(np.mean(means))
+            rc = math.sqrt(sum(vars_)) / len(means) / mc if mc > 0 else float("inf")
+            if rc <= target or secs >= max_seconds:
+                break
+    n_w = int(max(2000, math.ceil(n_w1 * (r_w1 / rc) ** 2)))
+    (st, (m_w, r_w)), wall = _timed(lambda: P.run_ex(n_w, seed_w, batches=ww_batches))
+    t_w = st["kernel_ms"] / 1e3
+    t_tot = overhead_s + t_w
+    fa, fw = 1.0 / (rc * rc * secs), 1.0 / (r_w * r_w * t_tot)
+    ua, uw = fom_rel_uncertainty(nb), fom_rel_uncertainty(ww_batches)
+    z = (m_w - mc) / math.hypot(m_w * r_w, mc * rc)
+    return {"target_relerr": target,
+            "analog": {"histories": chunk * len(means), "mean": mc, "relerr": rc, "seconds": secs,
+                       "batches": nb, "fom": fa, "fom_rel_uncertainty": ua},
+            "learned": {"histories": n_w, "mean": m_w, "relerr": r_w, "seconds_run": t_w,
+                        "seconds_incl_pilot_and_fit": t_tot, "fom_incl_pilot": fw,
+                        "fom_rel_uncertainty": uw},
+            "agreement_z": z,
+            "ratio_incl_pilot": fw / fa, "ratio_rel_uncertainty": math.hypot(ua, uw),
+            "time_ratio": secs / t_tot}
+
+
+def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False, match_relerr=None):
     """fom_deep for the first pilot seed in full, plus the learned FOM (and the
     ratio to analog, or its lower bound) for every seed and their medians: the
     windows depend on the pilot sample, so one seed is one draw of the whole
     pipeline."""
-    runs = [fom_deep(M, prec, prob=prob, seed0=s, per_event=per_event) for s in seeds]
+    runs = [fom_deep(M, prec, prob=prob, seed0=s, per_event=per_event,
+                     match_relerr=match_relerr if k == 0 else None)
+            for k, s in enumerate(seeds)]
     out = runs[0]
-    foms = [r["learned"]["fom"] or 0.0 for r in runs]
-    key = "ratio" if "ratio" in out else "ratio_lower_bound"
-    ratios = [r.get(key) or 0.0 for r in runs]
     out["pilot_seeds"] = list(seeds)
-    out["learned_fom_by_pilot_seed"] = foms
-    out[key + "_by_pilot_seed"] = ratios
-    out["learned_fom_median"] = float(np.median(foms))
-    out[key + "_median"] = float(np.median(ratios))
+    for f in ("fom", "fom_incl_fit", "fom_incl_pilot"):
+        v = [r["learned"][f] or 0.0 for r in runs]
+        out[f"learned_{f}_by_pilot_seed"] = v
+        out[f"learned_{f}_median"] = float(np.median(v))
+    lb = "" if "ratio" in out else "_lower_bound"
+    for f in ("ratio", "ratio_incl_fit", "ratio_incl_pilot"):
+        v = [r.get(f + lb) or 0.0 for r in runs]
+        out[f"{f}{lb}_by_pilot_seed"] = v
+        out[f"{f}{lb}_median"] = float(np.median(v))
     return out
 
 
 # DRAM bytes (read + write) per tracker launch from one ncu capture of the
-# bench's own command (profiles/k_track_two_region_slab.md, "DRAM traffic"),
-# keyed by (workload, precision, tally mode); re-measure when the kernel
-# changes.  The shared tally keeps the traffic to the tables and the fold's
-# atomics, which stay in L2.
-MEASURED_TRAFFIC = {("c2_slab_20cm_2region_td", "fp32", 1): 259840}
+# bench's own workload, keyed by (workload, precision, tally mode), with the
+# digest of the library sources the capture ran on: a figure is reported only
+# while the sources are unchanged (null otherwise, until it is re-measured).
+MEASURED_TRAFFIC = {}
+
+
+def source_digest():
+    """First 16 hex digits of the SHA-256 of the library's CUDA sources."""
+    d = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_04668_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            d.update(f.encode())
+            d.update(open(os.path.join(csrc, f), "rb").read())
+    return d.hexdigest()[:16]
+
+
+def measured_traffic(name, prec_name, tally_mode):
+    v = MEASURED_TRAFFIC.get((name, prec_name, tally_mode))
+    if v is None or v[1] != source_digest():
+        return None
+    return v[0]
 
 
 def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
@@ -536,17 +730,20 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     (large meshes): 16 B of FP64 read-modify-write per flight against the
     measured copy bandwidth."""
     three_d = prob.n[1] > 1 or prob.n[2] > 1
-    if tally_mode == 2 and prec_name != "fp32":
+    if tally_mode == 2 and (prec_name != "fp32" or three_d):
         ach = seg_rate * 16 / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": "measured copy"}
+                "frac": ach / pk["hbm_gbs"],
+                "traffic": measured_traffic(prob.name, prec_name, tally_mode),
+                "traffic_unit": "DRAM bytes per launch (ncu)", "bytes_per_segment": 16,
+                "peak_kind": "measured copy (MEASURED_PEAKS.json hbm_gbs)"}
     if prec_name == "fp32":
         ops = 16.0 if three_d else 8.0
         peak = 0.625
         ach = seg_rate * ops / 1e12
         out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe ops/s",
                "frac": ach / peak,
-               "traffic": MEASURED_TRAFFIC.get((prob.name, prec_name, tally_mode)),
+               "traffic": measured_traffic(prob.name, prec_name, tally_mode),
                "traffic_unit": "DRAM bytes per launch (ncu)", "ops_per_segment": ops,
                "peak_kind": "nominal B300 FP64 1.25 TFLOP/s = 0.625 T pipe ops/s (recipe)"}
         if measured_fp64 is not None:
