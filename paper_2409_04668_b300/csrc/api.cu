@@ -570,6 +570,10 @@ int set_net_kernel(mcdc_problem *pr, bool net) {
 namespace mcdc {
 int set_error(int code, const std::string &msg) { return fail(code, msg); }
 int ensure_overflow_for(mcdc_problem *pr) { return ensure_overflow(pr); }
+cudaMemPool_t device_mem_pool(int dev) {
+  const DevPool d = device_pool(dev);
+  return d.ok ? d.pool : nullptr;
+}
 }  // namespace mcdc
 
 extern "C" {

@@ -107,6 +107,9 @@ struct mcdc_problem;
 namespace mcdc {
 // Allocates the per-warp overflow stacks once weight windows are on.
 int ensure_overflow_for(mcdc_problem *pr);
+// The device's stream-ordered memory pool of problems (nullptr where pools
+// are unavailable), for temporaries allocated and freed on a caller's stream.
+cudaMemPool_t device_mem_pool(int dev);
 // importance network (mlp.cu)
 cudaError_t mlp_prepare();
 int64_t mlp_param_count(int n_in);

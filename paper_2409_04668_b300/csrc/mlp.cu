@@ -113,8 +113,11 @@ __global__ void __launch_bounds__(kTM) k_mlp_forward_tc(const float *__restrict_
   bool pending = false;
   for (int64_t base = (int64_t)blockIdx.x * kTM; base < n; base += (int64_t)gridDim.x * kTM) {
     const int64_t row = base + tid;
-    for (int c = 0; c < kIn; ++c)
-      st_bf16(s.X, tc::kmaj(tid, c, kIn), (row < n && c < n_in) ? X[row * n_in + c] : 0.0f);
+    float xr[kIn];                      // all loads first, then the stores
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) xr[c] = (row < n && c < n_in) ? X[row * n_in + c] : 0.0f;
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) st_bf16(s.X, tc::kmaj(tid, c, kIn), xr[c]);
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -175,224 +178,322 @@ __global__ void __launch_bounds__(kTM) k_mlp_forward_tc(const float *__restrict_
   }
 }
 
-// shared memory of the tcgen05 gradient kernel (operands K-major, no swizzle).
-// A CTA runs two independent tile pipelines (two groups of 4 warps); each
-// has its own operand tiles, tensor-memory columns, mbarrier and barrier.
-constexpr int kNB = 80;    // rows of BH: H1^T (64), ones (1), zero padding
-constexpr int kNX = 32;    // rows of XT: features (<= 16), ones (row 16), zero padding
+// shared memory of the tcgen05 gradient kernel (no swizzle).  A CTA runs two
+// independent tile pipelines (two groups of 4 warps); each has its own
+// operand tiles, tensor-memory columns, mbarrier and barrier.  Every tile is
+// stored sample-major ([sample][column], the K-major layout of an A operand
+// whose K is the column): the forward and dH1 products read them as K-major
+// A operands, the weight-gradient products (whose K is the sample) read the
+// same bytes as MN-major operands, so no transposed copy is written.
+constexpr int kNB = 80;    // columns of H1: hidden (64), ones (64), zero padding
+constexpr int kNX = 32;    // columns of X: features (<= 16), ones (16), zero padding
 constexpr int kGroups = 2;
 struct TcTile {
-  __nv_bfloat16 X[kTM * kIn];             // A of Z1:  [sample][in]
-  __nv_bfloat16 XT[kNX * kTM];            // B of dW1: [feature | 1][sample]
-  __nv_bfloat16 H1[kTM * kH];             // A of Z2:  [sample][hidden]
-  __nv_bfloat16 BH[kNB * kTM];            // B of dW2: [H1^T | 1][sample]
-  __nv_bfloat16 D2[kTM * kH];             // A of dH1: [sample][out]
-  __nv_bfloat16 DT[kTM * kTM];            // A of dW2 / dW1: [D2^T | 0] then [D1^T | 0]
+  __nv_bfloat16 X[kTM * kNX];             // [sample][feature | 1 | 0]
+  __nv_bfloat16 D[kTM * kTM];             // [sample][o | 0]: D2, then D1 (dL/dz1)
+  __nv_bfloat16 H1[kTM * kNB];            // [sample][hidden | 1 | 0]
   uint64_t mbar;
   int abort;
   int pad;
 };
 struct TcGrad {
+  TcTile t[kGroups];                      // first: every operand read of the tiles
+                                          // stays inside this structure
   __nv_bfloat16 W1[kH * kIn];             // B of Z1:  [out][in]
   __nv_bfloat16 W2[kH * kH];              // B of Z2:  [out][in]
   __nv_bfloat16 W2T[kH * kH];             // B of dH1: [in][out]
   float b1[kH], b2[kH], W3[kH];
   float red[kGroups * 4][kH + 2];         // per-warp sums of gW3, gb3, loss
+  float xch[kH * (kH + 18)];              // pipeline 1's weight gradients for pipeline 0
   uint32_t tmem;
   int pad[3];
-  TcTile t[kGroups];
 };
+
+// eight consecutive BF16 values (one 16-byte core-matrix row) in one store
+__device__ __forceinline__ void st_bf16x8(void *tile, uint32_t off, const float *v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    w[k] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(tile) + off) =
+      make_uint4(w[0], w[1], w[2], w[3]);
+}
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;\n" : : "r"(1 + g), "r"(kTM) : "memory");
 }
 
+// Writes the BF16 weight operands (W1, W2, W2^T) and the FP32 biases and
+// output weights of the parameter vector p into shared memory (all threads
+// of the CTA); returns b3.  Loads bypass L1 (cache at L2 only): in the fused
+// training kernel other CTAs rewrite p between steps.
+// The loads of a thread are all issued before its shared-memory stores (the
+// stores go through generic addresses, which the compiler cannot separate
+// from the loads, so interleaving them would cost an L2 round trip each).
+// Needs blockDim.x == kGroups * kTM.
+__device__ __forceinline__ float load_weights(TcGrad &s, const float *__restrict__ p, int n_in) {
+  constexpr int nt = kGroups * kTM;
+  constexpr int n1 = kH * kIn / nt, n2 = kH * kH / nt;
+  const int tid = threadIdx.x;
+  const Params q = split(p, n_in);
+  float w1[n1], w2[n2], bb[3];
+#pragma unroll
+  for (int j = 0; j < n1; ++j) {
+    const int i = tid + j * nt, rr = i / kIn, c = i % kIn;
+    w1[j] = c < n_in ? __ldcg(q.W1 + rr * n_in + c) : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < n2; ++j) w2[j] = __ldcg(q.W2 + tid + j * nt);
+  const int tb = tid & (kH - 1);
+  bb[0] = __ldcg(q.b1 + tb);
+  bb[1] = __ldcg(q.b2 + tb);
+  bb[2] = __ldcg(q.W3 + tb);
+  const float b3 = __ldcg(p + param_count(n_in) - 1);
+#pragma unroll
+  for (int j = 0; j < n1; ++j) {
+    const int i = tid + j * nt;
+    st_bf16(s.W1, tc::kmaj(i / kIn, i % kIn, kIn), w1[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < n2; ++j) {
+    const int i = tid + j * nt, rr = i / kH, c = i % kH;
+    st_bf16(s.W2, tc::kmaj(rr, c, kH), w2[j]);
+    st_bf16(s.W2T, tc::kmaj(c, rr, kH), w2[j]);
+  }
+  if (tid < kH) { s.b1[tid] = bb[0]; s.b2[tid] = bb[1]; s.W3[tid] = bb[2]; }
+  return b3;
+}
+
+// constant columns of a group's tiles: the ones of X (column 16) and H1
+// (column 64) that carry the bias gradients, and the zero padding of X, H1
+// and D; thread r of the group writes row r
+__device__ __forceinline__ void init_tile_constants(TcTile &t, int r) {
+  float z[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) z[k] = k == 0 ? 1.0f : 0.0f;
+  st_bf16x8(t.X, tc::kmaj(r, 16, kNX), z);
+  st_bf16x8(t.H1, tc::kmaj(r, kH, kNB), z);
+  z[0] = 0.0f;
+  st_bf16x8(t.X, tc::kmaj(r, 24, kNX), z);
+  st_bf16x8(t.H1, tc::kmaj(r, kH + 8, kNB), z);
+#pragma unroll
+  for (int c = kH; c < kTM; c += 8) st_bf16x8(t.D, tc::kmaj(r, c, kTM), z);
+}
+
+// State of one tile pipeline (a group of 128 threads) across its tiles.
+struct TileState {
+  uint32_t phase;          // parity of the group's mbarrier
+  bool pending;            // an MMA chain was committed and not yet waited for
+  bool started;            // the weight-gradient accumulators hold a tile
+  float loss, gb3;         // this thread's sample: loss and d loss / d b3 so far
+};
+
+// One tile of 128 samples (thread r of group g owns sample `row`, valid if
+// row < n) through forward and backward: Z1 = X W1^T, Z2 = H1 W2^T,
+// dH1 = D2 W2, and the weight gradients over the tile's samples,
+// [dW2 | gb2] += D2^T [H1 | 1] and [dW1 | gb1] += D1^T [X | 1], accumulated
+// in tensor memory across the group's tiles (ts.started); gW3 and gb3 build
+// up in registers.  The weight-gradient products take D (M = output unit,
+// padded to 128), H1 and X (N = input unit, with the ones column) as
+// MN-major operands over K = the tile's samples.  Tensor memory (512
+// columns), group g: Z1 in [128 g, 128 g + 64), Z2 and later dH1 in
+// [128 g + 64, 128 g + 128), the gradient accumulators in [256 + 112 g,
+// 256 + 112 g + 80) (rows o < 64 hold dW2 (cols 0-63) and gb2 (col 64)) and
+// [256 + 112 g + 80, 256 + 112 g + 112) (rows i < 64 hold dW1 (cols < n_in)
+// and gb1 (col 16)).  Returns false if a wait on the tensor cores gave up.
+__device__ __forceinline__ bool grad_tile(TcGrad &s, TcTile &t, int g, int r, uint32_t tm,
+                                          uint32_t lb, const float *__restrict__ Xs,
+                                          const float *__restrict__ Ys,
+                                          const float *__restrict__ Ws, int n_in, int64_t n,
+                                          int64_t row, float b3, float inv_wsum, TileState &ts,
+                                          float (&gw3)[kH]) {
+  const uint32_t cZ1 = 128u * g, cZ2 = cZ1 + 64, cW2 = 256u + 112u * g, cW1 = cW2 + 80;
+  const uint32_t aX = tc::smem_u32(t.X), aW1 = tc::smem_u32(s.W1), aH1 = tc::smem_u32(t.H1);
+  const uint32_t aW2 = tc::smem_u32(s.W2), aW2T = tc::smem_u32(s.W2T), aD = tc::smem_u32(t.D);
+  // byte strides of the sample-major tiles: 8-sample groups (the K groups of
+  // the MN-major reads) and 8-column groups
+  constexpr uint32_t sX = kNX / 8 * 128, sH = kNB / 8 * 128, sD = kTM / 8 * 128;
+  auto wait_mma = [&]() {
+    ts.pending = true;
+    if (!tc::mbar_wait(&t.mbar, ts.phase, g_tc_wait_limit)) { atomicOr(&g_tc_timeout, 1); t.abort = 1; }
+    ts.phase ^= 1u;
+    group_sync(g);
+    if (!t.abort) ts.pending = false;
+    tc::fence_after_sync();
+    return !t.abort;
+  };
+  const bool valid = row < n;
+  const float yv = valid ? Ys[row] : 0.0f, wv = valid ? Ws[row] : 0.0f;
+  {
+    float xr[kIn];                    // all loads first, then the stores
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) xr[c] = (valid && c < n_in) ? Xs[row * n_in + c] : 0.0f;
+    st_bf16x8(t.X, tc::kmaj(r, 0, kNX), xr);
+    st_bf16x8(t.X, tc::kmaj(r, 8, kNX), xr + 8);
+  }
+  tc::fence_async_smem();
+  group_sync(g);
+  if (r == 0) {
+    tc::fence_after_sync();
+    tc::mma(tm + cZ1, tc::desc(aX, 128, sX), tc::desc(aW1, 128, 256), tc::idesc_bf16(kTM, kH), 0);
+    tc::commit(&t.mbar);
+  }
+  if (!wait_mma()) return false;
+  // layer 1: H1
+  float v[16], u[16];
+#pragma unroll 1
+  for (int q4 = 0; q4 < 4; ++q4) {
+    tc::ld16(tm + lb + cZ1 + 16 * q4, v);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) u[c] = silu(v[c] + s.b1[16 * q4 + c]);
+    st_bf16x8(t.H1, tc::kmaj(r, 16 * q4, kNB), u);
+    st_bf16x8(t.H1, tc::kmaj(r, 16 * q4 + 8, kNB), u + 8);
+  }
+  tc::fence_before_sync();
+  tc::fence_async_smem();
+  group_sync(g);
+  if (r == 0) {
+    tc::fence_after_sync();
+#pragma unroll
+    for (int kk = 0; kk < kH / 16; ++kk)
+      tc::mma(tm + cZ2, tc::desc(aH1 + 256 * kk, 128, sH), tc::desc(aW2 + 256 * kk, 128, 1024),
+              tc::idesc_bf16(kTM, kH), kk > 0);
+    tc::commit(&t.mbar);
+  }
+  if (!wait_mma()) return false;
+  // layer 2 and the output: f, the loss, dL/df; then dL/dz2 and gW3
+  float f = b3;
+#pragma unroll 1
+  for (int q4 = 0; q4 < 4; ++q4) {
+    tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) f += silu(v[c] + s.b2[16 * q4 + c]) * s.W3[16 * q4 + c];
+  }
+  const float e = f - yv;
+  const float dy = 2.0f * wv * e * inv_wsum;
+  ts.loss += wv * e * e * inv_wsum;
+  ts.gb3 += dy;
+#pragma unroll
+  for (int q4 = 0; q4 < 4; ++q4) {
+    tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int o = 16 * q4 + c;
+      const float z2 = v[c] + s.b2[o];
+      gw3[o] += dy * silu(z2);
+      u[c] = dy * s.W3[o] * dsilu(z2);
+    }
+    st_bf16x8(t.D, tc::kmaj(r, 16 * q4, kTM), u);
+    st_bf16x8(t.D, tc::kmaj(r, 16 * q4 + 8, kTM), u + 8);
+  }
+  tc::fence_before_sync();
+  tc::fence_async_smem();
+  group_sync(g);
+  if (r == 0) {
+    tc::fence_after_sync();
+#pragma unroll
+    for (int kk = 0; kk < kH / 16; ++kk)           // dH1 = D2 W2 (over Z2's columns)
+      tc::mma(tm + cZ2, tc::desc(aD + 256 * kk, 128, sD), tc::desc(aW2T + 256 * kk, 128, 1024),
+              tc::idesc_bf16(kTM, kH), kk > 0);
+#pragma unroll
+    for (int kk = 0; kk < kTM / 16; ++kk)          // [dW2 | gb2] += D2^T [H1 | 1]
+      tc::mma(tm + cW2, tc::desc(aD + 2 * sD * kk, sD, 128), tc::desc(aH1 + 2 * sH * kk, sH, 128),
+              tc::idesc_bf16(kTM, kNB) | tc::kMnMajorA | tc::kMnMajorB,
+              (ts.started || kk > 0) ? 1u : 0u);
+    tc::commit(&t.mbar);
+  }
+  if (!wait_mma()) return false;
+  // dL/dz1 = dH1 * silu'(z1) -> D (D2 is no longer read)
+#pragma unroll 1
+  for (int q4 = 0; q4 < 4; ++q4) {
+    tc::ld16(tm + lb + cZ2 + 16 * q4, v);
+    tc::ld16(tm + lb + cZ1 + 16 * q4, u);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] *= dsilu(u[c] + s.b1[16 * q4 + c]);
+    st_bf16x8(t.D, tc::kmaj(r, 16 * q4, kTM), v);
+    st_bf16x8(t.D, tc::kmaj(r, 16 * q4 + 8, kTM), v + 8);
+  }
+  tc::fence_before_sync();
+  tc::fence_async_smem();
+  group_sync(g);
+  if (r == 0) {
+    tc::fence_after_sync();
+#pragma unroll
+    for (int kk = 0; kk < kTM / 16; ++kk)          // [dW1 | gb1] += D1^T [X | 1]
+      tc::mma(tm + cW1, tc::desc(aD + 2 * sD * kk, sD, 128), tc::desc(aX + 2 * sX * kk, sX, 128),
+              tc::idesc_bf16(kTM, kNX) | tc::kMnMajorA | tc::kMnMajorB,
+              (ts.started || kk > 0) ? 1u : 0u);
+    tc::commit(&t.mbar);
+  }
+  ts.started = true;
+  return wait_mma();
+}
+
+// gW3, gb3 and the loss of the CTA's tiles: warp sums of the per-thread
+// values into s.red (the caller synchronises before reading it).  gW3 goes
+// through a butterfly reduce-scatter: at each of the five levels every lane
+// keeps half of its values and adds the partner's copy of that half, so 62
+// shuffles leave lane l with the warp sums of outputs 2 l and 2 l + 1.
+__device__ __forceinline__ void reduce_output_grads(TcGrad &s, const TileState &ts,
+                                                    float (&gw3)[kH]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 16, half = 32; d >= 1; d >>= 1, half >>= 1) {
+    const bool upper = (lane & d) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float send = upper ? gw3[j] : gw3[j + half];
+      const float keep = upper ? gw3[j + half] : gw3[j];
+      gw3[j] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+    }
+  }
+  s.red[warp][2 * lane] = gw3[0];
+  s.red[warp][2 * lane + 1] = gw3[1];
+  float gb3 = ts.gb3, loss = ts.loss;
+  for (int d = 16; d > 0; d >>= 1) {
+    gb3 += __shfl_xor_sync(0xffffffffu, gb3, d);
+    loss += __shfl_xor_sync(0xffffffffu, loss, d);
+  }
+  if (lane == 0) { s.red[warp][kH] = gb3; s.red[warp][kH + 1] = loss; }
+}
+
 // Loss sum_i w_i (f(x_i) - y_i)^2 / wsum over samples [0, n) and its gradient
 // (added into grad, zeroed by the caller) with tcgen05, 128 samples per tile and
-// two tiles in flight per CTA.  Tensor memory (512 columns), group g:
-// Z1 in [128 g, 128 g + 64), Z2 and later dH1 in [128 g + 64, 128 g + 128),
-// and its weight-gradient accumulators across tiles in [256 + 112 g,
-// 256 + 112 g + 80) (DT x BH: rows o < 64 hold dW2 (cols 0-63) and gb2
-// (col 64)) and [256 + 112 g + 80, 256 + 112 g + 112) (DT x XT: rows i < 64
-// hold dW1 (cols < n_in) and gb1 (col 16)).  Thread r of a group owns
-// sample row r of its tile (its tensor-memory lane); gW3 and gb3 build up in
-// registers and are reduced once at the end.
+// two tile pipelines per CTA (grad_tile); the accumulators are added into
+// grad with atomics at the end.
 __global__ void __launch_bounds__(kGroups * kTM) k_mlp_grad_tc(
     const float *__restrict__ p, int n_in, const float *__restrict__ X,
     const float *__restrict__ Y, const float *__restrict__ Wt, int64_t n, int64_t first,
     float inv_wsum, float *__restrict__ grad, double *__restrict__ loss) {
   extern __shared__ __align__(128) unsigned char raw[];
   TcGrad &s = *reinterpret_cast<TcGrad *>(raw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int g = tid / kTM, r = tid % kTM;         // group and sample row
   TcTile &t = s.t[g];
-  const Params q = split(p, n_in);
-  for (int i = tid; i < kH * kIn; i += kGroups * kTM) {
-    const int rr = i / kIn, c = i % kIn;
-    st_bf16(s.W1, tc::kmaj(rr, c, kIn), c < n_in ? q.W1[rr * n_in + c] : 0.0f);
-  }
-  for (int i = tid; i < kH * kH; i += kGroups * kTM) {
-    const int rr = i / kH, c = i % kH;
-    st_bf16(s.W2, tc::kmaj(rr, c, kH), q.W2[i]);
-    st_bf16(s.W2T, tc::kmaj(c, rr, kH), q.W2[i]);
-  }
-  for (int i = tid; i < kH; i += kGroups * kTM) { s.b1[i] = q.b1[i]; s.b2[i] = q.b2[i]; s.W3[i] = q.W3[i]; }
-  // constant rows of this group's tiles: ones of XT (16) and BH (64), zero padding
-  for (int rr = 0; rr < kNX; ++rr) st_bf16(t.XT, tc::kmaj(rr, r, kTM), rr == 16 ? 1.0f : 0.0f);
-  st_bf16(t.BH, tc::kmaj(kH, r, kTM), 1.0f);
-  for (int rr = kH + 1; rr < kNB; ++rr) st_bf16(t.BH, tc::kmaj(rr, r, kTM), 0.0f);
-  for (int rr = kH; rr < kTM; ++rr) st_bf16(t.DT, tc::kmaj(rr, r, kTM), 0.0f);
-  const float b3 = p[param_count(n_in) - 1];
+  const float b3 = load_weights(s, p, n_in);
+  init_tile_constants(t, r);
   if (warp == 0) tc::tmem_alloc(&s.tmem, 512);
   if (r == 0) { tc::mbar_init(&t.mbar, 1); t.abort = 0; }
+  tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tm = s.tmem;
   const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;   // this warp's lanes
-  const uint32_t cZ1 = 128u * g, cZ2 = cZ1 + 64, cW2 = 256u + 112u * g, cW1 = cW2 + 80;
-  const uint32_t aX = tc::smem_u32(t.X), aW1 = tc::smem_u32(s.W1), aH1 = tc::smem_u32(t.H1);
-  const uint32_t aW2 = tc::smem_u32(s.W2), aW2T = tc::smem_u32(s.W2T), aD2 = tc::smem_u32(t.D2);
-  const uint32_t aDT = tc::smem_u32(t.DT), aBH = tc::smem_u32(t.BH), aXT = tc::smem_u32(t.XT);
-  uint32_t phase = 0;
-  bool pending = false, started = false;
-  float my_loss = 0.0f, my_gb3 = 0.0f, gw3[kH];
+  const uint32_t cW2 = 256u + 112u * g, cW1 = cW2 + 80;
+  TileState ts{0u, false, false, 0.0f, 0.0f};
+  float gw3[kH];
 #pragma unroll
   for (int o = 0; o < kH; ++o) gw3[o] = 0.0f;
-  const float *Xs = X + first * n_in;
-  const float *Ys = Y + first;
-  const float *Ws = Wt + first;
-  auto wait_mma = [&]() {
-    pending = true;
-    if (!tc::mbar_wait(&t.mbar, phase, g_tc_wait_limit)) { atomicOr(&g_tc_timeout, 1); t.abort = 1; }
-    phase ^= 1u;
-    group_sync(g);
-    if (!t.abort) pending = false;
-    tc::fence_after_sync();
-    return !t.abort;
-  };
   for (int64_t base = ((int64_t)blockIdx.x * kGroups + g) * kTM; base < n;
-       base += (int64_t)gridDim.x * kGroups * kTM) {
-    const int64_t row = base + r;
-    const bool valid = row < n;
-    const float yv = valid ? Ys[row] : 0.0f, wv = valid ? Ws[row] : 0.0f;
-    for (int c = 0; c < kIn; ++c) {
-      const float v = (valid && c < n_in) ? Xs[row * n_in + c] : 0.0f;
-      st_bf16(t.X, tc::kmaj(r, c, kIn), v);
-      if (c < n_in) st_bf16(t.XT, tc::kmaj(c, r, kTM), v);
-    }
-    tc::fence_async_smem();
-    group_sync(g);
-    if (r == 0) {
-      tc::fence_after_sync();
-      tc::mma(tm + cZ1, tc::desc(aX, 128, 256), tc::desc(aW1, 128, 256), tc::idesc_bf16(kTM, kH), 0);
-      tc::commit(&t.mbar);
-    }
-    if (!wait_mma()) break;
-    // layer 1: H1 and H1^T
-    float v[16], u[16];
-#pragma unroll 1
-    for (int q4 = 0; q4 < 4; ++q4) {
-      tc::ld16(tm + lb + cZ1 + 16 * q4, v);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int o = 16 * q4 + c;
-        const float h = silu(v[c] + s.b1[o]);
-        st_bf16(t.H1, tc::kmaj(r, o, kH), h);
-        st_bf16(t.BH, tc::kmaj(o, r, kTM), h);
-      }
-    }
-    tc::fence_before_sync();
-    tc::fence_async_smem();
-    group_sync(g);
-    if (r == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int kk = 0; kk < kH / 16; ++kk)
-        tc::mma(tm + cZ2, tc::desc(aH1 + 256 * kk, 128, 1024), tc::desc(aW2 + 256 * kk, 128, 1024),
-                tc::idesc_bf16(kTM, kH), kk > 0);
-      tc::commit(&t.mbar);
-    }
-    if (!wait_mma()) break;
-    // layer 2 and the output: f, the loss, dL/df; then dL/dz2 and gW3
-    float f = b3;
-#pragma unroll 1
-    for (int q4 = 0; q4 < 4; ++q4) {
-      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) f += silu(v[c] + s.b2[16 * q4 + c]) * s.W3[16 * q4 + c];
-    }
-    const float e = f - yv;
-    const float dy = 2.0f * wv * e * inv_wsum;
-    my_loss += wv * e * e * inv_wsum;
-    my_gb3 += dy;
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) {
-      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int o = 16 * q4 + c;
-        const float z2 = v[c] + s.b2[o];
-        gw3[o] += dy * silu(z2);
-        const float d2 = dy * s.W3[o] * dsilu(z2);
-        st_bf16(t.D2, tc::kmaj(r, o, kH), d2);
-        st_bf16(t.DT, tc::kmaj(o, r, kTM), d2);
-      }
-    }
-    tc::fence_before_sync();
-    tc::fence_async_smem();
-    group_sync(g);
-    if (r == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int kk = 0; kk < kH / 16; ++kk)           // dH1 = D2 W2 (over Z2's columns)
-        tc::mma(tm + cZ2, tc::desc(aD2 + 256 * kk, 128, 1024), tc::desc(aW2T + 256 * kk, 128, 1024),
-                tc::idesc_bf16(kTM, kH), kk > 0);
-#pragma unroll
-      for (int kk = 0; kk < kTM / 16; ++kk)          // [dW2 | gb2] += DT BH
-        tc::mma(tm + cW2, tc::desc(aDT + 256 * kk, 128, 2048), tc::desc(aBH + 256 * kk, 128, 2048),
-                tc::idesc_bf16(kTM, kNB), (started || kk > 0) ? 1u : 0u);
-      tc::commit(&t.mbar);
-    }
-    if (!wait_mma()) break;
-    // dL/dz1 = dH1 * silu'(z1) -> DT rows [0, 64)
-#pragma unroll 1
-    for (int q4 = 0; q4 < 4; ++q4) {
-      tc::ld16(tm + lb + cZ2 + 16 * q4, v);
-      tc::ld16(tm + lb + cZ1 + 16 * q4, u);
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int i = 16 * q4 + c;
-        st_bf16(t.DT, tc::kmaj(i, r, kTM), v[c] * dsilu(u[c] + s.b1[i]));
-      }
-    }
-    tc::fence_before_sync();
-    tc::fence_async_smem();
-    group_sync(g);
-    if (r == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int kk = 0; kk < kTM / 16; ++kk)          // [dW1 | gb1] += DT XT
-        tc::mma(tm + cW1, tc::desc(aDT + 256 * kk, 128, 2048), tc::desc(aXT + 256 * kk, 128, 2048),
-                tc::idesc_bf16(kTM, kNX), (started || kk > 0) ? 1u : 0u);
-      tc::commit(&t.mbar);
-    }
-    started = true;
-    if (!wait_mma()) break;
-  }
-  if (pending) tc::mbar_wait(&t.mbar, phase ^ 1u, kMbarTries);
-  // gW3, gb3 and the loss: warp sums into shared memory, then one pass
-#pragma unroll
-  for (int o = 0; o < kH; ++o) {
-    float a = gw3[o];
-    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
-    if (lane == 0) s.red[warp][o] = a;
-  }
-  for (int d = 16; d > 0; d >>= 1) {
-    my_gb3 += __shfl_xor_sync(0xffffffffu, my_gb3, d);
-    my_loss += __shfl_xor_sync(0xffffffffu, my_loss, d);
-  }
-  if (lane == 0) { s.red[warp][kH] = my_gb3; s.red[warp][kH + 1] = my_loss; }
+       base += (int64_t)gridDim.x * kGroups * kTM)
+    if (!grad_tile(s, t, g, r, tm, lb, X + first * n_in, Y + first, Wt + first, n_in, n,
+                   base + r, b3, inv_wsum, ts, gw3))
+      break;
+  if (ts.pending) tc::mbar_wait(&t.mbar, ts.phase ^ 1u, kMbarTries);
+  reduce_output_grads(s, ts, gw3);
   __syncthreads();
   const bool ok = !s.t[0].abort && !s.t[1].abort;
   float *gW1 = grad, *gb1 = gW1 + kH * n_in, *gW2 = gb1 + kH, *gb2 = gW2 + kH * kH;
@@ -404,7 +505,7 @@ __global__ void __launch_bounds__(kGroups * kTM) k_mlp_grad_tc(
     else if (tid == kH) atomicAdd(gb3, a);
     else atomicAdd(loss, (double)a);
   }
-  if (ok && started && (warp & 3) < 2) {
+  if (ok && ts.started && (warp & 3) < 2) {
     // this group's accumulators: lanes 0-63 are warps 0, 1 of the group
     tc::fence_after_sync();
     const int o = r;                                  // 0..63
@@ -434,18 +535,232 @@ __global__ void __launch_bounds__(kGroups * kTM) k_mlp_grad_tc(
   }
 }
 
-// Adam (Kingma & Ba): FP32 master weights and moments.
-__global__ void k_adam(int64_t np, float *__restrict__ p, float *__restrict__ m,
-                       float *__restrict__ v, const float *__restrict__ g, float lr, float b1,
-                       float b2, float eps, float c1, float c2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+// ---- a whole fit in one launch ----------------------------------------------
+
+// Arguments of k_mlp_train_tc.
+struct TrainArgs {
+  const float *X, *Y, *W;        // compacted samples [n][n_in], targets, weights
+  int64_t n_samples;             // minibatch b: samples [b batch, min(n, (b + 1) batch))
+  int batch;
+  const float *inv_wsum;         // [n_steps] 1 / its weight sum
+  int n_in, n_steps, epochs;
+  int np, np_pad;                // parameters; row length of part (multiple of 4)
+  float *p, *m, *v;              // FP32 master weights, Adam moments
+  float *part;                   // [gridDim.x][np_pad] per-CTA gradients of a step
+  double *losses;                // [2 n_steps]: loss per minibatch, first and last epoch
+  unsigned long long *bar;       // grid-barrier arrivals (zero at launch)
+  int *err;                      // set when a wait gives up; every CTA then leaves
+  float lr;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over the CTAs of a cooperative launch (all co-resident): every CTA
+// adds one arrival, then waits until `target` arrivals (the k-th barrier of
+// the launch waits for k x gridDim.x).  Bounded: a CTA gives up after `limit`
+// polls (setting *err), and leaves at once once another CTA has given up.
+// Returns false in both cases.
+__device__ bool grid_barrier(unsigned long long *bar, int *err, unsigned long long target,
+                             int limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // release: the CTA's writes (ordered before this thread by the barrier
+    // above) become visible before the arrival; acquire on the polls
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;\n" : : "l"(bar), "l"(1ull) : "memory");
+    int ok = 0;
+    for (int i = 0; i < limit; ++i) {
+      if (ld_acquire_u64(bar) >= target) { ok = 1; break; }
+      if (*reinterpret_cast<volatile int *>(err)) break;
+      if (i > 64) __nanosleep(32);
+    }
+    if (!ok) { atomicOr(err, 1); atomicOr(&g_tc_timeout, 1); }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole training of a fit in one persistent cooperative launch: for every
+// minibatch of every epoch, (1) every CTA converts the FP32 master weights to
+// its BF16 operands, (2) each of its two tile pipelines runs its tiles of the
+// minibatch (tile j of the step goes to pipeline j mod (2 x gridDim.x)) with
+// the weight gradients accumulating in tensor memory, (3) the CTA writes its
+// gradient to its row of `part` with plain stores, (4) grid barrier, (5) CTA c
+// sums the rows of its slice of the parameters in CTA order and applies Adam
+// to it, (6) grid barrier.  The sums have a fixed order, so a fit is
+// reproducible bit for bit.  The algorithm is the one of the per-minibatch
+// kernel (k_mlp_grad_tc) and Adam (Kingma & Ba) on FP32 master weights;
+// only the per-minibatch launches and the gradient atomics are gone.
+__global__ void __launch_bounds__(kGroups * kTM) k_mlp_train_tc(const TrainArgs A) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  TcGrad &s = *reinterpret_cast<TcGrad *>(raw);
+  __shared__ float s_acc[kGroups * kTM];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = tid / kTM, r = tid % kTM;
+  const int G = gridDim.x, n_in = A.n_in;
+  TcTile &t = s.t[g];
+  init_tile_constants(t, r);
+  if (warp == 0) tc::tmem_alloc(&s.tmem, 512);
+  if (r == 0) { tc::mbar_init(&t.mbar, 1); t.abort = 0; }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = s.tmem;
+  const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t cW2 = 256u + 112u * g, cW1 = cW2 + 80;
+  // parameter offsets (flat layout W1, b1, W2, b2, W3, b3)
+  const int oW1 = 0, ob1 = kH * n_in, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+            ob3 = oW3 + kH;
+  // this CTA's slice of the parameters for the reduction and Adam
+  const int PS = (A.np + G - 1) / G;
+  const int slice0 = blockIdx.x * PS, nslice = max(0, min(PS, A.np - slice0));
+  float *my_part = A.part + (size_t)blockIdx.x * A.np_pad;
+  TileState ts{0u, false, false, 0.0f, 0.0f};
+  const int total = A.epochs * A.n_steps;
+  unsigned long long arrivals = 0;
+  for (int k = 0; k < total; ++k) {
+    const int b = k % A.n_steps, ep = k / A.n_steps;
+    // (1) operands from the master weights (the previous step's Adam)
+    const float b3 = load_weights(s, A.p, n_in);
+    tc::fence_async_smem();
+    __syncthreads();
+    // (2) this pipeline's tiles of minibatch b
+    ts.started = false;
+    ts.loss = 0.0f;
+    ts.gb3 = 0.0f;
+    float gw3[kH];
+#pragma unroll
+    for (int o = 0; o < kH; ++o) gw3[o] = 0.0f;
+    const int64_t f0 = (int64_t)b * A.batch, cnt = min((int64_t)A.batch, A.n_samples - f0);
+    const float inv = A.inv_wsum[b];
+    for (int64_t base = ((int64_t)blockIdx.x * kGroups + g) * kTM; base < cnt;
+         base += (int64_t)G * kGroups * kTM)
+      if (!grad_tile(s, t, g, r, tm, lb, A.X + f0 * n_in, A.Y + f0, A.W + f0, n_in, cnt,
+                     base + r, b3, inv, ts, gw3))
+        break;
+    // (3) the CTA's gradient: gW3, gb3 (and the loss) from registers, the
+    // rest from both pipelines' tensor-memory accumulators; pipeline 1 hands
+    // its part to pipeline 0 through shared memory
+    reduce_output_grads(s, ts, gw3);
+    __syncthreads();
+    if (s.t[0].abort || s.t[1].abort) {
+      if (tid == 0) atomicOr(A.err, 1);
+      break;
+    }
+    if (tid <= kH) {
+      float a = 0.0f;
+      for (int w = 0; w < kGroups * 4; ++w) a += s.red[w][tid];
+      my_part[tid < kH ? oW3 + tid : ob3] = a;
+    } else if (tid == kH + 1 && (ep == 0 || ep == A.epochs - 1)) {
+      float a = 0.0f;
+      for (int w = 0; w < kGroups * 4; ++w) a += s.red[w][kH + 1];
+      atomicAdd(&A.losses[(ep == 0 ? 0 : A.n_steps) + b], (double)a);
+    }
+    // row o of a pipeline's accumulators: dW2[o][0..63], gb2[o] (column 64),
+    // dW1[o][0..15], gb1[o] (column 16 of the second block) -> 82 values
+    constexpr int kX = kH + 18;
+    float *xo = s.xch + (size_t)r * kX;
+    if ((warp & 3) < 2) {
+      float v[16];
+      tc::fence_after_sync();
+      if (g == 1) {
+#pragma unroll
+        for (int q4 = 0; q4 < 5; ++q4) {
+          if (ts.started) tc::ld16(tm + lb + cW2 + 16 * q4, v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (16 * q4 + c <= kH) xo[16 * q4 + c] = ts.started ? v[c] : 0.0f;
+        }
+        if (ts.started) tc::ld16(tm + lb + cW1, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) xo[kH + 1 + c] = ts.started ? v[c] : 0.0f;
+        if (ts.started) tc::ld16(tm + lb + cW1 + 16, v);
+        xo[kH + 17] = ts.started ? v[0] : 0.0f;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (g == 0 && (warp & 3) < 2) {
+      float v[16];
+      tc::fence_after_sync();
+      const int o = r;
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {              // dW2 row o: four float4 per block
+        if (ts.started) tc::ld16(tm + lb + cW2 + 16 * q4, v);
+        float4 *dst = reinterpret_cast<float4 *>(my_part + oW2 + o * kH + 16 * q4);
+#pragma unroll
+        for (int c = 0; c < 16; c += 4)
+          dst[c / 4] = make_float4((ts.started ? v[c] : 0.0f) + xo[16 * q4 + c],
+                                   (ts.started ? v[c + 1] : 0.0f) + xo[16 * q4 + c + 1],
+                                   (ts.started ? v[c + 2] : 0.0f) + xo[16 * q4 + c + 2],
+                                   (ts.started ? v[c + 3] : 0.0f) + xo[16 * q4 + c + 3]);
+      }
+      if (ts.started) tc::ld16(tm + lb + cW2 + 64, v);
+      my_part[ob2 + o] = (ts.started ? v[0] : 0.0f) + xo[kH];
+      if (ts.started) tc::ld16(tm + lb + cW1, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < n_in) my_part[oW1 + o * n_in + c] = (ts.started ? v[c] : 0.0f) + xo[kH + 1 + c];
+      if (ts.started) tc::ld16(tm + lb + cW1 + 16, v);
+      my_part[ob1 + o] = (ts.started ? v[0] : 0.0f) + xo[kH + 17];
+    }
+    tc::fence_before_sync();
+    // (4) every CTA's gradient is in part
+    arrivals += (unsigned long long)G;
+    if (!grid_barrier(A.bar, A.err, arrivals, g_tc_wait_limit)) break;
+    tc::fence_after_sync();
+    // (5) sum over CTAs (fixed order) and Adam on this CTA's slice
+    {
+      const float b1 = 0.9f, b2 = 0.999f;
+      const float c1 = 1.f - powf(b1, (float)(k + 1)), c2 = 1.f - powf(b2, (float)(k + 1));
+      const int nt = kGroups * kTM;
+      for (int c0 = 0; c0 < nslice; c0 += nt) {
+        const int nc = min(nt, nslice - c0);
+        const int R = max(1, nt / nc);             // threads per parameter
+        float acc = 0.0f;
+        if (tid < nc * R) {
+          // this thread's CTAs rr, rr + R, ... in order, up to 24 loads in flight
+          const int pl = tid / R, rr = tid % R;
+          const float *col = A.part + slice0 + c0 + pl;
+          for (int src = rr; src < G; src += 24 * R) {
+            float buf[24];
+#pragma unroll
+            for (int j = 0; j < 24; ++j)
+              buf[j] = src + j * R < G ? __ldcg(col + (size_t)(src + j * R) * A.np_pad) : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 24; ++j) acc += buf[j];
+          }
+        }
+        s_acc[tid] = acc;
+        __syncthreads();
+        if (tid < nc) {
+          float gi = 0.0f;
+          for (int rr = 0; rr < R; ++rr) gi += s_acc[tid * R + rr];
+          const int i = slice0 + c0 + tid;
+          const float mi = b1 * A.m[i] + (1.f - b1) * gi;
+          const float vi = b2 * A.v[i] + (1.f - b2) * gi * gi;
+          A.m[i] = mi;
+          A.v[i] = vi;
+          A.p[i] -= A.lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+        }
+        __syncthreads();
+      }
+    }
+    // (6) every slice is updated
+    arrivals += (unsigned long long)G;
+    if (!grid_barrier(A.bar, A.err, arrivals, g_tc_wait_limit)) break;
+  }
+  if (ts.pending) tc::mbar_wait(&t.mbar, ts.phase ^ 1u, kMbarTries);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tm, 512);
   }
 }
 
@@ -456,6 +771,9 @@ size_t mlp_smem_bytes() { return sizeof(TcGrad); }
 cudaError_t mlp_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(TcGrad));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TcGrad));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(TcFwd));
@@ -475,14 +793,6 @@ cudaError_t launch_mlp_forward(cudaStream_t st, int sms, const float *p, int n_i
   const int64_t tiles = (n + kTM - 1) / kTM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 2));
   k_mlp_forward_tc<<<grid, kTM, sizeof(TcFwd), st>>>(p, n_in, X, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adam(cudaStream_t st, int64_t np, float *p, float *m, float *v, const float *g,
-                        float lr, int64_t t) {
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-  k_adam<<<(int)((np + 255) / 256), 256, 0, st>>>(np, p, m, v, g, lr, b1, b2, 1e-8f, c1, c2);
   return cudaGetLastError();
 }
 
@@ -555,6 +865,24 @@ __global__ void k_normalize_targets(int64_t n, float *__restrict__ Y, const floa
     if (W[s] > 0.0f) Y[s] = (float)((Y[s] - mu) / sd);
 }
 
+// 1 / (sum of the weights of minibatch b), one block per minibatch (FP64 sums)
+__global__ void k_minibatch_inv(int64_t n, int batch, const float *__restrict__ W,
+                                float *__restrict__ inv) {
+  __shared__ double part[32];
+  const int64_t f0 = (int64_t)blockIdx.x * batch;
+  const int64_t f1 = f0 + batch < n ? f0 + batch : n;
+  double a = 0.0;
+  for (int64_t i = f0 + threadIdx.x; i < f1; i += blockDim.x) a += W[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    inv[blockIdx.x] = t > 0.0 ? (float)(1.0 / t) : 0.0f;
+  }
+}
+
 // the scored samples only (weight > 0), in their order: flags, then a gather
 // at the exclusive prefix sum of the flags
 __global__ void k_sample_flags(int64_t n, const float *__restrict__ W, int32_t *__restrict__ flag) {
@@ -574,26 +902,6 @@ __global__ void k_sample_gather(int64_t n, int n_in, const float *__restrict__ X
     for (int k = 0; k < n_in; ++k) Xc[d * n_in + k] = X[s * n_in + k];
     Yc[d] = Y[s];
     Wc[d] = W[s];
-  }
-}
-
-__global__ void k_step_counter(int64_t *t) { *t += 1; }
-
-// Adam whose step count lives on the device (so a captured epoch can be
-// replayed): c1 = 1 - b1^t, c2 = 1 - b2^t.
-__global__ void k_adam_dev(int64_t np, float *__restrict__ p, float *__restrict__ m,
-                           float *__restrict__ v, const float *__restrict__ g, float lr,
-                           const int64_t *__restrict__ t) {
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)*t), c2 = 1.f - powf(b2, (float)*t);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
   }
 }
 
@@ -790,6 +1098,23 @@ cudaError_t as_device(const T *p, size_t count, const T **out, void **keep) {
   return cudaSuccess;
 }
 
+// Temporaries of one call from a stream-ordered pool (plain cudaMalloc where
+// there is none), freed in the stream's order when the object goes away.
+struct PoolBufs {
+  cudaMemPool_t pool;
+  cudaStream_t s;
+  std::vector<void *> v;
+  template <class T>
+  cudaError_t get(T **p, size_t count) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, s) : cudaMalloc(&q, bytes);
+    if (e == cudaSuccess) { v.push_back(q); *p = (T *)q; }
+    return e;
+  }
+  ~PoolBufs() { for (void *q : v) { if (pool) cudaFreeAsync(q, s); else cudaFree(q); } }
+};
+
 struct Frees {
   std::vector<void *> v;
   ~Frees() { for (void *p : v) if (p) cudaFree(p); }
@@ -915,31 +1240,44 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   void *k;
   CKM(as_device(pilot_mean, (size_t)nb, &dmean, &k)); fr.add(k);
   if (pilot_relerr) { CKM(as_device(pilot_relerr, (size_t)nb, &drel, &k)); fr.add(k); }
-  float *X, *Y, *W, *pred, *prm, *m, *v, *g;
+  cudaEvent_t e0, e1, e2;
+  CKM(cudaEventCreate(&e0)); CKM(cudaEventCreate(&e1)); CKM(cudaEventCreate(&e2));
+  cudaStream_t st;
+  CKM(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  struct Cleanup {
+    cudaStream_t s; cudaEvent_t a, b, c;
+    ~Cleanup() {
+      cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c);
+      cudaStreamDestroy(s);
+    }
+  } cl{st, e0, e1, e2};
+  // temporaries from the device's stream-ordered pool on the training
+  // stream (freed in stream order when the call returns), so repeated fits
+  // pay no driver allocation
+  PoolBufs tmp{device_mem_pool(pr->device), st, {}};
+  float *X, *Y, *W, *pred, *prm, *m, *v;
   double *mom, *losses;
-  int64_t *tstep;
   unsigned long long *mx;
-  CKM(cudaMalloc(&X, sizeof(float) * nb * n_in)); fr.add(X);
-  CKM(cudaMalloc(&Y, sizeof(float) * nb)); fr.add(Y);
-  CKM(cudaMalloc(&W, sizeof(float) * nb)); fr.add(W);
-  CKM(cudaMalloc(&pred, sizeof(float) * nb)); fr.add(pred);
-  CKM(cudaMalloc(&prm, sizeof(float) * np)); fr.add(prm);
-  CKM(cudaMalloc(&m, sizeof(float) * np)); fr.add(m);
-  CKM(cudaMalloc(&v, sizeof(float) * np)); fr.add(v);
-  CKM(cudaMalloc(&g, sizeof(float) * np)); fr.add(g);
-  CKM(cudaMalloc(&mom, sizeof(double) * 8)); fr.add(mom);
-  CKM(cudaMalloc(&tstep, sizeof(int64_t))); fr.add(tstep);
-  CKM(cudaMalloc(&mx, 3 * sizeof(unsigned long long))); fr.add(mx);
+  const int np_pad = (int)((np + 3) & ~3ll);
+  CKM(tmp.get(&X, (size_t)nb * n_in));
+  CKM(tmp.get(&Y, (size_t)nb));
+  CKM(tmp.get(&W, (size_t)nb));
+  CKM(tmp.get(&pred, (size_t)nb));
+  CKM(tmp.get(&prm, (size_t)np_pad));
+  CKM(tmp.get(&m, (size_t)np));
+  CKM(tmp.get(&v, (size_t)np));
+  CKM(tmp.get(&mom, 8));
+  CKM(tmp.get(&mx, 3));
   const int64_t steps_per_epoch = (nb + o.batch - 1) / o.batch;
-  CKM(cudaMalloc(&losses, sizeof(double) * steps_per_epoch * 2)); fr.add(losses);
+  CKM(tmp.get(&losses, (size_t)steps_per_epoch * 2));
 
   // parameters: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
   std::vector<float> h(np, 0.0f);
   {
-    uint64_t st = o.seed * 0x9E3779B97F4A7C15ull + 12345;
+    uint64_t sd = o.seed * 0x9E3779B97F4A7C15ull + 12345;
     auto unif = [&]() {   // splitmix64 -> (0, 1)
-      st += 0x9E3779B97F4A7C15ull;
-      uint64_t z = st;
+      sd += 0x9E3779B97F4A7C15ull;
+      uint64_t z = sd;
       z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
       z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
       z ^= z >> 31;
@@ -953,19 +1291,6 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     off += (int64_t)kH * kH + kH;
     for (int64_t i = 0; i < kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
   }
-  cudaEvent_t e0, e1, e2;
-  CKM(cudaEventCreate(&e0)); CKM(cudaEventCreate(&e1)); CKM(cudaEventCreate(&e2));
-  cudaStream_t st;
-  CKM(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  struct Cleanup {
-    cudaStream_t s; cudaEvent_t a, b, c; cudaGraph_t gr = nullptr; cudaGraphExec_t ex = nullptr;
-    ~Cleanup() {
-      if (ex) cudaGraphExecDestroy(ex);
-      if (gr) cudaGraphDestroy(gr);
-      cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c);
-      cudaStreamDestroy(s);
-    }
-  } cl{st, e0, e1, e2};
   const int sms = pr->sms;
   const uint64_t stride = coprime_stride((uint64_t)nb);
   CKM(mlp_prepare());
@@ -974,80 +1299,94 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   CKM(cudaMemsetAsync(m, 0, sizeof(float) * np, st));
   CKM(cudaMemsetAsync(v, 0, sizeof(float) * np, st));
   CKM(cudaMemsetAsync(mom, 0, sizeof(double) * 8, st));
-  CKM(cudaMemsetAsync(tstep, 0, sizeof(int64_t), st));
   CKM(cudaMemsetAsync(losses, 0, sizeof(double) * steps_per_epoch * 2, st));
   const int blocks = sms * 8;
   k_make_samples<<<blocks, 256, 0, st>>>(P, n_in, stride, dmean, drel, X, Y, W, mom);
   CKM(cudaGetLastError());
   k_normalize_targets<<<blocks, 256, 0, st>>>(nb, Y, W, mom);
   CKM(cudaGetLastError());
-  double hmom[8];
-  CKM(cudaMemcpyAsync(hmom, mom, sizeof(hmom), cudaMemcpyDeviceToHost, st));
-  CKM(cudaStreamSynchronize(st));
-  if (!(hmom[0] > 0.0)) return fail(MCDC_ERR_INVALID, "the pilot tally scored no bin");
   // training set: the scored bins only, compacted in sample order (the
   // others carry zero weight and would only cost time)
   int32_t *flag, *pos;
   float *Xc, *Yc, *Wc;
   void *scan_tmp = nullptr;
   size_t scan_bytes = 0;
-  CKM(cudaMalloc(&flag, sizeof(int32_t) * nb)); fr.add(flag);
-  CKM(cudaMalloc(&pos, sizeof(int32_t) * nb)); fr.add(pos);
+  CKM(tmp.get(&flag, (size_t)nb));
+  CKM(tmp.get(&pos, (size_t)nb));
   CKM(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, flag, pos, nb, st));
-  CKM(cudaMalloc(&scan_tmp, scan_bytes)); fr.add(scan_tmp);
+  CKM(tmp.get((unsigned char **)&scan_tmp, scan_bytes));
   k_sample_flags<<<blocks, 256, 0, st>>>(nb, W, flag);
   CKM(cudaGetLastError());
   CKM(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, flag, pos, nb, st));
+  // one round trip: the target moments and the number of scored bins
+  double hmom[8];
   int32_t last[2];
+  CKM(cudaMemcpyAsync(hmom, mom, sizeof(hmom), cudaMemcpyDeviceToHost, st));
   CKM(cudaMemcpyAsync(&last[0], pos + nb - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CKM(cudaMemcpyAsync(&last[1], flag + nb - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CKM(cudaStreamSynchronize(st));
+  if (!(hmom[0] > 0.0)) return fail(MCDC_ERR_INVALID, "the pilot tally scored no bin");
   const int64_t n_samples = (int64_t)last[0] + last[1];
-  CKM(cudaMalloc(&Xc, sizeof(float) * std::max<int64_t>(1, n_samples) * n_in)); fr.add(Xc);
-  CKM(cudaMalloc(&Yc, sizeof(float) * std::max<int64_t>(1, n_samples))); fr.add(Yc);
-  CKM(cudaMalloc(&Wc, sizeof(float) * std::max<int64_t>(1, n_samples))); fr.add(Wc);
+  CKM(tmp.get(&Xc, (size_t)std::max<int64_t>(1, n_samples) * n_in));
+  CKM(tmp.get(&Yc, (size_t)std::max<int64_t>(1, n_samples)));
+  CKM(tmp.get(&Wc, (size_t)std::max<int64_t>(1, n_samples)));
   k_sample_gather<<<blocks, 256, 0, st>>>(nb, n_in, X, Y, W, flag, pos, Xc, Yc, Wc);
   CKM(cudaGetLastError());
-  // per-minibatch weight sums (host side, from the device weights)
-  const int64_t steps_used = (n_samples + o.batch - 1) / o.batch;
-  std::vector<float> hw(std::max<int64_t>(1, n_samples));
-  CKM(cudaMemcpyAsync(hw.data(), Wc, sizeof(float) * n_samples, cudaMemcpyDeviceToHost, st));
-  CKM(cudaStreamSynchronize(st));
-  std::vector<float> inv(steps_per_epoch, 0.0f);
-  for (int64_t b = 0; b < steps_used; ++b) {
-    double ws = 0.0;
-    for (int64_t i = b * o.batch; i < std::min<int64_t>(n_samples, (b + 1) * o.batch); ++i)
-      ws += hw[i];
-    inv[b] = ws > 0.0 ? (float)(1.0 / ws) : 0.0f;
+  // minibatch b is samples [b batch, (b + 1) batch); every compacted sample
+  // has positive weight, so every minibatch has a positive weight sum
+  const int n_steps = (int)((n_samples + o.batch - 1) / o.batch);
+  float *d_inv;
+  CKM(tmp.get(&d_inv, (size_t)std::max(1, n_steps)));
+  if (n_steps > 0) {
+    k_minibatch_inv<<<n_steps, 256, 0, st>>>(n_samples, o.batch, Wc, d_inv);
+    CKM(cudaGetLastError());
   }
-  // one epoch as a CUDA graph: per minibatch zero the gradient, forward and
-  // backward on the tensor cores, count the step, Adam
-  CKM(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  for (int64_t b = 0; b < steps_used; ++b) {
-    if (inv[b] == 0.0f) continue;
-    const int64_t first = b * o.batch, cnt = std::min<int64_t>(o.batch, n_samples - first);
-    cudaMemsetAsync(g, 0, sizeof(float) * np, st);
-    launch_mlp_grad(st, sms, prm, n_in, Xc, Yc, Wc, cnt, first, inv[b], g, losses + b);
-    k_step_counter<<<1, 1, 0, st>>>(tstep);
-    k_adam_dev<<<(int)((np + 255) / 256), 256, 0, st>>>(np, prm, m, v, g, (float)o.lr, tstep);
-  }
-  CKM(cudaStreamEndCapture(st, &cl.gr));
-  CKM(cudaGraphInstantiate(&cl.ex, cl.gr, 0));
+  // the whole training in one cooperative launch (k_mlp_train_tc): one CTA
+  // per SM at most, and no more than the two tile pipelines per CTA that
+  // cover a minibatch in one round
+  int occ = 0;
+  CKM(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_train_tc, kGroups * kTM,
+                                                     sizeof(TcGrad)));
+  if (occ < 1) return fail(MCDC_ERR_CUDA, "the training kernel does not fit on an SM");
+  const int64_t tiles = (o.batch + kTM - 1) / kTM;
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * occ, (tiles + kGroups - 1) / kGroups));
+  int32_t *d_err;
+  float *part;
+  unsigned long long *d_bar;
+  CKM(tmp.get(&part, (size_t)grid * np_pad));
+  CKM(tmp.get(&d_bar, 1));
+  CKM(tmp.get(&d_err, 1));
+  CKM(cudaMemsetAsync(d_bar, 0, sizeof(unsigned long long), st));
+  CKM(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
   double loss_first = 0.0, loss_last = 0.0;
-  std::vector<double> hl(steps_per_epoch);
   int32_t steps = 0;
-  for (int ep = 0; ep < o.epochs; ++ep) {
-    CKM(cudaMemsetAsync(losses, 0, sizeof(double) * steps_per_epoch, st));
-    CKM(cudaGraphLaunch(cl.ex, st));
-    if (ep == 0 || ep == o.epochs - 1) {
-      CKM(cudaMemcpyAsync(hl.data(), losses, sizeof(double) * steps_per_epoch, cudaMemcpyDeviceToHost, st));
-      CKM(cudaStreamSynchronize(st));
-      double s = 0.0, c = 0.0;
-      for (int64_t b = 0; b < steps_per_epoch; ++b)
-        if (inv[b] != 0.0f) { s += hl[b]; c += 1.0; }
-      (ep == 0 ? loss_first : loss_last) = c > 0 ? s / c : 0.0;
+  if (n_steps > 0) {
+    TrainArgs ta{};
+    ta.X = Xc; ta.Y = Yc; ta.W = Wc;
+    ta.n_samples = n_samples; ta.batch = o.batch; ta.inv_wsum = d_inv;
+    ta.n_in = n_in; ta.n_steps = n_steps; ta.epochs = o.epochs;
+    ta.np = (int)np; ta.np_pad = np_pad;
+    ta.p = prm; ta.m = m; ta.v = v;
+    ta.part = part; ta.losses = losses; ta.bar = d_bar; ta.err = d_err;
+    ta.lr = (float)o.lr;
+    void *kargs[] = {&ta};
+    CKM(cudaLaunchCooperativeKernel((const void *)k_mlp_train_tc, dim3(grid), dim3(kGroups * kTM),
+                                    kargs, sizeof(TcGrad), st));
+    std::vector<double> hl(2 * (size_t)n_steps);
+    int32_t herr = 0;
+    CKM(cudaMemcpyAsync(hl.data(), losses, sizeof(double) * 2 * n_steps, cudaMemcpyDeviceToHost, st));
+    CKM(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CKM(cudaStreamSynchronize(st));
+    if (herr) {
+      tc_status();
+      return fail(MCDC_ERR_TIMEOUT, "a wait in the training kernel ran out (importance network)");
     }
-    for (int64_t b = 0; b < steps_per_epoch; ++b) steps += inv[b] != 0.0f;
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = 0; b < n_steps; ++b) { s0 += hl[b]; s1 += hl[n_steps + b]; }
+    loss_first = s0 / n_steps;
+    loss_last = o.epochs > 1 ? s1 / n_steps : loss_first;
+    steps = n_steps * o.epochs;
   }
   CKM(cudaEventRecord(e1, st));
   // bake: predict every bin, weight windows proportional to the predicted flux

@@ -7,7 +7,8 @@
 // 8-row x 16-byte core matrices, element (r, k) of a tile with K columns at
 // byte (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 with
 // SBO = (K / 8) * 128; one MMA consumes K = 16 (two core matrices along K,
-// LBO = 128 bytes apart).
+// LBO = 128 bytes apart).  The same bytes read as an MN-major operand (MN =
+// the column, K = the row) have LBO = SBO above and SBO = 128.
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -37,6 +38,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+
+// instruction-descriptor bits that read A, or B, as an MN-major operand
+// (M, or N, contiguous in 16-byte core-matrix rows).  The matrix descriptor
+// of such an operand carries the byte stride between K groups of 8 rows as
+// its leading offset and the stride between 8-element MN groups as its
+// stride offset (the same fields that hold the K-group and 8-row-group
+// strides of a K-major operand).
+constexpr uint32_t kMnMajorA = 1u << 15;
+constexpr uint32_t kMnMajorB = 1u << 16;
 
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t accumulate) {
