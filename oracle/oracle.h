@@ -136,21 +136,38 @@ void orc_combine(int64_t n, const double *s1x, const double *s2x, const double *
                  const double *s2y, const double *s12, uint64_t n_hist, int32_t B,
                  double vol, double *mean, double *rel, double *alpha);
 
+/* Test hook: RNG-injection quadrature of collision-order-resolved track
+ * lengths (a product rule over chosen draw slots; see transport.c). */
+int orc_inject_grid(const orc_problem *p, int32_t n_slots, const double *fixed, int32_t n_dims,
+                    const int32_t *dim_slot, const int32_t *dim_m, const double *nodes,
+                    const double *weights, int32_t max_order, int32_t threads, double *out);
+
 /* Replays the listed histories one by one and summarises each primary. */
 int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
               int64_t n, orc_record *out);
 
-/* Importance network (mlp.c): in -> H -> H -> 1, SiLU hidden layers. */
+/* Importance network (mlp.c): in -> H -> H -> 1, SiLU hidden layers.
+ * bf16 = 1 rounds every operand of the matrix products to BF16 (the
+ * precision fixed for the network: BF16 weights, FP32 accumulation). */
 int64_t orc_mlp_param_count(int32_t in, int32_t H);
-void orc_mlp_forward(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
+void orc_mlp_forward(int32_t in, int32_t H, int32_t bf16, const double *p, int64_t n,
                      const double *X, double *out);
 /* R15: the network's inputs for a particle at (x, y, z, t) in time bin tbin
  * and group g (see transport.c). */
 void orc_net_features(const orc_problem *p, double x, double y, double z, double t,
                       int32_t tbin, int32_t g, double *f);
-double orc_mlp_loss_grad(int32_t in, int32_t H, int32_t unused, const double *p, int64_t n,
+double orc_mlp_loss_grad(int32_t in, int32_t H, int32_t bf16, const double *p, int64_t n,
                          const double *X, const double *y, const double *w, double *grad);
+/* Test tolerance: first-order bounds of the rounding error of a BF16-operand,
+ * FP32-accumulation evaluation, per output and per gradient element. */
+void orc_mlp_error_bounds(int32_t in, int32_t H, const double *p, int64_t n, const double *X,
+                          const double *y, const double *w, double *f_bound, double *g_bound,
+                          double *loss_bound, double *g_abssum, double *g_absmax);
 void orc_adam_step(int64_t np, double *p, double *m, double *v, const double *g, double lr,
                    double b1, double b2, double eps, int64_t t);
+/* Adam over minibatches of consecutive samples, `epochs` passes (mlp.c). */
+void orc_mlp_train(int32_t in, int32_t H, int32_t bf16, double *p, int64_t n, const double *X,
+                   const double *y, const double *w, int32_t epochs, int32_t batch, double lr,
+                   double *loss_first, double *loss_last);
 
 #endif

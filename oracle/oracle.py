@@ -86,6 +86,14 @@ def lib():
 
 
 def _bind_mlp(L):
+    L.orc_mlp_train.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_mlp_train.restype = None
+    L.orc_mlp_error_bounds.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]
+    L.orc_mlp_error_bounds.restype = None
     L.orc_mlp_param_count.argtypes = [C.c_int32, C.c_int32]
     L.orc_mlp_param_count.restype = C.c_int64
     L.orc_mlp_forward.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
@@ -296,25 +304,48 @@ def mlp_param_count(n_in, hidden=64):
     return int(lib().orc_mlp_param_count(int(n_in), int(hidden)))
 
 
-def mlp_forward(params, X, hidden=64):
+def mlp_forward(params, X, hidden=64, bf16=False):
+    """Network output per sample (FP64; bf16: the matrix products' operands
+    rounded to BF16 first, the precision the network runs in)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     p = np.ascontiguousarray(params, dtype=np.float64)
     out = np.zeros(X.shape[0])
-    lib().orc_mlp_forward(X.shape[1], hidden, 0, p.ctypes.data, X.shape[0], X.ctypes.data,
-                          out.ctypes.data)
+    lib().orc_mlp_forward(X.shape[1], hidden, int(bf16), p.ctypes.data, X.shape[0],
+                          X.ctypes.data, out.ctypes.data)
     return out
 
 
-def mlp_loss_grad(params, X, y, w, hidden=64):
-    """Weighted mean-square loss and its gradient (backpropagation, FP64)."""
+def mlp_loss_grad(params, X, y, w, hidden=64, bf16=False):
+    """Weighted mean-square loss and its gradient (backpropagation, FP64;
+    bf16 as in mlp_forward, the backward products included)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     p = np.ascontiguousarray(params, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     g = np.zeros(p.size)
-    loss = lib().orc_mlp_loss_grad(X.shape[1], hidden, 0, p.ctypes.data, X.shape[0],
+    loss = lib().orc_mlp_loss_grad(X.shape[1], hidden, int(bf16), p.ctypes.data, X.shape[0],
                                    X.ctypes.data, y.ctypes.data, w.ctypes.data, g.ctypes.data)
     return loss, g
+
+
+def mlp_error_bounds(params, X, y, w, hidden=64):
+    """Tolerance of the tensor-core evaluation: first-order bounds of the
+    rounding error of every forward output and every gradient element when
+    every matrix-product operand is rounded to BF16 and sums run in FP32
+    (see orc_mlp_error_bounds).  Returns (f_bound[n], g_bound[np], loss_bound,
+    g_abssum[np], g_absmax[np]): the last two are, per gradient element, the sum
+    and the largest of the absolute values of its per-sample terms."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    fb = np.zeros(X.shape[0])
+    gb, gs, gm = np.zeros(p.size), np.zeros(p.size), np.zeros(p.size)
+    lb = C.c_double()
+    lib().orc_mlp_error_bounds(X.shape[1], hidden, p.ctypes.data, X.shape[0], X.ctypes.data,
+                               y.ctypes.data, w.ctypes.data, fb.ctypes.data, gb.ctypes.data,
+                               C.byref(lb), gs.ctypes.data, gm.ctypes.data)
+    return fb, gb, lb.value, gs, gm
 
 
 def adam_step(p, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
@@ -324,3 +355,46 @@ def adam_step(p, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     g = np.ascontiguousarray(g, dtype=np.float64)
     lib().orc_adam_step(p.size, p.ctypes.data, m.ctypes.data, v.ctypes.data, g.ctypes.data,
                         lr, b1, b2, eps, int(t))
+
+
+def mlp_train(params, X, y, w, epochs, batch, lr, hidden=64, bf16=False):
+    """Adam over minibatches of consecutive samples (see orc_mlp_train);
+    returns (parameters, first-epoch loss, last-epoch loss)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    p = np.array(params, dtype=np.float64, order="C")
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    lf, ll = C.c_double(), C.c_double()
+    lib().orc_mlp_train(X.shape[1], hidden, int(bf16), p.ctypes.data, X.shape[0], X.ctypes.data,
+                        y.ctypes.data, w.ctypes.data, int(epochs), int(batch), float(lr),
+                        C.byref(lf), C.byref(ll))
+    return p, lf.value, ll.value
+
+
+def inject_grid(prob, n_slots, dims, max_order, fixed=None, threads=None):
+    """RNG-injection quadrature (test hook, see orc_inject_grid): the
+    weighted mean, over a product rule on the uniform numbers a history
+    draws, of the track length made after exactly k collisions, k =
+    0..max_order.  dims: list of (slot, nodes, weights), the weights of each
+    rule summing to 1; other slots hold `fixed` (default 0.5)."""
+    L = lib()
+    if not hasattr(L, "_inj_bound"):
+        L.orc_inject_grid.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                      C.c_void_p]
+        L.orc_inject_grid.restype = C.c_int
+        L._inj_bound = True
+    keep = _Keep()
+    st = _struct(prob, None, keep)
+    fx = np.full(n_slots, 0.5) if fixed is None else _f64(fixed)
+    ds = np.ascontiguousarray([d[0] for d in dims], dtype=np.int32)
+    dm = np.ascontiguousarray([len(d[1]) for d in dims], dtype=np.int32)
+    nodes = np.ascontiguousarray(np.concatenate([np.asarray(d[1], float) for d in dims]))
+    wts = np.ascontiguousarray(np.concatenate([np.asarray(d[2], float) for d in dims]))
+    out = np.zeros(max_order + 1)
+    rc = L.orc_inject_grid(C.byref(st), n_slots, fx.ctypes.data, len(dims), ds.ctypes.data,
+                           dm.ctypes.data, nodes.ctypes.data, wts.ctypes.data, int(max_order),
+                           int(threads or os.cpu_count() or 1), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the injection grid")
+    return out

@@ -130,8 +130,25 @@ static void push(stack *s, const part *P)
 /* ---- random numbers (R1) ------------------------------------------- */
 typedef struct { double a, b; } pair;
 
+/* Test hook (orc_inject_grid only): while g_inj is set on a thread, draws
+ * return its numbers in order, two per draw, instead of Philox blocks, and
+ * the track length of every segment is also added to g_order[k], k the
+ * number of collisions the particle has had; a history ends once it would
+ * start a segment of order beyond g_max_order. */
+static __thread const double *g_inj = NULL;
+static __thread int64_t g_inj_n = 0, g_inj_pos = 0;
+static __thread double *g_order = NULL;
+static __thread int32_t g_max_order = 0;
+
 static pair draw(uint64_t seed, uint64_t hid, part *P)
 {
+    if (g_inj) {
+        pair r = { 0.5, 0.5 };
+        if (g_inj_pos + 2 <= g_inj_n) { r.a = g_inj[g_inj_pos]; r.b = g_inj[g_inj_pos + 1]; }
+        g_inj_pos += 2;
+        P->ctr += 1;
+        return r;
+    }
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t ctr[4] = { P->ctr, P->serial, (uint32_t)hid, (uint32_t)(hid >> 32) };
     uint32_t out[4];
@@ -374,6 +391,7 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
         /* track-length tally into (cell, group, time bin) */
         int64_t bin = (cell * G + P->g) * tb->T1 + (p->n_tbin > 0 ? P->tbin : 0);
         if (p->estimator != ORC_EST_COLLISION) tally[bin] += P->w * d;
+        if (g_order) g_order[P->n_col] += P->w * d;          /* test hook */
 
         move_particle(P, d);
 
@@ -411,6 +429,7 @@ static int32_t transport(const orc_problem *p, const tables *tb, uint64_t seed,
             /* collision: absorb or scatter, new group, new direction */
             P->n_col += 1;
             c->collisions += 1;
+            if (g_order && (int32_t)P->n_col > g_max_order) return ORC_END_ABSORBED;  /* test hook */
             if (p->estimator != ORC_EST_TRACK)                                 /* R11, R14 */
                 tally[(p->estimator == ORC_EST_COMBINED ? tb->n_bins : 0) + bin] += P->w / sig_t;
             pair r1 = draw(seed, hid, P);
@@ -802,6 +821,101 @@ int orc_trace(const orc_problem *p, uint64_t seed, const uint64_t *hids,
     for (int64_t i = 0; i < n; ++i)
         run_history(p, &tb, seed, hids[i], tally, &c, &out[i]);
     free(tally);
+    free_tables(&tb);
+    return 0;
+}
+
+
+/* ---- RNG-injection quadrature (test hook) ------------------------------
+ * Averages, over a midpoint grid of the uniform numbers a history draws, the
+ * track length its particles make after exactly k collisions, k = 0 ..
+ * max_order (out[k]).  The history draws the numbers slot by slot (two per
+ * draw, in the order of the loop above); slot dim_slot[d] runs over the
+ * dim_m[d] nodes of its rule (nodes[], weights[], the rules of the
+ * dimensions one after the other, each rule's weights summing to 1), every
+ * other slot holds fixed[slot]; a grid point counts with the product of its
+ * nodes' weights.  On a problem whose histories draw the same slots for the
+ * same events (one cell, no census), out[k] is a product quadrature rule for
+ * the expected order-k track length, which converges to its integral as the
+ * rules are refined.  Threads split the grid. */
+typedef struct {
+    const orc_problem *p;
+    const tables *tb;
+    int32_t n_slots, n_dims, max_order;
+    const double *fixed, *nodes, *weights;
+    const int32_t *dim_slot, *dim_m, *dim_off;
+    int64_t i0, i1;
+    double out[16];
+} inj_job;
+
+static void *inj_work(void *arg)
+{
+    inj_job *J = (inj_job *)arg;
+    double *slots = (double *)malloc(sizeof(double) * J->n_slots);
+    double *tally = (double *)calloc((size_t)J->tb->n_bins * 2, sizeof(double));
+    double order[16];
+    orc_counts c;
+    memset(&c, 0, sizeof c);
+    memcpy(slots, J->fixed, sizeof(double) * J->n_slots);
+    for (int k = 0; k <= J->max_order; ++k) J->out[k] = 0.0;
+    g_inj = slots;
+    g_inj_n = J->n_slots;
+    g_order = order;
+    g_max_order = J->max_order;
+    for (int64_t i = J->i0; i < J->i1; ++i) {
+        int64_t q = i;
+        double wt = 1.0;
+        for (int32_t d = 0; d < J->n_dims; ++d) {
+            const int64_t m = J->dim_m[d], j = q % m;
+            slots[J->dim_slot[d]] = J->nodes[J->dim_off[d] + j];
+            wt *= J->weights[J->dim_off[d] + j];
+            q /= m;
+        }
+        for (int k = 0; k <= J->max_order; ++k) order[k] = 0.0;
+        g_inj_pos = 0;
+        run_history(J->p, J->tb, 0, 0, tally, &c, NULL);
+        for (int k = 0; k <= J->max_order; ++k) J->out[k] += wt * order[k];
+    }
+    g_inj = NULL;
+    g_order = NULL;
+    free(slots);
+    free(tally);
+    return NULL;
+}
+
+int orc_inject_grid(const orc_problem *p, int32_t n_slots, const double *fixed, int32_t n_dims,
+                    const int32_t *dim_slot, const int32_t *dim_m, const double *nodes,
+                    const double *weights, int32_t max_order, int32_t threads, double *out)
+{
+    if (max_order < 0 || max_order > 15 || n_dims < 1 || n_dims > 32 || threads < 1) return -1;
+    tables tb;
+    if (make_tables(p, &tb)) return -1;
+    int64_t total = 1;
+    int32_t off[32];
+    for (int32_t d = 0, o = 0; d < n_dims; ++d) {
+        if (dim_slot[d] < 0 || dim_slot[d] >= n_slots || dim_m[d] < 1) { free_tables(&tb); return -1; }
+        total *= dim_m[d];
+        off[d] = o;
+        o += dim_m[d];
+    }
+    inj_job *jobs = (inj_job *)calloc((size_t)threads, sizeof(inj_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    for (int32_t t = 0; t < threads; ++t) {
+        inj_job *J = &jobs[t];
+        J->p = p; J->tb = &tb; J->n_slots = n_slots; J->n_dims = n_dims;
+        J->max_order = max_order; J->fixed = fixed; J->dim_slot = dim_slot; J->dim_m = dim_m;
+        J->dim_off = off; J->nodes = nodes; J->weights = weights;
+        J->i0 = total * t / threads;
+        J->i1 = total * (t + 1) / threads;
+        pthread_create(&th[t], NULL, inj_work, J);
+    }
+    for (int k = 0; k <= max_order; ++k) out[k] = 0.0;
+    for (int32_t t = 0; t < threads; ++t) {                 /* fixed order of the sums */
+        pthread_join(th[t], NULL);
+        for (int k = 0; k <= max_order; ++k) out[k] += jobs[t].out[k];
+    }
+    free(jobs);
+    free(th);
     free_tables(&tb);
     return 0;
 }
