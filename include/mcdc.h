@@ -388,6 +388,25 @@ int mcdc_mlp_forward(const float *params, int32_t n_in, const float *X, int64_t 
 int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float *X, const float *y,
                        const float *w, int64_t n, float *grad, double *loss);
 
+/* Trains the network on n given samples with the library's training kernel
+ * (the one mcdc_train_importance runs): `epochs` passes of Adam (Kingma &
+ * Ba; step lr, b1 0.9, b2 0.999, eps 1e-8, FP32 master weights and moments)
+ * over minibatches of `batch` consecutive samples (the last one shorter),
+ * each minibatch's loss and gradient as in mcdc_mlp_loss_grad; the whole
+ * fit is one launch whose gradient sums have a fixed order, so it is
+ * reproducible bit for bit.  params (FP32, host or device, the layout of
+ * mcdc_mlp_forward) holds the starting parameters and receives the result;
+ * X [n][n_in], y [n], w [n] (FP32, host or device) are copied.  loss_first,
+ * loss_last (optional): the mean minibatch loss of the first and the last
+ * epoch.  Errors: MCDC_ERR_INVALID (n_in outside 1..16, n < 1 or >= 2^31,
+ * epochs < 1, batch < 64, lr <= 0, a minibatch whose weights sum to zero),
+ * MCDC_ERR_TIMEOUT, MCDC_ERR_OOM, MCDC_ERR_CUDA.  The network has no
+ * counterpart in the paper (the learned importance proposal is this
+ * library's own). */
+int mcdc_mlp_train(float *params, int32_t n_in, const float *X, const float *y, const float *w,
+                   int64_t n, int32_t epochs, int32_t batch, double lr, double *loss_first,
+                   double *loss_last);
+
 /* Tries of the bounded waits on tensor-core completion inside the network's
  * kernels (default 4194304; a negative value restores it).  A wait that runs
  * out makes the kernel stop, await its work in flight, free its tensor

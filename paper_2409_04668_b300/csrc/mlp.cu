@@ -1135,6 +1135,65 @@ int device_sms() {
       return fail(e_ == cudaErrorMemoryAllocation ? MCDC_ERR_OOM : MCDC_ERR_CUDA,        \
                   std::string(#call) + ": " + cudaGetErrorString(e_));                   \
   } while (0)
+// The whole training in one cooperative launch (k_mlp_train_tc) on stream st:
+// n_steps minibatches of `batch` consecutive samples (1 / weight sums in
+// d_inv), epochs passes, Adam on prm (n_in inputs; np_pad-padded), m, v;
+// losses [2 n_steps] zeroed by the caller.  One CTA per SM at most, and no
+// more than the two tile pipelines per CTA that cover a minibatch in one
+// round.  Waits for the launch.
+int train_fused(PoolBufs &tmp, cudaStream_t st, int sms, const float *Xc, const float *Yc,
+                const float *Wc, int64_t n_samples, int n_in, int epochs, int batch, float lr,
+                const float *d_inv, int n_steps, float *prm, float *m, float *v, double *losses,
+                double *loss_first, double *loss_last, int32_t *steps) {
+  *loss_first = *loss_last = 0.0;
+  *steps = 0;
+  if (n_steps <= 0) return MCDC_OK;
+  const int64_t np = mlp_param_count(n_in);
+  const int np_pad = (int)((np + 3) & ~3ll);
+  CKM(mlp_prepare());
+  int occ = 0;
+  CKM(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_train_tc, kGroups * kTM,
+                                                     sizeof(TcGrad)));
+  if (occ < 1) return fail(MCDC_ERR_CUDA, "the training kernel does not fit on an SM");
+  const int64_t tiles = (batch + kTM - 1) / kTM;
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * occ, (tiles + kGroups - 1) / kGroups));
+  int32_t *d_err;
+  float *part;
+  unsigned long long *d_bar;
+  CKM(tmp.get(&part, (size_t)grid * np_pad));
+  CKM(tmp.get(&d_bar, 1));
+  CKM(tmp.get(&d_err, 1));
+  CKM(cudaMemsetAsync(d_bar, 0, sizeof(unsigned long long), st));
+  CKM(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
+  TrainArgs ta{};
+  ta.X = Xc; ta.Y = Yc; ta.W = Wc;
+  ta.n_samples = n_samples; ta.batch = batch; ta.inv_wsum = d_inv;
+  ta.n_in = n_in; ta.n_steps = n_steps; ta.epochs = epochs;
+  ta.np = (int)np; ta.np_pad = np_pad;
+  ta.p = prm; ta.m = m; ta.v = v;
+  ta.part = part; ta.losses = losses; ta.bar = d_bar; ta.err = d_err;
+  ta.lr = lr;
+  void *kargs[] = {&ta};
+  CKM(cudaLaunchCooperativeKernel((const void *)k_mlp_train_tc, dim3(grid), dim3(kGroups * kTM),
+                                  kargs, sizeof(TcGrad), st));
+  std::vector<double> hl(2 * (size_t)n_steps);
+  int32_t herr = 0;
+  CKM(cudaMemcpyAsync(hl.data(), losses, sizeof(double) * 2 * n_steps, cudaMemcpyDeviceToHost, st));
+  CKM(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKM(cudaStreamSynchronize(st));
+  if (herr) {
+    tc_status();
+    return fail(MCDC_ERR_TIMEOUT, "a wait in the training kernel ran out (importance network)");
+  }
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = 0; b < n_steps; ++b) { s0 += hl[b]; s1 += hl[n_steps + b]; }
+  *loss_first = s0 / n_steps;
+  *loss_last = epochs > 1 ? s1 / n_steps : *loss_first;
+  *steps = n_steps * epochs;
+  return MCDC_OK;
+}
+
 }  // namespace
 
 extern "C" int64_t mcdc_mlp_param_count(int32_t n_in) {
@@ -1192,6 +1251,60 @@ extern "C" int mcdc_mlp_loss_grad(const float *params, int32_t n_in, const float
   CKM(cudaMemcpy(&lh, dl, sizeof(double), cudaMemcpyDeviceToHost));
   if (loss) *loss = lh;
   return tc_status();
+}
+
+extern "C" int mcdc_mlp_train(float *params, int32_t n_in, const float *X, const float *y,
+                              const float *w, int64_t n, int32_t epochs, int32_t batch,
+                              double lr, double *loss_first, double *loss_last) {
+  if (n_in < 1 || n_in > kIn) return fail(MCDC_ERR_INVALID, "n_in must be in 1..16");
+  if (n <= 0 || !params || !X || !y || !w || epochs < 1 || batch < kS || !(lr > 0.0) ||
+      n > 0x7fffffffll)
+    return fail(MCDC_ERR_INVALID, "bad arguments");
+  const int64_t np = mlp_param_count(n_in);
+  int dev = 0;
+  CKM(cudaGetDevice(&dev));
+  cudaStream_t st;
+  CKM(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  struct StreamGone {
+    cudaStream_t s;
+    ~StreamGone() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  } sg{st};
+  PoolBufs tmp{device_mem_pool(dev), st, {}};
+  float *dX, *dY, *dW, *prm, *m, *v, *d_inv;
+  double *losses;
+  const int n_steps = (int)((n + batch - 1) / batch);
+  CKM(tmp.get(&dX, (size_t)n * n_in));
+  CKM(tmp.get(&dY, (size_t)n));
+  CKM(tmp.get(&dW, (size_t)n));
+  CKM(tmp.get(&prm, (size_t)((np + 3) & ~3ll)));
+  CKM(tmp.get(&m, (size_t)np));
+  CKM(tmp.get(&v, (size_t)np));
+  CKM(tmp.get(&d_inv, (size_t)n_steps));
+  CKM(tmp.get(&losses, 2 * (size_t)n_steps));
+  CKM(cudaMemcpyAsync(dX, X, sizeof(float) * n * n_in, cudaMemcpyDefault, st));
+  CKM(cudaMemcpyAsync(dY, y, sizeof(float) * n, cudaMemcpyDefault, st));
+  CKM(cudaMemcpyAsync(dW, w, sizeof(float) * n, cudaMemcpyDefault, st));
+  CKM(cudaMemcpyAsync(prm, params, sizeof(float) * np, cudaMemcpyDefault, st));
+  CKM(cudaMemsetAsync(m, 0, sizeof(float) * np, st));
+  CKM(cudaMemsetAsync(v, 0, sizeof(float) * np, st));
+  CKM(cudaMemsetAsync(losses, 0, sizeof(double) * 2 * n_steps, st));
+  k_minibatch_inv<<<n_steps, 256, 0, st>>>(n, batch, dW, d_inv);
+  CKM(cudaGetLastError());
+  std::vector<float> hinv(n_steps);
+  CKM(cudaMemcpyAsync(hinv.data(), d_inv, sizeof(float) * n_steps, cudaMemcpyDeviceToHost, st));
+  CKM(cudaStreamSynchronize(st));
+  for (float x : hinv)
+    if (!(x > 0.0f)) return fail(MCDC_ERR_INVALID, "a minibatch has zero weight sum");
+  double lf, ll;
+  int32_t steps;
+  if (int rc = train_fused(tmp, st, device_sms(), dX, dY, dW, n, n_in, epochs, batch, (float)lr,
+                           d_inv, n_steps, prm, m, v, losses, &lf, &ll, &steps))
+    return rc;
+  CKM(cudaMemcpyAsync(params, prm, sizeof(float) * np, cudaMemcpyDefault, st));
+  CKM(cudaStreamSynchronize(st));
+  if (loss_first) *loss_first = lf;
+  if (loss_last) *loss_last = ll;
+  return MCDC_OK;
 }
 
 extern "C" int mcdc_set_wait_limit(int32_t tries) {
@@ -1341,53 +1454,12 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     k_minibatch_inv<<<n_steps, 256, 0, st>>>(n_samples, o.batch, Wc, d_inv);
     CKM(cudaGetLastError());
   }
-  // the whole training in one cooperative launch (k_mlp_train_tc): one CTA
-  // per SM at most, and no more than the two tile pipelines per CTA that
-  // cover a minibatch in one round
-  int occ = 0;
-  CKM(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_train_tc, kGroups * kTM,
-                                                     sizeof(TcGrad)));
-  if (occ < 1) return fail(MCDC_ERR_CUDA, "the training kernel does not fit on an SM");
-  const int64_t tiles = (o.batch + kTM - 1) / kTM;
-  const int grid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)sms * occ, (tiles + kGroups - 1) / kGroups));
-  int32_t *d_err;
-  float *part;
-  unsigned long long *d_bar;
-  CKM(tmp.get(&part, (size_t)grid * np_pad));
-  CKM(tmp.get(&d_bar, 1));
-  CKM(tmp.get(&d_err, 1));
-  CKM(cudaMemsetAsync(d_bar, 0, sizeof(unsigned long long), st));
-  CKM(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
   double loss_first = 0.0, loss_last = 0.0;
   int32_t steps = 0;
-  if (n_steps > 0) {
-    TrainArgs ta{};
-    ta.X = Xc; ta.Y = Yc; ta.W = Wc;
-    ta.n_samples = n_samples; ta.batch = o.batch; ta.inv_wsum = d_inv;
-    ta.n_in = n_in; ta.n_steps = n_steps; ta.epochs = o.epochs;
-    ta.np = (int)np; ta.np_pad = np_pad;
-    ta.p = prm; ta.m = m; ta.v = v;
-    ta.part = part; ta.losses = losses; ta.bar = d_bar; ta.err = d_err;
-    ta.lr = (float)o.lr;
-    void *kargs[] = {&ta};
-    CKM(cudaLaunchCooperativeKernel((const void *)k_mlp_train_tc, dim3(grid), dim3(kGroups * kTM),
-                                    kargs, sizeof(TcGrad), st));
-    std::vector<double> hl(2 * (size_t)n_steps);
-    int32_t herr = 0;
-    CKM(cudaMemcpyAsync(hl.data(), losses, sizeof(double) * 2 * n_steps, cudaMemcpyDeviceToHost, st));
-    CKM(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CKM(cudaStreamSynchronize(st));
-    if (herr) {
-      tc_status();
-      return fail(MCDC_ERR_TIMEOUT, "a wait in the training kernel ran out (importance network)");
-    }
-    double s0 = 0.0, s1 = 0.0;
-    for (int b = 0; b < n_steps; ++b) { s0 += hl[b]; s1 += hl[n_steps + b]; }
-    loss_first = s0 / n_steps;
-    loss_last = o.epochs > 1 ? s1 / n_steps : loss_first;
-    steps = n_steps * o.epochs;
-  }
+  if (int rc = train_fused(tmp, st, sms, Xc, Yc, Wc, n_samples, n_in, o.epochs, o.batch,
+                           (float)o.lr, d_inv, n_steps, prm, m, v, losses, &loss_first,
+                           &loss_last, &steps))
+    return rc;
   CKM(cudaEventRecord(e1, st));
   // bake: predict every bin, weight windows proportional to the predicted flux
   CKM(launch_mlp_forward(st, sms, prm, n_in, X, nb, pred));

@@ -136,6 +136,9 @@ SIGNATURES = {
     "mcdc_set_wait_limit": (C.c_int, [C.c_int32]),
     "mcdc_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
+    "mcdc_mlp_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcdc_measure_fp64_pipe": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -174,6 +177,7 @@ mcdc_train_importance = _lib.mcdc_train_importance
 mcdc_mlp_param_count = _lib.mcdc_mlp_param_count
 mcdc_mlp_forward = _lib.mcdc_mlp_forward
 mcdc_mlp_loss_grad = _lib.mcdc_mlp_loss_grad
+mcdc_mlp_train = _lib.mcdc_mlp_train
 mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
 mcdc_measure_fp64_pipe = _lib.mcdc_measure_fp64_pipe
 mcdc_set_network_windows = _lib.mcdc_set_network_windows
@@ -444,6 +448,19 @@ def mlp_loss_grad(params, X, y, w):
     check(mcdc_mlp_loss_grad(_ptr(p), X.shape[1], _ptr(X), _ptr(y), _ptr(w), X.shape[0], _ptr(g),
                              C.byref(loss)))
     return loss.value, g
+
+
+def mlp_train(params, X, y, w, epochs, batch, lr):
+    """Trains the network (see mcdc_mlp_train); returns (parameters,
+    first-epoch loss, last-epoch loss)."""
+    p = np.array(params, dtype=np.float32, order="C")
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    lf, ll = C.c_double(), C.c_double()
+    check(mcdc_mlp_train(_ptr(p), X.shape[1], _ptr(X), _ptr(y), _ptr(w), X.shape[0], int(epochs),
+                         int(batch), float(lr), C.byref(lf), C.byref(ll)))
+    return p, lf.value, ll.value
 
 
 def run_batched(problems, n_histories, seed, batches=0, means=None, relerrs=None):
