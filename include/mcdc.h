@@ -183,12 +183,14 @@ typedef struct mcdc_options {
                                    bounded run instead of an endless one        */
     int64_t slice_bytes_max;    /* global tally: a run puts every batch in one
                                    launch, each scoring its own tally slice, when
-                                   the slices (batches x bins x 8 bytes) fit in
-                                   this many bytes (0: 8 GiB; negative: never --
-                                   one launch and one fold per batch).  If the
-                                   slices cannot be allocated the run falls back
-                                   to one launch per batch.  Population control
-                                   always uses slices.                          */
+                                   the slices (batches x bins x 8 bytes in FP64
+                                   mode, 4 in the FP32 modes, whose slices are
+                                   FP32 and are folded in FP64) fit in this many
+                                   bytes (0: 8 GiB; negative: never -- one launch
+                                   and one fold per batch into an FP64 tally).
+                                   If the slices cannot be allocated the run
+                                   falls back to one launch per batch.
+                                   Population control always uses slices.       */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */

@@ -356,6 +356,9 @@ int default_batches(const mcdc_problem *pr, uint64_t n) {
 // one launch (population control, weight-window runs).
 // Growing them returns the smaller buffers first, so a problem never holds
 // two generations of slices.
+// The FP32 modes score into FP32 slices (half the memory and atomic traffic,
+// and no FP32-to-FP64 conversion on the FP64 pipe per score); the fold sums
+// the batches in FP64.
 int ensure_slices(mcdc_problem *pr, int B) {
   const long long bins = (long long)B * pr->P.n_tally;
   if (pr->pc_tally_bins >= bins) return MCDC_OK;
@@ -365,10 +368,13 @@ int ensure_slices(mcdc_problem *pr, int B) {
   pr->slice_rb = nullptr;
   pr->pc_tally_bins = 0;
   pr->slices_dirty = false;
+  pr->slice_bytes = pr->key.f64 ? 8 : 4;
   int rc;
-  if ((rc = dalloc(pr, &pr->pc_tally, (size_t)bins))) return rc;
+  unsigned char *t = nullptr;
+  if ((rc = dalloc(pr, &t, (size_t)bins * pr->slice_bytes))) return rc;
+  pr->pc_tally = t;
   if ((rc = dalloc(pr, &pr->slice_rb, (size_t)(2 * B)))) return rc;
-  if (cudaMemset(pr->pc_tally, 0, sizeof(double) * (size_t)bins) != cudaSuccess ||
+  if (cudaMemset(pr->pc_tally, 0, (size_t)pr->slice_bytes * (size_t)bins) != cudaSuccess ||
       cudaMemset(pr->slice_rb, 0, sizeof(double) * (size_t)(2 * B)) != cudaSuccess)
     return fail(MCDC_ERR_CUDA, "cudaMemset of the tally slices failed");
   pr->pc_tally_bins = bins;
@@ -378,16 +384,33 @@ int ensure_slices(mcdc_problem *pr, int B) {
 // Folds the B tally slices of a one-launch run: one pass over the bins when
 // the per-batch region partials fit a block's shared memory, else slice by
 // slice.
-cudaError_t fold_slices(mcdc_problem *pr, cudaStream_t s, const DevProblem &P, size_t nt, int B) {
+template <class ST>
+cudaError_t fold_slices_as(mcdc_problem *pr, cudaStream_t s, const DevProblem &P, ST *slices,
+                           size_t nt, int B) {
   if (B <= 2048)
-    return launch_fold_slices(s, P, pr->pc_tally, (long long)nt, B, pr->sum1, pr->sum2, pr->sum12,
+    return launch_fold_slices(s, P, slices, (long long)nt, B, pr->sum1, pr->sum2, pr->sum12,
                               pr->slice_rb, pr->region, pr->sms);
   for (int b = 0; b < B; ++b) {
-    cudaError_t e = launch_fold(s, P, pr->pc_tally + (size_t)b * nt, pr->sum1, pr->sum2,
-                                pr->sum12, pr->region_batch, pr->region, pr->sms);
+    cudaError_t e = launch_fold(s, P, slices + (size_t)b * nt, pr->sum1, pr->sum2, pr->sum12,
+                                pr->region_batch, pr->region, pr->sms);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+cudaError_t fold_slices(mcdc_problem *pr, cudaStream_t s, const DevProblem &P, size_t nt, int B) {
+  if (pr->slice_bytes == 4)
+    return fold_slices_as(pr, s, P, static_cast<float *>(pr->pc_tally), nt, B);
+  return fold_slices_as(pr, s, P, static_cast<double *>(pr->pc_tally), nt, B);
+}
+// the tracker's arguments for scoring into the slices
+void use_slices(const mcdc_problem *pr, RunArgs &A) {
+  if (pr->slice_bytes == 4) {
+    A.tally = nullptr;
+    A.tally32 = static_cast<float *>(pr->pc_tally);
+  } else {
+    A.tally = static_cast<double *>(pr->pc_tally);
+    A.tally32 = nullptr;
+  }
 }
 
 // Population control buffers: a census bank of cap particles, a combed
@@ -826,6 +849,10 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
       arena.upload(&P.faces[a], fc);
     }
     for (int a = 0; a < 3; ++a) P.width32[a] = bounded[a] ? (float)wid[a] : 0.0f;
+    for (int a = 0; a < 3; ++a) {
+      P.src_cell_a[a] = bounded[a] ? (float)((src->lo[a] - org[a]) / wid[a]) : 0.0f;
+      P.src_cell_b[a] = bounded[a] ? (float)((src->hi[a] - src->lo[a]) / wid[a]) : 0.0f;
+    }
     std::vector<float> bw(std::max(T, 1), 0.0f);
     for (int j = 0; j < T; ++j) bw[j] = (float)(edges[j + 1] - edges[j]);
     arena.upload(&P.binw32, bw);
@@ -1076,6 +1103,10 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   }
   A.batch_q = a->n_histories / (uint64_t)B;
   A.batch_r = a->n_histories % (uint64_t)B;
+  if (a->n_histories <= 0xFFFFFFFFull) {
+    A.div_q1.set((uint32_t)(A.batch_q + 1));
+    A.div_q.set((uint32_t)std::max<uint64_t>(1, A.batch_q));
+  }
 
   CK(cudaEventRecord(pr->ev1, s));
   // a run that returned early (a failed launch, the spill-pass limit) left
@@ -1086,7 +1117,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     pr->tally_dirty = false;
   }
   if (pr->slices_dirty && pr->pc_tally) {
-    CK(cudaMemsetAsync(pr->pc_tally, 0, sizeof(double) * (size_t)pr->pc_tally_bins, s));
+    CK(cudaMemsetAsync(pr->pc_tally, 0, (size_t)pr->slice_bytes * (size_t)pr->pc_tally_bins, s));
     CK(cudaMemsetAsync(pr->slice_rb, 0, sizeof(double) * 2 * (size_t)(pr->pc_tally_bins / std::max<long long>(1, P.n_tally)), s));
     pr->slices_dirty = false;
   }
@@ -1107,7 +1138,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       return rc;
     A.work = pr->work;
     A.batch = 0;
-    A.tally = pr->pc_tally;
+    use_slices(pr, A);
     A.tally_per_batch = 1;
     A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, N / ((uint64_t)pr->grid * 4) + 1));
     A.spill_in = nullptr;
@@ -1213,7 +1244,8 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     // launches, which need only the one batch tally.
     const double cap = pr->opt.slice_bytes_max > 0 ? (double)pr->opt.slice_bytes_max
                                                    : 8.0 * 1073741824.0;
-    bool merged = pr->opt.slice_bytes_max >= 0 && (double)B * (double)nt * 8.0 <= cap;
+    const double entry = pr->key.f64 ? 8.0 : 4.0;
+    bool merged = pr->opt.slice_bytes_max >= 0 && (double)B * (double)nt * entry <= cap;
     if (merged) {
       if (int rc = ensure_slices(pr, B)) {
         if (rc != MCDC_ERR_OOM) return rc;
@@ -1227,7 +1259,12 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     for (int b = 0; b < (merged ? 1 : B); ++b) {
       A.work = pr->work + b;
       A.batch = b;
-      A.tally = merged ? pr->pc_tally : pr->tally;
+      if (merged) {
+        use_slices(pr, A);
+      } else {
+        A.tally = pr->tally;
+        A.tally32 = nullptr;
+      }
       A.tally_per_batch = merged ? 1 : 0;
       const uint64_t nb_hist = merged ? a->n_histories : a->n_histories / B + 1;
       A.chunk = (int)std::max<uint64_t>(32, std::min<uint64_t>(pr->S, nb_hist / ((uint64_t)pr->grid * 4) + 1));

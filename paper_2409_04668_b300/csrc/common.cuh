@@ -41,6 +41,8 @@ struct DevProblem {
   const float *sigma_t32, *scat32, *cdf32, *speed32, *inv_speed32, *src_cdf32;
   // source
   double src_lo[3], src_hi[3];
+  float src_cell_a[3], src_cell_b[3];   // FP32 modes: a source coordinate in cell
+                                        // units is a + xi b (bounded axes)
   int32_t src_kind;
   double src_dir[3];
   double t0, t1;
@@ -116,6 +118,27 @@ struct RoundKeys {
   uint32_t k[20];
 };
 
+// Unsigned 32-bit division by a run constant d >= 1 as a multiply-high, two
+// subtractions and shifts (Granlund & Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (t + ((n - t) >> min(l, 1)))
+// >> max(l - 1, 0), t = mulhi(m, n), exactly for every 32-bit n.
+struct Div32 {
+  uint32_t m = 1;
+  int s1 = 0, s2 = 0;
+  __host__ void set(uint32_t d) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (uint64_t)d) ++l;
+    m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
 struct RunArgs {
   RoundKeys rk;               // round keys of `seed`
   uint64_t n_hist;            // histories in the whole run
@@ -128,6 +151,8 @@ struct RunArgs {
   int32_t batch;
   int32_t chunk;
   double *tally;              // global mode: batch tally [n_est x n_bins]
+  float *tally32;             // FP32 modes, one-launch runs: FP32 batch slices
+                              // (used instead of tally when set; folded in FP64)
   double *sum1, *sum2;        // shared mode: folded per batch ([n_est x n_bins])
   double *sum12;              // combined estimator: sums of track x collision batch products
   double *region;             // [5]: region batch sums and squares (track or the one
@@ -159,6 +184,7 @@ struct RunArgs {
   // one slice of n_est x n_bins per batch, picked from the particle's history id
   int32_t tally_per_batch;
   uint64_t batch_q, batch_r;  // n_hist / n_batches and n_hist % n_batches
+  Div32 div_q1, div_q;        // division by batch_q + 1 and by batch_q (n_hist < 2^32)
   // population control, one time step: every particle of the launch is in
   // time bin step_tbin, so it scores into a CTA-private shared tally of
   // step_bins = n_est x n_batches x cells x groups entries, added into the
@@ -182,8 +208,8 @@ __device__ __forceinline__ int32_t batch_of_run(const RunArgs &A, uint64_t h) {
   const uint64_t big = A.batch_r * (A.batch_q + 1);
   if (A.n_hist <= 0xFFFFFFFFull) {
     const uint32_t h32 = (uint32_t)h;
-    return (int32_t)(h < big ? h32 / (uint32_t)(A.batch_q + 1)
-                             : (uint32_t)A.batch_r + (h32 - (uint32_t)big) / (uint32_t)A.batch_q);
+    return (int32_t)(h < big ? A.div_q1.div(h32)
+                             : (uint32_t)A.batch_r + A.div_q.div(h32 - (uint32_t)big));
   }
   return (int32_t)(h < big ? h / (A.batch_q + 1) : A.batch_r + (h - big) / A.batch_q);
 }

@@ -75,12 +75,19 @@ int track_occupancy(const TrackKey &key, int block, int smem_bytes);
 cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
                         double *sum2, double *sum12, double *region_batch, double *region,
                         int sms);
+// the same for an FP32 batch tally (the FP32 modes' slices), folded in FP64
+cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, float *tally, double *sum1,
+                        double *sum2, double *sum12, double *region_batch, double *region,
+                        int sms);
 // all B tally slices of a one-launch run (slice b at tally + b nt) in one
 // pass: per bin the batch values in batch order into sum1, sum2 (and sum12),
 // the slices zeroed, each batch's region sum into rb[b] (rb[B + b]: the
 // collision half; rb: 2 B zeroed doubles), then region[0..4] as B calls of
 // launch_fold would leave it.  B <= 2048.
 cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, double *tally, long long nt,
+                               int B, double *sum1, double *sum2, double *sum12, double *rb,
+                               double *region, int sms);
+cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, float *tally, long long nt,
                                int B, double *sum1, double *sum2, double *sum12, double *rb,
                                double *region, int sms);
 // mean and relative error from the batch sums (host-side formula mirrored)

@@ -9,7 +9,10 @@ namespace mcdc {
 // read-modify-writes 32 B per bin that scored.  Combined estimator: the
 // collision tally (second half) likewise, plus sum12 += x_track x_collision
 // and the collision region sum.
-__global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__restrict__ tally,
+// ST: the batch tally's type (FP64, or FP32 for the FP32 modes' slices); the
+// sums are FP64 either way.
+template <class ST>
+__global__ void __launch_bounds__(512) k_fold(const DevProblem P, ST *__restrict__ tally,
                                               double *__restrict__ sum1,
                                               double *__restrict__ sum2,
                                               double *__restrict__ sum12,
@@ -21,17 +24,17 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
   const RegionTest region(P);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    const double v = tally[q];
-    const double vc = comb ? tally[n + q] : 0.0;
+    const double v = (double)tally[q];
+    const double vc = comb ? (double)tally[n + q] : 0.0;
     if (v != 0.0 || vc != 0.0) {
       sum1[q] += v;
       sum2[q] += v * v;
-      tally[q] = 0.0;
+      tally[q] = (ST)0;
       if (comb) {
         sum1[n + q] += vc;
         sum2[n + q] += vc * vc;
         sum12[q] += v * vc;
-        tally[n + q] = 0.0;
+        tally[n + q] = (ST)0;
       }
       if (region(P, q)) {
         rs += v;
@@ -57,7 +60,8 @@ __global__ void __launch_bounds__(512) k_fold(const DevProblem P, double *__rest
 // One-launch runs: every slice folded in one pass over the bins.  Reads each
 // slice once and writes zeros back, and read-modify-writes sum1 and sum2 once
 // per bin instead of once per batch.
-__global__ void __launch_bounds__(256) k_fold_slices(const DevProblem P, double *__restrict__ tally,
+template <class ST>
+__global__ void __launch_bounds__(256) k_fold_slices(const DevProblem P, ST *__restrict__ tally,
                                                      long long nt, int B,
                                                      double *__restrict__ sum1,
                                                      double *__restrict__ sum2,
@@ -75,18 +79,18 @@ __global__ void __launch_bounds__(256) k_fold_slices(const DevProblem P, double 
     bool any = false;
     int in = -1;                           // region test, taken at the first score
     for (int b = 0; b < B; ++b) {
-      double *slice = tally + (long long)b * nt;
-      const double v = slice[q];
-      const double vc = comb ? slice[n + q] : 0.0;
+      ST *slice = tally + (long long)b * nt;
+      const double v = (double)slice[q];
+      const double vc = comb ? (double)slice[n + q] : 0.0;
       if (v != 0.0 || vc != 0.0) {
         s1 += v;
         s2 += v * v;
-        slice[q] = 0.0;
+        slice[q] = (ST)0;
         if (comb) {
           c1 += vc;
           c2 += vc * vc;
           x12 += v * vc;
-          slice[n + q] = 0.0;
+          slice[n + q] = (ST)0;
         }
         any = true;
         if (in < 0) in = region(P, q) ? 1 : 0;
@@ -226,24 +230,46 @@ __global__ void __launch_bounds__(512) k_finalize_combined(
   }
 }
 
-cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
-                        double *sum2, double *sum12, double *region_batch, double *region,
-                        int sms) {
+template <class ST>
+cudaError_t fold_batch(cudaStream_t s, const DevProblem &P, ST *tally, double *sum1,
+                       double *sum2, double *sum12, double *region_batch, double *region,
+                       int sms) {
   const long long blocks = std::min<long long>((P.n_bins + 511) / 512, (long long)sms * 8);
-  k_fold<<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(P, tally, sum1, sum2, sum12,
-                                                             region_batch);
+  k_fold<ST><<<(int)std::max<long long>(blocks, 1), 512, 0, s>>>(P, tally, sum1, sum2, sum12,
+                                                                 region_batch);
   k_region_fold<<<1, 1, 0, s>>>(region_batch, region, P.estimator == 2);
   return cudaGetLastError();
 }
+cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, double *tally, double *sum1,
+                        double *sum2, double *sum12, double *region_batch, double *region,
+                        int sms) {
+  return fold_batch(s, P, tally, sum1, sum2, sum12, region_batch, region, sms);
+}
+cudaError_t launch_fold(cudaStream_t s, const DevProblem &P, float *tally, double *sum1,
+                        double *sum2, double *sum12, double *region_batch, double *region,
+                        int sms) {
+  return fold_batch(s, P, tally, sum1, sum2, sum12, region_batch, region, sms);
+}
 
-cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, double *tally, long long nt,
-                               int B, double *sum1, double *sum2, double *sum12, double *rb,
-                               double *region, int sms) {
+template <class ST>
+cudaError_t fold_slices_all(cudaStream_t s, const DevProblem &P, ST *tally, long long nt, int B,
+                            double *sum1, double *sum2, double *sum12, double *rb,
+                            double *region, int sms) {
   const long long blocks = std::min<long long>((P.n_bins + 255) / 256, (long long)sms * 16);
-  k_fold_slices<<<(int)std::max<long long>(blocks, 1), 256, 2 * B * sizeof(double), s>>>(
+  k_fold_slices<ST><<<(int)std::max<long long>(blocks, 1), 256, 2 * B * sizeof(double), s>>>(
       P, tally, nt, B, sum1, sum2, sum12, rb);
   k_region_slices<<<1, 1, 0, s>>>(rb, B, region, P.estimator == 2);
   return cudaGetLastError();
+}
+cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, double *tally, long long nt,
+                               int B, double *sum1, double *sum2, double *sum12, double *rb,
+                               double *region, int sms) {
+  return fold_slices_all(s, P, tally, nt, B, sum1, sum2, sum12, rb, region, sms);
+}
+cudaError_t launch_fold_slices(cudaStream_t s, const DevProblem &P, float *tally, long long nt,
+                               int B, double *sum1, double *sum2, double *sum12, double *rb,
+                               double *region, int sms) {
+  return fold_slices_all(s, P, tally, nt, B, sum1, sum2, sum12, rb, region, sms);
 }
 
 cudaError_t launch_finalize(cudaStream_t s, int64_t n_bins, const double *sum1,

@@ -54,7 +54,9 @@ struct mcdc_problem {
   int pc_cap = 0;                          // input positions the census bank holds
   long long pc_combed_cap = 0;             // particles the combed bank holds
   long long pc_tally_bins = 0;             // entries of the per-batch tally slices
-  double *pc_tally = nullptr;              // [batches][n_tally]
+  void *pc_tally = nullptr;                // [batches][n_tally]: FP64 in FP64 mode, FP32
+                                           // in the FP32 modes (folded in FP64)
+  int slice_bytes = 8;                     // bytes per slice entry (8 or 4)
   double *slice_rb = nullptr;              // [2 batches] per-batch region sums of the slices
   bool slices_dirty = false;               // a run left scores in the slices (returned early)
   bool tally_dirty = false;                // likewise for the batch tally

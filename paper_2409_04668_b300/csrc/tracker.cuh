@@ -470,27 +470,54 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
     isotropic<PR, DIM>(r2, p);
   }
   p.w = (R)1;
-  const double x = P.src_lo[0] + u01_f64(r0.a, r0.b) * (P.src_hi[0] - P.src_lo[0]);
-  const double y = P.src_lo[1] + u01_f64(r0.c, r0.d) * (P.src_hi[1] - P.src_lo[1]);
-  const double z = P.src_lo[2] + u01_f64(r1.a, r1.b) * (P.src_hi[2] - P.src_lo[2]);
-  const double t = P.t0 + u01_f64(r3.a, r3.b) * (P.t1 - P.t0);
-  // FP32 modes carry the optical depth to the first collision from here; it
-  // comes from the time block's third word (unused by the FP32 draws)
-  if constexpr (PR::kF64) p.tau = -1.0f; else p.tau = -logf(u01_f32(r3.c));
-  p.i = loc2index(P, 0, x);
-  p.j = (DIM == 3) ? loc2index(P, 1, y) : 0;
-  p.k = (DIM == 3) ? loc2index(P, 2, z) : 0;
-  p.tbin = 0;
-  if (P.T > 0)
-    while (p.tbin < P.T && tb.edges[p.tbin + 1] <= t) p.tbin += 1;
-  if constexpr (PR::kLocal) {
-    // offsets from the cell's low faces; time left to the next census edge
-    p.x = P.bounded[0] ? (float)(x - __ldg(P.faces[0] + p.i)) : 0.0f;
-    p.y = (DIM == 3 && P.bounded[1]) ? (float)(y - __ldg(P.faces[1] + p.j)) : 0.0f;
-    p.z = (DIM == 3 && P.bounded[2]) ? (float)(z - __ldg(P.faces[2] + p.k)) : 0.0f;
-    p.t = (P.T > 0 && p.tbin < P.T) ? (float)(tb.edges[p.tbin + 1] - t) : 0.0f;
-  } else {
+  if constexpr (PR::kF64) {
+    // FP64: the oracle's arithmetic (53-bit uniforms, loc2index)
+    const double x = P.src_lo[0] + u01_f64(r0.a, r0.b) * (P.src_hi[0] - P.src_lo[0]);
+    const double y = P.src_lo[1] + u01_f64(r0.c, r0.d) * (P.src_hi[1] - P.src_lo[1]);
+    const double z = P.src_lo[2] + u01_f64(r1.a, r1.b) * (P.src_hi[2] - P.src_lo[2]);
+    const double t = P.t0 + u01_f64(r3.a, r3.b) * (P.t1 - P.t0);
+    p.tau = -1.0f;
+    p.i = loc2index(P, 0, x);
+    p.j = (DIM == 3) ? loc2index(P, 1, y) : 0;
+    p.k = (DIM == 3) ? loc2index(P, 2, z) : 0;
+    p.tbin = 0;
+    if (P.T > 0)
+      while (p.tbin < P.T && tb.edges[p.tbin + 1] <= t) p.tbin += 1;
     p.x = x; p.y = y; p.z = z; p.t = t;
+  } else {
+    // FP32 modes: 24-bit uniforms (the top bits of the FP64 run's), each
+    // coordinate in cell units as one FP32 multiply-add, the cell its floor
+    // and the offset from the cell's low face the rest -- no FP64 division.
+    // The optical depth to the first collision comes from the time block's
+    // third word (unused by the FP32 draws).
+    p.tau = -logf(u01_f32(r3.c));
+    const float xi[3] = {u01_f32(r0.a), u01_f32(r0.c), u01_f32(r1.a)};
+    float off[3] = {0.0f, 0.0f, 0.0f};
+    int idx[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      if (!P.bounded[a]) continue;
+      const float f = fmaf(xi[a], P.src_cell_b[a], P.src_cell_a[a]);
+      const int i = min(max((int)floorf(f), 0), P.n[a] - 1);
+      idx[a] = i;
+      off[a] = fminf(fmaxf((f - (float)i) * P.width32[a], 0.0f), P.width32[a]);
+    }
+    p.i = idx[0]; p.j = idx[1]; p.k = idx[2];
+    // birth time: t0 for a pulse (no FP64 work), else uniform in [t0, t1]
+    const double t = P.t1 > P.t0 ? P.t0 + (double)u01_f32(r3.a) * (P.t1 - P.t0) : P.t0;
+    p.tbin = 0;
+    if (P.T > 0)
+      while (p.tbin < P.T && tb.edges[p.tbin + 1] <= t) p.tbin += 1;
+    if constexpr (PR::kLocal) {
+      // offsets from the cell's low faces; time left to the next census edge
+      p.x = off[0]; p.y = off[1]; p.z = off[2];
+      p.t = (P.T > 0 && p.tbin < P.T) ? (float)(tb.edges[p.tbin + 1] - t) : 0.0f;
+    } else {
+      p.x = P.bounded[0] ? __ldg(P.faces[0] + p.i) + (double)off[0] : 0.0;
+      p.y = (DIM == 3 && P.bounded[1]) ? __ldg(P.faces[1] + p.j) + (double)off[1] : 0.0;
+      p.z = (DIM == 3 && P.bounded[2]) ? __ldg(P.faces[2] + p.k) + (double)off[2] : 0.0;
+      p.t = t;
+    }
   }
 }
 
@@ -750,10 +777,11 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
 
 // ---------------------------------------------------------------------------
 // tally scatter of one warp: optional warp aggregation of equal bins
+// (global tallies: the FP32 slices gtally32 when set, else the FP64 gtally)
 template <class TT, class R>
-__device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool shared_mode,
-                                              bool aggregate, bool valid, int bin, R score,
-                                              long long goff = 0) {
+__device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, float *gtally32,
+                                              bool shared_mode, bool aggregate, bool valid,
+                                              int bin, R score, long long goff = 0) {
   bool act = valid && bin >= 0;
   R v = score;
   if (aggregate) {
@@ -776,6 +804,7 @@ __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, bool s
   }
   if (act) {
     if (shared_mode) atomicAdd(&stally[bin], (TT)v);
+    else if (gtally32 != nullptr) atomicAdd(&gtally32[goff + bin], (float)v);
     else atomicAdd(&gtally[goff + bin], (double)v);
   }
 }
@@ -1025,11 +1054,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             // combined estimator: the collision tally follows the track-length one
             const long long coff = P.estimator == 2 ? P.n_bins : 0;
             if (step_tally)
-              tally_scatter<TT, R>(stally, A.tally, true, agg, mine,
+              tally_scatter<TT, R>(stally, A.tally, A.tally32, true, agg, mine,
                                    (mine && cbin >= 0) ? step_bin(P, A, q.hid, cbin, P.estimator == 2)
                                                        : -1, cscore);
             else
-              tally_scatter<TT, R>(stally, A.tally, SHARED, agg, mine,
+              tally_scatter<TT, R>(stally, A.tally, A.tally32, SHARED, agg, mine,
                                    (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
                                    mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
           }
@@ -1222,10 +1251,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         if (step_tally)
-          tally_scatter<TT, R>(stally, A.tally, true, agg, flew,
+          tally_scatter<TT, R>(stally, A.tally, A.tally32, true, agg, flew,
                                (flew && bin >= 0) ? step_bin(P, A, p.hid, bin, 0) : -1, score);
         else
-          tally_scatter<TT, R>(stally, A.tally, SHARED, agg, flew, bin, score,
+          tally_scatter<TT, R>(stally, A.tally, A.tally32, SHARED, agg, flew, bin, score,
                                flew ? tally_offset(P, A, p.hid) : 0);
         if (A.census_out != nullptr) {
           // population control: a banked particle goes to its input position
@@ -1323,8 +1352,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
       if (v == 0.0) continue;
       const int cg = q % per, eb = q / per;
       const int b = eb % A.n_batches, e = eb / A.n_batches;
-      atomicAdd(&A.tally[(long long)b * P.n_tally + e * P.n_bins + (long long)cg * P.T1 +
-                         A.step_tbin], v);
+      const long long at = (long long)b * P.n_tally + e * P.n_bins + (long long)cg * P.T1 +
+                           A.step_tbin;
+      if (A.tally32 != nullptr) atomicAdd(&A.tally32[at], (float)v);
+      else atomicAdd(&A.tally[at], v);
     }
   }
 
