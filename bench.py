@@ -2,8 +2,11 @@
 scaling with disjoint history ranges per rank), printed as one JSON line.
 
 Default workload: the 20 cm two-region time-dependent slab (1e7 histories,
-50 time bins x 200 spatial bins, one group), FP32-split tracking with FP64
-position/time/tally reduction.  A step is one full run (every history of the
+50 time bins x 200 spatial bins, one group), FP32 flights with position and
+time kept exact in FP64 where they cross a cell face or a census edge (FP32
+offsets from those in between) and an FP64 tally reduction; the variant with
+FP64 position and time accumulated every flight is reported beside it.  A
+step is one full run (every history of the
 workload through source, flights, tally, collisions and the batch
 statistics).  Inputs (problem tables) are resident in HBM before timing; the
 per-step L2 flush writes a 256 MiB buffer.
@@ -166,7 +169,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--histories", type=int, default=0)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_local", "fp64"])
+    ap.add_argument("--precision", default="fp32_local", choices=["fp32", "fp32_local", "fp64"],
+                    help="fp32_local (default): FP32 flights with FP64 positions and times "
+                         "only where they cross a cell face or a census edge; fp32: FP64 "
+                         "position and time accumulated every flight; fp64: all FP64")
     ap.add_argument("--batches", type=int, default=0, help="batches per run (0: library default)")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0: library default)")
     ap.add_argument("--pc-target", type=int, default=0,
@@ -277,7 +283,7 @@ def main():
     e2e_val = n_hist * e2e_steps * world / te
 
     pk = peaks()
-    measured_fp64 = M.measure_fp64_pipe() if args.precision == "fp32" else None
+    measured_fp64 = M.measure_fp64_pipe()
     fom = None
     if scal_all and scal_all[-1] and scal_all[-1][1] > 0:
         fom = 1.0 / (scal_all[-1][1] ** 2 * (ms_step / 1e3))
@@ -285,7 +291,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 anchors)",
+        "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 faces and census edges)",
                   M.PREC_FP64: "f64"}[prec], "data": "synthetic",
         "config": {"workload": prob.name, "histories_per_step": n_hist, "precision": args.precision,
                    "tally_mode": ["auto", "shared", "global"][stats_all[-1]["tally_mode"]],
@@ -458,7 +464,7 @@ def run_batched_bench(args):
     line = {"metric": METRIC, "value": total / t, "unit": "histories/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 anchors)",
+            "dtype": {M.PREC_FP32: "f32+f64", M.PREC_FP32_LOCAL: "f32 (f64 faces and census edges)",
                       M.PREC_FP64: "f64"}[prec], "data": "synthetic",
             "config": {"workload": "c5_batched_256_problems", "problems": len(probs),
                        "histories_per_step": int(sum(hist)), "batches": 16,
@@ -473,7 +479,8 @@ def run_batched_bench(args):
 def variants(M, prob, n_hist, args, mean, rel, stream):
     """The headline workload in the other modes of the tracker: device-timed
     histories/s and the region scalar's figure of merit 1/(relerr^2 T) for
-    the cell-local FP32 mode, the FP64 mode (the oracle's arithmetic, event
+    the cell-local FP32 mode, the FP32 mode with FP64 position and time
+    accumulated every flight, the FP64 mode (the oracle's arithmetic, event
     for event) and, in the headline precision, for the
     collision estimator, for the combined track-length/collision estimator
     (both tallies, their minimum-variance combination), for implicit capture
@@ -483,6 +490,7 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
     prec = {"fp32": M.PREC_FP32, "fp32_local": M.PREC_FP32_LOCAL, "fp64": M.PREC_FP64}[args.precision]
     modes = {"track_analog": {"precision": prec},
              "fp32_local": {"precision": M.PREC_FP32_LOCAL},
+             "fp32_every_flight": {"precision": M.PREC_FP32},
              "fp64": {"precision": M.PREC_FP64},
              "collision_estimator": {"precision": prec, "estimator": M.EST_COLLISION},
              "combined_estimator": {"precision": prec, "estimator": M.EST_COMBINED},
@@ -632,8 +640,9 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
     until the combined relative error reaches `target` or max_seconds of
     device time are spent; the learned arm's final run is then repeated with
     the history count that reaches the analog's error (from its first run's
-    error, relerr ~ 1/sqrt(N)), and its T includes every cost of the
-    pipeline (pilot, fits, refit runs: overhead_s)."""
+    error, relerr ~ 1/sqrt(N), corrected up to twice from the error the run
+    reached), and its T includes every cost of the pipeline (pilot, fits,
+    refit runs: overhead_s) and the final run it kept.""" 
     import torch
     means, vars_, secs, nb = [], [], 0.0, 0
     with M.Problem(prob, precision=prec) as A:
@@ -649,8 +658,15 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
             rc = math.sqrt(sum(vars_)) / len(means) / mc if mc > 0 else float("inf")
             if rc <= target or secs >= max_seconds:
                 break
-    n_w = int(max(2000, math.ceil(n_w1 * (r_w1 / rc) ** 2)))
-    (st, (m_w, r_w)), wall = _timed(lambda: P.run_ex(n_w, seed_w, batches=ww_batches))
+    # the learned run's history count for the analog's error, from relerr ~
+    # 1/sqrt(N): three tries at most, each from the last run's own error
+    n_w, r_w1n = n_w1, r_w1
+    for attempt in range(3):
+        n_w = int(max(2000, math.ceil(n_w * (r_w1n / rc) ** 2)))
+        (st, (m_w, r_w)), wall = _timed(lambda: P.run_ex(n_w, seed_w + attempt, batches=ww_batches))
+        r_w1n = r_w
+        if abs(r_w / rc - 1.0) < 0.15:
+            break
     t_w = st["kernel_ms"] / 1e3
     t_tot = overhead_s + t_w
     fa, fw = 1.0 / (rc * rc * secs), 1.0 / (r_w * r_w * t_tot)
