@@ -642,7 +642,7 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
     the history count that reaches the analog's error (from its first run's
     error, relerr ~ 1/sqrt(N), corrected up to twice from the error the run
     reached), and its T includes every cost of the pipeline (pilot, fits,
-    refit runs: overhead_s) and the final run it kept.""" 
+    refit runs: overhead_s) and every try of the final run."""
     import torch
     means, vars_, secs, nb = [], [], 0.0, 0
     with M.Problem(prob, precision=prec) as A:
@@ -660,14 +660,14 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
                 break
     # the learned run's history count for the analog's error, from relerr ~
     # 1/sqrt(N): three tries at most, each from the last run's own error
-    n_w, r_w1n = n_w1, r_w1
+    n_w, r_w1n, t_w = n_w1, r_w1, 0.0
     for attempt in range(3):
         n_w = int(max(2000, math.ceil(n_w * (r_w1n / rc) ** 2)))
         (st, (m_w, r_w)), wall = _timed(lambda: P.run_ex(n_w, seed_w + attempt, batches=ww_batches))
+        t_w += st["kernel_ms"] / 1e3
         r_w1n = r_w
         if abs(r_w / rc - 1.0) < 0.15:
             break
-    t_w = st["kernel_ms"] / 1e3
     t_tot = overhead_s + t_w
     fa, fw = 1.0 / (rc * rc * secs), 1.0 / (r_w * r_w * t_tot)
     ua, uw = fom_rel_uncertainty(nb), fom_rel_uncertainty(ww_batches)
@@ -675,7 +675,8 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
     return {"target_relerr": target,
             "analog": {"histories": chunk * len(means), "mean": mc, "relerr": rc, "seconds": secs,
                        "batches": nb, "fom": fa, "fom_rel_uncertainty": ua},
-            "learned": {"histories": n_w, "mean": m_w, "relerr": r_w, "seconds_run": t_w,
+            "learned": {"histories": n_w, "mean": m_w, "relerr": r_w, "seconds_runs": t_w,
+                        "tries": attempt + 1,
                         "seconds_incl_pilot_and_fit": t_tot, "fom_incl_pilot": fw,
                         "fom_rel_uncertainty": uw},
             "agreement_z": z,
