@@ -1,6 +1,7 @@
 // api.cu -- the C-ABI (include/mcdc.h): problem validation, device tables,
 // launch-shape selection and the run sequence.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -226,6 +227,7 @@ void pinned_put(PinnedBlock *b) {
 
 void release(mcdc_problem *pr) {
   if (!pr) return;
+  if (pr->uid) mcdc::batched_forget(pr->uid);
   cudaSetDevice(pr->device);
   for (void *p : pr->allocs) cudaFree(p);
   pr->allocs.clear();
@@ -770,6 +772,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (int rc = device_limits(dev, &dl)) return rc;
 
   mcdc_problem *pr = new mcdc_problem();
+  static std::atomic<uint64_t> next_uid{1};
+  pr->uid = next_uid.fetch_add(1);
   pr->device = dev;
   pr->sms = dl.sms;
   pr->opt = o;

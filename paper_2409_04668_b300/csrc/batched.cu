@@ -2,13 +2,14 @@
 // persistent launch in which CTAs claim (problem, history range) work items
 // (largest first), load the item's problem tables into shared memory when the
 // problem changes, and score into that problem's device tally; then one fused
-// fold of every problem's batch tally.  The whole sequence is captured as a
-// CUDA graph and launched once.
+// fold of every problem's batch tally.  The whole sequence is captured once
+// as a CUDA graph per batch shape and replayed by later calls.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -57,6 +58,20 @@ __global__ void __launch_bounds__(512) k_fold_multi(const DevProblem *__restrict
   }
 }
 
+// Zeroes every problem's batch sums and region accumulators (one row of
+// blocks per problem) at the start of a batched run.
+__global__ void k_zero_multi(const DevProblem *__restrict__ probs, const FoldItem *__restrict__ fi,
+                             double *const *regions) {
+  const FoldItem f = fi[blockIdx.y];
+  const long long nb = probs[blockIdx.y].n_bins;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    f.sum1[b] = 0.0;
+    f.sum2[b] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 4) regions[blockIdx.y][threadIdx.x] = 0.0;
+}
+
 __global__ void k_region_fold_multi(const FoldItem *__restrict__ fi, double *const *regions, int n) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const double b = *fi[p].region_batch;
@@ -102,42 +117,50 @@ bool dev_ptr(const void *p) {
 }  // namespace
 
 namespace {
-// One batched run with a given launch shape: threads per CTA and histories
-// per work item.
-int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_histories,
-                uint64_t seed, int32_t n_batches, double *const *mean_out,
-                double *const *relerr_out, double *scalar_out, mcdc_stats *stats, int block,
-                unsigned long long chunk) {
-  if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
-  if (n > 65535) return fail(MCDC_ERR_INVALID, "at most 65535 problems per batched run");
-  const int B = n_batches > 0 ? n_batches : 16;
-  if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");
+// A batched run's plan: its device argument buffers and the whole run
+// captured once as a CUDA graph (zero the sums, per batch one persistent
+// launch over every problem and one fused fold, the per-problem
+// finalisations into device outputs).  Plans are cached by the run's shape
+// -- the problems (by identity), their history counts, the batches, the
+// launch shape and the device outputs -- so a repeated call uploads the
+// per-problem arguments (the seeds change) and replays the graph; nothing is
+// captured or instantiated again.  Destroying a problem drops the plans that
+// hold it.
+struct BatchedPlan {
+  std::vector<uint64_t> key;
+  int device = 0, block = 0, cps = 0, B = 0;
+  std::vector<uint64_t> uids;
+  std::vector<RunArgs> ha;              // host copy of the per-problem arguments
+  DevFree fr;                           // device buffers of the plan
+  Stats *d_stats = nullptr;
+  int32_t *d_err = nullptr;
+  RunArgs *d_args = nullptr;
+  double *scratch = nullptr;            // host outputs: [2][largest tally]
+  long long max_bins = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~BatchedPlan() {
+    cudaSetDevice(device);
+    if (st) cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaGetLastError();
+  }
+};
+
+std::mutex g_plan_mu;
+std::vector<std::unique_ptr<BatchedPlan>> g_plans;   // most recently used last
+constexpr size_t kMaxPlans = 4;
+
+int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
+               const uint64_t *n_histories, double *const *mean_dev, double *const *rel_dev,
+               int B, int block, unsigned long long chunk) {
   mcdc_problem *p0 = probs[0];
-  for (int i = 0; i < n; ++i) {
-    const mcdc_problem *p = probs[i];
-    if (!p) return fail(MCDC_ERR_INVALID, "problem is NULL");
-    if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
-        p->dim != p0->dim)
-      return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
-    if (ww_on(p->P) || p->P.implicit || p->P.pc_target > 0)
-      return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
-    if (p->P.estimator == MCDC_EST_COMBINED)
-      return fail(MCDC_ERR_INVALID, "batched runs score one estimator (no combined estimator)");
-    if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
-  }
-  CKB(cudaSetDevice(p0->device));
-  DevFree fr;
-  // every problem scores into a device tally of its own
-  for (int i = 0; i < n; ++i) {
-    mcdc_problem *p = probs[i];
-    if (!p->tally) {
-      double *t = nullptr;
-      CKB(cudaMalloc(&t, sizeof(double) * p->P.n_bins));
-      p->allocs.push_back(t);
-      p->tally = t;
-      CKB(cudaMemset(t, 0, sizeof(double) * p->P.n_bins));
-    }
-  }
   // launch shape: the largest tables of the batch, no shared tally
   TrackKey key = p0->key;
   key.shared = false;
@@ -161,32 +184,33 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   const int cps = track_occupancy(key, block, L.total);
   if (cps < 1) return fail(MCDC_ERR_INVALID, "launch shape does not fit");
   const int grid = p0->sms * cps;
+  pl.device = p0->device;
+  pl.block = block;
+  pl.cps = cps;
+  pl.B = B;
 
-  // per-problem device arguments, one stats block and error word for all
-  Stats *d_stats = nullptr;
-  int32_t *d_err = nullptr;
-  CKB(dnew(fr, &d_stats, 1));
-  CKB(dnew(fr, &d_err, 4));
+  CKB(dnew(pl.fr, &pl.d_stats, 1));
+  CKB(dnew(pl.fr, &pl.d_err, 4));
   std::vector<DevProblem> hp(n);
-  std::vector<RunArgs> ha(n);
   std::vector<FoldItem> hf(n);
   std::vector<double *> hreg(n);
+  pl.ha.resize(n);
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
     hp[i] = p->P;
     RunArgs A{};
     A.n_hist = n_histories[i];
     A.offset = 0;
-    A.seed = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;   // independent streams per problem
-    A.rk = round_keys(A.seed);
     A.n_batches = B;
     A.tally = p->tally;
-    A.stats = d_stats;
-    A.error = d_err;
+    A.stats = pl.d_stats;
+    A.error = pl.d_err;
     A.warp_aggregate = p->warp_aggregate;
-    ha[i] = A;
+    pl.ha[i] = A;
     hf[i] = {p->tally, p->sum1, p->sum2, p->region_batch};
     hreg[i] = p->region;
+    pl.uids.push_back(p->uid);
+    pl.max_bins = std::max<long long>(pl.max_bins, p->P.n_bins);
   }
   // work items, batch by batch, largest first within a batch
   std::vector<WorkItem> items;
@@ -204,107 +228,189 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     item_off[b + 1] = (int)items.size();
   }
   DevProblem *d_probs;
-  RunArgs *d_args;
   WorkItem *d_items;
   FoldItem *d_fold;
   double **d_reg;
   unsigned long long *d_ctr;
-  CKB(dnew(fr, &d_probs, n));
-  CKB(dnew(fr, &d_args, n));
-  CKB(dnew(fr, &d_items, items.size()));
-  CKB(dnew(fr, &d_fold, n));
-  CKB(dnew(fr, &d_reg, n));
-  CKB(dnew(fr, &d_ctr, B));
+  CKB(dnew(pl.fr, &d_probs, n));
+  CKB(dnew(pl.fr, &pl.d_args, n));
+  CKB(dnew(pl.fr, &d_items, items.size()));
+  CKB(dnew(pl.fr, &d_fold, n));
+  CKB(dnew(pl.fr, &d_reg, n));
+  CKB(dnew(pl.fr, &d_ctr, B));
   CKB(cudaMemcpy(d_probs, hp.data(), sizeof(DevProblem) * n, cudaMemcpyHostToDevice));
-  CKB(cudaMemcpy(d_args, ha.data(), sizeof(RunArgs) * n, cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_fold, hf.data(), sizeof(FoldItem) * n, cudaMemcpyHostToDevice));
   CKB(cudaMemcpy(d_reg, hreg.data(), sizeof(double *) * n, cudaMemcpyHostToDevice));
 
-  cudaStream_t st;
-  CKB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  cudaEvent_t e0, e1;
-  CKB(cudaEventCreate(&e0));
-  CKB(cudaEventCreate(&e1));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  struct Release {
-    cudaStream_t s; cudaEvent_t a, b; cudaGraph_t *g; cudaGraphExec_t *x;
-    ~Release() {
-      if (*x) cudaGraphExecDestroy(*x);
-      if (*g) cudaGraphDestroy(*g);
-      cudaEventDestroy(a); cudaEventDestroy(b); cudaStreamDestroy(s);
-    }
-  } rel{st, e0, e1, &graph, &exec};
-
-  // the run as one graph: zero the accumulators, then per batch one
-  // persistent launch over every problem and one fused fold
-  CKB(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaMemsetAsync(d_stats, 0, sizeof(Stats), st);
-  cudaMemsetAsync(d_err, 0, 4 * sizeof(int32_t), st);
-  cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * B, st);
-  for (int i = 0; i < n; ++i) {
-    mcdc_problem *p = probs[i];
-    cudaMemsetAsync(p->sum1, 0, sizeof(double) * p->P.n_bins, st);
-    cudaMemsetAsync(p->sum2, 0, sizeof(double) * p->P.n_bins, st);
-    cudaMemsetAsync(p->region, 0, 4 * sizeof(double), st);
-  }
+  CKB(cudaStreamCreateWithFlags(&pl.st, cudaStreamNonBlocking));
+  CKB(cudaEventCreate(&pl.e0));
+  CKB(cudaEventCreate(&pl.e1));
+  cudaStream_t st = pl.st;
   // fold grid: x blocks per problem (enough for the largest), one row per problem
-  long long max_bins = 1;
-  for (int i = 0; i < n; ++i) max_bins = std::max<long long>(max_bins, probs[i]->P.n_bins);
-  const dim3 fold_grid((unsigned)std::max<long long>(1, std::min<long long>((max_bins + 511) / 512, 64)),
-                       (unsigned)n);
+  const dim3 row_grid((unsigned)std::max<long long>(1, std::min<long long>((pl.max_bins + 511) / 512, 64)),
+                      (unsigned)n);
+  CKB(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaMemsetAsync(pl.d_stats, 0, sizeof(Stats), st);
+  cudaMemsetAsync(pl.d_err, 0, 4 * sizeof(int32_t), st);
+  cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * B, st);
+  k_zero_multi<<<row_grid, 512, 0, st>>>(d_probs, d_fold, d_reg);
   for (int b = 0; b < B; ++b) {
-    MultiArgs MA{d_probs, d_args, d_items + item_off[b], item_off[b + 1] - item_off[b], d_ctr + b};
-    launch_track(key, grid, block, L.total, st, hp[0], ha[0], L, &MA);
-    k_fold_multi<<<fold_grid, 512, 0, st>>>(d_probs, d_fold);
+    MultiArgs MA{d_probs, pl.d_args, d_items + item_off[b], item_off[b + 1] - item_off[b], d_ctr + b};
+    launch_track(key, grid, block, L.total, st, hp[0], pl.ha[0], L, &MA);
+    k_fold_multi<<<row_grid, 512, 0, st>>>(d_probs, d_fold);
     k_region_fold_multi<<<(n + 255) / 256, 256, 0, st>>>(d_fold, d_reg, n);
   }
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
-    double *m = mean_out && mean_out[i] && dev_ptr(mean_out[i]) ? mean_out[i] : nullptr;
-    double *r = relerr_out && relerr_out[i] && dev_ptr(relerr_out[i]) ? relerr_out[i] : nullptr;
+    double *m = mean_dev ? mean_dev[i] : nullptr;
+    double *r = rel_dev ? rel_dev[i] : nullptr;
     if (m || r)
       launch_finalize(st, p->P.n_bins, p->sum1, p->sum2, n_histories[i], B, p->P.volume, m, r, p->sms);
   }
-  CKB(cudaStreamEndCapture(st, &graph));
-  CKB(cudaGraphInstantiate(&exec, graph, 0));
-  CKB(cudaEventRecord(e0, st));
-  CKB(cudaGraphLaunch(exec, st));
-  CKB(cudaEventRecord(e1, st));
-  CKB(cudaStreamSynchronize(st));
+  const cudaError_t ec = cudaStreamEndCapture(st, &pl.graph);
+  if (ec != cudaSuccess) return fail(MCDC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  CKB(cudaGraphInstantiate(&pl.exec, pl.graph, 0));
+  return MCDC_OK;
+}
 
-  // host outputs: finalise on the device into scratch, then copy
+// One batched run with a given launch shape: threads per CTA and histories
+// per work item.
+// cache = false (the autotuner's trial runs): the plan is built for this call
+// only and not kept.
+int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_histories,
+                uint64_t seed, int32_t n_batches, double *const *mean_out,
+                double *const *relerr_out, double *scalar_out, mcdc_stats *stats, int block,
+                unsigned long long chunk, bool cache = true) {
+  if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
+  if (n > 65535) return fail(MCDC_ERR_INVALID, "at most 65535 problems per batched run");
+  const int B = n_batches > 0 ? n_batches : 16;
+  if (B < 2) return fail(MCDC_ERR_INVALID, "need at least 2 batches");
+  mcdc_problem *p0 = probs[0];
+  for (int i = 0; i < n; ++i) {
+    const mcdc_problem *p = probs[i];
+    if (!p) return fail(MCDC_ERR_INVALID, "problem is NULL");
+    if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
+        p->dim != p0->dim)
+      return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
+    if (ww_on(p->P) || p->P.implicit || p->P.pc_target > 0)
+      return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
+    if (p->P.estimator == MCDC_EST_COMBINED)
+      return fail(MCDC_ERR_INVALID, "batched runs score one estimator (no combined estimator)");
+    if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
+  }
+  CKB(cudaSetDevice(p0->device));
+  // every problem scores into a device tally of its own
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    if (!p->tally) {
+      double *t = nullptr;
+      CKB(cudaMalloc(&t, sizeof(double) * p->P.n_bins));
+      p->allocs.push_back(t);
+      p->tally = t;
+      CKB(cudaMemset(t, 0, sizeof(double) * p->P.n_bins));
+    }
+  }
+  // the plan's key: problems, histories, outputs written by the graph, shape
+  std::vector<double *> mdev(n, nullptr), rdev(n, nullptr);
+  bool any_host = false;
+  std::vector<uint64_t> key;
+  key.reserve(4 * (size_t)n + 4);
+  key.push_back((uint64_t)n);
+  key.push_back((uint64_t)B);
+  key.push_back((uint64_t)block);
+  key.push_back(chunk);
+  for (int i = 0; i < n; ++i) {
+    mdev[i] = mean_out && mean_out[i] && dev_ptr(mean_out[i]) ? mean_out[i] : nullptr;
+    rdev[i] = relerr_out && relerr_out[i] && dev_ptr(relerr_out[i]) ? relerr_out[i] : nullptr;
+    any_host = any_host || (mean_out && mean_out[i] && !mdev[i]) ||
+               (relerr_out && relerr_out[i] && !rdev[i]);
+    key.push_back(probs[i]->uid);
+    key.push_back(n_histories[i]);
+    key.push_back((uint64_t)(uintptr_t)mdev[i]);
+    key.push_back((uint64_t)(uintptr_t)rdev[i]);
+  }
+  std::unique_lock<std::mutex> lk(g_plan_mu);
+  BatchedPlan *pl = nullptr;
+  std::unique_ptr<BatchedPlan> once;
+  for (size_t k = 0; cache && k < g_plans.size(); ++k) {
+    if (g_plans[k]->key == key) {
+      std::unique_ptr<BatchedPlan> hit = std::move(g_plans[k]);
+      g_plans.erase(g_plans.begin() + (long)k);
+      g_plans.push_back(std::move(hit));
+      pl = g_plans.back().get();
+      break;
+    }
+  }
+  if (!pl) {
+    auto np = std::make_unique<BatchedPlan>();
+    np->key = key;
+    if (int rc = build_plan(*np, probs, n, n_histories, mdev.data(), rdev.data(), B, block, chunk))
+      return rc;
+    if (cache) {
+      if (g_plans.size() >= kMaxPlans) g_plans.erase(g_plans.begin());
+      g_plans.push_back(std::move(np));
+      pl = g_plans.back().get();
+    } else {
+      once = std::move(np);
+      pl = once.get();
+    }
+  }
+  // a single-problem run that returned early left scores in a tally
+  for (int i = 0; i < n; ++i) {
+    mcdc_problem *p = probs[i];
+    if (p->tally_dirty) {
+      CKB(cudaMemsetAsync(p->tally, 0, sizeof(double) * p->P.n_bins, pl->st));
+      p->tally_dirty = false;
+    }
+  }
+  // this call's seeds: independent streams per problem
+  for (int i = 0; i < n; ++i) {
+    RunArgs &A = pl->ha[i];
+    A.seed = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    A.rk = round_keys(A.seed);
+  }
+  cudaStream_t st = pl->st;
+  CKB(cudaMemcpyAsync(pl->d_args, pl->ha.data(), sizeof(RunArgs) * n, cudaMemcpyHostToDevice, st));
+  CKB(cudaEventRecord(pl->e0, st));
+  CKB(cudaGraphLaunch(pl->exec, st));
+  CKB(cudaEventRecord(pl->e1, st));
+
+  // host outputs: finalise on the device into the plan's scratch, then copy
+  if (any_host && !pl->scratch) CKB(dnew(pl->fr, &pl->scratch, 2 * (size_t)pl->max_bins));
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
     const size_t nb = (size_t)p->P.n_bins;
-    const bool hm = mean_out && mean_out[i] && !dev_ptr(mean_out[i]);
-    const bool hr = relerr_out && relerr_out[i] && !dev_ptr(relerr_out[i]);
+    const bool hm = mean_out && mean_out[i] && !mdev[i];
+    const bool hr = relerr_out && relerr_out[i] && !rdev[i];
     if (hm || hr) {
-      double *m = nullptr, *r = nullptr;
-      CKB(dnew(fr, &m, nb));
-      CKB(dnew(fr, &r, nb));
+      double *m = pl->scratch, *r = pl->scratch + pl->max_bins;
       CKB(launch_finalize(st, nb, p->sum1, p->sum2, n_histories[i], B, p->P.volume, m, r, p->sms));
       if (hm) CKB(cudaMemcpyAsync(mean_out[i], m, nb * 8, cudaMemcpyDeviceToHost, st));
       if (hr) CKB(cudaMemcpyAsync(relerr_out[i], r, nb * 8, cudaMemcpyDeviceToHost, st));
     }
-    if (scalar_out) {
-      double reg[2];
-      CKB(cudaMemcpyAsync(reg, p->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CKB(cudaStreamSynchronize(st));
-      const double nv = (double)n_histories[i] * p->P.volume, Bd = (double)B;
-      const double mm = reg[0] / nv;
-      double ss = reg[1] - reg[0] * reg[0] / Bd;
+  }
+  std::vector<double> reg(scalar_out ? 2 * (size_t)n : 0);
+  if (scalar_out)
+    for (int i = 0; i < n; ++i)
+      CKB(cudaMemcpyAsync(&reg[2 * i], probs[i]->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  Stats h;
+  int32_t herr = 0;
+  CKB(cudaMemcpyAsync(&h, pl->d_stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
+  CKB(cudaMemcpyAsync(&herr, pl->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKB(cudaStreamSynchronize(st));
+  if (scalar_out) {
+    for (int i = 0; i < n; ++i) {
+      const double nv = (double)n_histories[i] * probs[i]->P.volume, Bd = (double)B;
+      const double mm = reg[2 * i] / nv;
+      double ss = reg[2 * i + 1] - reg[2 * i] * reg[2 * i] / Bd;
       if (ss < 0.0) ss = 0.0;
       const double var = (Bd * Bd / (nv * nv)) * ss / (Bd * (Bd - 1.0));
       scalar_out[2 * i] = mm;
       scalar_out[2 * i + 1] = mm != 0.0 ? std::sqrt(var) / std::fabs(mm) : 0.0;
     }
   }
-  CKB(cudaStreamSynchronize(st));
   if (stats) {
-    Stats h;
-    CKB(cudaMemcpy(&h, d_stats, sizeof(Stats), cudaMemcpyDeviceToHost));
     std::memset(stats, 0, sizeof(*stats));
     stats->histories = h.histories; stats->segments = h.segments;
     stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
@@ -312,16 +418,14 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     stats->w_source = (double)h.histories; stats->w_absorbed = (double)h.absorbed;   // analog
     stats->w_leaked = (double)h.leaked; stats->w_censused = (double)h.censused;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, pl->e0, pl->e1);
     stats->kernel_ms = ms;
     stats->total_ms = ms;
-    stats->block_size = block;
-    stats->ctas_per_sm = cps;
+    stats->block_size = pl->block;
+    stats->ctas_per_sm = pl->cps;
     stats->tally_mode = MCDC_TALLY_GLOBAL;
     stats->n_batches = B;
   }
-  int32_t herr = 0;
-  CKB(cudaMemcpy(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (herr) return fail(MCDC_ERR_BANK_OVERFLOW, "device error flag set");
   return MCDC_OK;
 }
@@ -373,7 +477,7 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
       for (unsigned long long chunk : {1ull << 14, 1ull << 16}) {
         mcdc_stats st{};
         const int rc = run_batched(probs, n, trial.data(), seed ^ 0x5bd1e995ull, n_batches, nullptr,
-                                   nullptr, nullptr, &st, block, chunk);
+                                   nullptr, nullptr, &st, block, chunk, false);
         if (rc == MCDC_ERR_INVALID) continue;        // this shape does not fit
         if (rc != MCDC_OK) return rc;
         any = true;
@@ -386,3 +490,21 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
   return run_batched(probs, n, n_histories, seed, n_batches, mean_out, relerr_out, scalar_out, stats,
                      best.block, best.chunk);
 }
+
+namespace mcdc {
+void batched_forget(uint64_t uid) {
+  std::vector<std::unique_ptr<BatchedPlan>> gone;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (size_t k = 0; k < g_plans.size();) {
+      const auto &u = g_plans[k]->uids;
+      if (std::find(u.begin(), u.end(), uid) != u.end()) {
+        gone.push_back(std::move(g_plans[k]));
+        g_plans.erase(g_plans.begin() + (long)k);
+      } else {
+        ++k;
+      }
+    }
+  }
+}
+}  // namespace mcdc

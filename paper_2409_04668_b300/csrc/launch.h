@@ -114,6 +114,9 @@ struct mcdc_problem;
 namespace mcdc {
 // Allocates the per-warp overflow stacks once weight windows are on.
 int ensure_overflow_for(mcdc_problem *pr);
+// Drops every cached batched-run plan that holds the problem with this uid
+// (called when the problem is destroyed).
+void batched_forget(uint64_t uid);
 // The device's stream-ordered memory pool of problems (nullptr where pools
 // are unavailable), for temporaries allocated and freed on a caller's stream.
 cudaMemPool_t device_mem_pool(int dev);

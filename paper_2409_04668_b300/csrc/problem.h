@@ -8,6 +8,7 @@
 #include "tracker.cuh"
 
 struct mcdc_problem {
+  uint64_t uid = 0;           // unique over the process (batched-run plans key on it)
   int device = 0;
   int sms = 0;
   mcdc::DevProblem P{};

@@ -70,6 +70,52 @@ def test_fp64_3d_channel_small(mcdc, mode):
     assert g["scalar"][0] == pytest.approx(o["scalar"][0], rel=REL_TALLY)
 
 
+def test_fp64_batched_graph_replay_takes_each_calls_seed(mcdc):
+    """The batched layer captures a run once per shape and replays it: two
+    calls with different seeds each equal the oracle at their own seed
+    (1e-9), and after one problem is destroyed and a different one of the
+    same size takes its place, the next call equals the new problem's oracle
+    run (the destroyed problem's plan is dropped, not replayed)."""
+    probs, _ = W.c5_batch(n_problems=3, seed=23)
+    small = []
+    for p in probs:
+        k = min(p.n[0], 10)
+        small.append(W.box(p.name, (k, k, k), p.width, p.material[:k, :k, :k].copy(), p.sigma_t,
+                           p.sigma_s / p.sigma_t, p.transfer, p.speed, (0.0,) * 3, (float(k),) * 3,
+                           None, (0, 0, 0), (k, k, k)))
+    hist, B = [3000, 2500, 2048], 4
+    handles = [mcdc.Problem(p, precision=mcdc.PREC_FP64) for p in small]
+    means = [np.zeros(h.n_bins) for h in handles]
+
+    def check(seed, problems):
+        stats, scal = mcdc.run_batched(handles, hist, seed, batches=B, means=means)
+        assert stats["histories"] == sum(hist)
+        for i, p in enumerate(problems):
+            s = (seed + i * 0x9E3779B97F4A7C15) % (1 << 64)
+            o = O.run(p, hist[i], seed=s, batches=B)
+            got = means[i].reshape(p.tally_shape)
+            nz = o["mean"] != 0
+            np.testing.assert_allclose(got[nz], o["mean"][nz], rtol=REL_TALLY)
+            np.testing.assert_array_equal(got == 0, o["mean"] == 0)
+
+    try:
+        check(101, small)
+        check(202, small)                  # replay with another seed
+        # a different problem of the same size in slot 1
+        mat = small[1].material.copy()
+        mat = mat[::-1].copy()
+        other = W.box("other", small[1].n, small[1].width, mat, small[1].sigma_t,
+                      small[1].sigma_s / small[1].sigma_t, small[1].transfer, small[1].speed,
+                      (0.0,) * 3, tuple(float(v) for v in small[1].n), None, (0, 0, 0),
+                      tuple(small[1].n))
+        handles[1].close()
+        handles[1] = mcdc.Problem(other, precision=mcdc.PREC_FP64)
+        check(303, [small[0], other, small[2]])
+    finally:
+        for h in handles:
+            h.close()
+
+
 @pytest.mark.parametrize("cap", [-1, 4096])
 def test_fp64_global_tally_one_launch_per_batch(mcdc, cap):
     """The global tally's per-batch path (a launch and a fold per batch),
