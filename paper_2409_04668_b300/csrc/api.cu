@@ -502,11 +502,15 @@ int ensure_overflow(mcdc_problem *pr) {
 // ---- autotuner ---------------------------------------------------------------
 // Times candidate launch shapes on the problem itself -- threads per CTA
 // (which sets the CTA's particle bank: warps x 96 parked slots plus one
-// flying particle per lane), whole batches per CTA in the shared-tally mode,
-// and warp aggregation of tally atomics -- and keeps the fastest.  Choices
-// are cached per problem shape for the life of the process.
+// flying particle per lane), resident CTAs per SM (all that fit, or half),
+// whole batches per CTA in the shared-tally mode, and warp aggregation of
+// tally atomics -- and keeps the fastest.  Choices are cached per problem
+// shape for the life of the process.  (The 96 parked slots per warp are not
+// a tuning choice: the scheduler never parks more than 94, and fewer slots
+// would break that bound.)
 struct TuneChoice {
   int block, batch_per_cta, aggregate;
+  int cps;      // resident CTAs per SM; 0: as many as fit
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
@@ -525,6 +529,7 @@ int apply_choice(mcdc_problem *pr, const DeviceLimits &dl, const TuneChoice &c) 
   pr->opt.block_size = c.block;
   pr->opt.warp_aggregate = c.aggregate ? 1 : -1;
   pr->opt.tally_mode = pr->tally_mode;
+  pr->opt.ctas_per_sm = c.cps;
   pr->batch_per_cta = c.batch_per_cta;
   return choose_shape(pr, dl);
 }
@@ -544,11 +549,17 @@ int autotune(mcdc_problem *pr, const DeviceLimits &dl) {
   }
   const bool shared = pr->tally_mode == MCDC_TALLY_SHARED;
   std::vector<TuneChoice> cand;
-  for (int b : {128, 256, 512})
-    for (int bpc : shared ? std::vector<int>{1, 2, 4} : std::vector<int>{2})
-      for (int agg : pr->P.n_bins <= 65536 ? std::vector<int>{0, 1} : std::vector<int>{0})
-        cand.push_back({b, bpc, agg});
-  const TuneChoice keep{pr->block, pr->batch_per_cta, pr->warp_aggregate};
+  for (int b : {128, 256, 512}) {
+    // CTAs per SM: all that fit, and half of them when that is at least one
+    const int full = track_occupancy(pr->key, b, make_layout(pr, (b / 32) * kPool, pr->tally_mode).total);
+    std::vector<int> cps{0};
+    if (full >= 2) cps.push_back(full / 2);
+    for (int c : cps)
+      for (int bpc : shared ? std::vector<int>{1, 2, 4} : std::vector<int>{2})
+        for (int agg : pr->P.n_bins <= 65536 ? std::vector<int>{0, 1} : std::vector<int>{0})
+          cand.push_back({b, bpc, agg, c});
+  }
+  const TuneChoice keep{pr->block, pr->batch_per_cta, pr->warp_aggregate, pr->opt.ctas_per_sm};
   const uint64_t n_trial = 1ull << 20;
   double best_t = 1e300;
   TuneChoice best = keep;
@@ -1193,10 +1204,9 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       A.step_tbin = step;
       CK(launch_track(pr->key, pr->grid, pr->block, smem_pc, s, P, A, Ls));
       if (step >= P.T - 1) break;
-      CK(cudaMemcpyAsync(pr->h_spill, pr->pc_cnt, sizeof(unsigned long long),
-                         cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (*pr->h_spill == 0) break;
+      // no host round trip between steps: when nothing was banked the comb
+      // finds zero weight in every batch and the next step's launch finds
+      // an empty combed bank, so the remaining steps cost a few empty launches
       NvtxRange nvtx_comb("comb");
       CombArgs c{};
       c.bank = pr->pc_bank;

@@ -159,7 +159,7 @@ constexpr size_t kMaxPlans = 4;
 
 int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
                const uint64_t *n_histories, double *const *mean_dev, double *const *rel_dev,
-               int B, int block, unsigned long long chunk) {
+               int B, int block, unsigned long long chunk, int cps_want) {
   mcdc_problem *p0 = probs[0];
   // launch shape: the largest tables of the batch, no shared tally
   TrackKey key = p0->key;
@@ -181,8 +181,12 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   CKB(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p0->device));
   if (L.total > smem_max - 2048) return fail(MCDC_ERR_INVALID, "tables too large for shared memory");
   CKB(prepare_track(key, smem_max - 2048));
-  const int cps = track_occupancy(key, block, L.total);
+  int cps = track_occupancy(key, block, L.total);
   if (cps < 1) return fail(MCDC_ERR_INVALID, "launch shape does not fit");
+  if (cps_want > 0) {
+    if (cps_want > cps) return fail(MCDC_ERR_INVALID, "CTAs per SM beyond what fits");
+    cps = cps_want;
+  }
   const int grid = p0->sms * cps;
   pl.device = p0->device;
   pl.block = block;
@@ -281,7 +285,7 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
 int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_histories,
                 uint64_t seed, int32_t n_batches, double *const *mean_out,
                 double *const *relerr_out, double *scalar_out, mcdc_stats *stats, int block,
-                unsigned long long chunk, bool cache = true) {
+                unsigned long long chunk, int cps_want = 0, bool cache = true) {
   if (!probs || n < 1 || !n_histories) return fail(MCDC_ERR_INVALID, "need problems and history counts");
   if (n > 65535) return fail(MCDC_ERR_INVALID, "at most 65535 problems per batched run");
   const int B = n_batches > 0 ? n_batches : 16;
@@ -320,6 +324,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   key.push_back((uint64_t)B);
   key.push_back((uint64_t)block);
   key.push_back(chunk);
+  key.push_back((uint64_t)cps_want);
   for (int i = 0; i < n; ++i) {
     mdev[i] = mean_out && mean_out[i] && dev_ptr(mean_out[i]) ? mean_out[i] : nullptr;
     rdev[i] = relerr_out && relerr_out[i] && dev_ptr(relerr_out[i]) ? relerr_out[i] : nullptr;
@@ -345,7 +350,8 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
   if (!pl) {
     auto np = std::make_unique<BatchedPlan>();
     np->key = key;
-    if (int rc = build_plan(*np, probs, n, n_histories, mdev.data(), rdev.data(), B, block, chunk))
+    if (int rc = build_plan(*np, probs, n, n_histories, mdev.data(), rdev.data(), B, block, chunk,
+                            cps_want))
       return rc;
     if (cache) {
       if (g_plans.size() >= kMaxPlans) g_plans.erase(g_plans.begin());
@@ -431,7 +437,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
 }
 
 // launch shapes tried by the autotuner, and its choices per batch shape
-struct BatchedShape { int block; unsigned long long chunk; };
+struct BatchedShape { int block; unsigned long long chunk; int cps; };
 std::mutex g_batched_mu;
 std::map<std::string, BatchedShape> g_batched_cache;
 }  // namespace
@@ -444,8 +450,9 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
   if (!probs || n < 1 || !n_histories || !probs[0]) return fail(MCDC_ERR_INVALID, "need problems and history counts");
   // autotuner: the first time a batch shape is seen (problem count, total
   // histories to a power of two, precision, dimension, largest tables),
-  // time each candidate launch shape on the same problems with an eighth of
-  // the histories and keep the fastest
+  // time each candidate launch shape (threads per CTA, histories per work
+  // item, all or half the CTAs per SM that fit) on the same problems with an
+  // eighth of the histories and keep the fastest
   uint64_t total = 0;
   int maxM = 0, maxG = 0, maxT = 0;
   for (int i = 0; i < n; ++i) {
@@ -460,7 +467,7 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
   char kb[160];
   snprintf(kb, sizeof kb, "%d|%d|%d|%d|%d|%d|%d|%d|%d", n, lg, (int)probs[0]->key.f64,
            (int)probs[0]->key.local, probs[0]->dim, maxM, maxG, maxT, n_batches);
-  BatchedShape best{256, 1ull << 16};
+  BatchedShape best{256, 1ull << 16, 0};
   bool have = false;
   {
     std::lock_guard<std::mutex> lk(g_batched_mu);
@@ -475,20 +482,29 @@ extern "C" int mcdc_run_batched(struct mcdc_problem *const *probs, int32_t n,
     bool any = false;
     for (int block : {128, 256, 512})
       for (unsigned long long chunk : {1ull << 14, 1ull << 16}) {
-        mcdc_stats st{};
-        const int rc = run_batched(probs, n, trial.data(), seed ^ 0x5bd1e995ull, n_batches, nullptr,
-                                   nullptr, nullptr, &st, block, chunk, false);
-        if (rc == MCDC_ERR_INVALID) continue;        // this shape does not fit
-        if (rc != MCDC_OK) return rc;
-        any = true;
-        if (st.kernel_ms < best_ms) { best_ms = st.kernel_ms; best = {block, chunk}; }
+        int full_cps = 0;       // CTAs per SM of the full-occupancy trial
+        for (int half : {0, 1}) {
+          int cps = 0;
+          if (half) {
+            if (full_cps < 2) continue;
+            cps = full_cps / 2;
+          }
+          mcdc_stats st{};
+          const int rc = run_batched(probs, n, trial.data(), seed ^ 0x5bd1e995ull, n_batches,
+                                     nullptr, nullptr, nullptr, &st, block, chunk, cps, false);
+          if (rc == MCDC_ERR_INVALID) { mcdc::set_error(MCDC_OK, ""); continue; }   // does not fit
+          if (rc != MCDC_OK) return rc;
+          if (!half) full_cps = st.ctas_per_sm;
+          any = true;
+          if (st.kernel_ms < best_ms) { best_ms = st.kernel_ms; best = {block, chunk, cps}; }
+        }
       }
-    if (!any) best = {256, 1ull << 16};
+    if (!any) best = {256, 1ull << 16, 0};
     std::lock_guard<std::mutex> lk(g_batched_mu);
     g_batched_cache[kb] = best;
   }
   return run_batched(probs, n, n_histories, seed, n_batches, mean_out, relerr_out, scalar_out, stats,
-                     best.block, best.chunk);
+                     best.block, best.chunk, best.cps);
 }
 
 namespace mcdc {
