@@ -715,7 +715,11 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False, match_r
 # bench's own workload, keyed by (workload, precision, tally mode), with the
 # digest of the library sources the capture ran on: a figure is reported only
 # while the sources are unchanged (null otherwise, until it is re-measured).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one tracker launch
+    ("c2_slab_20cm_2region_td", "fp32_local", 1): (203776, "3bc10e6159f809e0"),
+    ("c3_channel_60cube_7g_td", "fp32_local", 2): (233970688 + 134276096, "3bc10e6159f809e0"),
+}
 
 
 def source_digest():
@@ -752,12 +756,15 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     (large meshes): 16 B of FP64 read-modify-write per flight against the
     measured copy bandwidth."""
     three_d = prob.n[1] > 1 or prob.n[2] > 1
-    if tally_mode == 2 and (prec_name != "fp32" or three_d):
-        ach = seg_rate * 16 / 1e9
+    if tally_mode == 2 and (prec_name == "fp64" or three_d):
+        # a read-modify-write of the scored bin: FP64 in FP64 mode, an FP32
+        # batch slice in the FP32 modes
+        bps = 16 if prec_name == "fp64" else 8
+        ach = seg_rate * bps / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"],
                 "traffic": measured_traffic(prob.name, prec_name, tally_mode),
-                "traffic_unit": "DRAM bytes per launch (ncu)", "bytes_per_segment": 16,
+                "traffic_unit": "DRAM bytes per launch (ncu)", "bytes_per_segment": bps,
                 "peak_kind": "measured copy (MEASURED_PEAKS.json hbm_gbs)"}
     if prec_name == "fp32":
         ops = 16.0 if three_d else 8.0
@@ -781,8 +788,10 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     peak = 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     ach = seg_rate * ops_per_seg / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T lane-ops/s",
-            "frac": ach / peak, "traffic": None, "ops_per_segment": ops_per_seg,
-            "peak_kind": "issue slots: 148 SM x 128 lanes x max SM clock"}
+            "frac": ach / peak, "traffic": measured_traffic(prob.name, prec_name, tally_mode),
+            "traffic_unit": "DRAM bytes per launch (ncu)", "ops_per_segment": ops_per_seg,
+            "peak_kind": "issue slots: 148 SM x 128 lanes x max SM clock (recipe unit "
+                         "counts and clock)"}
 
 
 if __name__ == "__main__":
