@@ -528,9 +528,13 @@ def variants(M, prob, n_hist, args, mean, rel, stream):
 # Weight-window settings of the learned windows: source window 0.25 (the
 # library default is 0.5), upper / survival ratios 4 / 2 (default 5 / 2.5).
 # Over five pilot seeds on both boxes their median learned FOM was 4.6e4 (deep)
-# and 7.0e4 (shallow) against 2.4e4 and 5.6e4 with the defaults; 20 epochs per
-# fit (instead of 6) raised the medians to 4.5e4 / 1.0e5 against 3.2e4 / 9.3e4
-# in the same sweep, and two refits are needed (one gave a deep median of 106).
+# and 7.0e4 (shallow) against 2.4e4 and 5.6e4 with the defaults, and two
+# refits are needed (one gave a deep median of 106).  The fits and the refit
+# runs count in the learned arm's time: swept over three pilot seeds with
+# pilot, fits and refits in T, 10 epochs of 32768-sample minibatches and
+# refit runs of 5e4 histories gave medians of 1.2e4 (deep) and 1.4e4
+# (shallow) against 1.05e4 and 6.7e3 for 20 epochs of 16384 and refits of
+# 1e5; 6 epochs, 40 epochs of 65536, or 3e4-history refits alone were worse.
 WW_SETTINGS = {"source_wl": 0.25, "upper_ratio": 4.0, "survival_ratio": 2.0}
 
 
@@ -553,7 +557,8 @@ def _timed(fn):
 
 
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7,
-             per_event=False, match_relerr=None, ww_batches=16):
+             per_event=False, match_relerr=None, ww_batches=16, epochs=10, fit_batch=32768,
+             n_refit=50_000):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
     region x in [90, 100]), analog against the learned weight windows.  The
@@ -595,13 +600,13 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         seed = seed0 + 4
         for it in range(refits + 1):
             rep, w = _timed(lambda: P.train_importance(
-                mean, rel, epochs=20, batch=16384, min_ratio=1e-20,
+                mean, rel, epochs=epochs, batch=fit_batch, min_ratio=1e-20,
                 per_event=int(per_event and it == refits), **WW_SETTINGS))
             fit_wall += w
             fit_dev += (rep["train_ms"] + rep["bake_ms"]) / 1e3
             if it < refits:
-                _, w = _timed(lambda: P.run_ex(n_ww, seed, batches=ww_batches, mean=mean,
-                                               relerr=rel))
+                _, w = _timed(lambda: P.run_ex(n_refit or n_ww, seed, batches=ww_batches,
+                                               mean=mean, relerr=rel))
                 ww_wall += w
                 seed += 1
         st, (m_w, r_w) = P.run_ex(n_ww, seed, batches=ww_batches)
