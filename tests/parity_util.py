@@ -46,12 +46,27 @@ COUNT_KEYS = ("histories", "segments", "collisions", "crossings", "census", "abs
               "censused", "splits", "children", "roulette_killed", "roulette_survived")
 
 
-def fp32_bins_agree(g, o, max_exceed=5, rel_max=0.25):
+def allowed_exceedances(n_bins, dof, z=4.0, p_fail=1e-3):
+    """The most bins that may show |z| > z by chance: the smallest k with
+    P(X > k) < p_fail for X ~ Binomial(n_bins, p), p the two-sided tail of
+    Student's t with `dof` degrees of freedom (a difference of two batch
+    means whose spreads are estimated from `dof` + 1 batches each; Welch's
+    combination has at least that many degrees of freedom, so the tail is
+    not underestimated)."""
+    from scipy import stats
+    p = 2.0 * stats.t.sf(z, dof)
+    k = 0
+    while stats.binom.sf(k, n_bins, p) >= p_fail:
+        k += 1
+    return k
+
+
+def fp32_bins_agree(g, o, batches, rel_max=0.25):
     """Per-bin statistical agreement of an FP32 run with an independent
-    oracle run: over the bins both estimate well (relative error <= rel_max,
-    about 16 or more scoring batches, where the batch-variance estimate is
-    close to normal) |z| > 4 at most max_exceed times; every bin the oracle
-    estimates well is scored by the GPU.  Returns (exceedances, bins)."""
+    oracle run: over the bins both estimate well (relative error <= rel_max)
+    |z| > 4 at most as often as chance allows (allowed_exceedances, with the
+    smaller run's batch count); every bin the oracle estimates well is
+    scored by the GPU.  Returns (exceedances, bins, allowed)."""
     gm, gr, om, orr = g["mean"], g["relerr"], o["mean"], o["relerr"]
     well_o = (om != 0) & (orr <= rel_max)
     assert np.all(gm[well_o] != 0), int((gm[well_o] == 0).sum())
@@ -59,8 +74,10 @@ def fp32_bins_agree(g, o, max_exceed=5, rel_max=0.25):
     s = np.sqrt((gm * gr) ** 2 + (om * orr) ** 2)[both]
     z = (gm - om)[both] / s
     n = int((np.abs(z) > 4).sum())
-    assert n <= max_exceed, (n, int(both.sum()))
-    return n, int(both.sum())
+    nb = int(both.sum())
+    k = allowed_exceedances(nb, batches - 1)
+    assert n <= k, (n, nb, k)
+    return n, nb, k
 
 
 def compare_counts(g, o):

@@ -120,7 +120,7 @@ def test_fp32_options_statistical(mcdc, prec, opts):
     z = (mg - mo) / np.hypot(mg * rg, mo * ro)
     assert abs(z) < 4.0, (mg, mo, z)
     # every well-estimated bin: |z| > 4 only about as often as chance allows
-    fp32_bins_agree(g, o)
+    fp32_bins_agree(g, o, batches=40)
 
 
 def test_batched_runs_take_the_collision_estimator_and_refuse_implicit_capture(mcdc):

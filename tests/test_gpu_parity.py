@@ -235,7 +235,7 @@ def test_fp32_c2_statistical_and_paired_bias(mcdc, prec):
     o = O.run(prob, 1_000_000, seed=1, batches=40)
     c = g32["counts"]
     assert c["absorbed"] + c["leaked"] + c["censused"] == N
-    n4, nbins = fp32_bins_agree(g32, o)
+    n4, nbins, _ = fp32_bins_agree(g32, o, batches=40)
     print("per-bin |z| > 4:", n4, "of", nbins, "well-estimated bins")
     # (2) coarse bins: neighbouring bins share histories, so the error of a
     # block comes from 32 independent replicas of each precision (the FP64

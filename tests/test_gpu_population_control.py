@@ -79,7 +79,7 @@ def test_fp32_population_control_statistical(mcdc, prec):
     (mg, rg), (mo, ro) = g["scalar"], o["scalar"]
     z = (mg - mo) / np.hypot(mg * rg, mo * ro)
     assert abs(z) < 4.0, (mg, mo, z)
-    fp32_bins_agree(g, o)
+    fp32_bins_agree(g, o, batches=B)
 
 
 def test_population_control_refusals(mcdc):
