@@ -470,22 +470,25 @@ int mcdc_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
 
 /* Per-event weight windows: instead of a table, every window check evaluates
  * the importance network (the layout of mcdc_mlp_forward with `hidden` units
- * per layer, 1..64; inputs 4 + G) at the particle itself.  Inputs: position
- * scaled to [-1, 1] over each bounded mesh axis (0 on an unbounded one), time
- * as 2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time bin j (0 in steady
- * state), then the group one-hot -- the continuous versions of the cell and
- * bin centres the network is trained on.  With its output y the lower bound
+ * per layer, 1..64) at the particle itself.  Inputs (n_in of them): position
+ * scaled to [-1, 1] over each bounded mesh axis (0 on an unbounded one); with
+ * n_in = 4 + G also time as 2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time
+ * bin j (0 in steady state) and the group one-hot -- the continuous versions
+ * of the cell and bin centres a network is trained on; with n_in = 3 the
+ * position alone.  With its output y the lower bound
  * is w_L = source_wl exp(min(0, max(y scale + shift, floor_lp) - top)); upper
  * and survival bounds and the split cap as in mcdc_set_weight_windows.
  * params: FP32, host or device, copied (FP64 mode evaluates in FP64 from the
- * same values); NULL turns windows off.  Replaces any table.  Needs the
- * global tally mode (the other kernels are built without the evaluation).
+ * same values, one check at a time; the FP32 modes evaluate the checks of a
+ * warp together on the tensor cores, BF16 operands, FP32 accumulation);
+ * NULL turns windows off.  Replaces any table.  Needs the global tally mode
+ * (the other kernels are built without the evaluation).
  * Errors: MCDC_ERR_INVALID (sizes, ratios, non-finite values, population
  * control, a shared-tally problem). */
-int mcdc_set_network_windows(struct mcdc_problem *prob, const float *params, int32_t hidden,
-                             double shift, double scale, double top, double floor_lp,
-                             double source_wl, double upper_ratio, double survival_ratio,
-                             int32_t nmax);
+int mcdc_set_network_windows(struct mcdc_problem *prob, const float *params, int32_t n_in,
+                             int32_t hidden, double shift, double scale, double top,
+                             double floor_lp, double source_wl, double upper_ratio,
+                             double survival_ratio, int32_t nmax);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);

@@ -153,6 +153,7 @@ int64_t orc_mlp_param_count(int32_t in, int32_t H);
 void orc_mlp_forward(int32_t in, int32_t H, int32_t bf16, const double *p, int64_t n,
                      const double *X, double *out);
 /* R15: the network's inputs for a particle at (x, y, z, t) in time bin tbin
+ * (a network of ww_net_in = 3 inputs takes the position alone)
  * and group g (see transport.c). */
 void orc_net_features(const orc_problem *p, double x, double y, double z, double t,
                       int32_t tbin, int32_t g, double *f);

@@ -150,10 +150,11 @@ def _struct(prob, ww=None, keep=None, estimator=EST_TRACK, implicit=None, pc_tar
     if ww is not None:
         # a table of lower bounds ("lower"), or per-event windows from the
         # network ("net": parameters, "hidden", "shift", "scale", "top",
-        # "floor", "wl0"; R15)
+        # "floor", "wl0", optional "n_in": 3 for a network over the position
+        # alone, else 4 + G; R15)
         if "net" in ww:
             s.ww_net = keep.ptr(_f64(ww["net"]))
-            s.ww_net_in = 4 + int(np.asarray(prob.sigma_t).shape[1])
+            s.ww_net_in = int(ww.get("n_in", 4 + int(np.asarray(prob.sigma_t).shape[1])))
             s.ww_net_h = int(ww.get("hidden", 64))
             s.ww_net_shift, s.ww_net_scale = float(ww["shift"]), float(ww["scale"])
             s.ww_net_top, s.ww_net_floor = float(ww["top"]), float(ww["floor"])
@@ -231,13 +232,14 @@ def run(prob, n, seed, offset=0, batches=32, threads=None, ww=None, estimator=ES
     return out
 
 
-def net_features(prob, x, y, z, t, tbin, g):
-    """The network's inputs for a particle (R15)."""
+def net_features(prob, x, y, z, t, tbin, g, n_in=None):
+    """The network's inputs for a particle (R15); n_in 3: the position only."""
     L = lib()
     keep = _Keep()
+    n_in = n_in or 4 + int(np.asarray(prob.sigma_t).shape[1])
     s = _struct(prob, {"net": np.zeros(1), "shift": 0.0, "scale": 1.0, "top": 0.0,
-                       "floor": 0.0, "wl0": 1.0}, keep)
-    f = np.zeros(4 + int(np.asarray(prob.sigma_t).shape[1]))
+                       "floor": 0.0, "wl0": 1.0, "n_in": n_in}, keep)
+    f = np.zeros(n_in)
     L.orc_net_features(C.byref(s), float(x), float(y), float(z), float(t), int(tbin), int(g),
                        f.ctypes.data)
     return f

@@ -266,6 +266,7 @@ void orc_net_features(const orc_problem *p, double x, double y, double z, double
         f[a] = axis_bounded(p, a)
                    ? 2.0 * (pos[a] - p->origin[a]) / ((double)p->n[a] * p->width[a]) - 1.0
                    : 0.0;
+    if (p->ww_net_in == 3) return;         /* a network over the position alone */
     if (p->n_tbin > 0) {
         int32_t j = tbin < p->n_tbin ? tbin : p->n_tbin - 1;
         double u = (t - p->edges[j]) / (p->edges[j + 1] - p->edges[j]);
@@ -611,7 +612,8 @@ static int make_tables(const orc_problem *p, tables *tb)
     if (p->pc_target > 0 &&
         (p->n_tbin < 2 || p->ww_lower != NULL || p->ww_net != NULL ||
          !(p->src_t1 < p->edges[1]))) return -1;
-    if (p->ww_net != NULL && (p->ww_net_in != 4 + p->n_grp || p->ww_net_in > 64 ||
+    if (p->ww_net != NULL && ((p->ww_net_in != 4 + p->n_grp && p->ww_net_in != 3) ||
+                              p->ww_net_in > 64 ||
                               p->ww_net_h < 1)) return -1;
     for (int64_t c = 0; c < tb->n_cells; ++c)
         if (p->material[c] >= M) return -1;

@@ -966,10 +966,10 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
   return ensure_overflow(pr);
 }
 
-int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32_t hidden,
-                              double shift, double scale, double top, double floor_lp,
-                              double source_wl, double upper_ratio, double survival_ratio,
-                              int32_t nmax) {
+int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32_t n_in,
+                              int32_t hidden, double shift, double scale, double top,
+                              double floor_lp, double source_wl, double upper_ratio,
+                              double survival_ratio, int32_t nmax) {
   g_err.clear();
   if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
   if (params == nullptr) return mcdc_set_weight_windows(pr, nullptr, 0.0, 0.0, 0);
@@ -984,8 +984,10 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   if (!(source_wl > 0.0) || !std::isfinite(shift) || !std::isfinite(scale) ||
       !std::isfinite(top) || !std::isfinite(floor_lp))
     return fail(MCDC_ERR_INVALID, "window constants must be finite (source_wl > 0)");
+  if (n_in != 3 && n_in != 4 + pr->P.G)
+    return fail(MCDC_ERR_INVALID, "n_in must be 3 (position) or 4 + groups (position, time, group)");
   CK(cudaSetDevice(pr->device));
-  const int in = 4 + pr->P.G;
+  const int in = n_in;
   // W1[hidden][in], b1[hidden], W2[hidden][hidden], b2[hidden], W3[hidden], b3
   const size_t n = (size_t)hidden * in + hidden + (size_t)hidden * hidden + 2 * (size_t)hidden + 1;
   std::vector<float> h32(n);

@@ -1488,7 +1488,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     low -= 1e4;
     const double floor_lp = std::fmax(low - 2.302585092994046,
                                       top + std::log(o.min_ratio > 0.0 ? o.min_ratio : 1e-8));
-    if (int rc = mcdc_set_network_windows(pr, prm, kH, hmom[3], hmom[4], top, floor_lp,
+    if (int rc = mcdc_set_network_windows(pr, prm, n_in, kH, hmom[3], hmom[4], top, floor_lp,
                                           o.source_wl, o.upper_ratio, o.survival_ratio, o.nmax))
       return rc;
   } else {

@@ -169,7 +169,21 @@ struct Layout {
   long long tally_bytes; // 0 in global mode
   int bank_bytes;
   int total;
+  int net_bytes;         // FP32 per-event network kernels: BF16 weights and per-warp input tiles
 };
+
+// Shared memory of the warp-batched network evaluation (FP32 modes): the
+// weights in BF16, zero-padded to 16 inputs and 64 hidden units, in rows
+// padded so that the 8 rows an ldmatrix phase reads fall in distinct banks,
+// and one 32-row input tile per warp.
+constexpr int kNetIn = 16, kNetH = 64;
+constexpr int kNetW1Row = 24;            // BF16 elements per row of W1 (48 bytes)
+constexpr int kNetW2Row = 72;            // BF16 elements per row of W2 (144 bytes)
+constexpr int kNetXRow = 24;             // BF16 elements per row of an input tile
+__host__ __device__ inline int net_smem_bytes(int warps) {
+  return kNetH * kNetW1Row * 2 + kNetH * kNetW2Row * 2 + 3 * kNetH * 4 +
+         warps * 32 * kNetXRow * 2;
+}
 
 __host__ __device__ inline int align16(long long v) { return (int)((v + 15) & ~15ll); }
 
@@ -267,12 +281,14 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
 
 // ---------------------------------------------------------------------------
 // Per-event windows: the importance network evaluated at the particle.
-// Inputs: position scaled to [-1, 1] over each bounded axis of the mesh,
-// time as 2 (j + (t - t_j) / (t_j+1 - t_j)) / T - 1 in time bin j (0 in steady
-// state), the group one-hot -- the continuous versions of the cell and bin
-// centres the network is trained on.  FP64 mode evaluates in FP64 in the
-// order of the oracle's loops; the FP32 modes in FP32.  Not inlined: the
-// hidden layer lives in this call's own frame, off the tracker's registers.
+// Inputs: position scaled to [-1, 1] over each bounded axis of the mesh; a
+// network of 4 + G inputs also takes time as 2 (j + (t - t_j) / (t_j+1 - t_j))
+// / T - 1 in time bin j (0 in steady state) and the group one-hot -- the
+// continuous versions of the cell and bin centres the network is trained on
+// (a network of 3 inputs takes the position alone).  FP64 mode evaluates in
+// FP64 in the order of the oracle's loops; the FP32 modes in FP32.  Not
+// inlined: the hidden layer lives in this call's own frame, off the
+// tracker's registers.
 template <class PR, int DIM>
 __device__ __noinline__ typename PR::R net_window(const DevProblem &P, const PartOf<PR> &p) {
   using R = typename PR::R;
@@ -289,7 +305,9 @@ __device__ __noinline__ typename PR::R net_window(const DevProblem &P, const Par
   for (int a = 0; a < 3; ++a)
     f[a] = P.bounded[a] ? (R)(2.0 * (pos[a] - P.origin[a]) / ((double)P.n[a] * P.width[a]) - 1.0)
                         : (R)0;
-  if (P.T > 0) {
+  if (P.ww_net_in == 3) {
+    // position only
+  } else if (P.T > 0) {
     const int j = p.tbin < P.T ? p.tbin : P.T - 1;
     const double u = (t - P.edges[j]) / (P.edges[j + 1] - P.edges[j]);
     f[3] = (R)(2.0 * ((double)j + u) / (double)P.T - 1.0);
@@ -328,20 +346,12 @@ __device__ __noinline__ typename PR::R net_window(const DevProblem &P, const Par
 // reservation of the run's children budget.  NET: the lower bound comes from
 // the network when one is set (separate instantiations, so that the others
 // carry no call).
-template <class PR, int DIM, bool NET>
-__device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> &tb,
-                              const RunArgs &A, const EndSink &es, PartOf<PR> &p,
-                              int *s_novf, PartOf<PR> *ovf) {
+// The split or roulette of a window check with lower bound wl (wl <= 0: no
+// window here).  Returns false if the particle is rouletted away.
+template <class PR, int DIM>
+__device__ bool ww_apply(const DevProblem &P, const RunArgs &A, const EndSink &es,
+                         PartOf<PR> &p, typename PR::R wl, int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
-  if (tb.ww == nullptr && !(NET && P.ww_net64 != nullptr)) return true;
-  R wl;
-  if (NET && P.ww_net64 != nullptr) {
-    if constexpr (NET) wl = net_window<PR, DIM>(P, p);
-  } else {
-    const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
-    const int bin = bin_index(P, cell, p.g, p.tbin);
-    if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
-  }
   if (!(wl > (R)0)) return true;
   const R wu = (R)P.ww_upper * wl;
   if (p.w > wu) {
@@ -416,6 +426,27 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
     return false;
   }
   return true;
+}
+
+// A window check: the lower bound from the table, or from the network
+// evaluated at the particle (one particle at a time; the FP32 network kernels
+// evaluate a warp's checks together instead, see net_window_warp), then the
+// split or roulette.
+template <class PR, int DIM, bool NET>
+__device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> &tb,
+                              const RunArgs &A, const EndSink &es, PartOf<PR> &p,
+                              int *s_novf, PartOf<PR> *ovf) {
+  using R = typename PR::R;
+  if (tb.ww == nullptr && !(NET && P.ww_net64 != nullptr)) return true;
+  R wl;
+  if (NET && P.ww_net64 != nullptr) {
+    if constexpr (NET) wl = net_window<PR, DIM>(P, p);
+  } else {
+    const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
+    const int bin = bin_index(P, cell, p.g, p.tbin);
+    if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
+  }
+  return ww_apply<PR, DIM>(P, A, es, p, wl, s_novf, ovf);
 }
 
 // ---------------------------------------------------------------------------

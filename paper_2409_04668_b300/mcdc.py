@@ -142,9 +142,9 @@ SIGNATURES = {
     "mcdc_run_noalloc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcdc_measure_fp64_pipe": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
-    "mcdc_set_network_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+    "mcdc_set_network_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                            C.c_double, C.c_double, C.c_double, C.c_double,
-                                           C.c_double, C.c_double, C.c_int32]),
+                                           C.c_double, C.c_double, C.c_double, C.c_int32]),
     "mcdc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
 }
@@ -333,13 +333,15 @@ class Problem:
                                _ptr(sum1), _ptr(sum2), _ptr(mean), _ptr(relerr), stream))
 
     def set_network_windows(self, params, hidden, shift, scale, top, floor, wl0,
-                            upper_ratio=5.0, survival_ratio=2.5, nmax=16):
+                            upper_ratio=5.0, survival_ratio=2.5, nmax=16, n_in=None):
         """Per-event windows from the network (see mcdc_set_network_windows);
-        params None turns windows off."""
+        params None turns windows off; n_in: 3 (position) or 4 + G (default)."""
         p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
-        check(mcdc_set_network_windows(self.handle, _ptr(p), int(hidden), float(shift),
-                                       float(scale), float(top), float(floor), float(wl0),
-                                       float(upper_ratio), float(survival_ratio), int(nmax)))
+        G = int(np.asarray(self.desc.sigma_t).shape[1])
+        check(mcdc_set_network_windows(self.handle, _ptr(p), int(n_in or 4 + G), int(hidden),
+                                       float(shift), float(scale), float(top), float(floor),
+                                       float(wl0), float(upper_ratio), float(survival_ratio),
+                                       int(nmax)))
 
     def train_importance(self, pilot_mean, pilot_relerr=None, **opts):
         """Fits the importance network to a pilot tally and switches this

@@ -7,7 +7,9 @@ from the CUDA path).
   group (no weight on position or time) gives, event for event, the run with
   the table of its values (identical tallies and counts);
 * unbiasedness: spatially varying network windows leave the infinite-medium
-  flux at its closed form 1 / Sigma_a, with splits and roulettes happening.
+  flux at its closed form 1 / Sigma_a, with splits and roulettes happening;
+* a network over the position alone (3 inputs) is, event for event, the
+  full-input network whose time and group weights are zero.
 """
 import numpy as np
 import pytest
@@ -96,3 +98,23 @@ def test_varying_network_windows_are_unbiased():
     m, r = res["scalar"]
     ref = 24.0 / (0.2 * 18.0)
     assert abs(m - ref) < 4.0 * m * r, (m, ref, r)
+
+
+def test_position_only_network_equals_full_network_without_time_and_group():
+    prob = _box()
+    G, H = 2, 8
+    rng = np.random.default_rng(19)
+    p3 = _net(3, H, rng)
+    W1 = p3[:H * 3].reshape(H, 3)
+    full = np.concatenate([np.concatenate([W1, np.zeros((H, 1 + G))], axis=1).ravel(),
+                           p3[H * 3:]])
+    consts = {"hidden": H, "shift": -0.3, "scale": 2.0, "top": 1.0, "floor": -3.0,
+              "wl0": 0.6, "upper_ratio": 4.0, "survival_ratio": 2.0, "nmax": 8}
+    f3 = O.net_features(prob, 0.6, 1.2, 0.3, 1.25, 1, 0, n_in=3)
+    assert f3.shape == (3,)
+    np.testing.assert_array_equal(f3, O.net_features(prob, 0.6, 1.2, 0.3, 1.25, 1, 0)[:3])
+    a = O.run(prob, 4000, seed=7, batches=8, ww={"net": p3, "n_in": 3, **consts}, threads=2)
+    b = O.run(prob, 4000, seed=7, batches=8, ww={"net": full, **consts}, threads=2)
+    assert a["counts"] == b["counts"]
+    assert a["counts"]["splits"] > 0 and a["counts"]["roulette_killed"] > 0
+    np.testing.assert_allclose(a["sum1"], b["sum1"], rtol=1e-12, atol=0)
