@@ -191,6 +191,15 @@ typedef struct mcdc_options {
                                    If the slices cannot be allocated the run
                                    falls back to one launch per batch.
                                    Population control always uses slices.       */
+    int32_t overflow_tail;      /* global tally with weight windows: stack slots a
+                                   warp keeps for new split children once its own
+                                   particles (source histories, or a pass's share
+                                   of the spilled ones) are used up; the children
+                                   beyond go to the device-wide banks, which every
+                                   warp shares in the next pass, instead of one
+                                   warp working through a large family while the
+                                   others have finished (-1: the whole stack;
+                                   default 8)                                   */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */
@@ -349,12 +358,18 @@ typedef struct mcdc_mlp_options {
                                    way to the region and are rouletted away from it;
                                    time and group folds then keep the smallest w_L */
     int32_t per_event;          /* 0 (default): bake a table of windows; 1: no table --
-                                   every window check evaluates the trained network
-                                   at the particle (mcdc_set_network_windows with the
-                                   bake's constants), so windows vary continuously in
-                                   position and time and are resolved in time and
-                                   group (the folds above do not apply).  Needs a
+                                   every window check evaluates a network at the
+                                   particle (mcdc_set_network_windows).  With the
+                                   time and group folds above (the defaults) the
+                                   baked table depends on the cell alone, and a
+                                   network of the position (3 inputs) is fitted to
+                                   its log, one sample per cell centre: windows
+                                   continuous in position, folded like the table.
+                                   With time_resolved or group_resolved set, the
+                                   trained network itself with the bake's
+                                   constants (resolved in time and group).  Needs a
                                    forward pilot (adjoint 0) and the global tally   */
+    int32_t distill_steps;      /* Adam steps of that position network (0: 2000)   */
 } mcdc_mlp_options;
 
 typedef struct mcdc_mlp_report {
@@ -363,6 +378,11 @@ typedef struct mcdc_mlp_report {
     double train_ms, bake_ms;   /* device time of training and of the bake       */
     int32_t steps;              /* Adam steps                                    */
     double target_mean;         /* weighted mean of the log-flux targets         */
+    int32_t distill_steps;      /* per-event windows of a cell-only table: Adam
+                                   steps of the position network fitted to it
+                                   (0 otherwise)                                 */
+    double distill_loss;        /* its mean minibatch loss in the last epoch
+                                   (targets normalised to unit variance)         */
 } mcdc_mlp_report;
 
 void mcdc_default_mlp_options(mcdc_mlp_options *opt);
@@ -489,6 +509,27 @@ int mcdc_set_network_windows(struct mcdc_problem *prob, const float *params, int
                              int32_t hidden, double shift, double scale, double top,
                              double floor_lp, double source_wl, double upper_ratio,
                              double survival_ratio, int32_t nmax);
+
+/* The lower bounds of the last window table: set by mcdc_set_weight_windows
+ * or baked by mcdc_train_importance (also the table a per-event position
+ * network was fitted to), [n_bins] doubles in the tally's bin layout into
+ * w_lower (host or device, caller-owned); blocks until copied.
+ * Errors: MCDC_ERR_INVALID (NULL arguments, no table yet), MCDC_ERR_CUDA. */
+int mcdc_get_weight_windows(const struct mcdc_problem *prob, double *w_lower);
+
+/* The lower bounds w_L that the window checks of the network set by
+ * mcdc_set_network_windows apply to particles in n given states: position
+ * x[3 i .. 3 i + 2], time t[i], group g[i].  Each state becomes a particle in
+ * the problem's own representation (the cell holding the position, clamped
+ * into the mesh; in MCDC_PREC_FP32_LOCAL the FP32 offsets from the cell's low
+ * faces and the time left to the next census edge) and goes through the
+ * tracker's own evaluation: FP64 mode one state at a time in FP64, the FP32
+ * modes 32 at a time on the tensor cores.  A group outside 0..G-1 gives NaN.
+ * x, t, g, w_lower: host or device, caller-owned; blocks until done.
+ * Errors: MCDC_ERR_INVALID (no network set, n < 0, NULL arrays),
+ * MCDC_ERR_OOM, MCDC_ERR_CUDA. */
+int mcdc_network_window_lower(struct mcdc_problem *prob, const double *x, const double *t,
+                              const int32_t *g, int64_t n, double *w_lower);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);

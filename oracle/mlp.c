@@ -280,6 +280,72 @@ void orc_mlp_error_bounds(int32_t in, int32_t H, const double *p, int64_t n, con
 }
 
 /*
+ * Tolerance of the warp-batched window evaluation (test infrastructure): a
+ * first-order bound, per sample, of |computed output - exact output| when
+ *   - every input carries an absolute error x_abs (its FP32 computation) and
+ *     is then rounded to an operand format of unit roundoff u, as are W1, W2
+ *     and W3;
+ *   - every sum accumulates in FP32 (K terms: at most 2 K 2^-24 times the sum
+ *     of the absolute terms, K the padded width: 16 or 32 inputs, 64 hidden);
+ *   - every activation is computed as s = round(h + h t), h = round(z / 2),
+ *     t = tanh(h) within eps_t (absolute): |s - silu(z)| <= u |z| |silu'(z)|
+ *     + eps_t |z| / 2 + u |silu(z)| to first order -- the layer-1 activation is
+ *     then an operand of layer 2 as it stands, the layer-2 one an operand of
+ *     the output layer (a product with W3, FP32 accumulation, then + b3).
+ * Bounds are carried as in orc_mlp_error_bounds.  f_bound[n].
+ */
+static double act_err(double z, double u, double eps_t)
+{
+    return u * fabs(z) * fabs(dsilu(z)) + 0.5 * eps_t * fabs(z) + u * fabs(silu(z));
+}
+
+void orc_mlp_window_bound(int32_t in, int32_t H, const double *p, int64_t n, const double *X,
+                          double u, double eps_t, double x_abs, double *f_bound)
+{
+    const double u32 = 1.0 / 16777216.0;
+    const double *W1 = p, *b1 = W1 + (int64_t)H * in, *W2 = b1 + H, *b2 = W2 + (int64_t)H * H;
+    const double *W3 = b2 + H, *b3 = W3 + H;
+    const double k1 = in > 16 ? 32.0 : 16.0, k2 = 64.0;
+    double *buf = (double *)malloc(sizeof(double) * 4 * H + sizeof(double) * in);
+    double *h1 = buf, *eh1 = h1 + H, *h2 = eh1 + H, *eh2 = h2 + H, *ex = eh2 + H;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = X + i * in;
+        for (int32_t k = 0; k < in; ++k) ex[k] = x_abs + u * (fabs(x[k]) + x_abs);
+        for (int32_t j = 0; j < H; ++j) {               /* layer 1 */
+            double a = b1[j], e = 0.0, s = fabs(b1[j]);
+            for (int32_t k = 0; k < in; ++k) {
+                const double t = fabs(W1[(int64_t)j * in + k]);
+                a += W1[(int64_t)j * in + k] * x[k];
+                e += t * ex[k] + u * t * fabs(x[k]);
+                s += t * fabs(x[k]);
+            }
+            const double ez = e + 2.0 * k1 * u32 * s;
+            h1[j] = silu(a);
+            eh1[j] = fabs(dsilu(a)) * ez + act_err(a, u, eps_t);
+        }
+        for (int32_t j = 0; j < H; ++j) {               /* layer 2 */
+            double a = b2[j], e = 0.0, s = fabs(b2[j]);
+            for (int32_t k = 0; k < H; ++k) {
+                const double t = fabs(W2[(int64_t)j * H + k]);
+                a += W2[(int64_t)j * H + k] * h1[k];
+                e += t * eh1[k] + u * t * fabs(h1[k]);
+                s += t * fabs(h1[k]);
+            }
+            const double ez = e + 2.0 * k2 * u32 * s;
+            h2[j] = silu(a);
+            eh2[j] = fabs(dsilu(a)) * ez + act_err(a, u, eps_t);
+        }
+        double ef = 0.0, sf = fabs(b3[0]);
+        for (int32_t k = 0; k < H; ++k) {
+            ef += fabs(W3[k]) * eh2[k] + u * fabs(W3[k]) * fabs(h2[k]);
+            sf += fabs(W3[k] * h2[k]);
+        }
+        f_bound[i] = ef + 2.0 * (k2 + 1.0) * u32 * sf;
+    }
+    free(buf);
+}
+
+/*
  * Training (test reference for the library's training call): `epochs` passes
  * over minibatches of `batch` consecutive samples (the last one shorter); per
  * minibatch the loss and gradient of orc_mlp_loss_grad (bf16 as there) and

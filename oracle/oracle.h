@@ -164,6 +164,11 @@ double orc_mlp_loss_grad(int32_t in, int32_t H, int32_t bf16, const double *p, i
 void orc_mlp_error_bounds(int32_t in, int32_t H, const double *p, int64_t n, const double *X,
                           const double *y, const double *w, double *f_bound, double *g_bound,
                           double *loss_bound, double *g_abssum, double *g_absmax);
+/* First-order bound of the warp-batched window evaluation's error per sample:
+ * inputs with absolute error x_abs, operands rounded with unit roundoff u,
+ * FP32 sums, activations h + h tanh(h) with tanh within eps_t (mlp.c). */
+void orc_mlp_window_bound(int32_t in, int32_t H, const double *p, int64_t n, const double *X,
+                          double u, double eps_t, double x_abs, double *f_bound);
 void orc_adam_step(int64_t np, double *p, double *m, double *v, const double *g, double lr,
                    double b1, double b2, double eps, int64_t t);
 /* Adam over minibatches of consecutive samples, `epochs` passes (mlp.c). */

@@ -94,6 +94,9 @@ def _bind_mlp(L):
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
     L.orc_mlp_error_bounds.restype = None
+    L.orc_mlp_window_bound.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.c_double, C.c_double, C.c_double, C.c_void_p]
+    L.orc_mlp_window_bound.restype = None
     L.orc_mlp_param_count.argtypes = [C.c_int32, C.c_int32]
     L.orc_mlp_param_count.restype = C.c_int64
     L.orc_mlp_forward.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
@@ -348,6 +351,19 @@ def mlp_error_bounds(params, X, y, w, hidden=64):
                                y.ctypes.data, w.ctypes.data, fb.ctypes.data, gb.ctypes.data,
                                C.byref(lb), gs.ctypes.data, gm.ctypes.data)
     return fb, gb, lb.value, gs, gm
+
+
+def mlp_window_bound(params, X, hidden=64, u=2.0 ** -11, eps_t=2.0 ** -9, x_abs=2.0 ** -22):
+    """First-order bound of the warp-batched window evaluation's output error
+    per sample (see orc_mlp_window_bound): operands of unit roundoff u (2^-11:
+    binary16), FP32 sums, activations h + h tanh(h) with tanh within eps_t,
+    inputs computed in FP32 with absolute error x_abs."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    lib().orc_mlp_window_bound(X.shape[1], hidden, p.ctypes.data, X.shape[0], X.ctypes.data,
+                               float(u), float(eps_t), float(x_abs), out.ctypes.data)
+    return out
 
 
 def adam_step(p, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

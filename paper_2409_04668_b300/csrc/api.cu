@@ -271,7 +271,8 @@ Layout make_layout(const mcdc_problem *pr, int S, int tally_mode) {
                       ? align16((long long)pr->P.n_tally * (f64 ? 8 : 4))
                       : 0;
   L.bank_bytes = S * slot_bytes(f64, pr->dim, pr->key.local);
-  L.total = (int)(L.tables_bytes + L.tally_bytes + L.bank_bytes + 64);
+  L.net_bytes = (pr->key.net && !f64) ? kNetFragBytes + (S / kPool) * kNetWarpBytes : 0;
+  L.total = (int)(L.tables_bytes + L.tally_bytes + L.bank_bytes + L.net_bytes + 64);
   return L;
 }
 
@@ -593,6 +594,77 @@ namespace {
 // Switches the problem between the tracker built with and without the
 // per-event network evaluation and redoes the launch shape for it (registers
 // and so CTAs per SM may differ).
+// IEEE binary16 of an FP32 value, rounded to nearest with ties to even
+// (finite inputs below the binary16 overflow threshold; subnormals kept)
+uint16_t f16_rne(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  const uint32_t sign = (u >> 16) & 0x8000u, mant = u & 0x7fffffu;
+  const int e = (int)((u >> 23) & 0xffu) - 127 + 15;   // binary16 biased exponent
+  uint32_t q, rem, half;
+  if (e >= 1) {                 // normal: 10 fraction bits, 13 dropped
+    q = ((uint32_t)e << 10) | (mant >> 13);
+    rem = mant & 0x1fffu;
+    half = 0x1000u;
+  } else {                      // subnormal: value / 2^-24, from the full significand
+    const int shift = 14 - e;
+    if (shift > 24) return (uint16_t)sign;
+    const uint32_t sig = mant | 0x800000u;
+    q = sig >> shift;
+    rem = sig & ((1u << shift) - 1u);
+    half = 1u << (shift - 1);
+  }
+  if (rem > half || (rem == half && (q & 1u))) q += 1u;   // a carry moves the exponent up
+  return (uint16_t)(sign | q);
+}
+
+// The network (layout of mcdc_mlp_forward: W1[H][in], b1, W2[H][H], b2, W3, b3)
+// as the tracker's fragment block: for n-tile j, K step s and lane L (column
+// g = L / 4 of the tile's 8, pair t = L % 4), the two words of the mma.sync
+// m16n8k16 B fragment, {B[16s+2t][g], B[16s+2t+1][g]} and {B[16s+2t+8][g],
+// B[16s+2t+9][g]} in binary16 (the lower index in the low half), with
+// B[k][g] = W[8j+g][k] / 2 for layers 1 and 2 and B[k][0] = W3[k] (other
+// columns zero) for the output layer, zero outside the network; b1 / 2 and
+// b2 / 2 in FP32, padded to 64.
+std::vector<uint32_t> net_fragments(const float *prm, int in, int H) {
+  std::vector<uint32_t> f(kNetFragWords, 0u);
+  const float *W1 = prm, *b1 = W1 + (size_t)H * in, *W2 = b1 + H, *b2 = W2 + (size_t)H * H,
+              *W3 = b2 + H;
+  auto w1 = [&](int n, int k) { return (n < H && k < in) ? 0.5f * W1[n * in + k] : 0.0f; };
+  auto w2 = [&](int n, int k) { return (n < H && k < H) ? 0.5f * W2[n * H + k] : 0.0f; };
+  auto w3 = [&](int n, int k) { return (n == 0 && k < H) ? W3[k] : 0.0f; };
+  auto pair = [](float lo, float hi) {
+    return (uint32_t)f16_rne(lo) | ((uint32_t)f16_rne(hi) << 16);
+  };
+  for (int L = 0; L < 32; ++L) {
+    const int g = L / 4, t = L % 4;
+    for (int j = 0; j < 8; ++j) {
+      const int n = 8 * j + g;
+      for (int s = 0; s < 2; ++s) {
+        const int k = 16 * s + 2 * t, at = kNetW1Frag + ((j * 2 + s) * 32 + L) * 2;
+        f[at] = pair(w1(n, k), w1(n, k + 1));
+        f[at + 1] = pair(w1(n, k + 8), w1(n, k + 9));
+      }
+      for (int s = 0; s < 4; ++s) {
+        const int k = 16 * s + 2 * t, at = kNetW2Frag + ((j * 4 + s) * 32 + L) * 2;
+        f[at] = pair(w2(n, k), w2(n, k + 1));
+        f[at + 1] = pair(w2(n, k + 8), w2(n, k + 9));
+      }
+    }
+    for (int s = 0; s < 4; ++s) {
+      const int k = 16 * s + 2 * t, at = kNetW3Frag + (s * 32 + L) * 2;
+      f[at] = pair(w3(g, k), w3(g, k + 1));
+      f[at + 1] = pair(w3(g, k + 8), w3(g, k + 9));
+    }
+  }
+  for (int n = 0; n < H; ++n) {
+    const float h1 = 0.5f * b1[n], h2 = 0.5f * b2[n];
+    std::memcpy(&f[kNetB1 + n], &h1, 4);
+    std::memcpy(&f[kNetB2 + n], &h2, 4);
+  }
+  return f;
+}
+
 int set_net_kernel(mcdc_problem *pr, bool net) {
   if (pr->key.net == net) return MCDC_OK;
   pr->key.net = net;
@@ -623,6 +695,7 @@ void mcdc_default_options(mcdc_options *o) {
   o->estimator = MCDC_EST_TRACK;
   o->weight_cutoff = 0.25;
   o->cutoff_survival = 0.5;
+  o->overflow_tail = 8;
 }
 
 const char *mcdc_last_error(void) { return g_err.c_str(); }
@@ -651,6 +724,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (o.pc_target < 0) return fail(MCDC_ERR_INVALID, "pc_target must be >= 0");
   if (o.flight_sampling != 0 && o.flight_sampling != 1)
     return fail(MCDC_ERR_INVALID, "flight_sampling must be 0 or 1");
+  if (o.overflow_tail < -1) return fail(MCDC_ERR_INVALID, "overflow_tail must be >= -1");
   if (o.pc_target > 0 && o.tally_mode == MCDC_TALLY_SHARED)
     return fail(MCDC_ERR_INVALID, "population control runs on the global tally");
 
@@ -932,6 +1006,7 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
     pr->P.ww_lower32 = nullptr;
     pr->P.ww_net64 = nullptr;
     pr->P.ww_net32 = nullptr;
+    pr->P.ww_netfrag = nullptr;
     return set_net_kernel(pr, false);
   }
   if (pr->P.pc_target > 0)
@@ -954,11 +1029,13 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
     if ((rc = dalloc(pr, &pr->ww32, nb))) return rc;
   }
   CK(cudaMemcpy(pr->ww64, h.data(), nb * 8, cudaMemcpyHostToDevice));
+  pr->ww_table_valid = true;
   CK(cudaMemcpy(pr->ww32, h32.data(), nb * 4, cudaMemcpyHostToDevice));
   pr->P.ww_lower = pr->ww64;
   pr->P.ww_lower32 = pr->ww32;
   pr->P.ww_net64 = nullptr;
   pr->P.ww_net32 = nullptr;
+  pr->P.ww_netfrag = nullptr;
   pr->P.ww_upper = upper_ratio;
   pr->P.ww_survival = survival_ratio;
   pr->P.ww_nmax = nmax;
@@ -998,14 +1075,30 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
     if (!std::isfinite(h32[q])) return fail(MCDC_ERR_INVALID, "network parameter is not finite");
     h64[q] = (double)h32[q];
   }
+  if (!pr->key.f64) {
+    // the FP32 modes hold W1 / 2, W2 / 2 and W3 in binary16
+    const size_t w1 = (size_t)hidden * in, b1 = w1 + hidden, w2 = b1 + (size_t)hidden * hidden,
+                 w3 = w2 + hidden;
+    for (size_t q = 0; q < w3 + hidden; ++q) {
+      const bool weight = q < w1 || (q >= b1 && q < w2) || q >= w3;
+      const float lim = q >= w3 ? 65504.0f : 131008.0f;
+      if (weight && std::fabs(h32[q]) >= lim)
+        return fail(MCDC_ERR_INVALID, "network weight beyond the binary16 range of the FP32 modes");
+    }
+  }
   if (pr->net_cap < n) {
     int rc;
     if ((rc = dalloc(pr, &pr->net64, n))) return rc;
     if ((rc = dalloc(pr, &pr->net32, n))) return rc;
     pr->net_cap = n;
   }
+  if (!pr->netfrag) {
+    if (int rc = dalloc(pr, &pr->netfrag, (size_t)kNetFragWords)) return rc;
+  }
+  const std::vector<uint32_t> frag = net_fragments(h32.data(), in, hidden);
   CK(cudaMemcpy(pr->net64, h64.data(), n * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pr->net32, h32.data(), n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pr->netfrag, frag.data(), (size_t)kNetFragBytes, cudaMemcpyHostToDevice));
   // the network kernel first: if its launch shape fails, nothing changes
   if (int rc = set_net_kernel(pr, true)) {
     const std::string msg = g_err;
@@ -1017,6 +1110,8 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   P.ww_lower32 = nullptr;
   P.ww_net64 = pr->net64;
   P.ww_net32 = pr->net32;
+  P.ww_netfrag = pr->netfrag;
+  P.ww_net_b3 = h32[n - 1];
   P.ww_net_in = in;
   P.ww_net_h = hidden;
   P.ww_net_shift = shift;
@@ -1028,6 +1123,61 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   P.ww_survival = survival_ratio;
   P.ww_nmax = nmax;
   return ensure_overflow(pr);
+}
+
+int mcdc_get_weight_windows(const struct mcdc_problem *pr, double *w_lower) {
+  g_err.clear();
+  if (!pr || !w_lower) return fail(MCDC_ERR_INVALID, "problem and w_lower are required");
+  if (!pr->ww_table_valid || !pr->ww64) return fail(MCDC_ERR_INVALID, "no window table yet");
+  CK(cudaSetDevice(pr->device));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(w_lower, pr->ww64, sizeof(double) * (size_t)pr->P.n_bins, cudaMemcpyDefault));
+  return MCDC_OK;
+}
+
+int mcdc_network_window_lower(struct mcdc_problem *pr, const double *x, const double *t,
+                              const int32_t *g, int64_t n, double *w_lower) {
+  g_err.clear();
+  if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
+  if (pr->P.ww_net64 == nullptr) return fail(MCDC_ERR_INVALID, "no network windows are set");
+  if (n < 0) return fail(MCDC_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return MCDC_OK;
+  if (!x || !t || !g || !w_lower) return fail(MCDC_ERR_INVALID, "x, t, g and w_lower are required");
+  CK(cudaSetDevice(pr->device));
+  // device copies of host arrays (a diagnostic entry point, not a hot path)
+  const size_t un = (size_t)n;
+  std::vector<void *> tmp;
+  auto dev_in = [&](const void *src, size_t bytes, const void **out) -> cudaError_t {
+    if (is_device_ptr(src)) { *out = src; return cudaSuccess; }
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return e;
+    tmp.push_back(d);
+    *out = d;
+    return cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+  };
+  const void *dx = nullptr, *dt = nullptr, *dg = nullptr;
+  void *dout = w_lower;
+  cudaError_t e = dev_in(x, 24 * un, &dx);
+  if (e == cudaSuccess) e = dev_in(t, 8 * un, &dt);
+  if (e == cudaSuccess) e = dev_in(g, 4 * un, &dg);
+  const bool host_out = !is_device_ptr(w_lower);
+  if (e == cudaSuccess && host_out) {
+    e = cudaMalloc(&dout, 8 * un);
+    if (e == cudaSuccess) tmp.push_back(dout);
+  }
+  if (e == cudaSuccess)
+    e = launch_net_lower(pr->key, nullptr, pr->P, (const double *)dx, (const double *)dt,
+                         (const int32_t *)dg, (long long)n, (double *)dout, pr->sms);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && host_out) e = cudaMemcpy(w_lower, dout, 8 * un, cudaMemcpyDeviceToHost);
+  for (void *d : tmp) cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? MCDC_ERR_OOM : MCDC_ERR_CUDA,
+                std::string("window evaluation: ") + cudaGetErrorString(e));
+  }
+  return MCDC_OK;
 }
 
 int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *stats) {
@@ -1107,6 +1257,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   A.error = pr->error;
   A.overflow = pr->overflow;
   A.overflow_cap = pr->overflow_cap;
+  A.overflow_tail = pr->opt.overflow_tail;
   A.warp_aggregate = pr->warp_aggregate;
   A.tally = pr->tally;
   if (pr->opt.max_children >= 0) {

@@ -54,6 +54,8 @@ struct DevProblem {
   // map of its output y to w_L = wl0 exp(min(0, max(y scale + shift, floor) - top))
   const double *ww_net64;
   const float *ww_net32;
+  const uint32_t *ww_netfrag; // the same network as BF16 mma.sync fragments (FP32 modes)
+  float ww_net_b3;            // its output bias
   int32_t ww_net_in, ww_net_h;
   double ww_net_shift, ww_net_scale, ww_net_top, ww_net_floor, ww_net_wl0;
   double ww_upper, ww_survival;
@@ -164,6 +166,8 @@ struct RunArgs {
   // per-warp overflow stacks for split children: [warps in grid][overflow_cap]
   void *overflow;
   int32_t overflow_cap;       // per warp
+  int32_t overflow_tail;      // slots a warp keeps once its own particles are exhausted
+                              // (children beyond spill; -1: overflow_cap)
   int32_t warp_aggregate;
   // global-tally mode with weight windows: children beyond the warp's stack
   // spill to a device-wide bank, run in a later pass by every warp

@@ -66,6 +66,11 @@ cudaError_t launch_track(const TrackKey &key, int grid, int block, int smem_byte
 cudaError_t prepare_track(const TrackKey &key, int smem_bytes);
 // Registers per thread of that instantiation (for occupancy decisions).
 int track_regs(const TrackKey &key);
+// The window lower bounds at n given states (positions x[3 n], times, groups)
+// through that precision's own evaluation (k_net_lower); all device pointers.
+cudaError_t launch_net_lower(const TrackKey &key, cudaStream_t s, const DevProblem &P,
+                             const double *x, const double *t, const int32_t *g, long long n,
+                             double *out, int sms);
 // Resident CTAs per SM for a block size and dynamic shared memory.
 int track_occupancy(const TrackKey &key, int block, int smem_bytes);
 

@@ -550,7 +550,8 @@ struct TrainArgs {
   double *losses;                // [2 n_steps]: loss per minibatch, first and last epoch
   unsigned long long *bar;       // grid-barrier arrivals (zero at launch)
   int *err;                      // set when a wait gives up; every CTA then leaves
-  float lr;
+  float lr, lr_end;               // step size: lr at the first step, cosine down to lr_end
+                                 // at the last (lr_end = lr: constant)
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
@@ -718,6 +719,9 @@ __global__ void __launch_bounds__(kGroups * kTM) k_mlp_train_tc(const TrainArgs 
     {
       const float b1 = 0.9f, b2 = 0.999f;
       const float c1 = 1.f - powf(b1, (float)(k + 1)), c2 = 1.f - powf(b2, (float)(k + 1));
+      const int k_last = A.epochs * A.n_steps - 1;
+      const float lr = A.lr_end + 0.5f * (A.lr - A.lr_end) *
+                                      (1.0f + cospif(k_last > 0 ? (float)k / (float)k_last : 0.0f));
       const int nt = kGroups * kTM;
       for (int c0 = 0; c0 < nslice; c0 += nt) {
         const int nc = min(nt, nslice - c0);
@@ -746,7 +750,7 @@ __global__ void __launch_bounds__(kGroups * kTM) k_mlp_train_tc(const TrainArgs 
           const float vi = b2 * A.v[i] + (1.f - b2) * gi * gi;
           A.m[i] = mi;
           A.v[i] = vi;
-          A.p[i] -= A.lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+          A.p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
         }
         __syncthreads();
       }
@@ -863,6 +867,37 @@ __global__ void k_normalize_targets(int64_t n, float *__restrict__ Y, const floa
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x)
     if (W[s] > 0.0f) Y[s] = (float)((Y[s] - mu) / sd);
+}
+
+// Samples of the spatial distillation: one per cell, the position inputs of
+// its centre (as k_make_samples) and the log of its window in a table that
+// depends on the cell alone (time and group folded); unit weights
+__global__ void k_distill_samples(const DevProblem P, const double *__restrict__ ww64,
+                                  float *__restrict__ X, float *__restrict__ Y,
+                                  float *__restrict__ W, double *__restrict__ moments) {
+  double sw = 0.0, swt = 0.0, swt2 = 0.0;
+  const int64_t nc = P.n_cells, per_cell = (int64_t)P.G * P.T1;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int idx[3] = {(int)(c % P.n[0]), (int)((c / P.n[0]) % P.n[1]),
+                        (int)(c / ((int64_t)P.n[0] * P.n[1]))};
+    for (int a = 0; a < 3; ++a)
+      X[c * 3 + a] = P.bounded[a] ? (float)(2.0 * (idx[a] + 0.5) / P.n[a] - 1.0) : 0.0f;
+    const double t = log(ww64[c * per_cell]);
+    Y[c] = (float)t;
+    W[c] = 1.0f;
+    sw += 1.0; swt += t; swt2 += t * t;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    swt += __shfl_xor_sync(0xffffffffu, swt, o);
+    swt2 += __shfl_xor_sync(0xffffffffu, swt2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&moments[0], sw);
+    atomicAdd(&moments[1], swt);
+    atomicAdd(&moments[2], swt2);
+  }
 }
 
 // 1 / (sum of the weights of minibatch b), one block per minibatch (FP64 sums)
@@ -1144,7 +1179,7 @@ int device_sms() {
 int train_fused(PoolBufs &tmp, cudaStream_t st, int sms, const float *Xc, const float *Yc,
                 const float *Wc, int64_t n_samples, int n_in, int epochs, int batch, float lr,
                 const float *d_inv, int n_steps, float *prm, float *m, float *v, double *losses,
-                double *loss_first, double *loss_last, int32_t *steps) {
+                double *loss_first, double *loss_last, int32_t *steps, float lr_end) {
   *loss_first = *loss_last = 0.0;
   *steps = 0;
   if (n_steps <= 0) return MCDC_OK;
@@ -1174,6 +1209,7 @@ int train_fused(PoolBufs &tmp, cudaStream_t st, int sms, const float *Xc, const 
   ta.p = prm; ta.m = m; ta.v = v;
   ta.part = part; ta.losses = losses; ta.bar = d_bar; ta.err = d_err;
   ta.lr = lr;
+  ta.lr_end = lr_end;
   void *kargs[] = {&ta};
   CKM(cudaLaunchCooperativeKernel((const void *)k_mlp_train_tc, dim3(grid), dim3(kGroups * kTM),
                                   kargs, sizeof(TcGrad), st));
@@ -1298,7 +1334,7 @@ extern "C" int mcdc_mlp_train(float *params, int32_t n_in, const float *X, const
   double lf, ll;
   int32_t steps;
   if (int rc = train_fused(tmp, st, device_sms(), dX, dY, dW, n, n_in, epochs, batch, (float)lr,
-                           d_inv, n_steps, prm, m, v, losses, &lf, &ll, &steps))
+                           d_inv, n_steps, prm, m, v, losses, &lf, &ll, &steps, (float)lr))
     return rc;
   CKM(cudaMemcpyAsync(params, prm, sizeof(float) * np, cudaMemcpyDefault, st));
   CKM(cudaStreamSynchronize(st));
@@ -1330,6 +1366,29 @@ extern "C" void mcdc_default_mlp_options(mcdc_mlp_options *o) {
   o->min_ratio = 1e-8;
 }
 
+// Initial parameters for n_in inputs: U(-1/sqrt(fan_in), 1/sqrt(fan_in))
+// weights (splitmix64 uniforms from the seed), zero biases
+std::vector<float> init_params(int n_in, uint64_t seed) {
+  std::vector<float> h((size_t)mlp_param_count(n_in), 0.0f);
+  uint64_t sd = seed * 0x9E3779B97F4A7C15ull + 12345;
+  auto unif = [&]() {   // splitmix64 -> (0, 1)
+    sd += 0x9E3779B97F4A7C15ull;
+    uint64_t z = sd;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * 0x1.0p-53;
+  };
+  const float a1 = 1.0f / std::sqrt((float)n_in), a2 = 1.0f / std::sqrt((float)kH);
+  int64_t off = 0;
+  for (int64_t i = 0; i < (int64_t)kH * n_in; ++i) h[off + i] = (float)((2 * unif() - 1) * a1);
+  off += (int64_t)kH * n_in + kH;
+  for (int64_t i = 0; i < (int64_t)kH * kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
+  off += (int64_t)kH * kH + kH;
+  for (int64_t i = 0; i < kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
+  return h;
+}
+
 extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilot_mean,
                                      const double *pilot_relerr, const mcdc_mlp_options *opt,
                                      mcdc_mlp_report *rep) {
@@ -1339,8 +1398,10 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
   mcdc_mlp_options o;
   if (opt) o = *opt; else mcdc_default_mlp_options(&o);
-  if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0))
-    return fail(MCDC_ERR_INVALID, "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0");
+  if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0) ||
+      o.distill_steps < 0)
+    return fail(MCDC_ERR_INVALID,
+                "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0, distill_steps >= 0");
   if (o.per_event && (o.adjoint || pr->tally_mode != MCDC_TALLY_GLOBAL))
     return fail(MCDC_ERR_INVALID, "per-event windows need a forward pilot and the global tally");
   const DevProblem &P = pr->P;
@@ -1384,26 +1445,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   const int64_t steps_per_epoch = (nb + o.batch - 1) / o.batch;
   CKM(tmp.get(&losses, (size_t)steps_per_epoch * 2));
 
-  // parameters: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
-  std::vector<float> h(np, 0.0f);
-  {
-    uint64_t sd = o.seed * 0x9E3779B97F4A7C15ull + 12345;
-    auto unif = [&]() {   // splitmix64 -> (0, 1)
-      sd += 0x9E3779B97F4A7C15ull;
-      uint64_t z = sd;
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      z ^= z >> 31;
-      return ((z >> 11) + 0.5) * 0x1.0p-53;
-    };
-    const float a1 = 1.0f / std::sqrt((float)n_in), a2 = 1.0f / std::sqrt((float)kH);
-    int64_t off = 0;
-    for (int64_t i = 0; i < (int64_t)kH * n_in; ++i) h[off + i] = (float)((2 * unif() - 1) * a1);
-    off += (int64_t)kH * n_in + kH;
-    for (int64_t i = 0; i < (int64_t)kH * kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
-    off += (int64_t)kH * kH + kH;
-    for (int64_t i = 0; i < kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
-  }
+  std::vector<float> h = init_params(n_in, o.seed);
   const int sms = pr->sms;
   const uint64_t stride = coprime_stride((uint64_t)nb);
   CKM(mlp_prepare());
@@ -1458,7 +1500,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   int32_t steps = 0;
   if (int rc = train_fused(tmp, st, sms, Xc, Yc, Wc, n_samples, n_in, o.epochs, o.batch,
                            (float)o.lr, d_inv, n_steps, prm, m, v, losses, &loss_first,
-                           &loss_last, &steps))
+                           &loss_last, &steps, (float)o.lr))
     return rc;
   CKM(cudaEventRecord(e1, st));
   // bake: predict every bin, weight windows proportional to the predicted flux
@@ -1473,7 +1515,12 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     k_pred_src_max<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx + 2);
     CKM(cudaGetLastError());
   }
-  if (o.per_event) {
+  const bool fold_g = !o.group_resolved && P.G > 1, fold_t = !o.time_resolved && P.T1 > 1;
+  // windows of the cell alone (time and group folded, or absent)
+  const bool spatial = (fold_g || P.G == 1) && (fold_t || P.T1 == 1);
+  int32_t d_steps = 0;
+  double d_loss = 0.0;
+  if (o.per_event && !spatial) {
     // the network itself sets every window: the constants of the bake below
     // (top, floor) with the trained parameters, evaluated at each event
     unsigned long long hmx[2];
@@ -1492,39 +1539,104 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
                                           o.source_wl, o.upper_ratio, o.survival_ratio, o.nmax))
       return rc;
   } else {
-  if (!pr->ww64) {
-    void *a, *b;
-    CKM(cudaMalloc(&a, sizeof(double) * nb));
-    pr->allocs.push_back(a);
-    CKM(cudaMalloc(&b, sizeof(float) * nb));
-    pr->allocs.push_back(b);
-    pr->ww64 = (double *)a;
-    pr->ww32 = (float *)b;
-  }
-  if (o.adjoint)
-    k_ww_from_importance<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, o.source_wl,
-                                                 o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
-                                                 pr->ww32);
-  else
-    k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
-                                           o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
-                                           pr->ww32);
-  CKM(cudaGetLastError());
-  const bool fold_g = !o.group_resolved && P.G > 1, fold_t = !o.time_resolved && P.T1 > 1;
-  if (fold_g || fold_t) {
-    k_ww_collapse<<<blocks, 256, 0, st>>>(P, fold_g, fold_t, o.adjoint != 0, pr->ww64, pr->ww32);
+    if (!pr->ww64) {
+      void *a, *b;
+      CKM(cudaMalloc(&a, sizeof(double) * nb));
+      pr->allocs.push_back(a);
+      CKM(cudaMalloc(&b, sizeof(float) * nb));
+      pr->allocs.push_back(b);
+      pr->ww64 = (double *)a;
+      pr->ww32 = (float *)b;
+    }
+    if (o.adjoint)
+      k_ww_from_importance<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, o.source_wl,
+                                                   o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
+                                                   pr->ww32);
+    else
+      k_ww_from_pred<<<blocks, 256, 0, st>>>(P, stride, pred, mom, mx, mx + 1, o.source_wl,
+                                             o.min_ratio > 0.0 ? o.min_ratio : 1e-8, pr->ww64,
+                                             pr->ww32);
     CKM(cudaGetLastError());
-  }
-  CKM(cudaEventRecord(e2, st));
-  CKM(cudaStreamSynchronize(st));
-  if (int rc = tc_status()) return rc;      // the windows are not switched on
-  // switch the problem to weight windows (w_U, w_S ratios as given)
-  pr->P.ww_lower = pr->ww64;
-  pr->P.ww_lower32 = pr->ww32;
-  pr->P.ww_upper = o.upper_ratio;
-  pr->P.ww_survival = o.survival_ratio;
-  pr->P.ww_nmax = o.nmax;
-  if (int rc = mcdc::ensure_overflow_for(pr)) return rc;
+    if (fold_g || fold_t) {
+      k_ww_collapse<<<blocks, 256, 0, st>>>(P, fold_g, fold_t, o.adjoint != 0, pr->ww64, pr->ww32);
+      CKM(cudaGetLastError());
+    }
+    pr->ww_table_valid = true;
+    if (o.per_event) {
+      // per-event windows of the cell-only table: a network of the position
+      // alone is fitted to the log of the folded table, one sample per cell
+      // centre, and evaluated at every window check (continuous in position,
+      // folded in time and group like the table)
+      const int64_t nc = P.n_cells;
+      const int64_t np3 = mlp_param_count(3);
+      float *X3, *Y3, *W3, *prm3, *m3, *v3, *inv3;
+      double *mom3, *loss3;
+      const int batch3 = (int)std::max<int64_t>(kS, std::min<int64_t>(o.batch, (nc + 7) / 8));
+      const int steps3 = (int)((nc + batch3 - 1) / batch3);
+      const int want3 = o.distill_steps > 0 ? o.distill_steps : 2000;
+    const int epochs3 = std::max(1, (want3 + steps3 - 1) / steps3);
+      CKM(tmp.get(&X3, (size_t)nc * 3));
+      CKM(tmp.get(&Y3, (size_t)nc));
+      CKM(tmp.get(&W3, (size_t)nc));
+      CKM(tmp.get(&prm3, (size_t)((np3 + 3) & ~3ll)));
+      CKM(tmp.get(&m3, (size_t)np3));
+      CKM(tmp.get(&v3, (size_t)np3));
+      CKM(tmp.get(&inv3, (size_t)steps3));
+      CKM(tmp.get(&mom3, 8));
+      CKM(tmp.get(&loss3, (size_t)steps3 * 2));
+      const std::vector<float> h3 = init_params(3, o.seed + 1);
+      CKM(cudaMemcpyAsync(prm3, h3.data(), sizeof(float) * np3, cudaMemcpyHostToDevice, st));
+      CKM(cudaMemsetAsync(m3, 0, sizeof(float) * np3, st));
+      CKM(cudaMemsetAsync(v3, 0, sizeof(float) * np3, st));
+      CKM(cudaMemsetAsync(mom3, 0, sizeof(double) * 8, st));
+      CKM(cudaMemsetAsync(loss3, 0, sizeof(double) * steps3 * 2, st));
+      k_distill_samples<<<blocks, 256, 0, st>>>(P, pr->ww64, X3, Y3, W3, mom3);
+      CKM(cudaGetLastError());
+      k_normalize_targets<<<blocks, 256, 0, st>>>(nc, Y3, W3, mom3);
+      CKM(cudaGetLastError());
+      k_minibatch_inv<<<steps3, 256, 0, st>>>(nc, batch3, W3, inv3);
+      CKM(cudaGetLastError());
+      double d_first = 0.0;
+      // the step size falls from lr to lr / 20 over the fit (cosine): the
+      // table is a fixed target, fitted as closely as the steps allow
+      if (int rc = train_fused(tmp, st, sms, X3, Y3, W3, nc, 3, epochs3, batch3, (float)o.lr, inv3,
+                               steps3, prm3, m3, v3, loss3, &d_first, &d_loss, &d_steps,
+                               (float)(o.lr / 20.0)))
+        return rc;
+      unsigned long long hmx[2];
+      double hm3[8];
+      CKM(cudaMemcpyAsync(hmx, mx, sizeof hmx, cudaMemcpyDeviceToHost, st));
+      CKM(cudaMemcpyAsync(hm3, mom3, sizeof hm3, cudaMemcpyDeviceToHost, st));
+      CKM(cudaEventRecord(e2, st));
+      CKM(cudaStreamSynchronize(st));
+      if (int rc = tc_status()) return rc;
+      double top, low;
+      std::memcpy(&top, &hmx[0], 8);
+      std::memcpy(&low, &hmx[1], 8);
+      top -= 1e4;
+      low -= 1e4;
+      // the table is source_wl exp(min(0, max(lp, floor_lp) - top)): its log
+      // lies in [log source_wl + floor_lp - top, log source_wl], so w_L =
+      // source_wl exp(min(0, max(y sd + mu, that floor) - log source_wl))
+      const double floor_lp = std::fmax(low - 2.302585092994046,
+                                        top + std::log(o.min_ratio > 0.0 ? o.min_ratio : 1e-8));
+      const double lw0 = std::log(o.source_wl);
+      if (int rc = mcdc_set_network_windows(pr, prm3, 3, kH, hm3[3], hm3[4], lw0,
+                                            lw0 + floor_lp - top, o.source_wl, o.upper_ratio,
+                                            o.survival_ratio, o.nmax))
+        return rc;
+    } else {
+      CKM(cudaEventRecord(e2, st));
+      CKM(cudaStreamSynchronize(st));
+      if (int rc = tc_status()) return rc;      // the windows are not switched on
+      // switch the problem to weight windows (w_U, w_S ratios as given)
+      pr->P.ww_lower = pr->ww64;
+      pr->P.ww_lower32 = pr->ww32;
+      pr->P.ww_upper = o.upper_ratio;
+      pr->P.ww_survival = o.survival_ratio;
+      pr->P.ww_nmax = o.nmax;
+      if (int rc = mcdc::ensure_overflow_for(pr)) return rc;
+    }
   }
   if (rep) {
     float a = 0.f, b = 0.f;
@@ -1537,6 +1649,8 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
     rep->bake_ms = b;
     rep->steps = steps;
     rep->target_mean = hmom[1] / hmom[0];
+    rep->distill_steps = d_steps;
+    rep->distill_loss = d_loss;
   }
   return MCDC_OK;
 }

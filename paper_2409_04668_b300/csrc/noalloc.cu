@@ -145,6 +145,7 @@ extern "C" int mcdc_run_noalloc(struct mcdc_problem *pr, uint64_t n_histories, u
   A.error = sc->error;
   A.overflow = pr->overflow;
   A.overflow_cap = pr->overflow_cap;
+  A.overflow_tail = pr->opt.overflow_tail;
   A.warp_aggregate = pr->warp_aggregate;
   A.tally = global ? sc->tally : nullptr;
   if (pr->opt.max_children >= 0) {

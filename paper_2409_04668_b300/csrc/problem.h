@@ -45,11 +45,13 @@ struct mcdc_problem {
   size_t overflow_bytes = 0;
   mcdc::Record *rec_tmp = nullptr;
   uint64_t rec_cap = 0;
-  double *ww64 = nullptr;
+  double *ww64 = nullptr;      // the last window table set or baked
+  bool ww_table_valid = false;
   float *ww32 = nullptr;
   double *net64 = nullptr;      // per-event windows: network parameters
   float *net32 = nullptr;
   size_t net_cap = 0;
+  uint32_t *netfrag = nullptr;  // the same network as BF16 mma.sync fragments (kNetFragWords)
   // population control: census bank (by input position), combed bank and
   // the comb's scratch
   int pc_cap = 0;                          // input positions the census bank holds

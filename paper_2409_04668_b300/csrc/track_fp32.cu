@@ -1,6 +1,8 @@
 // track_fp32.cu -- FP32-split instantiations of the tracker (FP32 direction,
 // distance and cross sections; FP64 position, time and tally reduction) and
 // the FP32 cell-local instantiations, and the dispatch over all precisions.
+#include <algorithm>
+
 #include "launch.h"
 #include "tracker.cuh"
 
@@ -11,6 +13,8 @@ cudaError_t launch_track_f64(const TrackKey &, int, int, int, cudaStream_t, cons
 cudaError_t prepare_track_f64(const TrackKey &, int);
 int track_regs_f64(const TrackKey &);
 int track_occupancy_f64(const TrackKey &, int, int);
+cudaError_t launch_net_lower_f64(const TrackKey &, cudaStream_t, const DevProblem &, const double *,
+                                 const double *, const int32_t *, long long, double *, int);
 
 namespace {
 template <class PR, bool SH, int DIM, bool MU, bool NET = false>
@@ -48,6 +52,30 @@ int track_occupancy(const TrackKey &key, int block, int smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(key), block, (size_t)smem) != cudaSuccess)
     return -1;
   return n;
+}
+
+namespace {
+template <class PR>
+cudaError_t net_lower_prec(const TrackKey &key, cudaStream_t s, const DevProblem &P,
+                           const double *x, const double *t, const int32_t *g, long long n,
+                           double *out, int blocks) {
+  void *k = key.dim == 1 ? (void *)k_net_lower<PR, 1> : (void *)k_net_lower<PR, 3>;
+  const int smem = kNetFragBytes + 8 * kNetWarpBytes;          // 256 threads: 8 warps
+  if (cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))
+    return e;
+  void *args[] = {(void *)&P, (void *)&x, (void *)&t, (void *)&g, (void *)&n, (void *)&out};
+  return cudaLaunchKernel(k, dim3(blocks), dim3(256), args, (size_t)smem, s);
+}
+}  // namespace
+
+cudaError_t launch_net_lower(const TrackKey &key, cudaStream_t s, const DevProblem &P,
+                             const double *x, const double *t, const int32_t *g, long long n,
+                             double *out, int sms) {
+  if (n <= 0) return cudaSuccess;
+  if (key.f64) return launch_net_lower_f64(key, s, P, x, t, g, n, out, sms);
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 8ll * sms);
+  return key.local ? net_lower_prec<PrecF32L>(key, s, P, x, t, g, n, out, blocks)
+                   : net_lower_prec<PrecF32>(key, s, P, x, t, g, n, out, blocks);
 }
 
 int track_regs(const TrackKey &key) {

@@ -1,6 +1,8 @@
 // track_fp64.cu -- FP64 instantiations of the tracker.  This translation unit
 // is compiled with -fmad=false so that every product and sum is rounded on
 // its own, in the order the source states them.
+#include <algorithm>
+
 #include "launch.h"
 #include "tracker.cuh"
 
@@ -34,6 +36,15 @@ int track_occupancy_f64(const TrackKey &key, int block, int smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(key), block, (size_t)smem) != cudaSuccess)
     return -1;
   return n;
+}
+
+cudaError_t launch_net_lower_f64(const TrackKey &key, cudaStream_t s, const DevProblem &P,
+                                 const double *x, const double *t, const int32_t *g,
+                                 long long n, double *out, int sms) {
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 8ll * sms);
+  if (key.dim == 1) k_net_lower<PrecF64, 1><<<blocks, 256, 0, s>>>(P, x, t, g, n, out);
+  else k_net_lower<PrecF64, 3><<<blocks, 256, 0, s>>>(P, x, t, g, n, out);
+  return cudaGetLastError();
 }
 
 int track_regs_f64(const TrackKey &key) {

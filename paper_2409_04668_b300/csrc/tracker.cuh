@@ -169,21 +169,29 @@ struct Layout {
   long long tally_bytes; // 0 in global mode
   int bank_bytes;
   int total;
-  int net_bytes;         // FP32 per-event network kernels: BF16 weights and per-warp input tiles
+  int net_bytes;         // FP32 per-event network kernels: the fragment block and the
+                         // warps' tiles (kNetFragBytes + warps x kNetWarpBytes)
 };
 
-// Shared memory of the warp-batched network evaluation (FP32 modes): the
-// weights in BF16, zero-padded to 16 inputs and 64 hidden units, in rows
-// padded so that the 8 rows an ldmatrix phase reads fall in distinct banks,
-// and one 32-row input tile per warp.
-constexpr int kNetIn = 16, kNetH = 64;
-constexpr int kNetW1Row = 24;            // BF16 elements per row of W1 (48 bytes)
-constexpr int kNetW2Row = 72;            // BF16 elements per row of W2 (144 bytes)
-constexpr int kNetXRow = 24;             // BF16 elements per row of an input tile
-__host__ __device__ inline int net_smem_bytes(int warps) {
-  return kNetH * kNetW1Row * 2 + kNetH * kNetW2Row * 2 + 3 * kNetH * 4 +
-         warps * 32 * kNetXRow * 2;
-}
+// The warp-batched network evaluation of the FP32 modes reads the network
+// from shared memory, arranged on the host in the order of the mma.sync
+// m16n8k16 B fragments (F16 pairs; hidden padded to 64, inputs to 32) so that
+// each lane loads its fragment as one 8-byte word:
+//   W1 / 2 fragments [n-tile 8][k-step 2][lane 32][2 words]   words    0 .. 1023
+//   W2 / 2 fragments [n-tile 8][k-step 4][lane 32][2 words]   words 1024 .. 3071
+//   b1 / 2, b2 / 2 in FP32, 64 each                           words 3072 .. 3199
+//   W3 fragments, output in column 0 of one n-tile:
+//                    [k-step 4][lane 32][2 words]             words 3200 .. 3455
+// (the halves make the hidden accumulators z / 2, the argument SiLU's tanh
+// takes; scaling by 2^-1 is exact)
+constexpr int kNetW1Frag = 0, kNetW2Frag = 1024, kNetB1 = 3072, kNetB2 = 3136, kNetW3Frag = 3200;
+constexpr int kNetFragWords = 3456;
+constexpr int kNetFragBytes = kNetFragWords * 4;     // 13824, a multiple of 16
+// then per warp: its input tile, 32 rows of 32 F16 inputs padded to 80 bytes
+// (the 8 rows of an ldmatrix phase fall in distinct banks), and the 32
+// outputs of its rows
+constexpr int kNetRowBytes = 80;
+constexpr int kNetWarpBytes = 32 * kNetRowBytes + 32 * 4;
 
 __host__ __device__ inline int align16(long long v) { return (int)((v + 15) & ~15ll); }
 
@@ -340,14 +348,11 @@ __device__ __noinline__ typename PR::R net_window(const DevProblem &P, const Par
 }
 
 // ---------------------------------------------------------------------------
-// weight window at collisions and cell crossings.  Returns false if the
-// particle is rouletted away.  Children go to the warp's overflow stack
-// (s_novf[0]: its size) or the spill bank; s_novf[16] is the warp's
-// reservation of the run's children budget.  NET: the lower bound comes from
-// the network when one is set (separate instantiations, so that the others
-// carry no call).
-// The split or roulette of a window check with lower bound wl (wl <= 0: no
-// window here).  Returns false if the particle is rouletted away.
+// Weight windows at collisions and cell crossings.  The split or roulette of
+// a window check with lower bound wl (wl <= 0: no window here); returns false
+// if the particle is rouletted away.  Children go to the warp's overflow
+// stack (s_novf[0]: its size, s_novf[32]: its current limit) or the spill
+// bank; s_novf[16] is the warp's reservation of the run's children budget.
 template <class PR, int DIM>
 __device__ bool ww_apply(const DevProblem &P, const RunArgs &A, const EndSink &es,
                          PartOf<PR> &p, typename PR::R wl, int *s_novf, PartOf<PR> *ovf) {
@@ -386,7 +391,7 @@ __device__ bool ww_apply(const DevProblem &P, const RunArgs &A, const EndSink &e
         ch.nseg = ch.ncol = ch.ncross = 0;
         ch.tau = -1.0f;                 // FP32 modes: drawn from the child's own stream
         const int slot = atomicAdd(s_novf, 1);
-        if (slot < A.overflow_cap) {
+        if (slot < s_novf[32]) {          // the warp's current stack limit
           ovf[slot] = ch;
           made += 1;
         } else {
@@ -440,7 +445,9 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
   if (tb.ww == nullptr && !(NET && P.ww_net64 != nullptr)) return true;
   R wl;
   if (NET && P.ww_net64 != nullptr) {
-    if constexpr (NET) wl = net_window<PR, DIM>(P, p);
+    // FP64 kernels; the FP32 ones check in warps (flight and collide defer)
+    if constexpr (NET && PR::kF64) wl = net_window<PR, DIM>(P, p);
+    else wl = (R)0;
   } else {
     const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
     const int bin = bin_index(P, cell, p.g, p.tbin);
@@ -555,7 +562,10 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 // ---------------------------------------------------------------------------
 // one flight.  Returns 0 continue, 1 collision queued, 2 ended (end code in
 // *end), 3 reached an interior census edge under population control (banked)
-enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3 };
+// 3 reached an interior census edge under population control (banked),
+// 4 crossed into a new cell with its window check left to the warp (FP32
+// network kernels: net_check_warp after the flight pass)
+enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3, OUT_WW = 4 };
 
 template <class PR, int DIM, bool NET>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
@@ -733,6 +743,9 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if (ax == 0) p.i = nxt; else if (ax == 1) p.j = nxt; else p.k = nxt;
     p.ncross += 1;
     lc.cross += 1;
+    if constexpr (NET && !PR::kF64) {
+      if (P.ww_net32 != nullptr) return OUT_WW;
+    }
     if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
     return OUT_CONT;
   }
@@ -750,7 +763,8 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
                                         const RunArgs &A, const EndSink &es,
                                         PartOf<PR> &p, int &end, LocalCount &lc,
                                         int *s_novf, PartOf<PR> *ovf,
-                                        int &cbin, typename PR::R &cscore, double &wabs) {
+                                        int &cbin, typename PR::R &cscore, double &wabs,
+                                        bool &ww_pend) {
   using R = typename PR::R;
   const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
   const int m = __ldg(P.material + cell);
@@ -801,6 +815,10 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
       p.w = wsurv;
       atomicAdd(&es.n_end[4], 1u);
     }
+  }
+  if constexpr (NET && !PR::kF64) {
+    // FP32 network kernels: the check is left to the warp (net_check_warp)
+    if (P.ww_net32 != nullptr) { ww_pend = true; return true; }
   }
   if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
   return true;
@@ -869,6 +887,251 @@ __device__ __forceinline__ int nth32(uint32_t m, int n) {
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-batched per-event windows (FP32 modes).  The window checks a warp
+// meets in one flight pass or one collision pass are gathered into the rows
+// of an M = 16 or 32 tile (the pending lanes in lane order: each writes its
+// inputs as binary16 into row `rank` of the warp's tile in shared memory)
+// and the network runs on the tensor cores as three products, mma.sync
+// m16n8k16 with binary16 operands and FP32 accumulation (A fragments of the
+// inputs by ldmatrix).  Layers 1 and 2 use halved weights and biases, so
+// their accumulators are h = z / 2, and SiLU(z) = h + h tanh(h) (sigma(z) =
+// (1 + tanh(z / 2)) / 2) runs on binary16 pairs, one tanh.approx.f16x2 for two
+// values; the pairs are already the A fragments of the next product (an
+// m16n8 C tile pair has the register layout of an m16k16 A tile).  The output
+// layer is a product with one n-tile whose column 0 holds W3: its
+// accumulator's column 0 is the output of each row.  Hidden units beyond the
+// network's width have zero weights and biases (SiLU(0) = 0 keeps them out);
+// inputs beyond n_in are zero.
+
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// SiLU(2 h0), SiLU(2 h1) as a binary16 pair: h + h tanh(h)
+__device__ __forceinline__ uint32_t silu_half_f16x2(float h0, float h1) {
+  const uint32_t h = pack_f16x2(h0, h1);
+  uint32_t t, r;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+  asm("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));
+  return r;
+}
+
+__device__ __forceinline__ void mma_f16_16816(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+
+// The network outputs y (before the window mapping) of rows 0..npend-1 of the
+// warp's tile, into ys[row]; all 32 lanes call it together.  nf: the fragment
+// block, tile/ys: the warp's tile and outputs (shared memory).
+static __device__ __noinline__ void net_eval_warp(const uint32_t *nf, const unsigned char *tile,
+                                                  float *ys, int npend, int H, bool k2,
+                                                  float b3) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nt = (H + 7) >> 3;          // n-tiles that hold hidden units
+  const int ks = (H + 15) >> 4;         // K steps over the hidden units
+  const uint2 *w1 = reinterpret_cast<const uint2 *>(nf + kNetW1Frag);
+  const uint2 *w2 = reinterpret_cast<const uint2 *>(nf + kNetW2Frag);
+  const uint2 *w3 = reinterpret_cast<const uint2 *>(nf + kNetW3Frag);
+  const float2 *b1 = reinterpret_cast<const float2 *>(nf + kNetB1);
+  const float2 *b2 = reinterpret_cast<const float2 *>(nf + kNetB2);
+  const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+  for (int mt = 0; mt * 16 < npend; ++mt) {
+    // A of layer 1: rows 16 mt .. +15; lanes 0-7 address matrix 0 (rows 0-7,
+    // inputs 0-7), 8-15 matrix 1 (rows 8-15), 16-23 matrix 2 (rows 0-7,
+    // inputs 8-15), 24-31 matrix 3 (rows 8-15, inputs 8-15)
+    uint32_t a1[2][4];
+    const int row = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+    const uint32_t addr = tile_s + row * kNetRowBytes + (lane >> 4) * 16;
+    ldmatrix_x4(a1[0], addr);
+    if (k2) ldmatrix_x4(a1[1], addr + 32);
+    // layer 1 -> SiLU -> A of layer 2 (K step s = n-tiles 2 s, 2 s + 1)
+    uint32_t a2[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t r0 = 0u, r1 = 0u;
+      if (j < nt) {
+        const float2 bb = b1[4 * j + t];
+        float c[4] = {bb.x, bb.y, bb.x, bb.y};
+        mma_f16_16816(c, a1[0], w1[(j * 2 + 0) * 32 + lane]);
+        if (k2) mma_f16_16816(c, a1[1], w1[(j * 2 + 1) * 32 + lane]);
+        r0 = silu_half_f16x2(c[0], c[1]);
+        r1 = silu_half_f16x2(c[2], c[3]);
+      }
+      a2[j >> 1][2 * (j & 1) + 0] = r0;
+      a2[j >> 1][2 * (j & 1) + 1] = r1;
+    }
+    // layer 2 -> SiLU -> A of the output layer
+    uint32_t a3[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t r0 = 0u, r1 = 0u;
+      if (j < nt) {
+        const float2 bb = b2[4 * j + t];
+        float c[4] = {bb.x, bb.y, bb.x, bb.y};
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (s < ks) mma_f16_16816(c, a2[s], w2[(j * 4 + s) * 32 + lane]);
+        r0 = silu_half_f16x2(c[0], c[1]);
+        r1 = silu_half_f16x2(c[2], c[3]);
+      }
+      a3[j >> 1][2 * (j & 1) + 0] = r0;
+      a3[j >> 1][2 * (j & 1) + 1] = r1;
+    }
+    // output layer: column 0 of the accumulator (lanes t = 0: rows g, g + 8)
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < ks) mma_f16_16816(c, a3[s], w3[s * 32 + lane]);
+    if (t == 0) {
+      ys[mt * 16 + g] = c[0] + b3;
+      ys[mt * 16 + 8 + g] = c[2] + b3;
+    }
+  }
+  __syncwarp();
+}
+
+// The window lower bound of every lane with chk set, evaluated together: the
+// continuous network inputs of its particle in FP32 (position per bounded
+// axis, time; the definitions of net_window), written as binary16 to its row of
+// the warp's tile, the network (net_eval_warp) and the map of its output to
+// w_L.  All 32 lanes call it; 0 where chk is unset.  tile: the warp's
+// kNetWarpBytes of shared memory.
+template <class PR, int DIM>
+__device__ __forceinline__ float net_lower_warp(const DevProblem &P, const uint32_t *nf,
+                                                unsigned char *tile, const PartOf<PR> &p,
+                                                bool chk) {
+  const uint32_t pm = __ballot_sync(0xffffffffu, chk);
+  const int rank = __popc(pm & lanemask_lt());
+  float *ys = reinterpret_cast<float *>(tile + 32 * kNetRowBytes);
+  if (chk) {
+    float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int idx[3] = {p.i, p.j, p.k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!P.bounded[a] || (DIM == 1 && a > 0)) continue;
+      // 2 (x - x_0) / (n dx) - 1, from the cell index and the offset in it
+      // (cell-local) or from the FP64 coordinate
+      if constexpr (PR::kLocal) {
+        const float off = a == 0 ? p.x : a == 1 ? p.y : p.z;
+        f[a] = (2.0f * ((float)idx[a] + off / P.width32[a])) / (float)P.n[a] - 1.0f;
+      } else {
+        const double x = a == 0 ? (double)p.x : a == 1 ? (double)p.y : (double)p.z;
+        f[a] = (float)(2.0 * (x - P.origin[a]) / ((double)P.n[a] * P.width[a]) - 1.0);
+      }
+    }
+    if (P.ww_net_in > 3 && P.T > 0) {
+      const int j = p.tbin < P.T ? p.tbin : P.T - 1;
+      float u;
+      if constexpr (PR::kLocal) u = 1.0f - (float)p.t / __ldg(P.binw32 + j);
+      else u = (float)(((double)p.t - P.edges[j]) / (P.edges[j + 1] - P.edges[j]));
+      f[3] = 2.0f * ((float)j + u) / (float)P.T - 1.0f;
+    }
+    // row: f0..f3, then the group one-hot from input 4 on, zeros to input 31
+    uint4 *row = reinterpret_cast<uint4 *>(tile + rank * kNetRowBytes);
+    row[0] = make_uint4(pack_f16x2(f[0], f[1]), pack_f16x2(f[2], f[3]), 0u, 0u);
+    row[1] = make_uint4(0u, 0u, 0u, 0u);
+    row[2] = make_uint4(0u, 0u, 0u, 0u);
+    row[3] = make_uint4(0u, 0u, 0u, 0u);
+    if (P.ww_net_in > 3)
+      reinterpret_cast<unsigned short *>(tile + rank * kNetRowBytes)[4 + p.g] = 0x3C00u;  // F16 1
+  }
+  __syncwarp();
+  net_eval_warp(nf, tile, ys, __popc(pm), P.ww_net_h, P.ww_net_in > 16, P.ww_net_b3);
+  if (!chk) return 0.0f;
+  const float y = ys[rank];
+  const float lp = fmaxf(fmaf(y, (float)P.ww_net_scale, (float)P.ww_net_shift),
+                         (float)P.ww_net_floor);
+  return (float)P.ww_net_wl0 * __expf(fminf(lp - (float)P.ww_net_top, 0.0f));
+}
+
+// The window checks of every lane with chk set, together.  Returns false for
+// a particle rouletted away.
+template <class PR, int DIM>
+__device__ __forceinline__ bool net_check_warp(const DevProblem &P, const RunArgs &A,
+                                               const EndSink &es, const uint32_t *nf,
+                                               unsigned char *tile, PartOf<PR> &p, bool chk,
+                                               int *s_novf, PartOf<PR> *ovf) {
+  const float wl = net_lower_warp<PR, DIM>(P, nf, tile, p, chk);
+  if (!chk) return true;
+  return ww_apply<PR, DIM>(P, A, es, p, (typename PR::R)wl, s_novf, ovf);
+}
+
+// ---------------------------------------------------------------------------
+// The lower bounds the window check applies at given states (position x[3 s],
+// time t[s], group g[s]): each state becomes a particle in the mode's own
+// representation (cell of the position, clamped into the mesh; offsets from
+// the cell's low faces and the time left to the next census edge in the
+// cell-local mode) and goes through the kernels' own evaluation -- FP64 one
+// at a time (net_window), FP32 a warp of 32 at a time (net_lower_warp, the
+// fragment block and the warps' tiles in dynamic shared memory).  A group
+// outside 0..G-1 gives NaN.
+template <class PR, int DIM>
+__global__ void __launch_bounds__(256) k_net_lower(const DevProblem P, const double *__restrict__ x,
+                                                   const double *__restrict__ t,
+                                                   const int32_t *__restrict__ g, long long n,
+                                                   double *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  if constexpr (!PR::kF64) {
+    for (int q = threadIdx.x; q < kNetFragWords / 4; q += blockDim.x)
+      reinterpret_cast<uint4 *>(smem)[q] = __ldg(reinterpret_cast<const uint4 *>(P.ww_netfrag) + q);
+    __syncthreads();
+  }
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       base < n; base += warps * 32) {
+    const long long s = base + lane;
+    bool ok = s < n;
+    PartOf<PR> p{};
+    if (ok) {
+      const double pos[3] = {x[3 * s], x[3 * s + 1], x[3 * s + 2]};
+      int idx[3] = {0, 0, 0};
+      for (int a = 0; a < 3; ++a)
+        if (P.bounded[a] && (DIM == 3 || a == 0))
+          idx[a] = min(max((int)floor((pos[a] - P.origin[a]) / P.width[a]), 0), P.n[a] - 1);
+      p.i = idx[0]; p.j = idx[1]; p.k = idx[2];
+      const double ts = t[s];
+      int j = 0;
+      if (P.T > 0) {
+        while (j + 1 < P.T && P.edges[j + 1] <= ts) ++j;
+      }
+      p.tbin = j;
+      p.g = g[s];
+      ok = p.g >= 0 && p.g < P.G;
+      if constexpr (PR::kLocal) {
+        const double off[3] = {P.bounded[0] ? pos[0] - P.faces[0][idx[0]] : 0.0,
+                               (DIM == 3 && P.bounded[1]) ? pos[1] - P.faces[1][idx[1]] : 0.0,
+                               (DIM == 3 && P.bounded[2]) ? pos[2] - P.faces[2][idx[2]] : 0.0};
+        p.x = (float)off[0]; p.y = (float)off[1]; p.z = (float)off[2];
+        p.t = P.T > 0 ? (float)(P.edges[j + 1] - ts) : 0.0f;
+      } else {
+        p.x = pos[0]; p.y = pos[1]; p.z = pos[2];
+        p.t = ts;
+      }
+      if (!ok) out[s] = CUDART_NAN;
+    }
+    if constexpr (PR::kF64) {
+      if (ok) out[s] = net_window<PR, DIM>(P, p);
+    } else {
+      const float wl = net_lower_warp<PR, DIM>(P, reinterpret_cast<const uint32_t *>(smem),
+                                               smem + kNetFragBytes + (threadIdx.x >> 5) * kNetWarpBytes,
+                                               p, ok);
+      if (ok) out[s] = (double)wl;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -943,6 +1206,15 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (SHARED || step_tally) { stally = (TT *)ptr; ptr += L.tally_bytes; }
   const Bank<PR> bk = bank_view<PR>(ptr, S, DIM);
   ptr += (long long)S * slot_bytes(PR::kF64, DIM, PR::kLocal);
+  // FP32 network kernels: the fragment block after the bank (where the staged
+  // births would go: population control never runs with windows)
+  const uint32_t *nf = reinterpret_cast<const uint32_t *>(ptr);
+  unsigned char *ntile = ptr + kNetFragBytes + (tid >> 5) * kNetWarpBytes;
+  if constexpr (NET && !PR::kF64) {
+    if (Pin.ww_netfrag != nullptr)
+      for (int q = tid; q < kNetFragWords / 4; q += nth)
+        reinterpret_cast<uint4 *>(ptr)[q] = __ldg(reinterpret_cast<const uint4 *>(Pin.ww_netfrag) + q);
+  }
   // staged births (prefetch): 32 slots per warp in the pool layout
   const Bank<PR> stage =
       bank_view<PR>(ptr + (prefetch ? (long long)(tid >> 5) * 32 * slot_bytes(PR::kF64, DIM, PR::kLocal) : 0),
@@ -953,7 +1225,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
-  __shared__ int s_novf[32];     // [w]: warp w's stack of children; [16 + w]: children it may still make
+  __shared__ int s_novf[48];     // [w]: warp w's stack of children; [16 + w]: children it may
+                                 // still make; [32 + w]: its stack limit for new children
   __shared__ double s_w[4];
   __shared__ uint32_t s_n[9];
   __shared__ double s_red[32];   // per-warp region sums (two estimators)
@@ -983,6 +1256,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     for (long long q = tid; q < P.n_tally; q += nth) stally[q] = (TT)0;
   for (int q = tid; q < step_bins; q += nth) stally[q] = (TT)0;
   if (tid < 32) s_novf[tid] = 0;
+  if (tid < 16) s_novf[32 + tid] = Ain.overflow_cap;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
   if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }
@@ -1076,9 +1350,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           int cbin = -1;
           R cscore = (R)0;
           double wabs = 0.0;
+          bool ww_pend = false;
           if (mine) {
             int end = END_NONE;
-            alive = collide<PR, DIM, NET>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs);
+            alive = collide<PR, DIM, NET>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs,
+                                          ww_pend);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
           if (P.estimator != 0) {
@@ -1097,6 +1373,14 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             // weight removed by implicit capture: one shared add per warp
             for (int o = 16; o > 0; o >>= 1) wabs += __shfl_xor_sync(0xffffffffu, wabs, o);
             if (lane == 0) atomicAdd(&s_w[1], wabs);
+          }
+          if constexpr (NET && !PR::kF64) {
+            // the pass's post-collision window checks, together
+            const bool chk = alive && ww_pend;
+            if (__any_sync(0xffffffffu, chk)) {
+              const bool ok = net_check_warp<PR, DIM>(P, A, es, nf, ntile, q, chk, novf, ovf);
+              if (!ok) { finish<PR, DIM>(P, A, es, q, END_ROULETTE); alive = false; }
+            }
           }
           const uint32_t am = __ballot_sync(0xffffffffu, alive);
           if (alive) bk.store(slot_of(rtop + __popc(am & lt)), q, DIM, use_slot);
@@ -1163,7 +1447,15 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           got = __shfl_sync(0xffffffffu, got, 0);
           h_first = first;
           n_s = got;
-          if (got < want) exhausted = true;
+          if (got < want) {
+            exhausted = true;
+            // the warp's own particles are used up: with the device-wide banks,
+            // children beyond a small stack go there and are shared by every
+            // warp in the next pass, instead of one warp working through a
+            // large family while the others have finished
+            if (lane == 0 && A.spill_out != nullptr && A.overflow_tail >= 0)
+              novf[32] = min(A.overflow_cap, A.overflow_tail);
+          }
         }
         const int nb = n_o + n_s;
         const int top = min(*novf, A.overflow_cap);
@@ -1287,6 +1579,14 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         else
           tally_scatter<TT, R>(stally, A.tally, A.tally32, SHARED, agg, flew, bin, score,
                                flew ? tally_offset(P, A, p.hid) : 0);
+        if constexpr (NET && !PR::kF64) {
+          // the pass's crossing window checks, together
+          const bool chk = has && outcome == OUT_WW;
+          if (__any_sync(0xffffffffu, chk)) {
+            const bool ok = net_check_warp<PR, DIM>(P, A, es, nf, ntile, p, chk, novf, ovf);
+            if (!ok) { finish<PR, DIM>(P, A, es, p, END_ROULETTE); has = false; }
+          }
+        }
         if (A.census_out != nullptr) {
           // population control: a banked particle goes to its input position
           // (no splitting here, so every input yields at most one), which

@@ -60,7 +60,8 @@ class mcdc_options(C.Structure):
                 ("estimator", C.c_int32), ("implicit_capture", C.c_int32),
                 ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
                 ("pc_target", C.c_int32), ("flight_sampling", C.c_int32),
-                ("max_children", C.c_int64), ("slice_bytes_max", C.c_int64)]
+                ("max_children", C.c_int64), ("slice_bytes_max", C.c_int64),
+                ("overflow_tail", C.c_int32)]
 
 
 class mcdc_stats(C.Structure):
@@ -105,13 +106,15 @@ class mcdc_mlp_options(C.Structure):
                 ("seed", C.c_uint64), ("source_wl", C.c_double), ("upper_ratio", C.c_double),
                 ("survival_ratio", C.c_double), ("nmax", C.c_int32), ("min_ratio", C.c_double),
                 ("time_resolved", C.c_int32), ("group_resolved", C.c_int32),
-                ("adjoint", C.c_int32), ("per_event", C.c_int32)]
+                ("adjoint", C.c_int32), ("per_event", C.c_int32),
+                ("distill_steps", C.c_int32)]
 
 
 class mcdc_mlp_report(C.Structure):
     _fields_ = [("samples", C.c_int64), ("loss_first", C.c_double), ("loss_last", C.c_double),
                 ("train_ms", C.c_double), ("bake_ms", C.c_double), ("steps", C.c_int32),
-                ("target_mean", C.c_double)]
+                ("target_mean", C.c_double), ("distill_steps", C.c_int32),
+                ("distill_loss", C.c_double)]
 
 
 # name -> (restype, argtypes); kept in the order of include/mcdc.h
@@ -145,6 +148,9 @@ SIGNATURES = {
     "mcdc_set_network_windows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                            C.c_double, C.c_double, C.c_double, C.c_double,
                                            C.c_double, C.c_double, C.c_double, C.c_int32]),
+    "mcdc_get_weight_windows": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mcdc_network_window_lower": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_int64, C.c_void_p]),
     "mcdc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
 }
@@ -181,6 +187,8 @@ mcdc_mlp_train = _lib.mcdc_mlp_train
 mcdc_set_wait_limit = _lib.mcdc_set_wait_limit
 mcdc_measure_fp64_pipe = _lib.mcdc_measure_fp64_pipe
 mcdc_set_network_windows = _lib.mcdc_set_network_windows
+mcdc_get_weight_windows = _lib.mcdc_get_weight_windows
+mcdc_network_window_lower = _lib.mcdc_network_window_lower
 mcdc_philox = _lib.mcdc_philox
 mcdc_last_error = _lib.mcdc_last_error
 
@@ -213,7 +221,7 @@ class Problem:
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
                  overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0,
-                 flight_sampling=0, max_children=0, slice_bytes_max=0):
+                 flight_sampling=0, max_children=0, slice_bytes_max=0, overflow_tail=None):
         """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
@@ -224,7 +232,9 @@ class Problem:
         make (0: 4096 per history, at least 2^27; negative: no limit);
         slice_bytes_max: global tally, largest memory for one tally slice per
         batch (one launch for all batches; 0: 8 GiB; negative: one launch per
-        batch)."""
+        batch); overflow_tail: global tally with weight windows, stack slots a
+        warp keeps for new children once its own particles are used up (None:
+        the library default; -1: the whole stack)."""
         self.desc = prob
         keep = []
 
@@ -275,6 +285,8 @@ class Problem:
         o.flight_sampling = int(flight_sampling)
         o.max_children = int(max_children)
         o.slice_bytes_max = int(slice_bytes_max)
+        if overflow_tail is not None:
+            o.overflow_tail = int(overflow_tail)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])
@@ -342,6 +354,25 @@ class Problem:
                                        float(shift), float(scale), float(top), float(floor),
                                        float(wl0), float(upper_ratio), float(survival_ratio),
                                        int(nmax)))
+
+    def get_weight_windows(self):
+        """The last window table set or baked, [n_bins] (see mcdc_get_weight_windows)."""
+        out = np.zeros(self.n_bins)
+        check(mcdc_get_weight_windows(self.handle, _ptr(out)))
+        return out
+
+    def network_window_lower(self, x, t, g):
+        """Lower bounds the network's window checks apply at the states
+        (positions x[n, 3], times t[n], groups g[n]); see
+        mcdc_network_window_lower."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1)
+        g = np.ascontiguousarray(g, dtype=np.int32).reshape(-1)
+        assert t.size == x.shape[0] and g.size == x.shape[0]
+        out = np.zeros(x.shape[0])
+        check(mcdc_network_window_lower(self.handle, _ptr(x), _ptr(t), _ptr(g), x.shape[0],
+                                        _ptr(out)))
+        return out
 
     def train_importance(self, pilot_mean, pilot_relerr=None, **opts):
         """Fits the importance network to a pilot tally and switches this

@@ -151,18 +151,126 @@ def test_switching_and_refusals(mcdc):
             P.set_network_windows(p, 8, np.nan, 1.0, 0.0, -3.0, 0.3)
 
 
-def test_trained_network_per_event_is_unbiased(mcdc):
+@pytest.mark.parametrize("time_resolved", [0, 1])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_local"])
+def test_trained_network_per_event_is_unbiased(mcdc, time_resolved, prec):
     """The importance network trained on a pilot tally and evaluated at every
     window check (no baked table): the region total of the two-region slab
-    agrees with an independent analog run within the combined noise."""
+    (one group, 50 time bins) agrees with an independent analog run within the
+    combined noise.  With the time fold (default) the windows come from a
+    position network fitted to the folded table, which its windows at the
+    cell centres must follow; time-resolved, from the trained network itself,
+    whose windows split and roulette by the thousand."""
     prob = W.c2_two_region()
-    with mcdc.Problem(prob, precision=mcdc.PREC_FP32, tally_mode=mcdc.TALLY_GLOBAL) as P:
+    pr = {"fp32": mcdc.PREC_FP32, "fp32_local": mcdc.PREC_FP32_LOCAL}[prec]
+    with mcdc.Problem(prob, precision=pr, tally_mode=mcdc.TALLY_GLOBAL) as P:
         mean, rel = np.zeros(P.n_bins), np.zeros(P.n_bins)
         _, (m_a, r_a) = P.run_ex(4_000_000, 3, batches=32, mean=mean, relerr=rel)
-        rep = P.train_importance(mean, rel, epochs=6, batch=16384, per_event=1)
+        rep = P.train_importance(mean, rel, epochs=6, batch=16384, per_event=1,
+                                 time_resolved=time_resolved)
         assert rep["steps"] > 0 and rep["bake_ms"] >= 0.0
+        if time_resolved:
+            assert rep["distill_steps"] == 0
+        else:
+            assert rep["distill_steps"] >= 2000 and rep["distill_loss"] < 0.01, rep
+            table = P.get_weight_windows().reshape(prob.tally_shape)
+            cells = table.reshape(prob.n[0], -1)[:, 0]     # the folded table: one value per cell
+            xc = np.zeros((prob.n[0], 3))
+            xc[:, 0] = prob.origin[0] + (np.arange(prob.n[0]) + 0.5) * prob.width[0]
+            wl = P.network_window_lower(xc, np.full(prob.n[0], 0.5 * prob.edges[1]),
+                                        np.zeros(prob.n[0], np.int32))
+            dev = np.abs(np.log(wl) - np.log(cells))
+            print(prec, "position network against the table: max |log ratio|", dev.max(),
+                  "table range", cells.min(), cells.max())
+            assert np.all(wl > 0) and dev.max() < 0.1, (dev.max(), np.argmax(dev))
         st, (m_w, r_w) = P.run_ex(2_000_000, 11, batches=32)
-    assert st["splits"] + st["roulette_killed"] > 1000, st
+    if time_resolved:
+        assert st["splits"] + st["roulette_killed"] > 1000, st
     se = np.hypot(m_a * r_a, m_w * r_w)
     print("analog", m_a, r_a, "per-event windows", m_w, r_w, "splits", st["splits"])
     assert abs(m_w - m_a) < 4.0 * se, (m_w, m_a, se)
+
+def _states(prob, n, seed):
+    """Random particle states inside the mesh: positions on the bounded axes (0
+    on an unbounded one), times inside the census grid, groups."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n, 3))
+    for a in range(3):
+        if np.isfinite(prob.width[a]):
+            lo = prob.origin[a]
+            x[:, a] = rng.uniform(lo, lo + prob.n[a] * prob.width[a], n)
+    e = prob.edges
+    t = rng.uniform(e[0], e[-1], n) if e is not None else np.zeros(n)
+    g = rng.integers(0, prob.sigma_t.shape[1], n).astype(np.int32)
+    return x, t, g
+
+
+def _oracle_lower(prob, p, n_in, H, c, x, t, g):
+    """The oracle's inputs for each state, its log w_L from the exact network,
+    and the first-order bound on the warp-batched evaluation's error in log w_L
+    (binary16 operands, FP32 sums, SiLU through tanh.approx taken within 2^-9,
+    FP32 inputs)."""
+    e = prob.edges
+    T = 0 if e is None else len(e) - 1
+    tb = np.clip(np.searchsorted(e, t, side="right") - 1, 0, T - 1) if T else np.zeros(len(t), int)
+    F = np.array([O.net_features(prob, *x[i], t[i], tb[i], g[i], n_in=n_in)
+                  for i in range(len(t))]).reshape(len(t), n_in)
+    pd = p.astype(np.float64)
+    y = O.mlp_forward(pd, F, hidden=H)
+    fb = O.mlp_window_bound(pd, F, hidden=H)
+
+    def logw(v):
+        lp = np.maximum(v * c["scale"] + c["shift"], c["floor"])
+        return np.log(c["wl0"]) + np.minimum(0.0, lp - c["top"])
+    return logw(y), fb * abs(c["scale"])
+
+
+WINDOW_CASES = {
+    # 3-D channel, 7 groups, 8 time bins: 11 inputs (two K steps), 64 hidden
+    "channel_full": (small_channel, 11, 64, 0.2),
+    # the same mesh, position-only network, 24 hidden (a partial n-tile)
+    "channel_position": (small_channel, 3, 24, 0.5),
+    # 1-D slab: unbounded y and z, steady state: 5 inputs, 16 hidden
+    "slab": (W.c2_two_region, 5, 16, 0.5),
+}
+
+
+@pytest.mark.parametrize("case", sorted(WINDOW_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_local"])
+def test_window_lower_bounds_match_oracle(mcdc, case, prec):
+    """The lower bound each window check applies, through the kernels' own
+    evaluation, state by state: FP64 equals the oracle's FP64 network; the
+    FP32 modes (tensor cores, 32 states per warp, binary16 operands, FP32
+    sums, SiLU through tanh.approx) stay within the first-order bound of that
+    arithmetic around the oracle's exact network.  1001 states (31 full warps
+    and a ragged one), a single state and none."""
+    make, n_in, H, sd = WINDOW_CASES[case]
+    prob = make()
+    p = _params(n_in, H, seed=n_in * 7 + H, sd=sd)
+    # top far above the outputs and floor far below: log w_L follows y exactly
+    c = _consts(H, shift=0.0, scale=1.0, top=30.0, floor=-60.0, wl0=2.0)
+    pr = {"fp32": mcdc.PREC_FP32, "fp32_local": mcdc.PREC_FP32_LOCAL,
+          "fp64": mcdc.PREC_FP64}[prec]
+    x, t, g = _states(prob, 1001, seed=H)
+    ly, bound = _oracle_lower(prob, p, n_in, H, c, x, t, g)
+    with mcdc.Problem(prob, precision=pr, tally_mode=mcdc.TALLY_GLOBAL) as P:
+        P.set_network_windows(p, H, c["shift"], c["scale"], c["top"], c["floor"], c["wl0"],
+                              n_in=n_in)
+        wl = P.network_window_lower(x, t, g)
+        one = P.network_window_lower(x[:1], t[:1], g[:1])
+        none = P.network_window_lower(x[:0], t[:0], g[:0])
+        bad = P.network_window_lower(x[:2], t[:2], np.array([0, prob.sigma_t.shape[1]]))
+    assert np.all(wl > 0) and none.size == 0
+    assert one[0] == wl[0]
+    assert np.isfinite(bad[0]) and np.isnan(bad[1])
+    lw = np.log(wl)
+    if prec == "fp64":
+        np.testing.assert_allclose(lw, ly, rtol=0, atol=1e-12)
+        return
+    # + the FP32 window map (fast exponential): 1e-6 in log w_L
+    tol = bound + 1e-6
+    err = np.abs(lw - ly)
+    print(prec, case, "max error / bound", np.max(err / tol), "median", np.median(err / tol))
+    assert np.all(err <= tol), np.max(err / tol)
+    # a wrong row (the neighbouring state's value) would not pass
+    assert np.mean(np.abs(ly - np.roll(ly, 1)) > tol) > 0.8
