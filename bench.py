@@ -181,8 +181,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
-    ap.add_argument("--fom-per-event", action="store_true",
-                    help="also measure the deep box with the network evaluated per event")
+    ap.add_argument("--no-fom-per-event", action="store_true",
+                    help="skip the deep box with the windows evaluated per event (a position "
+                         "network fitted to the folded table, on the tensor cores)")
     ap.add_argument("--no-extra-workloads", action="store_true",
                     help="skip the 60^3 channel (HBM roofline) and the 256 batched problems")
     ap.add_argument("--no-variants", action="store_true",
@@ -329,8 +330,13 @@ def main():
     if rank == 0 and not args.no_fom and world == 1:
         line["fom"] = fom_over_pilots(M, prec, None)
         line["fom_shallow"] = fom_over_pilots(M, prec, W.c4_shallow(), match_relerr=0.04)
-        if args.fom_per_event:
-            line["fom_per_event"] = fom_over_pilots(M, prec, None, per_event=True)
+        if not args.no_fom_per_event:
+            pe = fom_over_pilots(M, prec, None, per_event=True)
+            for f in ("fom", "fom_incl_fit", "fom_incl_pilot"):
+                if line["fom"].get(f"learned_{f}_median"):
+                    pe[f"{f}_median_table_over_per_event"] = (
+                        line["fom"][f"learned_{f}_median"] / max(pe[f"learned_{f}_median"], 1e-300))
+            line["fom_per_event"] = pe
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         h, sg, dt = oracle_sample(prob, args.cpu_seconds, os.cpu_count() or 1, offset=10**12)
         line["cpu_baseline"] = {"value": h / dt, "unit": "histories/s", "cores": os.cpu_count(),

@@ -369,7 +369,10 @@ typedef struct mcdc_mlp_options {
                                    trained network itself with the bake's
                                    constants (resolved in time and group).  Needs a
                                    forward pilot (adjoint 0) and the global tally   */
-    int32_t distill_steps;      /* Adam steps of that position network (0: 2000)   */
+    int32_t distill_steps;      /* Adam steps of that position network, the step
+                                   size falling from lr to lr / 20 (0: 8000)     */
+    int32_t distill_hidden;     /* its hidden width, 1..64 (0: 16; the FP32 modes
+                                   evaluate 16, 32 or 64 units, zero-padded)     */
 } mcdc_mlp_options;
 
 typedef struct mcdc_mlp_report {

@@ -1112,6 +1112,11 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   P.ww_net32 = pr->net32;
   P.ww_netfrag = pr->netfrag;
   P.ww_net_b3 = h32[n - 1];
+  for (int a = 0; a < 3; ++a) {
+    const bool b = P.bounded[a] != 0;
+    P.net_cell[a] = b ? (float)(2.0 / P.n[a]) : 0.0f;
+    P.net_off[a] = b ? (float)(2.0 / (P.n[a] * P.width[a])) : 0.0f;
+  }
   P.ww_net_in = in;
   P.ww_net_h = hidden;
   P.ww_net_shift = shift;

@@ -56,6 +56,8 @@ struct DevProblem {
   const float *ww_net32;
   const uint32_t *ww_netfrag; // the same network as BF16 mma.sync fragments (FP32 modes)
   float ww_net_b3;            // its output bias
+  float net_cell[3], net_off[3];   // input of axis a: cell i, offset o in it -> i net_cell[a]
+                                   // + o net_off[a] - 1 (2 / n, 2 / (n width); 0 unbounded)
   int32_t ww_net_in, ww_net_h;
   double ww_net_shift, ww_net_scale, ww_net_top, ww_net_floor, ww_net_wl0;
   double ww_upper, ww_survival;

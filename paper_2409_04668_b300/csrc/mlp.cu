@@ -1367,8 +1367,11 @@ extern "C" void mcdc_default_mlp_options(mcdc_mlp_options *o) {
 }
 
 // Initial parameters for n_in inputs: U(-1/sqrt(fan_in), 1/sqrt(fan_in))
-// weights (splitmix64 uniforms from the seed), zero biases
-std::vector<float> init_params(int n_in, uint64_t seed) {
+// weights (splitmix64 uniforms from the seed), zero biases.  active < kH:
+// hidden units active.. of both layers start at zero in every weight and
+// bias, and stay zero under training (their activations are SiLU(0) = 0 and
+// every gradient through them vanishes), so the network has `active` units.
+std::vector<float> init_params(int n_in, uint64_t seed, int active = kH) {
   std::vector<float> h((size_t)mlp_param_count(n_in), 0.0f);
   uint64_t sd = seed * 0x9E3779B97F4A7C15ull + 12345;
   auto unif = [&]() {   // splitmix64 -> (0, 1)
@@ -1386,7 +1389,32 @@ std::vector<float> init_params(int n_in, uint64_t seed) {
   for (int64_t i = 0; i < (int64_t)kH * kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
   off += (int64_t)kH * kH + kH;
   for (int64_t i = 0; i < kH; ++i) h[off + i] = (float)((2 * unif() - 1) * a2);
+  if (active < kH) {
+    float *W1 = h.data(), *W2 = W1 + (size_t)kH * n_in + kH, *W3 = W2 + (size_t)kH * kH + kH;
+    for (int j = active; j < kH; ++j) {
+      for (int k = 0; k < n_in; ++k) W1[j * n_in + k] = 0.0f;
+      for (int k = 0; k < kH; ++k) W2[j * kH + k] = W2[k * kH + j] = 0.0f;
+      W3[j] = 0.0f;
+    }
+  }
   return h;
+}
+
+// The first `active` hidden units of a kH-wide parameter vector as a network
+// of that width (layout of mcdc_mlp_forward)
+std::vector<float> narrow_params(const std::vector<float> &p, int n_in, int active) {
+  std::vector<float> q;
+  const float *W1 = p.data(), *b1 = W1 + (size_t)kH * n_in, *W2 = b1 + kH, *b2 = W2 + (size_t)kH * kH;
+  const float *W3 = b2 + kH, *b3 = W3 + kH;
+  for (int j = 0; j < active; ++j)
+    for (int k = 0; k < n_in; ++k) q.push_back(W1[j * n_in + k]);
+  for (int j = 0; j < active; ++j) q.push_back(b1[j]);
+  for (int j = 0; j < active; ++j)
+    for (int k = 0; k < active; ++k) q.push_back(W2[j * kH + k]);
+  for (int j = 0; j < active; ++j) q.push_back(b2[j]);
+  for (int j = 0; j < active; ++j) q.push_back(W3[j]);
+  q.push_back(b3[0]);
+  return q;
 }
 
 extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilot_mean,
@@ -1399,9 +1427,9 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
   mcdc_mlp_options o;
   if (opt) o = *opt; else mcdc_default_mlp_options(&o);
   if (o.epochs < 1 || o.batch < kS || !(o.lr > 0.0) || !(o.source_wl > 0.0) ||
-      o.distill_steps < 0)
-    return fail(MCDC_ERR_INVALID,
-                "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0, distill_steps >= 0");
+      o.distill_steps < 0 || o.distill_hidden < 0 || o.distill_hidden > kH)
+    return fail(MCDC_ERR_INVALID, "need epochs >= 1, batch >= 64, lr > 0, source_wl > 0, "
+                                  "distill_steps >= 0, 0 <= distill_hidden <= 64");
   if (o.per_event && (o.adjoint || pr->tally_mode != MCDC_TALLY_GLOBAL))
     return fail(MCDC_ERR_INVALID, "per-event windows need a forward pilot and the global tally");
   const DevProblem &P = pr->P;
@@ -1573,7 +1601,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       double *mom3, *loss3;
       const int batch3 = (int)std::max<int64_t>(kS, std::min<int64_t>(o.batch, (nc + 7) / 8));
       const int steps3 = (int)((nc + batch3 - 1) / batch3);
-      const int want3 = o.distill_steps > 0 ? o.distill_steps : 2000;
+      const int want3 = o.distill_steps > 0 ? o.distill_steps : 8000;
     const int epochs3 = std::max(1, (want3 + steps3 - 1) / steps3);
       CKM(tmp.get(&X3, (size_t)nc * 3));
       CKM(tmp.get(&Y3, (size_t)nc));
@@ -1584,7 +1612,8 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       CKM(tmp.get(&inv3, (size_t)steps3));
       CKM(tmp.get(&mom3, 8));
       CKM(tmp.get(&loss3, (size_t)steps3 * 2));
-      const std::vector<float> h3 = init_params(3, o.seed + 1);
+      const int h_d = o.distill_hidden > 0 ? o.distill_hidden : 16;
+      const std::vector<float> h3 = init_params(3, o.seed + 1, h_d);
       CKM(cudaMemcpyAsync(prm3, h3.data(), sizeof(float) * np3, cudaMemcpyHostToDevice, st));
       CKM(cudaMemsetAsync(m3, 0, sizeof(float) * np3, st));
       CKM(cudaMemsetAsync(v3, 0, sizeof(float) * np3, st));
@@ -1621,7 +1650,10 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       const double floor_lp = std::fmax(low - 2.302585092994046,
                                         top + std::log(o.min_ratio > 0.0 ? o.min_ratio : 1e-8));
       const double lw0 = std::log(o.source_wl);
-      if (int rc = mcdc_set_network_windows(pr, prm3, 3, kH, hm3[3], hm3[4], lw0,
+      std::vector<float> fit3(np3);
+      CKM(cudaMemcpy(fit3.data(), prm3, sizeof(float) * np3, cudaMemcpyDeviceToHost));
+      const std::vector<float> net3 = narrow_params(fit3, 3, h_d);
+      if (int rc = mcdc_set_network_windows(pr, net3.data(), 3, h_d, hm3[3], hm3[4], lw0,
                                             lw0 + floor_lp - top, o.source_wl, o.upper_ratio,
                                             o.survival_ratio, o.nmax))
         return rc;

@@ -933,125 +933,173 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t addr) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
 }
 
-// The network outputs y (before the window mapping) of rows 0..npend-1 of the
-// warp's tile, into ys[row]; all 32 lanes call it together.  nf: the fragment
-// block, tile/ys: the warp's tile and outputs (shared memory).
-static __device__ __noinline__ void net_eval_warp(const uint32_t *nf, const unsigned char *tile,
-                                                  float *ys, int npend, int H, bool k2,
-                                                  float b3) {
+// The network outputs y (before the window mapping) of rows 0..16 MT - 1 of
+// the warp's tile, into ys[row]; all 32 lanes call it together.  NT n-tiles
+// (8 hidden units each; even) hold the network's units, K2: a second K step
+// of inputs (more than 16), MT M-tiles of 16 rows, run side by side (each B
+// fragment is loaded once for both).  nf: the fragment block, tile_s: the
+// warp's tile (shared-window address), ys: its outputs.
+template <int NT, bool K2, int MT>
+__device__ __forceinline__ void net_eval_t(const uint32_t *nf, uint32_t tile_s, float *ys,
+                                           float b3) {
+  constexpr int KS = NT / 2;            // K steps over the hidden units
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int nt = (H + 7) >> 3;          // n-tiles that hold hidden units
-  const int ks = (H + 15) >> 4;         // K steps over the hidden units
   const uint2 *w1 = reinterpret_cast<const uint2 *>(nf + kNetW1Frag);
   const uint2 *w2 = reinterpret_cast<const uint2 *>(nf + kNetW2Frag);
   const uint2 *w3 = reinterpret_cast<const uint2 *>(nf + kNetW3Frag);
   const float2 *b1 = reinterpret_cast<const float2 *>(nf + kNetB1);
   const float2 *b2 = reinterpret_cast<const float2 *>(nf + kNetB2);
-  const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
-  for (int mt = 0; mt * 16 < npend; ++mt) {
-    // A of layer 1: rows 16 mt .. +15; lanes 0-7 address matrix 0 (rows 0-7,
-    // inputs 0-7), 8-15 matrix 1 (rows 8-15), 16-23 matrix 2 (rows 0-7,
-    // inputs 8-15), 24-31 matrix 3 (rows 8-15, inputs 8-15)
-    uint32_t a1[2][4];
+  // A of layer 1: lanes 0-7 address matrix 0 (rows 0-7, inputs 0-7), 8-15
+  // matrix 1 (rows 8-15), 16-23 matrix 2 (rows 0-7, inputs 8-15), 24-31
+  // matrix 3 (rows 8-15, inputs 8-15)
+  uint32_t a1[MT][K2 ? 2 : 1][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
     const int row = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
     const uint32_t addr = tile_s + row * kNetRowBytes + (lane >> 4) * 16;
-    ldmatrix_x4(a1[0], addr);
-    if (k2) ldmatrix_x4(a1[1], addr + 32);
-    // layer 1 -> SiLU -> A of layer 2 (K step s = n-tiles 2 s, 2 s + 1)
-    uint32_t a2[4][4];
+    ldmatrix_x4(a1[mt][0], addr);
+    if constexpr (K2) ldmatrix_x4(a1[mt][1], addr + 32);
+  }
+  // layer 1 -> SiLU -> A of layer 2 (K step s = n-tiles 2 s, 2 s + 1)
+  uint32_t a2[MT][KS][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t r0 = 0u, r1 = 0u;
-      if (j < nt) {
-        const float2 bb = b1[4 * j + t];
-        float c[4] = {bb.x, bb.y, bb.x, bb.y};
-        mma_f16_16816(c, a1[0], w1[(j * 2 + 0) * 32 + lane]);
-        if (k2) mma_f16_16816(c, a1[1], w1[(j * 2 + 1) * 32 + lane]);
-        r0 = silu_half_f16x2(c[0], c[1]);
-        r1 = silu_half_f16x2(c[2], c[3]);
-      }
-      a2[j >> 1][2 * (j & 1) + 0] = r0;
-      a2[j >> 1][2 * (j & 1) + 1] = r1;
+  for (int j = 0; j < NT; ++j) {
+    const float2 bb = b1[4 * j + t];
+    const uint2 f0 = w1[(j * 2 + 0) * 32 + lane];
+    uint2 f1 = make_uint2(0u, 0u);
+    if constexpr (K2) f1 = w1[(j * 2 + 1) * 32 + lane];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      float c[4] = {bb.x, bb.y, bb.x, bb.y};
+      mma_f16_16816(c, a1[mt][0], f0);
+      if constexpr (K2) mma_f16_16816(c, a1[mt][1], f1);
+      a2[mt][j >> 1][2 * (j & 1) + 0] = silu_half_f16x2(c[0], c[1]);
+      a2[mt][j >> 1][2 * (j & 1) + 1] = silu_half_f16x2(c[2], c[3]);
     }
-    // layer 2 -> SiLU -> A of the output layer
-    uint32_t a3[4][4];
+  }
+  // layer 2 -> SiLU -> A of the output layer
+  uint32_t a3[MT][KS][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t r0 = 0u, r1 = 0u;
-      if (j < nt) {
-        const float2 bb = b2[4 * j + t];
-        float c[4] = {bb.x, bb.y, bb.x, bb.y};
+  for (int j = 0; j < NT; ++j) {
+    const float2 bb = b2[4 * j + t];
+    float c[MT][4];
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
-          if (s < ks) mma_f16_16816(c, a2[s], w2[(j * 4 + s) * 32 + lane]);
-        r0 = silu_half_f16x2(c[0], c[1]);
-        r1 = silu_half_f16x2(c[2], c[3]);
-      }
-      a3[j >> 1][2 * (j & 1) + 0] = r0;
-      a3[j >> 1][2 * (j & 1) + 1] = r1;
+    for (int mt = 0; mt < MT; ++mt) {
+      c[mt][0] = bb.x; c[mt][1] = bb.y; c[mt][2] = bb.x; c[mt][3] = bb.y;
     }
-    // output layer: column 0 of the accumulator (lanes t = 0: rows g, g + 8)
-    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (s < ks) mma_f16_16816(c, a3[s], w3[s * 32 + lane]);
-    if (t == 0) {
-      ys[mt * 16 + g] = c[0] + b3;
-      ys[mt * 16 + 8 + g] = c[2] + b3;
+    for (int s = 0; s < KS; ++s) {
+      const uint2 f = w2[(j * 4 + s) * 32 + lane];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) mma_f16_16816(c[mt], a2[mt][s], f);
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      a3[mt][j >> 1][2 * (j & 1) + 0] = silu_half_f16x2(c[mt][0], c[mt][1]);
+      a3[mt][j >> 1][2 * (j & 1) + 1] = silu_half_f16x2(c[mt][2], c[mt][3]);
+    }
+  }
+  // output layer: column 0 of the accumulator (lanes t = 0: rows g, g + 8)
+  float c[MT][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.0f;
+#pragma unroll
+  for (int s = 0; s < KS; ++s) {
+    const uint2 f = w3[s * 32 + lane];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) mma_f16_16816(c[mt], a3[mt][s], f);
+  }
+  if (t == 0) {
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      ys[mt * 16 + g] = c[mt][0] + b3;
+      ys[mt * 16 + 8 + g] = c[mt][2] + b3;
     }
   }
   __syncwarp();
 }
 
+// The network output y for every lane with chk set (0 elsewhere); all 32
+// lanes call it together.  Each such lane writes its inputs (f0..f3 and the
+// group one-hot from input 4 on, as binary16, zeros to input 31) into row
+// `rank` of the warp's tile; the tile then runs through the instantiation for
+// the network's width (16, 32 or 64 units, zero-padded), its inputs (K = 16
+// or 32) and its rows (one or two M tiles) -- the same choice in every lane.
+// One copy, called from both check sites, so the tracker's instruction
+// working set stays small.
+static __device__ __noinline__ float net_y_warp(const uint32_t *nf, unsigned char *tile,
+                                                float f0, float f1, float f2, float f3, int grp,
+                                                bool chk, int n_in, int H, float b3) {
+  const uint32_t pm = __ballot_sync(0xffffffffu, chk);
+  const int rank = __popc(pm & lanemask_lt());
+  const int npend = __popc(pm);
+  float *ys = reinterpret_cast<float *>(tile + 32 * kNetRowBytes);
+  if (chk) {
+    uint4 *row = reinterpret_cast<uint4 *>(tile + rank * kNetRowBytes);
+    row[0] = make_uint4(pack_f16x2(f0, f1), pack_f16x2(f2, f3), 0u, 0u);
+    row[1] = make_uint4(0u, 0u, 0u, 0u);
+    row[2] = make_uint4(0u, 0u, 0u, 0u);
+    row[3] = make_uint4(0u, 0u, 0u, 0u);
+    if (n_in > 3)
+      reinterpret_cast<unsigned short *>(tile + rank * kNetRowBytes)[4 + grp] = 0x3C00u;  // 1
+  }
+  __syncwarp();
+  const uint32_t ts = (uint32_t)__cvta_generic_to_shared(tile);
+  const int v = (H <= 16 ? 0 : H <= 32 ? 1 : 2) * 4 + (n_in > 16 ? 2 : 0) + (npend > 16 ? 1 : 0);
+  switch (v) {
+    case 0: net_eval_t<2, false, 1>(nf, ts, ys, b3); break;
+    case 1: net_eval_t<2, false, 2>(nf, ts, ys, b3); break;
+    case 2: net_eval_t<2, true, 1>(nf, ts, ys, b3); break;
+    case 3: net_eval_t<2, true, 2>(nf, ts, ys, b3); break;
+    case 4: net_eval_t<4, false, 1>(nf, ts, ys, b3); break;
+    case 5: net_eval_t<4, false, 2>(nf, ts, ys, b3); break;
+    case 6: net_eval_t<4, true, 1>(nf, ts, ys, b3); break;
+    case 7: net_eval_t<4, true, 2>(nf, ts, ys, b3); break;
+    case 8: net_eval_t<8, false, 1>(nf, ts, ys, b3); break;
+    case 9: net_eval_t<8, false, 2>(nf, ts, ys, b3); break;
+    case 10: net_eval_t<8, true, 1>(nf, ts, ys, b3); break;
+    default: net_eval_t<8, true, 2>(nf, ts, ys, b3); break;
+  }
+  return chk ? ys[rank] : 0.0f;
+}
+
 // The window lower bound of every lane with chk set, evaluated together: the
 // continuous network inputs of its particle in FP32 (position per bounded
-// axis, time; the definitions of net_window), written as binary16 to its row of
-// the warp's tile, the network (net_eval_warp) and the map of its output to
-// w_L.  All 32 lanes call it; 0 where chk is unset.  tile: the warp's
-// kNetWarpBytes of shared memory.
+// axis, time; the definitions of net_window), the network (net_y_warp) and
+// the map of its output to w_L.  All 32 lanes call it; 0 where chk is unset.
+// tile: the warp's kNetWarpBytes of shared memory.
 template <class PR, int DIM>
 __device__ __forceinline__ float net_lower_warp(const DevProblem &P, const uint32_t *nf,
                                                 unsigned char *tile, const PartOf<PR> &p,
                                                 bool chk) {
-  const uint32_t pm = __ballot_sync(0xffffffffu, chk);
-  const int rank = __popc(pm & lanemask_lt());
-  float *ys = reinterpret_cast<float *>(tile + 32 * kNetRowBytes);
+  float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   if (chk) {
-    float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     const int idx[3] = {p.i, p.j, p.k};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (!P.bounded[a] || (DIM == 1 && a > 0)) continue;
-      // 2 (x - x_0) / (n dx) - 1, from the cell index and the offset in it
-      // (cell-local) or from the FP64 coordinate
+      // 2 (x - x_0) / (n dx) - 1 = i (2 / n) + o (2 / (n dx)) - 1 with the
+      // offset o in cell i (cell-local), or from the FP64 coordinate
       if constexpr (PR::kLocal) {
         const float off = a == 0 ? p.x : a == 1 ? p.y : p.z;
-        f[a] = (2.0f * ((float)idx[a] + off / P.width32[a])) / (float)P.n[a] - 1.0f;
+        f[a] = fmaf((float)idx[a], P.net_cell[a], fmaf(off, P.net_off[a], -1.0f));
       } else {
         const double x = a == 0 ? (double)p.x : a == 1 ? (double)p.y : (double)p.z;
-        f[a] = (float)(2.0 * (x - P.origin[a]) / ((double)P.n[a] * P.width[a]) - 1.0);
+        f[a] = fmaf((float)(x - P.origin[a]), P.net_off[a], -1.0f);
       }
     }
     if (P.ww_net_in > 3 && P.T > 0) {
+      // 2 (j + u) / T - 1, u the fraction of bin j passed
       const int j = p.tbin < P.T ? p.tbin : P.T - 1;
       float u;
-      if constexpr (PR::kLocal) u = 1.0f - (float)p.t / __ldg(P.binw32 + j);
+      if constexpr (PR::kLocal) u = 1.0f - __fdividef((float)p.t, __ldg(P.binw32 + j));
       else u = (float)(((double)p.t - P.edges[j]) / (P.edges[j + 1] - P.edges[j]));
-      f[3] = 2.0f * ((float)j + u) / (float)P.T - 1.0f;
+      f[3] = fmaf((float)j + u, 2.0f / (float)P.T, -1.0f);
     }
-    // row: f0..f3, then the group one-hot from input 4 on, zeros to input 31
-    uint4 *row = reinterpret_cast<uint4 *>(tile + rank * kNetRowBytes);
-    row[0] = make_uint4(pack_f16x2(f[0], f[1]), pack_f16x2(f[2], f[3]), 0u, 0u);
-    row[1] = make_uint4(0u, 0u, 0u, 0u);
-    row[2] = make_uint4(0u, 0u, 0u, 0u);
-    row[3] = make_uint4(0u, 0u, 0u, 0u);
-    if (P.ww_net_in > 3)
-      reinterpret_cast<unsigned short *>(tile + rank * kNetRowBytes)[4 + p.g] = 0x3C00u;  // F16 1
   }
-  __syncwarp();
-  net_eval_warp(nf, tile, ys, __popc(pm), P.ww_net_h, P.ww_net_in > 16, P.ww_net_b3);
+  const float y = net_y_warp(nf, tile, f[0], f[1], f[2], f[3], chk ? p.g : 0, chk,
+                             P.ww_net_in, P.ww_net_h, P.ww_net_b3);
   if (!chk) return 0.0f;
-  const float y = ys[rank];
   const float lp = fmaxf(fmaf(y, (float)P.ww_net_scale, (float)P.ww_net_shift),
                          (float)P.ww_net_floor);
   return (float)P.ww_net_wl0 * __expf(fminf(lp - (float)P.ww_net_top, 0.0f));

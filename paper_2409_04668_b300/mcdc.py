@@ -107,7 +107,7 @@ class mcdc_mlp_options(C.Structure):
                 ("survival_ratio", C.c_double), ("nmax", C.c_int32), ("min_ratio", C.c_double),
                 ("time_resolved", C.c_int32), ("group_resolved", C.c_int32),
                 ("adjoint", C.c_int32), ("per_event", C.c_int32),
-                ("distill_steps", C.c_int32)]
+                ("distill_steps", C.c_int32), ("distill_hidden", C.c_int32)]
 
 
 class mcdc_mlp_report(C.Structure):

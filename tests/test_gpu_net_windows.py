@@ -172,7 +172,7 @@ def test_trained_network_per_event_is_unbiased(mcdc, time_resolved, prec):
         if time_resolved:
             assert rep["distill_steps"] == 0
         else:
-            assert rep["distill_steps"] >= 2000 and rep["distill_loss"] < 0.01, rep
+            assert rep["distill_steps"] >= 8000 and rep["distill_loss"] < 0.01, rep
             table = P.get_weight_windows().reshape(prob.tally_shape)
             cells = table.reshape(prob.n[0], -1)[:, 0]     # the folded table: one value per cell
             xc = np.zeros((prob.n[0], 3))
