@@ -181,6 +181,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-fom", action="store_true", help="skip the learned-vs-analog FOM leg")
+    ap.add_argument("--profile-deep", choices=["table", "per_event"], default=None,
+                    help="only a compact deep-box run for an ncu capture: FP64 pilot, then "
+                         "one FP32 cell-local run of 1e5 histories with learned windows "
+                         "(baked table or per event); its first tracker launch is the only "
+                         "cell-local one")
     ap.add_argument("--no-fom-per-event", action="store_true",
                     help="skip the deep box with the windows evaluated per event (a position "
                          "network fitted to the folded table, on the tensor cores)")
@@ -193,6 +198,9 @@ def main():
 
     if args.workload == "c5":
         run_batched_bench(args)
+        return
+    if args.profile_deep:
+        profile_deep(args.profile_deep)
         return
     make, n_default = WORKLOADS[args.workload]
     prob = make()
@@ -698,6 +706,33 @@ def equal_variance(M, P, prob, prec, seed0, target, r_w1, n_w1, seed_w, ww_batch
             "agreement_z": z,
             "ratio_incl_pilot": fw / fa, "ratio_rel_uncertainty": math.hypot(ua, uw),
             "time_ratio": secs / t_tot}
+
+
+def profile_deep(mode):
+    """The deep box's learned-window transport in a form small enough to
+    capture: the pilot in FP64 (another kernel instantiation), windows trained
+    from it on an FP32 cell-local problem (a baked table, or per event), then
+    one run of 1e5 histories whose first tracker launch is the first FP32
+    cell-local one; spill banks of 2^22 particles keep the device memory to a
+    few GB.  Prints the run's counts and device time."""
+    import torch
+    from paper_2409_04668_b300 import mcdc as M
+    prob = W.c4_deep()
+    dev = torch.device("cuda")
+    with M.Problem(prob, precision=M.PREC_FP64, tally_mode=M.TALLY_GLOBAL, block_size=512) as P0:
+        mean = torch.zeros(P0.n_bins, dtype=torch.float64, device=dev)
+        rel = torch.zeros_like(mean)
+        P0.run_ex(10_000_000, 7, mean=mean, relerr=rel)
+    with M.Problem(prob, precision=M.PREC_FP32_LOCAL, tally_mode=M.TALLY_GLOBAL, block_size=512,
+                   spill_particles=1 << 22) as P:
+        P.train_importance(mean, rel, epochs=10, batch=32768, min_ratio=1e-20,
+                           per_event=int(mode == "per_event"), **WW_SETTINGS)
+        st, (m, r) = P.run_ex(100_000, 20, batches=16)
+    print(json.dumps({"profile": f"deep_box_{mode}", "workload": prob.name, "histories": 100_000,
+                      "kernel_ms": st["kernel_ms"], "segments": st["segments"],
+                      "collisions": st["collisions"], "crossings": st["crossings"],
+                      "splits": st["splits"], "splits_dropped": st["splits_dropped"]}),
+          flush=True)
 
 
 def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False, match_relerr=None):

@@ -200,6 +200,10 @@ typedef struct mcdc_options {
                                    warp working through a large family while the
                                    others have finished (-1: the whole stack;
                                    default 8)                                   */
+    int64_t spill_particles;    /* global tally with weight windows: particles each
+                                   of the two device-wide spill banks holds; a
+                                   child that finds them full is not made (counted
+                                   in splits_dropped; 0: 2^26)                   */
 } mcdc_options;
 
 /* Event and weight counts of one run (summed over all particles). */

@@ -472,7 +472,9 @@ int ensure_overflow(mcdc_problem *pr) {
     // deep-penetration box 64 per warp ran 3-5x faster than 256)
     cap = pr->opt.overflow_per_cta > 0 ? std::min(cap, 256) : 64;
     if (!pr->spill[0]) {
-      const unsigned long long scap = 1ull << 26;   // particles per bank (4.3 GB in FP32)
+      // particles per bank (2^26 by default: 4.3 GB in FP32)
+      const unsigned long long scap =
+          pr->opt.spill_particles > 0 ? (unsigned long long)pr->opt.spill_particles : 1ull << 26;
       const size_t pb = pr->key.f64 ? sizeof(Part<double>)
                         : (pr->key.local ? sizeof(Part<float, float>) : sizeof(Part<float>));
       unsigned char *a = nullptr, *b = nullptr;
@@ -725,6 +727,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   if (o.flight_sampling != 0 && o.flight_sampling != 1)
     return fail(MCDC_ERR_INVALID, "flight_sampling must be 0 or 1");
   if (o.overflow_tail < -1) return fail(MCDC_ERR_INVALID, "overflow_tail must be >= -1");
+  if (o.spill_particles < 0 || o.spill_particles > (1ll << 31))
+    return fail(MCDC_ERR_INVALID, "spill_particles must be in 0..2^31");
   if (o.pc_target > 0 && o.tally_mode == MCDC_TALLY_SHARED)
     return fail(MCDC_ERR_INVALID, "population control runs on the global tally");
 

@@ -61,7 +61,7 @@ class mcdc_options(C.Structure):
                 ("weight_cutoff", C.c_double), ("cutoff_survival", C.c_double),
                 ("pc_target", C.c_int32), ("flight_sampling", C.c_int32),
                 ("max_children", C.c_int64), ("slice_bytes_max", C.c_int64),
-                ("overflow_tail", C.c_int32)]
+                ("overflow_tail", C.c_int32), ("spill_particles", C.c_int64)]
 
 
 class mcdc_stats(C.Structure):
@@ -221,7 +221,8 @@ class Problem:
     def __init__(self, prob, precision=PREC_FP32, tally_mode=TALLY_AUTO, n_batches=0,
                  block_size=0, bank_per_cta=0, ctas_per_sm=0, warp_aggregate=0,
                  overflow_per_cta=0, region=None, estimator=0, implicit=None, pc_target=0,
-                 flight_sampling=0, max_children=0, slice_bytes_max=0, overflow_tail=None):
+                 flight_sampling=0, max_children=0, slice_bytes_max=0, overflow_tail=None,
+                 spill_particles=0):
         """estimator: EST_TRACK, EST_COLLISION or EST_COMBINED; implicit: None (analog
         collisions) or (weight cutoff, survival weight) for implicit capture;
         pc_target: population control, particles per batch after each comb
@@ -234,7 +235,8 @@ class Problem:
         batch (one launch for all batches; 0: 8 GiB; negative: one launch per
         batch); overflow_tail: global tally with weight windows, stack slots a
         warp keeps for new children once its own particles are used up (None:
-        the library default; -1: the whole stack)."""
+        the library default; -1: the whole stack); spill_particles: global tally
+        with weight windows, capacity of each spill bank (0: 2^26)."""
         self.desc = prob
         keep = []
 
@@ -287,6 +289,7 @@ class Problem:
         o.slice_bytes_max = int(slice_bytes_max)
         if overflow_tail is not None:
             o.overflow_tail = int(overflow_tail)
+        o.spill_particles = int(spill_particles)
         if implicit is not None:
             o.implicit_capture = 1
             o.weight_cutoff, o.cutoff_survival = float(implicit[0]), float(implicit[1])
