@@ -725,10 +725,12 @@ def profile_deep(mode):
         P0.run_ex(10_000_000, 7, mean=mean, relerr=rel)
     with M.Problem(prob, precision=M.PREC_FP32_LOCAL, tally_mode=M.TALLY_GLOBAL, block_size=512,
                    spill_particles=1 << 22) as P:
-        P.train_importance(mean, rel, epochs=10, batch=32768, min_ratio=1e-20,
-                           per_event=int(mode == "per_event"), **WW_SETTINGS)
+        rep = P.train_importance(mean, rel, epochs=10, batch=32768, min_ratio=1e-20,
+                                 per_event=int(mode == "per_event"), **WW_SETTINGS)
         st, (m, r) = P.run_ex(100_000, 20, batches=16)
     print(json.dumps({"profile": f"deep_box_{mode}", "workload": prob.name, "histories": 100_000,
+                      "fit": {k: rep[k] for k in ("samples", "steps", "train_ms", "bake_ms",
+                                                  "distill_steps")},
                       "kernel_ms": st["kernel_ms"], "segments": st["segments"],
                       "collisions": st["collisions"], "crossings": st["crossings"],
                       "splits": st["splits"], "splits_dropped": st["splits_dropped"]}),
