@@ -302,12 +302,18 @@ int64_t mcdc_tally_size(const struct mcdc_problem *prob);
 
 void mcdc_problem_destroy(struct mcdc_problem *prob);
 
-/* Many independent problems in one run (analog): per batch, one persistent
- * launch in which CTAs claim (problem, history range) work items, largest
- * first, and load a problem's tables when they switch to it; then one fused
- * fold of every problem's batch tally; the whole run is one CUDA graph.  All
- * problems must share device, precision and dimension and have no weight
+/* Many independent problems in one run: per batch, one persistent launch in
+ * which CTAs claim (problem, history range) work items, largest first, and
+ * load a problem's tables (its window table included) when they switch to
+ * it; then one fused fold of every problem's batch tally; the whole run is
+ * one CUDA graph, captured once per run shape and replayed.  All problems
+ * must share device, precision and dimension and have no per-event network
  * windows, implicit capture, population control or combined estimator.
+ * Table windows (mcdc_set_weight_windows) are applied per problem; a warp
+ * keeps the split children of the work item it serves in a stack of 1024
+ * (there is no spill bank here: a child that finds the stack full is not
+ * made, counted in splits_dropped -- unbiased), within a children budget of
+ * max(2^27, 4096 x all histories) per call.
  * Problem i uses seed + i * 0x9E3779B97F4A7C15 (mod 2^64) and
  * histories [0, n_histories[i]) in n_batches batches (0: 16).
  * mean_out[i] / relerr_out[i]: [n_bins of problem i], host or device, or

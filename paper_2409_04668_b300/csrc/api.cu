@@ -1005,6 +1005,7 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
                             double survival_ratio, int32_t nmax) {
   g_err.clear();
   if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
+  pr->p_version += 1;
   if (w_lower == nullptr) {
     pr->P.ww_lower = nullptr;
     pr->P.ww_lower32 = nullptr;
@@ -1054,6 +1055,7 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   g_err.clear();
   if (!pr) return fail(MCDC_ERR_INVALID, "problem is NULL");
   if (params == nullptr) return mcdc_set_weight_windows(pr, nullptr, 0.0, 0.0, 0);
+  pr->p_version += 1;
   if (pr->P.pc_target > 0)
     return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
   if (hidden < 1 || hidden > 64) return fail(MCDC_ERR_INVALID, "hidden width must be 1..64");
@@ -1544,7 +1546,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->w_source = h.w_source; stats->w_absorbed = h.w_absorbed;
     stats->w_leaked = h.w_leaked; stats->w_censused = h.w_censused;
-    if (!ww_on(P) && !P.implicit && P.pc_target == 0) {   // analog: every weight is 1
+    if (!weights_summed(P)) {   // analog: every weight is 1
       stats->w_source = (double)h.histories;
       stats->w_absorbed = (double)h.absorbed;
       stats->w_leaked = (double)h.leaked;

@@ -134,6 +134,7 @@ struct BatchedPlan {
   DevFree fr;                           // device buffers of the plan
   Stats *d_stats = nullptr;
   int32_t *d_err = nullptr;
+  unsigned long long *d_children = nullptr;   // children made this call (windows)
   RunArgs *d_args = nullptr;
   double *scratch = nullptr;            // host outputs: [2][largest tally]
   long long max_bins = 0;
@@ -152,6 +153,8 @@ struct BatchedPlan {
     cudaGetLastError();
   }
 };
+
+constexpr int kBatchedStack = 1024;   // split-children slots per warp (weight windows)
 
 std::mutex g_plan_mu;
 std::vector<std::unique_ptr<BatchedPlan>> g_plans;   // most recently used last
@@ -195,6 +198,28 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
 
   CKB(dnew(pl.fr, &pl.d_stats, 1));
   CKB(dnew(pl.fr, &pl.d_err, 4));
+  // weight windows: one stack of split children per warp of the launch
+  // (kBatchedStack slots; there is no spill bank here, so a child that finds
+  // the stack full is not made -- counted, and unbiased), and the run's
+  // children budget as in a single-problem run
+  bool windows = false;
+  uint64_t hist_total = 0;
+  for (int i = 0; i < n; ++i) {
+    windows = windows || ww_on(probs[i]->P);
+    hist_total += n_histories[i];
+  }
+  void *d_ovf = nullptr;
+  unsigned long long *d_children = nullptr;
+  if (windows) {
+    const size_t pb = key.f64 ? sizeof(Part<double>)
+                      : (key.local ? sizeof(Part<float, float>) : sizeof(Part<float>));
+    const size_t warps = (size_t)grid * (block / 32);
+    unsigned char *o = nullptr;
+    CKB(dnew(pl.fr, &o, warps * kBatchedStack * pb));
+    d_ovf = o;
+    CKB(dnew(pl.fr, &d_children, 1));
+  }
+  pl.d_children = d_children;
   std::vector<DevProblem> hp(n);
   std::vector<FoldItem> hf(n);
   std::vector<double *> hreg(n);
@@ -202,6 +227,7 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
     hp[i] = p->P;
+    hp[i].sum_weights = 1;        // one weight sum over problems with and without windows
     RunArgs A{};
     A.n_hist = n_histories[i];
     A.offset = 0;
@@ -210,6 +236,13 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
     A.stats = pl.d_stats;
     A.error = pl.d_err;
     A.warp_aggregate = p->warp_aggregate;
+    if (windows) {
+      A.overflow = d_ovf;
+      A.overflow_cap = kBatchedStack;
+      A.overflow_tail = -1;
+      A.children_made = d_children;
+      A.children_budget = std::max<unsigned long long>(1ull << 27, 4096ull * hist_total);
+    }
     pl.ha[i] = A;
     hf[i] = {p->tally, p->sum1, p->sum2, p->region_batch};
     hreg[i] = p->region;
@@ -258,6 +291,7 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   cudaMemsetAsync(pl.d_stats, 0, sizeof(Stats), st);
   cudaMemsetAsync(pl.d_err, 0, 4 * sizeof(int32_t), st);
   cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * B, st);
+  if (d_children) cudaMemsetAsync(d_children, 0, sizeof(unsigned long long), st);
   k_zero_multi<<<row_grid, 512, 0, st>>>(d_probs, d_fold, d_reg);
   for (int b = 0; b < B; ++b) {
     MultiArgs MA{d_probs, pl.d_args, d_items + item_off[b], item_off[b + 1] - item_off[b], d_ctr + b};
@@ -297,8 +331,10 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     if (p->device != p0->device || p->key.f64 != p0->key.f64 || p->key.local != p0->key.local ||
         p->dim != p0->dim)
       return fail(MCDC_ERR_INVALID, "batched problems need the same device, precision and dimension");
-    if (ww_on(p->P) || p->P.implicit || p->P.pc_target > 0)
-      return fail(MCDC_ERR_INVALID, "batched runs are analog (no weight windows, implicit capture or population control)");
+    if (p->P.ww_net64 != nullptr || p->P.implicit || p->P.pc_target > 0)
+      return fail(MCDC_ERR_INVALID, "batched runs take analog collisions and table windows "
+                                    "(no per-event network windows, implicit capture or "
+                                    "population control)");
     if (p->P.estimator == MCDC_EST_COMBINED)
       return fail(MCDC_ERR_INVALID, "batched runs score one estimator (no combined estimator)");
     if (n_histories[i] < (uint64_t)B) return fail(MCDC_ERR_INVALID, "every problem needs >= n_batches histories");
@@ -331,6 +367,7 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     any_host = any_host || (mean_out && mean_out[i] && !mdev[i]) ||
                (relerr_out && relerr_out[i] && !rdev[i]);
     key.push_back(probs[i]->uid);
+    key.push_back(probs[i]->p_version);
     key.push_back(n_histories[i]);
     key.push_back((uint64_t)(uintptr_t)mdev[i]);
     key.push_back((uint64_t)(uintptr_t)rdev[i]);
@@ -421,8 +458,13 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     stats->histories = h.histories; stats->segments = h.segments;
     stats->collisions = h.collisions; stats->crossings = h.crossings; stats->census = h.census;
     stats->absorbed = h.absorbed; stats->leaked = h.leaked; stats->censused = h.censused;
-    stats->w_source = (double)h.histories; stats->w_absorbed = (double)h.absorbed;   // analog
-    stats->w_leaked = (double)h.leaked; stats->w_censused = (double)h.censused;
+    stats->splits = h.splits; stats->children = h.children;
+    stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
+    stats->splits_dropped = h.splits_dropped;
+    stats->w_source = h.w_source;     // summed on the device for every problem
+    stats->w_absorbed = h.w_absorbed;
+    stats->w_leaked = h.w_leaked;
+    stats->w_censused = h.w_censused;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, pl->e0, pl->e1);
     stats->kernel_ms = ms;

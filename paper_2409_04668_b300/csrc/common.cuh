@@ -70,11 +70,18 @@ struct DevProblem {
   float wcut32, wsurv32;
   int32_t pc_target;          // population control: particles per batch after a comb (0: off)
   int32_t fresh_tau;          // FP32 modes: 1 = sample the distance to collision every flight
+  int32_t sum_weights;        // 1: sum weights even when every particle keeps weight 1
 };
 
 // weight windows are on: a table or the network
 __host__ __device__ inline bool ww_on(const DevProblem &P) {
   return P.ww_lower != nullptr || P.ww_net64 != nullptr;
+}
+
+// particle weights are summed on the device (births and ends): weighted runs,
+// and every problem of a batched run (whose problems share one sum)
+__host__ __device__ inline bool weights_summed(const DevProblem &P) {
+  return P.sum_weights || ww_on(P) || P.implicit || P.pc_target > 0;
 }
 
 // One particle as it moves between the tracker phases (kept in registers).

@@ -1662,6 +1662,7 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       CKM(cudaStreamSynchronize(st));
       if (int rc = tc_status()) return rc;      // the windows are not switched on
       // switch the problem to weight windows (w_U, w_S ratios as given)
+      pr->p_version += 1;
       pr->P.ww_lower = pr->ww64;
       pr->P.ww_lower32 = pr->ww32;
       pr->P.ww_upper = o.upper_ratio;

@@ -8,7 +8,9 @@
 #include "tracker.cuh"
 
 struct mcdc_problem {
-  uint64_t uid = 0;           // unique over the process (batched-run plans key on it)
+  uint64_t uid = 0;             // unique over the process (batched-run plans key on it)
+  uint64_t p_version = 0;       // bumped whenever P changes after create (windows):
+                                // cached batched plans hold a copy of P
   int device = 0;
   int sms = 0;
   mcdc::DevProblem P{};

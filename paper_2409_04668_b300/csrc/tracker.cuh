@@ -261,7 +261,7 @@ __device__ __forceinline__ void finish(const DevProblem &P, const RunArgs &A, co
                                        const PartOf<PR> &p, int end) {
   // analog runs carry weight 1 throughout: their weight sums are the counts
   // (filled in on the host), so only weighted runs add weights here
-  const bool weighted = ww_on(P) || P.implicit || P.pc_target > 0;
+  const bool weighted = weights_summed(P);
   if (end == END_ABSORBED) { atomicAdd(&es.n_end[0], 1u); if (weighted) atomicAdd(&es.w_end[1], (double)p.w); }
   else if (end == END_LEAKED) { atomicAdd(&es.n_end[1], 1u); if (weighted) atomicAdd(&es.w_end[2], (double)p.w); }
   else if (end == END_CENSUSED) { atomicAdd(&es.n_end[2], 1u); if (weighted) atomicAdd(&es.w_end[3], (double)p.w); }
@@ -1320,8 +1320,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   EndSink es{s_w, s_n};
   LocalCount lc{0, 0, 0, 0};
   const int wid = blockIdx.x * nwarps + warp;                 // warp id in the grid
-  PartOf<PR> *ovf = MULTI ? nullptr
-                          : reinterpret_cast<PartOf<PR> *>(A.overflow) + (size_t)wid * A.overflow_cap;
+  // the warp's stack of split children (batched launches: one stack per warp
+  // for every problem it serves; none when no problem has windows)
+  PartOf<PR> *ovf = Ain.overflow == nullptr
+                        ? nullptr
+                        : reinterpret_cast<PartOf<PR> *>(Ain.overflow) + (size_t)wid * Ain.overflow_cap;
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
   bool agg = MULTI ? false : A.warp_aggregate != 0;
@@ -1527,7 +1530,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
             if (use_slot) q.slot = (uint32_t)(h_first + (lane - n_o));   // history's position in the run
-            if (ww_on(P) || P.implicit || P.pc_target > 0) atomicAdd(&s_w[0], 1.0);
+            if (weights_summed(P)) atomicAdd(&s_w[0], 1.0);
             atomicAdd(&s_n[7], 1u);
             alive = !(P.T > 0 && q.tbin >= P.T);
             if (!alive) finish<PR, DIM>(P, A, es, q, END_CENSUSED);
@@ -1743,7 +1746,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   // claimed an item must not read its per-problem arguments.)
   Stats *const stats = MULTI ? MA.args[0].stats : A.stats;
   int32_t *const errw = MULTI ? MA.args[0].error : A.error;
-  const int ovf_cap = MULTI ? 0 : A.overflow_cap;
+  const int ovf_cap = Ain.overflow_cap;
   uint32_t c4[4] = {lc.seg, lc.col, lc.cross, lc.census};
 #pragma unroll
   for (int f = 0; f < 4; ++f)

@@ -12,7 +12,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2409_04668_b300 import workloads as W
-from parity_util import (REL_TALLY, compare_counts, compare_records, compare_tallies,
+from parity_util import (COUNT_KEYS, REL_TALLY, compare_counts, compare_records, compare_tallies,
                          fp32_bins_agree, small_channel)
 
 pytestmark = pytest.mark.gpu
@@ -407,3 +407,60 @@ def test_uncollided_beam_through_void_gap_and_census(mcdc, prec, sampling):
     assert np.all(np.abs(z) < 4.5), (np.abs(z).max(), int(np.abs(z).argmax()))
     # the void cells: every history that reaches the gap crosses it whole
     np.testing.assert_allclose(s1[rv], np.exp(-2.4), rtol=6 * np.sqrt((1 - np.exp(-2.4)) / (np.exp(-2.4) * N)))
+
+
+def _ww_boxes():
+    """Three small 3-D problems of different sizes and materials, all faces
+    reflecting (every history ends by absorption), each with its own table of
+    lower bounds drawn so that both splits and roulettes happen."""
+    out = []
+    for k, (n, c, seed) in enumerate((((4, 2, 2), 0.8, 7), ((3, 3, 2), 0.7, 8), ((5, 2, 3), 0.85, 9))):
+        mat = np.zeros((n[2], n[1], n[0]), np.uint8)
+        w = (0.5, 1.0, 0.7)
+        ext = tuple(a * b for a, b in zip(n, w))
+        prob = W.box(f"ww_box{k}", n, w, mat, [[1.0]], [[c]], np.ones((1, 1, 1)), [1.0],
+                     (0.0, 0.0, 0.0), ext, None, (0, 0, 0), n, bc=(W.BC_REFLECT,) * 6)
+        lower = np.random.default_rng(seed).uniform(0.05, 0.6, size=prob.n_bins)
+        out.append((prob, lower))
+    return out
+
+
+def test_fp64_batched_weight_windows_match_oracle(mcdc):
+    """Table windows in a batched run: every problem splits and roulettes with
+    its own table in the shared launch, its children staying in the warp that
+    serves its work item, and equals the oracle at its own seed (1e-9, event
+    counts summed over the problems exactly).  Turning the windows off makes
+    the next call analog (the cached plan holds the problems' tables, so it
+    must not be replayed)."""
+    boxes = _ww_boxes()
+    hist, seed, B = [6000, 5000, 4000], 31, 4
+    handles = [mcdc.Problem(p, precision=mcdc.PREC_FP64) for p, _ in boxes]
+    try:
+        for h, (p, lower) in zip(handles, boxes):
+            h.set_weight_windows(lower, 5.0, 2.5, 16)
+        means = [np.zeros(h.n_bins) for h in handles]
+        for windows in (True, False):
+            stats, scal = mcdc.run_batched(handles, hist, seed, batches=B, means=means)
+            tot = {k: 0 for k in COUNT_KEYS}
+            for i, (p, lower) in enumerate(boxes):
+                s = (seed + i * 0x9E3779B97F4A7C15) % (1 << 64)
+                ww = ({"lower": lower, "upper_ratio": 5.0, "survival_ratio": 2.5, "nmax": 16}
+                      if windows else None)
+                o = O.run(p, hist[i], seed=s, batches=B, ww=ww)
+                for k in COUNT_KEYS:
+                    tot[k] += o["counts"][k]
+                got = means[i].reshape(p.tally_shape)
+                nz = o["mean"] != 0
+                np.testing.assert_allclose(got[nz], o["mean"][nz], rtol=REL_TALLY)
+                np.testing.assert_array_equal(got == 0, o["mean"] == 0)
+            compare_counts(stats, tot)
+            if windows:
+                assert stats["splits"] > 100 and stats["roulette_killed"] > 100, stats
+                assert stats["splits_dropped"] == 0
+                for h in handles:
+                    h.set_weight_windows(None, 0.0, 0.0, 0)
+            else:
+                assert stats["splits"] == 0 and stats["roulette_killed"] == 0
+    finally:
+        for h in handles:
+            h.close()
