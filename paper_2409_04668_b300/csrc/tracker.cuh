@@ -160,6 +160,7 @@ __device__ __forceinline__ Bank<PR> bank_view(void *base, long long cap, int dim
 
 // particles a warp can park in shared memory besides the 32 in flight
 constexpr int kPool = 96;
+constexpr int kReserve = 256;   // population control: input positions a warp reserves at once
 
 // shared-memory layout of one CTA
 struct Layout {
@@ -1270,6 +1271,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   __shared__ uint64_t s_pf_bar[16];            // one mbarrier per warp
   __shared__ unsigned long long s_pf_first[16];
   __shared__ int s_pf_got[16], s_pf_phase[16], s_pf_lost[16];
+  // population control: each warp's reservation [next, end) of input positions
+  __shared__ unsigned long long s_res_next[16], s_res_end[16];
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -1311,6 +1314,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (prefetch && (tid & 31) == 0) {
     tc::mbar_init(&s_pf_bar[tid >> 5], 1);
     s_pf_got[tid >> 5] = 0;
+    s_res_next[tid >> 5] = s_res_end[tid >> 5] = 0;
     s_pf_phase[tid >> 5] = 0;
     s_pf_lost[tid >> 5] = -1;
   }
@@ -1328,6 +1332,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
   bool agg = MULTI ? false : A.warp_aggregate != 0;
+  // particles in this launch's input bank (fixed while it runs: written by the
+  // comb or the previous pass), read once instead of at every claim
+  const unsigned long long in_total =
+      (!MULTI && Ain.spill_in != nullptr) ? min(*Ain.spill_in_count, Ain.spill_cap) : 0ull;
   uint64_t g_h0 = 0, g_h1 = 0;
   if (!SHARED && !MULTI) {
     g_h0 = A.tally_per_batch ? 0 : batch_start(A.n_hist, A.n_batches, A.batch);
@@ -1384,6 +1392,20 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     bool exhausted = false;
     const uint32_t lt = lanemask_lt();
     auto slot_of = [&](int s) { return pool0 + min(max(s, 0), kPool - 1); };
+    // population control (lane 0): the first of the next 32 input positions,
+    // from the warp's reservation, which one atomic refills kReserve at a
+    // time (a claim per 32 would hold the warp for an atomic's round trip
+    // every ~3 flights); 32-aligned, so a claim never straddles two
+    // reservations, and a short claim still means the input is used up
+    auto claim32 = [&]() -> unsigned long long {
+      unsigned long long nx = s_res_next[warp];
+      if (nx >= s_res_end[warp]) {
+        nx = atomicAdd(A.spill_in_cursor, (unsigned long long)kReserve);
+        s_res_end[warp] = nx + kReserve;
+      }
+      s_res_next[warp] = nx + 32ull;
+      return nx;
+    };
     for (;;) {
       __syncwarp();   // every lane sees the same overflow count below
       // (1) collisions: a dense pass when 32 are parked, or whatever is
@@ -1482,8 +1504,9 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           int got = 0;
           if (lane == 0) {
             if (A.spill_in != nullptr && !MULTI) {
-              const unsigned long long total = min(*A.spill_in_count, A.spill_cap);
-              first = atomicAdd(A.spill_in_cursor, (unsigned long long)want);
+              const unsigned long long total = in_total;
+              first = (prefetch && want == 32) ? claim32()
+                                               : atomicAdd(A.spill_in_cursor, (unsigned long long)want);
               got = first < total ? (int)min((unsigned long long)want, total - first) : 0;
             } else if (SHARED || MULTI) {
               first = atomicAdd(&s_h_next, (unsigned long long)want);
@@ -1580,8 +1603,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         if (prefetch && !exhausted && s_pf_got[warp] == 0) {
           int ng = 0;
           if (lane == 0) {
-            const unsigned long long total = min(*A.spill_in_count, A.spill_cap);
-            const unsigned long long nf = atomicAdd(A.spill_in_cursor, 32ull);
+            const unsigned long long total = in_total;
+            const unsigned long long nf = claim32();
             ng = nf < total ? (int)min(32ull, total - nf) : 0;
             if (ng > 0) {
               const Bank<PR> src =
