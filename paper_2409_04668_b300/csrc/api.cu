@@ -521,10 +521,10 @@ std::map<std::string, TuneChoice> g_tune_cache;
 std::string tune_key(const mcdc_problem *pr) {
   const DevProblem &P = pr->P;
   char b[256];
-  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d|%d", (int)pr->key.f64,
-           (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T, (long long)P.n_bins,
-           P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit, P.fresh_tau,
-           (int)pr->key.net);
+  snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d",
+           (int)pr->key.f64, (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T,
+           (long long)P.n_bins, P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit,
+           P.fresh_tau, (int)pr->key.net, pr->user_aggregate, pr->user_cps);
   return b;
 }
 
@@ -555,12 +555,16 @@ int autotune(mcdc_problem *pr, const DeviceLimits &dl) {
   for (int b : {128, 256, 512}) {
     // CTAs per SM: all that fit, and half of them when that is at least one
     const int full = track_occupancy(pr->key, b, make_layout(pr, (b / 32) * kPool, pr->tally_mode).total);
+    // the caller's own choices (warp aggregation on or off, CTAs per SM) are
+    // kept; the tuner chooses only what was left to it
     std::vector<int> cps{0};
-    if (full >= 2) cps.push_back(full / 2);
+    if (pr->user_cps > 0) cps = {pr->user_cps};
+    else if (full >= 2) cps.push_back(full / 2);
+    std::vector<int> aggs = pr->P.n_bins <= 65536 ? std::vector<int>{0, 1} : std::vector<int>{0};
+    if (pr->user_aggregate != 0) aggs = {pr->user_aggregate > 0 ? 1 : 0};
     for (int c : cps)
       for (int bpc : shared ? std::vector<int>{1, 2, 4} : std::vector<int>{2})
-        for (int agg : pr->P.n_bins <= 65536 ? std::vector<int>{0, 1} : std::vector<int>{0})
-          cand.push_back({b, bpc, agg, c});
+        for (int agg : aggs) cand.push_back({b, bpc, agg, c});
   }
   const TuneChoice keep{pr->block, pr->batch_per_cta, pr->warp_aggregate, pr->opt.ctas_per_sm};
   const uint64_t n_trial = 1ull << 20;
@@ -866,6 +870,8 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   pr->device = dev;
   pr->sms = dl.sms;
   pr->opt = o;
+  pr->user_aggregate = o.warp_aggregate;
+  pr->user_cps = o.ctas_per_sm;
   pr->edges = edges;
   DevProblem &P = pr->P;
   for (int a = 0; a < 3; ++a) {
