@@ -227,7 +227,10 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   for (int i = 0; i < n; ++i) {
     mcdc_problem *p = probs[i];
     hp[i] = p->P;
-    hp[i].sum_weights = 1;        // one weight sum over problems with and without windows
+    // with windows in the run, every problem's weights are summed on the
+    // device (one sum over problems with and without windows); analog runs
+    // carry unit weights, and their counts are the weights
+    hp[i].sum_weights = windows ? 1 : 0;
     RunArgs A{};
     A.n_hist = n_histories[i];
     A.offset = 0;
@@ -461,10 +464,12 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     stats->splits = h.splits; stats->children = h.children;
     stats->roulette_killed = h.roulette_killed; stats->roulette_survived = h.roulette_survived;
     stats->splits_dropped = h.splits_dropped;
-    stats->w_source = h.w_source;     // summed on the device for every problem
-    stats->w_absorbed = h.w_absorbed;
-    stats->w_leaked = h.w_leaked;
-    stats->w_censused = h.w_censused;
+    // summed on the device when the run has windows, else unit weights
+    const bool wsum = h.w_source > 0.0;
+    stats->w_source = wsum ? h.w_source : (double)h.histories;
+    stats->w_absorbed = wsum ? h.w_absorbed : (double)h.absorbed;
+    stats->w_leaked = wsum ? h.w_leaked : (double)h.leaked;
+    stats->w_censused = wsum ? h.w_censused : (double)h.censused;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, pl->e0, pl->e1);
     stats->kernel_ms = ms;
