@@ -919,6 +919,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   pr->key.f64 = (o.precision == MCDC_PREC_FP64);
   pr->key.local = (o.precision == MCDC_PREC_FP32_LOCAL);
   pr->key.dim = pr->dim;
+  pr->key.pc = o.pc_target > 0;
 
   int rc = MCDC_OK;
   auto bail = [&](int code) {

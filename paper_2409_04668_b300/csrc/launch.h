@@ -56,6 +56,7 @@ struct TrackKey {
   bool shared;
   int dim;   // 1 or 3
   bool net = false;     // per-event network windows (global tally, single problem)
+  bool pc = false;      // population control (global tally, single problem)
 };
 
 // Launches the persistent tracker for one configuration (MA: batched mode only).

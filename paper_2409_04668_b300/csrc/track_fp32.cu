@@ -17,11 +17,13 @@ cudaError_t launch_net_lower_f64(const TrackKey &, cudaStream_t, const DevProble
                                  const double *, const int32_t *, long long, double *, int);
 
 namespace {
-template <class PR, bool SH, int DIM, bool MU, bool NET = false>
-void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU, NET>; }
+template <class PR, bool SH, int DIM, bool MU, bool NET = false, bool PC = false>
+void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU, NET, PC>; }
 
 template <class PR>
 void *pick_prec(const TrackKey &k) {
+  if (k.pc) return k.dim == 1 ? fp32_kernel<PR, false, 1, false, false, true>()
+                              : fp32_kernel<PR, false, 3, false, false, true>();
   if (k.net) return k.dim == 1 ? fp32_kernel<PR, false, 1, false, true>()
                                : fp32_kernel<PR, false, 3, false, true>();
   if (k.multi) return k.dim == 1 ? fp32_kernel<PR, false, 1, true>() : fp32_kernel<PR, false, 3, true>();

@@ -8,10 +8,12 @@
 
 namespace mcdc {
 namespace {
-template <bool SH, int DIM, bool MU, bool NET = false>
-void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET>; }
+template <bool SH, int DIM, bool MU, bool NET = false, bool PC = false>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET, PC>; }
 
 void *pick(const TrackKey &k) {
+  if (k.pc) return k.dim == 1 ? fp64_kernel<false, 1, false, false, true>()
+                              : fp64_kernel<false, 3, false, false, true>();
   if (k.net) return k.dim == 1 ? fp64_kernel<false, 1, false, true>() : fp64_kernel<false, 3, false, true>();
   if (k.multi) return k.dim == 1 ? fp64_kernel<false, 1, true>() : fp64_kernel<false, 3, true>();
   if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1, false>() : fp64_kernel<true, 3, false>();

@@ -568,7 +568,7 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 // network kernels: net_check_warp after the flight pass)
 enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3, OUT_WW = 4 };
 
-template <class PR, int DIM, bool NET>
+template <class PR, int DIM, bool NET, bool PC>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
                                       PartOf<PR> &p, int &bin,
@@ -713,7 +713,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if constexpr (PR::kLocal) p.t = p.tbin < P.T ? __ldg(P.binw32 + p.tbin) : 0.0f;
     else p.t = tb.edges[p.tbin];
     if (p.tbin == P.T) { end = END_CENSUSED; return OUT_DEAD; }
-    if (A.census_out != nullptr) return OUT_BANKED;   // waits for the comb
+    if (PC && A.census_out != nullptr) return OUT_BANKED;   // waits for the comb
     return OUT_CONT;
   }
   if (ev == 1) {
@@ -1215,7 +1215,10 @@ struct MultiArgs {
   unsigned long long *counter;
 };
 
-template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false>
+// PC: the population-control instantiation (global tally, one problem): census
+// banking, the step tally, staged births and reserved input claims exist only
+// there, so the other kernels carry none of their code.
+template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false, bool PC = false>
 __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
                                                const MultiArgs MA) {
   using R = typename PR::R;
@@ -1231,11 +1234,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   const RunArgs &A = MULTI ? sA : Ain;
   // population-control step tally: from the launch's own arguments (batched
   // launches fill sA only when a CTA claims an item, and never use it)
-  const bool step_tally = !SHARED && !MULTI && Ain.step_tally != 0;
+  const bool step_tally = PC && Ain.step_tally != 0;
   const int step_bins = step_tally ? Ain.step_bins : 0;
-  const bool prefetch = !SHARED && !MULTI && Ain.prefetch != 0 && Ain.spill_in != nullptr;
+  const bool prefetch = PC && Ain.prefetch != 0 && Ain.spill_in != nullptr;
   // input positions matter to population control alone (global tally, single problem)
-  const bool use_slot = !SHARED && !MULTI && Ain.census_out != nullptr;
+  const bool use_slot = PC && Ain.census_out != nullptr;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
@@ -1271,8 +1274,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   __shared__ uint64_t s_pf_bar[16];            // one mbarrier per warp
   __shared__ unsigned long long s_pf_first[16];
   __shared__ int s_pf_got[16], s_pf_phase[16], s_pf_lost[16];
-  // population control: each warp's reservation [next, end) of input positions
-  __shared__ unsigned long long s_res_next[16], s_res_end[16];
+  // population control: each warp's reservation [next, end) of input positions;
+  // the particles in this launch's input bank (fixed while it runs: written by
+  // the comb or the previous pass), read once instead of at every claim
+  __shared__ unsigned long long s_res_next[16], s_res_end[16], s_in_total;
 
   __shared__ unsigned long long s_h_next, s_h_end;
   __shared__ int s_done, s_batch;
@@ -1310,7 +1315,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   if (tid < 16) s_novf[32 + tid] = Ain.overflow_cap;
   if (tid < 4) s_w[tid] = 0.0;
   if (tid < 9) s_n[tid] = 0u;
-  if (tid == 0) { s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1; }
+  if (tid == 0) {
+    s_done = 0; s_batch = -1; s_h_next = s_h_end = 0; s_cur_p = -1;
+    s_in_total = (!MULTI && Ain.spill_in != nullptr) ? min(*Ain.spill_in_count, Ain.spill_cap) : 0ull;
+  }
   if (prefetch && (tid & 31) == 0) {
     tc::mbar_init(&s_pf_bar[tid >> 5], 1);
     s_pf_got[tid >> 5] = 0;
@@ -1332,10 +1340,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
   bool agg = MULTI ? false : A.warp_aggregate != 0;
-  // particles in this launch's input bank (fixed while it runs: written by the
-  // comb or the previous pass), read once instead of at every claim
-  const unsigned long long in_total =
-      (!MULTI && Ain.spill_in != nullptr) ? min(*Ain.spill_in_count, Ain.spill_cap) : 0ull;
+
   uint64_t g_h0 = 0, g_h1 = 0;
   if (!SHARED && !MULTI) {
     g_h0 = A.tally_per_batch ? 0 : batch_start(A.n_hist, A.n_batches, A.batch);
@@ -1504,7 +1509,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           int got = 0;
           if (lane == 0) {
             if (A.spill_in != nullptr && !MULTI) {
-              const unsigned long long total = in_total;
+              const unsigned long long total = s_in_total;
               first = (prefetch && want == 32) ? claim32()
                                                : atomicAdd(A.spill_in_cursor, (unsigned long long)want);
               got = first < total ? (int)min((unsigned long long)want, total - first) : 0;
@@ -1543,7 +1548,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             const long long at = (long long)h_first + (lane - n_o);
             if (staged)                      // staged by the bulk copies
               stage.load(lane, q, DIM);
-            else if (A.census_out != nullptr)     // population control: the combed bank (pool layout)
+            else if (PC && A.census_out != nullptr)     // population control: the combed bank (pool layout)
               bank_view<PR>(const_cast<void *>(A.spill_in), (long long)A.spill_cap, DIM)
                   .load((int)at, q, DIM);
             else
@@ -1603,7 +1608,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         if (prefetch && !exhausted && s_pf_got[warp] == 0) {
           int ng = 0;
           if (lane == 0) {
-            const unsigned long long total = in_total;
+            const unsigned long long total = s_in_total;
             const unsigned long long nf = claim32();
             ng = nf < total ? (int)min(32ull, total - nf) : 0;
             if (ng > 0) {
@@ -1644,7 +1649,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         R score = (R)0;
         const bool flew = has;
         if (has) {
-          outcome = flight<PR, DIM, NET>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
+          outcome = flight<PR, DIM, NET, PC>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         if (step_tally)
@@ -1661,7 +1666,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             if (!ok) { finish<PR, DIM>(P, A, es, p, END_ROULETTE); has = false; }
           }
         }
-        if (A.census_out != nullptr) {
+        if (PC && A.census_out != nullptr) {
           // population control: a banked particle goes to its input position
           // (no splitting here, so every input yields at most one), which
           // keeps the bank in the order the step ran its particles
