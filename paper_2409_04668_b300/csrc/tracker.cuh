@@ -1532,7 +1532,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             // children beyond a small stack go there and are shared by every
             // warp in the next pass, instead of one warp working through a
             // large family while the others have finished
-            if (lane == 0 && A.spill_out != nullptr && A.overflow_tail >= 0)
+            if (!SHARED && !MULTI && lane == 0 && A.spill_out != nullptr && A.overflow_tail >= 0)
               novf[32] = min(A.overflow_cap, A.overflow_tail);
           }
         }
