@@ -1334,9 +1334,11 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   const int wid = blockIdx.x * nwarps + warp;                 // warp id in the grid
   // the warp's stack of split children (batched launches: one stack per warp
   // for every problem it serves; none when no problem has windows)
-  PartOf<PR> *ovf = Ain.overflow == nullptr
-                        ? nullptr
-                        : reinterpret_cast<PartOf<PR> *>(Ain.overflow) + (size_t)wid * Ain.overflow_cap;
+  PartOf<PR> *ovf =
+      MULTI ? (Ain.overflow == nullptr
+                   ? nullptr
+                   : reinterpret_cast<PartOf<PR> *>(Ain.overflow) + (size_t)wid * Ain.overflow_cap)
+            : reinterpret_cast<PartOf<PR> *>(A.overflow) + (size_t)wid * A.overflow_cap;
   int *novf = &s_novf[warp];
   const int pool0 = warp * kPool;                              // first slot of this warp
   bool agg = MULTI ? false : A.warp_aggregate != 0;
@@ -1774,7 +1776,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   // claimed an item must not read its per-problem arguments.)
   Stats *const stats = MULTI ? MA.args[0].stats : A.stats;
   int32_t *const errw = MULTI ? MA.args[0].error : A.error;
-  const int ovf_cap = Ain.overflow_cap;
+  const int ovf_cap = MULTI ? Ain.overflow_cap : A.overflow_cap;
   uint32_t c4[4] = {lc.seg, lc.col, lc.cross, lc.census};
 #pragma unroll
   for (int f = 0; f < 4; ++f)
