@@ -524,7 +524,7 @@ std::string tune_key(const mcdc_problem *pr) {
   snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d",
            (int)pr->key.f64, (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T,
            (long long)P.n_bins, P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit,
-           P.fresh_tau, (int)pr->key.net, pr->user_aggregate, pr->user_cps);
+           P.fresh_tau, (int)pr->key.net * 2 + (int)pr->key.ww, pr->user_aggregate, pr->user_cps);
   return b;
 }
 
@@ -671,9 +671,13 @@ std::vector<uint32_t> net_fragments(const float *prm, int in, int H) {
   return f;
 }
 
-int set_net_kernel(mcdc_problem *pr, bool net) {
-  if (pr->key.net == net) return MCDC_OK;
+// Switches the problem's tracker instantiation: with the per-event network
+// evaluation (net), with the window checks of a table (ww), or analog; the
+// launch shape is redone for it (registers, so CTAs per SM, may differ).
+int set_track_kernel_impl(mcdc_problem *pr, bool net, bool ww) {
+  if (pr->key.net == net && pr->key.ww == ww) return MCDC_OK;
   pr->key.net = net;
+  pr->key.ww = ww;
   DeviceLimits dl;
   if (int rc = device_limits(pr->device, &dl)) return rc;
   pr->opt.tally_mode = pr->tally_mode;
@@ -683,6 +687,7 @@ int set_net_kernel(mcdc_problem *pr, bool net) {
 
 namespace mcdc {
 int set_error(int code, const std::string &msg) { return fail(code, msg); }
+int set_track_kernel(mcdc_problem *pr, bool net, bool ww) { return set_track_kernel_impl(pr, net, ww); }
 int ensure_overflow_for(mcdc_problem *pr) { return ensure_overflow(pr); }
 cudaMemPool_t device_mem_pool(int dev) {
   const DevPool d = device_pool(dev);
@@ -1019,7 +1024,7 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
     pr->P.ww_net64 = nullptr;
     pr->P.ww_net32 = nullptr;
     pr->P.ww_netfrag = nullptr;
-    return set_net_kernel(pr, false);
+    return set_track_kernel_impl(pr, false, false);
   }
   if (pr->P.pc_target > 0)
     return fail(MCDC_ERR_INVALID, "weight windows and population control do not combine");
@@ -1051,7 +1056,7 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
   pr->P.ww_upper = upper_ratio;
   pr->P.ww_survival = survival_ratio;
   pr->P.ww_nmax = nmax;
-  if (int rc = set_net_kernel(pr, false)) return rc;
+  if (int rc = set_track_kernel_impl(pr, false, true)) return rc;
   return ensure_overflow(pr);
 }
 
@@ -1113,9 +1118,9 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   CK(cudaMemcpy(pr->net32, h32.data(), n * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pr->netfrag, frag.data(), (size_t)kNetFragBytes, cudaMemcpyHostToDevice));
   // the network kernel first: if its launch shape fails, nothing changes
-  if (int rc = set_net_kernel(pr, true)) {
+  if (int rc = set_track_kernel_impl(pr, true, false)) {
     const std::string msg = g_err;
-    set_net_kernel(pr, false);
+    set_track_kernel_impl(pr, false, false);
     return fail(rc, msg);
   }
   DevProblem &P = pr->P;

@@ -169,6 +169,9 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   key.shared = false;
   key.multi = true;
   key.net = false;
+  key.pc = false;
+  key.ww = false;
+  for (int i = 0; i < n; ++i) key.ww = key.ww || ww_on(probs[i]->P);
   Layout L{};
   for (int i = 0; i < n; ++i) {
     L.M = std::max(L.M, probs[i]->P.M);

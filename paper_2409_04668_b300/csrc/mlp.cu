@@ -1665,9 +1665,13 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       pr->p_version += 1;
       pr->P.ww_lower = pr->ww64;
       pr->P.ww_lower32 = pr->ww32;
+      pr->P.ww_net64 = nullptr;
+      pr->P.ww_net32 = nullptr;
+      pr->P.ww_netfrag = nullptr;
       pr->P.ww_upper = o.upper_ratio;
       pr->P.ww_survival = o.survival_ratio;
       pr->P.ww_nmax = o.nmax;
+      if (int rc = mcdc::set_track_kernel(pr, false, true)) return rc;
       if (int rc = mcdc::ensure_overflow_for(pr)) return rc;
     }
   }

@@ -8,16 +8,23 @@
 
 namespace mcdc {
 namespace {
-template <bool SH, int DIM, bool MU, bool NET = false, bool PC = false>
-void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET, PC>; }
+template <bool SH, int DIM, bool MU, bool NET = false, bool PC = false, bool WW = false>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET, PC, WW>; }
+
+template <bool SH, bool MU>
+void *pick_ww(const TrackKey &k) {
+  if (k.ww) return k.dim == 1 ? fp64_kernel<SH, 1, MU, false, false, true>()
+                              : fp64_kernel<SH, 3, MU, false, false, true>();
+  return k.dim == 1 ? fp64_kernel<SH, 1, MU>() : fp64_kernel<SH, 3, MU>();
+}
 
 void *pick(const TrackKey &k) {
   if (k.pc) return k.dim == 1 ? fp64_kernel<false, 1, false, false, true>()
                               : fp64_kernel<false, 3, false, false, true>();
   if (k.net) return k.dim == 1 ? fp64_kernel<false, 1, false, true>() : fp64_kernel<false, 3, false, true>();
-  if (k.multi) return k.dim == 1 ? fp64_kernel<false, 1, true>() : fp64_kernel<false, 3, true>();
-  if (k.shared) return k.dim == 1 ? fp64_kernel<true, 1, false>() : fp64_kernel<true, 3, false>();
-  return k.dim == 1 ? fp64_kernel<false, 1, false>() : fp64_kernel<false, 3, false>();
+  if (k.multi) return pick_ww<false, true>(k);
+  if (k.shared) return pick_ww<true, false>(k);
+  return pick_ww<false, false>(k);
 }
 }  // namespace
 

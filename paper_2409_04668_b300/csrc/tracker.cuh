@@ -568,7 +568,7 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 // network kernels: net_check_warp after the flight pass)
 enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3, OUT_WW = 4 };
 
-template <class PR, int DIM, bool NET, bool PC>
+template <class PR, int DIM, bool NET, bool PC, bool WW>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
                                       PartOf<PR> &p, int &bin,
@@ -747,7 +747,9 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if constexpr (NET && !PR::kF64) {
       if (P.ww_net32 != nullptr) return OUT_WW;
     }
-    if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
+    if constexpr (WW || NET) {
+      if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
+    }
     return OUT_CONT;
   }
   return OUT_COLL;
@@ -759,7 +761,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 // capture: the weight is multiplied by sigma_s / sigma_t (the removed part is
 // returned in wabs), a weight that reaches 0 ends as absorbed, and a weight
 // below the cutoff is rouletted after the scatter (one more block).
-template <class PR, int DIM, bool NET>
+template <class PR, int DIM, bool NET, bool WW>
 __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typename PR::R> &tb,
                                         const RunArgs &A, const EndSink &es,
                                         PartOf<PR> &p, int &end, LocalCount &lc,
@@ -821,7 +823,9 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
     // FP32 network kernels: the check is left to the warp (net_check_warp)
     if (P.ww_net32 != nullptr) { ww_pend = true; return true; }
   }
-  if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
+  if constexpr (WW || NET) {
+    if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
+  }
   return true;
 }
 
@@ -1218,7 +1222,10 @@ struct MultiArgs {
 // PC: the population-control instantiation (global tally, one problem): census
 // banking, the step tally, staged births and reserved input claims exist only
 // there, so the other kernels carry none of their code.
-template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false, bool PC = false>
+// WW: a window table is set -- the instantiation that carries the window
+// checks (split, roulette, children), which analog kernels leave out.
+template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false, bool PC = false,
+          bool WW = false>
 __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
                                                const MultiArgs MA) {
   using R = typename PR::R;
@@ -1433,8 +1440,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           bool ww_pend = false;
           if (mine) {
             int end = END_NONE;
-            alive = collide<PR, DIM, NET>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore, wabs,
-                                          ww_pend);
+            alive = collide<PR, DIM, NET, WW>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore,
+                                              wabs, ww_pend);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
           if (P.estimator != 0) {
@@ -1651,7 +1658,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         R score = (R)0;
         const bool flew = has;
         if (has) {
-          outcome = flight<PR, DIM, NET, PC>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
+          outcome = flight<PR, DIM, NET, PC, WW>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         if (step_tally)
