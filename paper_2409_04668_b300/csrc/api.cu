@@ -524,7 +524,7 @@ std::string tune_key(const mcdc_problem *pr) {
   snprintf(b, sizeof b, "%d|%d|%d|%d|%d|%d|%d|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d",
            (int)pr->key.f64, (int)pr->key.local, pr->dim, pr->tally_mode, P.M, P.G, P.T,
            (long long)P.n_bins, P.n[0], P.n[1], P.n[2], pr->sms, P.estimator, P.implicit,
-           P.fresh_tau, (int)pr->key.net * 2 + (int)pr->key.ww, pr->user_aggregate, pr->user_cps);
+           P.fresh_tau, (int)pr->key.net * 2 + (int)pr->key.vr, pr->user_aggregate, pr->user_cps);
   return b;
 }
 
@@ -672,12 +672,14 @@ std::vector<uint32_t> net_fragments(const float *prm, int in, int H) {
 }
 
 // Switches the problem's tracker instantiation: with the per-event network
-// evaluation (net), with the window checks of a table (ww), or analog; the
+// evaluation (net), with the window checks of a table (ww) -- or implicit
+// capture, which also varies weights --, or analog; the
 // launch shape is redone for it (registers, so CTAs per SM, may differ).
 int set_track_kernel_impl(mcdc_problem *pr, bool net, bool ww) {
-  if (pr->key.net == net && pr->key.ww == ww) return MCDC_OK;
+  const bool vr = ww || pr->P.implicit != 0;     // implicit capture varies weights too
+  if (pr->key.net == net && pr->key.vr == vr) return MCDC_OK;
   pr->key.net = net;
-  pr->key.ww = ww;
+  pr->key.vr = vr;
   DeviceLimits dl;
   if (int rc = device_limits(pr->device, &dl)) return rc;
   pr->opt.tally_mode = pr->tally_mode;
@@ -925,6 +927,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   pr->key.local = (o.precision == MCDC_PREC_FP32_LOCAL);
   pr->key.dim = pr->dim;
   pr->key.pc = o.pc_target > 0;
+  pr->key.vr = o.implicit_capture != 0;
 
   int rc = MCDC_OK;
   auto bail = [&](int code) {

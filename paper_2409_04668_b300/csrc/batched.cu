@@ -170,8 +170,8 @@ int build_plan(BatchedPlan &pl, struct mcdc_problem *const *probs, int32_t n,
   key.multi = true;
   key.net = false;
   key.pc = false;
-  key.ww = false;
-  for (int i = 0; i < n; ++i) key.ww = key.ww || ww_on(probs[i]->P);
+  key.vr = false;
+  for (int i = 0; i < n; ++i) key.vr = key.vr || ww_on(probs[i]->P);
   Layout L{};
   for (int i = 0; i < n; ++i) {
     L.M = std::max(L.M, probs[i]->P.M);

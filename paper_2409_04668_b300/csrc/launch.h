@@ -57,7 +57,7 @@ struct TrackKey {
   int dim;   // 1 or 3
   bool net = false;     // per-event network windows (global tally, single problem)
   bool pc = false;      // population control (global tally, single problem)
-  bool ww = false;      // a weight-window table is set
+  bool vr = false;      // weights vary: a window table is set, or implicit capture is on
 };
 
 // Launches the persistent tracker for one configuration (MA: batched mode only).
@@ -122,7 +122,7 @@ namespace mcdc {
 // Allocates the per-warp overflow stacks once weight windows are on.
 int ensure_overflow_for(mcdc_problem *pr);
 // Selects the problem's tracker instantiation (per-event network windows, a
-// window table, or analog) and redoes its launch shape.
+// window table -- or implicit capture --, or analog) and redoes its launch shape.
 int set_track_kernel(mcdc_problem *pr, bool net, bool ww);
 // Drops every cached batched-run plan that holds the problem with this uid
 // (called when the problem is destroyed).

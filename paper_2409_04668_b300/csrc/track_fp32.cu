@@ -17,13 +17,13 @@ cudaError_t launch_net_lower_f64(const TrackKey &, cudaStream_t, const DevProble
                                  const double *, const int32_t *, long long, double *, int);
 
 namespace {
-template <class PR, bool SH, int DIM, bool MU, bool NET = false, bool PC = false, bool WW = false>
-void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU, NET, PC, WW>; }
+template <class PR, bool SH, int DIM, bool MU, bool NET = false, bool PC = false, bool VR = false>
+void *fp32_kernel() { return (void *)k_track<PR, SH, DIM, MU, NET, PC, VR>; }
 
-// the instantiation for a tally mode and dimension, with or without windows
+// the instantiation for a tally mode and dimension, with or without varying weights
 template <class PR, bool SH, bool MU>
-void *pick_ww(const TrackKey &k) {
-  if (k.ww) return k.dim == 1 ? fp32_kernel<PR, SH, 1, MU, false, false, true>()
+void *pick_vr(const TrackKey &k) {
+  if (k.vr) return k.dim == 1 ? fp32_kernel<PR, SH, 1, MU, false, false, true>()
                               : fp32_kernel<PR, SH, 3, MU, false, false, true>();
   return k.dim == 1 ? fp32_kernel<PR, SH, 1, MU>() : fp32_kernel<PR, SH, 3, MU>();
 }
@@ -34,9 +34,9 @@ void *pick_prec(const TrackKey &k) {
                               : fp32_kernel<PR, false, 3, false, false, true>();
   if (k.net) return k.dim == 1 ? fp32_kernel<PR, false, 1, false, true>()
                                : fp32_kernel<PR, false, 3, false, true>();
-  if (k.multi) return pick_ww<PR, false, true>(k);
-  if (k.shared) return pick_ww<PR, true, false>(k);
-  return pick_ww<PR, false, false>(k);
+  if (k.multi) return pick_vr<PR, false, true>(k);
+  if (k.shared) return pick_vr<PR, true, false>(k);
+  return pick_vr<PR, false, false>(k);
 }
 
 void *pick(const TrackKey &k) { return k.local ? pick_prec<PrecF32L>(k) : pick_prec<PrecF32>(k); }

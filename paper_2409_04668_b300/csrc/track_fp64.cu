@@ -8,12 +8,12 @@
 
 namespace mcdc {
 namespace {
-template <bool SH, int DIM, bool MU, bool NET = false, bool PC = false, bool WW = false>
-void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET, PC, WW>; }
+template <bool SH, int DIM, bool MU, bool NET = false, bool PC = false, bool VR = false>
+void *fp64_kernel() { return (void *)k_track<PrecF64, SH, DIM, MU, NET, PC, VR>; }
 
 template <bool SH, bool MU>
-void *pick_ww(const TrackKey &k) {
-  if (k.ww) return k.dim == 1 ? fp64_kernel<SH, 1, MU, false, false, true>()
+void *pick_vr(const TrackKey &k) {
+  if (k.vr) return k.dim == 1 ? fp64_kernel<SH, 1, MU, false, false, true>()
                               : fp64_kernel<SH, 3, MU, false, false, true>();
   return k.dim == 1 ? fp64_kernel<SH, 1, MU>() : fp64_kernel<SH, 3, MU>();
 }
@@ -22,9 +22,9 @@ void *pick(const TrackKey &k) {
   if (k.pc) return k.dim == 1 ? fp64_kernel<false, 1, false, false, true>()
                               : fp64_kernel<false, 3, false, false, true>();
   if (k.net) return k.dim == 1 ? fp64_kernel<false, 1, false, true>() : fp64_kernel<false, 3, false, true>();
-  if (k.multi) return pick_ww<false, true>(k);
-  if (k.shared) return pick_ww<true, false>(k);
-  return pick_ww<false, false>(k);
+  if (k.multi) return pick_vr<false, true>(k);
+  if (k.shared) return pick_vr<true, false>(k);
+  return pick_vr<false, false>(k);
 }
 }  // namespace
 

@@ -568,7 +568,7 @@ __device__ void source_particle(const DevProblem &P, const Tables<typename PR::R
 // network kernels: net_check_warp after the flight pass)
 enum Outcome { OUT_CONT = 0, OUT_COLL = 1, OUT_DEAD = 2, OUT_BANKED = 3, OUT_WW = 4 };
 
-template <class PR, int DIM, bool NET, bool PC, bool WW>
+template <class PR, int DIM, bool NET, bool PC, bool VR>
 __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename PR::R> &tb,
                                       const RunArgs &A, const EndSink &es,
                                       PartOf<PR> &p, int &bin,
@@ -747,7 +747,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
     if constexpr (NET && !PR::kF64) {
       if (P.ww_net32 != nullptr) return OUT_WW;
     }
-    if constexpr (WW || NET) {
+    if constexpr (VR || NET) {
       if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return OUT_DEAD; }
     }
     return OUT_CONT;
@@ -761,7 +761,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
 // capture: the weight is multiplied by sigma_s / sigma_t (the removed part is
 // returned in wabs), a weight that reaches 0 ends as absorbed, and a weight
 // below the cutoff is rouletted after the scatter (one more block).
-template <class PR, int DIM, bool NET, bool WW>
+template <class PR, int DIM, bool NET, bool PC, bool VR>
 __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typename PR::R> &tb,
                                         const RunArgs &A, const EndSink &es,
                                         PartOf<PR> &p, int &end, LocalCount &lc,
@@ -792,7 +792,9 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   R xi1, xi2;
   if constexpr (PR::kF64) { xi1 = u01_f64(r1.a, r1.b); xi2 = u01_f64(r1.c, r1.d); }
   else { xi1 = u01_f32(r1.a); xi2 = u01_f32(r1.c); }
-  if (P.implicit) {
+  // implicit capture exists in the weighted instantiations only
+  constexpr bool kImplicit = VR || NET || PC;
+  if (kImplicit && P.implicit) {
     if constexpr (PR::kF64) wabs = p.w * (1.0 - ratio);
     else wabs = (double)p.w * (1.0 - (double)ratio);
     p.w *= ratio;
@@ -806,7 +808,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   // FP32 modes: optical depth to the next collision from the direction
   // block's second word (unused by the FP32 draws)
   if constexpr (!PR::kF64) p.tau = -logf(u01_f32(r2.b));
-  if (P.implicit) {
+  if (kImplicit && P.implicit) {
     R wcut, wsurv;
     if constexpr (PR::kF64) { wcut = P.wcut; wsurv = P.wsurv; }
     else { wcut = P.wcut32; wsurv = P.wsurv32; }
@@ -823,7 +825,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
     // FP32 network kernels: the check is left to the warp (net_check_warp)
     if (P.ww_net32 != nullptr) { ww_pend = true; return true; }
   }
-  if constexpr (WW || NET) {
+  if constexpr (VR || NET) {
     if (!weight_window<PR, DIM, NET>(P, tb, A, es, p, s_novf, ovf)) { end = END_ROULETTE; return false; }
   }
   return true;
@@ -1222,10 +1224,11 @@ struct MultiArgs {
 // PC: the population-control instantiation (global tally, one problem): census
 // banking, the step tally, staged births and reserved input claims exist only
 // there, so the other kernels carry none of their code.
-// WW: a window table is set -- the instantiation that carries the window
-// checks (split, roulette, children), which analog kernels leave out.
+// VR: particle weights vary (a window table is set, or implicit capture is
+// on) -- the instantiation that carries the window checks (split, roulette,
+// children) and implicit capture, which analog kernels leave out.
 template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false, bool PC = false,
-          bool WW = false>
+          bool VR = false>
 __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
                                                const MultiArgs MA) {
   using R = typename PR::R;
@@ -1440,8 +1443,8 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           bool ww_pend = false;
           if (mine) {
             int end = END_NONE;
-            alive = collide<PR, DIM, NET, WW>(P, tb, A, es, q, end, lc, novf, ovf, cbin, cscore,
-                                              wabs, ww_pend);
+            alive = collide<PR, DIM, NET, PC, VR>(P, tb, A, es, q, end, lc, novf, ovf, cbin,
+                                                  cscore, wabs, ww_pend);
             if (!alive) finish<PR, DIM>(P, A, es, q, end);
           }
           if (P.estimator != 0) {
@@ -1456,7 +1459,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
                                    (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
                                    mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
           }
-          if (P.implicit) {
+          if ((VR || NET || PC) && P.implicit) {
             // weight removed by implicit capture: one shared add per warp
             for (int o = 16; o > 0; o >>= 1) wabs += __shfl_xor_sync(0xffffffffu, wabs, o);
             if (lane == 0) atomicAdd(&s_w[1], wabs);
@@ -1658,7 +1661,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         R score = (R)0;
         const bool flew = has;
         if (has) {
-          outcome = flight<PR, DIM, NET, PC, WW>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
+          outcome = flight<PR, DIM, NET, PC, VR>(P, tb, A, es, p, bin, score, end, lc, novf, ovf);
           if (outcome == OUT_DEAD) { finish<PR, DIM>(P, A, es, p, end); has = false; }
         }
         if (step_tally)
