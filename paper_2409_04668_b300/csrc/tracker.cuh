@@ -1249,6 +1249,10 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
   const bool prefetch = PC && Ain.prefetch != 0 && Ain.spill_in != nullptr;
   // input positions matter to population control alone (global tally, single problem)
   const bool use_slot = PC && Ain.census_out != nullptr;
+  // split children (warp stacks, spill banks) exist only where weights vary;
+  // spilled or combed particles come in only there and under population control
+  constexpr bool kChildren = VR || NET;
+  constexpr bool kSpillIn = VR || NET || PC;
 
   // ---- carve shared memory
   unsigned char *ptr = smem;
@@ -1493,7 +1497,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
       const bool staged_ready = prefetch && s_pf_got[warp] > 0;
       if (__any_sync(0xffffffffu, !has) && rtop == 0 &&
           !(exhausted && *novf == 0 && !staged_ready)) {
-        const int n_o = min(32, min(*novf, A.overflow_cap));
+        const int n_o = kChildren ? min(32, min(*novf, A.overflow_cap)) : 0;
         int n_s = 0;
         unsigned long long h_first = 0;
         bool staged = false;
@@ -1520,7 +1524,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           unsigned long long first = 0;
           int got = 0;
           if (lane == 0) {
-            if (A.spill_in != nullptr && !MULTI) {
+            if (kSpillIn && A.spill_in != nullptr && !MULTI) {
               const unsigned long long total = s_in_total;
               first = (prefetch && want == 32) ? claim32()
                                                : atomicAdd(A.spill_in_cursor, (unsigned long long)want);
@@ -1556,7 +1560,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
           if (lane < n_o) {
             q = ovf[top - 1 - lane];
             alive = true;
-          } else if (A.spill_in != nullptr && !MULTI) {
+          } else if (kSpillIn && A.spill_in != nullptr && !MULTI) {
             const long long at = (long long)h_first + (lane - n_o);
             if (staged)                      // staged by the bulk copies
               stage.load(lane, q, DIM);
@@ -1584,7 +1588,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         const int r = __popc(empty & lt);              // rank of my empty lane
         if (alive && k >= ne) bk.store(slot_of(k - ne), q, DIM, use_slot);
         __syncwarp();
-        if (lane == 0) *novf = min(*novf, A.overflow_cap) - n_o;
+        if (kChildren && lane == 0) *novf = min(*novf, A.overflow_cap) - n_o;
         // lane with the r-th empty slot receives the r-th newborn (a shuffle per field)
         const int src = (r < na) ? (int)nth32(am, r) : 0;
         PartOf<PR> got;
