@@ -57,6 +57,9 @@ extern "C" {
 #define MCDC_ERR_TIMEOUT        -5   /* a bounded device wait gave up (tensor-core
                                         kernels of the importance network)     */
 #define MCDC_ERR_NO_DEVICE      -6   /* no usable sm_103 device                 */
+#define MCDC_ERR_CHECK          -7   /* checked build only: an index failed its
+                                        bounds check and its access was skipped
+                                        (mcdc_last_error: the site and index)  */
 
 #define MCDC_BC_VACUUM   0
 #define MCDC_BC_REFLECT  1
@@ -513,7 +516,7 @@ int mcdc_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
  * and survival bounds and the split cap as in mcdc_set_weight_windows.
  * params: FP32, host or device, copied (FP64 mode evaluates in FP64 from the
  * same values, one check at a time; the FP32 modes evaluate the checks of a
- * warp together on the tensor cores, BF16 operands, FP32 accumulation);
+ * warp together on the tensor cores, binary16 operands, FP32 accumulation);
  * NULL turns windows off.  Replaces any table.  Needs the global tally mode
  * (the other kernels are built without the evaluation).
  * Errors: MCDC_ERR_INVALID (sizes, ratios, non-finite values, population
@@ -543,6 +546,29 @@ int mcdc_get_weight_windows(const struct mcdc_problem *prob, double *w_lower);
  * MCDC_ERR_OOM, MCDC_ERR_CUDA. */
 int mcdc_network_window_lower(struct mcdc_problem *prob, const double *x, const double *t,
                               const int32_t *g, int64_t n, double *w_lower);
+
+/* The checked build.  Compiled with -DMCDC_CHECKS into libmcdc_b300_checks.so
+ * (the same entry points), every tracker and comb kernel compares each index
+ * it computes into a table (cell, material, group, time bin, window bin), a
+ * tally (shared, step or global slices), a warp's particle pool or stack of
+ * split children, an input bank or the comb's output with the extent of what
+ * it indexes, before the access.  A bad index skips the access (its particle
+ * or copy is lost) and the call that ran the kernel returns MCDC_ERR_CHECK,
+ * mcdc_last_error naming the first failing site and its index.  Returns 1 in
+ * the checked build, 0 in the normal one (which has no checks: its kernels
+ * are compiled without them).  mcdc_run_noalloc reports no device errors,
+ * checks included. */
+int mcdc_build_checked(void);
+
+/* Self-test of the checks: one warp indexes a 16-entry shared array at its
+ * lane number (half of the lanes beyond the end), each access behind its
+ * check and also behind an explicit bound, so no build accesses out of
+ * bounds.  words[0..4] receives the kernel's error words (flags, site, index
+ * low word, index high word) and the number of accesses made (16): in the
+ * checked build flag 4, site 12 (the self-test) and an index in 16..31; in
+ * the normal build zeros.  words: 5 host words, caller-owned.
+ * Errors: MCDC_ERR_INVALID (NULL), MCDC_ERR_NO_DEVICE, MCDC_ERR_OOM, MCDC_ERR_CUDA. */
+int mcdc_check_selftest(int32_t *words);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *mcdc_last_error(void);

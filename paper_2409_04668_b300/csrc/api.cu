@@ -1415,6 +1415,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
       c.temp = pr->pc_temp;
       c.temp_bytes = pr->pc_temp_bytes;
       c.stats = pr->stats;
+      c.error = pr->error;
       CK(comb_bank(pr->key, s, c));
       CK(cudaMemsetAsync(pr->pc_cnt + 2, 0, sizeof(unsigned long long), s));
       A.spill_in = pr->pc_combed;
@@ -1526,7 +1527,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
   if (a->records && !rec_dev)
     CK(cudaMemcpyAsync(a->records, rec_buf, n_rec * sizeof(Record), d2h, s));
   CK(cudaMemcpyAsync(pr->h_stats, pr->stats, sizeof(Stats), d2h, s));
-  CK(cudaMemcpyAsync(pr->h_error, pr->error, sizeof(int32_t), d2h, s));
+  CK(cudaMemcpyAsync(pr->h_error, pr->error, 4 * sizeof(int32_t), d2h, s));
   double region_h[5] = {0, 0, 0, 0, 0};
   const bool want_region = a->scalar_out || (comb && a->scalar_parts_out);
   const bool need_sync = (s == nullptr) || stats || want_region || (a->mean_out && !mean_dev) ||
@@ -1579,6 +1580,7 @@ int mcdc_run_ex(struct mcdc_problem *pr, const mcdc_run_args *a, mcdc_stats *sta
     stats->n_batches = B;
     stats->warp_aggregate = pr->warp_aggregate;
   }
+  if (*pr->h_error & ERRBIT_CHECK) return fail(MCDC_ERR_CHECK, check_message(pr->h_error));
   if (*pr->h_error & ERRBIT_OVERFLOW)
     return fail(MCDC_ERR_BANK_OVERFLOW, "split children overflowed the warp stacks or the device-wide spill bank");
   if (*pr->h_error & ERRBIT_TIMEOUT) return fail(MCDC_ERR_TIMEOUT, "a bounded device wait gave up");

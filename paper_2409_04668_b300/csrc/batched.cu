@@ -444,9 +444,9 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     for (int i = 0; i < n; ++i)
       CKB(cudaMemcpyAsync(&reg[2 * i], probs[i]->region, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   Stats h;
-  int32_t herr = 0;
+  int32_t herr_w[4] = {0, 0, 0, 0};
   CKB(cudaMemcpyAsync(&h, pl->d_stats, sizeof(Stats), cudaMemcpyDeviceToHost, st));
-  CKB(cudaMemcpyAsync(&herr, pl->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKB(cudaMemcpyAsync(herr_w, pl->d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CKB(cudaStreamSynchronize(st));
   if (scalar_out) {
     for (int i = 0; i < n; ++i) {
@@ -482,7 +482,8 @@ int run_batched(struct mcdc_problem *const *probs, int32_t n, const uint64_t *n_
     stats->tally_mode = MCDC_TALLY_GLOBAL;
     stats->n_batches = B;
   }
-  if (herr) return fail(MCDC_ERR_BANK_OVERFLOW, "device error flag set");
+  if (herr_w[0] & ERRBIT_CHECK) return fail(MCDC_ERR_CHECK, mcdc::check_message(herr_w));
+  if (herr_w[0]) return fail(MCDC_ERR_BANK_OVERFLOW, "device error flag set");
   return MCDC_OK;
 }
 

@@ -129,6 +129,7 @@ __global__ void k_comb_teeth(CombArgs c) {
     while (j < s1 && !(c.w[j] > 0.0)) ++j;
     const int k1 = j < s1 ? c.key[j] : c.M;
     if (k1 <= k0) continue;
+    if (!MCDC_CHK(c.error, CHK_COMB_IN, i < c.bank_cap, i)) continue;
     PartOf<PR> parent;
     in.load(i, parent, DIM);
     const R wc = (R)wn;
@@ -139,6 +140,9 @@ __global__ void k_comb_teeth(CombArgs c) {
       p.ctr = 0;
       p.tau = -1.0f;            // FP32 modes: every copy draws its own optical depth
       p.w = wc;
+      if (!MCDC_CHK(c.error, CHK_COMB_OUT,
+                    k >= 0 && (long long)chunk * c.M + k < c.out_cap, (long long)chunk * c.M + k))
+        continue;
       out.store(chunk * c.M + k, p, DIM);
     }
   }

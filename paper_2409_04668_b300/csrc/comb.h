@@ -41,6 +41,7 @@ struct CombArgs {
   void *temp;                   // CUB scratch
   size_t temp_bytes;
   Stats *stats;
+  int32_t *error;               // the run's error words (bounds checks of the checked build)
 };
 
 // CUB scratch bytes for up to cap input positions.

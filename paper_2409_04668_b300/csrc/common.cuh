@@ -13,7 +13,52 @@ constexpr int kWarp = 32;
 enum End : int32_t { END_NONE = 0, END_ABSORBED = 1, END_LEAKED = 2, END_CENSUSED = 3,
                      END_ROULETTE = 4 };
 
-enum ErrBits : int32_t { ERRBIT_OVERFLOW = 1, ERRBIT_TIMEOUT = 2 };
+enum ErrBits : int32_t { ERRBIT_OVERFLOW = 1, ERRBIT_TIMEOUT = 2, ERRBIT_CHECK = 4 };
+
+// Bounds checks of the checked build (compiled with -DMCDC_CHECKS): each
+// index a kernel computes into a table, a tally, a stack, a bank or a record
+// array is compared with the extent of what it indexes before the access.  A
+// bad one sets ERRBIT_CHECK in error[0], the first failing site and its index
+// go to error[1] and error[2..3] (low, high word), and the access is skipped.
+// In the normal build every check is the constant `true` and its operands are
+// not evaluated, so the checks leave no code behind.
+enum CheckSite : int32_t {
+  CHK_NONE = 0,
+  CHK_CELL = 1,        // cell index of a particle (flight, collision, window)
+  CHK_GROUP = 2,       // energy group of a particle (shared cross-section tables)
+  CHK_MATERIAL = 3,    // material id of a cell
+  CHK_TBIN = 4,        // time bin of a scoring particle
+  CHK_TALLY = 5,       // tally entry (shared, step or global slices)
+  CHK_WW_BIN = 6,      // window-table entry
+  CHK_POOL = 7,        // slot of a warp's particle pool
+  CHK_STACK = 8,       // warp stack of split children (push or pop)
+  CHK_SPILL_IN = 9,    // position in the bank a pass runs
+  CHK_COMB_OUT = 10,   // comb output slot
+  CHK_COMB_IN = 11,    // comb input position
+  CHK_SELFTEST = 12,   // the checked build's self-test
+  CHK_SITES = 13
+};
+
+#ifdef MCDC_CHECKS
+static __device__ __noinline__ bool check_failed(int32_t *err, int32_t site, long long idx) {
+  if (err != nullptr) {
+    atomicOr(err, ERRBIT_CHECK);
+    if (atomicCAS(err + 1, 0, site) == 0) {
+      err[2] = (int32_t)(idx & 0xFFFFFFFFll);
+      err[3] = (int32_t)(idx >> 32);
+    }
+  }
+  return false;
+}
+#define MCDC_CHK(err, site, ok, idx) \
+  ((ok) ? true : ::mcdc::check_failed((err), (site), (long long)(idx)))
+#define MCDC_CHECKED_ONLY(x) (x)     // an operand only the checks use
+constexpr bool kChecked = true;
+#else
+#define MCDC_CHK(err, site, ok, idx) true
+#define MCDC_CHECKED_ONLY(x) 0
+constexpr bool kChecked = false;
+#endif
 
 // Problem tables in device memory (built once at create).
 struct DevProblem {

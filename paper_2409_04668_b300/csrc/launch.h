@@ -116,6 +116,8 @@ void combine_scalar(const double r[5], uint64_t n_hist, int n_batches, double vo
 
 // Records the calling thread's error message (read by mcdc_last_error).
 int set_error(int code, const std::string &msg);
+// message of a failed bounds check from a run's error words (checked build)
+std::string check_message(const int32_t *words);
 }  // namespace mcdc
 struct mcdc_problem;
 namespace mcdc {

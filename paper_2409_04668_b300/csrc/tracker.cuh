@@ -452,6 +452,7 @@ __device__ bool weight_window(const DevProblem &P, const Tables<typename PR::R> 
   } else {
     const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
     const int bin = bin_index(P, cell, p.g, p.tbin);
+    if (!MCDC_CHK(A.error, CHK_WW_BIN, bin >= 0 && bin < P.n_bins, bin)) return true;
     if constexpr (PR::kF64) wl = tb.ww[bin]; else wl = tb.ww32[bin];
   }
   return ww_apply<PR, DIM>(P, A, es, p, wl, s_novf, ovf);
@@ -576,6 +577,13 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
                                       int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
+  if (!MCDC_CHK(A.error, CHK_CELL, cell >= 0 && cell < P.n_cells, cell) ||
+      !MCDC_CHK(A.error, CHK_GROUP, p.g >= 0 && p.g < P.G, p.g) ||
+      !MCDC_CHK(A.error, CHK_MATERIAL, __ldg(P.material + cell) < P.M, __ldg(P.material + cell))) {
+    bin = -1; score = (R)0;
+    end = END_LEAKED;
+    return OUT_DEAD;
+  }
   const int m = __ldg(P.material + cell);
   const int mg = m * P.G + p.g;
   const R sig_t = tb.sigma_t[mg];
@@ -690,6 +698,7 @@ __device__ __forceinline__ int flight(const DevProblem &P, const Tables<typename
   if (P.estimator != 1) {         // track-length estimator (alone or combined)
     bin = bin_index(P, cell, p.g, p.tbin);
     score = p.w * d;
+    if (!MCDC_CHK(A.error, CHK_TBIN, P.T == 0 || (p.tbin >= 0 && p.tbin < P.T), p.tbin)) bin = -1;
   }
 
   // move_particle (Figure "jitfunctions"): x += u d, t += d / v
@@ -770,6 +779,12 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
                                         bool &ww_pend) {
   using R = typename PR::R;
   const int cell = cell_index<DIM>(P, p.i, p.j, p.k);
+  if (!MCDC_CHK(A.error, CHK_CELL, cell >= 0 && cell < P.n_cells, cell) ||
+      !MCDC_CHK(A.error, CHK_GROUP, p.g >= 0 && p.g < P.G, p.g) ||
+      !MCDC_CHK(A.error, CHK_MATERIAL, __ldg(P.material + cell) < P.M, __ldg(P.material + cell))) {
+    end = END_ABSORBED;
+    return false;
+  }
   const int m = __ldg(P.material + cell);
   const int mg = m * P.G + p.g;
   p.ncol += 1;
@@ -777,6 +792,7 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
   if (P.estimator != 0) {         // collision estimator (alone or combined)
     cbin = bin_index(P, cell, p.g, p.tbin);
     cscore = p.w / tb.sigma_t[mg];
+    if (!MCDC_CHK(A.error, CHK_TBIN, P.T == 0 || (p.tbin >= 0 && p.tbin < P.T), p.tbin)) cbin = -1;
   }
   const U4 r1 = draw(p, p.ctr, A.rk);
   // FP32 modes with the optical depth carried use one 24-bit number per
@@ -837,8 +853,10 @@ __device__ __forceinline__ bool collide(const DevProblem &P, const Tables<typena
 template <class TT, class R>
 __device__ __forceinline__ void tally_scatter(TT *stally, double *gtally, float *gtally32,
                                               bool shared_mode, bool aggregate, bool valid,
-                                              int bin, R score, long long goff = 0) {
+                                              int bin, R score, long long goff, int32_t *err,
+                                              long long extent) {
   bool act = valid && bin >= 0;
+  if (act && !MCDC_CHK(err, CHK_TALLY, goff + bin < extent, goff + bin)) act = false;
   R v = score;
   if (aggregate) {
     // lanes scoring into the same bin add their scores first; the lowest
@@ -1412,7 +1430,19 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
     int rtop = 0, ctop = 0;          // identical in every lane
     bool exhausted = false;
     const uint32_t lt = lanemask_lt();
-    auto slot_of = [&](int s) { return pool0 + min(max(s, 0), kPool - 1); };
+    auto slot_of = [&](int s) {
+      (void)MCDC_CHK(A.error, CHK_POOL, s >= 0 && s < kPool, s);
+      return pool0 + min(max(s, 0), kPool - 1);
+    };
+#ifdef MCDC_CHECKS
+    // entries of the tally a scatter indexes: the step tally, the CTA's
+    // shared tally, or the global tally (one slice per batch when per batch)
+    auto tally_extent = [&](bool step) -> long long {
+      if (step) return step_bins;
+      if (SHARED) return P.n_tally;
+      return (A.tally_per_batch ? (long long)A.n_batches : 1ll) * P.n_tally;
+    };
+#endif
     // population control (lane 0): the first of the next 32 input positions,
     // from the warp's reservation, which one atomic refills kReserve at a
     // time (a claim per 32 would hold the warp for an atomic's round trip
@@ -1457,11 +1487,13 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             if (step_tally)
               tally_scatter<TT, R>(stally, A.tally, A.tally32, true, agg, mine,
                                    (mine && cbin >= 0) ? step_bin(P, A, q.hid, cbin, P.estimator == 2)
-                                                       : -1, cscore);
+                                                       : -1, cscore, 0, A.error,
+                                   MCDC_CHECKED_ONLY(tally_extent(true)));
             else
               tally_scatter<TT, R>(stally, A.tally, A.tally32, SHARED, agg, mine,
                                    (SHARED && mine) ? cbin + (int)coff : cbin, cscore,
-                                   mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0);
+                                   mine ? tally_offset(P, A, q.hid) + (SHARED ? 0 : coff) : 0,
+                                   A.error, MCDC_CHECKED_ONLY(tally_extent(false)));
           }
           if ((VR || NET || PC) && P.implicit) {
             // weight removed by implicit capture: one shared add per warp
@@ -1558,11 +1590,20 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         PartOf<PR> q;
         if (lane < nb) {
           if (lane < n_o) {
-            q = ovf[top - 1 - lane];
-            alive = true;
+            if (MCDC_CHK(A.error, CHK_STACK,
+                         top - 1 - lane >= 0 &&
+                             top - 1 - lane < (MULTI ? Ain.overflow_cap : A.overflow_cap),
+                         top - 1 - lane)) {
+              q = ovf[top - 1 - lane];
+              alive = true;
+            }
           } else if (kSpillIn && A.spill_in != nullptr && !MULTI) {
             const long long at = (long long)h_first + (lane - n_o);
-            if (staged)                      // staged by the bulk copies
+            const bool in_ok =
+                MCDC_CHK(A.error, CHK_SPILL_IN, at >= 0 && (unsigned long long)at < s_in_total, at);
+            if (!in_ok) {
+              // not read: the particle is lost and the run reports the check
+            } else if (staged)               // staged by the bulk copies
               stage.load(lane, q, DIM);
             else if (PC && A.census_out != nullptr)     // population control: the combed bank (pool layout)
               bank_view<PR>(const_cast<void *>(A.spill_in), (long long)A.spill_cap, DIM)
@@ -1570,7 +1611,7 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
             else
               q = reinterpret_cast<const PartOf<PR> *>(A.spill_in)[at];
             if (use_slot) q.slot = (uint32_t)at;             // position in the step's input
-            alive = true;
+            alive = in_ok;
           } else {
             source_particle<PR, DIM>(P, tb, A.rk, A.offset + h_first + (lane - n_o), q);
             if (use_slot) q.slot = (uint32_t)(h_first + (lane - n_o));   // history's position in the run
@@ -1670,10 +1711,12 @@ __global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunAr
         }
         if (step_tally)
           tally_scatter<TT, R>(stally, A.tally, A.tally32, true, agg, flew,
-                               (flew && bin >= 0) ? step_bin(P, A, p.hid, bin, 0) : -1, score);
+                               (flew && bin >= 0) ? step_bin(P, A, p.hid, bin, 0) : -1, score, 0,
+                               A.error, MCDC_CHECKED_ONLY(tally_extent(true)));
         else
           tally_scatter<TT, R>(stally, A.tally, A.tally32, SHARED, agg, flew, bin, score,
-                               flew ? tally_offset(P, A, p.hid) : 0);
+                               flew ? tally_offset(P, A, p.hid) : 0, A.error,
+                               MCDC_CHECKED_ONLY(tally_extent(false)));
         if constexpr (NET && !PR::kF64) {
           // the pass's crossing window checks, together
           const bool chk = has && outcome == OUT_WW;

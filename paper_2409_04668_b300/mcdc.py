@@ -8,7 +8,10 @@ The low-level functions keep the C names (``mcdc_problem_create``,
 ``data_ptr``); the run's stream is torch's current stream unless given.
 
 Importing this module loads ``libmcdc_b300.so`` and raises if it is missing:
-there is no fallback path.
+there is no fallback path.  With the environment variable ``MCDC_CHECKS=1``
+it loads the checked build ``libmcdc_b300_checks.so`` instead (the same entry
+points; every kernel index bounds-checked, a failure returned as
+``MCDC_ERR_CHECK``).
 """
 from __future__ import annotations
 
@@ -18,11 +21,13 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmcdc_b300.so")
+LIB_NAME = "libmcdc_b300_checks.so" if os.environ.get("MCDC_CHECKS") == "1" else "libmcdc_b300.so"
+LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 MCDC_OK = 0
 MCDC_ERR_INVALID, MCDC_ERR_OOM, MCDC_ERR_CUDA = -1, -2, -3
 MCDC_ERR_BANK_OVERFLOW, MCDC_ERR_TIMEOUT, MCDC_ERR_NO_DEVICE = -4, -5, -6
+MCDC_ERR_CHECK = -7
 PREC_FP64, PREC_FP32, PREC_FP32_LOCAL = 0, 1, 2
 TALLY_AUTO, TALLY_SHARED, TALLY_GLOBAL = 0, 1, 2
 EST_TRACK, EST_COLLISION, EST_COMBINED = 0, 1, 2
@@ -152,6 +157,8 @@ SIGNATURES = {
     "mcdc_network_window_lower": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_int64, C.c_void_p]),
     "mcdc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mcdc_build_checked": (C.c_int, []),
+    "mcdc_check_selftest": (C.c_int, [C.c_void_p]),
     "mcdc_last_error": (C.c_char_p, []),
 }
 
@@ -190,6 +197,8 @@ mcdc_set_network_windows = _lib.mcdc_set_network_windows
 mcdc_get_weight_windows = _lib.mcdc_get_weight_windows
 mcdc_network_window_lower = _lib.mcdc_network_window_lower
 mcdc_philox = _lib.mcdc_philox
+mcdc_build_checked = _lib.mcdc_build_checked
+mcdc_check_selftest = _lib.mcdc_check_selftest
 mcdc_last_error = _lib.mcdc_last_error
 
 
@@ -466,6 +475,20 @@ def measure_fp64_pipe():
     a, c = C.c_double(), C.c_double()
     check(mcdc_measure_fp64_pipe(C.byref(a), C.byref(c)))
     return a.value, c.value
+
+
+def build_checked():
+    """True when the loaded library is the checked build (mcdc_build_checked)."""
+    return bool(mcdc_build_checked())
+
+
+def check_selftest():
+    """The checks' self-test kernel (mcdc_check_selftest): the error words
+    (flags, site, index low, index high) and the accesses made."""
+    w = np.zeros(5, dtype=np.int32)
+    check(mcdc_check_selftest(w.ctypes.data))
+    idx = (int(np.uint32(w[3])) << 32) | int(np.uint32(w[2]))
+    return {"flags": int(w[0]), "site": int(w[1]), "index": idx, "made": int(w[4])}
 
 
 def set_wait_limit(tries):

@@ -45,6 +45,33 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in lib.SIGNATURES, name
 
 
+def test_checked_build_loads_and_exports_every_declared_symbol(lib):
+    """The bounds-checked twin (-DMCDC_CHECKS) builds, exports the same
+    boundary and says it is checked; the normal build says it is not (no
+    device is needed for either answer)."""
+    path = B.build(checked=True)
+    raw = C.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+    raw.mcdc_build_checked.restype = C.c_int
+    assert raw.mcdc_build_checked() == 1
+    assert lib.build_checked() is (os.environ.get("MCDC_CHECKS") == "1")
+    words = np.zeros(5, dtype=np.int32)
+    raw.mcdc_check_selftest.restype = C.c_int
+    raw.mcdc_check_selftest.argtypes = [C.c_void_p]
+    if not _has_gpu():
+        assert raw.mcdc_check_selftest(None) == lib.MCDC_ERR_INVALID
+        assert raw.mcdc_check_selftest(words.ctypes.data) == lib.MCDC_ERR_NO_DEVICE
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
 def _create(lib, prob, **kw):
     try:
         P = lib.Problem(prob, **kw)
