@@ -600,6 +600,15 @@ def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, s
         mean = torch.zeros(P.n_bins, dtype=torch.float64, device=dev)
         rel = torch.zeros_like(mean)
         P.run_ex(1_000_000, seed0, mean=mean, relerr=rel)        # warm-up
+        # the learned pipeline warms up too: its kernels (training, bake,
+        # weighted tracker; the distillation when per event) load on their
+        # first use, a once-per-process cost like the analog kernel's above.
+        # One short fit on the warm-up tally and a 1000-history run with its
+        # windows; then the problem is analog again for the pilot
+        P.train_importance(mean, rel, epochs=1, batch=fit_batch, min_ratio=1e-20,
+                           per_event=int(per_event), distill_steps=16, **WW_SETTINGS)
+        P.run_ex(1000, seed0 + 999, batches=ww_batches)
+        P.set_weight_windows(None)
         (st, (m_a, r_a)), wall_a = _timed(lambda: P.run_ex(n_analog, seed0, mean=mean, relerr=rel))
         t_a = st["kernel_ms"] / 1e3
         nb_a = st["n_batches"]

@@ -296,6 +296,8 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   const bool f64 = pr->key.f64;
   int block = o.block_size > 0 ? o.block_size : 256;
   if (block % 32 != 0 || block > 512) return fail(MCDC_ERR_INVALID, "block_size must be a multiple of 32, <= 512");
+  // the network instantiations are built for at most kNetBlockMax threads
+  if (pr->key.net && block > kNetBlockMax) block = kNetBlockMax;
   // every warp parks up to kPool particles besides its 32 in flight
   const int S = (block / 32) * kPool;
   int mode = o.tally_mode;
@@ -1058,6 +1060,8 @@ int mcdc_set_weight_windows(struct mcdc_problem *pr, const double *w_lower, doub
   pr->P.ww_netfrag = nullptr;
   pr->P.ww_upper = upper_ratio;
   pr->P.ww_survival = survival_ratio;
+  pr->P.ww_upper32 = (float)upper_ratio;
+  pr->P.ww_survival32 = (float)survival_ratio;
   pr->P.ww_nmax = nmax;
   if (int rc = set_track_kernel_impl(pr, false, true)) return rc;
   return ensure_overflow(pr);
@@ -1147,6 +1151,13 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   P.ww_net_wl0 = source_wl;
   P.ww_upper = upper_ratio;
   P.ww_survival = survival_ratio;
+  P.ww_net_shift32 = (float)shift;
+  P.ww_net_scale32 = (float)scale;
+  P.ww_net_top32 = (float)top;
+  P.ww_net_floor32 = (float)floor_lp;
+  P.ww_net_wl0_32 = (float)source_wl;
+  P.ww_upper32 = (float)upper_ratio;
+  P.ww_survival32 = (float)survival_ratio;
   P.ww_nmax = nmax;
   return ensure_overflow(pr);
 }

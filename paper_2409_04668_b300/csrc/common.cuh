@@ -99,13 +99,17 @@ struct DevProblem {
   // map of its output y to w_L = wl0 exp(min(0, max(y scale + shift, floor) - top))
   const double *ww_net64;
   const float *ww_net32;
-  const uint32_t *ww_netfrag; // the same network as BF16 mma.sync fragments (FP32 modes)
+  const uint32_t *ww_netfrag; // the same network as binary16 mma.sync fragments (FP32 modes)
   float ww_net_b3;            // its output bias
   float net_cell[3], net_off[3];   // input of axis a: cell i, offset o in it -> i net_cell[a]
                                    // + o net_off[a] - 1 (2 / n, 2 / (n width); 0 unbounded)
   int32_t ww_net_in, ww_net_h;
   double ww_net_shift, ww_net_scale, ww_net_top, ww_net_floor, ww_net_wl0;
   double ww_upper, ww_survival;
+  // FP32 copies (rounded to nearest on the host) for the FP32 modes' checks:
+  // a conversion in the kernel would occupy the FP64 pipe at every check
+  float ww_net_shift32, ww_net_scale32, ww_net_top32, ww_net_floor32, ww_net_wl0_32;
+  float ww_upper32, ww_survival32;
   int32_t ww_nmax;
   int32_t region_lo[3], region_hi[3];
   // estimator and collision physics options

@@ -1670,6 +1670,8 @@ extern "C" int mcdc_train_importance(struct mcdc_problem *pr, const double *pilo
       pr->P.ww_netfrag = nullptr;
       pr->P.ww_upper = o.upper_ratio;
       pr->P.ww_survival = o.survival_ratio;
+      pr->P.ww_upper32 = (float)o.upper_ratio;
+      pr->P.ww_survival32 = (float)o.survival_ratio;
       pr->P.ww_nmax = o.nmax;
       if (int rc = mcdc::set_track_kernel(pr, false, true)) return rc;
       if (int rc = mcdc::ensure_overflow_for(pr)) return rc;

@@ -55,7 +55,7 @@ struct mcdc_problem {
   double *net64 = nullptr;      // per-event windows: network parameters
   float *net32 = nullptr;
   size_t net_cap = 0;
-  uint32_t *netfrag = nullptr;  // the same network as BF16 mma.sync fragments (kNetFragWords)
+  uint32_t *netfrag = nullptr;  // the same network as binary16 mma.sync fragments (kNetFragWords)
   // population control: census bank (by input position), combed bank and
   // the comb's scratch
   int pc_cap = 0;                          // input positions the census bank holds

@@ -193,6 +193,10 @@ constexpr int kNetFragBytes = kNetFragWords * 4;     // 13824, a multiple of 16
 // outputs of its rows
 constexpr int kNetRowBytes = 80;
 constexpr int kNetWarpBytes = 32 * kNetRowBytes + 32 * 4;
+// threads per CTA of the network instantiations: at most 384, so that each
+// thread may hold 168 registers (the evaluation's fragments and accumulators
+// on top of the event loop's state) where 512 threads would cap it at 128
+constexpr int kNetBlockMax = 384;
 
 __host__ __device__ inline int align16(long long v) { return (int)((v + 15) & ~15ll); }
 
@@ -359,7 +363,8 @@ __device__ bool ww_apply(const DevProblem &P, const RunArgs &A, const EndSink &e
                          PartOf<PR> &p, typename PR::R wl, int *s_novf, PartOf<PR> *ovf) {
   using R = typename PR::R;
   if (!(wl > (R)0)) return true;
-  const R wu = (R)P.ww_upper * wl;
+  R wu;
+  if constexpr (PR::kF64) wu = P.ww_upper * wl; else wu = P.ww_upper32 * wl;
   if (p.w > wu) {
     const R nd = ceil(p.w / wu);
     const int n = nd > (R)P.ww_nmax ? P.ww_nmax : (int)nd;
@@ -420,7 +425,8 @@ __device__ bool ww_apply(const DevProblem &P, const RunArgs &A, const EndSink &e
     return true;
   }
   if (p.w < wl) {
-    const R ws = (R)P.ww_survival * wl;
+    R ws;
+    if constexpr (PR::kF64) ws = P.ww_survival * wl; else ws = P.ww_survival32 * wl;
     const U4 r = draw(p, p.ctr, A.rk);
     R xi;
     if constexpr (PR::kF64) xi = u01_f64(r.a, r.b); else xi = u01_f32(r.a);
@@ -1125,9 +1131,8 @@ __device__ __forceinline__ float net_lower_warp(const DevProblem &P, const uint3
   const float y = net_y_warp(nf, tile, f[0], f[1], f[2], f[3], chk ? p.g : 0, chk,
                              P.ww_net_in, P.ww_net_h, P.ww_net_b3);
   if (!chk) return 0.0f;
-  const float lp = fmaxf(fmaf(y, (float)P.ww_net_scale, (float)P.ww_net_shift),
-                         (float)P.ww_net_floor);
-  return (float)P.ww_net_wl0 * __expf(fminf(lp - (float)P.ww_net_top, 0.0f));
+  const float lp = fmaxf(fmaf(y, P.ww_net_scale32, P.ww_net_shift32), P.ww_net_floor32);
+  return P.ww_net_wl0_32 * __expf(fminf(lp - P.ww_net_top32, 0.0f));
 }
 
 // The window checks of every lane with chk set, together.  Returns false for
@@ -1247,7 +1252,7 @@ struct MultiArgs {
 // children) and implicit capture, which analog kernels leave out.
 template <class PR, bool SHARED, int DIM, bool MULTI, bool NET = false, bool PC = false,
           bool VR = false>
-__global__ void __launch_bounds__(512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
+__global__ void __launch_bounds__(NET ? kNetBlockMax : 512) k_track(const DevProblem Pin, const RunArgs Ain, const Layout L,
                                                const MultiArgs MA) {
   using R = typename PR::R;
   using TT = typename PR::TT;
