@@ -775,8 +775,8 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207), per_event=False, match_r
 MEASURED_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the timed
     # tracker launches of the bench's own configuration
-    ("c2_slab_20cm_2region_td", "fp32_local", 1): (475221, "bfb7819593d028a9"),
-    ("c3_channel_60cube_7g_td", "fp32_local", 2): (364587093, "bfb7819593d028a9"),
+    ("c2_slab_20cm_2region_td", "fp32_local", 1): (437845, "77cbbe5068197735"),
+    ("c3_channel_60cube_7g_td", "fp32_local", 2): (364660053, "77cbbe5068197735"),
 }
 
 
