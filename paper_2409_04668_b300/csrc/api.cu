@@ -296,8 +296,10 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   const bool f64 = pr->key.f64;
   int block = o.block_size > 0 ? o.block_size : 256;
   if (block % 32 != 0 || block > 512) return fail(MCDC_ERR_INVALID, "block_size must be a multiple of 32, <= 512");
-  // the network instantiations are built for at most kNetBlockMax threads
-  if (pr->key.net && block > kNetBlockMax) block = kNetBlockMax;
+  // the network instantiations are built for at most kNetBlockMax threads:
+  // they take that many (their registers allow one such CTA per SM) unless
+  // the caller asked for fewer
+  if (pr->key.net) block = pr->user_block > 0 ? std::min(pr->user_block, kNetBlockMax) : kNetBlockMax;
   // every warp parks up to kPool particles besides its 32 in flight
   const int S = (block / 32) * kPool;
   int mode = o.tally_mode;
@@ -323,8 +325,11 @@ int choose_shape(mcdc_problem *pr, const DeviceLimits &dl) {
   int cps = track_occupancy(pr->key, block, L.total);
   if (cps < 1) return fail(MCDC_ERR_INVALID, "launch shape does not fit on an SM (registers or shared memory)");
   if (o.ctas_per_sm > 0) {
-    if (o.ctas_per_sm > cps) return fail(MCDC_ERR_INVALID, "ctas_per_sm exceeds what fits on an SM");
-    cps = o.ctas_per_sm;
+    // the tuner's choice for another instantiation: as many as fit when fewer
+    // fit here; the caller's own choice must fit
+    if (o.ctas_per_sm > cps && (pr->user_cps > 0 || !pr->key.net))
+      return fail(MCDC_ERR_INVALID, "ctas_per_sm exceeds what fits on an SM");
+    cps = std::min(cps, o.ctas_per_sm);
   }
   pr->block = block;
   pr->S = S;
@@ -881,6 +886,7 @@ int mcdc_problem_create(const mcdc_mesh *mesh, const mcdc_materials *mat, const 
   pr->opt = o;
   pr->user_aggregate = o.warp_aggregate;
   pr->user_cps = o.ctas_per_sm;
+  pr->user_block = o.block_size;
   pr->edges = edges;
   DevProblem &P = pr->P;
   for (int a = 0; a < 3; ++a) {

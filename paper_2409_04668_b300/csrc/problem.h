@@ -11,6 +11,7 @@ struct mcdc_problem {
   uint64_t uid = 0;             // unique over the process (batched-run plans key on it)
   int user_aggregate = 0;       // the caller's warp_aggregate and ctas_per_sm (0: the tuner's)
   int user_cps = 0;
+  int user_block = 0;           // the caller's block_size (0: the tuner's)
   uint64_t p_version = 0;       // bumped whenever P changes after create (windows):
                                 // cached batched plans hold a copy of P
   int device = 0;
