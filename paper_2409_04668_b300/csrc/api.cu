@@ -1131,9 +1131,11 @@ int mcdc_set_network_windows(struct mcdc_problem *pr, const float *params, int32
   CK(cudaMemcpy(pr->net32, h32.data(), n * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(pr->netfrag, frag.data(), (size_t)kNetFragBytes, cudaMemcpyHostToDevice));
   // the network kernel first: if its launch shape fails, nothing changes
+  // (the kernel of the windows already set, table or network, stays)
+  const bool prev_net = pr->key.net, prev_ww = pr->P.ww_lower != nullptr;
   if (int rc = set_track_kernel_impl(pr, true, false)) {
     const std::string msg = g_err;
-    set_track_kernel_impl(pr, false, false);
+    set_track_kernel_impl(pr, prev_net, prev_ww);
     return fail(rc, msg);
   }
   DevProblem &P = pr->P;

@@ -151,6 +151,41 @@ def test_switching_and_refusals(mcdc):
             P.set_network_windows(p, 8, np.nan, 1.0, 0.0, -3.0, 0.3)
 
 
+def test_network_kernels_take_their_own_launch_shape(mcdc):
+    """The network instantiations run 384 threads per CTA whatever shape the
+    autotuner chose for the analog kernel (their registers fit one such CTA
+    per SM), fewer only when the caller asked for fewer; the caller's own
+    CTAs per SM must fit.  Turning the windows off restores the analog shape."""
+    prob = W.c2_two_region()
+    p = _params(5, 8, seed=2)
+    c = _consts(8, shift=0.0, scale=1.0, top=0.0, floor=-3.0, wl0=0.3)
+    for kw, want in (({}, 384), ({"block_size": 512}, 384), ({"block_size": 256}, 256)):
+        with mcdc.Problem(prob, precision=mcdc.PREC_FP32_LOCAL, tally_mode=mcdc.TALLY_GLOBAL,
+                          **kw) as P:
+            st0, _ = P.run_ex(20_000, 3, batches=4)
+            P.set_network_windows(p, 8, c["shift"], c["scale"], c["top"], c["floor"], c["wl0"])
+            st, _ = P.run_ex(20_000, 3, batches=4)
+            assert st["block_size"] == want, (kw, st["block_size"])
+            assert st["ctas_per_sm"] >= 1
+            P.set_network_windows(None, 8, 0.0, 1.0, 0.0, -3.0, 0.3)
+            st1, _ = P.run_ex(20_000, 3, batches=4)
+            assert (st1["block_size"], st1["ctas_per_sm"]) == (st0["block_size"], st0["ctas_per_sm"])
+            assert st1["segments"] == st0["segments"]
+    with mcdc.Problem(prob, precision=mcdc.PREC_FP32_LOCAL, tally_mode=mcdc.TALLY_GLOBAL,
+                      block_size=256, ctas_per_sm=2) as P:
+        st0, _ = P.run_ex(20_000, 3, batches=4)
+        P.set_weight_windows(np.full(P.n_bins, 0.1), 5.0, 2.5, 16)   # w = 1 splits in two
+        stw, _ = P.run_ex(20_000, 3, batches=4)
+        with pytest.raises(mcdc.MCDCError, match="ctas_per_sm"):
+            P.set_network_windows(p, 8, c["shift"], c["scale"], c["top"], c["floor"], c["wl0"])
+        # the refused network left the table windows and their kernel in place
+        st, _ = P.run_ex(20_000, 3, batches=4)
+        assert (st["block_size"], st["ctas_per_sm"]) == (256, 2)
+        for k in ("segments", "splits", "roulette_killed"):
+            assert st[k] == stw[k], k
+        assert stw["splits"] + stw["roulette_killed"] > 0 and st0["splits"] == 0
+
+
 @pytest.mark.parametrize("time_resolved", [0, 1])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_local"])
 def test_trained_network_per_event_is_unbiased(mcdc, time_resolved, prec):
