@@ -813,7 +813,8 @@ def roofline(prob, seg_rate, pk, tally_mode, prec_name, measured_fp64=None):
     optical-depth update 2, lookup 3, face 4, census 3, nearest event 4,
     tally 4, move 4, resolution 4, collisions 18 and births 5 amortised = 52)
     against 148 SMs x 128 lanes x max SM clock.  Global tally
-    (large meshes): 16 B of FP64 read-modify-write per flight against the
+    (large meshes): a read-modify-write of the scored bin per flight, 8 B of
+    an FP32 batch slice (16 B of an FP64 bin in FP64 mode), against the
     measured copy bandwidth."""
     three_d = prob.n[1] > 1 or prob.n[2] > 1
     if tally_mode == 2 and (prec_name == "fp64" or three_d):
