@@ -97,21 +97,12 @@ __device__ __forceinline__ int first_tooth_at_or_after(double s, double xi, doub
   return k;
 }
 
-// first tooth of every banked particle (into key[], which the scan no longer needs)
-__global__ void k_comb_first(CombArgs c) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n_in; i += gridDim.x * blockDim.x) {
-    if (!(c.w[i] > 0.0)) continue;
-    const int q = c.first_step ? batch_of(c.n_hist, c.B, (uint64_t)i) : i / c.M;
-    if (c.seg[2 * c.B + q] < 0) continue;
-    c.key[i] = first_tooth_at_or_after(c.S[i], c.segd[c.B + q], c.segd[2 * c.B + q],
-                                       c.segd[3 * c.B + q], c.M);
-  }
-}
-
 // Banked particle i owns the teeth with S_i <= T_k < S_j, j the next banked
 // particle of its segment (all teeth from S_i on if there is none): the
-// assignment "last particle with S <= T_k" made per tooth.  Both banks have
-// the pool's structure-of-arrays layout.
+// assignment "last particle with S <= T_k" made per tooth.  Each thread finds
+// the first tooth at or after S_i and at or after S_j itself (a few FP64
+// operations each), so no pass writes them out first.  Both banks have the
+// pool's structure-of-arrays layout.
 template <class PR, int DIM>
 __global__ void k_comb_teeth(CombArgs c) {
   using R = typename PR::R;
@@ -123,11 +114,11 @@ __global__ void k_comb_teeth(CombArgs c) {
     const int chunk = c.seg[2 * c.B + q];
     if (chunk < 0) continue;
     const int s1 = c.seg[c.B + q];
-    const double wn = c.segd[2 * c.B + q];
-    const int k0 = c.key[i];
+    const double xi = c.segd[c.B + q], wn = c.segd[2 * c.B + q], inv = c.segd[3 * c.B + q];
+    const int k0 = first_tooth_at_or_after(c.S[i], xi, wn, inv, c.M);
     int j = i + 1;
     while (j < s1 && !(c.w[j] > 0.0)) ++j;
-    const int k1 = j < s1 ? c.key[j] : c.M;
+    const int k1 = j < s1 ? first_tooth_at_or_after(c.S[j], xi, wn, inv, c.M) : c.M;
     if (k1 <= k0) continue;
     if (!MCDC_CHK(c.error, CHK_COMB_IN, i < c.bank_cap, i)) continue;
     PartOf<PR> parent;
@@ -165,7 +156,6 @@ static cudaError_t comb_impl(cudaStream_t s, const CombArgs &c) {
                                                      ::cuda::std::equal_to<>(), s);
   if (e != cudaSuccess) return e;
   k_comb_bases<PR><<<1, 1, 0, s>>>(c);
-  k_comb_first<<<blocks, threads, 0, s>>>(c);
   if (c.dim == 3) k_comb_teeth<PR, 3><<<blocks, threads, 0, s>>>(c);
   else k_comb_teeth<PR, 1><<<blocks, threads, 0, s>>>(c);
   return cudaGetLastError();

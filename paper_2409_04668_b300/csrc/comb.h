@@ -33,8 +33,7 @@ struct CombArgs {
   int B;                        // batches
   int step;                     // index of the time bin that just ended
   RoundKeys rk;
-  int32_t *key;                 // [n_in] scratch: segment of each input position, then the
-                                //   first tooth of each banked particle
+  int32_t *key;                 // [n_in] scratch: segment of each input position (the scan's keys)
   double *S;                    // [n_in] scratch: per-segment exclusive sums of w
   int32_t *seg;                 // [3 B] scratch: per segment first, end, output chunk (-1: none)
   double *segd;                 // [4 B] scratch: per segment W, xi, W / M, M / W
