@@ -777,8 +777,8 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207, 307, 407), per_event=Fals
 MEASURED_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the timed
     # tracker launches of the bench's own configuration
-    ("c2_slab_20cm_2region_td", "fp32_local", 1): (480000, "b425ae36e0e1682b"),
-    ("c3_channel_60cube_7g_td", "fp32_local", 2): (364914261, "b425ae36e0e1682b"),
+    ("c2_slab_20cm_2region_td", "fp32_local", 1): (341333, "23d89968d84502dc"),
+    ("c3_channel_60cube_7g_td", "fp32_local", 2): (364779861, "23d89968d84502dc"),
 }
 
 
