@@ -571,7 +571,7 @@ def _timed(fn):
 
 
 def fom_deep(M, prec, n_analog=100_000_000, n_ww=100_000, refits=2, prob=None, seed0=7,
-             per_event=False, match_relerr=None, ww_batches=16, epochs=10, fit_batch=32768,
+             per_event=False, match_relerr=None, ww_batches=32, epochs=10, fit_batch=32768,
              n_refit=50_000):
     """Figure of merit 1 / (relerr^2 T) of the far-region flux on the
     deep-penetration box (30 mfp absorber between a corner source and the
@@ -751,7 +751,7 @@ def fom_over_pilots(M, prec, prob, seeds=(7, 107, 207, 307, 407), per_event=Fals
     """fom_deep for the first pilot seed in full, plus the learned FOM (and the
     ratio to analog, or its lower bound) for every seed and their medians: the
     windows depend on the pilot sample, so one seed is one draw of the whole
-    pipeline (each FOM carries the +-37 % of its 16 batches, and the pipeline
+    pipeline (each FOM carries the +-25 % of its 32 batches, and the pipeline
     scatters beyond that; the median of five is the figure reported)."""
     runs = [fom_deep(M, prec, prob=prob, seed0=s, per_event=per_event,
                      match_relerr=match_relerr if k == 0 else None)
