@@ -105,6 +105,38 @@ def test_noalloc_weight_windows_match_run_ex_twice(env):
             _close(out[3], ref[3], 1e-6)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_local"])
+def test_noalloc_network_windows_match_run_ex(env, prec):
+    """Per-event network windows (global tally, the network kernels with their
+    own launch shape and fragment block): the allocation-free run takes the
+    same kernel and makes the same splits and roulettes as mcdc_run_ex while
+    no warp stack overflows (whole stacks kept, so mcdc_run_ex spills nothing
+    either) -- FP64 tallies to 1e-9; FP32 ones to FP32 summation-order noise."""
+    M, torch = env
+    prob = _inf_medium_ww()
+    n_in, H = 3, 8
+    npar = H * n_in + H + H * H + H + H + 1
+    params = np.random.default_rng(5).normal(0.0, 0.5, npar).astype(np.float32)
+    precision = M.PREC_FP64 if prec == "fp64" else M.PREC_FP32_LOCAL
+    rtol = REL if prec == "fp64" else 1e-5
+    n, B = 5_000, 10
+    dev = torch.device("cuda", 0)
+    with M.Problem(prob, precision=precision, tally_mode=M.TALLY_GLOBAL, overflow_tail=-1) as P:
+        P.set_network_windows(params, H, 0.0, 1.5, 2.0, -4.0, 0.5, 4.0, 2.0, 4, n_in=n_in)
+        ref = [torch.zeros(P.n_bins, dtype=torch.float64, device=dev) for _ in range(2)]
+        st, _ = P.run_ex(n, 17, batches=B, sum1=ref[0], sum2=ref[1])
+        torch.cuda.synchronize()
+        assert st["splits"] > 1000 and st["roulette_killed"] > 20 and st["splits_dropped"] == 0
+        stream = torch.cuda.current_stream().cuda_stream
+        for call in range(2):
+            out = [torch.full((P.n_bins,), float("nan"), dtype=torch.float64, device=dev)
+                   for _ in range(2)]
+            P.run_noalloc(n, 17, out[0], out[1], batches=B, stream=stream)
+            torch.cuda.synchronize()
+            _close(out[0], ref[0], rtol)
+            _close(out[1], ref[1], rtol)
+
+
 def _explosive():
     nc = 40
     prob = W.slab("explosive_windows", 20.0, nc, np.zeros(nc), [[1.0]], [[0.9]], src=(0.0, 2.0))
